@@ -1,0 +1,427 @@
+"""CPU oracle for compressed patch-based relaxation (Harper & Tuminaro,
+"Compression and Reduced Representation Techniques for Patch-Based
+Relaxation", arXiv 2306.10025).
+
+TEST INFRASTRUCTURE.  This module is a plain, slow FP64 restatement of what
+the method computes, written to check the CUDA library against.  Only the test
+suite, the smoke check and the benchmark's CPU-baseline leg may import it; the
+library never calls it and has no CPU fallback.  It shares no code with the
+CUDA path: inputs come from ``problems`` (the seeded generators), everything
+else is here.
+
+Every function cites the passage it follows.  Readings adopted where the paper
+is silent or ambiguous:
+
+* Criterion form.  The paper writes d(A_i, B_j) = ||I - A_i B_j^{-1}||_2
+  (Alg. 1, Eq. 4, Eq. 5).  With B_j the stored patch A_c this equals
+  ||(A_c - A_i) B_c^{-1}||_2 exactly in real arithmetic; we evaluate that
+  "difference form", which gives exactly 0 for identical patches.
+* The 2-norm is "computed exactly by a small SVD" (section 3 remark): the
+  largest singular value from LAPACK's SVD (a library primitive).
+* Alg. 1: first match in database creation order, strict "< eps".
+* Pivoting: partial pivoting, pivot = largest |entry| in the column, lowest
+  row index on ties; a pivot with |u_kk| <= p_s * 2^-53 * max|A_k| marks the
+  patch singular.
+* Weighting: LEFT (the paper's W * sum V^T B^-1 V, Eq. 1 / Eq. 3) and SYM
+  (W^1/2 (sum V^T B^-1 V) W^1/2, which is symmetric and used with CG).
+* FGMRES residual history = |g_{j+1}| of the Givens-rotated least-squares
+  problem (the recursively updated residual norm), divided by ||r_0||.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+U_FP64 = 2.0 ** -53
+
+
+# ---------------------------------------------------------------------------
+# a1: patch extraction A_k = V_k A V_k^T   (section 2, definition of A_k)
+# ---------------------------------------------------------------------------
+
+def csr_lookup(rowptr, colidx, vals, n, rows, cols):
+    """A(rows, cols) entrywise for a CSR matrix with sorted unique columns;
+    entries absent from the pattern are 0.  Uses the row-major key
+    row*n + col, which is sorted over the whole CSR array."""
+    rowptr = np.asarray(rowptr, dtype=np.int64)
+    r_of = np.repeat(np.arange(n, dtype=np.int64), np.diff(rowptr))
+    keys = r_of * n + np.asarray(colidx, dtype=np.int64)
+    q = np.asarray(rows, dtype=np.int64) * n + np.asarray(cols, dtype=np.int64)
+    pos = np.searchsorted(keys, q)
+    pos_c = np.minimum(pos, keys.size - 1)
+    hit = (pos < keys.size) & (keys[pos_c] == q)
+    out = np.where(hit, np.asarray(vals)[pos_c], 0.0)
+    return out
+
+
+def extract_patches(rowptr, colidx, vals, n, dofs):
+    """A_k(i, j) = A(dofs[k, i], dofs[k, j]) for a (n_p, p_s) map of equal-size
+    patches (section 2: A_k = V_k A V_k^T, (V_k)_{ij} = 1 iff global DOF j is
+    local DOF i of patch k).  Returns (n_p, p_s, p_s)."""
+    dofs = np.asarray(dofs, dtype=np.int64)
+    npch, p = dofs.shape
+    rows = np.repeat(dofs, p, axis=1)          # row index dofs[k, i]
+    cols = np.tile(dofs, (1, p))               # col index dofs[k, j]
+    return csr_lookup(rowptr, colidx, vals, n, rows, cols).reshape(npch, p, p)
+
+
+def extract_patches_ragged(rowptr, colidx, vals, n, offsets, flat):
+    """Patches of varying size: list of A_k in patch order (Remark after Eq. 1)."""
+    out = []
+    for k in range(len(offsets) - 1):
+        d = np.asarray(flat[offsets[k]:offsets[k + 1]], dtype=np.int64)
+        out.append(extract_patches(rowptr, colidx, vals, n, d[None])[0])
+    return out
+
+
+# ---------------------------------------------------------------------------
+# a1': multiplicity and W = (sum_l V_l^T V_l)^{-1}   (section 2)
+# ---------------------------------------------------------------------------
+
+def multiplicity(n, flat_dofs):
+    """mult[i] = number of patches containing global DOF i."""
+    return np.bincount(np.asarray(flat_dofs, dtype=np.int64), minlength=n).astype(np.int64)
+
+
+def weights(mult):
+    """W_ii = 1 / mult[i]; a DOF in no patch makes W undefined."""
+    if np.any(mult == 0):
+        raise ValueError("a DOF belongs to no patch: W = (sum V^T V)^-1 does not exist")
+    return 1.0 / mult.astype(np.float64)
+
+
+# ---------------------------------------------------------------------------
+# a2: LU with partial pivoting and the explicit inverse
+#     (Eq. 1 needs A_k^{-1}; Exp. 3 factors with GETRF)
+# ---------------------------------------------------------------------------
+
+def lu_factor(A):
+    """Batched LU with partial pivoting of A (B, p, p): P A = L U.
+
+    Returns (L, U, perm, singular) with perm[b, i] = original row placed at
+    row i, L unit lower, U upper, singular[b] True when some pivot satisfies
+    |u_kk| <= p * 2^-53 * max|A_b|."""
+    A = np.array(A, dtype=np.float64, copy=True)
+    if A.ndim == 2:
+        A = A[None]
+    B, p, _ = A.shape
+    U = A.copy()
+    L = np.zeros_like(A)
+    perm = np.tile(np.arange(p), (B, 1))
+    bidx = np.arange(B)
+    thresh = p * U_FP64 * np.max(np.abs(A).reshape(B, -1), axis=1)
+    singular = np.zeros(B, dtype=bool)
+    for k in range(p):
+        piv = k + np.argmax(np.abs(U[:, k:, k]), axis=1)   # first max = lowest row
+        # swap rows k <-> piv in U, in the computed part of L, and in perm
+        rk = U[bidx, k, :].copy()
+        U[bidx, k, :] = U[bidx, piv, :]
+        U[bidx, piv, :] = rk
+        lk = L[bidx, k, :k].copy()
+        L[bidx, k, :k] = L[bidx, piv, :k]
+        L[bidx, piv, :k] = lk
+        pk = perm[bidx, k].copy()
+        perm[bidx, k] = perm[bidx, piv]
+        perm[bidx, piv] = pk
+        pv = U[:, k, k]
+        bad = np.abs(pv) <= thresh
+        singular |= bad
+        safe = np.where(bad, 1.0, pv)
+        L[:, k, k] = 1.0
+        if k + 1 < p:
+            m = U[:, k + 1:, k] / safe[:, None]
+            L[:, k + 1:, k] = m
+            U[:, k + 1:, k:] -= m[:, :, None] * U[:, None, k, k:]
+            U[:, k + 1:, k] = 0.0
+    return L, U, perm, singular
+
+
+def lu_inverse(A):
+    """Explicit inverse by solving L U X = P (column by column, forward then
+    back substitution).  Returns (Ainv (B,p,p), singular (B,))."""
+    L, U, perm, singular = lu_factor(A)
+    B, p, _ = U.shape
+    # right-hand side P: row i of P is e_{perm[i]}^T
+    P = np.zeros((B, p, p))
+    P[np.arange(B)[:, None], np.arange(p)[None, :], perm] = 1.0
+    Y = np.zeros_like(P)
+    for i in range(p):                    # L Y = P, L unit lower
+        Y[:, i, :] = P[:, i, :] - np.einsum("bk,bkj->bj", L[:, i, :i], Y[:, :i, :])
+    X = np.zeros_like(P)
+    diag = np.where(singular[:, None], 1.0, np.diagonal(U, axis1=1, axis2=2))
+    for i in range(p - 1, -1, -1):        # U X = Y
+        s = Y[:, i, :] - np.einsum("bk,bkj->bj", U[:, i, i + 1:], X[:, i + 1:, :])
+        X[:, i, :] = s / diag[:, i, None]
+    X[singular] = np.nan
+    return X, singular
+
+
+# ---------------------------------------------------------------------------
+# a3: criterion d(A_i, B_c) = ||I - A_i B_c^{-1}||_2 and Alg. 1
+# ---------------------------------------------------------------------------
+
+def spectral_norm(E):
+    """Largest singular value of each matrix of a (B, m, m) stack ("computed
+    exactly by a small SVD", section 3 remark)."""
+    E = np.asarray(E, dtype=np.float64)
+    if E.ndim == 2:
+        E = E[None]
+    s = np.linalg.svd(E, compute_uv=False)
+    return s[:, 0]
+
+
+def criterion(A_i, A_c, Binv_c):
+    """d(A_i, B_c) with B_c = A_c, evaluated as ||(A_c - A_i) B_c^{-1}||_2.
+
+    Broadcasts: A_i (B,p,p) or (p,p); A_c/Binv_c likewise."""
+    D = np.asarray(A_c, dtype=np.float64) - np.asarray(A_i, dtype=np.float64)
+    E = np.matmul(D, Binv_c)
+    return spectral_norm(E)
+
+
+def alg1(A, tol, near_tie_rel=1e-6):
+    """Alg. 1 (Patch Tolerance Construction) on equal-size patches A (n_p,p,p).
+
+    For i = 1..n_p: compare A_i with the database entries in creation order;
+    the first j with ||I - A_i B_j^{-1}||_2 < tol gives phi(i) = j; if none,
+    A_i^{-1} is appended and phi(i) = |B|.
+
+    Returns dict(phi, reps, Binv, evals, near_ties, singular) where reps are
+    the patch indices whose inverses form the database (in creation order),
+    evals counts the criterion evaluations of the printed loop (up to the
+    first match), and near_ties lists (i, j, d) with |d - tol| <= near_tie_rel
+    * tol among those evaluations.  (Evaluating patch i against all entries
+    at once and keeping the first hit gives the same phi as the loop with
+    its break.)
+    """
+    A = np.asarray(A, dtype=np.float64)
+    npch, p, _ = A.shape
+    phi = np.full(npch, -1, dtype=np.int64)
+    reps: list[int] = []
+    Binv = np.zeros((0, p, p))
+    evals = 0
+    near = []
+    singular = []
+    for i in range(npch):
+        j_hit = -1
+        if reps:
+            d = criterion(A[i][None], A[reps], Binv)
+            hits = np.flatnonzero(d < tol)
+            j_hit = int(hits[0]) if hits.size else -1
+            upto = j_hit + 1 if j_hit >= 0 else len(reps)
+            evals += upto
+            if tol > 0:
+                close = np.flatnonzero(np.abs(d[:upto] - tol) <= near_tie_rel * tol)
+                near.extend((i, int(j), float(d[j])) for j in close)
+        if j_hit >= 0:
+            phi[i] = j_hit
+        else:
+            inv, sing = lu_inverse(A[i][None])
+            if sing[0]:
+                singular.append(i)
+            reps.append(i)
+            Binv = np.concatenate([Binv, inv], axis=0)
+            phi[i] = len(reps) - 1
+    return {"phi": phi, "reps": np.array(reps, dtype=np.int64), "Binv": Binv,
+            "evals": evals, "near_ties": near, "singular": singular}
+
+
+def alg1_closest(A, reps, Binv):
+    """Closest-match assignment (section 3.1, the variant that picks the
+    closest of the database entries): argmin_j d(A_i, B_j), lowest j on ties.
+    Returns (phi, dmin)."""
+    A = np.asarray(A, dtype=np.float64)
+    out = np.zeros(A.shape[0], dtype=np.int64)
+    dmin = np.zeros(A.shape[0])
+    for i in range(A.shape[0]):
+        d = criterion(A[i][None], A[reps], Binv)
+        out[i] = int(np.argmin(d))
+        dmin[i] = d[out[i]]
+    return out, dmin
+
+
+# ---------------------------------------------------------------------------
+# a4: apply z = W sum_k V_k^T B_{phi(k)}^{-1} V_k r   (Eq. 1, Eq. 3)
+# ---------------------------------------------------------------------------
+
+def apply(r, dofs, Binv, phi, W, weighting="left"):
+    """Eq. (3) with equal-size patches dofs (n_p, p_s), database Binv
+    (m_p, p_s, p_s), map phi (n_p,), weights W (n,).
+
+    LEFT: z = W * sum_k V_k^T B^{-1} V_k r (the paper's form).
+    SYM : z = W^1/2 * sum_k V_k^T B^{-1} V_k (W^1/2 r)."""
+    r = np.asarray(r, dtype=np.float64)
+    dofs = np.asarray(dofs, dtype=np.int64)
+    if weighting == "sym":
+        sw = np.sqrt(W)
+        rk = (sw * r)[dofs]
+    else:
+        rk = r[dofs]
+    yk = np.einsum("kab,kb->ka", Binv[phi], rk)
+    acc = np.zeros_like(r)
+    np.add.at(acc, dofs.reshape(-1), yk.reshape(-1))
+    if weighting == "sym":
+        return np.sqrt(W) * acc
+    return W * acc
+
+
+def apply_ragged(r, offsets, flat, Binv_list, phi, W, weighting="left"):
+    """Eq. (3) for patches of varying size; Binv_list[j] is database entry j."""
+    r = np.asarray(r, dtype=np.float64)
+    sw = np.sqrt(W)
+    x = sw * r if weighting == "sym" else r
+    acc = np.zeros_like(r)
+    for k in range(len(offsets) - 1):
+        d = np.asarray(flat[offsets[k]:offsets[k + 1]], dtype=np.int64)
+        y = Binv_list[phi[k]] @ x[d]
+        np.add.at(acc, d, y)
+    return sw * acc if weighting == "sym" else W * acc
+
+
+def dense_preconditioner(n, dofs, Binv, phi, W, weighting="left"):
+    """The n x n matrix W sum_k V_k^T B_{phi(k)}^{-1} V_k formed explicitly
+    (tiny meshes only)."""
+    M = np.zeros((n, n))
+    dofs = np.asarray(dofs, dtype=np.int64)
+    for k in range(dofs.shape[0]):
+        d = dofs[k]
+        M[np.ix_(d, d)] += Binv[phi[k]]
+    if weighting == "sym":
+        s = np.sqrt(W)
+        return s[:, None] * M * s[None, :]
+    return W[:, None] * M
+
+
+# ---------------------------------------------------------------------------
+# a5: outer Krylov solvers (x0 = 0, stop at ||r_k|| <= rtol ||r_0||)
+# ---------------------------------------------------------------------------
+
+def csr_matvec(rowptr, colidx, vals, x):
+    rowptr = np.asarray(rowptr, dtype=np.int64)
+    prod = np.asarray(vals) * x[np.asarray(colidx, dtype=np.int64)]
+    out = np.add.reduceat(prod, rowptr[:-1]) if prod.size else np.zeros(len(rowptr) - 1)
+    out[np.diff(rowptr) == 0] = 0.0
+    return out
+
+
+def pcg(matvec, prec, b, rtol=1e-8, maxit=10000):
+    """Preconditioned conjugate gradients (Hestenes-Stiefel), x0 = 0.
+    Returns (x, history of ||r_k||/||r_0||, iterations, converged)."""
+    b = np.asarray(b, dtype=np.float64)
+    x = np.zeros_like(b)
+    r = b.copy()
+    r0 = np.linalg.norm(r)
+    hist = [1.0]
+    if r0 == 0.0:
+        return x, hist, 0, True
+    z = prec(r)
+    p = z.copy()
+    rz = r @ z
+    for k in range(1, maxit + 1):
+        q = matvec(p)
+        alpha = rz / (p @ q)
+        x += alpha * p
+        r -= alpha * q
+        rn = np.linalg.norm(r)
+        hist.append(rn / r0)
+        if rn <= rtol * r0:
+            return x, hist, k, True
+        z = prec(r)
+        rz_new = r @ z
+        beta = rz_new / rz
+        rz = rz_new
+        p = z + beta * p
+    return x, hist, maxit, False
+
+
+def fgmres(matvec, prec, b, restart=30, rtol=1e-8, maxit=10000):
+    """Flexible GMRES(m) with right preconditioning (Saad 1993), modified
+    Gram-Schmidt Arnoldi, Givens rotations, x0 = 0.
+
+    history[k] = |g_{k+1}| / ||r_0|| after inner iteration k (history[0] = 1).
+    At a restart x is updated and the true residual b - A x starts the next
+    cycle.  Returns (x, history, iterations, converged)."""
+    b = np.asarray(b, dtype=np.float64)
+    n = b.size
+    x = np.zeros(n)
+    r = b.copy()
+    r0 = np.linalg.norm(r)
+    hist = [1.0]
+    if r0 == 0.0:
+        return x, hist, 0, True
+    it = 0
+    beta = r0
+    m = restart
+    while it < maxit:
+        V = np.zeros((m + 1, n))
+        Z = np.zeros((m, n))
+        H = np.zeros((m + 1, m))
+        cs = np.zeros(m)
+        sn = np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        V[0] = r / beta
+        j_done = 0
+        converged = False
+        for j in range(m):
+            Z[j] = prec(V[j])
+            w = matvec(Z[j])
+            for i in range(j + 1):
+                H[i, j] = w @ V[i]
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            if H[j + 1, j] != 0.0:
+                V[j + 1] = w / H[j + 1, j]
+            for i in range(j):
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            den = np.hypot(H[j, j], H[j + 1, j])
+            cs[j] = H[j, j] / den
+            sn[j] = H[j + 1, j] / den
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            it += 1
+            j_done = j + 1
+            hist.append(abs(g[j + 1]) / r0)
+            if abs(g[j + 1]) <= rtol * r0 or it >= maxit or H[j, j] == 0.0:
+                converged = abs(g[j + 1]) <= rtol * r0
+                break
+        k = j_done
+        y = np.zeros(k)
+        for i in range(k - 1, -1, -1):
+            y[i] = (g[i] - H[i, i + 1:k] @ y[i + 1:k]) / H[i, i]
+        x = x + Z[:k].T @ y
+        if converged:
+            return x, hist, it, True
+        r = b - matvec(x)
+        beta = np.linalg.norm(r)
+        if beta == 0.0:
+            return x, hist, it, True
+    return x, hist, it, False
+
+
+# ---------------------------------------------------------------------------
+# Whole setup (Alg. 1 + inverses) and solve, on equal-size patches
+# ---------------------------------------------------------------------------
+
+def setup(rowptr, colidx, vals, n, dofs, tol):
+    """Setup of the approximate preconditioner (Eq. 3): extract the patches,
+    run Alg. 1 with tolerance tol (tol = 0 never matches: full storage,
+    Eq. 1), and compute W."""
+    A = extract_patches(rowptr, colidx, vals, n, dofs)
+    res = alg1(A, tol)
+    mult = multiplicity(n, np.asarray(dofs).reshape(-1))
+    res.update({"A": A, "W": weights(mult), "mult": mult, "dofs": np.asarray(dofs)})
+    return res
+
+
+def solve(rowptr, colidx, vals, n, b, st, krylov="cg", weighting="sym",
+          restart=30, rtol=1e-8, maxit=10000):
+    """Outer solve of A x = b preconditioned by Eq. (3)."""
+    mv = lambda v: csr_matvec(rowptr, colidx, vals, v)
+    pc = lambda v: apply(v, st["dofs"], st["Binv"], st["phi"], st["W"], weighting)
+    if krylov == "cg":
+        return pcg(mv, pc, b, rtol=rtol, maxit=maxit)
+    return fgmres(mv, pc, b, restart=restart, rtol=rtol, maxit=maxit)
