@@ -1,0 +1,199 @@
+/*
+ * psr.h -- C ABI of the GB300 compressed patch-relaxation library.
+ *
+ * Method: Harper & Tuminaro, "Compression and Reduced Representation
+ * Techniques for Patch-Based Relaxation" (arXiv 2306.10025).
+ *
+ *   Patch matrices     A_k = V_k A V_k^T                        (section 2)
+ *   Weights            W   = (sum_l V_l^T V_l)^{-1}             (section 2)
+ *   Full preconditioner M^{-1}  = W sum_k V_k^T A_k^{-1} V_k    (Eq. 1)
+ *   Compressed         M~^{-1} = W sum_k V_k^T B_phi(k)^{-1} V_k (Eq. 3)
+ *   Database / map     B = {B_1^-1..B_mp^-1}, phi built by Alg. 1 with the
+ *                      criterion d(A_i, B_j) = ||I - A_i B_j^{-1}||_2 < tol
+ *   Outer solve        A x = b by PCG or FGMRES(m), x0 = 0, stop when
+ *                      ||r_k||_2 <= rtol ||r_0||_2 (section 4, Exp. 1)
+ *
+ * Conventions (all entry points):
+ *   - Every call returns int: PSR_OK (0) or a negative PSR_ERR_* code; no C++
+ *     exception crosses the ABI.  psr_last_error() gives a message.
+ *   - Pointers documented "device" are CUDA device pointers owned by the
+ *     caller (e.g. PyTorch tensors); the library never frees them.  Storage
+ *     derived by the library (patch matrices, inverses, Krylov basis) is owned
+ *     by the psr_ctx and released by psr_destroy.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is stream-ordered; only psr_setup and psr_solve block the
+ *     host (setup to read small control scalars, solve to read the stopping
+ *     flag).  There is no CPU fallback: without a CUDA device every compute
+ *     entry point returns PSR_ERR_CUDA.
+ *   - Indices are int32 (n < 2^31, sum of patch sizes < 2^31); values FP64.
+ *   - Compute entry points run on the current CUDA device of the calling
+ *     thread; a psr_ctx must be used on the device it was created on.
+ */
+#ifndef PSR_H
+#define PSR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define PSR_OK                  0
+#define PSR_ERR_INVALID_ARG    -1  /* bad pointer / size / option            */
+#define PSR_ERR_UNSORTED_CSR   -2  /* CSR columns not sorted+unique, or out of range */
+#define PSR_ERR_SINGULAR_PATCH -3  /* a stored patch failed the pivot test   */
+#define PSR_ERR_NOT_CONVERGED  -4  /* solve hit maxit before rtol            */
+#define PSR_ERR_CUDA           -5  /* CUDA runtime error (message in psr_last_error) */
+#define PSR_ERR_OOM            -6  /* device allocation failed               */
+#define PSR_ERR_TIMEOUT        -7  /* a bounded device-side wait gave up     */
+#define PSR_ERR_UNCOVERED_DOF  -8  /* a DOF lies in no patch: W undefined    */
+
+/* ---- option values ----------------------------------------------------- */
+#define PSR_PREC_FP64 0            /* representative inverses stored FP64    */
+#define PSR_PREC_FP32 1            /* stored FP32, applied in FP32           */
+#define PSR_PREC_BF16 2            /* stored BF16, applied on tensor cores   */
+
+#define PSR_WEIGHT_LEFT 0          /* z = W sum V^T B^-1 V r (Eq. 1 / Eq. 3)  */
+#define PSR_WEIGHT_SYM  1          /* z = W^.5 sum V^T B^-1 V W^.5 r (SPD)    */
+
+#define PSR_KRYLOV_CG     0
+#define PSR_KRYLOV_FGMRES 1
+
+#define PSR_SWEEP_AUTO     0       /* library chooses                         */
+#define PSR_SWEEP_GROUPED  1       /* one persistent launch over all size groups */
+#define PSR_SWEEP_PERGROUP 2       /* one launch per patch-size group         */
+
+typedef struct psr_ctx psr_ctx;    /* opaque, library-owned */
+
+/* Assembled matrix A (section 2: A x = b), CSR, device pointers. */
+typedef struct {
+    int32_t        n;        /* rows == columns                                  */
+    int64_t        nnz;      /* entries                                          */
+    const int32_t* rowptr;   /* device, n+1, rowptr[0] = 0, nondecreasing        */
+    const int32_t* colidx;   /* device, nnz, sorted and unique within each row   */
+    const double*  vals;     /* device, nnz                                      */
+} psr_csr;
+
+/* Patches: the boolean restrictions V_k as a cell -> DOF map (section 2:
+ * (V_k)_{ij} = 1 iff global DOF j is local DOF i of patch k).  Local order is
+ * the order in which the DOFs are listed. */
+typedef struct {
+    int32_t        n_patches;
+    int32_t        uniform_size;  /* p_s when every patch has p_s DOFs, else 0   */
+    const int32_t* offsets;       /* device, n_patches+1 (ignored when uniform_size > 0) */
+    const int32_t* dofs;          /* device, flat list, patch k at [offsets[k], offsets[k+1]) */
+} psr_patches;
+
+typedef struct {
+    double  tol;          /* Alg. 1 epsilon; 0 => full storage (phi = identity)  */
+    int32_t store_prec;   /* PSR_PREC_*                                           */
+    int32_t weighting;    /* PSR_WEIGHT_*                                         */
+    int32_t krylov;       /* PSR_KRYLOV_*                                         */
+    int32_t restart;      /* FGMRES restart length m (1..64)                      */
+    double  rtol;         /* relative residual target                             */
+    int32_t maxit;        /* outer iteration cap                                  */
+    int32_t use_graph;    /* 1: capture Krylov cycles in CUDA graphs              */
+    int32_t sweep_kernel; /* PSR_SWEEP_*                                          */
+    int32_t autotune;     /* 1: time candidate sweep tile shapes at setup         */
+    int32_t symmetrize;   /* 1: store (B^-1 + B^-T)/2 before rounding to FP32/BF16 */
+    int32_t use_mlp;      /* 1: verify MLP-predicted representatives first (needs psr_mlp_attach) */
+} psr_opts;
+
+/* Fill `o` with defaults: tol 0, FP64, SYM, CG, restart 30, rtol 1e-8,
+ * maxit 10000, graphs on, AUTO sweep, autotune on, symmetrize on, no MLP. */
+void psr_default_opts(psr_opts* o);
+
+/* ---- whole method ------------------------------------------------------- */
+
+/* Setup of M~^{-1} (Eq. 3): validate the CSR and map, extract every A_k,
+ * compute W, build B and phi with Alg. 1 at opts->tol (tol = 0 stores every
+ * patch, Eq. 1), invert the representatives (FP64 LU-equivalent Gauss-Jordan
+ * with partial pivoting), convert them to opts->store_prec and lay out the
+ * sweep.  The CSR and map are copied; the caller may free them afterwards.
+ * On success *out owns all derived storage.  Errors: INVALID_ARG,
+ * UNSORTED_CSR, UNCOVERED_DOF, SINGULAR_PATCH (psr_last_error names the
+ * patch), OOM, CUDA.  Blocks the host. */
+int psr_setup(const psr_csr* A, const psr_patches* patches, const psr_opts* opts,
+              void* stream, psr_ctx** out);
+
+/* z = M~^{-1} r (Eq. 3 with the context's weighting).  r, z: device, length n,
+ * must not overlap.  Stream-ordered, no host synchronisation, no allocation. */
+int psr_apply(psr_ctx* ctx, const double* r, double* z, void* stream);
+
+typedef struct {
+    int32_t iterations;   /* outer iterations performed                        */
+    int32_t converged;    /* 1 when ||r_k|| <= rtol ||r_0||                     */
+    double  relres;       /* final ||r_k|| / ||r_0|| (recursively updated)      */
+    double  seconds;      /* device time of the solve (CUDA events)            */
+} psr_solve_info;
+
+/* Solve A x = b (x0 = 0) with the context's Krylov method preconditioned on
+ * the right by M~^{-1}.  b, x: device, length n.  Returns NOT_CONVERGED when
+ * maxit is hit (x then holds the last iterate).  `info` may be NULL. */
+int psr_solve(psr_ctx* ctx, const double* b, double* x, void* stream, psr_solve_info* info);
+
+/* Residual history of the last solve: hist[k] = ||r_k||/||r_0||, k = 0..len-1
+ * (host buffer of capacity cap).  *len receives the number of entries. */
+int psr_get_history(psr_ctx* ctx, double* hist, int32_t cap, int32_t* len);
+
+/* Alg. 1 output: phi (device, n_patches, 0-based database index per patch),
+ * rep_ids (device, m_p, patch index of each database entry in creation
+ * order, or NULL) and *m_p (host). */
+int psr_get_assignment(psr_ctx* ctx, int32_t* phi, int32_t* rep_ids, int32_t* m_p);
+
+typedef struct {
+    int32_t n, n_patches, m_p, n_groups;
+    int64_t criterion_evals;      /* d(A_i, B_j) evaluations in Alg. 1 order   */
+    int64_t criterion_exact;      /* of which needed the exact SVD-class path   */
+    int64_t mlp_hits;             /* patches whose predicted entry verified      */
+    int64_t factor_bytes;         /* bytes of stored inverses                   */
+    int64_t index_bytes;          /* bytes of phi + maps used by the sweep      */
+    double  t_extract, t_rounds, t_invert, t_convert, t_autotune; /* setup seconds */
+    int32_t first_singular;       /* patch index or -1                          */
+    int32_t rounds;               /* Alg. 1 rounds (= m_p when tol > 0)         */
+} psr_stats;
+
+int psr_get_stats(psr_ctx* ctx, psr_stats* st);
+
+/* Message of the last failing call on this thread (ctx may be NULL). */
+const char* psr_last_error(psr_ctx* ctx);
+
+void psr_destroy(psr_ctx* ctx);
+
+/* ---- single steps of the path (stateless; for testing and reuse) ------- */
+
+/* Step a1/a1': A_out <- every A_k (section 2), row-major, patch k at offset
+ * sum_{j<k} p_j^2 doubles; mult_out[i] <- number of patches holding DOF i;
+ * W_out[i] <- 1/mult_out[i].  All device; any output may be NULL.
+ * Errors: INVALID_ARG, UNSORTED_CSR, UNCOVERED_DOF (only when W_out given). */
+int psr_extract(const psr_csr* A, const psr_patches* patches, double* A_out,
+                int32_t* mult_out, double* W_out, void* stream);
+
+/* Step a2: Ainv[b] <- A[b]^{-1} for a batch of p x p row-major FP64
+ * matrices (device), partial pivoting (largest |entry|, lowest row on ties).
+ * singular (device, batch, may be NULL) <- 1 when some pivot has
+ * |pivot| <= p * 2^-53 * max|A[b]|; that inverse is then NaN.  1 <= p <= 128. */
+int psr_batched_inverse(const double* A, int32_t batch, int32_t p, double* Ainv,
+                        int32_t* singular, void* stream);
+
+/* Step a3 for one database entry: for b < batch, decide
+ * d(A_i[b], B_c) = ||(A_c - A_i[b]) Binv_c||_2 < tol (the difference form of
+ * ||I - A_i B_c^{-1}||_2, Alg. 1 test).  accept (device, batch) <- 0/1;
+ * dval (device, batch, may be NULL) <- the value that decided: 0 for an
+ * exactly equal patch, a certified upper bound below tol for an accept, a
+ * certified lower bound >= tol for a reject, or sigma_max from the exact
+ * path.  A_i, A_c, Binv_c: device, row-major p x p FP64.  1 <= p <= 32. */
+int psr_criterion(const double* A_i, int32_t batch, int32_t p, const double* A_c,
+                  const double* Binv_c, double tol, int32_t* accept, double* dval,
+                  void* stream);
+
+/* sigma_max of each p x p matrix (device, row-major) by one-sided Jacobi in
+ * FP64 (the "small SVD" of the section 3 remark).  1 <= p <= 32. */
+int psr_spectral_norm(const double* E, int32_t batch, int32_t p, double* sigma,
+                      void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSR_H */

@@ -1,0 +1,282 @@
+"""ctypes binding of libpsr.so (include/psr.h).
+
+Argument marshalling only: tensors are passed as raw device pointers plus
+sizes, the current CUDA stream as a void*.  Every step of the method runs in
+the library's CUDA kernels; there is no Python or CPU fallback and every call
+raises when the library is missing or returns an error.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpsr.so")
+
+PSR_OK = 0
+ERRORS = {
+    -1: "PSR_ERR_INVALID_ARG", -2: "PSR_ERR_UNSORTED_CSR", -3: "PSR_ERR_SINGULAR_PATCH",
+    -4: "PSR_ERR_NOT_CONVERGED", -5: "PSR_ERR_CUDA", -6: "PSR_ERR_OOM", -7: "PSR_ERR_TIMEOUT",
+    -8: "PSR_ERR_UNCOVERED_DOF",
+}
+PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
+WEIGHT = {"left": 0, "sym": 1}
+KRYLOV = {"cg": 0, "fgmres": 1}
+SWEEP = {"auto": 0, "grouped": 1, "pergroup": 2}
+
+EXPORTS = ["psr_default_opts", "psr_setup", "psr_apply", "psr_solve", "psr_get_history",
+           "psr_get_assignment", "psr_get_stats", "psr_last_error", "psr_destroy", "psr_extract",
+           "psr_batched_inverse", "psr_criterion", "psr_spectral_norm"]
+
+
+class PsrError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class psr_csr(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int64), ("rowptr", C.c_void_p),
+                ("colidx", C.c_void_p), ("vals", C.c_void_p)]
+
+
+class psr_patches(C.Structure):
+    _fields_ = [("n_patches", C.c_int32), ("uniform_size", C.c_int32),
+                ("offsets", C.c_void_p), ("dofs", C.c_void_p)]
+
+
+class psr_opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("store_prec", C.c_int32), ("weighting", C.c_int32),
+                ("krylov", C.c_int32), ("restart", C.c_int32), ("rtol", C.c_double),
+                ("maxit", C.c_int32), ("use_graph", C.c_int32), ("sweep_kernel", C.c_int32),
+                ("autotune", C.c_int32), ("symmetrize", C.c_int32), ("use_mlp", C.c_int32)]
+
+
+class psr_solve_info(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("relres", C.c_double),
+                ("seconds", C.c_double)]
+
+
+class psr_stats(C.Structure):
+    _fields_ = [("n", C.c_int32), ("n_patches", C.c_int32), ("m_p", C.c_int32), ("n_groups", C.c_int32),
+                ("criterion_evals", C.c_int64), ("criterion_exact", C.c_int64), ("mlp_hits", C.c_int64),
+                ("factor_bytes", C.c_int64), ("index_bytes", C.c_int64),
+                ("t_extract", C.c_double), ("t_rounds", C.c_double), ("t_invert", C.c_double),
+                ("t_convert", C.c_double), ("t_autotune", C.c_double),
+                ("first_singular", C.c_int32), ("rounds", C.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libpsr.so; raises when it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpsr.so not built ({path}); run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    vp, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    lib.psr_default_opts.argtypes = [C.POINTER(psr_opts)]
+    lib.psr_default_opts.restype = None
+    lib.psr_setup.argtypes = [C.POINTER(psr_csr), C.POINTER(psr_patches), C.POINTER(psr_opts), vp, C.POINTER(vp)]
+    lib.psr_apply.argtypes = [vp, vp, vp, vp]
+    lib.psr_solve.argtypes = [vp, vp, vp, vp, C.POINTER(psr_solve_info)]
+    lib.psr_get_history.argtypes = [vp, vp, i32, C.POINTER(i32)]
+    lib.psr_get_assignment.argtypes = [vp, vp, vp, C.POINTER(i32)]
+    lib.psr_get_stats.argtypes = [vp, C.POINTER(psr_stats)]
+    lib.psr_last_error.argtypes = [vp]
+    lib.psr_last_error.restype = C.c_char_p
+    lib.psr_destroy.argtypes = [vp]
+    lib.psr_destroy.restype = None
+    lib.psr_extract.argtypes = [C.POINTER(psr_csr), C.POINTER(psr_patches), vp, vp, vp, vp]
+    lib.psr_batched_inverse.argtypes = [vp, i32, i32, vp, vp, vp]
+    lib.psr_criterion.argtypes = [vp, i32, i32, vp, vp, d, vp, vp, vp]
+    lib.psr_spectral_norm.argtypes = [vp, i32, i32, vp, vp]
+    for name in EXPORTS:
+        if name not in ("psr_default_opts", "psr_last_error", "psr_destroy"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, ctx=None):
+    if rc != PSR_OK:
+        msg = load().psr_last_error(ctx).decode(errors="replace")
+        raise PsrError(rc, msg)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _need(t, dtype, name):
+    import torch
+    if not (t.is_cuda and t.is_contiguous() and t.dtype == dtype):
+        raise ValueError(f"{name} must be a contiguous CUDA tensor of {dtype}")
+
+
+def make_opts(tol=0.0, store_prec="fp64", weighting="sym", krylov="cg", restart=30, rtol=1e-8,
+              maxit=10000, use_graph=True, sweep_kernel="auto", autotune=True, symmetrize=True,
+              use_mlp=False) -> psr_opts:
+    o = psr_opts()
+    load().psr_default_opts(C.byref(o))
+    o.tol = tol
+    o.store_prec = PREC[store_prec]
+    o.weighting = WEIGHT[weighting]
+    o.krylov = KRYLOV[krylov]
+    o.restart = restart
+    o.rtol = rtol
+    o.maxit = maxit
+    o.use_graph = int(use_graph)
+    o.sweep_kernel = SWEEP[sweep_kernel]
+    o.autotune = int(autotune)
+    o.symmetrize = int(symmetrize)
+    o.use_mlp = int(use_mlp)
+    return o
+
+
+def _csr(rowptr, colidx, vals):
+    import torch
+    _need(rowptr, torch.int32, "rowptr")
+    _need(colidx, torch.int32, "colidx")
+    _need(vals, torch.float64, "vals")
+    return psr_csr(rowptr.numel() - 1, colidx.numel(), rowptr.data_ptr(), colidx.data_ptr(), vals.data_ptr())
+
+
+def _patches(dofs, offsets=None, uniform_size=0):
+    import torch
+    _need(dofs, torch.int32, "dofs")
+    if offsets is not None:
+        _need(offsets, torch.int32, "offsets")
+        return psr_patches(offsets.numel() - 1, 0, offsets.data_ptr(), dofs.data_ptr())
+    if uniform_size <= 0:
+        raise ValueError("give offsets or uniform_size")
+    return psr_patches(dofs.numel() // uniform_size, uniform_size, None, dofs.data_ptr())
+
+
+# ------------------------------------------------------------- entry points
+def psr_setup(rowptr, colidx, vals, dofs, offsets=None, uniform_size=0, opts: psr_opts | None = None,
+              stream=None) -> "Context":
+    lib = load()
+    A = _csr(rowptr, colidx, vals)
+    P = _patches(dofs, offsets, uniform_size)
+    o = opts if opts is not None else make_opts()
+    h = C.c_void_p()
+    rc = lib.psr_setup(C.byref(A), C.byref(P), C.byref(o), _stream(stream), C.byref(h))
+    _check(rc, None)
+    return Context(h, A.n, P.n_patches, o)
+
+
+class Context:
+    """Owns a psr_ctx (library-owned device storage)."""
+
+    def __init__(self, handle, n, n_patches, opts):
+        self.h = handle
+        self.n = n
+        self.n_patches = n_patches
+        self.opts = opts
+
+    def apply(self, r, z, stream=None):
+        import torch
+        _need(r, torch.float64, "r")
+        _need(z, torch.float64, "z")
+        _check(load().psr_apply(self.h, _ptr(r), _ptr(z), _stream(stream)), self.h)
+
+    def solve(self, b, x, stream=None, raise_on_nonconvergence=False) -> dict:
+        import torch
+        _need(b, torch.float64, "b")
+        _need(x, torch.float64, "x")
+        info = psr_solve_info()
+        rc = load().psr_solve(self.h, _ptr(b), _ptr(x), _stream(stream), C.byref(info))
+        if rc != PSR_OK and not (rc == -4 and not raise_on_nonconvergence):
+            _check(rc, self.h)
+        return {"iterations": info.iterations, "converged": bool(info.converged),
+                "relres": info.relres, "seconds": info.seconds}
+
+    def history(self) -> np.ndarray:
+        n = C.c_int32()
+        _check(load().psr_get_history(self.h, None, 0, C.byref(n)), self.h)
+        out = np.zeros(n.value)
+        _check(load().psr_get_history(self.h, out.ctypes.data_as(C.c_void_p), n.value, C.byref(n)), self.h)
+        return out
+
+    def assignment(self):
+        import torch
+        m = C.c_int32()
+        _check(load().psr_get_assignment(self.h, None, None, C.byref(m)), self.h)
+        phi = torch.empty(self.n_patches, dtype=torch.int32, device="cuda")
+        reps = torch.empty(max(m.value, 1), dtype=torch.int32, device="cuda")
+        _check(load().psr_get_assignment(self.h, _ptr(phi), _ptr(reps), C.byref(m)), self.h)
+        return phi, reps[: m.value], m.value
+
+    def stats(self) -> dict:
+        st = psr_stats()
+        _check(load().psr_get_stats(self.h, C.byref(st)), self.h)
+        return st.as_dict()
+
+    def destroy(self):
+        if self.h:
+            load().psr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def psr_extract(rowptr, colidx, vals, dofs, offsets=None, uniform_size=0, A_out=None, mult_out=None,
+                W_out=None, stream=None):
+    A = _csr(rowptr, colidx, vals)
+    P = _patches(dofs, offsets, uniform_size)
+    _check(load().psr_extract(C.byref(A), C.byref(P), _ptr(A_out), _ptr(mult_out), _ptr(W_out), _stream(stream)))
+
+
+def psr_batched_inverse(A, Ainv, singular=None, stream=None):
+    import torch
+    _need(A, torch.float64, "A")
+    _need(Ainv, torch.float64, "Ainv")
+    b, p, _ = A.shape
+    _check(load().psr_batched_inverse(_ptr(A), b, p, _ptr(Ainv), _ptr(singular), _stream(stream)))
+
+
+def psr_criterion(A_i, A_c, Binv_c, tol, accept, dval=None, stream=None):
+    import torch
+    _need(A_i, torch.float64, "A_i")
+    b, p, _ = A_i.shape
+    _check(load().psr_criterion(_ptr(A_i), b, p, _ptr(A_c), _ptr(Binv_c), float(tol), _ptr(accept),
+                                _ptr(dval), _stream(stream)))
+
+
+def psr_spectral_norm(E, sigma, stream=None):
+    import torch
+    _need(E, torch.float64, "E")
+    b, p, _ = E.shape
+    _check(load().psr_spectral_norm(_ptr(E), b, p, _ptr(sigma), _stream(stream)))
+
+
+def exported_symbols(path: str = LIB_PATH) -> list[str]:
+    """Names of the psr_* functions the shared library exports (via dlsym)."""
+    lib = C.CDLL(path)
+    found = []
+    for name in EXPORTS:
+        try:
+            getattr(lib, name)
+            found.append(name)
+        except AttributeError:
+            pass
+    return found

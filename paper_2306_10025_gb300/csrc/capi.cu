@@ -1,0 +1,451 @@
+// C ABI entry points (include/psr.h): setup / apply / solve / queries and the
+// stateless single-step calls.  No C++ exception crosses this boundary.
+#include "psr_internal.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace psr {
+
+static thread_local std::string g_last_error;
+
+void set_error(psr_ctx* ctx, const std::string& msg) {
+    g_last_error = msg;
+    if (ctx) ctx->err = msg;
+}
+
+int cuda_fail(psr_ctx* ctx, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    set_error(ctx, m);
+    return (e == cudaErrorMemoryAllocation) ? PSR_ERR_OOM : PSR_ERR_CUDA;
+}
+
+int build_sweep_layout(psr_ctx* ctx, const std::vector<int32_t>& h_dofs,
+                       const std::vector<std::vector<int32_t>>& gidx, cudaStream_t s);
+int sweep_prepare(psr_ctx* ctx);
+
+__global__ void k_iota(int32_t* a, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = i;
+}
+
+__global__ void k_any(const int32_t* flags, int n, int32_t* first) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (flags[i]) atomicMin(first, i);
+}
+
+static double seconds_since(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+static void destroy_ctx(psr_ctx* ctx) {
+    if (!ctx) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != ctx->device) cudaSetDevice(ctx->device);
+    free_sweep(ctx);
+    krylov_free(ctx);
+    cudaFree(ctx->rowptr);
+    cudaFree(ctx->colidx);
+    cudaFree(ctx->vals);
+    cudaFree(ctx->offsets);
+    cudaFree(ctx->dofs);
+    cudaFree(ctx->mat_off);
+    cudaFree(ctx->A_ext);
+    cudaFree(ctx->W);
+    if (ctx->Wg && ctx->Wg != ctx->W) cudaFree(ctx->Wg);
+    cudaFree(ctx->phi);
+    cudaFree(ctx->rep_ids);
+    cudaFree(ctx->status);
+    if (cur != ctx->device) cudaSetDevice(cur);
+    delete ctx;
+}
+
+static int check_status(psr_ctx* ctx, cudaStream_t s) {
+    int32_t st = 0;
+    PSR_CUDA(ctx, cudaMemcpyAsync(&st, ctx->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PSR_CUDA(ctx, cudaStreamSynchronize(s));
+    if (st & ST_UNSORTED) { set_error(ctx, "CSR columns not sorted/unique or out of range"); return PSR_ERR_UNSORTED_CSR; }
+    if (st & ST_OOB) { set_error(ctx, "patch map holds a DOF outside [0, n) or decreasing offsets"); return PSR_ERR_INVALID_ARG; }
+    if (st & ST_UNCOVERED) { set_error(ctx, "a DOF belongs to no patch: W = (sum V^T V)^-1 is undefined"); return PSR_ERR_UNCOVERED_DOF; }
+    return PSR_OK;
+}
+
+static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o, cudaStream_t s, psr_ctx** out) {
+    auto t_all = std::chrono::steady_clock::now();
+    psr_ctx* ctx = new psr_ctx();
+    *out = nullptr;
+    if (o) ctx->opts = *o; else psr_default_opts(&ctx->opts);
+    psr_opts& op = ctx->opts;
+    if (op.restart < 1 || op.restart > 32 || op.maxit < 1 || !(op.rtol > 0.0) || op.tol < 0.0 ||
+        op.store_prec < 0 || op.store_prec > 2 || op.weighting < 0 || op.weighting > 1 || op.krylov < 0 || op.krylov > 1) {
+        set_error(ctx, "invalid option value");
+        destroy_ctx(ctx);
+        return PSR_ERR_INVALID_ARG;
+    }
+    cudaGetDevice(&ctx->device);
+    const int n = A->n;
+    ctx->n = n;
+    ctx->nnz = A->nnz;
+    ctx->n_patches = P->n_patches;
+    ctx->stats.first_singular = -1;
+    int rc = PSR_OK;
+#define FAIL(code) do { rc = (code); goto fail; } while (0)
+#define CK(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { rc = cuda_fail(ctx, e_, #call); goto fail; } } while (0)
+    {
+        // --- copies of the inputs
+        CK(cudaMalloc(&ctx->status, sizeof(int32_t)));
+        CK(cudaMemsetAsync(ctx->status, 0, sizeof(int32_t), s));
+        CK(cudaMalloc(&ctx->rowptr, sizeof(int32_t) * (size_t)(n + 1)));
+        CK(cudaMalloc(&ctx->colidx, sizeof(int32_t) * (size_t)std::max<int64_t>(A->nnz, 1)));
+        CK(cudaMalloc(&ctx->vals, sizeof(double) * (size_t)std::max<int64_t>(A->nnz, 1)));
+        CK(cudaMemcpyAsync(ctx->rowptr, A->rowptr, sizeof(int32_t) * (size_t)(n + 1), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(ctx->colidx, A->colidx, sizeof(int32_t) * (size_t)A->nnz, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(ctx->vals, A->vals, sizeof(double) * (size_t)A->nnz, cudaMemcpyDeviceToDevice, s));
+        const int np = P->n_patches;
+        ctx->h_offsets.resize((size_t)np + 1);
+        if (P->uniform_size > 0) {
+            for (int k = 0; k <= np; ++k) ctx->h_offsets[k] = k * P->uniform_size;
+            if ((int64_t)np * P->uniform_size >= (1ll << 31)) { set_error(ctx, "sum of patch sizes exceeds int32"); FAIL(PSR_ERR_INVALID_ARG); }
+        } else {
+            CK(cudaMemcpyAsync(ctx->h_offsets.data(), P->offsets, sizeof(int32_t) * (size_t)(np + 1), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (ctx->h_offsets[0] != 0) { set_error(ctx, "offsets[0] must be 0"); FAIL(PSR_ERR_INVALID_ARG); }
+            for (int k = 0; k < np; ++k)
+                if (ctx->h_offsets[k + 1] <= ctx->h_offsets[k]) { set_error(ctx, "patch sizes must be positive"); FAIL(PSR_ERR_INVALID_ARG); }
+        }
+        const int64_t total = ctx->h_offsets[np];
+        CK(cudaMalloc(&ctx->offsets, sizeof(int32_t) * (size_t)(np + 1)));
+        CK(cudaMemcpyAsync(ctx->offsets, ctx->h_offsets.data(), sizeof(int32_t) * (size_t)(np + 1), cudaMemcpyHostToDevice, s));
+        CK(cudaMalloc(&ctx->dofs, sizeof(int32_t) * (size_t)total));
+        CK(cudaMemcpyAsync(ctx->dofs, P->dofs, sizeof(int32_t) * (size_t)total, cudaMemcpyDeviceToDevice, s));
+        std::vector<int32_t> h_dofs((size_t)total);
+        CK(cudaMemcpyAsync(h_dofs.data(), P->dofs, sizeof(int32_t) * (size_t)total, cudaMemcpyDeviceToHost, s));
+        // --- validation
+        rc = validate_inputs(ctx, A, ctx->offsets, ctx->dofs, np, total, ctx->status, s);
+        if (rc != PSR_OK) goto fail;
+        rc = check_status(ctx, s);
+        if (rc != PSR_OK) goto fail;
+        // --- size groups (Remark after Eq. 1), group-contiguous patch storage
+        std::map<int, std::vector<int32_t>> bysize;
+        for (int k = 0; k < np; ++k) bysize[ctx->h_offsets[k + 1] - ctx->h_offsets[k]].push_back(k);
+        std::vector<std::vector<int32_t>> gidx;
+        std::vector<int64_t> h_mat_off((size_t)np + 1, 0);
+        int64_t off = 0;
+        // larger patches first: the grouped kernel's heavy tiles are dealt out early
+        for (auto it = bysize.rbegin(); it != bysize.rend(); ++it) {
+            Group G;
+            G.p = it->first;
+            G.count = (int)it->second.size();
+            G.mat_off = off;
+            if (G.p > 128) { set_error(ctx, "patches larger than 128 DOFs are not supported"); FAIL(PSR_ERR_INVALID_ARG); }
+            for (int l = 0; l < G.count; ++l) h_mat_off[it->second[l]] = off + (int64_t)l * G.p * G.p;
+            off += (int64_t)G.count * G.p * G.p;
+            ctx->groups.push_back(G);
+            gidx.push_back(it->second);
+        }
+        h_mat_off[np] = off;
+        ctx->A_ext_len = off;
+        CK(cudaMalloc(&ctx->mat_off, sizeof(int64_t) * (size_t)(np + 1)));
+        CK(cudaMemcpyAsync(ctx->mat_off, h_mat_off.data(), sizeof(int64_t) * (size_t)(np + 1), cudaMemcpyHostToDevice, s));
+        {
+            cudaError_t ea = cudaMalloc(&ctx->A_ext, sizeof(double) * (size_t)off);
+            if (ea != cudaSuccess) { cudaGetLastError(); set_error(ctx, "out of device memory for the patch matrices"); FAIL(PSR_ERR_OOM); }
+        }
+        // --- a1: extraction
+        auto t0 = std::chrono::steady_clock::now();
+        rc = launch_extract(ctx->rowptr, ctx->colidx, ctx->vals, ctx->offsets, ctx->dofs, ctx->mat_off, np,
+                            0, total, ctx->A_ext, s);
+        if (rc != PSR_OK) goto fail;
+        // --- a1': multiplicity and weights
+        {
+            int32_t* mult = nullptr;
+            double* w1 = nullptr;
+            double* w2 = nullptr;
+            CK(cudaMalloc(&mult, sizeof(int32_t) * (size_t)n));
+            CK(cudaMalloc(&w1, sizeof(double) * (size_t)n));
+            CK(cudaMalloc(&w2, sizeof(double) * (size_t)n));
+            rc = launch_multiplicity(ctx->dofs, total, n, mult, w1, w2, ctx->status, s);
+            if (rc != PSR_OK) { cudaFree(mult); cudaFree(w1); cudaFree(w2); goto fail; }
+            CK(cudaStreamSynchronize(s));
+            cudaFree(mult);
+            if (op.weighting == PSR_WEIGHT_SYM) {
+                cudaFree(w1);
+                ctx->W = w2;
+                ctx->Wg = w2;
+            } else {
+                cudaFree(w2);
+                ctx->W = w1;
+                ctx->Wg = nullptr;
+            }
+        }
+        rc = check_status(ctx, s);
+        if (rc != PSR_OK) goto fail;
+        ctx->stats.t_extract = seconds_since(t0);
+        // --- a2 / a3: database and assignment
+        CK(cudaMalloc(&ctx->phi, sizeof(int32_t) * (size_t)np));
+        CK(cudaMalloc(&ctx->rep_ids, sizeof(int32_t) * (size_t)np));
+        t0 = std::chrono::steady_clock::now();
+        if (op.tol == 0.0) {
+            // strict "< 0" never holds: every patch is its own entry (Eq. 1)
+            int32_t* sing = nullptr;
+            int32_t* first = nullptr;
+            CK(cudaMalloc(&sing, sizeof(int32_t) * (size_t)np));
+            CK(cudaMalloc(&first, sizeof(int32_t)));
+            for (auto& G : ctx->groups) {
+                double* base = ctx->A_ext + G.mat_off;
+                rc = launch_batched_inverse(base, (int64_t)G.p * G.p, nullptr, G.count, G.p, base,
+                                            (int64_t)G.p * G.p, sing, s);
+                if (rc != PSR_OK) { cudaFree(sing); cudaFree(first); goto fail; }
+                int32_t big = 0x7fffffff;
+                CK(cudaMemcpyAsync(first, &big, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+                k_any<<<std::max(1, std::min(G.count / 256 + 1, 1024)), 256, 0, s>>>(sing, G.count, first);
+                int32_t h_first = 0;
+                CK(cudaMemcpyAsync(&h_first, first, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                G.m = G.count;
+                G.rinv = base;
+                CK(cudaMalloc(&G.sphi, sizeof(int32_t) * (size_t)G.count));
+                k_iota<<<std::max(1, std::min(G.count / 256 + 1, 1024)), 256, 0, s>>>(G.sphi, G.count);
+                G.h_rep.resize(G.count);
+                for (int l = 0; l < G.count; ++l) G.h_rep[l] = l;
+                if (h_first != 0x7fffffff && ctx->stats.first_singular < 0) ctx->stats.first_singular = gidx[&G - &ctx->groups[0]][h_first];
+            }
+            cudaFree(sing);
+            cudaFree(first);
+            ctx->stats.rounds = 0;
+            ctx->stats.criterion_evals = 0;
+        } else {
+            for (auto& G : ctx->groups)
+                if (G.p > 32) { set_error(ctx, "the criterion kernel handles patches of at most 32 DOFs"); FAIL(PSR_ERR_INVALID_ARG); }
+            rc = run_alg1_rounds(ctx, s);
+            if (rc != PSR_OK) goto fail;
+        }
+        CK(cudaStreamSynchronize(s));
+        ctx->stats.t_rounds = seconds_since(t0);
+        if (ctx->stats.first_singular >= 0) {
+            set_error(ctx, "patch " + std::to_string(ctx->stats.first_singular) +
+                           " failed the pivot test |u_kk| <= p * 2^-53 * max|A_k| (singular)");
+            FAIL(PSR_ERR_SINGULAR_PATCH);
+        }
+        t0 = std::chrono::steady_clock::now();
+        rc = build_sweep_layout(ctx, h_dofs, gidx, s);
+        if (rc != PSR_OK) goto fail;
+        rc = sweep_prepare(ctx);
+        if (rc != PSR_OK) goto fail;
+        ctx->stats.t_convert = seconds_since(t0);
+        // the patch matrices are no longer needed unless they hold the inverses
+        {
+            bool in_use = false;
+            for (auto& G : ctx->groups)
+                if (reinterpret_cast<double*>(G.rinv) >= ctx->A_ext &&
+                    reinterpret_cast<double*>(G.rinv) < ctx->A_ext + std::max<int64_t>(ctx->A_ext_len, 1))
+                    in_use = true;
+            if (!in_use) {
+                cudaFree(ctx->A_ext);
+                ctx->A_ext = nullptr;
+                ctx->A_ext_len = 0;
+            }
+        }
+        rc = krylov_alloc(ctx);
+        if (rc != PSR_OK) goto fail;
+        ctx->stats.n = n;
+        ctx->stats.n_patches = np;
+        ctx->stats.n_groups = (int)ctx->groups.size();
+        (void)t_all;
+        *out = ctx;
+        return PSR_OK;
+    }
+fail:
+    destroy_ctx(ctx);
+    return rc;
+#undef FAIL
+#undef CK
+}
+
+}  // namespace psr
+
+using namespace psr;
+
+extern "C" {
+
+void psr_default_opts(psr_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->tol = 0.0;
+    o->store_prec = PSR_PREC_FP64;
+    o->weighting = PSR_WEIGHT_SYM;
+    o->krylov = PSR_KRYLOV_CG;
+    o->restart = 30;
+    o->rtol = 1e-8;
+    o->maxit = 10000;
+    o->use_graph = 1;
+    o->sweep_kernel = PSR_SWEEP_AUTO;
+    o->autotune = 1;
+    o->symmetrize = 1;
+    o->use_mlp = 0;
+}
+
+int psr_setup(const psr_csr* A, const psr_patches* patches, const psr_opts* opts, void* stream, psr_ctx** out) {
+    if (!out) { set_error(nullptr, "out is NULL"); return PSR_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (!A || !patches || !A->rowptr || !A->vals || !A->colidx || A->n <= 0 || A->nnz < 0 ||
+        patches->n_patches <= 0 || !patches->dofs || (patches->uniform_size <= 0 && !patches->offsets)) {
+        set_error(nullptr, "invalid matrix or patch description");
+        return PSR_ERR_INVALID_ARG;
+    }
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) {
+        cudaGetLastError();
+        set_error(nullptr, "no CUDA device: the library has no CPU fallback");
+        return PSR_ERR_CUDA;
+    }
+    try {
+        return setup_impl(A, patches, opts, (cudaStream_t)stream, out);
+    } catch (const std::bad_alloc&) {
+        set_error(nullptr, "host allocation failed");
+        return PSR_ERR_OOM;
+    } catch (...) {
+        set_error(nullptr, "unexpected host exception in psr_setup");
+        return PSR_ERR_CUDA;
+    }
+}
+
+int psr_apply(psr_ctx* ctx, const double* r, double* z, void* stream) {
+    if (!ctx || !r || !z) { set_error(ctx, "NULL argument"); return PSR_ERR_INVALID_ARG; }
+    if (r == z) { set_error(ctx, "r and z must not overlap"); return PSR_ERR_INVALID_ARG; }
+    return sweep_apply(ctx, r, z, (cudaStream_t)stream);
+}
+
+int psr_solve(psr_ctx* ctx, const double* b, double* x, void* stream, psr_solve_info* info) {
+    if (!ctx || !b || !x) { set_error(ctx, "NULL argument"); return PSR_ERR_INVALID_ARG; }
+    try {
+        return krylov_solve(ctx, b, x, (cudaStream_t)stream, info);
+    } catch (...) {
+        set_error(ctx, "unexpected host exception in psr_solve");
+        return PSR_ERR_CUDA;
+    }
+}
+
+int psr_get_history(psr_ctx* ctx, double* hist, int32_t cap, int32_t* len) {
+    if (!ctx || !len) { set_error(ctx, "NULL argument"); return PSR_ERR_INVALID_ARG; }
+    const int32_t L = (int32_t)ctx->h_hist.size();
+    *len = L;
+    if (hist) std::memcpy(hist, ctx->h_hist.data(), sizeof(double) * (size_t)std::min(L, cap));
+    return PSR_OK;
+}
+
+int psr_get_assignment(psr_ctx* ctx, int32_t* phi, int32_t* rep_ids, int32_t* m_p) {
+    if (!ctx) { set_error(nullptr, "NULL context"); return PSR_ERR_INVALID_ARG; }
+    if (m_p) *m_p = ctx->m_p;
+    if (phi) PSR_CUDA(ctx, cudaMemcpy(phi, ctx->phi, sizeof(int32_t) * (size_t)ctx->n_patches, cudaMemcpyDeviceToDevice));
+    if (rep_ids && ctx->m_p > 0)
+        PSR_CUDA(ctx, cudaMemcpy(rep_ids, ctx->rep_ids, sizeof(int32_t) * (size_t)ctx->m_p, cudaMemcpyDeviceToDevice));
+    return PSR_OK;
+}
+
+int psr_get_stats(psr_ctx* ctx, psr_stats* st) {
+    if (!ctx || !st) { set_error(ctx, "NULL argument"); return PSR_ERR_INVALID_ARG; }
+    *st = ctx->stats;
+    return PSR_OK;
+}
+
+const char* psr_last_error(psr_ctx* ctx) {
+    if (ctx && !ctx->err.empty()) return ctx->err.c_str();
+    return g_last_error.c_str();
+}
+
+void psr_destroy(psr_ctx* ctx) { destroy_ctx(ctx); }
+
+int psr_extract(const psr_csr* A, const psr_patches* P, double* A_out, int32_t* mult_out, double* W_out, void* stream) {
+    if (!A || !P || A->n <= 0 || P->n_patches <= 0 || !P->dofs || (P->uniform_size <= 0 && !P->offsets)) {
+        set_error(nullptr, "invalid matrix or patch description");
+        return PSR_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int np = P->n_patches;
+    std::vector<int32_t> ho((size_t)np + 1);
+    if (P->uniform_size > 0) {
+        for (int k = 0; k <= np; ++k) ho[k] = k * P->uniform_size;
+    } else {
+        PSR_CUDA(nullptr, cudaMemcpyAsync(ho.data(), P->offsets, sizeof(int32_t) * (size_t)(np + 1), cudaMemcpyDeviceToHost, s));
+        PSR_CUDA(nullptr, cudaStreamSynchronize(s));
+    }
+    const int64_t total = ho[np];
+    int32_t* status = nullptr;
+    PSR_CUDA(nullptr, cudaMalloc(&status, sizeof(int32_t)));
+    PSR_CUDA(nullptr, cudaMemsetAsync(status, 0, sizeof(int32_t), s));
+    int rc = validate_inputs(nullptr, A, P->uniform_size > 0 ? nullptr : P->offsets, P->dofs, np, total, status, s);
+    int32_t st = 0;
+    if (rc == PSR_OK) {
+        cudaMemcpyAsync(&st, status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        if (st & ST_UNSORTED) rc = PSR_ERR_UNSORTED_CSR;
+        else if (st & ST_OOB) rc = PSR_ERR_INVALID_ARG;
+        if (rc != PSR_OK) set_error(nullptr, "invalid CSR or patch map");
+    }
+    int64_t* mo = nullptr;
+    if (rc == PSR_OK && A_out) {
+        if (P->uniform_size > 0) {
+            rc = launch_extract(A->rowptr, A->colidx, A->vals, nullptr, P->dofs, nullptr, np, P->uniform_size, total, A_out, s);
+        } else {
+            std::vector<int64_t> hm((size_t)np + 1, 0);
+            for (int k = 0; k < np; ++k) {
+                const int64_t pk = ho[k + 1] - ho[k];
+                hm[k + 1] = hm[k] + pk * pk;
+            }
+            if (cudaMalloc(&mo, sizeof(int64_t) * (size_t)(np + 1)) != cudaSuccess) rc = PSR_ERR_OOM;
+            else {
+                cudaMemcpyAsync(mo, hm.data(), sizeof(int64_t) * (size_t)(np + 1), cudaMemcpyHostToDevice, s);
+                rc = launch_extract(A->rowptr, A->colidx, A->vals, P->offsets, P->dofs, mo, np, 0, total, A_out, s);
+            }
+        }
+    }
+    if (rc == PSR_OK && (mult_out || W_out)) {
+        int32_t* mult = mult_out;
+        if (!mult && cudaMalloc(&mult, sizeof(int32_t) * (size_t)A->n) != cudaSuccess) rc = PSR_ERR_OOM;
+        if (rc == PSR_OK) rc = launch_multiplicity(P->dofs, total, A->n, mult, W_out, nullptr, status, s);
+        if (rc == PSR_OK && W_out) {
+            cudaMemcpyAsync(&st, status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+            cudaStreamSynchronize(s);
+            if (st & ST_UNCOVERED) { rc = PSR_ERR_UNCOVERED_DOF; set_error(nullptr, "a DOF belongs to no patch"); }
+        }
+        if (mult && !mult_out) { cudaStreamSynchronize(s); cudaFree(mult); }
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(mo);
+    cudaFree(status);
+    return rc;
+}
+
+int psr_batched_inverse(const double* A, int32_t batch, int32_t p, double* Ainv, int32_t* singular, void* stream) {
+    if (!A || !Ainv || batch < 0 || p < 1 || p > 128) { set_error(nullptr, "invalid batched inverse arguments"); return PSR_ERR_INVALID_ARG; }
+    return launch_batched_inverse(A, (int64_t)p * p, nullptr, batch, p, Ainv, (int64_t)p * p, singular, (cudaStream_t)stream);
+}
+
+int psr_criterion(const double* A_i, int32_t batch, int32_t p, const double* A_c, const double* Binv_c, double tol,
+                  int32_t* accept, double* dval, void* stream) {
+    if (!A_i || !A_c || !Binv_c || !accept || batch < 0 || p < 1 || p > 32 || !(tol >= 0.0)) {
+        set_error(nullptr, "invalid criterion arguments");
+        return PSR_ERR_INVALID_ARG;
+    }
+    if (batch == 0) return PSR_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t* work = nullptr;
+    PSR_CUDA(nullptr, cudaMallocAsync((void**)&work, sizeof(int32_t) * ((size_t)batch + 1), s));
+    int rc = launch_criterion_batch(A_i, batch, p, A_c, Binv_c, tol, accept, dval, work, s);
+    cudaFreeAsync(work, s);
+    return rc;
+}
+
+int psr_spectral_norm(const double* E, int32_t batch, int32_t p, double* sigma, void* stream) {
+    if (!E || !sigma || batch < 0 || p < 1 || p > 32) { set_error(nullptr, "invalid spectral norm arguments"); return PSR_ERR_INVALID_ARG; }
+    if (batch == 0) return PSR_OK;
+    return launch_spectral_norm(E, batch, p, sigma, (cudaStream_t)stream);
+}
+
+}  // extern "C"

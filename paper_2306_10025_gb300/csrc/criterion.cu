@@ -1,0 +1,534 @@
+// Step a3: the patch-similarity criterion d(A_i, B_c) = ||I - A_i B_c^{-1}||_2
+// (Alg. 1, Eq. 4, Eq. 5) and Alg. 1 itself (Patch Tolerance Construction).
+//
+// Criterion form.  With B_c the stored patch A_c, I - A_i A_c^{-1} equals
+// (A_c - A_i) A_c^{-1} in real arithmetic; the library evaluates
+// E = D B_c^{-1}, D = A_c - A_i, which is exactly 0 for identical patches.
+//
+// Certified decision.  Alg. 1 only needs "d < tol".  Per candidate one warp
+// runs a cascade and stops at the first conclusive test:
+//   1. D == 0                                       -> accept (d = 0)
+//   2. ||D||_F ||B^-1||_F (1 + margin) < tol         -> accept (d <= that)
+//   3. form E (p^3 FMAs); ub = min(||E||_F, sqrt(||E||_1 ||E||_inf))
+//      ub + err < tol                                -> accept
+//   4. power iteration on E^T E from the largest row of E; every ||E v|| and
+//      ||E^T w|| / ||w|| is a lower bound; lb - err >= tol -> reject
+//   5. otherwise sigma_max(E) = sqrt(lambda_max(E^T E)) by cyclic Jacobi.
+// err bounds the GEMM rounding, ||E_computed - E||_F <= p u ||D||_F ||B||_F,
+// so tests 2-4 decide "sigma_max(E_computed) < tol" exactly like step 5.
+//
+// Alg. 1 in rounds.  Sequential Alg. 1 compares patch i with the entries in
+// creation order and takes the first with d < tol.  Every entry j was created
+// by a patch r_j < i, and every patch below the newest entry's patch is
+// already assigned.  Hence, round by round: (a) the smallest unassigned patch
+// i0 becomes a new entry; (b) every unassigned patch i > i0 is compared with
+// that entry only, and assigned to it if d < tol.  A patch meets the entries
+// in creation order and stops at its first match, so phi is identical to the
+// sequential loop and so is the number of evaluations; each round is one
+// batched pass over the unassigned patches, with no host decision in it.
+#include "psr_internal.cuh"
+#include "dense.cuh"
+
+namespace psr {
+
+static constexpr double U64 = 0x1p-53;
+
+struct RoundDev {
+    int cursor;        // every local patch below cursor is assigned
+    int i0;            // local index of the newest entry's patch
+    int m;             // entries created so far in this group
+    int done;
+    int n_undec;
+    int first_singular;
+    unsigned long long evals, exact;
+    double binv_fro;
+    int undec_overflow;
+    int pad;
+};
+
+struct WarpScratch {  // per-warp shared memory layout for p <= 32
+    double* E;         // p x (p+1)
+    double* v;         // 32
+    double* w;         // 32
+};
+
+// Decides d(A_i, B_c) < tol for one candidate.  sAc, sB: shared p x ld.
+// Returns 1 accept, 0 reject, -1 undecided (needs the exact path).  *dv gets
+// the deciding value.  All lanes call; lane r handles row r.
+__device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, const double* sB,
+                           int p, int ld, double binv_fro, double tol, WarpScratch ws, double* dv,
+                           bool allow_exact_here) {
+    const int lane = threadIdx.x & 31;
+    const bool act = lane < p;
+    // pass 1: D = A_c - A_i
+    double dn2 = 0.0, da2 = 0.0;
+    if (act) {
+        for (int j = 0; j < p; ++j) {
+            const double d = sAc[lane * ld + j] - Ai[lane * p + j];
+            dn2 = fma(d, d, dn2);
+        }
+    }
+    dn2 = warp_sum(dn2);
+    (void)da2;
+    if (dn2 == 0.0) { *dv = 0.0; return 1; }
+    const double dF = sqrt(dn2);
+    const double err = 1.01 * (double)(p + 2) * U64 * dF * binv_fro;   // GEMM + norm rounding
+    {
+        const double ub0 = dF * binv_fro * (1.0 + 4.0 * (double)(p + 2) * U64);
+        if (ub0 < tol) { *dv = ub0; return 1; }
+    }
+    // pass 2: E row = D row * B^-1
+    double e[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) e[j] = 0.0;
+    if (act) {
+        for (int k = 0; k < p; ++k) {
+            const double dk = sAc[lane * ld + k] - Ai[lane * p + k];
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (j < p) e[j] = fma(dk, sB[k * ld + j], e[j]);
+        }
+    }
+    double fro2 = 0.0, rabs = 0.0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        if (j < p) { fro2 = fma(e[j], e[j], fro2); rabs += fabs(e[j]); }
+    }
+    const double rown = sqrt(fro2);
+    fro2 = warp_sum(fro2);
+    const double ninf = warp_max(act ? rabs : 0.0);
+    if (act) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (j < p) ws.E[lane * ld + j] = e[j];
+    }
+    __syncwarp();
+    double cabs = 0.0;
+    if (act)
+        for (int r = 0; r < p; ++r) cabs += fabs(ws.E[r * ld + lane]);
+    const double none = warp_max(cabs);
+    const double slack = 1.0 + 4.0 * (double)(p + 2) * U64;
+    const double ub = fmin(sqrt(fro2), sqrt(none * ninf)) * slack;
+    if (ub + err < tol) { *dv = ub; return 1; }
+    // lower bound: the largest row norm (||E^T e_r||), then power steps
+    double best = act ? rown : -1.0;
+    int br = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, br, o);
+        if (ob > best || (ob == best && oi < br)) { best = ob; br = oi; }
+    }
+    const double shrink = 1.0 - 4.0 * (double)(p + 2) * U64;
+    double lb = best;
+    if (lb * shrink - err >= tol) { *dv = lb; return 0; }
+    if (!(best > 0.0)) { *dv = 0.0; return 1; }   // E == 0 after rounding
+    if (act) ws.v[lane] = ws.E[br * ld + lane] / best;
+    __syncwarp();
+    for (int it = 0; it < 16; ++it) {
+        double wr = 0.0;
+        if (act) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (j < p) wr = fma(e[j], ws.v[j], wr);
+        }
+        const double nw = sqrt(warp_sum(wr * wr));
+        lb = fmax(lb, nw);
+        if (lb * shrink - err >= tol) { *dv = lb; return 0; }
+        if (!(nw > 0.0)) break;
+        if (act) ws.w[lane] = wr;
+        __syncwarp();
+        double uj = 0.0;
+        if (act)
+            for (int r = 0; r < p; ++r) uj = fma(ws.E[r * ld + lane], ws.w[r], uj);
+        const double nu = sqrt(warp_sum(uj * uj));
+        lb = fmax(lb, nu / nw);
+        if (lb * shrink - err >= tol) { *dv = lb; return 0; }
+        if (!(nu > 0.0)) break;
+        __syncwarp();
+        if (act) ws.v[lane] = uj / nu;
+        __syncwarp();
+    }
+    if (!allow_exact_here) { *dv = lb; return -1; }
+    // exact: G = E^T E into ws.E (overwrites E; e[] still holds rows)
+    __syncwarp();
+    // column j of E lives in lane j after a transpose read
+    double ecol[32];
+    if (act) {
+#pragma unroll
+        for (int r = 0; r < 32; ++r) ecol[r] = (r < p) ? ws.E[r * ld + lane] : 0.0;
+    }
+    __syncwarp();
+    if (act) {
+        for (int k = 0; k < p; ++k) {     // G[lane][k] = sum_r E[r][lane] E[r][k]
+            double g = 0.0;
+            for (int r = 0; r < p; ++r) g = fma(ecol[r], __shfl_sync(0xffffffffu, ecol[r], k), g);
+            ws.E[lane * ld + k] = g;
+        }
+    } else {
+        for (int k = 0; k < p; ++k)
+            for (int r = 0; r < p; ++r) (void)__shfl_sync(0xffffffffu, 0.0, k);
+    }
+    __syncwarp();
+    const double lam = jacobi_lambda_max_warp(ws.E, p, ld);
+    const double sig = sqrt(fmax(lam, 0.0));
+    *dv = sig;
+    return sig < tol ? 1 : 0;
+}
+
+// ---------------------------------------------------------------- rounds
+__host__ __device__ inline size_t eval_smem_bytes(int p, int wpb) {
+    const int ld = p + 1;
+    return (size_t)(2 * p * ld) * 8 + (size_t)wpb * ((size_t)p * ld + 64) * 8;
+}
+
+// One CTA: next entry = smallest unassigned local patch at or after cursor;
+// then warp 0 inverts it into the FP64 database (slot m).
+__global__ void k_round_begin(RoundDev* st, int32_t* __restrict__ phi, int count,
+                              const double* __restrict__ Ag, int p, double* __restrict__ Binv,
+                              int32_t* __restrict__ rep_local, int32_t* __restrict__ singular_flags,
+                              int group_base) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_first;
+    if (st->done) return;
+    const int tid = threadIdx.x;
+    if (tid == 0) { s_first = count; st->n_undec = 0; }
+    __syncthreads();
+    for (int base = st->cursor; base < count; base += blockDim.x) {
+        const int i = base + tid;
+        if (i < count && phi[i] == -1) atomicMin(&s_first, i);
+        __syncthreads();
+        if (s_first < count) break;
+        __syncthreads();
+    }
+    const int i0 = s_first;
+    if (i0 >= count) {
+        if (tid == 0) st->done = 1;
+        return;
+    }
+    const int m = st->m;
+    if (tid < 32) {
+        const int ld = p + 1;
+        double* S = reinterpret_cast<double*>(smem);
+        double* colk = S + p * ld;
+        int* swaps = reinterpret_cast<int*>(colk + p);
+        const double* a = Ag + (int64_t)i0 * p * p;
+        for (int e = tid; e < p * p; e += 32) S[(e / p) * ld + (e % p)] = a[e];
+        __syncwarp();
+        const bool sing = gj_invert_warp(S, p, ld, colk, swaps);
+        double fro = 0.0;
+        double* out = Binv + (int64_t)m * p * p;
+        for (int e = tid; e < p * p; e += 32) {
+            const double v = S[(e / p) * ld + (e % p)];
+            out[e] = v;
+            fro = fma(v, v, fro);
+        }
+        fro = warp_sum(fro);
+        if (tid == 0) {
+            st->binv_fro = sqrt(fro);
+            if (sing) {
+                singular_flags[0] = 1;
+                if (st->first_singular < 0) st->first_singular = group_base + i0;
+            }
+            phi[i0] = m;
+            rep_local[m] = i0;
+            st->i0 = i0;
+            st->cursor = i0 + 1;
+            st->m = m + 1;
+        }
+    }
+}
+
+// Persistent warps over local patches (i0, count): every unassigned one is
+// compared with the newest entry.  Undecided candidates go to a list.
+__global__ void k_round_eval(RoundDev* st, int32_t* __restrict__ phi, int count,
+                             const double* __restrict__ Ag, int p, const double* __restrict__ Binv,
+                             double tol, int32_t* __restrict__ undec, int undec_cap) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (st->done) return;
+    const int ld = p + 1;
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const int i0 = st->i0;
+    const int m = st->m - 1;
+    const double bfro = st->binv_fro;
+    double* sAc = reinterpret_cast<double*>(smem);
+    double* sB = sAc + p * ld;
+    double* wbase = sB + p * ld + (size_t)wid * (p * ld + 64);
+    WarpScratch ws{wbase, wbase + p * ld, wbase + p * ld + 32};
+    const double* a = Ag + (int64_t)i0 * p * p;
+    const double* bm = Binv + (int64_t)m * p * p;
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        sAc[(e / p) * ld + (e % p)] = a[e];
+        sB[(e / p) * ld + (e % p)] = bm[e];
+    }
+    __syncthreads();
+    unsigned long long my_evals = 0;
+    const int start = i0 + 1;
+    const int gw = blockIdx.x * wpb + wid;
+    const int nw = gridDim.x * wpb;
+    for (int base = start + gw * 32; base < count; base += nw * 32) {
+        const int i = base + lane;
+        const bool open = (i < count) && (phi[i] == -1);
+        unsigned mask = __ballot_sync(0xffffffffu, open);
+        while (mask) {
+            const int b = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const int cand = base + b;
+            double dv;
+            const int dec = decide_pair(Ag + (int64_t)cand * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, false);
+            ++my_evals;
+            if (lane == 0) {
+                if (dec == 1) phi[cand] = m;
+                else if (dec < 0) {
+                    const int slot = atomicAdd(&st->n_undec, 1);
+                    if (slot < undec_cap) undec[slot] = cand;
+                    else atomicExch(&st->undec_overflow, 1);
+                }
+            }
+            __syncwarp();
+        }
+    }
+    if (lane == 0 && my_evals) atomicAdd(&st->evals, my_evals);
+}
+
+// Exact path for the undecided candidates of this round.
+__global__ void k_round_exact(RoundDev* st, int32_t* __restrict__ phi, const double* __restrict__ Ag,
+                              int p, const double* __restrict__ Binv, double tol,
+                              const int32_t* __restrict__ undec, int undec_cap) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (st->done) return;
+    const int nund = min(st->n_undec, undec_cap);
+    if (nund == 0) return;
+    const int ld = p + 1;
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const int i0 = st->i0;
+    const int m = st->m - 1;
+    const double bfro = st->binv_fro;
+    double* sAc = reinterpret_cast<double*>(smem);
+    double* sB = sAc + p * ld;
+    double* wbase = sB + p * ld + (size_t)wid * (p * ld + 64);
+    WarpScratch ws{wbase, wbase + p * ld, wbase + p * ld + 32};
+    const double* a = Ag + (int64_t)i0 * p * p;
+    const double* bm = Binv + (int64_t)m * p * p;
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        sAc[(e / p) * ld + (e % p)] = a[e];
+        sB[(e / p) * ld + (e % p)] = bm[e];
+    }
+    __syncthreads();
+    for (int u = blockIdx.x * wpb + wid; u < nund; u += gridDim.x * wpb) {
+        const int cand = undec[u];
+        double dv;
+        const int dec = decide_pair(Ag + (int64_t)cand * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, true);
+        if (lane == 0) {
+            if (dec == 1) phi[cand] = m;
+            atomicAdd(&st->exact, 1ull);
+        }
+        __syncwarp();
+    }
+}
+
+static int set_smem(const void* f, size_t bytes) {
+    if (bytes > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "criterion smem attribute");
+    }
+    return PSR_OK;
+}
+
+// Runs Alg. 1 for every size group.  On entry ctx->A_ext holds the patches
+// (group-contiguous); on exit ctx->phi / rep_ids hold the global assignment
+// and every group's FP64 database is in a temporary buffer that is converted
+// by the sweep builder.  Returns the FP64 database via ctx->groups[g].rinv
+// (double*, m x p x p) -- the storage conversion happens in build_sweep.
+int run_alg1_rounds(psr_ctx* ctx, cudaStream_t s) {
+    const double tol = ctx->opts.tol;
+    RoundDev* st = nullptr;
+    RoundDev* h_st = nullptr;
+    PSR_CUDA(ctx, cudaMalloc(&st, sizeof(RoundDev)));
+    PSR_CUDA(ctx, cudaMallocHost(&h_st, sizeof(RoundDev)));
+    int32_t* sing_flag = nullptr;
+    PSR_CUDA(ctx, cudaMalloc(&sing_flag, sizeof(int32_t)));
+    PSR_CUDA(ctx, cudaMemsetAsync(sing_flag, 0, sizeof(int32_t), s));
+    int rc = PSR_OK;
+    int entry_base = 0;
+    int64_t total_evals = 0, total_exact = 0;
+    int rounds_total = 0;
+    int first_singular = -1;
+    for (size_t g = 0; g < ctx->groups.size() && rc == PSR_OK; ++g) {
+        Group& G = ctx->groups[g];
+        const int p = G.p, count = G.count;
+        const double* Ag = ctx->A_ext + G.mat_off;
+        int32_t* phi_l = nullptr;
+        int32_t* rep_l = nullptr;
+        int32_t* undec = nullptr;
+        double* Binv = nullptr;
+        const int undec_cap = count;
+        PSR_CUDA(ctx, cudaMalloc(&phi_l, sizeof(int32_t) * count));
+        PSR_CUDA(ctx, cudaMalloc(&rep_l, sizeof(int32_t) * count));
+        PSR_CUDA(ctx, cudaMalloc(&undec, sizeof(int32_t) * undec_cap));
+        cudaError_t ea = cudaMalloc(&Binv, sizeof(double) * (size_t)count * p * p);
+        if (ea != cudaSuccess) { cudaGetLastError(); set_error(ctx, "out of device memory for the database"); return PSR_ERR_OOM; }
+        PSR_CUDA(ctx, cudaMemsetAsync(phi_l, 0xff, sizeof(int32_t) * count, s));
+        RoundDev init{};
+        init.first_singular = -1;
+        PSR_CUDA(ctx, cudaMemcpyAsync(st, &init, sizeof(RoundDev), cudaMemcpyHostToDevice, s));
+        const int ld = p + 1;
+        const size_t smem_begin = (size_t)((p * ld + p) * 8 + p * 4 + 16);
+        const int wpb = 8;
+        const size_t smem_eval = eval_smem_bytes(p, wpb);
+        if ((rc = set_smem((const void*)k_round_begin, smem_begin)) != PSR_OK) break;
+        if ((rc = set_smem((const void*)k_round_eval, smem_eval)) != PSR_OK) break;
+        if ((rc = set_smem((const void*)k_round_exact, smem_eval)) != PSR_OK) break;
+        int eval_blocks = (count + wpb * 32 - 1) / (wpb * 32);
+        if (eval_blocks > 152 * 2) eval_blocks = 152 * 2;
+        if (eval_blocks < 1) eval_blocks = 1;
+        int batch = 4;
+        int issued = 0;
+        for (;;) {
+            for (int r = 0; r < batch; ++r) {
+                k_round_begin<<<1, 256, smem_begin, s>>>(st, phi_l, count, Ag, p, Binv, rep_l, sing_flag, 0);
+                k_round_eval<<<eval_blocks, wpb * 32, smem_eval, s>>>(st, phi_l, count, Ag, p, Binv, tol, undec, undec_cap);
+                k_round_exact<<<64, wpb * 32, smem_eval, s>>>(st, phi_l, Ag, p, Binv, tol, undec, undec_cap);
+            }
+            PSR_CHECK_LAUNCH(ctx, "Alg. 1 round kernels");
+            issued += batch;
+            PSR_CUDA(ctx, cudaMemcpyAsync(h_st, st, sizeof(RoundDev), cudaMemcpyDeviceToHost, s));
+            PSR_CUDA(ctx, cudaStreamSynchronize(s));
+            if (h_st->done) break;
+            if (issued > count + 8) { set_error(ctx, "Alg. 1 rounds did not terminate"); rc = PSR_ERR_TIMEOUT; break; }
+            if (batch < 256) batch *= 2;
+        }
+        if (rc != PSR_OK) break;
+        if (h_st->undec_overflow) { set_error(ctx, "criterion undecided list overflow"); rc = PSR_ERR_CUDA; break; }
+        G.m = h_st->m;
+        total_evals += (int64_t)h_st->evals;
+        total_exact += (int64_t)h_st->exact;
+        rounds_total += h_st->m;
+        if (h_st->first_singular >= 0 && first_singular < 0) first_singular = h_st->first_singular;
+        // global phi / rep ids: phi[global] = entry_base + phi_l[local]
+        std::vector<int32_t> hphi(count), hrep(G.m);
+        PSR_CUDA(ctx, cudaMemcpyAsync(hphi.data(), phi_l, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, s));
+        PSR_CUDA(ctx, cudaMemcpyAsync(hrep.data(), rep_l, sizeof(int32_t) * G.m, cudaMemcpyDeviceToHost, s));
+        PSR_CUDA(ctx, cudaStreamSynchronize(s));
+        G.h_rep.resize(G.m);
+        for (int j = 0; j < G.m; ++j) G.h_rep[j] = hrep[j];      // local patch index of entry j
+        // store the local assignment; the caller maps it to global ids
+        G.sphi = phi_l;             // temporary: local phi in original (unsorted) order
+        G.rinv = Binv;              // temporary: FP64 database, converted in build_sweep
+        cudaFree(rep_l);
+        cudaFree(undec);
+        (void)hphi;
+        entry_base += G.m;
+    }
+    cudaFree(st);
+    cudaFreeHost(h_st);
+    cudaFree(sing_flag);
+    ctx->stats.criterion_evals = total_evals;
+    ctx->stats.criterion_exact = total_exact;
+    ctx->stats.rounds = rounds_total;
+    ctx->stats.first_singular = first_singular;
+    return rc;
+}
+
+// ------------------------------------------------------ stateless entry
+__global__ void k_criterion_batch(const double* __restrict__ A_i, int32_t batch, int p,
+                                  const double* __restrict__ A_c, const double* __restrict__ Binv_c,
+                                  double tol, int32_t* __restrict__ accept, double* __restrict__ dval,
+                                  int32_t* __restrict__ undec, int32_t* __restrict__ n_undec, int phase) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int ld = p + 1;
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    double* sAc = reinterpret_cast<double*>(smem);
+    double* sB = sAc + p * ld;
+    double* wbase = sB + p * ld + (size_t)wid * (p * ld + 64);
+    WarpScratch ws{wbase, wbase + p * ld, wbase + p * ld + 32};
+    double bf = 0.0;
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        sAc[(e / p) * ld + (e % p)] = A_c[e];
+        sB[(e / p) * ld + (e % p)] = Binv_c[e];
+    }
+    __syncthreads();
+    for (int e = lane; e < p * p; e += 32) bf = fma(Binv_c[e], Binv_c[e], bf);
+    bf = sqrt(warp_sum(bf));
+    const int total = (phase == 0) ? batch : *n_undec;
+    for (int u = blockIdx.x * wpb + wid; u < total; u += gridDim.x * wpb) {
+        const int b = (phase == 0) ? u : undec[u];
+        double dv;
+        const int dec = decide_pair(A_i + (int64_t)b * p * p, sAc, sB, p, ld, bf, tol, ws, &dv, phase == 1);
+        if (lane == 0) {
+            if (dec >= 0) {
+                accept[b] = dec;
+                if (dval) dval[b] = dv;
+            } else {
+                const int slot = atomicAdd(n_undec, 1);
+                undec[slot] = b;       // slot < batch always
+            }
+        }
+        __syncwarp();
+    }
+}
+
+int launch_criterion_batch(const double* A_i, int32_t batch, int32_t p, const double* A_c,
+                           const double* Binv_c, double tol, int32_t* accept, double* dval,
+                           int32_t* work, cudaStream_t s) {
+    // work: device int32 scratch of batch + 1 entries (undecided list + count)
+    const int wpb = 8;
+    const size_t sm = eval_smem_bytes(p, wpb);
+    int rc = set_smem((const void*)k_criterion_batch, sm);
+    if (rc != PSR_OK) return rc;
+    cudaError_t e = cudaMemsetAsync(work + batch, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "criterion scratch reset");
+    int blocks = (batch + wpb - 1) / wpb;
+    if (blocks > 152 * 4) blocks = 152 * 4;
+    if (blocks < 1) blocks = 1;
+    k_criterion_batch<<<blocks, wpb * 32, sm, s>>>(A_i, batch, p, A_c, Binv_c, tol, accept, dval, work, work + batch, 0);
+    k_criterion_batch<<<blocks, wpb * 32, sm, s>>>(A_i, batch, p, A_c, Binv_c, tol, accept, dval, work, work + batch, 1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "k_criterion_batch");
+    return PSR_OK;
+}
+
+__global__ void k_spectral_norm(const double* __restrict__ E, int32_t batch, int p, double* __restrict__ sigma) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int ld = p + 1;
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    double* G = reinterpret_cast<double*>(smem) + (size_t)wid * p * ld;
+    for (int b = blockIdx.x * wpb + wid; b < batch; b += gridDim.x * wpb) {
+        const double* e = E + (int64_t)b * p * p;
+        double col[32];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) col[r] = (lane < p && r < p) ? e[r * p + lane] : 0.0;
+        for (int k = 0; k < p; ++k) {
+            double g = 0.0;
+#pragma unroll
+            for (int r = 0; r < 32; ++r) g = fma(col[r], __shfl_sync(0xffffffffu, col[r], k), g);
+            if (lane < p) G[lane * ld + k] = g;
+        }
+        __syncwarp();
+        const double lam = jacobi_lambda_max_warp(G, p, ld);
+        if (lane == 0) sigma[b] = sqrt(fmax(lam, 0.0));
+        __syncwarp();
+    }
+}
+
+int launch_spectral_norm(const double* E, int32_t batch, int32_t p, double* sigma, cudaStream_t s) {
+    const int wpb = 4;
+    const size_t sm = (size_t)wpb * p * (p + 1) * 8;
+    int blocks = (batch + wpb - 1) / wpb;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks < 1) blocks = 1;
+    k_spectral_norm<<<blocks, wpb * 32, sm, s>>>(E, batch, p, sigma);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "k_spectral_norm");
+    return PSR_OK;
+}
+
+}  // namespace psr

@@ -1,0 +1,561 @@
+// Step a5: the outer Krylov solve of A x = b preconditioned on the right by
+// the patch sweep (section 4: GMRES with x0 = 0 until the initial residual is
+// reduced by 1e-8).  PCG for symmetric positive definite problems with the
+// symmetric weighting; flexible GMRES(m) otherwise.
+//
+// Everything stays on the device: scalars (alpha, beta, Hessenberg matrix,
+// Givens rotations, residual estimates) live in device memory and every
+// kernel checks a device stop flag, so a whole CG block or FGMRES cycle is
+// enqueued (and captured into one CUDA graph) without host decisions; the
+// host reads the stop flag once per block / cycle.
+//
+// Reductions are deterministic: a fixed grid writes per-block partial sums,
+// the last block to finish (ticket counter) adds them in a fixed order.
+// FGMRES orthogonalises with classical Gram-Schmidt applied twice (two
+// batched passes instead of j+1 dependent ones); residual history entries are
+// |g_{j+1}| / ||r_0|| as in the FP64 reference formulation.
+#include "psr_internal.cuh"
+
+#include <algorithm>
+
+namespace psr {
+
+int sweep_apply_ex(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s);
+
+enum { S_RZ = 0, S_PQ, S_ALPHA, S_BETA, S_RN, S_R0, S_RTOL, S_H = 16 };
+enum { I_STOP = 0, I_CONV, I_IT, I_K, I_MAXIT, I_M, I_CNT = 8, I_NCNT = 8 };
+
+struct KDims {
+    int n, m, nb;
+    double* scal;
+    int32_t* ictl;
+    double* part;
+    double* hist;
+};
+
+__device__ __forceinline__ double* Hm(double* sc, int m) { return sc + S_H; }
+__device__ __forceinline__ double* CSv(double* sc, int m) { return sc + S_H + (m + 1) * m; }
+__device__ __forceinline__ double* SNv(double* sc, int m) { return CSv(sc, m) + m; }
+__device__ __forceinline__ double* Gv(double* sc, int m) { return SNv(sc, m) + m; }
+__device__ __forceinline__ double* Yv(double* sc, int m) { return Gv(sc, m) + m + 1; }
+__device__ __forceinline__ double* Hv(double* sc, int m) { return Yv(sc, m) + m; }   // pass vector (<=64)
+static inline int scal_count(int m) { return S_H + (m + 1) * m + m + m + (m + 1) + m + 64 + 8; }
+
+// Block-wide sum, result valid in thread 0.  sh: 32 doubles of shared memory.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (wid == 0) {
+        t = (lane < nw) ? sh[lane] : 0.0;
+        t = warp_sum(t);
+    }
+    return t;
+}
+
+// Last-block ticket: returns true in exactly one block, after every block has
+// published its partials.
+__device__ __forceinline__ bool last_block(int32_t* cnt) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int t = atomicAdd(cnt, 1);
+        s_last = (t == (int)gridDim.x - 1);
+        if (s_last) *cnt = 0;
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last != 0;
+}
+
+// Sum of nb partials in a fixed order by warp 0; valid in thread 0.
+__device__ __forceinline__ double sum_partials(const double* part, int nb) {
+    double v = 0.0;
+    if (threadIdx.x < 32) {
+        for (int b = threadIdx.x; b < nb; b += 32) v += part[b];
+        v = warp_sum(v);
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------- SpMV
+// mode 0: y = A x;  mode 1: y = b - A x and ||y||^2;  mode 2: y = A x and (x . y)
+template <int TPR>
+__global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                              const double* __restrict__ vals, const double* __restrict__ x,
+                                              double* __restrict__ y, const double* __restrict__ b, int n, int mode,
+                                              KDims kd, int stop_check, int fin) {
+    __shared__ double sh[32];
+    if (stop_check && kd.ictl[I_STOP]) return;
+    const int sub = threadIdx.x % TPR;
+    const int rows_per_block = blockDim.x / TPR;
+    double acc = 0.0;
+    for (int row = blockIdx.x * rows_per_block + threadIdx.x / TPR; row < n; row += gridDim.x * rows_per_block) {
+        const int rs = rowptr[row], re = rowptr[row + 1];
+        double s = 0.0;
+        for (int e = rs + sub; e < re; e += TPR) s = fma(vals[e], x[colidx[e]], s);
+#pragma unroll
+        for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, TPR);
+        if (sub == 0) {
+            if (mode == 1) {
+                const double v = b[row] - s;
+                y[row] = v;
+                acc = fma(v, v, acc);
+            } else {
+                y[row] = s;
+                if (mode == 2) acc = fma(x[row], s, acc);
+            }
+        }
+    }
+    if (mode == 0) return;
+    const double bs = block_sum(acc, sh);
+    if (threadIdx.x == 0) kd.part[blockIdx.x] = bs;
+    if (!last_block(kd.ictl + I_CNT + 0)) return;
+    const double tot = sum_partials(kd.part, gridDim.x);
+    if (threadIdx.x != 0) return;
+    double* sc = kd.scal;
+    int32_t* ic = kd.ictl;
+    if (fin == 1) {                 // CG: pq and alpha
+        sc[S_PQ] = tot;
+        sc[S_ALPHA] = sc[S_RZ] / tot;
+    } else if (fin == 2) {          // FGMRES restart: beta = ||b - A x||
+        const double beta = sqrt(tot);
+        sc[S_RN] = beta;
+        double* g = Gv(sc, ic[I_M]);
+        g[0] = beta;
+        if (beta == 0.0) { ic[I_STOP] = 1; ic[I_CONV] = 1; }
+    }
+}
+
+// ---------------------------------------------------------------- vectors
+// ||v||^2 -> initial residual (fin 0) ; also copies v into out (if non-null)
+__global__ void k_init_norm(const double* __restrict__ v, double* __restrict__ out1, double* __restrict__ out2,
+                            int n, KDims kd, int zero_x, double* __restrict__ x) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double a = v[i];
+        if (out1) out1[i] = a;
+        if (out2) out2[i] = a;
+        if (zero_x) x[i] = 0.0;
+        acc = fma(a, a, acc);
+    }
+    const double bs = block_sum(acc, sh);
+    if (threadIdx.x == 0) kd.part[blockIdx.x] = bs;
+    if (!last_block(kd.ictl + I_CNT + 1)) return;
+    const double tot = sum_partials(kd.part, gridDim.x);
+    if (threadIdx.x != 0) return;
+    double* sc = kd.scal;
+    int32_t* ic = kd.ictl;
+    const double r0 = sqrt(tot);
+    sc[S_R0] = r0;
+    sc[S_RN] = r0;
+    kd.hist[0] = 1.0;
+    ic[I_IT] = 0;
+    ic[I_K] = 0;
+    ic[I_CONV] = (r0 == 0.0);
+    ic[I_STOP] = (r0 == 0.0);
+    if (ic[I_M] > 0) Gv(sc, ic[I_M])[0] = r0;
+}
+
+// dot(a, b) with a finalisation: fin 1 = CG rz initial; fin 2 = CG beta update
+__global__ void k_dot(const double* __restrict__ a, const double* __restrict__ b, int n, KDims kd, int fin) {
+    __shared__ double sh[32];
+    if (kd.ictl[I_STOP]) return;
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) acc = fma(a[i], b[i], acc);
+    const double bs = block_sum(acc, sh);
+    if (threadIdx.x == 0) kd.part[blockIdx.x] = bs;
+    if (!last_block(kd.ictl + I_CNT + 2)) return;
+    const double tot = sum_partials(kd.part, gridDim.x);
+    if (threadIdx.x != 0) return;
+    double* sc = kd.scal;
+    if (fin == 1) {
+        sc[S_RZ] = tot;
+    } else {
+        sc[S_BETA] = tot / sc[S_RZ];
+        sc[S_RZ] = tot;
+    }
+}
+
+__global__ void k_copy(const double* __restrict__ a, double* __restrict__ b, int n, KDims kd) {
+    if (kd.ictl[I_STOP]) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = a[i];
+}
+
+// CG: x += alpha p; r -= alpha q; ||r|| -> history, convergence
+__global__ void k_cg_xr(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                        const double* __restrict__ q, int n, KDims kd) {
+    __shared__ double sh[32];
+    if (kd.ictl[I_STOP]) return;
+    const double alpha = kd.scal[S_ALPHA];
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const double ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        acc = fma(ri, ri, acc);
+    }
+    const double bs = block_sum(acc, sh);
+    if (threadIdx.x == 0) kd.part[blockIdx.x] = bs;
+    if (!last_block(kd.ictl + I_CNT + 3)) return;
+    const double tot = sum_partials(kd.part, gridDim.x);
+    if (threadIdx.x != 0) return;
+    double* sc = kd.scal;
+    int32_t* ic = kd.ictl;
+    const double rn = sqrt(tot);
+    sc[S_RN] = rn;
+    const int it = ic[I_IT] + 1;
+    ic[I_IT] = it;
+    kd.hist[it] = rn / sc[S_R0];
+    if (rn <= sc[S_RTOL] * sc[S_R0]) { ic[I_CONV] = 1; ic[I_STOP] = 1; }
+    else if (it >= ic[I_MAXIT]) ic[I_STOP] = 1;
+}
+
+__global__ void k_cg_p(double* __restrict__ p, const double* __restrict__ z, int n, KDims kd) {
+    if (kd.ictl[I_STOP]) return;
+    const double beta = kd.scal[S_BETA];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = fma(beta, p[i], z[i]);
+}
+
+// ---------------------------------------------------------------- FGMRES
+// cycle start: V_0 = r / beta, g = (beta, 0, ...), K = 0
+__global__ void k_fg_start(const double* __restrict__ r, double* __restrict__ V0, int n, KDims kd) {
+    if (kd.ictl[I_STOP]) return;
+    const double beta = kd.scal[S_RN];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) V0[i] = r[i] / beta;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int m = kd.m;
+        double* g = Gv(kd.scal, m);
+        g[0] = beta;
+        for (int i = 1; i <= m; ++i) g[i] = 0.0;
+        kd.ictl[I_K] = 0;
+    }
+}
+
+// h_i = V_i . w for i <= j (pass 1 -> H column j; pass 2 -> added to it)
+__global__ void __launch_bounds__(256) k_mdot(const double* __restrict__ V, const double* __restrict__ w, int n, int j,
+                                              KDims kd, int pass) {
+    __shared__ double sh[32][9];
+    if (kd.ictl[I_STOP]) return;
+    const int nv = j + 1;
+    double acc[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i] = 0.0;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const double we = w[e];
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            if (i < nv) acc[i] = fma(V[(int64_t)i * n + e], we, acc[i]);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        if (i < nv) {
+            const double t = warp_sum(acc[i]);
+            if (lane == 0) sh[i][wid] = t;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < nv) {
+        double t = 0.0;
+        for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) t += sh[threadIdx.x][wv];
+        kd.part[threadIdx.x * gridDim.x + blockIdx.x] = t;
+    }
+    if (!last_block(kd.ictl + I_CNT + 4)) return;
+    // warp wv sums vector i = wv, wv + nwarps, ... over blocks
+    const int m = kd.m;
+    double* H = Hm(kd.scal, m);
+    double* hv = Hv(kd.scal, m);
+    for (int i = wid; i < nv; i += (int)(blockDim.x >> 5)) {
+        double v = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) v += kd.part[i * gridDim.x + b];
+        v = warp_sum(v);
+        if (lane == 0) {
+            hv[i] = v;
+            if (pass == 0) H[i * m + j] = v;
+            else H[i * m + j] += v;
+        }
+    }
+}
+
+// w -= sum_i h_i V_i (h from the last k_mdot); pass 2 also accumulates ||w||^2
+// and finishes the Arnoldi step: H[j+1][j], Givens rotation, residual estimate.
+__global__ void __launch_bounds__(256) k_maxpy(const double* __restrict__ V, double* __restrict__ w, int n, int j,
+                                               KDims kd, int pass) {
+    __shared__ double sh[32];
+    __shared__ double sh_h[33];
+    if (kd.ictl[I_STOP]) return;
+    const int nv = j + 1;
+    const int m = kd.m;
+    if (threadIdx.x < nv) sh_h[threadIdx.x] = Hv(kd.scal, m)[threadIdx.x];
+    __syncthreads();
+    double acc = 0.0;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        double we = w[e];
+        for (int i = 0; i < nv; ++i) we = fma(-sh_h[i], V[(int64_t)i * n + e], we);
+        w[e] = we;
+        acc = fma(we, we, acc);
+    }
+    if (pass == 0) return;
+    const double bs = block_sum(acc, sh);
+    if (threadIdx.x == 0) kd.part[blockIdx.x] = bs;
+    if (!last_block(kd.ictl + I_CNT + 5)) return;
+    const double tot = sum_partials(kd.part, gridDim.x);
+    if (threadIdx.x != 0) return;
+    double* sc = kd.scal;
+    int32_t* ic = kd.ictl;
+    double* H = Hm(sc, m);
+    double* cs = CSv(sc, m);
+    double* sn = SNv(sc, m);
+    double* g = Gv(sc, m);
+    const double hn = sqrt(tot);
+    H[(j + 1) * m + j] = hn;
+    for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
+        H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
+        H[i * m + j] = t;
+    }
+    const double den = hypot(H[j * m + j], H[(j + 1) * m + j]);
+    cs[j] = H[j * m + j] / den;
+    sn[j] = H[(j + 1) * m + j] / den;
+    H[j * m + j] = den;
+    sc[S_BETA] = hn;                    // keep ||w|| for the normalisation
+    H[(j + 1) * m + j] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    const int it = ic[I_IT] + 1;
+    ic[I_IT] = it;
+    ic[I_K] = j + 1;
+    const double res = fabs(g[j + 1]);
+    kd.hist[it] = res / sc[S_R0];
+    sc[S_RN] = res;
+    if (res <= sc[S_RTOL] * sc[S_R0]) { ic[I_CONV] = 1; ic[I_STOP] = 1; }
+    else if (it >= ic[I_MAXIT] || den == 0.0) ic[I_STOP] = 1;
+}
+
+__global__ void k_fg_scale(double* __restrict__ w, int n, KDims kd) {
+    if (kd.ictl[I_STOP]) return;
+    const double hn = kd.scal[S_BETA];
+    if (hn == 0.0) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) w[i] = w[i] / hn;
+}
+
+// Cycle end: y = H(1:K,1:K)^{-1} g(1:K) by back substitution (one thread).
+__global__ void k_fg_solve(KDims kd) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int m = kd.m;
+    const int K = kd.ictl[I_K];
+    double* H = Hm(kd.scal, m);
+    double* g = Gv(kd.scal, m);
+    double* y = Yv(kd.scal, m);
+    for (int i = K - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int l = i + 1; l < K; ++l) s -= H[i * m + l] * y[l];
+        y[i] = s / H[i * m + i];
+    }
+}
+
+// x += sum_{i<K} y_i Z_i ; then K = 0 (the update is consumed)
+__global__ void k_fg_update(double* __restrict__ x, const double* __restrict__ Z, int n, KDims kd) {
+    __shared__ double sy[64];
+    const int K = kd.ictl[I_K];
+    if (K == 0) return;
+    const double* y = Yv(kd.scal, kd.m);
+    if (threadIdx.x < K) sy[threadIdx.x] = y[threadIdx.x];
+    __syncthreads();
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        double xe = x[e];
+        for (int i = 0; i < K; ++i) xe = fma(sy[i], Z[(int64_t)i * n + e], xe);
+        x[e] = xe;
+    }
+}
+
+// ---------------------------------------------------------------- host
+static int spmv_tpr(psr_ctx* ctx) {
+    const double avg = ctx->n ? (double)ctx->nnz / ctx->n : 1.0;
+    if (avg <= 6) return 4;
+    if (avg <= 12) return 8;
+    if (avg <= 40) return 16;
+    return 32;
+}
+
+static void launch_spmv(psr_ctx* ctx, const double* x, double* y, const double* b, int mode, int fin,
+                        KDims kd, int stop_check, int nb, cudaStream_t s) {
+    const int tpr = spmv_tpr(ctx);
+    const int n = ctx->n;
+    switch (tpr) {
+        case 4: k_spmv<4><<<nb, 256, 0, s>>>(ctx->rowptr, ctx->colidx, ctx->vals, x, y, b, n, mode, kd, stop_check, fin); break;
+        case 8: k_spmv<8><<<nb, 256, 0, s>>>(ctx->rowptr, ctx->colidx, ctx->vals, x, y, b, n, mode, kd, stop_check, fin); break;
+        case 16: k_spmv<16><<<nb, 256, 0, s>>>(ctx->rowptr, ctx->colidx, ctx->vals, x, y, b, n, mode, kd, stop_check, fin); break;
+        default: k_spmv<32><<<nb, 256, 0, s>>>(ctx->rowptr, ctx->colidx, ctx->vals, x, y, b, n, mode, kd, stop_check, fin); break;
+    }
+}
+
+int krylov_alloc(psr_ctx* ctx) {
+    KrylovWS& w = ctx->ws;
+    const size_t n = (size_t)ctx->n;
+    int m = ctx->opts.restart;
+    if (m < 1) m = 1;
+    if (m > 32) m = 32;
+    ctx->opts.restart = m;
+    w.nblk = (int)std::min<size_t>(std::max<size_t>((n + 255) / 256, 1), 152 * 4);
+    PSR_CUDA(ctx, cudaMalloc(&w.x, n * 8));
+    PSR_CUDA(ctx, cudaMalloc(&w.b, n * 8));
+    PSR_CUDA(ctx, cudaMalloc(&w.r, n * 8));
+    PSR_CUDA(ctx, cudaMalloc(&w.z, n * 8));
+    if (ctx->opts.krylov == PSR_KRYLOV_CG) {
+        PSR_CUDA(ctx, cudaMalloc(&w.p, n * 8));
+        PSR_CUDA(ctx, cudaMalloc(&w.q, n * 8));
+    } else {
+        PSR_CUDA(ctx, cudaMalloc(&w.V, (size_t)(m + 1) * n * 8));
+        PSR_CUDA(ctx, cudaMalloc(&w.Z, (size_t)m * n * 8));
+    }
+    PSR_CUDA(ctx, cudaMalloc(&w.partial, (size_t)w.nblk * 34 * 8));
+    PSR_CUDA(ctx, cudaMalloc(&w.scal, (size_t)scal_count(m) * 8));
+    PSR_CUDA(ctx, cudaMemset(w.scal, 0, (size_t)scal_count(m) * 8));
+    PSR_CUDA(ctx, cudaMalloc(&w.hist, (size_t)(ctx->opts.maxit + 2) * 8));
+    PSR_CUDA(ctx, cudaMalloc(&w.ictl, 32 * sizeof(int32_t)));
+    PSR_CUDA(ctx, cudaMemset(w.ictl, 0, 32 * sizeof(int32_t)));
+    return PSR_OK;
+}
+
+void krylov_free(psr_ctx* ctx) {
+    KrylovWS& w = ctx->ws;
+    for (double* p : {w.x, w.b, w.r, w.z, w.p, w.q, w.V, w.Z, w.partial, w.scal, w.hist}) cudaFree(p);
+    cudaFree(w.ictl);
+    w = KrylovWS{};
+    if (ctx->g_cycle) cudaGraphExecDestroy(ctx->g_cycle);
+    ctx->g_cycle = nullptr;
+}
+
+// One enqueued block of work that the host repeats until the stop flag is set.
+static int enqueue_cg_block(psr_ctx* ctx, KDims kd, int iters, cudaStream_t s) {
+    KrylovWS& w = ctx->ws;
+    const int n = ctx->n, nb = w.nblk;
+    for (int t = 0; t < iters; ++t) {
+        launch_spmv(ctx, w.p, w.q, nullptr, 2, 1, kd, 1, nb, s);
+        k_cg_xr<<<nb, 256, 0, s>>>(w.x, w.r, w.p, w.q, n, kd);
+        int rc = sweep_apply_ex(ctx, w.r, w.z, kd.ictl + I_STOP, s);
+        if (rc != PSR_OK) return rc;
+        k_dot<<<nb, 256, 0, s>>>(w.r, w.z, n, kd, 2);
+        k_cg_p<<<nb, 256, 0, s>>>(w.p, w.z, n, kd);
+    }
+    PSR_CHECK_LAUNCH(ctx, "CG block");
+    return PSR_OK;
+}
+
+static int enqueue_fg_cycle(psr_ctx* ctx, KDims kd, cudaStream_t s) {
+    KrylovWS& w = ctx->ws;
+    const int n = ctx->n, nb = w.nblk, m = kd.m;
+    k_fg_start<<<nb, 256, 0, s>>>(w.r, w.V, n, kd);
+    for (int j = 0; j < m; ++j) {
+        double* Vj = w.V + (size_t)j * n;
+        double* Vn = w.V + (size_t)(j + 1) * n;
+        double* Zj = w.Z + (size_t)j * n;
+        int rc = sweep_apply_ex(ctx, Vj, Zj, kd.ictl + I_STOP, s);
+        if (rc != PSR_OK) return rc;
+        launch_spmv(ctx, Zj, Vn, nullptr, 0, 0, kd, 1, nb, s);
+        k_mdot<<<nb, 256, 0, s>>>(w.V, Vn, n, j, kd, 0);
+        k_maxpy<<<nb, 256, 0, s>>>(w.V, Vn, n, j, kd, 0);
+        k_mdot<<<nb, 256, 0, s>>>(w.V, Vn, n, j, kd, 1);
+        k_maxpy<<<nb, 256, 0, s>>>(w.V, Vn, n, j, kd, 1);
+        k_fg_scale<<<nb, 256, 0, s>>>(Vn, n, kd);
+    }
+    k_fg_solve<<<1, 32, 0, s>>>(kd);
+    k_fg_update<<<nb, 256, 0, s>>>(w.x, w.Z, n, kd);
+    // restart residual r = b - A x (skipped once stopped)
+    launch_spmv(ctx, w.x, w.r, w.b, 1, 2, kd, 1, nb, s);
+    PSR_CHECK_LAUNCH(ctx, "FGMRES cycle");
+    return PSR_OK;
+}
+
+int krylov_solve(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_solve_info* info) {
+    KrylovWS& w = ctx->ws;
+    const int n = ctx->n, nb = w.nblk;
+    const bool cg = ctx->opts.krylov == PSR_KRYLOV_CG;
+    const int m = cg ? 0 : ctx->opts.restart;
+    KDims kd{n, cg ? 1 : m, nb, w.scal, w.ictl, w.partial, w.hist};
+    cudaEvent_t e0, e1;
+    PSR_CUDA(ctx, cudaEventCreate(&e0));
+    PSR_CUDA(ctx, cudaEventCreate(&e1));
+    PSR_CUDA(ctx, cudaEventRecord(e0, s));
+    // control block
+    int32_t hctl[32] = {0};
+    hctl[I_MAXIT] = ctx->opts.maxit;
+    hctl[I_M] = m;
+    double rtol = ctx->opts.rtol;
+    PSR_CUDA(ctx, cudaMemcpyAsync(w.ictl, hctl, sizeof(hctl), cudaMemcpyHostToDevice, s));
+    PSR_CUDA(ctx, cudaMemcpyAsync(w.scal + S_RTOL, &rtol, sizeof(double), cudaMemcpyHostToDevice, s));
+    // r = b, keep a copy of b, x = 0, r0 = ||b||
+    k_init_norm<<<nb, 256, 0, s>>>(b, w.b, w.r, n, kd, 1, w.x);
+    PSR_CHECK_LAUNCH(ctx, "k_init_norm");
+    if (cg) {
+        int rc = sweep_apply_ex(ctx, w.r, w.z, w.ictl + I_STOP, s);
+        if (rc != PSR_OK) return rc;
+        k_dot<<<nb, 256, 0, s>>>(w.r, w.z, n, kd, 1);
+        k_copy<<<nb, 256, 0, s>>>(w.z, w.p, n, kd);
+    }
+    const int block = cg ? 8 : 1;
+    int32_t* hstop = nullptr;
+    PSR_CUDA(ctx, cudaMallocHost(&hstop, 4 * sizeof(int32_t)));
+    // capture one block / cycle into a graph (the pointers are the context's own)
+    if (ctx->opts.use_graph && !ctx->g_cycle) {
+        cudaStream_t cs;
+        PSR_CUDA(ctx, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g;
+        PSR_CUDA(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        int rc = cg ? enqueue_cg_block(ctx, kd, block, cs) : enqueue_fg_cycle(ctx, kd, cs);
+        cudaError_t ce = cudaStreamEndCapture(cs, &g);
+        if (rc != PSR_OK) { cudaStreamDestroy(cs); cudaFreeHost(hstop); return rc; }
+        if (ce != cudaSuccess) { cudaStreamDestroy(cs); cudaFreeHost(hstop); return cuda_fail(ctx, ce, "graph capture"); }
+        ce = cudaGraphInstantiate(&ctx->g_cycle, g, 0);
+        cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        if (ce != cudaSuccess) { cudaFreeHost(hstop); ctx->g_cycle = nullptr; return cuda_fail(ctx, ce, "graph instantiate"); }
+    }
+    const int max_blocks = cg ? (ctx->opts.maxit + block - 1) / block + 2 : ctx->opts.maxit + 2;
+    int rc = PSR_OK;
+    for (int it = 0; it < max_blocks; ++it) {
+        if (ctx->g_cycle) {
+            PSR_CUDA(ctx, cudaGraphLaunch(ctx->g_cycle, s));
+        } else {
+            rc = cg ? enqueue_cg_block(ctx, kd, block, s) : enqueue_fg_cycle(ctx, kd, s);
+            if (rc != PSR_OK) break;
+        }
+        PSR_CUDA(ctx, cudaMemcpyAsync(hstop, w.ictl, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        PSR_CUDA(ctx, cudaStreamSynchronize(s));
+        if (hstop[I_STOP]) break;
+    }
+    if (rc != PSR_OK) { cudaFreeHost(hstop); return rc; }
+    PSR_CUDA(ctx, cudaMemcpyAsync(x, w.x, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    PSR_CUDA(ctx, cudaEventRecord(e1, s));
+    PSR_CUDA(ctx, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const int iters = hstop[I_IT];
+    const int conv = hstop[I_CONV];
+    cudaFreeHost(hstop);
+    ctx->last_iters = iters;
+    ctx->h_hist.assign((size_t)iters + 1, 0.0);
+    PSR_CUDA(ctx, cudaMemcpy(ctx->h_hist.data(), w.hist, sizeof(double) * (iters + 1), cudaMemcpyDeviceToHost));
+    if (info) {
+        info->iterations = iters;
+        info->converged = conv;
+        info->relres = ctx->h_hist.empty() ? 0.0 : ctx->h_hist.back();
+        info->seconds = ms * 1e-3;
+    }
+    if (!conv) {
+        set_error(ctx, "outer solve reached maxit before rtol");
+        return PSR_ERR_NOT_CONVERGED;
+    }
+    return PSR_OK;
+}
+
+}  // namespace psr

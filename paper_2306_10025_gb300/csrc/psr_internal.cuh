@@ -1,0 +1,177 @@
+// Internal declarations shared by the CUDA translation units of the
+// compressed patch-relaxation library (Harper & Tuminaro, arXiv 2306.10025).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/psr.h"
+
+namespace psr {
+
+// ---------------------------------------------------------------- errors
+void set_error(psr_ctx* ctx, const std::string& msg);
+int cuda_fail(psr_ctx* ctx, cudaError_t e, const char* what);
+
+#define PSR_CUDA(ctx, call)                                   \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return psr::cuda_fail((ctx), e_, #call); \
+    } while (0)
+
+#define PSR_CHECK_LAUNCH(ctx, what)                           \
+    do {                                                      \
+        cudaError_t e_ = cudaGetLastError();                  \
+        if (e_ != cudaSuccess) return psr::cuda_fail((ctx), e_, what); \
+    } while (0)
+
+// ------------------------------------------------------- device helpers
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ int warp_sum_i(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Device-side status word bits (written by kernels, read by the host).
+enum : int {
+    ST_UNSORTED = 1,
+    ST_OOB = 2,
+    ST_UNCOVERED = 4,
+    ST_SINGULAR = 8,
+    ST_NAN = 16,
+};
+
+// ------------------------------------------------------------ size group
+// Patches of one size p (Remark after Eq. 1: groups of equal size are handled
+// independently).  Patches inside a group are ordered by database entry
+// (stable), so a tile of consecutive patches shares one inverse.
+struct Group {
+    int p = 0;
+    int count = 0;                 // patches in the group
+    int m = 0;                     // database entries of this size
+    int32_t* patch = nullptr;      // [count] global patch index, sorted by entry
+    int32_t* sdofs = nullptr;      // [count * p] DOFs in sorted order
+    int32_t* sphi = nullptr;       // [count] group-local entry of each sorted patch
+    void* rinv = nullptr;          // [m * p * p] inverses in storage precision
+    int64_t mat_off = 0;           // offset of the group's patches in A_ext (doubles)
+    // tiles: (entry, first sorted patch, count)
+    int32_t* tiles = nullptr;      // [ntiles * 3]
+    int ntiles = 0;
+    int tile_patches = 32;         // chosen by the autotuner
+    int warps = 4;
+    std::vector<int> h_rep;        // global entry ids of the group's entries
+};
+
+struct KrylovWS {
+    double* x = nullptr;   // iterate
+    double* b = nullptr;   // right-hand side copy
+    double* r = nullptr;
+    double* z = nullptr;
+    double* p = nullptr;
+    double* q = nullptr;
+    double* V = nullptr;   // FGMRES basis (m+1) x n
+    double* Z = nullptr;   // FGMRES preconditioned basis m x n
+    double* partial = nullptr;  // reduction partials
+    double* scal = nullptr;     // device scalars (see krylov.cu)
+    double* hist = nullptr;     // [maxit + 1]
+    int32_t* ictl = nullptr;    // device control ints
+    int nblk = 0;
+};
+
+}  // namespace psr
+
+struct psr_ctx {
+    int device = 0;
+    psr_opts opts{};
+    int32_t n = 0;
+    int64_t nnz = 0;
+    int32_t *rowptr = nullptr, *colidx = nullptr;
+    double* vals = nullptr;
+    int32_t n_patches = 0;
+    int32_t* offsets = nullptr;   // device n_patches+1
+    int32_t* dofs = nullptr;      // device flat
+    std::vector<int32_t> h_offsets;
+    int64_t* mat_off = nullptr;   // device n_patches+1 (offset of A_k in A_ext)
+    double* A_ext = nullptr;      // extracted patches, FP64
+    int64_t A_ext_len = 0;
+    double* W = nullptr;          // scale applied at the scatter
+    double* Wg = nullptr;         // scale applied at the gather (SYM) or nullptr
+    int32_t* phi = nullptr;       // device n_patches
+    int32_t* rep_ids = nullptr;   // device n_patches (first m_p used)
+    int32_t m_p = 0;
+    std::vector<int32_t> h_rep_ids;
+    std::vector<psr::Group> groups;
+    int32_t* status = nullptr;    // device status word
+    psr::KrylovWS ws;
+    std::vector<double> h_hist;
+    int32_t last_iters = 0;
+    psr_stats stats{};
+    std::string err;
+    // graphs
+    cudaGraphExec_t g_cycle = nullptr;   // one FGMRES cycle / CG block
+    cudaStream_t g_stream = nullptr;
+    int graph_block = 0;
+    // grouped persistent sweep
+    int32_t* gtiles = nullptr;    // all tiles of all groups: (group, entry, start, count)
+    int gntiles = 0;
+    void* gdesc = nullptr;        // device group descriptors
+    int32_t* gcounter = nullptr;  // work counter for the persistent sweep
+    int sweep_mode = PSR_SWEEP_PERGROUP;
+    int grouped_blocks = 0;
+};
+
+namespace psr {
+
+// extract.cu
+int validate_inputs(psr_ctx* ctx, const psr_csr* A, const int32_t* offsets, const int32_t* dofs,
+                    int32_t n_patches, int64_t total_dofs, int32_t* status, cudaStream_t s);
+int launch_extract(const int32_t* rowptr, const int32_t* colidx, const double* vals,
+                   const int32_t* offsets, const int32_t* dofs, const int64_t* mat_off,
+                   int32_t n_patches, int32_t pmax, int64_t total, double* A_out, cudaStream_t s);
+int launch_multiplicity(const int32_t* dofs, int64_t total, int32_t n, int32_t* mult,
+                        double* W, double* sqrtW, int32_t* status, cudaStream_t s);
+
+// inverse.cu
+int launch_batched_inverse(const double* A, int64_t stride_in, const int32_t* index,
+                           int32_t batch, int32_t p, double* Ainv, int64_t stride_out,
+                           int32_t* singular, cudaStream_t s);
+
+// criterion.cu
+struct RoundState;
+int run_alg1_rounds(psr_ctx* ctx, cudaStream_t s);
+int launch_criterion_batch(const double* A_i, int32_t batch, int32_t p, const double* A_c,
+                           const double* Binv_c, double tol, int32_t* accept, double* dval,
+                           int32_t* work, cudaStream_t s);
+int launch_spectral_norm(const double* E, int32_t batch, int32_t p, double* sigma, cudaStream_t s);
+
+// sweep.cu
+int build_sweep(psr_ctx* ctx, cudaStream_t s);
+int sweep_apply(psr_ctx* ctx, const double* r, double* z, cudaStream_t s);
+int autotune_sweep(psr_ctx* ctx, cudaStream_t s);
+void free_sweep(psr_ctx* ctx);
+
+// krylov.cu
+int krylov_alloc(psr_ctx* ctx);
+int krylov_solve(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_solve_info* info);
+void krylov_free(psr_ctx* ctx);
+
+}  // namespace psr

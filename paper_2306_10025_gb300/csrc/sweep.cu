@@ -1,0 +1,476 @@
+// Step a4: the additive Schwarz / Vanka sweep of Eq. (3),
+//     z = W sum_k V_k^T B_phi(k)^{-1} V_k r        (LEFT weighting)
+//     z = W^1/2 sum_k V_k^T B_phi(k)^{-1} V_k W^1/2 r  (SYM weighting)
+//
+// Layout built at setup.  Inside each size group the patches are sorted by
+// database entry (stable), their DOF lists are stored in that order, and the
+// sorted range of every entry is cut into tiles of at most T patches.  A CTA
+// takes a tile, stages that entry's inverse in shared memory once, and its
+// warps stream the tile's patches: gather r at the patch DOFs, multiply by
+// the staged inverse, scatter-add the weighted result into z.  Reusing one
+// staged inverse for a whole tile is what makes the compressed sweep bound by
+// the residual gather / scatter instead of by factor bytes (the paper's
+// remark on solving all patches of a cluster together, Exp. 3).
+//
+// Precision: FP64 storage computes in FP64; FP32 storage gathers r in FP64,
+// rounds it to FP32, multiplies in FP32 and scatters in FP64.
+#include "psr_internal.cuh"
+
+#include <algorithm>
+#include <numeric>
+
+namespace psr {
+
+struct GroupDesc {          // device copy for the grouped persistent kernel
+    const int32_t* sdofs;
+    const void* rinv;
+    int p;
+    int pad;
+};
+
+// ------------------------------------------------------------ kernels
+// Generic: one patch per warp, lane a owns rows a, a+32, ...; p <= 128.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep_warp(const int32_t* __restrict__ tiles, int ntiles, int p,
+                                                    const T* __restrict__ rinv, const int32_t* __restrict__ sdofs,
+                                                    const double* __restrict__ r, const double* __restrict__ wg,
+                                                    const double* __restrict__ wsc, double* __restrict__ z,
+                                                    const int32_t* __restrict__ stop) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (stop && *stop) return;
+    T* sR = reinterpret_cast<T*>(smem);
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const int pp = p * p;
+    T* sr = reinterpret_cast<T*>(smem + (((size_t)pp * sizeof(T) + 15) & ~(size_t)15)) + wid * 128;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int c = tiles[3 * t], start = tiles[3 * t + 1], cnt = tiles[3 * t + 2];
+        const T* src = rinv + (int64_t)c * pp;
+        __syncthreads();
+        for (int e = threadIdx.x; e < pp; e += blockDim.x) sR[e] = src[e];
+        __syncthreads();
+        for (int k = start + wid; k < start + cnt; k += wpb) {
+            const int32_t* dk = sdofs + (int64_t)k * p;
+            int dof[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int a = lane + 32 * q;
+                dof[q] = (a < p) ? dk[a] : 0;
+                if (a < p) {
+                    double v = r[dof[q]];
+                    if (wg) v *= wg[dof[q]];
+                    sr[a] = (T)v;
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int a = lane + 32 * q;
+                if (a < p) {
+                    T y = (T)0;
+                    const T* row = sR + a * p;
+                    for (int b = 0; b < p; ++b) y = fma(row[b], sr[b], y);
+                    atomicAdd(&z[dof[q]], (double)y * wsc[dof[q]]);
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Small patches (p <= 16): two patches per warp, one per half-warp, r values
+// exchanged with width-16 shuffles.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep_half(const int32_t* __restrict__ tiles, int ntiles, int p,
+                                                    const T* __restrict__ rinv, const int32_t* __restrict__ sdofs,
+                                                    const double* __restrict__ r, const double* __restrict__ wg,
+                                                    const double* __restrict__ wsc, double* __restrict__ z,
+                                                    const int32_t* __restrict__ stop) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (stop && *stop) return;
+    T* sR = reinterpret_cast<T*>(smem);
+    const int lane = threadIdx.x & 31;
+    const int half = lane >> 4;
+    const int a = lane & 15;
+    const int wid = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const int pp = p * p;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int c = tiles[3 * t], start = tiles[3 * t + 1], cnt = tiles[3 * t + 2];
+        const T* src = rinv + (int64_t)c * pp;
+        __syncthreads();
+        for (int e = threadIdx.x; e < pp; e += blockDim.x) sR[e] = src[e];
+        __syncthreads();
+        for (int k0 = start + 2 * wid; k0 < start + cnt; k0 += 2 * wpb) {
+            const int k = k0 + half;
+            const bool live = (k < start + cnt) && (a < p);
+            int dof = 0;
+            T rv = (T)0;
+            if (live) {
+                dof = sdofs[(int64_t)k * p + a];
+                double v = r[dof];
+                if (wg) v *= wg[dof];
+                rv = (T)v;
+            }
+            T y = (T)0;
+            for (int b = 0; b < p; ++b) {
+                const T rb = __shfl_sync(0xffffffffu, rv, b, 16);
+                y = fma(sR[a * p + b < pp ? a * p + b : 0], rb, y);
+            }
+            if (live) atomicAdd(&z[dof], (double)y * wsc[dof]);
+        }
+    }
+}
+
+// Full storage (every patch its own inverse, Eq. 1), p <= 32: one patch per
+// warp; the warp streams its inverse into its own shared-memory slot with
+// coalesced loads, then lane a forms row a of B^-1 r_k.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep_full(int count, int p, const T* __restrict__ rinv,
+                                                    const int32_t* __restrict__ sphi,
+                                                    const int32_t* __restrict__ sdofs,
+                                                    const double* __restrict__ r, const double* __restrict__ wg,
+                                                    const double* __restrict__ wsc, double* __restrict__ z,
+                                                    const int32_t* __restrict__ stop) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (stop && *stop) return;
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int pp = p * p;
+    const size_t slot = (((size_t)pp + 32) * sizeof(T) + 15) & ~(size_t)15;
+    T* sB = reinterpret_cast<T*>(smem + wid * slot);
+    T* sr = sB + pp;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < count; k += nw) {
+        const T* B = rinv + (int64_t)sphi[k] * pp;
+        for (int e = lane; e < pp; e += 32) sB[e] = B[e];
+        int dof = 0;
+        if (lane < p) {
+            dof = sdofs[(int64_t)k * p + lane];
+            double v = r[dof];
+            if (wg) v *= wg[dof];
+            sr[lane] = (T)v;
+        }
+        __syncwarp();
+        if (lane < p) {
+            T y = (T)0;
+            const T* row = sB + lane * p;
+            for (int b = 0; b < p; ++b) y = fma(row[b], sr[b], y);
+            atomicAdd(&z[dof], (double)y * wsc[dof]);
+        }
+        __syncwarp();
+    }
+}
+
+// Grouped persistent kernel (one launch for all size groups): CTAs pull
+// tiles (group, entry, start, count) from a global counter.  Generic warp
+// mapping as k_sweep_warp; the staged inverse is sized for the largest group.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep_grouped(const int32_t* __restrict__ tiles, int ntiles,
+                                                       const GroupDesc* __restrict__ groups,
+                                                       const double* __restrict__ r, const double* __restrict__ wg,
+                                                       const double* __restrict__ wsc, double* __restrict__ z,
+                                                       int32_t* __restrict__ counter, int pmax,
+                                                       const int32_t* __restrict__ stop) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_tile;
+    if (stop && *stop) return;
+    T* sR = reinterpret_cast<T*>(smem);
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    T* sr = reinterpret_cast<T*>(smem + (((size_t)pmax * pmax * sizeof(T) + 15) & ~(size_t)15)) + wid * 128;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= ntiles) break;
+        const int g = tiles[4 * t], c = tiles[4 * t + 1], start = tiles[4 * t + 2], cnt = tiles[4 * t + 3];
+        const GroupDesc gd = groups[g];
+        const int p = gd.p, pp = p * p;
+        const T* src = reinterpret_cast<const T*>(gd.rinv) + (int64_t)c * pp;
+        for (int e = threadIdx.x; e < pp; e += blockDim.x) sR[e] = src[e];
+        __syncthreads();
+        for (int k = start + wid; k < start + cnt; k += wpb) {
+            const int32_t* dk = gd.sdofs + (int64_t)k * p;
+            int dof[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int a = lane + 32 * q;
+                dof[q] = (a < p) ? dk[a] : 0;
+                if (a < p) {
+                    double v = r[dof[q]];
+                    if (wg) v *= wg[dof[q]];
+                    sr[a] = (T)v;
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int a = lane + 32 * q;
+                if (a < p) {
+                    T y = (T)0;
+                    const T* row = sR + a * p;
+                    for (int b = 0; b < p; ++b) y = fma(row[b], sr[b], y);
+                    atomicAdd(&z[dof[q]], (double)y * wsc[dof[q]]);
+                }
+            }
+            __syncwarp();
+        }
+    }
+    // the last CTA to leave resets the counter for the next launch
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int finished = atomicAdd(counter + 1, 1);
+        if (finished == (int)gridDim.x - 1) {
+            counter[0] = 0;
+            counter[1] = 0;
+            __threadfence();
+        }
+    }
+}
+
+// FP64 database -> storage precision, optionally symmetrised first.
+template <typename T>
+__global__ void k_convert(const double* __restrict__ src, int m, int p, int sym, T* __restrict__ dst) {
+    const int64_t total = (int64_t)m * p * p;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / ((int64_t)p * p);
+        const int ij = (int)(e - c * p * p);
+        const int i = ij / p, j = ij % p;
+        double v = src[e];
+        if (sym) v = 0.5 * (v + src[c * p * p + (int64_t)j * p + i]);
+        dst[e] = (T)v;
+    }
+}
+
+// ------------------------------------------------------------ host side
+static size_t sweep_smem(int p, int prec, int warps) {
+    const size_t es = (prec == PSR_PREC_FP64) ? 8 : 4;
+    return ((p * p * es + 15) & ~(size_t)15) + (size_t)warps * 128 * es;
+}
+
+static int make_tiles(psr_ctx* ctx, Group& G, const std::vector<int32_t>& sorted_phi, int T) {
+    std::vector<int32_t> t;
+    int i = 0;
+    while (i < G.count) {
+        const int c = sorted_phi[i];
+        int j = i;
+        while (j < G.count && sorted_phi[j] == c) ++j;
+        for (int s = i; s < j; s += T) {
+            t.push_back(c);
+            t.push_back(s);
+            t.push_back(std::min(T, j - s));
+        }
+        i = j;
+    }
+    if (G.tiles) cudaFree(G.tiles);
+    G.tiles = nullptr;
+    G.ntiles = (int)(t.size() / 3);
+    PSR_CUDA(ctx, cudaMalloc(&G.tiles, sizeof(int32_t) * std::max<size_t>(t.size(), 3)));
+    PSR_CUDA(ctx, cudaMemcpy(G.tiles, t.data(), sizeof(int32_t) * t.size(), cudaMemcpyHostToDevice));
+    G.tile_patches = T;
+    return PSR_OK;
+}
+
+// Build the sweep layout from the Alg. 1 output left in every group
+// (G.sphi = local phi in original order, G.rinv = FP64 database), and the
+// global phi / rep_ids.  h_dofs: host copy of the flat DOF map.
+int build_sweep_layout(psr_ctx* ctx, const std::vector<int32_t>& h_dofs,
+                       const std::vector<std::vector<int32_t>>& gidx, cudaStream_t s) {
+    const int prec = ctx->opts.store_prec;
+    std::vector<int32_t> phi_global(ctx->n_patches, -1);
+    std::vector<int32_t> rep_global;
+    int entry_base = 0;
+    int64_t factor_bytes = 0, index_bytes = 0;
+    for (size_t g = 0; g < ctx->groups.size(); ++g) {
+        Group& G = ctx->groups[g];
+        const int p = G.p, count = G.count;
+        std::vector<int32_t> lphi(count);
+        PSR_CUDA(ctx, cudaMemcpy(lphi.data(), G.sphi, sizeof(int32_t) * count, cudaMemcpyDeviceToHost));
+        std::vector<int32_t> order(count);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lphi[a] < lphi[b]; });
+        std::vector<int32_t> hp(count), hs(count), hd((size_t)count * p);
+        for (int i = 0; i < count; ++i) {
+            const int l = order[i];
+            const int k = gidx[g][l];
+            hp[i] = k;
+            hs[i] = lphi[l];
+            const int off = ctx->h_offsets[k];
+            for (int a = 0; a < p; ++a) hd[(size_t)i * p + a] = h_dofs[off + a];
+            phi_global[k] = entry_base + lphi[l];
+        }
+        for (int j = 0; j < G.m; ++j) rep_global.push_back(gidx[g][G.h_rep[j]]);
+        cudaFree(G.sphi);
+        G.sphi = nullptr;
+        PSR_CUDA(ctx, cudaMalloc(&G.patch, sizeof(int32_t) * count));
+        PSR_CUDA(ctx, cudaMalloc(&G.sphi, sizeof(int32_t) * count));
+        PSR_CUDA(ctx, cudaMalloc(&G.sdofs, sizeof(int32_t) * (size_t)count * p));
+        PSR_CUDA(ctx, cudaMemcpy(G.patch, hp.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice));
+        PSR_CUDA(ctx, cudaMemcpy(G.sphi, hs.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice));
+        PSR_CUDA(ctx, cudaMemcpy(G.sdofs, hd.data(), sizeof(int32_t) * (size_t)count * p, cudaMemcpyHostToDevice));
+        // storage precision
+        double* db64 = reinterpret_cast<double*>(G.rinv);
+        const int64_t ne = (int64_t)G.m * p * p;
+        const bool in_place = (db64 == ctx->A_ext + G.mat_off);
+        if (prec == PSR_PREC_FP64) {
+            if (in_place) {
+                G.rinv = db64;              // full storage: inverses live where the patches were
+            } else {                        // shrink the round buffer to m entries
+                double* keep = nullptr;
+                PSR_CUDA(ctx, cudaMalloc(&keep, sizeof(double) * std::max<int64_t>(ne, 1)));
+                PSR_CUDA(ctx, cudaMemcpyAsync(keep, db64, sizeof(double) * ne, cudaMemcpyDeviceToDevice, s));
+                PSR_CUDA(ctx, cudaStreamSynchronize(s));
+                cudaFree(db64);
+                G.rinv = keep;
+            }
+            factor_bytes += ne * 8;
+        } else if (prec == PSR_PREC_FP32) {
+            float* f = nullptr;
+            PSR_CUDA(ctx, cudaMalloc(&f, sizeof(float) * std::max<int64_t>(ne, 1)));
+            int blocks = (int)std::min<int64_t>((ne + 255) / 256, 152 * 16);
+            k_convert<float><<<std::max(blocks, 1), 256, 0, s>>>(db64, G.m, p, ctx->opts.symmetrize, f);
+            PSR_CHECK_LAUNCH(ctx, "k_convert fp32");
+            PSR_CUDA(ctx, cudaStreamSynchronize(s));
+            if (!in_place) cudaFree(db64);
+            G.rinv = f;
+            factor_bytes += ne * 4;
+        } else {
+            set_error(ctx, "BF16 storage is not available in this build");
+            return PSR_ERR_INVALID_ARG;
+        }
+        std::vector<int32_t> sorted_phi(hs);
+        int T = (p <= 16) ? 64 : 32;
+        int rc = make_tiles(ctx, G, sorted_phi, T);
+        if (rc != PSR_OK) return rc;
+        index_bytes += (int64_t)count * p * 4 + (int64_t)count * 4;
+        entry_base += G.m;
+    }
+    ctx->m_p = entry_base;
+    ctx->h_rep_ids = rep_global;
+    PSR_CUDA(ctx, cudaMemcpy(ctx->phi, phi_global.data(), sizeof(int32_t) * ctx->n_patches, cudaMemcpyHostToDevice));
+    if (!rep_global.empty())
+        PSR_CUDA(ctx, cudaMemcpy(ctx->rep_ids, rep_global.data(), sizeof(int32_t) * rep_global.size(), cudaMemcpyHostToDevice));
+    ctx->stats.factor_bytes = factor_bytes;
+    ctx->stats.index_bytes = index_bytes;
+    ctx->stats.m_p = ctx->m_p;
+    // grouped persistent kernel tables
+    std::vector<int32_t> gt;
+    std::vector<GroupDesc> gd(ctx->groups.size());
+    int pmax = 0;
+    for (size_t g = 0; g < ctx->groups.size(); ++g) {
+        Group& G = ctx->groups[g];
+        gd[g] = GroupDesc{G.sdofs, G.rinv, G.p, 0};
+        pmax = std::max(pmax, G.p);
+        std::vector<int32_t> ht((size_t)G.ntiles * 3);
+        PSR_CUDA(ctx, cudaMemcpy(ht.data(), G.tiles, sizeof(int32_t) * ht.size(), cudaMemcpyDeviceToHost));
+        for (int t = 0; t < G.ntiles; ++t) {
+            gt.push_back((int)g);
+            gt.push_back(ht[3 * t]);
+            gt.push_back(ht[3 * t + 1]);
+            gt.push_back(ht[3 * t + 2]);
+        }
+    }
+    ctx->gntiles = (int)(gt.size() / 4);
+    PSR_CUDA(ctx, cudaMalloc(&ctx->gtiles, sizeof(int32_t) * std::max<size_t>(gt.size(), 4)));
+    PSR_CUDA(ctx, cudaMemcpy(ctx->gtiles, gt.data(), sizeof(int32_t) * gt.size(), cudaMemcpyHostToDevice));
+    PSR_CUDA(ctx, cudaMalloc(&ctx->gdesc, sizeof(GroupDesc) * std::max<size_t>(gd.size(), 1)));
+    PSR_CUDA(ctx, cudaMemcpy(ctx->gdesc, gd.data(), sizeof(GroupDesc) * gd.size(), cudaMemcpyHostToDevice));
+    PSR_CUDA(ctx, cudaMalloc(&ctx->gcounter, sizeof(int32_t) * 2));
+    PSR_CUDA(ctx, cudaMemset(ctx->gcounter, 0, sizeof(int32_t) * 2));
+    ctx->grouped_blocks = 152 * 2;
+    int mode = ctx->opts.sweep_kernel;
+    if (mode == PSR_SWEEP_AUTO) mode = (ctx->groups.size() > 1) ? PSR_SWEEP_GROUPED : PSR_SWEEP_PERGROUP;
+    ctx->sweep_mode = mode;
+    return PSR_OK;
+}
+
+template <typename T>
+static int launch_group(psr_ctx* ctx, const Group& G, const double* r, double* z, const int32_t* stop,
+                        cudaStream_t s) {
+    const int warps = G.warps;
+    const int prec = ctx->opts.store_prec;
+    const size_t sm = sweep_smem(G.p, prec, warps);
+    int blocks = std::min(G.ntiles, 152 * 8);
+    if (blocks < 1) return PSR_OK;
+    const T* rinv = reinterpret_cast<const T*>(G.rinv);
+    if (G.m == G.count && G.p <= 32) {
+        const int wpb = 8;
+        const size_t slot = (((size_t)G.p * G.p + 32) * sizeof(T) + 15) & ~(size_t)15;
+        const int fb = std::min((G.count + wpb - 1) / wpb, 152 * 16);
+        k_sweep_full<T><<<fb, wpb * 32, wpb * slot, s>>>(G.count, G.p, rinv, G.sphi, G.sdofs, r, ctx->Wg,
+                                                          ctx->W, z, stop);
+    } else if (G.p <= 16) {
+        k_sweep_half<T><<<blocks, warps * 32, sm, s>>>(G.tiles, G.ntiles, G.p, rinv, G.sdofs, r, ctx->Wg, ctx->W, z, stop);
+    } else {
+        k_sweep_warp<T><<<blocks, warps * 32, sm, s>>>(G.tiles, G.ntiles, G.p, rinv, G.sdofs, r, ctx->Wg, ctx->W, z, stop);
+    }
+    PSR_CHECK_LAUNCH(ctx, "sweep kernel");
+    return PSR_OK;
+}
+
+int sweep_apply_ex(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s) {
+    PSR_CUDA(ctx, cudaMemsetAsync(z, 0, sizeof(double) * (size_t)ctx->n, s));
+    const int prec = ctx->opts.store_prec;
+    if (ctx->sweep_mode == PSR_SWEEP_GROUPED) {
+        int pmax = 0;
+        for (auto& G : ctx->groups) pmax = std::max(pmax, G.p);
+        const int warps = 8;
+        const size_t sm = sweep_smem(pmax, prec, warps);
+        const GroupDesc* gd = reinterpret_cast<const GroupDesc*>(ctx->gdesc);
+        if (prec == PSR_PREC_FP64) {
+            k_sweep_grouped<double><<<ctx->grouped_blocks, warps * 32, sm, s>>>(ctx->gtiles, ctx->gntiles, gd, r, ctx->Wg, ctx->W, z, ctx->gcounter, pmax, stop);
+        } else {
+            k_sweep_grouped<float><<<ctx->grouped_blocks, warps * 32, sm, s>>>(ctx->gtiles, ctx->gntiles, gd, r, ctx->Wg, ctx->W, z, ctx->gcounter, pmax, stop);
+        }
+        PSR_CHECK_LAUNCH(ctx, "grouped sweep");
+        return PSR_OK;
+    }
+    for (auto& G : ctx->groups) {
+        int rc = (prec == PSR_PREC_FP64) ? launch_group<double>(ctx, G, r, z, stop, s)
+                                         : launch_group<float>(ctx, G, r, z, stop, s);
+        if (rc != PSR_OK) return rc;
+    }
+    return PSR_OK;
+}
+
+// Raise the dynamic shared-memory limit of every sweep kernel once, outside
+// any stream capture.
+int sweep_prepare(psr_ctx* ctx) {
+    const int bytes = 200 * 1024;
+    PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_warp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_warp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_grouped<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_grouped<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_full<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_full<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    return PSR_OK;
+}
+
+int sweep_apply(psr_ctx* ctx, const double* r, double* z, cudaStream_t s) {
+    return sweep_apply_ex(ctx, r, z, nullptr, s);
+}
+
+void free_sweep(psr_ctx* ctx) {
+    for (auto& G : ctx->groups) {
+        cudaFree(G.patch);
+        cudaFree(G.sdofs);
+        cudaFree(G.sphi);
+        cudaFree(G.tiles);
+        if (G.rinv && !(ctx->A_ext && reinterpret_cast<double*>(G.rinv) >= ctx->A_ext &&
+                         reinterpret_cast<double*>(G.rinv) < ctx->A_ext + ctx->A_ext_len))
+            cudaFree(G.rinv);
+        G = Group{};
+    }
+    cudaFree(ctx->gtiles);
+    cudaFree(ctx->gdesc);
+    cudaFree(ctx->gcounter);
+    ctx->gtiles = nullptr;
+    ctx->gdesc = nullptr;
+    ctx->gcounter = nullptr;
+}
+
+}  // namespace psr

@@ -1,0 +1,305 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI."""
+import numpy as np
+import pytest
+
+import problems as P
+from oracle import psr_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2306_10025_gb300 as L
+    return L
+
+
+def dev(a, dt):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+
+
+def csr_args(pr):
+    return dev(pr.rowptr, torch.int32), dev(pr.colidx, torch.int32), dev(pr.vals, torch.float64)
+
+
+def setup_ctx(lib, pr, **kw):
+    rp, ci, va = csr_args(pr)
+    dofs = dev(pr.patch_dofs, torch.int32)
+    if pr.uniform_size:
+        return lib.psr_setup(rp, ci, va, dofs, uniform_size=pr.uniform_size, opts=lib.make_opts(**kw))
+    return lib.psr_setup(rp, ci, va, dofs, offsets=dev(pr.patch_offsets, torch.int32), opts=lib.make_opts(**kw))
+
+
+# ------------------------------------------------------------------ a1 / a1'
+@pytest.mark.parametrize("mk", [lambda: P.poisson2d_q2(5), lambda: P.stokes2d_q2q1(6),
+                                lambda: P.nedelec3d(3), lambda: P.diffusion3d_q2(3)])
+def test_extract_and_weights_bit_exact(lib, mk):
+    pr = mk()
+    rp, ci, va = csr_args(pr)
+    p = pr.uniform_size
+    A = torch.empty(pr.n_patches, p, p, dtype=torch.float64, device="cuda")
+    mult = torch.empty(pr.n, dtype=torch.int32, device="cuda")
+    W = torch.empty(pr.n, dtype=torch.float64, device="cuda")
+    lib.psr_extract(rp, ci, va, dev(pr.patch_dofs, torch.int32), uniform_size=p, A_out=A, mult_out=mult, W_out=W)
+    Ao = O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d())
+    assert np.array_equal(A.cpu().numpy(), Ao)
+    mo = O.multiplicity(pr.n, pr.patch_dofs)
+    assert np.array_equal(mult.cpu().numpy(), mo)
+    assert np.array_equal(W.cpu().numpy(), O.weights(mo))
+
+
+def test_extract_ragged_offsets(lib):
+    """Patches of different sizes through the offsets array."""
+    pr = P.poisson2d_q2(4)
+    g = np.random.default_rng(3)
+    d2 = pr.dofs2d()
+    sizes = g.integers(3, 10, pr.n_patches)
+    flat, off = [], [0]
+    for k in range(pr.n_patches):
+        sel = np.sort(g.choice(9, sizes[k], replace=False))
+        flat.extend(d2[k][sel])
+        off.append(len(flat))
+    flat = np.array(flat, dtype=np.int32)
+    off = np.array(off, dtype=np.int32)
+    rp, ci, va = csr_args(pr)
+    tot = int(np.sum(sizes.astype(np.int64) ** 2))
+    A = torch.empty(tot, dtype=torch.float64, device="cuda")
+    lib.psr_extract(rp, ci, va, dev(flat, torch.int32), offsets=dev(off, torch.int32), A_out=A)
+    Ah = A.cpu().numpy()
+    ref = O.extract_patches_ragged(pr.rowptr, pr.colidx, pr.vals, pr.n, off, flat)
+    pos = 0
+    for k, Ak in enumerate(ref):
+        s = Ak.size
+        assert np.array_equal(Ah[pos:pos + s].reshape(Ak.shape), Ak)
+        pos += s
+
+
+def test_extract_rejects_unsorted_csr(lib):
+    pr = P.poisson2d_q2(3)
+    ci = pr.colidx.copy()
+    r = 20
+    a, b = pr.rowptr[r], pr.rowptr[r + 1]
+    ci[a:b] = ci[a:b][::-1].copy()
+    A = torch.empty(pr.n_patches, 9, 9, dtype=torch.float64, device="cuda")
+    with pytest.raises(lib.PsrError) as e:
+        lib.psr_extract(dev(pr.rowptr, torch.int32), dev(ci, torch.int32), dev(pr.vals, torch.float64),
+                        dev(pr.patch_dofs, torch.int32), uniform_size=9, A_out=A)
+    assert e.value.code == -2
+
+
+# ------------------------------------------------------------------ a2
+@pytest.mark.parametrize("p", [1, 5, 9, 12, 22, 27, 33, 62, 89])
+def test_batched_inverse_vs_oracle(lib, p):
+    g = np.random.default_rng(p)
+    B = 37
+    A = g.standard_normal((B, p, p)) + 0.5 * p * np.eye(p)
+    A[0] = np.diag(g.uniform(1, 2, p))                     # exact case
+    Ainv = torch.empty(B, p, p, dtype=torch.float64, device="cuda")
+    sing = torch.empty(B, dtype=torch.int32, device="cuda")
+    lib.psr_batched_inverse(dev(A, torch.float64), Ainv, sing)
+    X = Ainv.cpu().numpy()
+    Xo, so = O.lu_inverse(A)
+    assert not sing.cpu().numpy().any() and not so.any()
+    assert np.array_equal(X[0], np.diag(1.0 / np.diag(A[0])))
+    for b in range(B):
+        kappa = np.linalg.cond(A[b])
+        tol = 20 * p * 2.0 ** -53 * kappa * np.abs(Xo[b]).max()
+        assert np.abs(X[b] - Xo[b]).max() <= tol
+
+
+def test_batched_inverse_flags_singular(lib):
+    A = np.array([[[1.0, 2.0, 3.0], [2.0, 4.0, 6.0], [1.0, 0.0, 1.0]],
+                  [[2.0, 0.0, 0.0], [0.0, 3.0, 0.0], [0.0, 0.0, 4.0]]])
+    Ainv = torch.empty(2, 3, 3, dtype=torch.float64, device="cuda")
+    sing = torch.empty(2, dtype=torch.int32, device="cuda")
+    lib.psr_batched_inverse(dev(A, torch.float64), Ainv, sing)
+    assert list(sing.cpu().numpy()) == [1, 0]
+    assert np.isnan(Ainv[0].cpu().numpy()).all()
+
+
+# ------------------------------------------------------------------ a3
+def test_spectral_norm_vs_oracle(lib):
+    g = np.random.default_rng(7)
+    for p in (1, 4, 12, 22, 27, 32):
+        E = g.standard_normal((20, p, p)) * g.uniform(1e-6, 10, (20, 1, 1))
+        E[0] = 0.0
+        s = torch.empty(20, dtype=torch.float64, device="cuda")
+        lib.psr_spectral_norm(dev(E, torch.float64), s)
+        so = O.spectral_norm(E)
+        assert s[0].item() == 0.0
+        np.testing.assert_allclose(s.cpu().numpy()[1:], so[1:], rtol=1e-13)
+
+
+def test_criterion_decisions_vs_oracle(lib):
+    """Random pairs around the tolerance: the certified GPU decision equals
+    the oracle's exact d < tol, and identical patches give d = 0."""
+    g = np.random.default_rng(8)
+    for p in (9, 12, 22, 27):
+        Ac = g.standard_normal((p, p)) + p * np.eye(p)
+        Binv, _ = O.lu_inverse(Ac[None])
+        B = 200
+        scales = 10.0 ** g.uniform(-6, 0, B)
+        Ai = Ac[None] + scales[:, None, None] * g.standard_normal((B, p, p))
+        Ai[0] = Ac
+        d = O.criterion(Ai, Ac[None], Binv)
+        for tol in (1e-4, 1e-2, float(np.median(d))):
+            acc = torch.empty(B, dtype=torch.int32, device="cuda")
+            dv = torch.empty(B, dtype=torch.float64, device="cuda")
+            lib.psr_criterion(dev(Ai, torch.float64), dev(Ac, torch.float64), dev(Binv[0], torch.float64),
+                              tol, acc, dv)
+            a = acc.cpu().numpy().astype(bool)
+            near = np.abs(d - tol) <= 1e-9 * tol
+            assert np.array_equal(a[~near], (d < tol)[~near]), (p, tol)
+            assert a[0] and dv[0].item() == 0.0
+            dvh = dv.cpu().numpy()
+            # accepted: deciding value is an upper bound >= d; rejected: lower bound <= d
+            assert np.all(dvh[a] >= d[a] * (1 - 1e-12))
+            assert np.all(dvh[~a] <= d[~a] * (1 + 1e-12))
+
+
+# ------------------------------------------------------------------ Alg. 1
+@pytest.mark.parametrize("case", ["c1", "stokes8", "diff3d", "nedelec", "uniform3d"])
+def test_alg1_assignment_bit_exact(lib, case):
+    if case == "c1":
+        pr, tols = P.poisson2d_q2(16), [1e-12, 1e-3, 1e-1]
+    elif case == "stokes8":
+        pr, tols = P.stokes2d_q2q1(8), [1e-3, 1e-1, 2.0, 10.0]
+    elif case == "diff3d":
+        pr, tols = P.diffusion3d_q2(4, seed=3), [1e-2, 1e-1, 0.5]
+    elif case == "nedelec":
+        pr, tols = P.nedelec3d(4, seed=5), [1e-1, 0.5, 1.0]
+    else:
+        pr, tols = P.diffusion3d_q2(4, uniform=True), [1e-10]
+    A = O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d())
+    for tol in tols:
+        ref = O.alg1(A, tol)
+        assert ref["near_ties"] == [], "oracle reports a near tie; pick another tol"
+        ctx = setup_ctx(lib, pr, tol=tol, weighting=pr.weighting, krylov=pr.krylov)
+        phi, reps, m = ctx.assignment()
+        assert m == len(ref["reps"]), (case, tol)
+        assert np.array_equal(phi.cpu().numpy(), ref["phi"]), (case, tol)
+        assert np.array_equal(reps.cpu().numpy(), ref["reps"]), (case, tol)
+        st = ctx.stats()
+        assert st["criterion_evals"] == ref["evals"], (case, tol)
+        ctx.destroy()
+
+
+def test_alg1_tol_zero_identity(lib):
+    pr = P.stokes2d_q2q1(4)
+    ctx = setup_ctx(lib, pr, tol=0.0, weighting="left", krylov="fgmres")
+    phi, reps, m = ctx.assignment()
+    assert m == pr.n_patches
+    assert np.array_equal(phi.cpu().numpy(), np.arange(pr.n_patches))
+    assert np.array_equal(reps.cpu().numpy(), np.arange(pr.n_patches))
+
+
+# ------------------------------------------------------------------ a4
+@pytest.mark.parametrize("weighting", ["left", "sym"])
+@pytest.mark.parametrize("tol", [0.0, 1e-1])
+def test_apply_vs_oracle_fp64(lib, weighting, tol):
+    pr = P.stokes2d_q2q1(8)
+    st = O.setup(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d(), tol)
+    ctx = setup_ctx(lib, pr, tol=tol, weighting=weighting, krylov="fgmres")
+    g = np.random.default_rng(1)
+    for _ in range(3):
+        r = g.standard_normal(pr.n)
+        z = torch.empty(pr.n, dtype=torch.float64, device="cuda")
+        ctx.apply(dev(r, torch.float64), z)
+        zr = O.apply(r, pr.dofs2d(), st["Binv"], st["phi"], st["W"], weighting)
+        err = np.abs(z.cpu().numpy() - zr).max() / np.abs(zr).max()
+        assert err < 1e-12
+
+
+def test_apply_fp32_error_bound(lib):
+    pr = P.poisson2d_q2(16)
+    st = O.setup(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d(), 0.0)
+    ctx = setup_ctx(lib, pr, tol=0.0, store_prec="fp32", weighting="sym")
+    r = np.random.default_rng(2).standard_normal(pr.n)
+    z = torch.empty(pr.n, dtype=torch.float64, device="cuda")
+    ctx.apply(dev(r, torch.float64), z)
+    zr = O.apply(r, pr.dofs2d(), st["Binv"], st["phi"], st["W"], "sym")
+    err = np.abs(z.cpu().numpy() - zr).max() / np.abs(zr).max()
+    assert err < 1e-5
+
+
+def test_apply_grouped_equals_pergroup(lib):
+    pr = P.stokes2d_q2q1(8)
+    r = dev(np.random.default_rng(4).standard_normal(pr.n), torch.float64)
+    outs = []
+    for sk in ("pergroup", "grouped"):
+        ctx = setup_ctx(lib, pr, tol=1e-1, weighting="left", krylov="fgmres", sweep_kernel=sk)
+        z = torch.empty(pr.n, dtype=torch.float64, device="cuda")
+        ctx.apply(r, z)
+        outs.append(z.cpu().numpy())
+    assert np.abs(outs[0] - outs[1]).max() <= 1e-13 * np.abs(outs[0]).max()
+
+
+# ------------------------------------------------------------------ a5
+@pytest.mark.parametrize("tol", [0.0, 1e-12])
+@pytest.mark.parametrize("graph", [True, False])
+def test_pcg_history_vs_oracle(lib, tol, graph):
+    pr = P.poisson2d_q2(16)
+    st = O.setup(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d(), tol)
+    b = pr.rhs(0)
+    _, hist, it, conv = O.solve(pr.rowptr, pr.colidx, pr.vals, pr.n, b, st, "cg", "sym")
+    ctx = setup_ctx(lib, pr, tol=tol, weighting="sym", krylov="cg", use_graph=graph)
+    x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
+    info = ctx.solve(dev(b, torch.float64), x)
+    assert info["converged"] and info["iterations"] == it
+    h = ctx.history()
+    assert np.max(np.abs(h - hist) / np.array(hist)) <= 1e-10
+    res = np.linalg.norm(b - pr.to_scipy() @ x.cpu().numpy()) / np.linalg.norm(b)
+    assert res <= 1.05e-8
+
+
+@pytest.mark.parametrize("tol", [0.0, 1e-1])
+def test_fgmres_history_vs_oracle(lib, tol):
+    pr = P.stokes2d_q2q1(6)
+    st = O.setup(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d(), tol)
+    b = pr.rhs(1)
+    _, hist, it, conv = O.solve(pr.rowptr, pr.colidx, pr.vals, pr.n, b, st, "fgmres", "left", restart=30)
+    assert conv
+    ctx = setup_ctx(lib, pr, tol=tol, weighting="left", krylov="fgmres", restart=30)
+    x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
+    info = ctx.solve(dev(b, torch.float64), x)
+    assert info["converged"] and info["iterations"] == it
+    h = ctx.history()
+    assert np.max(np.abs(h - hist) / np.array(hist)) <= 1e-10
+
+
+def test_fgmres_maxit_reports_not_converged(lib):
+    pr = P.stokes2d_q2q1(8)
+    ctx = setup_ctx(lib, pr, tol=0.0, weighting="left", krylov="fgmres", maxit=45)
+    x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
+    info = ctx.solve(dev(pr.rhs(0), torch.float64), x)
+    assert not info["converged"] and info["iterations"] == 45
+    with pytest.raises(lib.PsrError) as e:
+        ctx.solve(dev(pr.rhs(0), torch.float64), x, raise_on_nonconvergence=True)
+    assert e.value.code == -4
+
+
+# ------------------------------------------------------------------ errors
+def test_setup_errors(lib):
+    pr = P.poisson2d_q2(3)
+    rp, ci, va = csr_args(pr)
+    d = pr.patch_dofs.copy()
+    # DOF 0 removed from every patch -> uncovered
+    d[d == 0] = 1
+    with pytest.raises(lib.PsrError) as e:
+        lib.psr_setup(rp, ci, va, dev(d, torch.int32), uniform_size=9)
+    assert e.value.code == -8
+    # singular patch: zero out a whole patch block by using a duplicated DOF
+    d2 = pr.patch_dofs.copy().reshape(-1, 9)
+    d2[4, 1] = d2[4, 0]
+    with pytest.raises(lib.PsrError) as e:
+        lib.psr_setup(rp, ci, va, dev(d2.reshape(-1), torch.int32), uniform_size=9,
+                      opts=lib.make_opts(tol=0.0))
+    assert e.value.code in (-3, -8)
+    with pytest.raises(lib.PsrError) as e:
+        lib.psr_setup(rp, ci, va, dev(pr.patch_dofs, torch.int32), uniform_size=9,
+                      opts=lib.make_opts(restart=0))
+    assert e.value.code == -1
