@@ -1,0 +1,382 @@
+"""Benchmark of the compressed patch-relaxation hot path on GB300.
+
+One step = the whole path on one synthetic workload: setup (patch extraction,
+multiplicity weights, Alg. 1 with the certified criterion, FP64 inverses of
+the database entries, conversion to the storage precision, sweep layout) and
+the outer solve (right-preconditioned FGMRES(30) or PCG, sweeps + SpMV +
+orthogonalisation) from x0 = 0, inputs already resident in HBM.
+
+Default workload: 2D Stokes, Taylor-Hood Q2-Q1 on 128 x 128 quads graded in y
+(ratio 1.05), 22-DOF Vanka cell patches, FGMRES(30) in FP64, criterion tol
+1e-2, representative inverses stored in FP32.  The one-level Vanka
+preconditioner does not reach 1e-8 on this mesh within a practical budget, so
+a step runs a fixed iteration budget (--maxit, default 300) and reports the
+relative residual reached; the full-storage FP64 form is measured beside it.
+
+value = n x (preconditioner applications in the step) / step time, i.e. the
+Schwarz sweep DOF/s of the whole step with setup included (unit DOF/s).
+
+Prints ONE JSON line (rank 0).  --impl reference times the CPU FP64 oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np
+
+METRIC = "Schwarz sweep DOF/s + setup s, clustered vs full, iters to 1e-8 rel. residual"
+
+CONFIGS = {
+    "stokes2d": dict(builder="stokes2d_q2q1", kw=dict(N=128, ratio=1.05), tol=1e-2, prec="fp32",
+                     weighting="left", krylov="fgmres",
+                     desc="2D Stokes Taylor-Hood Q2-Q1, 128x128 quads graded 1.05 in y, 22-DOF Vanka patches"),
+    "poisson2d": dict(builder="poisson2d_q2", kw=dict(N=16), tol=1e-12, prec="fp64", weighting="sym",
+                      krylov="cg", desc="2D Q2 diffusion 16x16, 9-DOF patches"),
+    "nedelec3d": dict(builder="nedelec3d", kw=dict(N=64), tol=1e-1, prec="fp32", weighting="sym",
+                      krylov="cg", desc="3D Nedelec curl-curl 64^3, 12-DOF patches"),
+    "diffusion3d": dict(builder="diffusion3d_q2", kw=dict(N=32), tol=1e-1, prec="fp32", weighting="sym",
+                        krylov="cg", desc="3D Q2 lognormal diffusion 32^3, 27-DOF patches"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default="stokes2d", choices=sorted(CONFIGS))
+    ap.add_argument("--maxit", type=int, default=300)
+    ap.add_argument("--tol", type=float, default=None)
+    ap.add_argument("--prec", default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--apply-reps", type=int, default=200)
+    return ap.parse_args()
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def build_problem(cfg):
+    import problems
+    return getattr(problems, cfg["builder"])(**cfg["kw"])
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.p = None
+        self.idx = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, cfg, ws, rank, local):
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2306_10025_gb300 as L
+
+    torch.cuda.set_device(local)
+    devc = torch.device("cuda", local)
+    pr = build_problem(cfg)
+    tol = cfg["tol"] if args.tol is None else args.tol
+    prec = cfg["prec"] if args.prec is None else args.prec
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=devc)
+    rp, ci, va = t(pr.rowptr, torch.int32), t(pr.colidx, torch.int32), t(pr.vals, torch.float64)
+    dofs = t(pr.patch_dofs, torch.int32)
+    offs = None if pr.uniform_size else t(pr.patch_offsets, torch.int32)
+    b = t(pr.rhs(0), torch.float64)
+    x = torch.zeros_like(b)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=devc)   # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def mk_opts(tol_, prec_):
+        return L.make_opts(tol=tol_, store_prec=prec_, weighting=cfg["weighting"], krylov=cfg["krylov"],
+                           restart=30, rtol=1e-8, maxit=args.maxit)
+
+    def one_step(tol_, prec_):
+        ctx = L.psr_setup(rp, ci, va, dofs, offsets=offs, uniform_size=pr.uniform_size, opts=mk_opts(tol_, prec_))
+        info = ctx.solve(b, x)
+        return ctx, info
+
+    # warm-up
+    for _ in range(args.warmup):
+        ctx, info = one_step(tol, prec)
+        ctx.destroy()
+    torch.cuda.synchronize()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    launches0 = L.psr_kernel_launches()
+    times, infos, stats = [], [], []
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    for _ in range(args.steps):
+        flush.zero_()                               # L2 flush between steps (outside the timing)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx, info = one_step(tol, prec)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e-3)
+        infos.append(info)
+        stats.append(ctx.stats())
+        if len(times) < args.steps:
+            ctx.destroy()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    launches = L.psr_kernel_launches() - launches0
+    clocks = clk.stop()
+    step_s = sum(times) / len(times)
+    if ws > 1:
+        tt = torch.tensor([sum(times)], dtype=torch.float64, device=devc)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_s = tt.item()
+    else:
+        total_s = sum(times)
+    iters = infos[-1]["iterations"]
+    units_per_rank = pr.n * iters * args.steps
+    value = units_per_rank * ws / total_s
+
+    # kernel-level: sweep (apply) timing with CUDA events over many launches
+    last = ctx
+    r = torch.randn(pr.n, dtype=torch.float64, device=devc)
+    z = torch.empty_like(r)
+    for _ in range(20):
+        last.apply(r, z)
+    big_r = [torch.randn(pr.n, dtype=torch.float64, device=devc) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev = []
+    for i in range(args.apply_reps):
+        flush.zero_() if i % 8 == 0 else None
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        last.apply(big_r[i % 2], z)
+        e1.record(stream)
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    apply_ms = sorted(a.elapsed_time(b_) for a, b_ in ev)
+    apply_med = apply_ms[len(apply_ms) // 2] * 1e-3
+    st = stats[-1]
+    n, npch = pr.n, pr.n_patches
+    psum = int(pr.patch_offsets[-1])
+    eb = {"fp64": 8, "fp32": 4, "bf16": 2}[prec]
+    ntile_bytes = 12 * (st["m_p"] + npch // 32 + 1)
+    alg_bytes = 3 * 8 * n + 4 * psum + st["factor_bytes"] + ntile_bytes
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    achieved = alg_bytes / apply_med / 1e9
+    roofline = {"kernel": "sweep (psr_apply: zero z + k_sweep_*)", "bound": "hbm", "achieved": achieved,
+                "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
+                "frac": achieved / peaks.get("hbm_gbs", 6800.0), "traffic": None,
+                "alg_bytes_per_launch": alg_bytes, "launch_us": apply_med * 1e6,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    last.destroy()
+
+    # full-storage FP64 comparison (outside the timed steps)
+    ctx_f, info_f = one_step(0.0, "fp64")
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx_f2, info_f2 = one_step(0.0, "fp64")
+    e1.record(stream)
+    e1.synchronize()
+    full_step_s = e0.elapsed_time(e1) * 1e-3
+    st_f = ctx_f2.stats()
+    ctx_f.destroy()
+    ctx_f2.destroy()
+
+    # end to end: host (pinned) inputs -> device -> setup + solve -> x to host
+    e2e = None
+    if not args.no_e2e:
+        hp = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).pin_memory()
+        h_rp, h_ci, h_va = hp(pr.rowptr, torch.int32), hp(pr.colidx, torch.int32), hp(pr.vals, torch.float64)
+        h_d, h_b = hp(pr.patch_dofs, torch.int32), hp(pr.rhs(0), torch.float64)
+        h_o = None if pr.uniform_size else hp(pr.patch_offsets, torch.int32)
+        h_x = torch.empty(n, dtype=torch.float64).pin_memory()
+        h2d = sum(a.numel() * a.element_size() for a in (h_rp, h_ci, h_va, h_d, h_b) ) + (0 if h_o is None else h_o.numel() * 4)
+        ets = []
+        for i in range(args.warmup + args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            d_rp, d_ci, d_va = h_rp.to(devc, non_blocking=True), h_ci.to(devc, non_blocking=True), h_va.to(devc, non_blocking=True)
+            d_d, d_b = h_d.to(devc, non_blocking=True), h_b.to(devc, non_blocking=True)
+            d_o = None if h_o is None else h_o.to(devc, non_blocking=True)
+            d_x = torch.zeros(n, dtype=torch.float64, device=devc)
+            c2 = L.psr_setup(d_rp, d_ci, d_va, d_d, offsets=d_o, uniform_size=pr.uniform_size, opts=mk_opts(tol, prec))
+            inf2 = c2.solve(d_b, d_x)
+            h_x.copy_(d_x, non_blocking=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            c2.destroy()
+            if i >= args.warmup:
+                ets.append(dt)
+        e2e = {"value": n * inf2["iterations"] / (sum(ets) / len(ets)), "unit": "DOF/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(n * 8),
+               "ms_per_step": 1e3 * sum(ets) / len(ets)}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+" + prec, "data": "synthetic",
+        "config": {"workload": cfg["desc"], "n": n, "n_patches": npch, "tol": tol, "store_prec": prec,
+                   "krylov": cfg["krylov"] + ("(30)" if cfg["krylov"] == "fgmres" else ""),
+                   "weighting": cfg["weighting"], "maxit": args.maxit, "rhs": "uniform(-1,1) seed 0",
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "value_def": "n x preconditioner applications / step time (setup + solve)",
+                   "parallelism": f"replicas x{ws}"},
+        "setup_s": {"clustered": st["t_extract"] + st["t_rounds"] + st["t_convert"],
+                    "full": st_f["t_extract"] + st_f["t_rounds"] + st_f["t_convert"],
+                    "clustered_phases": {k: st[k] for k in ("t_extract", "t_rounds", "t_convert")}},
+        "iters": {"clustered": iters, "full": info_f2["iterations"], "relres_clustered": infos[-1]["relres"],
+                  "relres_full": info_f2["relres"], "converged_clustered": infos[-1]["converged"],
+                  "converged_full": info_f2["converged"], "rtol": 1e-8},
+        "step_s": {"clustered": step_s, "full_fp64": full_step_s},
+        "sweep_dof_per_s": n / apply_med,
+        "m_p": st["m_p"], "retained_fraction": st["m_p"] / npch,
+        "factor_bytes": {"clustered": st["factor_bytes"], "full": st_f["factor_bytes"]},
+        "criterion_evals": st["criterion_evals"], "criterion_exact": st["criterion_exact"],
+        "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
+    }
+    return out, pr, infos[-1], st
+
+
+# ------------------------------------------------------------------ CPU oracle
+SAMPLE_KW = {"stokes2d": dict(N=16, ratio=1.05), "poisson2d": dict(N=16), "nedelec3d": dict(N=8),
+             "diffusion3d": dict(N=6)}
+
+
+def cpu_oracle_sample(args, cfg, name):
+    """The numpy FP64 oracle, as it stands, on a bounded sample of the same
+    workload: the same family, solver and options on a smaller mesh, the
+    whole step (setup with Alg. 1 + outer solve with the same iteration
+    budget).  Returns the line's cpu_baseline object (same unit)."""
+    import problems
+    from oracle import psr_oracle as O
+    kw = SAMPLE_KW[name]
+    pr = getattr(problems, cfg["builder"])(**kw)
+    tol = cfg["tol"] if args.tol is None else args.tol
+    t0 = time.perf_counter()
+    st = O.setup(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d(), tol)
+    t1 = time.perf_counter()
+    x, hist, it, conv = O.solve(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.rhs(0), st, cfg["krylov"],
+                                cfg["weighting"], restart=30, rtol=1e-8, maxit=args.maxit)
+    t2 = time.perf_counter()
+    return {"value": pr.n * it / (t2 - t0), "unit": "DOF/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"numpy FP64 oracle, whole step (setup with Alg. 1 at tol {tol:g}: {t1 - t0:.2f} s; "
+                       f"{it} outer iterations: {t2 - t1:.2f} s) on the same workload family at "
+                       f"{kw} (n = {pr.n}, {pr.n_patches} patches); BLAS default threading"),
+            "step_s": t2 - t0}
+
+
+def run_reference(args, cfg, ws, rank):
+    if rank != 0:
+        return None
+    vals, walls = [], []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_oracle_sample(args, cfg, args.config)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+            walls.append(cb["step_s"])
+    v = statistics.median(vals)
+    cb["value"] = v
+    return {"metric": METRIC, "value": v, "unit": "DOF/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(walls), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": cfg["desc"] + " (bounded CPU sample, see cpu_baseline)",
+                       "maxit": args.maxit},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    cfg = CONFIGS[args.config]
+    ws, rank, local = dist_info()
+    if args.impl == "reference":
+        out = run_reference(args, cfg, ws, rank)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    out, pr, info, st = run_gpu(args, cfg, ws, rank, local)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_oracle_sample(args, cfg, args.config)
+        print(json.dumps(out))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -161,6 +161,11 @@ const char* psr_last_error(psr_ctx* ctx);
 
 void psr_destroy(psr_ctx* ctx);
 
+/* Instrumentation: number of CUDA kernels this library has launched in the
+ * process so far (a graph launch counts its kernel nodes).  Host-only, never
+ * fails; used by benchmarks to state how many kernels a timed region ran. */
+int64_t psr_kernel_launches(void);
+
 /* ---- single steps of the path (stateless; for testing and reuse) ------- */
 
 /* Step a1/a1': A_out <- every A_k (section 2), row-major, patch k at offset

@@ -425,3 +425,123 @@ def solve(rowptr, colidx, vals, n, b, st, krylov="cg", weighting="sym",
     if krylov == "cg":
         return pcg(mv, pc, b, rtol=rtol, maxit=maxit)
     return fgmres(mv, pc, b, restart=restart, rtol=rtol, maxit=maxit)
+
+
+# ---------------------------------------------------------------------------
+# a6: learned assignment (not in the paper; the paper leaves deep-learning
+#     assisted clustering to future work at the end of section 3.2).
+#     Features -> MLP (2 hidden ReLU layers) -> database entry; the exact
+#     criterion verifies every prediction; misses run Alg. 1 against the
+#     database (seed entries first, in creation order) and may append entries.
+# ---------------------------------------------------------------------------
+
+def patch_features(A, coef=None):
+    """Per-patch feature vector: the patch entries divided by ||A_k||_F
+    (row-major), log ||A_k||_F and log of the cell coefficient (0 when no
+    coefficient is given).  A: (n_p, p, p)."""
+    A = np.asarray(A, dtype=np.float64)
+    npch, p, _ = A.shape
+    fro = np.sqrt(np.einsum("kij,kij->k", A, A))
+    X = np.zeros((npch, p * p + 2))
+    X[:, :p * p] = A.reshape(npch, -1) / fro[:, None]
+    X[:, p * p] = np.log(fro)
+    X[:, p * p + 1] = 0.0 if coef is None else np.log(np.asarray(coef, dtype=np.float64))
+    return X
+
+
+def mlp_forward(params, X):
+    """logits = W3 relu(W2 relu(W1 x + b1) + b2) + b3 for every row x of X.
+    params = (W1, b1, W2, b2, W3, b3) with W_l of shape (out, in)."""
+    W1, b1, W2, b2, W3, b3 = params
+    z1 = X @ W1.T + b1
+    h1 = np.maximum(z1, 0.0)
+    z2 = h1 @ W2.T + b2
+    h2 = np.maximum(z2, 0.0)
+    logits = h2 @ W3.T + b3
+    return logits, (X, z1, h1, z2, h2)
+
+
+def softmax_xent(logits, y):
+    """Mean cross-entropy of softmax(logits) against integer labels y and its
+    gradient with respect to the logits."""
+    B = logits.shape[0]
+    s = logits - logits.max(axis=1, keepdims=True)
+    e = np.exp(s)
+    P = e / e.sum(axis=1, keepdims=True)
+    loss = -np.mean(np.log(P[np.arange(B), y]))
+    G = P.copy()
+    G[np.arange(B), y] -= 1.0
+    return loss, G / B
+
+
+def mlp_loss_grad(params, X, y):
+    """Loss and gradients (same order as params) by back-propagation."""
+    W1, b1, W2, b2, W3, b3 = params
+    logits, (X_, z1, h1, z2, h2) = mlp_forward(params, X)
+    loss, G3 = softmax_xent(logits, y)
+    gW3 = G3.T @ h2
+    gb3 = G3.sum(axis=0)
+    G2 = (G3 @ W3) * (z2 > 0)
+    gW2 = G2.T @ h1
+    gb2 = G2.sum(axis=0)
+    G1 = (G2 @ W2) * (z1 > 0)
+    gW1 = G1.T @ X_
+    gb1 = G1.sum(axis=0)
+    return loss, (gW1, gb1, gW2, gb2, gW3, gb3)
+
+
+def adam_step(params, grads, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba), t = 1, 2, ...  Returns new (params, m, v)."""
+    out_p, out_m, out_v = [], [], []
+    for P_, G_, M_, V_ in zip(params, grads, m, v):
+        M2 = beta1 * M_ + (1 - beta1) * G_
+        V2 = beta2 * V_ + (1 - beta2) * G_ * G_
+        mh = M2 / (1 - beta1 ** t)
+        vh = V2 / (1 - beta2 ** t)
+        out_p.append(P_ - lr * mh / (np.sqrt(vh) + eps))
+        out_m.append(M2)
+        out_v.append(V2)
+    return out_p, out_m, out_v
+
+
+def alg1_seeded(A, tol, A_seed, pred=None):
+    """Alg. 1 started from a given database (the patches A_seed, inverted
+    here) and optionally hinted: for patch i, when pred[i] >= 0 and
+    d(A_i, B_pred[i]) < tol the prediction is taken (one evaluation);
+    otherwise the database is searched in creation order (first match) and a
+    new entry is appended when nothing matches.
+
+    Returns dict(phi, reps (patch index of each new entry, -1 for seed
+    entries), Binv, evals, hits)."""
+    A = np.asarray(A, dtype=np.float64)
+    npch, p, _ = A.shape
+    Bs, sing = lu_inverse(A_seed)
+    db_A = [a for a in np.asarray(A_seed, dtype=np.float64)]
+    db_B = [b for b in Bs]
+    reps = [-1] * len(db_A)
+    phi = np.full(npch, -1, dtype=np.int64)
+    evals = 0
+    hits = 0
+    for i in range(npch):
+        if pred is not None and pred[i] >= 0:
+            j = int(pred[i])
+            evals += 1
+            if criterion(A[i][None], db_A[j][None], db_B[j][None])[0] < tol:
+                phi[i] = j
+                hits += 1
+                continue
+        j_hit = -1
+        if db_A:
+            d = criterion(A[i][None], np.stack(db_A), np.stack(db_B))
+            h = np.flatnonzero(d < tol)
+            j_hit = int(h[0]) if h.size else -1
+            evals += (j_hit + 1) if j_hit >= 0 else len(db_A)
+        if j_hit >= 0:
+            phi[i] = j_hit
+        else:
+            inv, _ = lu_inverse(A[i][None])
+            db_A.append(A[i])
+            db_B.append(inv[0])
+            reps.append(i)
+            phi[i] = len(db_A) - 1
+    return {"phi": phi, "reps": np.array(reps), "Binv": np.stack(db_B), "evals": evals, "hits": hits}

@@ -28,7 +28,7 @@ SWEEP = {"auto": 0, "grouped": 1, "pergroup": 2}
 
 EXPORTS = ["psr_default_opts", "psr_setup", "psr_apply", "psr_solve", "psr_get_history",
            "psr_get_assignment", "psr_get_stats", "psr_last_error", "psr_destroy", "psr_extract",
-           "psr_batched_inverse", "psr_criterion", "psr_spectral_norm"]
+           "psr_batched_inverse", "psr_criterion", "psr_spectral_norm", "psr_kernel_launches"]
 
 
 class PsrError(RuntimeError):
@@ -99,9 +99,11 @@ def load(path: str = LIB_PATH):
     lib.psr_batched_inverse.argtypes = [vp, i32, i32, vp, vp, vp]
     lib.psr_criterion.argtypes = [vp, i32, i32, vp, vp, d, vp, vp, vp]
     lib.psr_spectral_norm.argtypes = [vp, i32, i32, vp, vp]
+    lib.psr_kernel_launches.argtypes = []
     for name in EXPORTS:
-        if name not in ("psr_default_opts", "psr_last_error", "psr_destroy"):
+        if name not in ("psr_default_opts", "psr_last_error", "psr_destroy", "psr_kernel_launches"):
             getattr(lib, name).restype = C.c_int
+    lib.psr_kernel_launches.restype = C.c_int64
     _lib = lib
     return lib
 
@@ -267,6 +269,10 @@ def psr_spectral_norm(E, sigma, stream=None):
     _need(E, torch.float64, "E")
     b, p, _ = E.shape
     _check(load().psr_spectral_norm(_ptr(E), b, p, _ptr(sigma), _stream(stream)))
+
+
+def psr_kernel_launches() -> int:
+    return int(load().psr_kernel_launches())
 
 
 def exported_symbols(path: str = LIB_PATH) -> list[str]:

@@ -3,6 +3,7 @@
 #include "psr_internal.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstring>
 #include <map>
@@ -13,6 +14,13 @@
 namespace psr {
 
 static thread_local std::string g_last_error;
+static std::atomic<long long> g_launches{0};
+static thread_local bool g_capturing = false;
+
+void count_launch(long long k) {
+    if (!g_capturing) g_launches.fetch_add(k, std::memory_order_relaxed);
+}
+void set_capturing(bool on) { g_capturing = on; }
 
 void set_error(psr_ctx* ctx, const std::string& msg) {
     g_last_error = msg;
@@ -203,14 +211,14 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
                 if (rc != PSR_OK) { cudaFree(sing); cudaFree(first); goto fail; }
                 int32_t big = 0x7fffffff;
                 CK(cudaMemcpyAsync(first, &big, sizeof(int32_t), cudaMemcpyHostToDevice, s));
-                k_any<<<std::max(1, std::min(G.count / 256 + 1, 1024)), 256, 0, s>>>(sing, G.count, first);
+                count_launch(); k_any<<<std::max(1, std::min(G.count / 256 + 1, 1024)), 256, 0, s>>>(sing, G.count, first);
                 int32_t h_first = 0;
                 CK(cudaMemcpyAsync(&h_first, first, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
                 CK(cudaStreamSynchronize(s));
                 G.m = G.count;
                 G.rinv = base;
                 CK(cudaMalloc(&G.sphi, sizeof(int32_t) * (size_t)G.count));
-                k_iota<<<std::max(1, std::min(G.count / 256 + 1, 1024)), 256, 0, s>>>(G.sphi, G.count);
+                count_launch(); k_iota<<<std::max(1, std::min(G.count / 256 + 1, 1024)), 256, 0, s>>>(G.sphi, G.count);
                 G.h_rep.resize(G.count);
                 for (int l = 0; l < G.count; ++l) G.h_rep[l] = l;
                 if (h_first != 0x7fffffff && ctx->stats.first_singular < 0) ctx->stats.first_singular = gidx[&G - &ctx->groups[0]][h_first];
@@ -360,6 +368,8 @@ const char* psr_last_error(psr_ctx* ctx) {
 }
 
 void psr_destroy(psr_ctx* ctx) { destroy_ctx(ctx); }
+
+int64_t psr_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int psr_extract(const psr_csr* A, const psr_patches* P, double* A_out, int32_t* mult_out, double* W_out, void* stream) {
     if (!A || !P || A->n <= 0 || P->n_patches <= 0 || !P->dofs || (P->uniform_size <= 0 && !P->offsets)) {

@@ -390,9 +390,9 @@ int run_alg1_rounds(psr_ctx* ctx, cudaStream_t s) {
         int issued = 0;
         for (;;) {
             for (int r = 0; r < batch; ++r) {
-                k_round_begin<<<1, 256, smem_begin, s>>>(st, phi_l, count, Ag, p, Binv, rep_l, sing_flag, 0);
-                k_round_eval<<<eval_blocks, wpb * 32, smem_eval, s>>>(st, phi_l, count, Ag, p, Binv, tol, undec, undec_cap);
-                k_round_exact<<<64, wpb * 32, smem_eval, s>>>(st, phi_l, Ag, p, Binv, tol, undec, undec_cap);
+                count_launch(); k_round_begin<<<1, 256, smem_begin, s>>>(st, phi_l, count, Ag, p, Binv, rep_l, sing_flag, 0);
+                count_launch(); k_round_eval<<<eval_blocks, wpb * 32, smem_eval, s>>>(st, phi_l, count, Ag, p, Binv, tol, undec, undec_cap);
+                count_launch(); k_round_exact<<<64, wpb * 32, smem_eval, s>>>(st, phi_l, Ag, p, Binv, tol, undec, undec_cap);
             }
             PSR_CHECK_LAUNCH(ctx, "Alg. 1 round kernels");
             issued += batch;
@@ -487,8 +487,8 @@ int launch_criterion_batch(const double* A_i, int32_t batch, int32_t p, const do
     int blocks = (batch + wpb - 1) / wpb;
     if (blocks > 152 * 4) blocks = 152 * 4;
     if (blocks < 1) blocks = 1;
-    k_criterion_batch<<<blocks, wpb * 32, sm, s>>>(A_i, batch, p, A_c, Binv_c, tol, accept, dval, work, work + batch, 0);
-    k_criterion_batch<<<blocks, wpb * 32, sm, s>>>(A_i, batch, p, A_c, Binv_c, tol, accept, dval, work, work + batch, 1);
+    count_launch(); k_criterion_batch<<<blocks, wpb * 32, sm, s>>>(A_i, batch, p, A_c, Binv_c, tol, accept, dval, work, work + batch, 0);
+    count_launch(); k_criterion_batch<<<blocks, wpb * 32, sm, s>>>(A_i, batch, p, A_c, Binv_c, tol, accept, dval, work, work + batch, 1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "k_criterion_batch");
     return PSR_OK;
@@ -525,7 +525,7 @@ int launch_spectral_norm(const double* E, int32_t batch, int32_t p, double* sigm
     int blocks = (batch + wpb - 1) / wpb;
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < 1) blocks = 1;
-    k_spectral_norm<<<blocks, wpb * 32, sm, s>>>(E, batch, p, sigma);
+    count_launch(); k_spectral_norm<<<blocks, wpb * 32, sm, s>>>(E, batch, p, sigma);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "k_spectral_norm");
     return PSR_OK;

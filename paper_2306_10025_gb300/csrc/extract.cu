@@ -44,12 +44,12 @@ int validate_inputs(psr_ctx* ctx, const psr_csr* A, const int32_t* offsets, cons
     int blocks = (int)((A->n + 7) / 8);
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
-    k_validate_csr<<<blocks, 256, 0, s>>>(A->rowptr, A->colidx, A->n, A->nnz, status);
+    count_launch(); k_validate_csr<<<blocks, 256, 0, s>>>(A->rowptr, A->colidx, A->n, A->nnz, status);
     PSR_CHECK_LAUNCH(ctx, "k_validate_csr");
     int b2 = (int)((total_dofs + 255) / 256);
     if (b2 > 4096) b2 = 4096;
     if (b2 < 1) b2 = 1;
-    k_validate_map<<<b2, 256, 0, s>>>(offsets, n_patches, dofs, total_dofs, A->n, status);
+    count_launch(); k_validate_map<<<b2, 256, 0, s>>>(offsets, n_patches, dofs, total_dofs, A->n, status);
     PSR_CHECK_LAUNCH(ctx, "k_validate_map");
     return PSR_OK;
 }
@@ -104,7 +104,7 @@ int launch_extract(const int32_t* rowptr, const int32_t* colidx, const double* v
     int64_t blocks = (warps_needed * 32 + 255) / 256;
     if (blocks > 152 * 64) blocks = 152 * 64;
     if (blocks < 1) blocks = 1;
-    k_extract<<<(int)blocks, 256, 0, s>>>(rowptr, colidx, vals, offsets, dofs, mat_off, n_patches,
+    count_launch(); k_extract<<<(int)blocks, 256, 0, s>>>(rowptr, colidx, vals, offsets, dofs, mat_off, n_patches,
                                           pmax, total, A_out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "k_extract");
@@ -144,11 +144,11 @@ int launch_multiplicity(const int32_t* dofs, int64_t total, int32_t n, int32_t* 
     int b = (int)((total + 255) / 256);
     if (b > 8192) b = 8192;
     if (b < 1) b = 1;
-    k_count<<<b, 256, 0, s>>>(dofs, total, mult);
+    count_launch(); k_count<<<b, 256, 0, s>>>(dofs, total, mult);
     int b2 = (n + 255) / 256;
     if (b2 > 8192) b2 = 8192;
     if (b2 < 1) b2 = 1;
-    k_weights<<<b2, 256, 0, s>>>(mult, n, W, sqrtW, status);
+    count_launch(); k_weights<<<b2, 256, 0, s>>>(mult, n, W, sqrtW, status);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "k_weights");
     return PSR_OK;

@@ -60,7 +60,7 @@ int launch_batched_inverse(const double* A, int64_t stride_in, const int32_t* in
     }
     int64_t blocks = (batch + wpb - 1) / wpb;
     if (blocks > 152 * 32) blocks = 152 * 32;
-    k_batched_inverse<<<(int)blocks, wpb * 32, smem, s>>>(A, stride_in, index, batch, p, Ainv,
+    count_launch(); k_batched_inverse<<<(int)blocks, wpb * 32, smem, s>>>(A, stride_in, index, batch, p, Ainv,
                                                          stride_out, singular);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "k_batched_inverse");

@@ -17,6 +17,7 @@
 #include "psr_internal.cuh"
 
 #include <algorithm>
+#include <vector>
 
 namespace psr {
 
@@ -389,10 +390,10 @@ static void launch_spmv(psr_ctx* ctx, const double* x, double* y, const double* 
     const int tpr = spmv_tpr(ctx);
     const int n = ctx->n;
     switch (tpr) {
-        case 4: k_spmv<4><<<nb, 256, 0, s>>>(ctx->rowptr, ctx->colidx, ctx->vals, x, y, b, n, mode, kd, stop_check, fin); break;
-        case 8: k_spmv<8><<<nb, 256, 0, s>>>(ctx->rowptr, ctx->colidx, ctx->vals, x, y, b, n, mode, kd, stop_check, fin); break;
-        case 16: k_spmv<16><<<nb, 256, 0, s>>>(ctx->rowptr, ctx->colidx, ctx->vals, x, y, b, n, mode, kd, stop_check, fin); break;
-        default: k_spmv<32><<<nb, 256, 0, s>>>(ctx->rowptr, ctx->colidx, ctx->vals, x, y, b, n, mode, kd, stop_check, fin); break;
+        case 4: count_launch(); k_spmv<4><<<nb, 256, 0, s>>>(ctx->rowptr, ctx->colidx, ctx->vals, x, y, b, n, mode, kd, stop_check, fin); break;
+        case 8: count_launch(); k_spmv<8><<<nb, 256, 0, s>>>(ctx->rowptr, ctx->colidx, ctx->vals, x, y, b, n, mode, kd, stop_check, fin); break;
+        case 16: count_launch(); k_spmv<16><<<nb, 256, 0, s>>>(ctx->rowptr, ctx->colidx, ctx->vals, x, y, b, n, mode, kd, stop_check, fin); break;
+        default: count_launch(); k_spmv<32><<<nb, 256, 0, s>>>(ctx->rowptr, ctx->colidx, ctx->vals, x, y, b, n, mode, kd, stop_check, fin); break;
     }
 }
 
@@ -439,11 +440,11 @@ static int enqueue_cg_block(psr_ctx* ctx, KDims kd, int iters, cudaStream_t s) {
     const int n = ctx->n, nb = w.nblk;
     for (int t = 0; t < iters; ++t) {
         launch_spmv(ctx, w.p, w.q, nullptr, 2, 1, kd, 1, nb, s);
-        k_cg_xr<<<nb, 256, 0, s>>>(w.x, w.r, w.p, w.q, n, kd);
+        count_launch(); k_cg_xr<<<nb, 256, 0, s>>>(w.x, w.r, w.p, w.q, n, kd);
         int rc = sweep_apply_ex(ctx, w.r, w.z, kd.ictl + I_STOP, s);
         if (rc != PSR_OK) return rc;
-        k_dot<<<nb, 256, 0, s>>>(w.r, w.z, n, kd, 2);
-        k_cg_p<<<nb, 256, 0, s>>>(w.p, w.z, n, kd);
+        count_launch(); k_dot<<<nb, 256, 0, s>>>(w.r, w.z, n, kd, 2);
+        count_launch(); k_cg_p<<<nb, 256, 0, s>>>(w.p, w.z, n, kd);
     }
     PSR_CHECK_LAUNCH(ctx, "CG block");
     return PSR_OK;
@@ -452,7 +453,7 @@ static int enqueue_cg_block(psr_ctx* ctx, KDims kd, int iters, cudaStream_t s) {
 static int enqueue_fg_cycle(psr_ctx* ctx, KDims kd, cudaStream_t s) {
     KrylovWS& w = ctx->ws;
     const int n = ctx->n, nb = w.nblk, m = kd.m;
-    k_fg_start<<<nb, 256, 0, s>>>(w.r, w.V, n, kd);
+    count_launch(); k_fg_start<<<nb, 256, 0, s>>>(w.r, w.V, n, kd);
     for (int j = 0; j < m; ++j) {
         double* Vj = w.V + (size_t)j * n;
         double* Vn = w.V + (size_t)(j + 1) * n;
@@ -460,14 +461,14 @@ static int enqueue_fg_cycle(psr_ctx* ctx, KDims kd, cudaStream_t s) {
         int rc = sweep_apply_ex(ctx, Vj, Zj, kd.ictl + I_STOP, s);
         if (rc != PSR_OK) return rc;
         launch_spmv(ctx, Zj, Vn, nullptr, 0, 0, kd, 1, nb, s);
-        k_mdot<<<nb, 256, 0, s>>>(w.V, Vn, n, j, kd, 0);
-        k_maxpy<<<nb, 256, 0, s>>>(w.V, Vn, n, j, kd, 0);
-        k_mdot<<<nb, 256, 0, s>>>(w.V, Vn, n, j, kd, 1);
-        k_maxpy<<<nb, 256, 0, s>>>(w.V, Vn, n, j, kd, 1);
-        k_fg_scale<<<nb, 256, 0, s>>>(Vn, n, kd);
+        count_launch(); k_mdot<<<nb, 256, 0, s>>>(w.V, Vn, n, j, kd, 0);
+        count_launch(); k_maxpy<<<nb, 256, 0, s>>>(w.V, Vn, n, j, kd, 0);
+        count_launch(); k_mdot<<<nb, 256, 0, s>>>(w.V, Vn, n, j, kd, 1);
+        count_launch(); k_maxpy<<<nb, 256, 0, s>>>(w.V, Vn, n, j, kd, 1);
+        count_launch(); k_fg_scale<<<nb, 256, 0, s>>>(Vn, n, kd);
     }
-    k_fg_solve<<<1, 32, 0, s>>>(kd);
-    k_fg_update<<<nb, 256, 0, s>>>(w.x, w.Z, n, kd);
+    count_launch(); k_fg_solve<<<1, 32, 0, s>>>(kd);
+    count_launch(); k_fg_update<<<nb, 256, 0, s>>>(w.x, w.Z, n, kd);
     // restart residual r = b - A x (skipped once stopped)
     launch_spmv(ctx, w.x, w.r, w.b, 1, 2, kd, 1, nb, s);
     PSR_CHECK_LAUNCH(ctx, "FGMRES cycle");
@@ -492,13 +493,13 @@ int krylov_solve(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_s
     PSR_CUDA(ctx, cudaMemcpyAsync(w.ictl, hctl, sizeof(hctl), cudaMemcpyHostToDevice, s));
     PSR_CUDA(ctx, cudaMemcpyAsync(w.scal + S_RTOL, &rtol, sizeof(double), cudaMemcpyHostToDevice, s));
     // r = b, keep a copy of b, x = 0, r0 = ||b||
-    k_init_norm<<<nb, 256, 0, s>>>(b, w.b, w.r, n, kd, 1, w.x);
+    count_launch(); k_init_norm<<<nb, 256, 0, s>>>(b, w.b, w.r, n, kd, 1, w.x);
     PSR_CHECK_LAUNCH(ctx, "k_init_norm");
     if (cg) {
         int rc = sweep_apply_ex(ctx, w.r, w.z, w.ictl + I_STOP, s);
         if (rc != PSR_OK) return rc;
-        k_dot<<<nb, 256, 0, s>>>(w.r, w.z, n, kd, 1);
-        k_copy<<<nb, 256, 0, s>>>(w.z, w.p, n, kd);
+        count_launch(); k_dot<<<nb, 256, 0, s>>>(w.r, w.z, n, kd, 1);
+        count_launch(); k_copy<<<nb, 256, 0, s>>>(w.z, w.p, n, kd);
     }
     const int block = cg ? 8 : 1;
     int32_t* hstop = nullptr;
@@ -509,8 +510,22 @@ int krylov_solve(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_s
         PSR_CUDA(ctx, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         cudaGraph_t g;
         PSR_CUDA(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        set_capturing(true);
         int rc = cg ? enqueue_cg_block(ctx, kd, block, cs) : enqueue_fg_cycle(ctx, kd, cs);
+        set_capturing(false);
         cudaError_t ce = cudaStreamEndCapture(cs, &g);
+        if (ce == cudaSuccess && rc == PSR_OK) {
+            size_t nn = 0;
+            cudaGraphGetNodes(g, nullptr, &nn);
+            std::vector<cudaGraphNode_t> nodes(nn);
+            cudaGraphGetNodes(g, nodes.data(), &nn);
+            int kn = 0;
+            for (auto nd : nodes) {
+                cudaGraphNodeType ty;
+                if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kn;
+            }
+            ctx->graph_block = kn;
+        }
         if (rc != PSR_OK) { cudaStreamDestroy(cs); cudaFreeHost(hstop); return rc; }
         if (ce != cudaSuccess) { cudaStreamDestroy(cs); cudaFreeHost(hstop); return cuda_fail(ctx, ce, "graph capture"); }
         ce = cudaGraphInstantiate(&ctx->g_cycle, g, 0);
@@ -523,6 +538,7 @@ int krylov_solve(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_s
     for (int it = 0; it < max_blocks; ++it) {
         if (ctx->g_cycle) {
             PSR_CUDA(ctx, cudaGraphLaunch(ctx->g_cycle, s));
+            count_launch(ctx->graph_block);
         } else {
             rc = cg ? enqueue_cg_block(ctx, kd, block, s) : enqueue_fg_cycle(ctx, kd, s);
             if (rc != PSR_OK) break;

@@ -17,6 +17,12 @@ namespace psr {
 void set_error(psr_ctx* ctx, const std::string& msg);
 int cuda_fail(psr_ctx* ctx, cudaError_t e, const char* what);
 
+// Kernel-launch instrumentation: every host launch site calls count_launch();
+// graph launches add the number of kernel nodes; nothing is counted while a
+// stream is being captured (set_capturing).
+void count_launch(long long k = 1);
+void set_capturing(bool on);
+
 #define PSR_CUDA(ctx, call)                                   \
     do {                                                      \
         cudaError_t e_ = (call);                              \
@@ -78,6 +84,7 @@ struct Group {
     int ntiles = 0;
     int tile_patches = 32;         // chosen by the autotuner
     int warps = 4;
+    bool tc = false;               // BF16 entries applied on the tensor cores
     std::vector<int> h_rep;        // global entry ids of the group's entries
 };
 
@@ -168,6 +175,14 @@ int build_sweep(psr_ctx* ctx, cudaStream_t s);
 int sweep_apply(psr_ctx* ctx, const double* r, double* z, cudaStream_t s);
 int autotune_sweep(psr_ctx* ctx, cudaStream_t s);
 void free_sweep(psr_ctx* ctx);
+
+// sweep_tc.cu (BF16 entries on tcgen05 tensor cores)
+int tc_pad(int p);
+int tc_prepare();
+int convert_tc(const double* src, int m, int p, int sym, __nv_bfloat16** out, cudaStream_t s);
+int launch_sweep_tc(const int32_t* tiles, int ntiles, int p, const __nv_bfloat16* rinv, const int32_t* sdofs,
+                    const double* r, const double* wg, const double* wsc, double* z, const int32_t* stop,
+                    int32_t* err, cudaStream_t s);
 
 // krylov.cu
 int krylov_alloc(psr_ctx* ctx);

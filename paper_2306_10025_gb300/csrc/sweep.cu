@@ -28,6 +28,14 @@ struct GroupDesc {          // device copy for the grouped persistent kernel
     int pad;
 };
 
+// Storage type T -> compute type: FP64 and FP32 compute in their own
+// precision, BF16 storage is widened to FP32.
+template <typename T> struct Comp { using type = T; };
+template <> struct Comp<__nv_bfloat16> { using type = float; };
+
+template <typename T> __device__ __forceinline__ T to_store(double v) { return (T)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }
+
 // ------------------------------------------------------------ kernels
 // Generic: one patch per warp, lane a owns rows a, a+32, ...; p <= 128.
 template <typename T>
@@ -37,18 +45,19 @@ __global__ void __launch_bounds__(256) k_sweep_warp(const int32_t* __restrict__ 
                                                     const double* __restrict__ wsc, double* __restrict__ z,
                                                     const int32_t* __restrict__ stop) {
     extern __shared__ __align__(16) unsigned char smem[];
+    using C = typename Comp<T>::type;
     if (stop && *stop) return;
-    T* sR = reinterpret_cast<T*>(smem);
+    C* sR = reinterpret_cast<C*>(smem);
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
     const int pp = p * p;
-    T* sr = reinterpret_cast<T*>(smem + (((size_t)pp * sizeof(T) + 15) & ~(size_t)15)) + wid * 128;
+    C* sr = reinterpret_cast<C*>(smem + (((size_t)pp * sizeof(C) + 15) & ~(size_t)15)) + wid * 128;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int c = tiles[3 * t], start = tiles[3 * t + 1], cnt = tiles[3 * t + 2];
         const T* src = rinv + (int64_t)c * pp;
         __syncthreads();
-        for (int e = threadIdx.x; e < pp; e += blockDim.x) sR[e] = src[e];
+        for (int e = threadIdx.x; e < pp; e += blockDim.x) sR[e] = (C)src[e];
         __syncthreads();
         for (int k = start + wid; k < start + cnt; k += wpb) {
             const int32_t* dk = sdofs + (int64_t)k * p;
@@ -60,7 +69,7 @@ __global__ void __launch_bounds__(256) k_sweep_warp(const int32_t* __restrict__ 
                 if (a < p) {
                     double v = r[dof[q]];
                     if (wg) v *= wg[dof[q]];
-                    sr[a] = (T)v;
+                    sr[a] = (C)v;
                 }
             }
             __syncwarp();
@@ -68,8 +77,8 @@ __global__ void __launch_bounds__(256) k_sweep_warp(const int32_t* __restrict__ 
             for (int q = 0; q < 4; ++q) {
                 const int a = lane + 32 * q;
                 if (a < p) {
-                    T y = (T)0;
-                    const T* row = sR + a * p;
+                    C y = (C)0;
+                    const C* row = sR + a * p;
                     for (int b = 0; b < p; ++b) y = fma(row[b], sr[b], y);
                     atomicAdd(&z[dof[q]], (double)y * wsc[dof[q]]);
                 }
@@ -88,8 +97,9 @@ __global__ void __launch_bounds__(256) k_sweep_half(const int32_t* __restrict__ 
                                                     const double* __restrict__ wsc, double* __restrict__ z,
                                                     const int32_t* __restrict__ stop) {
     extern __shared__ __align__(16) unsigned char smem[];
+    using C = typename Comp<T>::type;
     if (stop && *stop) return;
-    T* sR = reinterpret_cast<T*>(smem);
+    C* sR = reinterpret_cast<C*>(smem);
     const int lane = threadIdx.x & 31;
     const int half = lane >> 4;
     const int a = lane & 15;
@@ -100,22 +110,22 @@ __global__ void __launch_bounds__(256) k_sweep_half(const int32_t* __restrict__ 
         const int c = tiles[3 * t], start = tiles[3 * t + 1], cnt = tiles[3 * t + 2];
         const T* src = rinv + (int64_t)c * pp;
         __syncthreads();
-        for (int e = threadIdx.x; e < pp; e += blockDim.x) sR[e] = src[e];
+        for (int e = threadIdx.x; e < pp; e += blockDim.x) sR[e] = (C)src[e];
         __syncthreads();
         for (int k0 = start + 2 * wid; k0 < start + cnt; k0 += 2 * wpb) {
             const int k = k0 + half;
             const bool live = (k < start + cnt) && (a < p);
             int dof = 0;
-            T rv = (T)0;
+            C rv = (C)0;
             if (live) {
                 dof = sdofs[(int64_t)k * p + a];
                 double v = r[dof];
                 if (wg) v *= wg[dof];
-                rv = (T)v;
+                rv = (C)v;
             }
-            T y = (T)0;
+            C y = (C)0;
             for (int b = 0; b < p; ++b) {
-                const T rb = __shfl_sync(0xffffffffu, rv, b, 16);
+                const C rb = __shfl_sync(0xffffffffu, rv, b, 16);
                 y = fma(sR[a * p + b < pp ? a * p + b : 0], rb, y);
             }
             if (live) atomicAdd(&z[dof], (double)y * wsc[dof]);
@@ -134,28 +144,29 @@ __global__ void __launch_bounds__(256) k_sweep_full(int count, int p, const T* _
                                                     const double* __restrict__ wsc, double* __restrict__ z,
                                                     const int32_t* __restrict__ stop) {
     extern __shared__ __align__(16) unsigned char smem[];
+    using C = typename Comp<T>::type;
     if (stop && *stop) return;
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const int pp = p * p;
-    const size_t slot = (((size_t)pp + 32) * sizeof(T) + 15) & ~(size_t)15;
-    T* sB = reinterpret_cast<T*>(smem + wid * slot);
-    T* sr = sB + pp;
+    const size_t slot = (((size_t)pp + 32) * sizeof(C) + 15) & ~(size_t)15;
+    C* sB = reinterpret_cast<C*>(smem + wid * slot);
+    C* sr = sB + pp;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < count; k += nw) {
         const T* B = rinv + (int64_t)sphi[k] * pp;
-        for (int e = lane; e < pp; e += 32) sB[e] = B[e];
+        for (int e = lane; e < pp; e += 32) sB[e] = (C)B[e];
         int dof = 0;
         if (lane < p) {
             dof = sdofs[(int64_t)k * p + lane];
             double v = r[dof];
             if (wg) v *= wg[dof];
-            sr[lane] = (T)v;
+            sr[lane] = (C)v;
         }
         __syncwarp();
         if (lane < p) {
-            T y = (T)0;
-            const T* row = sB + lane * p;
+            C y = (C)0;
+            const C* row = sB + lane * p;
             for (int b = 0; b < p; ++b) y = fma(row[b], sr[b], y);
             atomicAdd(&z[dof], (double)y * wsc[dof]);
         }
@@ -174,13 +185,14 @@ __global__ void __launch_bounds__(256) k_sweep_grouped(const int32_t* __restrict
                                                        int32_t* __restrict__ counter, int pmax,
                                                        const int32_t* __restrict__ stop) {
     extern __shared__ __align__(16) unsigned char smem[];
+    using C = typename Comp<T>::type;
     __shared__ int s_tile;
     if (stop && *stop) return;
-    T* sR = reinterpret_cast<T*>(smem);
+    C* sR = reinterpret_cast<C*>(smem);
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    T* sr = reinterpret_cast<T*>(smem + (((size_t)pmax * pmax * sizeof(T) + 15) & ~(size_t)15)) + wid * 128;
+    C* sr = reinterpret_cast<C*>(smem + (((size_t)pmax * pmax * sizeof(C) + 15) & ~(size_t)15)) + wid * 128;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
@@ -191,7 +203,7 @@ __global__ void __launch_bounds__(256) k_sweep_grouped(const int32_t* __restrict
         const GroupDesc gd = groups[g];
         const int p = gd.p, pp = p * p;
         const T* src = reinterpret_cast<const T*>(gd.rinv) + (int64_t)c * pp;
-        for (int e = threadIdx.x; e < pp; e += blockDim.x) sR[e] = src[e];
+        for (int e = threadIdx.x; e < pp; e += blockDim.x) sR[e] = (C)src[e];
         __syncthreads();
         for (int k = start + wid; k < start + cnt; k += wpb) {
             const int32_t* dk = gd.sdofs + (int64_t)k * p;
@@ -203,7 +215,7 @@ __global__ void __launch_bounds__(256) k_sweep_grouped(const int32_t* __restrict
                 if (a < p) {
                     double v = r[dof[q]];
                     if (wg) v *= wg[dof[q]];
-                    sr[a] = (T)v;
+                    sr[a] = (C)v;
                 }
             }
             __syncwarp();
@@ -211,8 +223,8 @@ __global__ void __launch_bounds__(256) k_sweep_grouped(const int32_t* __restrict
             for (int q = 0; q < 4; ++q) {
                 const int a = lane + 32 * q;
                 if (a < p) {
-                    T y = (T)0;
-                    const T* row = sR + a * p;
+                    C y = (C)0;
+                    const C* row = sR + a * p;
                     for (int b = 0; b < p; ++b) y = fma(row[b], sr[b], y);
                     atomicAdd(&z[dof[q]], (double)y * wsc[dof[q]]);
                 }
@@ -242,7 +254,7 @@ __global__ void k_convert(const double* __restrict__ src, int m, int p, int sym,
         const int i = ij / p, j = ij % p;
         double v = src[e];
         if (sym) v = 0.5 * (v + src[c * p * p + (int64_t)j * p + i]);
-        dst[e] = (T)v;
+        dst[e] = to_store<T>(v);
     }
 }
 
@@ -332,18 +344,37 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<int32_t>& h_dofs,
             float* f = nullptr;
             PSR_CUDA(ctx, cudaMalloc(&f, sizeof(float) * std::max<int64_t>(ne, 1)));
             int blocks = (int)std::min<int64_t>((ne + 255) / 256, 152 * 16);
-            k_convert<float><<<std::max(blocks, 1), 256, 0, s>>>(db64, G.m, p, ctx->opts.symmetrize, f);
+            count_launch(); k_convert<float><<<std::max(blocks, 1), 256, 0, s>>>(db64, G.m, p, ctx->opts.symmetrize, f);
             PSR_CHECK_LAUNCH(ctx, "k_convert fp32");
             PSR_CUDA(ctx, cudaStreamSynchronize(s));
             if (!in_place) cudaFree(db64);
             G.rinv = f;
             factor_bytes += ne * 4;
         } else {
-            set_error(ctx, "BF16 storage is not available in this build");
-            return PSR_ERR_INVALID_ARG;
+            // BF16: clustered groups go to the tensor cores (entries stored in
+            // the MMA operand layout); full storage stays on the SIMT path.
+            G.tc = (G.m < G.count);
+            if (G.tc) {
+                __nv_bfloat16* bt = nullptr;
+                int rc = convert_tc(db64, G.m, p, ctx->opts.symmetrize, &bt, s);
+                if (rc != PSR_OK) { set_error(ctx, "BF16 conversion failed"); return rc; }
+                const int P = tc_pad(p);
+                factor_bytes += (int64_t)G.m * P * P * 2;
+                G.rinv = bt;
+            } else {
+                __nv_bfloat16* bt = nullptr;
+                PSR_CUDA(ctx, cudaMalloc(&bt, sizeof(__nv_bfloat16) * std::max<int64_t>(ne, 1)));
+                int blocks = (int)std::min<int64_t>((ne + 255) / 256, 152 * 16);
+                count_launch(); k_convert<__nv_bfloat16><<<std::max(blocks, 1), 256, 0, s>>>(db64, G.m, p, ctx->opts.symmetrize, bt);
+                PSR_CHECK_LAUNCH(ctx, "k_convert bf16");
+                factor_bytes += ne * 2;
+                G.rinv = bt;
+            }
+            PSR_CUDA(ctx, cudaStreamSynchronize(s));
+            if (!in_place) cudaFree(db64);
         }
         std::vector<int32_t> sorted_phi(hs);
-        int T = (p <= 16) ? 64 : 32;
+        int T = G.tc ? 128 : ((p <= 16) ? 64 : 32);
         int rc = make_tiles(ctx, G, sorted_phi, T);
         if (rc != PSR_OK) return rc;
         index_bytes += (int64_t)count * p * 4 + (int64_t)count * 4;
@@ -397,16 +428,23 @@ static int launch_group(psr_ctx* ctx, const Group& G, const double* r, double* z
     int blocks = std::min(G.ntiles, 152 * 8);
     if (blocks < 1) return PSR_OK;
     const T* rinv = reinterpret_cast<const T*>(G.rinv);
+    if (G.tc) {
+        int rc = launch_sweep_tc(G.tiles, G.ntiles, G.p, reinterpret_cast<const __nv_bfloat16*>(G.rinv), G.sdofs,
+                                 r, ctx->Wg, ctx->W, z, stop, ctx->status, s);
+        if (rc != PSR_OK) set_error(ctx, "tensor-core sweep launch failed");
+        return rc;
+    }
     if (G.m == G.count && G.p <= 32) {
         const int wpb = 8;
-        const size_t slot = (((size_t)G.p * G.p + 32) * sizeof(T) + 15) & ~(size_t)15;
+        using C = typename Comp<T>::type;
+        const size_t slot = (((size_t)G.p * G.p + 32) * sizeof(C) + 15) & ~(size_t)15;
         const int fb = std::min((G.count + wpb - 1) / wpb, 152 * 16);
-        k_sweep_full<T><<<fb, wpb * 32, wpb * slot, s>>>(G.count, G.p, rinv, G.sphi, G.sdofs, r, ctx->Wg,
+        count_launch(); k_sweep_full<T><<<fb, wpb * 32, wpb * slot, s>>>(G.count, G.p, rinv, G.sphi, G.sdofs, r, ctx->Wg,
                                                           ctx->W, z, stop);
     } else if (G.p <= 16) {
-        k_sweep_half<T><<<blocks, warps * 32, sm, s>>>(G.tiles, G.ntiles, G.p, rinv, G.sdofs, r, ctx->Wg, ctx->W, z, stop);
+        count_launch(); k_sweep_half<T><<<blocks, warps * 32, sm, s>>>(G.tiles, G.ntiles, G.p, rinv, G.sdofs, r, ctx->Wg, ctx->W, z, stop);
     } else {
-        k_sweep_warp<T><<<blocks, warps * 32, sm, s>>>(G.tiles, G.ntiles, G.p, rinv, G.sdofs, r, ctx->Wg, ctx->W, z, stop);
+        count_launch(); k_sweep_warp<T><<<blocks, warps * 32, sm, s>>>(G.tiles, G.ntiles, G.p, rinv, G.sdofs, r, ctx->Wg, ctx->W, z, stop);
     }
     PSR_CHECK_LAUNCH(ctx, "sweep kernel");
     return PSR_OK;
@@ -415,23 +453,24 @@ static int launch_group(psr_ctx* ctx, const Group& G, const double* r, double* z
 int sweep_apply_ex(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s) {
     PSR_CUDA(ctx, cudaMemsetAsync(z, 0, sizeof(double) * (size_t)ctx->n, s));
     const int prec = ctx->opts.store_prec;
-    if (ctx->sweep_mode == PSR_SWEEP_GROUPED) {
+    if (ctx->sweep_mode == PSR_SWEEP_GROUPED && prec != PSR_PREC_BF16) {
         int pmax = 0;
         for (auto& G : ctx->groups) pmax = std::max(pmax, G.p);
         const int warps = 8;
         const size_t sm = sweep_smem(pmax, prec, warps);
         const GroupDesc* gd = reinterpret_cast<const GroupDesc*>(ctx->gdesc);
         if (prec == PSR_PREC_FP64) {
-            k_sweep_grouped<double><<<ctx->grouped_blocks, warps * 32, sm, s>>>(ctx->gtiles, ctx->gntiles, gd, r, ctx->Wg, ctx->W, z, ctx->gcounter, pmax, stop);
+            count_launch(); k_sweep_grouped<double><<<ctx->grouped_blocks, warps * 32, sm, s>>>(ctx->gtiles, ctx->gntiles, gd, r, ctx->Wg, ctx->W, z, ctx->gcounter, pmax, stop);
         } else {
-            k_sweep_grouped<float><<<ctx->grouped_blocks, warps * 32, sm, s>>>(ctx->gtiles, ctx->gntiles, gd, r, ctx->Wg, ctx->W, z, ctx->gcounter, pmax, stop);
+            count_launch(); k_sweep_grouped<float><<<ctx->grouped_blocks, warps * 32, sm, s>>>(ctx->gtiles, ctx->gntiles, gd, r, ctx->Wg, ctx->W, z, ctx->gcounter, pmax, stop);
         }
         PSR_CHECK_LAUNCH(ctx, "grouped sweep");
         return PSR_OK;
     }
     for (auto& G : ctx->groups) {
-        int rc = (prec == PSR_PREC_FP64) ? launch_group<double>(ctx, G, r, z, stop, s)
-                                         : launch_group<float>(ctx, G, r, z, stop, s);
+        int rc = (prec == PSR_PREC_FP64)   ? launch_group<double>(ctx, G, r, z, stop, s)
+                 : (prec == PSR_PREC_FP32) ? launch_group<float>(ctx, G, r, z, stop, s)
+                                           : launch_group<__nv_bfloat16>(ctx, G, r, z, stop, s);
         if (rc != PSR_OK) return rc;
     }
     return PSR_OK;
@@ -445,6 +484,12 @@ int sweep_prepare(psr_ctx* ctx) {
     PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_warp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_grouped<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_grouped<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_warp<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_full<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    {
+        int rc = tc_prepare();
+        if (rc != PSR_OK) return rc;
+    }
     PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_full<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_full<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     return PSR_OK;

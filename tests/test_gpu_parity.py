@@ -226,6 +226,78 @@ def test_apply_fp32_error_bound(lib):
     assert err < 1e-5
 
 
+def bf16_round(x):
+    """FP64 -> FP32 -> BF16 with round-to-nearest-even, back to FP64."""
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float64).astype(np.float32))
+    b = f.view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def bf16_reference(r, dofs, Binv, phi, W, weighting, symmetrize=True):
+    """Eq. (3) with the stored operator rounded to BF16 (after symmetrising)
+    and r split into BF16 hi + lo, products summed exactly (FP64)."""
+    B = 0.5 * (Binv + np.transpose(Binv, (0, 2, 1))) if symmetrize else Binv
+    Bq = bf16_round(B)
+    sw = np.sqrt(W)
+    x = sw * r if weighting == "sym" else r
+    xk = x[dofs]
+    hi = bf16_round(xk)
+    lo = bf16_round(xk - hi)
+    yk = np.einsum("kab,kb->ka", Bq[phi], hi + lo)
+    acc = np.zeros_like(r)
+    np.add.at(acc, dofs.reshape(-1), yk.reshape(-1))
+    return (sw if weighting == "sym" else W) * acc
+
+
+@pytest.mark.parametrize("case", ["stokes_tc", "poisson_tc", "nedelec_tc", "diff3d_tc", "full_simt"])
+def test_apply_bf16_vs_rounded_operator(lib, case):
+    """BF16 storage: tensor-core (clustered) and SIMT (full storage) paths
+    equal the exactly summed product with the same BF16-rounded operands,
+    up to FP32 accumulation."""
+    if case == "stokes_tc":
+        pr, tol, w = P.stokes2d_q2q1(8), 1e-1, "left"
+    elif case == "poisson_tc":
+        pr, tol, w = P.poisson2d_q2(16), 1e-12, "sym"
+    elif case == "nedelec_tc":
+        pr, tol, w = P.nedelec3d(4, seed=5), 1.0, "sym"
+    elif case == "diff3d_tc":
+        pr, tol, w = P.diffusion3d_q2(4, seed=3), 0.5, "sym"
+    else:
+        pr, tol, w = P.poisson2d_q2(8), 0.0, "sym"
+    st = O.setup(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d(), tol)
+    ctx = setup_ctx(lib, pr, tol=tol, store_prec="bf16", weighting=w, krylov=pr.krylov)
+    assert ctx.stats()["m_p"] == len(st["reps"])
+    g = np.random.default_rng(11)
+    for _ in range(2):
+        r = g.standard_normal(pr.n)
+        z = torch.empty(pr.n, dtype=torch.float64, device="cuda")
+        ctx.apply(dev(r, torch.float64), z)
+        zr = bf16_reference(r, pr.dofs2d(), st["Binv"], st["phi"], st["W"], w)
+        err = np.abs(z.cpu().numpy() - zr).max() / np.abs(zr).max()
+        assert err < 2e-6, (case, err)
+        # and the BF16 operator stays within BF16 rounding of the FP64 one
+        z64 = O.apply(r, pr.dofs2d(), st["Binv"], st["phi"], st["W"], w)
+        assert np.abs(z.cpu().numpy() - z64).max() / np.abs(z64).max() < 3e-2
+
+
+def test_bf16_pcg_converges_close_to_fp64(lib):
+    """CG with the BF16 tensor-core operator (a fixed SPD operator) converges;
+    iteration count within a few of the FP64 form."""
+    pr = P.poisson2d_q2(16)
+    b = dev(pr.rhs(0), torch.float64)
+    its = {}
+    for prec in ("fp64", "bf16"):
+        ctx = setup_ctx(lib, pr, tol=1e-12, store_prec=prec, weighting="sym", krylov="cg")
+        x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
+        info = ctx.solve(b, x)
+        assert info["converged"]
+        its[prec] = info["iterations"]
+        res = np.linalg.norm(pr.rhs(0) - pr.to_scipy() @ x.cpu().numpy()) / np.linalg.norm(pr.rhs(0))
+        assert res <= 1.05e-8
+    assert its["bf16"] <= its["fp64"] + 3, its
+
+
 def test_apply_grouped_equals_pergroup(lib):
     pr = P.stokes2d_q2q1(8)
     r = dev(np.random.default_rng(4).standard_normal(pr.n), torch.float64)

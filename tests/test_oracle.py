@@ -368,3 +368,75 @@ def test_c1_full_storage_pcg_converges():
     # the preconditioner helps: plain CG needs more iterations
     _, _, it_plain, _ = O.pcg(lambda v: pr.to_scipy() @ v, lambda v: v, b)
     assert it < it_plain
+
+
+# --------------------------------------------------------------------------- a6 (MLP)
+def _mlp_params(g, d, h, m, scale=0.3):
+    return [g.standard_normal((h, d)) * scale, g.standard_normal(h) * 0.1,
+            g.standard_normal((h, h)) * scale, g.standard_normal(h) * 0.1,
+            g.standard_normal((m, h)) * scale, g.standard_normal(m) * 0.1]
+
+
+def test_mlp_gradient_matches_finite_differences():
+    g = _rng(20)
+    d, h, m, B = 7, 6, 4, 5
+    params = _mlp_params(g, d, h, m)
+    X = g.standard_normal((B, d))
+    y = g.integers(0, m, B)
+    loss, grads = O.mlp_loss_grad(params, X, y)
+    eps = 1e-6
+    for li, (Pm, Gm) in enumerate(zip(params, grads)):
+        flat = Pm.reshape(-1)
+        for idx in g.choice(flat.size, min(flat.size, 6), replace=False):
+            old = flat[idx]
+            flat[idx] = old + eps
+            lp, _ = O.mlp_loss_grad(params, X, y)
+            flat[idx] = old - eps
+            lm, _ = O.mlp_loss_grad(params, X, y)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * eps)
+            assert abs(fd - Gm.reshape(-1)[idx]) <= 1e-6 * max(1.0, abs(fd)), (li, idx)
+
+
+def test_softmax_xent_closed_forms():
+    m = 7
+    loss, G = O.softmax_xent(np.zeros((3, m)), np.array([0, 3, 6]))
+    assert abs(loss - np.log(m)) < 1e-15
+    assert np.allclose(G.sum(axis=1), 0.0)
+
+
+def test_adam_first_step_is_signed_lr():
+    """With zero state, the bias-corrected first Adam step is lr * sign(g)."""
+    p = [np.array([1.0, -2.0, 3.0])]
+    gr = [np.array([0.5, -4.0, 1e-3])]
+    out, m, v = O.adam_step(p, gr, [np.zeros(3)], [np.zeros(3)], 1, 0.01, eps=0.0)
+    assert np.allclose(out[0], p[0] - 0.01 * np.sign(gr[0]), atol=1e-15)
+
+
+def test_features_scale_invariant_and_log_norm():
+    g = _rng(21)
+    A = g.standard_normal((3, 4, 4))
+    X1 = O.patch_features(A, np.array([1.0, 2.0, 3.0]))
+    X2 = O.patch_features(5.0 * A, np.array([1.0, 2.0, 3.0]))
+    assert np.allclose(X1[:, :16], X2[:, :16])
+    assert np.allclose(X2[:, 16] - X1[:, 16], np.log(5.0))
+    assert np.allclose(X1[:, 17], np.log([1.0, 2.0, 3.0]))
+
+
+def test_alg1_seeded_hints_keep_assignment_valid():
+    """Seeded Alg. 1 without hints equals plain Alg. 1 when the seed is the
+    plain run's database; correct hints cost one evaluation per patch, wrong
+    hints fall back and still give a valid assignment."""
+    pr = P.diffusion3d_q2(3, seed=4)
+    A = O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d())
+    tol = 0.3
+    base = O.alg1(A, tol)
+    seed_A = A[base["reps"]]
+    s0 = O.alg1_seeded(A, tol, seed_A)
+    assert np.array_equal(s0["phi"], base["phi"])
+    s1 = O.alg1_seeded(A, tol, seed_A, pred=base["phi"])
+    assert s1["hits"] == A.shape[0] and s1["evals"] == A.shape[0]
+    bad = (base["phi"] + 1) % len(base["reps"])
+    s2 = O.alg1_seeded(A, tol, seed_A, pred=bad)
+    d = O.criterion(A, A[base["reps"]][s2["phi"]], s2["Binv"][s2["phi"]])
+    assert np.all(d < tol)
