@@ -117,6 +117,19 @@ void psr_default_opts(psr_opts* o);
 int psr_setup(const psr_csr* A, const psr_patches* patches, const psr_opts* opts,
               void* stream, psr_ctx** out);
 
+/* Setup whose Alg. 1 starts from a given database and optional hints
+ * (learned assignment; no counterpart in the paper beyond its closing remark
+ * on deep-learning assisted clustering).  seed_A: device, m0 x p x p patch
+ * matrices forming database entries 0..m0-1 (inverted here).  hints: device,
+ * n_patches entries in [-1, m0); patch i with hints[i] >= 0 is first compared
+ * with that entry (one criterion evaluation) and assigned to it when
+ * d < tol; every other patch runs Alg. 1 against the database in creation
+ * order (seed entries first) and may append new entries.  Needs tol > 0 and
+ * patches of one size p <= 32.  psr_get_stats reports the hits. */
+int psr_setup_seeded(const psr_csr* A, const psr_patches* patches, const psr_opts* opts,
+                     const double* seed_A, int32_t m0, const int32_t* hints, void* stream,
+                     psr_ctx** out);
+
 /* z = M~^{-1} r (Eq. 3 with the context's weighting).  r, z: device, length n,
  * must not overlap.  Stream-ordered, no host synchronisation, no allocation. */
 int psr_apply(psr_ctx* ctx, const double* r, double* z, void* stream);
@@ -197,6 +210,39 @@ int psr_criterion(const double* A_i, int32_t batch, int32_t p, const double* A_c
  * FP64 (the "small SVD" of the section 3 remark).  1 <= p <= 32. */
 int psr_spectral_norm(const double* E, int32_t batch, int32_t p, double* sigma,
                       void* stream);
+
+/* ---- learned assignment: per-patch features and a small MLP ------------ */
+
+/* X[k] <- (A_k / ||A_k||_F row-major, log ||A_k||_F, log coef[k]) as FP32,
+ * row stride p*p + 2.  A: device n_patches x p x p FP64; coef: device FP64
+ * cell coefficient per patch or NULL (feature 0). */
+int psr_features(const double* A, int32_t n_patches, int32_t p, const double* coef, float* X,
+                 void* stream);
+
+typedef struct psr_mlp psr_mlp;   /* opaque, library-owned */
+
+/* d -> h -> h -> m network, ReLU hidden layers, softmax cross-entropy, Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8).  Parameters are FP32 and packed as
+ * W1 (h x d), b1 (h), W2 (h x h), b2 (h), W3 (m x h), b3 (m), row-major;
+ * they start at zero until psr_mlp_set_params. */
+int psr_mlp_create(int32_t in_dim, int32_t hidden, int32_t classes, psr_mlp** out);
+int64_t psr_mlp_num_params(const psr_mlp* net);
+/* packed: device, psr_mlp_num_params floats; also resets the Adam state. */
+int psr_mlp_set_params(psr_mlp* net, const float* packed, void* stream);
+int psr_mlp_get_params(const psr_mlp* net, float* packed, void* stream);
+/* Mean loss over the batch (device scalar, may be NULL) and its gradient
+ * (device, packed like the parameters, may be NULL).  X: device batch x d
+ * FP32, y: device batch labels in [0, m). */
+int psr_mlp_loss_grad(psr_mlp* net, const float* X, const int32_t* y, int32_t batch, float* loss,
+                      float* grads, void* stream);
+/* One Adam step on the batch; loss as above. */
+int psr_mlp_train_step(psr_mlp* net, const float* X, const int32_t* y, int32_t batch, float lr,
+                       float* loss, void* stream);
+/* cls (device, batch, may be NULL) <- argmax of the logits (lowest index on
+ * ties); logits (device, batch x m, may be NULL). */
+int psr_mlp_predict(psr_mlp* net, const float* X, int32_t batch, int32_t* cls, float* logits,
+                    void* stream);
+void psr_mlp_destroy(psr_mlp* net);
 
 #ifdef __cplusplus
 }

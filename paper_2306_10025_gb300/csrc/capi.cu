@@ -83,7 +83,8 @@ static int check_status(psr_ctx* ctx, cudaStream_t s) {
     return PSR_OK;
 }
 
-static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o, cudaStream_t s, psr_ctx** out) {
+static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o, cudaStream_t s, psr_ctx** out,
+                      const double* seed_A, int m0, const int32_t* hints) {
     auto t_all = std::chrono::steady_clock::now();
     psr_ctx* ctx = new psr_ctx();
     *out = nullptr;
@@ -153,6 +154,7 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
             if (G.p > 128) { set_error(ctx, "patches larger than 128 DOFs are not supported"); FAIL(PSR_ERR_INVALID_ARG); }
             for (int l = 0; l < G.count; ++l) h_mat_off[it->second[l]] = off + (int64_t)l * G.p * G.p;
             off += (int64_t)G.count * G.p * G.p;
+            G.h_gidx = it->second;
             ctx->groups.push_back(G);
             gidx.push_back(it->second);
         }
@@ -198,7 +200,7 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
         CK(cudaMalloc(&ctx->phi, sizeof(int32_t) * (size_t)np));
         CK(cudaMalloc(&ctx->rep_ids, sizeof(int32_t) * (size_t)np));
         t0 = std::chrono::steady_clock::now();
-        if (op.tol == 0.0) {
+        if (op.tol == 0.0 && m0 == 0) {
             // strict "< 0" never holds: every patch is its own entry (Eq. 1)
             int32_t* sing = nullptr;
             int32_t* first = nullptr;
@@ -230,7 +232,7 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
         } else {
             for (auto& G : ctx->groups)
                 if (G.p > 32) { set_error(ctx, "the criterion kernel handles patches of at most 32 DOFs"); FAIL(PSR_ERR_INVALID_ARG); }
-            rc = run_alg1_rounds(ctx, s);
+            rc = run_alg1(ctx, s, seed_A, m0, hints);
             if (rc != PSR_OK) goto fail;
         }
         CK(cudaStreamSynchronize(s));
@@ -313,12 +315,39 @@ int psr_setup(const psr_csr* A, const psr_patches* patches, const psr_opts* opts
         return PSR_ERR_CUDA;
     }
     try {
-        return setup_impl(A, patches, opts, (cudaStream_t)stream, out);
+        return setup_impl(A, patches, opts, (cudaStream_t)stream, out, nullptr, 0, nullptr);
     } catch (const std::bad_alloc&) {
         set_error(nullptr, "host allocation failed");
         return PSR_ERR_OOM;
     } catch (...) {
         set_error(nullptr, "unexpected host exception in psr_setup");
+        return PSR_ERR_CUDA;
+    }
+}
+
+int psr_setup_seeded(const psr_csr* A, const psr_patches* patches, const psr_opts* opts, const double* seed_A,
+                     int32_t m0, const int32_t* hints, void* stream, psr_ctx** out) {
+    if (!out) { set_error(nullptr, "out is NULL"); return PSR_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (!A || !patches || !A->rowptr || !A->vals || !A->colidx || A->n <= 0 || patches->n_patches <= 0 ||
+        !patches->dofs || patches->uniform_size <= 0 || patches->uniform_size > 32 || m0 < 0 ||
+        (m0 > 0 && !seed_A) || (hints && m0 == 0)) {
+        set_error(nullptr, "invalid seeded setup arguments (uniform patches of at most 32 DOFs, m0 >= 0)");
+        return PSR_ERR_INVALID_ARG;
+    }
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) {
+        cudaGetLastError();
+        set_error(nullptr, "no CUDA device: the library has no CPU fallback");
+        return PSR_ERR_CUDA;
+    }
+    psr_opts o;
+    if (opts) o = *opts; else psr_default_opts(&o);
+    if (!(o.tol > 0.0)) { set_error(nullptr, "a seeded setup needs tol > 0"); return PSR_ERR_INVALID_ARG; }
+    try {
+        return setup_impl(A, patches, &o, (cudaStream_t)stream, out, seed_A, m0, hints);
+    } catch (...) {
+        set_error(nullptr, "unexpected host exception in psr_setup_seeded");
         return PSR_ERR_CUDA;
     }
 }

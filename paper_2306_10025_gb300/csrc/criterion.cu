@@ -41,7 +41,6 @@ struct RoundDev {
     int n_undec;
     int first_singular;
     unsigned long long evals, exact;
-    double binv_fro;
     int undec_overflow;
     int pad;
 };
@@ -154,20 +153,14 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
     __syncwarp();
     // column j of E lives in lane j after a transpose read
     double ecol[32];
-    if (act) {
 #pragma unroll
-        for (int r = 0; r < 32; ++r) ecol[r] = (r < p) ? ws.E[r * ld + lane] : 0.0;
-    }
+    for (int r = 0; r < 32; ++r) ecol[r] = (act && r < p) ? ws.E[r * ld + lane] : 0.0;
     __syncwarp();
-    if (act) {
-        for (int k = 0; k < p; ++k) {     // G[lane][k] = sum_r E[r][lane] E[r][k]
-            double g = 0.0;
-            for (int r = 0; r < p; ++r) g = fma(ecol[r], __shfl_sync(0xffffffffu, ecol[r], k), g);
-            ws.E[lane * ld + k] = g;
-        }
-    } else {
-        for (int k = 0; k < p; ++k)
-            for (int r = 0; r < p; ++r) (void)__shfl_sync(0xffffffffu, 0.0, k);
+    // G[lane][k] = sum_r E[r][lane] E[r][k]; every lane runs every shuffle
+    for (int k = 0; k < p; ++k) {
+        double g = 0.0;
+        for (int r = 0; r < p; ++r) g = fma(ecol[r], __shfl_sync(0xffffffffu, ecol[r], k), g);
+        if (act) ws.E[lane * ld + k] = g;
     }
     __syncwarp();
     const double lam = jacobi_lambda_max_warp(ws.E, p, ld);
@@ -182,12 +175,19 @@ __host__ __device__ inline size_t eval_smem_bytes(int p, int wpb) {
     return (size_t)(2 * p * ld) * 8 + (size_t)wpb * ((size_t)p * ld + 64) * 8;
 }
 
+// Entry database of one size group: patch matrices A_c, inverses B_c^{-1}
+// and ||B_c^{-1}||_F of every entry, in creation order.
+struct EntryDB {
+    double* A;
+    double* Binv;
+    double* fro;
+};
+
 // One CTA: next entry = smallest unassigned local patch at or after cursor;
-// then warp 0 inverts it into the FP64 database (slot m).
+// warp 0 copies it into the database (slot m) and inverts it there.
 __global__ void k_round_begin(RoundDev* st, int32_t* __restrict__ phi, int count,
-                              const double* __restrict__ Ag, int p, double* __restrict__ Binv,
-                              int32_t* __restrict__ rep_local, int32_t* __restrict__ singular_flags,
-                              int group_base) {
+                              const double* __restrict__ Ag, int p, EntryDB db,
+                              int32_t* __restrict__ rep_local, int32_t* __restrict__ singular_flags) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_first;
     if (st->done) return;
@@ -213,11 +213,16 @@ __global__ void k_round_begin(RoundDev* st, int32_t* __restrict__ phi, int count
         double* colk = S + p * ld;
         int* swaps = reinterpret_cast<int*>(colk + p);
         const double* a = Ag + (int64_t)i0 * p * p;
-        for (int e = tid; e < p * p; e += 32) S[(e / p) * ld + (e % p)] = a[e];
+        double* acopy = db.A + (int64_t)m * p * p;
+        for (int e = tid; e < p * p; e += 32) {
+            const double v = a[e];
+            acopy[e] = v;
+            S[(e / p) * ld + (e % p)] = v;
+        }
         __syncwarp();
         const bool sing = gj_invert_warp(S, p, ld, colk, swaps);
         double fro = 0.0;
-        double* out = Binv + (int64_t)m * p * p;
+        double* out = db.Binv + (int64_t)m * p * p;
         for (int e = tid; e < p * p; e += 32) {
             const double v = S[(e / p) * ld + (e % p)];
             out[e] = v;
@@ -225,10 +230,10 @@ __global__ void k_round_begin(RoundDev* st, int32_t* __restrict__ phi, int count
         }
         fro = warp_sum(fro);
         if (tid == 0) {
-            st->binv_fro = sqrt(fro);
+            db.fro[m] = sqrt(fro);
             if (sing) {
                 singular_flags[0] = 1;
-                if (st->first_singular < 0) st->first_singular = group_base + i0;
+                if (st->first_singular < 0) st->first_singular = i0;
             }
             phi[i0] = m;
             rep_local[m] = i0;
@@ -239,33 +244,61 @@ __global__ void k_round_begin(RoundDev* st, int32_t* __restrict__ phi, int count
     }
 }
 
-// Persistent warps over local patches (i0, count): every unassigned one is
-// compared with the newest entry.  Undecided candidates go to a list.
+__global__ void k_reset_undec(RoundDev* st) { st->n_undec = 0; }
+
+// ||B_j^{-1}||_F of every seed entry (one warp each); flags a singular seed.
+__global__ void k_entry_fro(const double* __restrict__ Binv, int m, int p, double* __restrict__ fro,
+                            const int32_t* __restrict__ sflags, int32_t* __restrict__ any_bad) {
+    const int lane = threadIdx.x & 31;
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= m) return;
+    double s = 0.0;
+    for (int e = lane; e < p * p; e += 32) s = fma(Binv[(int64_t)j * p * p + e], Binv[(int64_t)j * p * p + e], s);
+    s = warp_sum(s);
+    if (lane == 0) {
+        fro[j] = sqrt(s);
+        if (sflags[j]) atomicOr(any_bad, 1);
+    }
+}
+
+// Stages entry `e` (fixed >= 0) or the newest entry, and returns the first
+// candidate index: all patches for a fixed entry, patches after the newest
+// entry's patch otherwise.
+__device__ __forceinline__ int stage_entry(const RoundDev* st, EntryDB db, int p, int fixed, double* sAc, double* sB,
+                                           int* entry, double* bfro) {
+    const int ld = p + 1;
+    const int e = (fixed >= 0) ? fixed : st->m - 1;
+    const double* a = db.A + (int64_t)e * p * p;
+    const double* bm = db.Binv + (int64_t)e * p * p;
+    for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+        sAc[(t / p) * ld + (t % p)] = a[t];
+        sB[(t / p) * ld + (t % p)] = bm[t];
+    }
+    *entry = e;
+    *bfro = db.fro[e];
+    return (fixed >= 0) ? 0 : st->i0 + 1;
+}
+
+// Persistent warps over the candidate range: every unassigned patch is
+// compared with one entry.  Undecided candidates go to a list.
 __global__ void k_round_eval(RoundDev* st, int32_t* __restrict__ phi, int count,
-                             const double* __restrict__ Ag, int p, const double* __restrict__ Binv,
-                             double tol, int32_t* __restrict__ undec, int undec_cap) {
+                             const double* __restrict__ Ag, int p, EntryDB db,
+                             double tol, int32_t* __restrict__ undec, int undec_cap, int fixed) {
     extern __shared__ __align__(16) unsigned char smem[];
     if (st->done) return;
     const int ld = p + 1;
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    const int i0 = st->i0;
-    const int m = st->m - 1;
-    const double bfro = st->binv_fro;
     double* sAc = reinterpret_cast<double*>(smem);
     double* sB = sAc + p * ld;
     double* wbase = sB + p * ld + (size_t)wid * (p * ld + 64);
     WarpScratch ws{wbase, wbase + p * ld, wbase + p * ld + 32};
-    const double* a = Ag + (int64_t)i0 * p * p;
-    const double* bm = Binv + (int64_t)m * p * p;
-    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-        sAc[(e / p) * ld + (e % p)] = a[e];
-        sB[(e / p) * ld + (e % p)] = bm[e];
-    }
+    int m;
+    double bfro;
+    const int start = stage_entry(st, db, p, fixed, sAc, sB, &m, &bfro);
     __syncthreads();
     unsigned long long my_evals = 0;
-    const int start = i0 + 1;
     const int gw = blockIdx.x * wpb + wid;
     const int nw = gridDim.x * wpb;
     for (int base = start + gw * 32; base < count; base += nw * 32) {
@@ -293,10 +326,10 @@ __global__ void k_round_eval(RoundDev* st, int32_t* __restrict__ phi, int count,
     if (lane == 0 && my_evals) atomicAdd(&st->evals, my_evals);
 }
 
-// Exact path for the undecided candidates of this round.
+// Exact path for the undecided candidates of this pass.
 __global__ void k_round_exact(RoundDev* st, int32_t* __restrict__ phi, const double* __restrict__ Ag,
-                              int p, const double* __restrict__ Binv, double tol,
-                              const int32_t* __restrict__ undec, int undec_cap) {
+                              int p, EntryDB db, double tol, const int32_t* __restrict__ undec,
+                              int undec_cap, int fixed) {
     extern __shared__ __align__(16) unsigned char smem[];
     if (st->done) return;
     const int nund = min(st->n_undec, undec_cap);
@@ -305,19 +338,13 @@ __global__ void k_round_exact(RoundDev* st, int32_t* __restrict__ phi, const dou
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    const int i0 = st->i0;
-    const int m = st->m - 1;
-    const double bfro = st->binv_fro;
     double* sAc = reinterpret_cast<double*>(smem);
     double* sB = sAc + p * ld;
     double* wbase = sB + p * ld + (size_t)wid * (p * ld + 64);
     WarpScratch ws{wbase, wbase + p * ld, wbase + p * ld + 32};
-    const double* a = Ag + (int64_t)i0 * p * p;
-    const double* bm = Binv + (int64_t)m * p * p;
-    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-        sAc[(e / p) * ld + (e % p)] = a[e];
-        sB[(e / p) * ld + (e % p)] = bm[e];
-    }
+    int m;
+    double bfro;
+    stage_entry(st, db, p, fixed, sAc, sB, &m, &bfro);
     __syncthreads();
     for (int u = blockIdx.x * wpb + wid; u < nund; u += gridDim.x * wpb) {
         const int cand = undec[u];
@@ -331,6 +358,49 @@ __global__ void k_round_exact(RoundDev* st, int32_t* __restrict__ phi, const dou
     }
 }
 
+// Hints: patch i with hint[i] >= 0 is compared with that entry first (one
+// evaluation, exact path inline when the bounds do not decide).
+__global__ void k_verify_hints(RoundDev* st, int32_t* __restrict__ phi, int count, const double* __restrict__ Ag,
+                               int p, EntryDB db, int m0, double tol, const int32_t* __restrict__ hint,
+                               int32_t* __restrict__ hits) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int ld = p + 1;
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    double* wbase = reinterpret_cast<double*>(smem) + (size_t)wid * (2 * p * ld + p * ld + 64);
+    double* sAc = wbase;
+    double* sB = wbase + p * ld;
+    WarpScratch ws{wbase + 2 * p * ld, wbase + 3 * p * ld, wbase + 3 * p * ld + 32};
+    unsigned long long ev = 0, ex = 0;
+    int my_hits = 0;
+    for (int i = blockIdx.x * wpb + wid; i < count; i += gridDim.x * wpb) {
+        const int e = hint[i];
+        if (e < 0 || e >= m0) continue;
+        const double* a = db.A + (int64_t)e * p * p;
+        const double* bm = db.Binv + (int64_t)e * p * p;
+        for (int t = lane; t < p * p; t += 32) {
+            sAc[(t / p) * ld + (t % p)] = a[t];
+            sB[(t / p) * ld + (t % p)] = bm[t];
+        }
+        __syncwarp();
+        double dv;
+        int dec = decide_pair(Ag + (int64_t)i * p * p, sAc, sB, p, ld, db.fro[e], tol, ws, &dv, false);
+        if (dec < 0) {
+            dec = decide_pair(Ag + (int64_t)i * p * p, sAc, sB, p, ld, db.fro[e], tol, ws, &dv, true);
+            ++ex;
+        }
+        ++ev;
+        if (lane == 0 && dec == 1) { phi[i] = e; ++my_hits; }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        if (ev) atomicAdd(&st->evals, ev);
+        if (ex) atomicAdd(&st->exact, ex);
+        if (my_hits) atomicAdd(hits, my_hits);
+    }
+}
+
 static int set_smem(const void* f, size_t bytes) {
     if (bytes > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -340,24 +410,25 @@ static int set_smem(const void* f, size_t bytes) {
 }
 
 // Runs Alg. 1 for every size group.  On entry ctx->A_ext holds the patches
-// (group-contiguous); on exit ctx->phi / rep_ids hold the global assignment
-// and every group's FP64 database is in a temporary buffer that is converted
-// by the sweep builder.  Returns the FP64 database via ctx->groups[g].rinv
-// (double*, m x p x p) -- the storage conversion happens in build_sweep.
-int run_alg1_rounds(psr_ctx* ctx, cudaStream_t s) {
+// (group-contiguous).  With a seed database (seed_A, m0 entries; single size
+// group only) the search starts from it, and with hints every patch first
+// tries its hinted entry.  On exit every group carries its local assignment
+// (G.sphi, original order) and its FP64 inverses (G.rinv, m x p x p), which the
+// sweep builder converts and lays out.
+int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const int32_t* hints) {
     const double tol = ctx->opts.tol;
     RoundDev* st = nullptr;
     RoundDev* h_st = nullptr;
     PSR_CUDA(ctx, cudaMalloc(&st, sizeof(RoundDev)));
     PSR_CUDA(ctx, cudaMallocHost(&h_st, sizeof(RoundDev)));
     int32_t* sing_flag = nullptr;
-    PSR_CUDA(ctx, cudaMalloc(&sing_flag, sizeof(int32_t)));
-    PSR_CUDA(ctx, cudaMemsetAsync(sing_flag, 0, sizeof(int32_t), s));
+    PSR_CUDA(ctx, cudaMalloc(&sing_flag, 2 * sizeof(int32_t)));
+    PSR_CUDA(ctx, cudaMemsetAsync(sing_flag, 0, 2 * sizeof(int32_t), s));
     int rc = PSR_OK;
-    int entry_base = 0;
-    int64_t total_evals = 0, total_exact = 0;
+    int64_t total_evals = 0, total_exact = 0, total_hits = 0;
     int rounds_total = 0;
     int first_singular = -1;
+    if (m0 > 0 && ctx->groups.size() != 1) { set_error(ctx, "a seed database needs patches of one size"); return PSR_ERR_INVALID_ARG; }
     for (size_t g = 0; g < ctx->groups.size() && rc == PSR_OK; ++g) {
         Group& G = ctx->groups[g];
         const int p = G.p, count = G.count;
@@ -365,16 +436,23 @@ int run_alg1_rounds(psr_ctx* ctx, cudaStream_t s) {
         int32_t* phi_l = nullptr;
         int32_t* rep_l = nullptr;
         int32_t* undec = nullptr;
-        double* Binv = nullptr;
+        EntryDB db{nullptr, nullptr, nullptr};
+        const int cap = count + m0;
         const int undec_cap = count;
         PSR_CUDA(ctx, cudaMalloc(&phi_l, sizeof(int32_t) * count));
-        PSR_CUDA(ctx, cudaMalloc(&rep_l, sizeof(int32_t) * count));
+        PSR_CUDA(ctx, cudaMalloc(&rep_l, sizeof(int32_t) * cap));
         PSR_CUDA(ctx, cudaMalloc(&undec, sizeof(int32_t) * undec_cap));
-        cudaError_t ea = cudaMalloc(&Binv, sizeof(double) * (size_t)count * p * p);
-        if (ea != cudaSuccess) { cudaGetLastError(); set_error(ctx, "out of device memory for the database"); return PSR_ERR_OOM; }
+        PSR_CUDA(ctx, cudaMalloc(&db.fro, sizeof(double) * cap));
+        if (cudaMalloc(&db.Binv, sizeof(double) * (size_t)cap * p * p) != cudaSuccess ||
+            cudaMalloc(&db.A, sizeof(double) * (size_t)cap * p * p) != cudaSuccess) {
+            cudaGetLastError();
+            set_error(ctx, "out of device memory for the database");
+            return PSR_ERR_OOM;
+        }
         PSR_CUDA(ctx, cudaMemsetAsync(phi_l, 0xff, sizeof(int32_t) * count, s));
         RoundDev init{};
         init.first_singular = -1;
+        init.m = m0;
         PSR_CUDA(ctx, cudaMemcpyAsync(st, &init, sizeof(RoundDev), cudaMemcpyHostToDevice, s));
         const int ld = p + 1;
         const size_t smem_begin = (size_t)((p * ld + p) * 8 + p * 4 + 16);
@@ -386,13 +464,53 @@ int run_alg1_rounds(psr_ctx* ctx, cudaStream_t s) {
         int eval_blocks = (count + wpb * 32 - 1) / (wpb * 32);
         if (eval_blocks > 152 * 2) eval_blocks = 152 * 2;
         if (eval_blocks < 1) eval_blocks = 1;
+        if (m0 > 0) {
+            // seed entries: copy, invert, norms
+            PSR_CUDA(ctx, cudaMemcpyAsync(db.A, seed_A, sizeof(double) * (size_t)m0 * p * p, cudaMemcpyDeviceToDevice, s));
+            int32_t* sflags = nullptr;
+            PSR_CUDA(ctx, cudaMalloc(&sflags, sizeof(int32_t) * m0));
+            rc = launch_batched_inverse(db.A, (int64_t)p * p, nullptr, m0, p, db.Binv, (int64_t)p * p, sflags, s);
+            if (rc != PSR_OK) break;
+            count_launch();
+            k_entry_fro<<<(m0 + 7) / 8, 256, 0, s>>>(db.Binv, m0, p, db.fro, sflags, sing_flag + 1);
+            std::vector<int32_t> seq(m0);
+            for (int j = 0; j < m0; ++j) seq[j] = -1;
+            PSR_CUDA(ctx, cudaMemcpyAsync(rep_l, seq.data(), sizeof(int32_t) * m0, cudaMemcpyHostToDevice, s));
+            int32_t h_bad = 0;
+            PSR_CUDA(ctx, cudaMemcpyAsync(&h_bad, sing_flag + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            PSR_CUDA(ctx, cudaStreamSynchronize(s));
+            cudaFree(sflags);
+            if (h_bad) { set_error(ctx, "a seed database entry is singular"); rc = PSR_ERR_SINGULAR_PATCH; break; }
+            if (hints) {
+                int32_t* hits = nullptr;
+                PSR_CUDA(ctx, cudaMalloc(&hits, sizeof(int32_t)));
+                PSR_CUDA(ctx, cudaMemsetAsync(hits, 0, sizeof(int32_t), s));
+                const size_t smem_h = (size_t)wpb * (3 * p * ld + 64) * 8;
+                if ((rc = set_smem((const void*)k_verify_hints, smem_h)) != PSR_OK) break;
+                const int hb = std::max(1, std::min((count + wpb - 1) / wpb, 152 * 8));
+                count_launch();
+                k_verify_hints<<<hb, wpb * 32, smem_h, s>>>(st, phi_l, count, Ag, p, db, m0, tol, hints, hits);
+                int32_t h_hits = 0;
+                PSR_CUDA(ctx, cudaMemcpyAsync(&h_hits, hits, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+                PSR_CUDA(ctx, cudaStreamSynchronize(s));
+                total_hits += h_hits;
+                cudaFree(hits);
+            }
+            // misses: first match over the seed entries, in creation order
+            for (int j = 0; j < m0; ++j) {
+                count_launch(); k_reset_undec<<<1, 1, 0, s>>>(st);
+                count_launch(); k_round_eval<<<eval_blocks, wpb * 32, smem_eval, s>>>(st, phi_l, count, Ag, p, db, tol, undec, undec_cap, j);
+                count_launch(); k_round_exact<<<64, wpb * 32, smem_eval, s>>>(st, phi_l, Ag, p, db, tol, undec, undec_cap, j);
+            }
+            PSR_CHECK_LAUNCH(ctx, "seeded Alg. 1 passes");
+        }
         int batch = 4;
         int issued = 0;
         for (;;) {
             for (int r = 0; r < batch; ++r) {
-                count_launch(); k_round_begin<<<1, 256, smem_begin, s>>>(st, phi_l, count, Ag, p, Binv, rep_l, sing_flag, 0);
-                count_launch(); k_round_eval<<<eval_blocks, wpb * 32, smem_eval, s>>>(st, phi_l, count, Ag, p, Binv, tol, undec, undec_cap);
-                count_launch(); k_round_exact<<<64, wpb * 32, smem_eval, s>>>(st, phi_l, Ag, p, Binv, tol, undec, undec_cap);
+                count_launch(); k_round_begin<<<1, 256, smem_begin, s>>>(st, phi_l, count, Ag, p, db, rep_l, sing_flag);
+                count_launch(); k_round_eval<<<eval_blocks, wpb * 32, smem_eval, s>>>(st, phi_l, count, Ag, p, db, tol, undec, undec_cap, -1);
+                count_launch(); k_round_exact<<<64, wpb * 32, smem_eval, s>>>(st, phi_l, Ag, p, db, tol, undec, undec_cap, -1);
             }
             PSR_CHECK_LAUNCH(ctx, "Alg. 1 round kernels");
             issued += batch;
@@ -407,28 +525,25 @@ int run_alg1_rounds(psr_ctx* ctx, cudaStream_t s) {
         G.m = h_st->m;
         total_evals += (int64_t)h_st->evals;
         total_exact += (int64_t)h_st->exact;
-        rounds_total += h_st->m;
-        if (h_st->first_singular >= 0 && first_singular < 0) first_singular = h_st->first_singular;
-        // global phi / rep ids: phi[global] = entry_base + phi_l[local]
-        std::vector<int32_t> hphi(count), hrep(G.m);
-        PSR_CUDA(ctx, cudaMemcpyAsync(hphi.data(), phi_l, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, s));
+        rounds_total += h_st->m - m0;
+        if (h_st->first_singular >= 0 && first_singular < 0) first_singular = G.h_gidx[h_st->first_singular];
+        std::vector<int32_t> hrep(G.m);
         PSR_CUDA(ctx, cudaMemcpyAsync(hrep.data(), rep_l, sizeof(int32_t) * G.m, cudaMemcpyDeviceToHost, s));
         PSR_CUDA(ctx, cudaStreamSynchronize(s));
-        G.h_rep.resize(G.m);
-        for (int j = 0; j < G.m; ++j) G.h_rep[j] = hrep[j];      // local patch index of entry j
-        // store the local assignment; the caller maps it to global ids
-        G.sphi = phi_l;             // temporary: local phi in original (unsorted) order
-        G.rinv = Binv;              // temporary: FP64 database, converted in build_sweep
+        G.h_rep.assign(hrep.begin(), hrep.end());   // local patch of each entry, -1 for seed entries
+        G.sphi = phi_l;             // local phi in original (unsorted) order
+        G.rinv = db.Binv;           // FP64 database, converted in the sweep builder
+        cudaFree(db.A);
+        cudaFree(db.fro);
         cudaFree(rep_l);
         cudaFree(undec);
-        (void)hphi;
-        entry_base += G.m;
     }
     cudaFree(st);
     cudaFreeHost(h_st);
     cudaFree(sing_flag);
     ctx->stats.criterion_evals = total_evals;
     ctx->stats.criterion_exact = total_exact;
+    ctx->stats.mlp_hits = total_hits;
     ctx->stats.rounds = rounds_total;
     ctx->stats.first_singular = first_singular;
     return rc;

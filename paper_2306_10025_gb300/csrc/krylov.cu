@@ -95,13 +95,19 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ rowptr
     const int sub = threadIdx.x % TPR;
     const int rows_per_block = blockDim.x / TPR;
     double acc = 0.0;
-    for (int row = blockIdx.x * rows_per_block + threadIdx.x / TPR; row < n; row += gridDim.x * rows_per_block) {
-        const int rs = rowptr[row], re = rowptr[row + 1];
+    // The loop bound is uniform across the warp (rows of one warp move
+    // together), so every lane reaches the width-TPR shuffles.
+    for (int base = blockIdx.x * rows_per_block; base < n; base += gridDim.x * rows_per_block) {
+        const int row = base + threadIdx.x / TPR;
+        const bool valid = row < n;
         double s = 0.0;
-        for (int e = rs + sub; e < re; e += TPR) s = fma(vals[e], x[colidx[e]], s);
+        if (valid) {
+            const int rs = rowptr[row], re = rowptr[row + 1];
+            for (int e = rs + sub; e < re; e += TPR) s = fma(vals[e], x[colidx[e]], s);
+        }
 #pragma unroll
         for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, TPR);
-        if (sub == 0) {
+        if (valid && sub == 0) {
             if (mode == 1) {
                 const double v = b[row] - s;
                 y[row] = v;

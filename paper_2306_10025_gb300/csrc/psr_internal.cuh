@@ -85,7 +85,8 @@ struct Group {
     int tile_patches = 32;         // chosen by the autotuner
     int warps = 4;
     bool tc = false;               // BF16 entries applied on the tensor cores
-    std::vector<int> h_rep;        // global entry ids of the group's entries
+    std::vector<int> h_rep;        // local patch of each entry (-1: seed entry)
+    std::vector<int32_t> h_gidx;   // global patch index of each local patch
 };
 
 struct KrylovWS {
@@ -164,7 +165,7 @@ int launch_batched_inverse(const double* A, int64_t stride_in, const int32_t* in
 
 // criterion.cu
 struct RoundState;
-int run_alg1_rounds(psr_ctx* ctx, cudaStream_t s);
+int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const int32_t* hints);
 int launch_criterion_batch(const double* A_i, int32_t batch, int32_t p, const double* A_c,
                            const double* Binv_c, double tol, int32_t* accept, double* dval,
                            int32_t* work, cudaStream_t s);

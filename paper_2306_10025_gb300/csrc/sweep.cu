@@ -315,7 +315,7 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<int32_t>& h_dofs,
             for (int a = 0; a < p; ++a) hd[(size_t)i * p + a] = h_dofs[off + a];
             phi_global[k] = entry_base + lphi[l];
         }
-        for (int j = 0; j < G.m; ++j) rep_global.push_back(gidx[g][G.h_rep[j]]);
+        for (int j = 0; j < G.m; ++j) rep_global.push_back(G.h_rep[j] >= 0 ? gidx[g][G.h_rep[j]] : -1);
         cudaFree(G.sphi);
         G.sphi = nullptr;
         PSR_CUDA(ctx, cudaMalloc(&G.patch, sizeof(int32_t) * count));
