@@ -28,7 +28,9 @@ SWEEP = {"auto": 0, "grouped": 1, "pergroup": 2}
 
 EXPORTS = ["psr_default_opts", "psr_setup", "psr_apply", "psr_solve", "psr_get_history",
            "psr_get_assignment", "psr_get_stats", "psr_last_error", "psr_destroy", "psr_extract",
-           "psr_batched_inverse", "psr_criterion", "psr_spectral_norm", "psr_kernel_launches"]
+           "psr_batched_inverse", "psr_criterion", "psr_spectral_norm", "psr_kernel_launches",
+           "psr_setup_seeded", "psr_features", "psr_mlp_create", "psr_mlp_num_params", "psr_mlp_set_params",
+           "psr_mlp_get_params", "psr_mlp_loss_grad", "psr_mlp_train_step", "psr_mlp_predict", "psr_mlp_destroy"]
 
 
 class PsrError(RuntimeError):
@@ -100,10 +102,25 @@ def load(path: str = LIB_PATH):
     lib.psr_criterion.argtypes = [vp, i32, i32, vp, vp, d, vp, vp, vp]
     lib.psr_spectral_norm.argtypes = [vp, i32, i32, vp, vp]
     lib.psr_kernel_launches.argtypes = []
+    lib.psr_setup_seeded.argtypes = [C.POINTER(psr_csr), C.POINTER(psr_patches), C.POINTER(psr_opts), vp, i32, vp,
+                                     vp, C.POINTER(vp)]
+    lib.psr_features.argtypes = [vp, i32, i32, vp, vp, vp]
+    lib.psr_mlp_create.argtypes = [i32, i32, i32, C.POINTER(vp)]
+    lib.psr_mlp_num_params.argtypes = [vp]
+    lib.psr_mlp_set_params.argtypes = [vp, vp, vp]
+    lib.psr_mlp_get_params.argtypes = [vp, vp, vp]
+    lib.psr_mlp_loss_grad.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+    lib.psr_mlp_train_step.argtypes = [vp, vp, vp, i32, C.c_float, vp, vp]
+    lib.psr_mlp_predict.argtypes = [vp, vp, i32, vp, vp, vp]
+    lib.psr_mlp_destroy.argtypes = [vp]
+    void_ret = ("psr_default_opts", "psr_last_error", "psr_destroy", "psr_kernel_launches", "psr_mlp_num_params",
+                "psr_mlp_destroy")
     for name in EXPORTS:
-        if name not in ("psr_default_opts", "psr_last_error", "psr_destroy", "psr_kernel_launches"):
+        if name not in void_ret:
             getattr(lib, name).restype = C.c_int
     lib.psr_kernel_launches.restype = C.c_int64
+    lib.psr_mlp_num_params.restype = C.c_int64
+    lib.psr_mlp_destroy.restype = None
     _lib = lib
     return lib
 
@@ -233,6 +250,83 @@ class Context:
         if self.h:
             load().psr_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def psr_setup_seeded(rowptr, colidx, vals, dofs, uniform_size, seed_A, hints=None, opts: psr_opts | None = None,
+                     stream=None) -> "Context":
+    """Alg. 1 started from the database seed_A (m0 x p x p, device FP64) with
+    optional per-patch hints (device int32, -1 = none)."""
+    import torch
+    lib = load()
+    A = _csr(rowptr, colidx, vals)
+    P = _patches(dofs, None, uniform_size)
+    _need(seed_A, torch.float64, "seed_A")
+    if hints is not None:
+        _need(hints, torch.int32, "hints")
+    o = opts if opts is not None else make_opts()
+    h = C.c_void_p()
+    rc = lib.psr_setup_seeded(C.byref(A), C.byref(P), C.byref(o), _ptr(seed_A), seed_A.shape[0], _ptr(hints),
+                              _stream(stream), C.byref(h))
+    _check(rc, None)
+    return Context(h, A.n, P.n_patches, o)
+
+
+def psr_features(A, coef, X, stream=None):
+    import torch
+    _need(A, torch.float64, "A")
+    _need(X, torch.float32, "X")
+    n, p, _ = A.shape
+    _check(load().psr_features(_ptr(A), n, p, _ptr(coef), _ptr(X), _stream(stream)))
+
+
+class MLP:
+    """Owns a psr_mlp (d -> h -> h -> m ReLU network, FP32 parameters)."""
+
+    def __init__(self, d, h, m):
+        self.d, self.h, self.m = d, h, m
+        self.ptr = C.c_void_p()
+        _check(load().psr_mlp_create(d, h, m, C.byref(self.ptr)))
+        self.num_params = int(load().psr_mlp_num_params(self.ptr))
+
+    def set_params(self, packed, stream=None):
+        import torch
+        _need(packed, torch.float32, "packed")
+        _check(load().psr_mlp_set_params(self.ptr, _ptr(packed), _stream(stream)))
+
+    def get_params(self, stream=None):
+        import torch
+        out = torch.empty(self.num_params, dtype=torch.float32, device="cuda")
+        _check(load().psr_mlp_get_params(self.ptr, _ptr(out), _stream(stream)))
+        return out
+
+    def loss_grad(self, X, y, stream=None):
+        import torch
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        g = torch.empty(self.num_params, dtype=torch.float32, device="cuda")
+        _check(load().psr_mlp_loss_grad(self.ptr, _ptr(X), _ptr(y), X.shape[0], _ptr(loss), _ptr(g), _stream(stream)))
+        return loss, g
+
+    def train_step(self, X, y, lr, loss=None, stream=None):
+        _check(load().psr_mlp_train_step(self.ptr, _ptr(X), _ptr(y), X.shape[0], float(lr), _ptr(loss),
+                                         _stream(stream)))
+
+    def predict(self, X, stream=None, logits=False):
+        import torch
+        cls = torch.empty(X.shape[0], dtype=torch.int32, device="cuda")
+        lg = torch.empty(X.shape[0], self.m, dtype=torch.float32, device="cuda") if logits else None
+        _check(load().psr_mlp_predict(self.ptr, _ptr(X), X.shape[0], _ptr(cls), _ptr(lg), _stream(stream)))
+        return (cls, lg) if logits else cls
+
+    def destroy(self):
+        if self.ptr:
+            load().psr_mlp_destroy(self.ptr)
+            self.ptr = None
 
     def __del__(self):
         try:
