@@ -263,6 +263,11 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
         }
         rc = krylov_alloc(ctx);
         if (rc != PSR_OK) goto fail;
+        t0 = std::chrono::steady_clock::now();
+        rc = autotune_sweep(ctx, s);
+        if (rc != PSR_OK) goto fail;
+        CK(cudaStreamSynchronize(s));
+        ctx->stats.t_autotune = seconds_since(t0);
         ctx->stats.n = n;
         ctx->stats.n_patches = np;
         ctx->stats.n_groups = (int)ctx->groups.size();

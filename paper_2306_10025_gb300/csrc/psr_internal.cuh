@@ -87,6 +87,7 @@ struct Group {
     bool tc = false;               // BF16 entries applied on the tensor cores
     std::vector<int> h_rep;        // local patch of each entry (-1: seed entry)
     std::vector<int32_t> h_gidx;   // global patch index of each local patch
+    std::vector<int32_t> h_sorted_phi;  // entry of each patch in sweep order
 };
 
 struct KrylovWS {
@@ -175,6 +176,8 @@ int launch_spectral_norm(const double* E, int32_t batch, int32_t p, double* sigm
 int build_sweep(psr_ctx* ctx, cudaStream_t s);
 int sweep_apply(psr_ctx* ctx, const double* r, double* z, cudaStream_t s);
 int autotune_sweep(psr_ctx* ctx, cudaStream_t s);
+int sweep_apply_ex(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s);
+int build_grouped_tables(psr_ctx* ctx);
 void free_sweep(psr_ctx* ctx);
 
 // sweep_tc.cu (BF16 entries on tcgen05 tensor cores)

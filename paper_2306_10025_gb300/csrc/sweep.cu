@@ -373,9 +373,9 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<int32_t>& h_dofs,
             PSR_CUDA(ctx, cudaStreamSynchronize(s));
             if (!in_place) cudaFree(db64);
         }
-        std::vector<int32_t> sorted_phi(hs);
+        G.h_sorted_phi = hs;
         int T = G.tc ? 128 : ((p <= 16) ? 64 : 32);
-        int rc = make_tiles(ctx, G, sorted_phi, T);
+        int rc = make_tiles(ctx, G, G.h_sorted_phi, T);
         if (rc != PSR_OK) return rc;
         index_bytes += (int64_t)count * p * 4 + (int64_t)count * 4;
         entry_base += G.m;
@@ -388,14 +388,26 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<int32_t>& h_dofs,
     ctx->stats.factor_bytes = factor_bytes;
     ctx->stats.index_bytes = index_bytes;
     ctx->stats.m_p = ctx->m_p;
-    // grouped persistent kernel tables
+    int rc = build_grouped_tables(ctx);
+    if (rc != PSR_OK) return rc;
+    PSR_CUDA(ctx, cudaMalloc(&ctx->gcounter, sizeof(int32_t) * 2));
+    PSR_CUDA(ctx, cudaMemset(ctx->gcounter, 0, sizeof(int32_t) * 2));
+    ctx->grouped_blocks = 152 * 2;
+    int mode = ctx->opts.sweep_kernel;
+    if (mode == PSR_SWEEP_AUTO) mode = (ctx->groups.size() > 1) ? PSR_SWEEP_GROUPED : PSR_SWEEP_PERGROUP;
+    ctx->sweep_mode = mode;
+    return PSR_OK;
+}
+
+// Tile table of the grouped persistent kernel: every group's tiles as
+// (group, entry, first, count), larger groups first (their heavier tiles are
+// dealt out early), plus one descriptor per group.
+int build_grouped_tables(psr_ctx* ctx) {
     std::vector<int32_t> gt;
     std::vector<GroupDesc> gd(ctx->groups.size());
-    int pmax = 0;
     for (size_t g = 0; g < ctx->groups.size(); ++g) {
         Group& G = ctx->groups[g];
         gd[g] = GroupDesc{G.sdofs, G.rinv, G.p, 0};
-        pmax = std::max(pmax, G.p);
         std::vector<int32_t> ht((size_t)G.ntiles * 3);
         PSR_CUDA(ctx, cudaMemcpy(ht.data(), G.tiles, sizeof(int32_t) * ht.size(), cudaMemcpyDeviceToHost));
         for (int t = 0; t < G.ntiles; ++t) {
@@ -405,18 +417,96 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<int32_t>& h_dofs,
             gt.push_back(ht[3 * t + 2]);
         }
     }
+    cudaFree(ctx->gtiles);
+    cudaFree(ctx->gdesc);
     ctx->gntiles = (int)(gt.size() / 4);
     PSR_CUDA(ctx, cudaMalloc(&ctx->gtiles, sizeof(int32_t) * std::max<size_t>(gt.size(), 4)));
     PSR_CUDA(ctx, cudaMemcpy(ctx->gtiles, gt.data(), sizeof(int32_t) * gt.size(), cudaMemcpyHostToDevice));
     PSR_CUDA(ctx, cudaMalloc(&ctx->gdesc, sizeof(GroupDesc) * std::max<size_t>(gd.size(), 1)));
     PSR_CUDA(ctx, cudaMemcpy(ctx->gdesc, gd.data(), sizeof(GroupDesc) * gd.size(), cudaMemcpyHostToDevice));
-    PSR_CUDA(ctx, cudaMalloc(&ctx->gcounter, sizeof(int32_t) * 2));
-    PSR_CUDA(ctx, cudaMemset(ctx->gcounter, 0, sizeof(int32_t) * 2));
-    ctx->grouped_blocks = 152 * 2;
-    int mode = ctx->opts.sweep_kernel;
-    if (mode == PSR_SWEEP_AUTO) mode = (ctx->groups.size() > 1) ? PSR_SWEEP_GROUPED : PSR_SWEEP_PERGROUP;
-    ctx->sweep_mode = mode;
     return PSR_OK;
+}
+
+// Project-written autotuner: times candidate tile shapes of the sweep on the
+// caller's stream (CUDA events, median of 5 after 2 warm-up launches) and
+// keeps the fastest.  Per size group for the per-group kernels (patches per
+// tile x warps per CTA); tiles per group x persistent grid size for the
+// grouped kernel.  Tensor-core tiles are fixed at 128 patches (M = 128).
+int autotune_sweep(psr_ctx* ctx, cudaStream_t s) {
+    if (!ctx->opts.autotune) return PSR_OK;
+    double* r = ctx->ws.r;
+    double* z = ctx->ws.z;
+    if (!r || !z) return PSR_OK;
+    PSR_CUDA(ctx, cudaMemsetAsync(r, 0, sizeof(double) * (size_t)ctx->n, s));
+    cudaEvent_t e0, e1;
+    PSR_CUDA(ctx, cudaEventCreate(&e0));
+    PSR_CUDA(ctx, cudaEventCreate(&e1));
+    auto time_apply = [&](float* out_ms) -> int {
+        for (int w = 0; w < 2; ++w) {
+            int rc = sweep_apply_ex(ctx, r, z, nullptr, s);
+            if (rc != PSR_OK) return rc;
+        }
+        std::vector<float> ts;
+        for (int it = 0; it < 5; ++it) {
+            cudaEventRecord(e0, s);
+            int rc = sweep_apply_ex(ctx, r, z, nullptr, s);
+            if (rc != PSR_OK) return rc;
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ts.push_back(ms);
+        }
+        std::sort(ts.begin(), ts.end());
+        *out_ms = ts[ts.size() / 2];
+        return PSR_OK;
+    };
+    int rc = PSR_OK;
+    if (ctx->sweep_mode == PSR_SWEEP_GROUPED && ctx->opts.store_prec != PSR_PREC_BF16) {
+        const int Ts[] = {16, 32, 64, 128};
+        const int Bs[] = {152 * 2, 152 * 4, 152 * 8};
+        float best = 1e30f;
+        int bT = 32, bB = 152 * 2;
+        for (int T : Ts) {
+            for (auto& G : ctx->groups)
+                if ((rc = make_tiles(ctx, G, G.h_sorted_phi, T)) != PSR_OK) break;
+            if (rc != PSR_OK || (rc = build_grouped_tables(ctx)) != PSR_OK) break;
+            for (int B : Bs) {
+                ctx->grouped_blocks = B;
+                float ms;
+                if ((rc = time_apply(&ms)) != PSR_OK) break;
+                if (ms < best) { best = ms; bT = T; bB = B; }
+            }
+            if (rc != PSR_OK) break;
+        }
+        if (rc == PSR_OK) {
+            for (auto& G : ctx->groups)
+                if ((rc = make_tiles(ctx, G, G.h_sorted_phi, bT)) != PSR_OK) break;
+            if (rc == PSR_OK) rc = build_grouped_tables(ctx);
+            ctx->grouped_blocks = bB;
+        }
+    } else {
+        for (auto& G : ctx->groups) {
+            if (G.tc || (G.m == G.count && G.p <= 32)) continue;   // fixed shapes
+            const int cand[][2] = {{16, 4}, {32, 4}, {64, 4}, {32, 8}, {64, 8}, {128, 8}};
+            float best = 1e30f;
+            int bT = G.tile_patches, bW = G.warps;
+            for (auto& c : cand) {
+                if ((rc = make_tiles(ctx, G, G.h_sorted_phi, c[0])) != PSR_OK) break;
+                G.warps = c[1];
+                float ms;
+                if ((rc = time_apply(&ms)) != PSR_OK) break;
+                if (ms < best) { best = ms; bT = c[0]; bW = c[1]; }
+            }
+            if (rc != PSR_OK) break;
+            G.warps = bW;
+            if ((rc = make_tiles(ctx, G, G.h_sorted_phi, bT)) != PSR_OK) break;
+        }
+        if (rc == PSR_OK) rc = build_grouped_tables(ctx);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
 }
 
 template <typename T>
