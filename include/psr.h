@@ -206,6 +206,26 @@ int psr_criterion(const double* A_i, int32_t batch, int32_t p, const double* A_c
                   const double* Binv_c, double tol, int32_t* accept, double* dval,
                   void* stream);
 
+/* The same decision as psr_criterion, for callers that cannot let the
+ * library allocate device memory (an application whose memory manager owns
+ * all device memory, or a pipeline that cannot afford the device-wide
+ * synchronisation an allocation may cause).  The paper has no counterpart;
+ * this is a deployment variant.  It calls no allocator: its scratch is a
+ * fixed device array of PSR_CRITERION_NOALLOC_MAX + 1 int32 (about 1 MiB)
+ * that every GPU loading the library holds until the process exits.
+ *   - batch > PSR_CRITERION_NOALLOC_MAX returns PSR_ERR_INVALID_ARG.
+ *   - The first call on a device looks up the array's device address (a
+ *     one-time set-up per device, done with that device current); make that
+ *     first call before any stream capture on the device.
+ *   - All calls share the array (it keeps the last call's contents; the
+ *     counter is cleared at the start of every call), so calls whose work
+ *     overlaps on the GPU race: order them on one stream or synchronise.
+ * Arguments, layout and results as psr_criterion. */
+#define PSR_CRITERION_NOALLOC_MAX 262144
+int psr_criterion_noalloc(const double* A_i, int32_t batch, int32_t p, const double* A_c,
+                          const double* Binv_c, double tol, int32_t* accept, double* dval,
+                          void* stream);
+
 /* sigma_max of each p x p matrix (device, row-major) by one-sided Jacobi in
  * FP64 (the "small SVD" of the section 3 remark).  1 <= p <= 32. */
 int psr_spectral_norm(const double* E, int32_t batch, int32_t p, double* sigma,

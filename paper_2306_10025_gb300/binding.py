@@ -30,7 +30,8 @@ EXPORTS = ["psr_default_opts", "psr_setup", "psr_apply", "psr_solve", "psr_get_h
            "psr_get_assignment", "psr_get_stats", "psr_last_error", "psr_destroy", "psr_extract",
            "psr_batched_inverse", "psr_criterion", "psr_spectral_norm", "psr_kernel_launches",
            "psr_setup_seeded", "psr_features", "psr_mlp_create", "psr_mlp_num_params", "psr_mlp_set_params",
-           "psr_mlp_get_params", "psr_mlp_loss_grad", "psr_mlp_train_step", "psr_mlp_predict", "psr_mlp_destroy"]
+           "psr_mlp_get_params", "psr_mlp_loss_grad", "psr_mlp_train_step", "psr_mlp_predict", "psr_mlp_destroy",
+           "psr_criterion_noalloc"]
 
 
 class PsrError(RuntimeError):
@@ -101,6 +102,7 @@ def load(path: str = LIB_PATH):
     lib.psr_batched_inverse.argtypes = [vp, i32, i32, vp, vp, vp]
     lib.psr_criterion.argtypes = [vp, i32, i32, vp, vp, d, vp, vp, vp]
     lib.psr_spectral_norm.argtypes = [vp, i32, i32, vp, vp]
+    lib.psr_criterion_noalloc.argtypes = [vp, i32, i32, vp, vp, d, vp, vp, vp]
     lib.psr_kernel_launches.argtypes = []
     lib.psr_setup_seeded.argtypes = [C.POINTER(psr_csr), C.POINTER(psr_patches), C.POINTER(psr_opts), vp, i32, vp,
                                      vp, C.POINTER(vp)]
@@ -356,6 +358,18 @@ def psr_criterion(A_i, A_c, Binv_c, tol, accept, dval=None, stream=None):
     b, p, _ = A_i.shape
     _check(load().psr_criterion(_ptr(A_i), b, p, _ptr(A_c), _ptr(Binv_c), float(tol), _ptr(accept),
                                 _ptr(dval), _stream(stream)))
+
+
+def psr_criterion_noalloc(A_i, A_c, Binv_c, tol, accept, dval=None, stream=None):
+    """psr_criterion without any device allocation: for callers whose memory
+    manager owns all device memory or who cannot afford an allocation's
+    implicit synchronisation.  Its scratch is a fixed array in the library
+    (batch <= PSR_CRITERION_NOALLOC_MAX); calls overlapping on the GPU race."""
+    import torch
+    _need(A_i, torch.float64, "A_i")
+    b, p, _ = A_i.shape
+    _check(load().psr_criterion_noalloc(_ptr(A_i), b, p, _ptr(A_c), _ptr(Binv_c), float(tol), _ptr(accept),
+                                        _ptr(dval), _stream(stream)))
 
 
 def psr_spectral_norm(E, sigma, stream=None):

@@ -647,3 +647,61 @@ int launch_spectral_norm(const double* E, int32_t batch, int32_t p, double* sigm
 }
 
 }  // namespace psr
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of psr_criterion.
+//
+// Some callers cannot let a library allocate device memory: an application
+// whose own memory manager has reserved (or must account for) all device
+// memory, or a latency-sensitive pipeline that cannot afford the implicit
+// device-wide synchronisation a cudaMalloc may cause.  psr_criterion_noalloc
+// serves them: its only scratch (the list of candidates whose bounds did not
+// decide, plus its counter) lives in the fixed array below, which every GPU
+// that loads this library holds until the process exits.
+// ---------------------------------------------------------------------------
+
+#include <mutex>
+
+static __device__ __align__(256) int32_t g_criterion_scratch[PSR_CRITERION_NOALLOC_MAX + 1];
+
+namespace {
+std::mutex g_scratch_mutex;
+void* g_scratch_addr[256] = {nullptr};   // device address of the array, per device ordinal
+}
+
+extern "C" int psr_criterion_noalloc(const double* A_i, int32_t batch, int32_t p, const double* A_c,
+                                     const double* Binv_c, double tol, int32_t* accept, double* dval,
+                                     void* stream) {
+    using namespace psr;
+    if (!A_i || !A_c || !Binv_c || !accept || batch < 0 || p < 1 || p > 32 || !(tol >= 0.0)) {
+        set_error(nullptr, "invalid criterion arguments");
+        return PSR_ERR_INVALID_ARG;
+    }
+    if (batch > PSR_CRITERION_NOALLOC_MAX) {
+        set_error(nullptr, "psr_criterion_noalloc: batch " + std::to_string(batch) +
+                               " exceeds its fixed scratch of " + std::to_string(PSR_CRITERION_NOALLOC_MAX) +
+                               " candidates; split the batch or call psr_criterion");
+        return PSR_ERR_INVALID_ARG;
+    }
+    if (batch == 0) return PSR_OK;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
+    if (dev < 0 || dev >= 256) { set_error(nullptr, "device ordinal out of range"); return PSR_ERR_INVALID_ARG; }
+    void* scratch = nullptr;
+    {
+        // One-time set-up per device, with that device current: the array's
+        // name is only a host-side stand-in, its device address must be asked for.
+        std::lock_guard<std::mutex> lock(g_scratch_mutex);
+        if (!g_scratch_addr[dev]) {
+            void* ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_criterion_scratch);
+            if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress(criterion scratch)");
+            g_scratch_addr[dev] = ptr;
+        }
+        scratch = g_scratch_addr[dev];
+    }
+    // launch_criterion_batch clears the counter (scratch[batch]) before use.
+    return launch_criterion_batch(A_i, batch, p, A_c, Binv_c, tol, accept, dval,
+                                  reinterpret_cast<int32_t*>(scratch), (cudaStream_t)stream);
+}
