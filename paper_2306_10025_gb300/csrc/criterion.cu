@@ -52,29 +52,37 @@ struct WarpScratch {  // per-warp shared memory layout for p <= 32
 };
 
 // Decides d(A_i, B_c) < tol for one candidate.  sAc, sB: shared p x ld.
+// probe (may be NULL): w = B_c^{-1} v / ||v|| for a unit-ish v, so that
+// ||D w|| = ||E v|| / ||v|| <= sigma_max(E) is an O(p^2) lower bound.
 // Returns 1 accept, 0 reject, -1 undecided (needs the exact path).  *dv gets
 // the deciding value.  All lanes call; lane r handles row r.
 __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, const double* sB,
                            int p, int ld, double binv_fro, double tol, WarpScratch ws, double* dv,
-                           bool allow_exact_here) {
+                           bool allow_exact_here, const double* probe = nullptr) {
     const int lane = threadIdx.x & 31;
     const bool act = lane < p;
-    // pass 1: D = A_c - A_i
-    double dn2 = 0.0, da2 = 0.0;
+    // pass 1: D = A_c - A_i, ||D||_F and (D w)_lane
+    double dn2 = 0.0, dw = 0.0;
     if (act) {
         for (int j = 0; j < p; ++j) {
             const double d = sAc[lane * ld + j] - Ai[lane * p + j];
             dn2 = fma(d, d, dn2);
+            if (probe) dw = fma(d, probe[j], dw);
         }
     }
     dn2 = warp_sum(dn2);
-    (void)da2;
     if (dn2 == 0.0) { *dv = 0.0; return 1; }
     const double dF = sqrt(dn2);
     const double err = 1.01 * (double)(p + 2) * U64 * dF * binv_fro;   // GEMM + norm rounding
+    const double shrink = 1.0 - 4.0 * (double)(p + 2) * U64;
     {
         const double ub0 = dF * binv_fro * (1.0 + 4.0 * (double)(p + 2) * U64);
         if (ub0 < tol) { *dv = ub0; return 1; }
+    }
+    if (probe) {
+        // w carries its own rounding (B^-1 v computed in FP64): widen by 2 err
+        const double lb1 = sqrt(warp_sum(dw * dw));
+        if (lb1 * shrink - 2.0 * err >= tol) { *dv = lb1; return 0; }
     }
     // pass 2: E row = D row * B^-1
     double e[32];
@@ -118,7 +126,6 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
         int oi = __shfl_xor_sync(0xffffffffu, br, o);
         if (ob > best || (ob == best && oi < br)) { best = ob; br = oi; }
     }
-    const double shrink = 1.0 - 4.0 * (double)(p + 2) * U64;
     double lb = best;
     if (lb * shrink - err >= tol) { *dv = lb; return 0; }
     if (!(best > 0.0)) { *dv = 0.0; return 1; }   // E == 0 after rounding
@@ -172,16 +179,51 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
 // ---------------------------------------------------------------- rounds
 __host__ __device__ inline size_t eval_smem_bytes(int p, int wpb) {
     const int ld = p + 1;
-    return (size_t)(2 * p * ld) * 8 + (size_t)wpb * ((size_t)p * ld + 64) * 8;
+    return (size_t)(2 * p * ld + 32) * 8 + (size_t)wpb * ((size_t)p * ld + 64) * 8;
 }
 
-// Entry database of one size group: patch matrices A_c, inverses B_c^{-1}
-// and ||B_c^{-1}||_F of every entry, in creation order.
+// Entry database of one size group: patch matrices A_c, inverses B_c^{-1},
+// ||B_c^{-1}||_F and the probe vector w_c (32 doubles) of every entry, in
+// creation order.
 struct EntryDB {
     double* A;
     double* Binv;
     double* fro;
+    double* w;
 };
+
+// Probe vector of an entry: v ~ the dominant right singular vector of B^{-1}
+// (power iteration on B^-T B^-1 from the all-ones vector), w = B^{-1} v / ||v||.
+// Any v gives a valid lower bound ||E v|| <= sigma_max(E); the dominant one
+// makes it tight where B^{-1} amplifies most.  One warp, p <= 32, B with row
+// stride ld (shared or global memory).
+__device__ void probe_vector_warp(const double* B, int p, int ld, double* w_out) {
+    const int lane = threadIdx.x & 31;
+    const bool act = lane < p;
+    double row[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) row[k] = (act && k < p) ? B[lane * ld + k] : 0.0;
+    double v = act ? 1.0 : 0.0;                        // lane k holds v_k
+    for (int it = 0; it < 24; ++it) {
+        double t = 0.0;                                // t_lane = (B v)_lane
+#pragma unroll
+        for (int k = 0; k < 32; ++k) t = fma(row[k], __shfl_sync(0xffffffffu, v, k), t);
+        double u = 0.0;                                // u_k = (B^T t)_k
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            const double c = warp_sum(row[k] * t);
+            if (lane == k) u = c;
+        }
+        const double nu = sqrt(warp_sum(u * u));
+        if (!(nu > 0.0)) break;
+        v = u / nu;
+    }
+    const double nv = sqrt(warp_sum(v * v));
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) t = fma(row[k], __shfl_sync(0xffffffffu, v, k), t);
+    w_out[lane] = (act && nv > 0.0) ? t / nv : 0.0;
+}
 
 // One CTA: next entry = smallest unassigned local patch at or after cursor;
 // warp 0 copies it into the database (slot m) and inverts it there.
@@ -229,6 +271,7 @@ __global__ void k_round_begin(RoundDev* st, int32_t* __restrict__ phi, int count
             fro = fma(v, v, fro);
         }
         fro = warp_sum(fro);
+        probe_vector_warp(S, p, ld, db.w + (int64_t)m * 32);
         if (tid == 0) {
             db.fro[m] = sqrt(fro);
             if (sing) {
@@ -244,17 +287,17 @@ __global__ void k_round_begin(RoundDev* st, int32_t* __restrict__ phi, int count
     }
 }
 
-__global__ void k_reset_undec(RoundDev* st) { st->n_undec = 0; }
-
 // ||B_j^{-1}||_F of every seed entry (one warp each); flags a singular seed.
 __global__ void k_entry_fro(const double* __restrict__ Binv, int m, int p, double* __restrict__ fro,
-                            const int32_t* __restrict__ sflags, int32_t* __restrict__ any_bad) {
+                            double* __restrict__ w, const int32_t* __restrict__ sflags,
+                            int32_t* __restrict__ any_bad) {
     const int lane = threadIdx.x & 31;
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (j >= m) return;
     double s = 0.0;
     for (int e = lane; e < p * p; e += 32) s = fma(Binv[(int64_t)j * p * p + e], Binv[(int64_t)j * p * p + e], s);
     s = warp_sum(s);
+    probe_vector_warp(Binv + (int64_t)j * p * p, p, p, w + (int64_t)j * 32);
     if (lane == 0) {
         fro[j] = sqrt(s);
         if (sflags[j]) atomicOr(any_bad, 1);
@@ -265,7 +308,7 @@ __global__ void k_entry_fro(const double* __restrict__ Binv, int m, int p, doubl
 // candidate index: all patches for a fixed entry, patches after the newest
 // entry's patch otherwise.
 __device__ __forceinline__ int stage_entry(const RoundDev* st, EntryDB db, int p, int fixed, double* sAc, double* sB,
-                                           int* entry, double* bfro) {
+                                           double* sw, int* entry, double* bfro) {
     const int ld = p + 1;
     const int e = (fixed >= 0) ? fixed : st->m - 1;
     const double* a = db.A + (int64_t)e * p * p;
@@ -274,16 +317,17 @@ __device__ __forceinline__ int stage_entry(const RoundDev* st, EntryDB db, int p
         sAc[(t / p) * ld + (t % p)] = a[t];
         sB[(t / p) * ld + (t % p)] = bm[t];
     }
+    if (threadIdx.x < 32) sw[threadIdx.x] = db.w[(int64_t)e * 32 + threadIdx.x];
     *entry = e;
     *bfro = db.fro[e];
     return (fixed >= 0) ? 0 : st->i0 + 1;
 }
 
 // Persistent warps over the candidate range: every unassigned patch is
-// compared with one entry.  Undecided candidates go to a list.
-__global__ void k_round_eval(RoundDev* st, int32_t* __restrict__ phi, int count,
-                             const double* __restrict__ Ag, int p, EntryDB db,
-                             double tol, int32_t* __restrict__ undec, int undec_cap, int fixed) {
+// compared with one entry, one candidate per warp at a time; the rare pairs
+// the bounds cannot decide take the exact path in place.
+__global__ void __launch_bounds__(256, 2) k_round_eval(RoundDev* st, int32_t* __restrict__ phi, int count,
+                             const double* __restrict__ Ag, int p, EntryDB db, double tol, int fixed) {
     extern __shared__ __align__(16) unsigned char smem[];
     if (st->done) return;
     const int ld = p + 1;
@@ -292,69 +336,30 @@ __global__ void k_round_eval(RoundDev* st, int32_t* __restrict__ phi, int count,
     const int wpb = blockDim.x >> 5;
     double* sAc = reinterpret_cast<double*>(smem);
     double* sB = sAc + p * ld;
-    double* wbase = sB + p * ld + (size_t)wid * (p * ld + 64);
+    double* sw = sB + p * ld;
+    double* wbase = sw + 32 + (size_t)wid * (p * ld + 64);
     WarpScratch ws{wbase, wbase + p * ld, wbase + p * ld + 32};
     int m;
     double bfro;
-    const int start = stage_entry(st, db, p, fixed, sAc, sB, &m, &bfro);
+    const int start = stage_entry(st, db, p, fixed, sAc, sB, sw, &m, &bfro);
     __syncthreads();
-    unsigned long long my_evals = 0;
-    const int gw = blockIdx.x * wpb + wid;
+    unsigned long long my_evals = 0, my_exact = 0;
     const int nw = gridDim.x * wpb;
-    for (int base = start + gw * 32; base < count; base += nw * 32) {
-        const int i = base + lane;
-        const bool open = (i < count) && (phi[i] == -1);
-        unsigned mask = __ballot_sync(0xffffffffu, open);
-        while (mask) {
-            const int b = __ffs(mask) - 1;
-            mask &= mask - 1;
-            const int cand = base + b;
-            double dv;
-            const int dec = decide_pair(Ag + (int64_t)cand * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, false);
-            ++my_evals;
-            if (lane == 0) {
-                if (dec == 1) phi[cand] = m;
-                else if (dec < 0) {
-                    const int slot = atomicAdd(&st->n_undec, 1);
-                    if (slot < undec_cap) undec[slot] = cand;
-                    else atomicExch(&st->undec_overflow, 1);
-                }
-            }
-            __syncwarp();
-        }
-    }
-    if (lane == 0 && my_evals) atomicAdd(&st->evals, my_evals);
-}
-
-// Exact path for the undecided candidates of this pass.
-__global__ void k_round_exact(RoundDev* st, int32_t* __restrict__ phi, const double* __restrict__ Ag,
-                              int p, EntryDB db, double tol, const int32_t* __restrict__ undec,
-                              int undec_cap, int fixed) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    if (st->done) return;
-    const int nund = min(st->n_undec, undec_cap);
-    if (nund == 0) return;
-    const int ld = p + 1;
-    const int lane = threadIdx.x & 31;
-    const int wid = threadIdx.x >> 5;
-    const int wpb = blockDim.x >> 5;
-    double* sAc = reinterpret_cast<double*>(smem);
-    double* sB = sAc + p * ld;
-    double* wbase = sB + p * ld + (size_t)wid * (p * ld + 64);
-    WarpScratch ws{wbase, wbase + p * ld, wbase + p * ld + 32};
-    int m;
-    double bfro;
-    stage_entry(st, db, p, fixed, sAc, sB, &m, &bfro);
-    __syncthreads();
-    for (int u = blockIdx.x * wpb + wid; u < nund; u += gridDim.x * wpb) {
-        const int cand = undec[u];
+    for (int cand = start + blockIdx.x * wpb + wid; cand < count; cand += nw) {
+        if (phi[cand] != -1) continue;                 // warp-uniform
         double dv;
-        const int dec = decide_pair(Ag + (int64_t)cand * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, true);
-        if (lane == 0) {
-            if (dec == 1) phi[cand] = m;
-            atomicAdd(&st->exact, 1ull);
+        int dec = decide_pair(Ag + (int64_t)cand * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, false, sw);
+        if (dec < 0) {
+            dec = decide_pair(Ag + (int64_t)cand * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, true, sw);
+            ++my_exact;
         }
+        ++my_evals;
+        if (lane == 0 && dec == 1) phi[cand] = m;
         __syncwarp();
+    }
+    if (lane == 0) {
+        if (my_evals) atomicAdd(&st->evals, my_evals);
+        if (my_exact) atomicAdd(&st->exact, my_exact);
     }
 }
 
@@ -385,9 +390,10 @@ __global__ void k_verify_hints(RoundDev* st, int32_t* __restrict__ phi, int coun
         }
         __syncwarp();
         double dv;
-        int dec = decide_pair(Ag + (int64_t)i * p * p, sAc, sB, p, ld, db.fro[e], tol, ws, &dv, false);
+        const double* pw = db.w + (int64_t)e * 32;
+        int dec = decide_pair(Ag + (int64_t)i * p * p, sAc, sB, p, ld, db.fro[e], tol, ws, &dv, false, pw);
         if (dec < 0) {
-            dec = decide_pair(Ag + (int64_t)i * p * p, sAc, sB, p, ld, db.fro[e], tol, ws, &dv, true);
+            dec = decide_pair(Ag + (int64_t)i * p * p, sAc, sB, p, ld, db.fro[e], tol, ws, &dv, true, pw);
             ++ex;
         }
         ++ev;
@@ -435,14 +441,12 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         const double* Ag = ctx->A_ext + G.mat_off;
         int32_t* phi_l = nullptr;
         int32_t* rep_l = nullptr;
-        int32_t* undec = nullptr;
-        EntryDB db{nullptr, nullptr, nullptr};
+        EntryDB db{nullptr, nullptr, nullptr, nullptr};
         const int cap = count + m0;
-        const int undec_cap = count;
         PSR_CUDA(ctx, cudaMalloc(&phi_l, sizeof(int32_t) * count));
         PSR_CUDA(ctx, cudaMalloc(&rep_l, sizeof(int32_t) * cap));
-        PSR_CUDA(ctx, cudaMalloc(&undec, sizeof(int32_t) * undec_cap));
         PSR_CUDA(ctx, cudaMalloc(&db.fro, sizeof(double) * cap));
+        PSR_CUDA(ctx, cudaMalloc(&db.w, sizeof(double) * (size_t)cap * 32));
         if (cudaMalloc(&db.Binv, sizeof(double) * (size_t)cap * p * p) != cudaSuccess ||
             cudaMalloc(&db.A, sizeof(double) * (size_t)cap * p * p) != cudaSuccess) {
             cudaGetLastError();
@@ -460,9 +464,9 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         const size_t smem_eval = eval_smem_bytes(p, wpb);
         if ((rc = set_smem((const void*)k_round_begin, smem_begin)) != PSR_OK) break;
         if ((rc = set_smem((const void*)k_round_eval, smem_eval)) != PSR_OK) break;
-        if ((rc = set_smem((const void*)k_round_exact, smem_eval)) != PSR_OK) break;
-        int eval_blocks = (count + wpb * 32 - 1) / (wpb * 32);
-        if (eval_blocks > 152 * 2) eval_blocks = 152 * 2;
+        // one warp per candidate: enough warps for every SM, a few candidates each
+        int eval_blocks = (count + wpb - 1) / wpb;
+        if (eval_blocks > 152 * 4) eval_blocks = 152 * 4;
         if (eval_blocks < 1) eval_blocks = 1;
         if (m0 > 0) {
             // seed entries: copy, invert, norms
@@ -472,7 +476,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
             rc = launch_batched_inverse(db.A, (int64_t)p * p, nullptr, m0, p, db.Binv, (int64_t)p * p, sflags, s);
             if (rc != PSR_OK) break;
             count_launch();
-            k_entry_fro<<<(m0 + 7) / 8, 256, 0, s>>>(db.Binv, m0, p, db.fro, sflags, sing_flag + 1);
+            k_entry_fro<<<(m0 + 7) / 8, 256, 0, s>>>(db.Binv, m0, p, db.fro, db.w, sflags, sing_flag + 1);
             std::vector<int32_t> seq(m0);
             for (int j = 0; j < m0; ++j) seq[j] = -1;
             PSR_CUDA(ctx, cudaMemcpyAsync(rep_l, seq.data(), sizeof(int32_t) * m0, cudaMemcpyHostToDevice, s));
@@ -498,9 +502,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
             }
             // misses: first match over the seed entries, in creation order
             for (int j = 0; j < m0; ++j) {
-                count_launch(); k_reset_undec<<<1, 1, 0, s>>>(st);
-                count_launch(); k_round_eval<<<eval_blocks, wpb * 32, smem_eval, s>>>(st, phi_l, count, Ag, p, db, tol, undec, undec_cap, j);
-                count_launch(); k_round_exact<<<64, wpb * 32, smem_eval, s>>>(st, phi_l, Ag, p, db, tol, undec, undec_cap, j);
+                count_launch(); k_round_eval<<<eval_blocks, wpb * 32, smem_eval, s>>>(st, phi_l, count, Ag, p, db, tol, j);
             }
             PSR_CHECK_LAUNCH(ctx, "seeded Alg. 1 passes");
         }
@@ -509,8 +511,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         for (;;) {
             for (int r = 0; r < batch; ++r) {
                 count_launch(); k_round_begin<<<1, 256, smem_begin, s>>>(st, phi_l, count, Ag, p, db, rep_l, sing_flag);
-                count_launch(); k_round_eval<<<eval_blocks, wpb * 32, smem_eval, s>>>(st, phi_l, count, Ag, p, db, tol, undec, undec_cap, -1);
-                count_launch(); k_round_exact<<<64, wpb * 32, smem_eval, s>>>(st, phi_l, Ag, p, db, tol, undec, undec_cap, -1);
+                count_launch(); k_round_eval<<<eval_blocks, wpb * 32, smem_eval, s>>>(st, phi_l, count, Ag, p, db, tol, -1);
             }
             PSR_CHECK_LAUNCH(ctx, "Alg. 1 round kernels");
             issued += batch;
@@ -535,8 +536,8 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         G.rinv = db.Binv;           // FP64 database, converted in the sweep builder
         cudaFree(db.A);
         cudaFree(db.fro);
+        cudaFree(db.w);
         cudaFree(rep_l);
-        cudaFree(undec);
     }
     cudaFree(st);
     cudaFreeHost(h_st);

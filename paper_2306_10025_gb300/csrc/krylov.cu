@@ -260,13 +260,21 @@ __global__ void __launch_bounds__(256) k_mdot(const double* __restrict__ V, cons
             if (i < nv) acc[i] = fma(V[(int64_t)i * n + e], we, acc[i]);
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // Reduce the 32 accumulators across the warp by recursive halving: at
+    // each step a lane keeps the half of the vector indices selected by one
+    // of its lane bits and adds its partner's copy of that half, so after 31
+    // shuffles lane L holds the warp total of vector L.
 #pragma unroll
-    for (int i = 0; i < 32; ++i) {
-        if (i < nv) {
-            const double t = warp_sum(acc[i]);
-            if (lane == 0) sh[i][wid] = t;
+    for (int h = 16; h >= 1; h >>= 1) {
+        const bool upper = (lane & h) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const double send = upper ? acc[i] : acc[i + h];
+            const double keep = upper ? acc[i + h] : acc[i];
+            acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
         }
     }
+    sh[lane][wid] = acc[0];
     __syncthreads();
     if (threadIdx.x < nv) {
         double t = 0.0;

@@ -488,7 +488,7 @@ int autotune_sweep(psr_ctx* ctx, cudaStream_t s) {
     } else {
         for (auto& G : ctx->groups) {
             if (G.tc || (G.m == G.count && G.p <= 32)) continue;   // fixed shapes
-            const int cand[][2] = {{16, 4}, {32, 4}, {64, 4}, {32, 8}, {64, 8}, {128, 8}};
+            const int cand[][2] = {{8, 8}, {16, 8}, {16, 4}, {32, 4}, {64, 4}, {32, 8}, {64, 8}, {128, 8}};
             float best = 1e30f;
             int bT = G.tile_patches, bW = G.warps;
             for (auto& c : cand) {
