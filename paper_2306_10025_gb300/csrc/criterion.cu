@@ -200,19 +200,20 @@ struct EntryDB {
 __device__ void probe_vector_warp(const double* B, int p, int ld, double* w_out) {
     const int lane = threadIdx.x & 31;
     const bool act = lane < p;
+    // lane r keeps row r of B; column sums read B directly (row stride ld), so
+    // each product is p fused multiply-adds per lane and no warp reductions
     double row[32];
 #pragma unroll
     for (int k = 0; k < 32; ++k) row[k] = (act && k < p) ? B[lane * ld + k] : 0.0;
     double v = act ? 1.0 : 0.0;                        // lane k holds v_k
-    for (int it = 0; it < 24; ++it) {
+    for (int it = 0; it < 10; ++it) {
         double t = 0.0;                                // t_lane = (B v)_lane
 #pragma unroll
         for (int k = 0; k < 32; ++k) t = fma(row[k], __shfl_sync(0xffffffffu, v, k), t);
-        double u = 0.0;                                // u_k = (B^T t)_k
-#pragma unroll
-        for (int k = 0; k < 32; ++k) {
-            const double c = warp_sum(row[k] * t);
-            if (lane == k) u = c;
+        double u = 0.0;                                // u_lane = (B^T t)_lane
+        for (int r = 0; r < p; ++r) {
+            const double tr = __shfl_sync(0xffffffffu, t, r);
+            if (act) u = fma(B[r * ld + lane], tr, u);
         }
         const double nu = sqrt(warp_sum(u * u));
         if (!(nu > 0.0)) break;

@@ -73,14 +73,12 @@ __device__ __forceinline__ bool last_block(int32_t* cnt) {
     return s_last != 0;
 }
 
-// Sum of nb partials in a fixed order by warp 0; valid in thread 0.
+// Sum of nb partials in a fixed order by the whole block; valid in thread 0.
 __device__ __forceinline__ double sum_partials(const double* part, int nb) {
+    __shared__ double sp[32];
     double v = 0.0;
-    if (threadIdx.x < 32) {
-        for (int b = threadIdx.x; b < nb; b += 32) v += part[b];
-        v = warp_sum(v);
-    }
-    return v;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[b];
+    return block_sum(v, sp);
 }
 
 // ---------------------------------------------------------------- SpMV
@@ -282,19 +280,20 @@ __global__ void __launch_bounds__(256) k_mdot(const double* __restrict__ V, cons
         kd.part[threadIdx.x * gridDim.x + blockIdx.x] = t;
     }
     if (!last_block(kd.ictl + I_CNT + 4)) return;
-    // warp wv sums vector i = wv, wv + nwarps, ... over blocks
+    // 8 threads per vector (256 threads, <= 32 vectors), fixed order
     const int m = kd.m;
     double* H = Hm(kd.scal, m);
     double* hv = Hv(kd.scal, m);
-    for (int i = wid; i < nv; i += (int)(blockDim.x >> 5)) {
-        double v = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += 32) v += kd.part[i * gridDim.x + b];
-        v = warp_sum(v);
-        if (lane == 0) {
-            hv[i] = v;
-            if (pass == 0) H[i * m + j] = v;
-            else H[i * m + j] += v;
-        }
+    const int i = threadIdx.x >> 3, q = threadIdx.x & 7;
+    double v = 0.0;
+    if (i < nv)
+        for (int b = q; b < (int)gridDim.x; b += 8) v += kd.part[i * gridDim.x + b];
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, 8);
+    if (i < nv && q == 0) {
+        hv[i] = v;
+        if (pass == 0) H[i * m + j] = v;
+        else H[i * m + j] += v;
     }
 }
 
@@ -312,7 +311,12 @@ __global__ void __launch_bounds__(256) k_maxpy(const double* __restrict__ V, dou
     double acc = 0.0;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         double we = w[e];
-        for (int i = 0; i < nv; ++i) we = fma(-sh_h[i], V[(int64_t)i * n + e], we);
+        double vi[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) vi[i] = (i < nv) ? V[(int64_t)i * n + e] : 0.0;
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            if (i < nv) we = fma(-sh_h[i], vi[i], we);
         w[e] = we;
         acc = fma(we, we, acc);
     }
@@ -400,9 +404,12 @@ static int spmv_tpr(psr_ctx* ctx) {
 }
 
 static void launch_spmv(psr_ctx* ctx, const double* x, double* y, const double* b, int mode, int fin,
-                        KDims kd, int stop_check, int nb, cudaStream_t s) {
+                        KDims kd, int stop_check, int nb_max, cudaStream_t s) {
     const int tpr = spmv_tpr(ctx);
     const int n = ctx->n;
+    // one row per TPR-thread group, all rows in one pass when the partials fit
+    const int rows_per_block = 256 / tpr;
+    const int nb = (int)std::max(1, std::min((n + rows_per_block - 1) / rows_per_block, nb_max));
     switch (tpr) {
         case 4: count_launch(); k_spmv<4><<<nb, 256, 0, s>>>(ctx->rowptr, ctx->colidx, ctx->vals, x, y, b, n, mode, kd, stop_check, fin); break;
         case 8: count_launch(); k_spmv<8><<<nb, 256, 0, s>>>(ctx->rowptr, ctx->colidx, ctx->vals, x, y, b, n, mode, kd, stop_check, fin); break;
@@ -418,7 +425,7 @@ int krylov_alloc(psr_ctx* ctx) {
     if (m < 1) m = 1;
     if (m > 32) m = 32;
     ctx->opts.restart = m;
-    w.nblk = (int)std::min<size_t>(std::max<size_t>((n + 255) / 256, 1), 152 * 4);
+    w.nblk = (int)std::min<size_t>(std::max<size_t>((n + 255) / 256, 1), 152 * 16);
     PSR_CUDA(ctx, cudaMalloc(&w.x, n * 8));
     PSR_CUDA(ctx, cudaMalloc(&w.b, n * 8));
     PSR_CUDA(ctx, cudaMalloc(&w.r, n * 8));
@@ -430,7 +437,8 @@ int krylov_alloc(psr_ctx* ctx) {
         PSR_CUDA(ctx, cudaMalloc(&w.V, (size_t)(m + 1) * n * 8));
         PSR_CUDA(ctx, cudaMalloc(&w.Z, (size_t)m * n * 8));
     }
-    PSR_CUDA(ctx, cudaMalloc(&w.partial, (size_t)w.nblk * 34 * 8));
+    w.nspmv = 152 * 32;                     // partial slots available to the SpMV reductions
+    PSR_CUDA(ctx, cudaMalloc(&w.partial, (size_t)std::max(w.nblk * 34, w.nspmv) * 8));
     PSR_CUDA(ctx, cudaMalloc(&w.scal, (size_t)scal_count(m) * 8));
     PSR_CUDA(ctx, cudaMemset(w.scal, 0, (size_t)scal_count(m) * 8));
     PSR_CUDA(ctx, cudaMalloc(&w.hist, (size_t)(ctx->opts.maxit + 2) * 8));
@@ -453,7 +461,7 @@ static int enqueue_cg_block(psr_ctx* ctx, KDims kd, int iters, cudaStream_t s) {
     KrylovWS& w = ctx->ws;
     const int n = ctx->n, nb = w.nblk;
     for (int t = 0; t < iters; ++t) {
-        launch_spmv(ctx, w.p, w.q, nullptr, 2, 1, kd, 1, nb, s);
+        launch_spmv(ctx, w.p, w.q, nullptr, 2, 1, kd, 1, w.nspmv, s);
         count_launch(); k_cg_xr<<<nb, 256, 0, s>>>(w.x, w.r, w.p, w.q, n, kd);
         int rc = sweep_apply_ex(ctx, w.r, w.z, kd.ictl + I_STOP, s);
         if (rc != PSR_OK) return rc;
@@ -474,7 +482,7 @@ static int enqueue_fg_cycle(psr_ctx* ctx, KDims kd, cudaStream_t s) {
         double* Zj = w.Z + (size_t)j * n;
         int rc = sweep_apply_ex(ctx, Vj, Zj, kd.ictl + I_STOP, s);
         if (rc != PSR_OK) return rc;
-        launch_spmv(ctx, Zj, Vn, nullptr, 0, 0, kd, 1, nb, s);
+        launch_spmv(ctx, Zj, Vn, nullptr, 0, 0, kd, 1, w.nspmv, s);
         count_launch(); k_mdot<<<nb, 256, 0, s>>>(w.V, Vn, n, j, kd, 0);
         count_launch(); k_maxpy<<<nb, 256, 0, s>>>(w.V, Vn, n, j, kd, 0);
         count_launch(); k_mdot<<<nb, 256, 0, s>>>(w.V, Vn, n, j, kd, 1);
@@ -484,7 +492,7 @@ static int enqueue_fg_cycle(psr_ctx* ctx, KDims kd, cudaStream_t s) {
     count_launch(); k_fg_solve<<<1, 32, 0, s>>>(kd);
     count_launch(); k_fg_update<<<nb, 256, 0, s>>>(w.x, w.Z, n, kd);
     // restart residual r = b - A x (skipped once stopped)
-    launch_spmv(ctx, w.x, w.r, w.b, 1, 2, kd, 1, nb, s);
+    launch_spmv(ctx, w.x, w.r, w.b, 1, 2, kd, 1, w.nspmv, s);
     PSR_CHECK_LAUNCH(ctx, "FGMRES cycle");
     return PSR_OK;
 }

@@ -85,6 +85,10 @@ struct Group {
     int tile_patches = 32;         // chosen by the autotuner
     int warps = 4;
     bool tc = false;               // BF16 entries applied on the tensor cores
+    bool tpp = false;              // clustered p <= 32: one patch per thread
+    int32_t* sdofs_t = nullptr;    // [p * count] DOFs, local-DOF major (tpp kernel)
+    int32_t* wtiles = nullptr;     // [nwt * 3] warp tiles (entry, first, count <= 32)
+    int nwt = 0;
     std::vector<int> h_rep;        // local patch of each entry (-1: seed entry)
     std::vector<int32_t> h_gidx;   // global patch index of each local patch
     std::vector<int32_t> h_sorted_phi;  // entry of each patch in sweep order
@@ -104,6 +108,7 @@ struct KrylovWS {
     double* hist = nullptr;     // [maxit + 1]
     int32_t* ictl = nullptr;    // device control ints
     int nblk = 0;
+    int nspmv = 0;
 };
 
 }  // namespace psr

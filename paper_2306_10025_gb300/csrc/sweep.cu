@@ -133,6 +133,53 @@ __global__ void __launch_bounds__(256) k_sweep_half(const int32_t* __restrict__ 
     }
 }
 
+// Clustered, p <= 32: one patch per THREAD.  A warp tile is up to 32
+// consecutive sorted patches that share one entry, so every lane reads the
+// same inverse element at the same time (one broadcast load from L1); each
+// lane keeps its patch's p residual values in registers, which puts p
+// independent gathers in flight per thread.  DOFs come from the transposed
+// map (local DOF major), so lane k's load of DOF a is coalesced across the warp.
+template <typename T, int PM>
+__global__ void __launch_bounds__(256) k_sweep_tpp(const int32_t* __restrict__ wtiles, int nwt, int p, int count,
+                                                   const T* __restrict__ rinv, const int32_t* __restrict__ sdofs_t,
+                                                   const double* __restrict__ r, const double* __restrict__ wg,
+                                                   const double* __restrict__ wsc, double* __restrict__ z,
+                                                   const int32_t* __restrict__ stop) {
+    using C = typename Comp<T>::type;
+    if (stop && *stop) return;
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nwt; t += nw) {
+        const int c = wtiles[3 * t], start = wtiles[3 * t + 1], cnt = wtiles[3 * t + 2];
+        const bool live = lane < cnt;
+        const int k = start + lane;
+        int dof[PM];
+        C x[PM];
+#pragma unroll
+        for (int a = 0; a < PM; ++a) {
+            dof[a] = 0;
+            x[a] = (C)0;
+            if (live && a < p) {
+                dof[a] = sdofs_t[(int64_t)a * count + k];
+                double v = r[dof[a]];
+                if (wg) v *= wg[dof[a]];
+                x[a] = (C)v;
+            }
+        }
+        const T* B = rinv + (int64_t)c * p * p;
+#pragma unroll
+        for (int a = 0; a < PM; ++a) {
+            if (a >= p) break;
+            C y = (C)0;
+            const T* row = B + a * p;
+#pragma unroll
+            for (int b = 0; b < PM; ++b)
+                if (b < p) y = fma((C)__ldg(row + b), x[b], y);
+            if (live) atomicAdd(&z[dof[a]], (double)y * wsc[dof[a]]);
+        }
+    }
+}
+
 // Full storage (every patch its own inverse, Eq. 1), p <= 32: one patch per
 // warp; the warp streams its inverse into its own shared-memory slot with
 // coalesced loads, then lane a forms row a of B^-1 r_k.
@@ -374,6 +421,28 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<int32_t>& h_dofs,
             if (!in_place) cudaFree(db64);
         }
         G.h_sorted_phi = hs;
+        if (!G.tc && G.m < G.count && p <= 32) {
+            std::vector<int32_t> ht((size_t)count * p), wt;
+            for (int i = 0; i < count; ++i)
+                for (int a = 0; a < p; ++a) ht[(size_t)a * count + i] = hd[(size_t)i * p + a];
+            PSR_CUDA(ctx, cudaMalloc(&G.sdofs_t, sizeof(int32_t) * (size_t)count * p));
+            PSR_CUDA(ctx, cudaMemcpy(G.sdofs_t, ht.data(), sizeof(int32_t) * ht.size(), cudaMemcpyHostToDevice));
+            int i = 0;
+            while (i < count) {
+                int j = i;
+                while (j < count && hs[j] == hs[i]) ++j;
+                for (int s0 = i; s0 < j; s0 += 32) {
+                    wt.push_back(hs[i]);
+                    wt.push_back(s0);
+                    wt.push_back(std::min(32, j - s0));
+                }
+                i = j;
+            }
+            G.nwt = (int)(wt.size() / 3);
+            PSR_CUDA(ctx, cudaMalloc(&G.wtiles, sizeof(int32_t) * wt.size()));
+            PSR_CUDA(ctx, cudaMemcpy(G.wtiles, wt.data(), sizeof(int32_t) * wt.size(), cudaMemcpyHostToDevice));
+            G.tpp = true;
+        }
         int T = G.tc ? 128 : ((p <= 16) ? 64 : 32);
         int rc = make_tiles(ctx, G, G.h_sorted_phi, T);
         if (rc != PSR_OK) return rc;
@@ -491,15 +560,25 @@ int autotune_sweep(psr_ctx* ctx, cudaStream_t s) {
             const int cand[][2] = {{8, 8}, {16, 8}, {16, 4}, {32, 4}, {64, 4}, {32, 8}, {64, 8}, {128, 8}};
             float best = 1e30f;
             int bT = G.tile_patches, bW = G.warps;
+            const bool has_tpp = G.tpp;
+            bool b_tpp = false;
+            if (has_tpp) {
+                float ms;
+                if ((rc = time_apply(&ms)) != PSR_OK) break;
+                best = ms;
+                b_tpp = true;
+                G.tpp = false;
+            }
             for (auto& c : cand) {
                 if ((rc = make_tiles(ctx, G, G.h_sorted_phi, c[0])) != PSR_OK) break;
                 G.warps = c[1];
                 float ms;
                 if ((rc = time_apply(&ms)) != PSR_OK) break;
-                if (ms < best) { best = ms; bT = c[0]; bW = c[1]; }
+                if (ms < best) { best = ms; bT = c[0]; bW = c[1]; b_tpp = false; }
             }
             if (rc != PSR_OK) break;
             G.warps = bW;
+            G.tpp = b_tpp;
             if ((rc = make_tiles(ctx, G, G.h_sorted_phi, bT)) != PSR_OK) break;
         }
         if (rc == PSR_OK) rc = build_grouped_tables(ctx);
@@ -523,6 +602,16 @@ static int launch_group(psr_ctx* ctx, const Group& G, const double* r, double* z
                                  r, ctx->Wg, ctx->W, z, stop, ctx->status, s);
         if (rc != PSR_OK) set_error(ctx, "tensor-core sweep launch failed");
         return rc;
+    }
+    if (G.tpp) {
+        const int tb = std::max(1, std::min((G.nwt + 7) / 8, 152 * 16));
+        if (G.p <= 16) {
+            count_launch(); k_sweep_tpp<T, 16><<<tb, 256, 0, s>>>(G.wtiles, G.nwt, G.p, G.count, rinv, G.sdofs_t, r, ctx->Wg, ctx->W, z, stop);
+        } else {
+            count_launch(); k_sweep_tpp<T, 32><<<tb, 256, 0, s>>>(G.wtiles, G.nwt, G.p, G.count, rinv, G.sdofs_t, r, ctx->Wg, ctx->W, z, stop);
+        }
+        PSR_CHECK_LAUNCH(ctx, "sweep kernel (thread per patch)");
+        return PSR_OK;
     }
     if (G.m == G.count && G.p <= 32) {
         const int wpb = 8;
@@ -595,6 +684,8 @@ void free_sweep(psr_ctx* ctx) {
         cudaFree(G.sdofs);
         cudaFree(G.sphi);
         cudaFree(G.tiles);
+        cudaFree(G.sdofs_t);
+        cudaFree(G.wtiles);
         if (G.rinv && !(ctx->A_ext && reinterpret_cast<double*>(G.rinv) >= ctx->A_ext &&
                          reinterpret_cast<double*>(G.rinv) < ctx->A_ext + ctx->A_ext_len))
             cudaFree(G.rinv);
