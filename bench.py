@@ -62,6 +62,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--apply-reps", type=int, default=200)
+    ap.add_argument("--mlp", action="store_true", help="learned-assignment gain on the 3D lognormal workload")
+    ap.add_argument("--mlp-n", type=int, default=32)
+    ap.add_argument("--mlp-epochs", type=int, default=300)
+    ap.add_argument("--mlp-lr", type=float, default=1e-3)
     return ap.parse_args()
 
 
@@ -125,6 +129,22 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ replicas
+def aggregate_replicas(seconds: float, units: float, device=None):
+    """Whole-job throughput of independent replicas (one per rank, no
+    collective on the data path): the units every rank processed, divided
+    by the slowest rank's time.  Returns (value, max_seconds, total_units)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return units / seconds, seconds, units
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return u.item() / t.item(), t.item(), u.item()
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -191,15 +211,9 @@ def run_gpu(args, cfg, ws, rank, local):
     launches = L.psr_kernel_launches() - launches0
     clocks = clk.stop()
     step_s = sum(times) / len(times)
-    if ws > 1:
-        tt = torch.tensor([sum(times)], dtype=torch.float64, device=devc)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_s = tt.item()
-    else:
-        total_s = sum(times)
     iters = infos[-1]["iterations"]
-    units_per_rank = pr.n * iters * args.steps
-    value = units_per_rank * ws / total_s
+    units_local = pr.n * sum(i["iterations"] for i in infos)
+    value, total_s, _ = aggregate_replicas(sum(times), units_local, devc)
 
     # kernel-level: sweep (apply) timing with CUDA events over many launches
     last = ctx
@@ -355,8 +369,85 @@ def run_reference(args, cfg, ws, rank):
             "e2e": {"value": v, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ------------------------------------------------------------------ learned assignment
+def run_mlp_gain(args):
+    """What the learned assignment gains on the 3D lognormal Q2 workload:
+    Alg. 1 on the first half of the patches (in patch order) gives the
+    database and the training labels; an MLP (731 -> 256 -> 256 -> m, trained
+    on the GPU) predicts the entry of every patch; Alg. 1 then runs on all
+    patches from that database without and with the verified predictions."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2306_10025_gb300 as L
+    import problems
+    dev = torch.device("cuda", 0)
+    N = args.mlp_n
+    pr = problems.diffusion3d_q2(N=N, seed=0)
+    tol = 0.1 if args.tol is None else args.tol
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    rp, ci, va = t(pr.rowptr, torch.int32), t(pr.colidx, torch.int32), t(pr.vals, torch.float64)
+    dofs = t(pr.patch_dofs, torch.int32)
+    opts = L.make_opts(tol=tol, weighting="sym", krylov="cg")
+    p = pr.uniform_size
+    A = torch.empty(pr.n_patches, p, p, dtype=torch.float64, device=dev)
+    L.psr_extract(rp, ci, va, dofs, uniform_size=p, A_out=A)
+    full = L.psr_setup(rp, ci, va, dofs, uniform_size=p, opts=opts)
+    phi, reps, m = full.assignment()
+    st_full = full.stats()
+    half = pr.n_patches // 2
+    reps_h = reps[reps < half]
+    m0 = int(reps_h.numel())
+    seed_A = A[reps_h.long()].contiguous()
+    d = p * p + 2
+    X = torch.empty(pr.n_patches, d, dtype=torch.float32, device=dev)
+    L.psr_features(A, t(pr.cell_coef, torch.float64), X)
+    net = L.MLP(d, 256, m0)
+    g = np.random.Generator(np.random.PCG64(1))
+    params = [g.standard_normal((256, d)) / np.sqrt(d), np.zeros(256), g.standard_normal((256, 256)) / 16.0,
+              np.zeros(256), g.standard_normal((m0, 256)) / 16.0, np.zeros(m0)]
+    net.set_params(t(np.concatenate([q.reshape(-1) for q in params]).astype(np.float32), torch.float32))
+    Xtr = X[:half].contiguous()
+    ytr = phi[:half].contiguous()
+    loss = torch.empty(1, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for ep in range(args.mlp_epochs):
+        net.train_step(Xtr, ytr, args.mlp_lr, loss)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hints = net.predict(X)
+    torch.cuda.synchronize()
+    t_pred = time.perf_counter() - t0
+    acc_train = (hints[:half] == ytr).float().mean().item()
+    res = {}
+    for name, h in (("without", None), ("with", hints)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c = L.psr_setup_seeded(rp, ci, va, dofs, p, seed_A, h, opts=opts)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        s = c.stats()
+        res[name] = {"setup_s": dt, "t_rounds": s["t_rounds"], "criterion_evals": s["criterion_evals"],
+                     "hits": s["mlp_hits"], "m_p": s["m_p"]}
+        c.destroy()
+    out = {"metric": "learned assignment gain (criterion evaluations, setup s)", "workload":
+           f"3D Q2 lognormal diffusion {N}^3 (sigma 1, correlation 8 cells), tol {tol}",
+           "n_patches": pr.n_patches, "m_p_full_alg1": m, "m_seed_first_half": m0,
+           "mlp": {"shape": f"{d}->256->256->{m0}", "epochs": args.mlp_epochs, "lr": args.mlp_lr,
+                   "train_s": t_train, "predict_s": t_pred, "final_loss": loss.item(),
+                   "train_accuracy": acc_train},
+           "alg1_full_evals": st_full["criterion_evals"], "seeded": res,
+           "evals_saved_fraction": 1.0 - res["with"]["criterion_evals"] / max(res["without"]["criterion_evals"], 1)}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
+    if args.mlp:
+        run_mlp_gain(args)
+        return
     cfg = CONFIGS[args.config]
     ws, rank, local = dist_info()
     if args.impl == "reference":

@@ -34,15 +34,13 @@ namespace psr {
 static constexpr double U64 = 0x1p-53;
 
 struct RoundDev {
-    int cursor;        // every local patch below cursor is assigned
-    int i0;            // local index of the newest entry's patch
+    int next;          // patch that becomes the next entry (smallest unassigned)
     int m;             // entries created so far in this group
     int done;
-    int n_undec;
     int first_singular;
+    int ticket;        // last-block counter of the round kernel
+    int next_new;      // smallest candidate the current round rejected
     unsigned long long evals, exact;
-    int undec_overflow;
-    int pad;
 };
 
 struct WarpScratch {  // per-warp shared memory layout for p <= 32
@@ -226,69 +224,8 @@ __device__ void probe_vector_warp(const double* B, int p, int ld, double* w_out)
     w_out[lane] = (act && nv > 0.0) ? t / nv : 0.0;
 }
 
-// One CTA: next entry = smallest unassigned local patch at or after cursor;
-// warp 0 copies it into the database (slot m) and inverts it there.
-__global__ void k_round_begin(RoundDev* st, int32_t* __restrict__ phi, int count,
-                              const double* __restrict__ Ag, int p, EntryDB db,
-                              int32_t* __restrict__ rep_local, int32_t* __restrict__ singular_flags) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_first;
-    if (st->done) return;
-    const int tid = threadIdx.x;
-    if (tid == 0) { s_first = count; st->n_undec = 0; }
-    __syncthreads();
-    for (int base = st->cursor; base < count; base += blockDim.x) {
-        const int i = base + tid;
-        if (i < count && phi[i] == -1) atomicMin(&s_first, i);
-        __syncthreads();
-        if (s_first < count) break;
-        __syncthreads();
-    }
-    const int i0 = s_first;
-    if (i0 >= count) {
-        if (tid == 0) st->done = 1;
-        return;
-    }
-    const int m = st->m;
-    if (tid < 32) {
-        const int ld = p + 1;
-        double* S = reinterpret_cast<double*>(smem);
-        double* colk = S + p * ld;
-        int* swaps = reinterpret_cast<int*>(colk + p);
-        const double* a = Ag + (int64_t)i0 * p * p;
-        double* acopy = db.A + (int64_t)m * p * p;
-        for (int e = tid; e < p * p; e += 32) {
-            const double v = a[e];
-            acopy[e] = v;
-            S[(e / p) * ld + (e % p)] = v;
-        }
-        __syncwarp();
-        const bool sing = gj_invert_warp(S, p, ld, colk, swaps);
-        double fro = 0.0;
-        double* out = db.Binv + (int64_t)m * p * p;
-        for (int e = tid; e < p * p; e += 32) {
-            const double v = S[(e / p) * ld + (e % p)];
-            out[e] = v;
-            fro = fma(v, v, fro);
-        }
-        fro = warp_sum(fro);
-        probe_vector_warp(S, p, ld, db.w + (int64_t)m * 32);
-        if (tid == 0) {
-            db.fro[m] = sqrt(fro);
-            if (sing) {
-                singular_flags[0] = 1;
-                if (st->first_singular < 0) st->first_singular = i0;
-            }
-            phi[i0] = m;
-            rep_local[m] = i0;
-            st->i0 = i0;
-            st->cursor = i0 + 1;
-            st->m = m + 1;
-        }
-    }
-}
-
-// ||B_j^{-1}||_F of every seed entry (one warp each); flags a singular seed.
+// ||B^{-1}||_F and the probe vector of every matrix of a batch of inverses
+// (one warp each); flags (any_bad, may be NULL) when a singular one is among them.
 __global__ void k_entry_fro(const double* __restrict__ Binv, int m, int p, double* __restrict__ fro,
                             double* __restrict__ w, const int32_t* __restrict__ sflags,
                             int32_t* __restrict__ any_bad) {
@@ -301,17 +238,94 @@ __global__ void k_entry_fro(const double* __restrict__ Binv, int m, int p, doubl
     probe_vector_warp(Binv + (int64_t)j * p * p, p, p, w + (int64_t)j * 32);
     if (lane == 0) {
         fro[j] = sqrt(s);
-        if (sflags[j]) atomicOr(any_bad, 1);
+        if (any_bad && sflags[j]) atomicOr(any_bad, 1);
     }
 }
 
-// Stages entry `e` (fixed >= 0) or the newest entry, and returns the first
-// candidate index: all patches for a fixed entry, patches after the newest
-// entry's patch otherwise.
-__device__ __forceinline__ int stage_entry(const RoundDev* st, EntryDB db, int p, int fixed, double* sAc, double* sB,
-                                           double* sw, int* entry, double* bfro) {
+__device__ __forceinline__ bool round_last_block(int* ticket) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int t = atomicAdd(ticket, 1);
+        s_last = (t == (int)gridDim.x - 1);
+        if (s_last) *ticket = 0;
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last != 0;
+}
+
+// One round of Alg. 1 in one kernel.  Every patch's inverse, probe vector and
+// ||A^-1||_F were computed up front in batched launches, so the new entry
+// (patch st->next) is ready to stage.  Each warp takes candidates after it;
+// a rejected candidate stays unassigned and bids for being the next entry
+// (atomicMin): the smallest rejected index is exactly the smallest unassigned
+// patch after the round.  The last block records the entry and the next one.
+__global__ void __launch_bounds__(256, 2) k_round(RoundDev* st, int32_t* __restrict__ phi, int count,
+                                                 const double* __restrict__ Ag, int p,
+                                                 const double* __restrict__ Ball, const double* __restrict__ fro_all,
+                                                 const double* __restrict__ w_all, const int32_t* __restrict__ sing_all,
+                                                 double tol, int32_t* __restrict__ rep_local) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (st->done) return;
     const int ld = p + 1;
-    const int e = (fixed >= 0) ? fixed : st->m - 1;
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const int i0 = st->next;
+    const int m = st->m;
+    double* sAc = reinterpret_cast<double*>(smem);
+    double* sB = sAc + p * ld;
+    double* sw = sB + p * ld;
+    double* wbase = sw + 32 + (size_t)wid * (p * ld + 64);
+    WarpScratch ws{wbase, wbase + p * ld, wbase + p * ld + 32};
+    const double* a = Ag + (int64_t)i0 * p * p;
+    const double* bm = Ball + (int64_t)i0 * p * p;
+    for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+        sAc[(t / p) * ld + (t % p)] = a[t];
+        sB[(t / p) * ld + (t % p)] = bm[t];
+    }
+    if (threadIdx.x < 32) sw[threadIdx.x] = w_all[(int64_t)i0 * 32 + threadIdx.x];
+    const double bfro = fro_all[i0];
+    __syncthreads();
+    unsigned long long my_evals = 0, my_exact = 0;
+    int my_min = count;
+    const int nw = gridDim.x * wpb;
+    for (int cand = i0 + 1 + blockIdx.x * wpb + wid; cand < count; cand += nw) {
+        if (phi[cand] != -1) continue;                 // warp-uniform
+        double dv;
+        int dec = decide_pair(Ag + (int64_t)cand * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, false, sw);
+        if (dec < 0) {
+            dec = decide_pair(Ag + (int64_t)cand * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, true, sw);
+            ++my_exact;
+        }
+        ++my_evals;
+        if (dec == 1) { if (lane == 0) phi[cand] = m; }
+        else my_min = min(my_min, cand);
+        __syncwarp();
+    }
+    if (lane == 0) {
+        if (my_evals) atomicAdd(&st->evals, my_evals);
+        if (my_exact) atomicAdd(&st->exact, my_exact);
+        if (my_min < count) atomicMin(&st->next_new, my_min);
+    }
+    if (!round_last_block(&st->ticket)) return;
+    if (threadIdx.x == 0) {
+        phi[i0] = m;
+        rep_local[m] = i0;
+        if (sing_all[i0] && st->first_singular < 0) st->first_singular = i0;
+        st->m = m + 1;
+        const int nx = st->next_new;
+        st->next_new = count;
+        st->next = nx;
+        if (nx >= count) st->done = 1;
+    }
+}
+
+// Stages seed entry e (patch matrix, inverse, probe) into shared memory.
+__device__ __forceinline__ void stage_seed(EntryDB db, int p, int e, double* sAc, double* sB, double* sw) {
+    const int ld = p + 1;
     const double* a = db.A + (int64_t)e * p * p;
     const double* bm = db.Binv + (int64_t)e * p * p;
     for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
@@ -319,18 +333,13 @@ __device__ __forceinline__ int stage_entry(const RoundDev* st, EntryDB db, int p
         sB[(t / p) * ld + (t % p)] = bm[t];
     }
     if (threadIdx.x < 32) sw[threadIdx.x] = db.w[(int64_t)e * 32 + threadIdx.x];
-    *entry = e;
-    *bfro = db.fro[e];
-    return (fixed >= 0) ? 0 : st->i0 + 1;
 }
 
-// Persistent warps over the candidate range: every unassigned patch is
-// compared with one entry, one candidate per warp at a time; the rare pairs
-// the bounds cannot decide take the exact path in place.
-__global__ void __launch_bounds__(256, 2) k_round_eval(RoundDev* st, int32_t* __restrict__ phi, int count,
-                             const double* __restrict__ Ag, int p, EntryDB db, double tol, int fixed) {
+// Seeded Alg. 1: every still unassigned patch compared with seed entry e.
+__global__ void __launch_bounds__(256, 2) k_seed_pass(RoundDev* st, int32_t* __restrict__ phi, int count,
+                                                     const double* __restrict__ Ag, int p, EntryDB db, double tol,
+                                                     int e) {
     extern __shared__ __align__(16) unsigned char smem[];
-    if (st->done) return;
     const int ld = p + 1;
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
@@ -340,14 +349,13 @@ __global__ void __launch_bounds__(256, 2) k_round_eval(RoundDev* st, int32_t* __
     double* sw = sB + p * ld;
     double* wbase = sw + 32 + (size_t)wid * (p * ld + 64);
     WarpScratch ws{wbase, wbase + p * ld, wbase + p * ld + 32};
-    int m;
-    double bfro;
-    const int start = stage_entry(st, db, p, fixed, sAc, sB, sw, &m, &bfro);
+    stage_seed(db, p, e, sAc, sB, sw);
+    const double bfro = db.fro[e];
     __syncthreads();
     unsigned long long my_evals = 0, my_exact = 0;
     const int nw = gridDim.x * wpb;
-    for (int cand = start + blockIdx.x * wpb + wid; cand < count; cand += nw) {
-        if (phi[cand] != -1) continue;                 // warp-uniform
+    for (int cand = blockIdx.x * wpb + wid; cand < count; cand += nw) {
+        if (phi[cand] != -1) continue;
         double dv;
         int dec = decide_pair(Ag + (int64_t)cand * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, false, sw);
         if (dec < 0) {
@@ -355,12 +363,38 @@ __global__ void __launch_bounds__(256, 2) k_round_eval(RoundDev* st, int32_t* __
             ++my_exact;
         }
         ++my_evals;
-        if (lane == 0 && dec == 1) phi[cand] = m;
+        if (lane == 0 && dec == 1) phi[cand] = e;
         __syncwarp();
     }
     if (lane == 0) {
         if (my_evals) atomicAdd(&st->evals, my_evals);
         if (my_exact) atomicAdd(&st->exact, my_exact);
+    }
+}
+
+// Smallest unassigned patch -> st->next (done when there is none).
+__global__ void k_first_open(RoundDev* st, const int32_t* __restrict__ phi, int count) {
+    int mn = count;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+        if (phi[i] == -1) mn = min(mn, i);
+    for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    if ((threadIdx.x & 31) == 0 && mn < count) atomicMin(&st->next, mn);
+}
+
+__global__ void k_finish_first(RoundDev* st, int count) {
+    if (st->next >= count) st->done = 1;
+}
+
+// Database assembly: entry j < m0 from the seed inverses, entry j >= m0 from
+// the inverse of its patch.
+__global__ void k_gather_db(const double* __restrict__ seedB, int m0, const double* __restrict__ Ball,
+                            const int32_t* __restrict__ rep_local, int m, int p, double* __restrict__ out) {
+    const int64_t pp = (int64_t)p * p;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)m * pp;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / pp);
+        const int64_t o = e - (int64_t)j * pp;
+        out[e] = (j < m0) ? seedB[(int64_t)j * pp + o] : Ball[(int64_t)rep_local[j] * pp + o];
     }
 }
 
@@ -428,9 +462,8 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
     RoundDev* h_st = nullptr;
     PSR_CUDA(ctx, cudaMalloc(&st, sizeof(RoundDev)));
     PSR_CUDA(ctx, cudaMallocHost(&h_st, sizeof(RoundDev)));
-    int32_t* sing_flag = nullptr;
-    PSR_CUDA(ctx, cudaMalloc(&sing_flag, 2 * sizeof(int32_t)));
-    PSR_CUDA(ctx, cudaMemsetAsync(sing_flag, 0, 2 * sizeof(int32_t), s));
+    int32_t* flag = nullptr;
+    PSR_CUDA(ctx, cudaMalloc(&flag, sizeof(int32_t)));
     int rc = PSR_OK;
     int64_t total_evals = 0, total_exact = 0, total_hits = 0;
     int rounds_total = 0;
@@ -442,47 +475,58 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         const double* Ag = ctx->A_ext + G.mat_off;
         int32_t* phi_l = nullptr;
         int32_t* rep_l = nullptr;
+        int32_t* sing_all = nullptr;
+        double *Ball = nullptr, *fro_all = nullptr, *w_all = nullptr;
         EntryDB db{nullptr, nullptr, nullptr, nullptr};
         const int cap = count + m0;
         PSR_CUDA(ctx, cudaMalloc(&phi_l, sizeof(int32_t) * count));
         PSR_CUDA(ctx, cudaMalloc(&rep_l, sizeof(int32_t) * cap));
-        PSR_CUDA(ctx, cudaMalloc(&db.fro, sizeof(double) * cap));
-        PSR_CUDA(ctx, cudaMalloc(&db.w, sizeof(double) * (size_t)cap * 32));
-        if (cudaMalloc(&db.Binv, sizeof(double) * (size_t)cap * p * p) != cudaSuccess ||
-            cudaMalloc(&db.A, sizeof(double) * (size_t)cap * p * p) != cudaSuccess) {
+        PSR_CUDA(ctx, cudaMalloc(&sing_all, sizeof(int32_t) * count));
+        PSR_CUDA(ctx, cudaMalloc(&fro_all, sizeof(double) * count));
+        PSR_CUDA(ctx, cudaMalloc(&w_all, sizeof(double) * (size_t)count * 32));
+        if (cudaMalloc(&Ball, sizeof(double) * (size_t)count * p * p) != cudaSuccess) {
             cudaGetLastError();
-            set_error(ctx, "out of device memory for the database");
+            set_error(ctx, "out of device memory for the patch inverses");
             return PSR_ERR_OOM;
         }
         PSR_CUDA(ctx, cudaMemsetAsync(phi_l, 0xff, sizeof(int32_t) * count, s));
+        // every patch's inverse, norm and probe, batched (any patch may become an entry)
+        rc = launch_batched_inverse(Ag, (int64_t)p * p, nullptr, count, p, Ball, (int64_t)p * p, sing_all, s);
+        if (rc != PSR_OK) break;
+        count_launch();
+        k_entry_fro<<<(count + 7) / 8, 256, 0, s>>>(Ball, count, p, fro_all, w_all, sing_all, nullptr);
         RoundDev init{};
         init.first_singular = -1;
         init.m = m0;
+        init.next = 0;
+        init.next_new = count;
         PSR_CUDA(ctx, cudaMemcpyAsync(st, &init, sizeof(RoundDev), cudaMemcpyHostToDevice, s));
         const int ld = p + 1;
-        const size_t smem_begin = (size_t)((p * ld + p) * 8 + p * 4 + 16);
         const int wpb = 8;
         const size_t smem_eval = eval_smem_bytes(p, wpb);
-        if ((rc = set_smem((const void*)k_round_begin, smem_begin)) != PSR_OK) break;
-        if ((rc = set_smem((const void*)k_round_eval, smem_eval)) != PSR_OK) break;
+        if ((rc = set_smem((const void*)k_round, smem_eval)) != PSR_OK) break;
+        if ((rc = set_smem((const void*)k_seed_pass, smem_eval)) != PSR_OK) break;
         // one warp per candidate: enough warps for every SM, a few candidates each
         int eval_blocks = (count + wpb - 1) / wpb;
         if (eval_blocks > 152 * 4) eval_blocks = 152 * 4;
         if (eval_blocks < 1) eval_blocks = 1;
         if (m0 > 0) {
-            // seed entries: copy, invert, norms
+            PSR_CUDA(ctx, cudaMalloc(&db.A, sizeof(double) * (size_t)m0 * p * p));
+            PSR_CUDA(ctx, cudaMalloc(&db.Binv, sizeof(double) * (size_t)m0 * p * p));
+            PSR_CUDA(ctx, cudaMalloc(&db.fro, sizeof(double) * m0));
+            PSR_CUDA(ctx, cudaMalloc(&db.w, sizeof(double) * (size_t)m0 * 32));
             PSR_CUDA(ctx, cudaMemcpyAsync(db.A, seed_A, sizeof(double) * (size_t)m0 * p * p, cudaMemcpyDeviceToDevice, s));
             int32_t* sflags = nullptr;
             PSR_CUDA(ctx, cudaMalloc(&sflags, sizeof(int32_t) * m0));
             rc = launch_batched_inverse(db.A, (int64_t)p * p, nullptr, m0, p, db.Binv, (int64_t)p * p, sflags, s);
             if (rc != PSR_OK) break;
+            PSR_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
             count_launch();
-            k_entry_fro<<<(m0 + 7) / 8, 256, 0, s>>>(db.Binv, m0, p, db.fro, db.w, sflags, sing_flag + 1);
-            std::vector<int32_t> seq(m0);
-            for (int j = 0; j < m0; ++j) seq[j] = -1;
+            k_entry_fro<<<(m0 + 7) / 8, 256, 0, s>>>(db.Binv, m0, p, db.fro, db.w, sflags, flag);
+            std::vector<int32_t> seq(m0, -1);
             PSR_CUDA(ctx, cudaMemcpyAsync(rep_l, seq.data(), sizeof(int32_t) * m0, cudaMemcpyHostToDevice, s));
             int32_t h_bad = 0;
-            PSR_CUDA(ctx, cudaMemcpyAsync(&h_bad, sing_flag + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            PSR_CUDA(ctx, cudaMemcpyAsync(&h_bad, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
             PSR_CUDA(ctx, cudaStreamSynchronize(s));
             cudaFree(sflags);
             if (h_bad) { set_error(ctx, "a seed database entry is singular"); rc = PSR_ERR_SINGULAR_PATCH; break; }
@@ -503,27 +547,35 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
             }
             // misses: first match over the seed entries, in creation order
             for (int j = 0; j < m0; ++j) {
-                count_launch(); k_round_eval<<<eval_blocks, wpb * 32, smem_eval, s>>>(st, phi_l, count, Ag, p, db, tol, j);
+                count_launch();
+                k_seed_pass<<<eval_blocks, wpb * 32, smem_eval, s>>>(st, phi_l, count, Ag, p, db, tol, j);
             }
             PSR_CHECK_LAUNCH(ctx, "seeded Alg. 1 passes");
+            // the first new entry is the smallest patch still unassigned
+            int big = count;
+            PSR_CUDA(ctx, cudaMemcpyAsync(&st->next, &big, sizeof(int), cudaMemcpyHostToDevice, s));
+            count_launch();
+            k_first_open<<<std::max(1, std::min((count + 255) / 256, 1024)), 256, 0, s>>>(st, phi_l, count);
+            count_launch();
+            k_finish_first<<<1, 1, 0, s>>>(st, count);
         }
-        int batch = 4;
+        int batch = 8;
         int issued = 0;
         for (;;) {
             for (int r = 0; r < batch; ++r) {
-                count_launch(); k_round_begin<<<1, 256, smem_begin, s>>>(st, phi_l, count, Ag, p, db, rep_l, sing_flag);
-                count_launch(); k_round_eval<<<eval_blocks, wpb * 32, smem_eval, s>>>(st, phi_l, count, Ag, p, db, tol, -1);
+                count_launch();
+                k_round<<<eval_blocks, wpb * 32, smem_eval, s>>>(st, phi_l, count, Ag, p, Ball, fro_all, w_all,
+                                                                 sing_all, tol, rep_l);
             }
-            PSR_CHECK_LAUNCH(ctx, "Alg. 1 round kernels");
+            PSR_CHECK_LAUNCH(ctx, "Alg. 1 round kernel");
             issued += batch;
             PSR_CUDA(ctx, cudaMemcpyAsync(h_st, st, sizeof(RoundDev), cudaMemcpyDeviceToHost, s));
             PSR_CUDA(ctx, cudaStreamSynchronize(s));
             if (h_st->done) break;
             if (issued > count + 8) { set_error(ctx, "Alg. 1 rounds did not terminate"); rc = PSR_ERR_TIMEOUT; break; }
-            if (batch < 256) batch *= 2;
+            if (batch < 512) batch *= 2;
         }
         if (rc != PSR_OK) break;
-        if (h_st->undec_overflow) { set_error(ctx, "criterion undecided list overflow"); rc = PSR_ERR_CUDA; break; }
         G.m = h_st->m;
         total_evals += (int64_t)h_st->evals;
         total_exact += (int64_t)h_st->exact;
@@ -531,18 +583,31 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         if (h_st->first_singular >= 0 && first_singular < 0) first_singular = G.h_gidx[h_st->first_singular];
         std::vector<int32_t> hrep(G.m);
         PSR_CUDA(ctx, cudaMemcpyAsync(hrep.data(), rep_l, sizeof(int32_t) * G.m, cudaMemcpyDeviceToHost, s));
+        double* Bdb = nullptr;
+        PSR_CUDA(ctx, cudaMalloc(&Bdb, sizeof(double) * (size_t)std::max(G.m, 1) * p * p));
+        {
+            const int64_t tot = (int64_t)G.m * p * p;
+            const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 152 * 16));
+            count_launch();
+            k_gather_db<<<gb, 256, 0, s>>>(db.Binv, m0, Ball, rep_l, G.m, p, Bdb);
+        }
         PSR_CUDA(ctx, cudaStreamSynchronize(s));
         G.h_rep.assign(hrep.begin(), hrep.end());   // local patch of each entry, -1 for seed entries
         G.sphi = phi_l;             // local phi in original (unsorted) order
-        G.rinv = db.Binv;           // FP64 database, converted in the sweep builder
+        G.rinv = Bdb;               // FP64 database, converted in the sweep builder
+        cudaFree(Ball);
+        cudaFree(fro_all);
+        cudaFree(w_all);
+        cudaFree(sing_all);
         cudaFree(db.A);
+        cudaFree(db.Binv);
         cudaFree(db.fro);
         cudaFree(db.w);
         cudaFree(rep_l);
     }
     cudaFree(st);
     cudaFreeHost(h_st);
-    cudaFree(sing_flag);
+    cudaFree(flag);
     ctx->stats.criterion_evals = total_evals;
     ctx->stats.criterion_exact = total_exact;
     ctx->stats.mlp_hits = total_hits;

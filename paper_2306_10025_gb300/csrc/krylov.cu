@@ -73,12 +73,25 @@ __device__ __forceinline__ bool last_block(int32_t* cnt) {
     return s_last != 0;
 }
 
+// part[start], part[start + step], ... below end, with four independent
+// accumulators so the loads overlap instead of forming one dependent chain.
+__device__ __forceinline__ double sum_strided(const double* part, int start, int end, int step) {
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int b = start;
+    for (; b + 3 * step < end; b += 4 * step) {
+        a0 += part[b];
+        a1 += part[b + step];
+        a2 += part[b + 2 * step];
+        a3 += part[b + 3 * step];
+    }
+    for (; b < end; b += step) a0 += part[b];
+    return (a0 + a1) + (a2 + a3);
+}
+
 // Sum of nb partials in a fixed order by the whole block; valid in thread 0.
 __device__ __forceinline__ double sum_partials(const double* part, int nb) {
     __shared__ double sp[32];
-    double v = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[b];
-    return block_sum(v, sp);
+    return block_sum(sum_strided(part, threadIdx.x, nb, blockDim.x), sp);
 }
 
 // ---------------------------------------------------------------- SpMV
@@ -242,10 +255,13 @@ __global__ void k_fg_start(const double* __restrict__ r, double* __restrict__ V0
     }
 }
 
-// h_i = V_i . w for i <= j (pass 1 -> H column j; pass 2 -> added to it)
-__global__ void __launch_bounds__(256) k_mdot(const double* __restrict__ V, const double* __restrict__ w, int n, int j,
-                                              KDims kd, int pass) {
-    __shared__ double sh[32][9];
+// h_i = V_i . w for i <= j (pass 1 -> H column j; pass 2 -> added to it).
+// 512-thread blocks; at most MDOT_BLOCKS partials per vector.
+constexpr int MDOT_THREADS = 512;
+constexpr int MDOT_BLOCKS = 152 * 2;
+__global__ void __launch_bounds__(MDOT_THREADS) k_mdot(const double* __restrict__ V, const double* __restrict__ w, int n,
+                                                       int j, KDims kd, int pass) {
+    __shared__ double sh[32][MDOT_THREADS / 32 + 1];
     if (kd.ictl[I_STOP]) return;
     const int nv = j + 1;
     double acc[32];
@@ -280,16 +296,14 @@ __global__ void __launch_bounds__(256) k_mdot(const double* __restrict__ V, cons
         kd.part[threadIdx.x * gridDim.x + blockIdx.x] = t;
     }
     if (!last_block(kd.ictl + I_CNT + 4)) return;
-    // 8 threads per vector (256 threads, <= 32 vectors), fixed order
+    // 16 threads per vector (512 threads, <= 32 vectors), fixed order
     const int m = kd.m;
     double* H = Hm(kd.scal, m);
     double* hv = Hv(kd.scal, m);
-    const int i = threadIdx.x >> 3, q = threadIdx.x & 7;
-    double v = 0.0;
-    if (i < nv)
-        for (int b = q; b < (int)gridDim.x; b += 8) v += kd.part[i * gridDim.x + b];
+    const int i = threadIdx.x >> 4, q = threadIdx.x & 15;
+    double v = (i < nv) ? sum_strided(kd.part + (int64_t)i * gridDim.x, q, gridDim.x, 16) : 0.0;
 #pragma unroll
-    for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, 8);
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, 16);
     if (i < nv && q == 0) {
         hv[i] = v;
         if (pass == 0) H[i * m + j] = v;
@@ -425,7 +439,7 @@ int krylov_alloc(psr_ctx* ctx) {
     if (m < 1) m = 1;
     if (m > 32) m = 32;
     ctx->opts.restart = m;
-    w.nblk = (int)std::min<size_t>(std::max<size_t>((n + 255) / 256, 1), 152 * 16);
+    w.nblk = (int)std::min<size_t>(std::max<size_t>((n + 255) / 256, 1), 152 * 4);
     PSR_CUDA(ctx, cudaMalloc(&w.x, n * 8));
     PSR_CUDA(ctx, cudaMalloc(&w.b, n * 8));
     PSR_CUDA(ctx, cudaMalloc(&w.r, n * 8));
@@ -437,7 +451,7 @@ int krylov_alloc(psr_ctx* ctx) {
         PSR_CUDA(ctx, cudaMalloc(&w.V, (size_t)(m + 1) * n * 8));
         PSR_CUDA(ctx, cudaMalloc(&w.Z, (size_t)m * n * 8));
     }
-    w.nspmv = 152 * 32;                     // partial slots available to the SpMV reductions
+    w.nspmv = 152 * 16;                     // partial slots available to the SpMV reductions
     PSR_CUDA(ctx, cudaMalloc(&w.partial, (size_t)std::max(w.nblk * 34, w.nspmv) * 8));
     PSR_CUDA(ctx, cudaMalloc(&w.scal, (size_t)scal_count(m) * 8));
     PSR_CUDA(ctx, cudaMemset(w.scal, 0, (size_t)scal_count(m) * 8));
@@ -483,9 +497,10 @@ static int enqueue_fg_cycle(psr_ctx* ctx, KDims kd, cudaStream_t s) {
         int rc = sweep_apply_ex(ctx, Vj, Zj, kd.ictl + I_STOP, s);
         if (rc != PSR_OK) return rc;
         launch_spmv(ctx, Zj, Vn, nullptr, 0, 0, kd, 1, w.nspmv, s);
-        count_launch(); k_mdot<<<nb, 256, 0, s>>>(w.V, Vn, n, j, kd, 0);
+        const int mb = std::max(1, std::min((n + MDOT_THREADS - 1) / MDOT_THREADS, MDOT_BLOCKS));
+        count_launch(); k_mdot<<<mb, MDOT_THREADS, 0, s>>>(w.V, Vn, n, j, kd, 0);
         count_launch(); k_maxpy<<<nb, 256, 0, s>>>(w.V, Vn, n, j, kd, 0);
-        count_launch(); k_mdot<<<nb, 256, 0, s>>>(w.V, Vn, n, j, kd, 1);
+        count_launch(); k_mdot<<<mb, MDOT_THREADS, 0, s>>>(w.V, Vn, n, j, kd, 1);
         count_launch(); k_maxpy<<<nb, 256, 0, s>>>(w.V, Vn, n, j, kd, 1);
         count_launch(); k_fg_scale<<<nb, 256, 0, s>>>(Vn, n, kd);
     }
