@@ -56,7 +56,8 @@ struct WarpScratch {  // per-warp shared memory layout for p <= 32
 // the deciding value.  All lanes call; lane r handles row r.
 __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, const double* sB,
                            int p, int ld, double binv_fro, double tol, WarpScratch ws, double* dv,
-                           bool allow_exact_here, const double* probe = nullptr) {
+                           bool allow_exact_here, const double* probe = nullptr,
+                           const float* sB32 = nullptr) {
     const int lane = threadIdx.x & 31;
     const bool act = lane < p;
     // pass 1: D = A_c - A_i, ||D||_F and (D w)_lane
@@ -81,6 +82,92 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
         // w carries its own rounding (B^-1 v computed in FP64): widen by 2 err
         const double lb1 = sqrt(warp_sum(dw * dw));
         if (lb1 * shrink - 2.0 * err >= tol) { *dv = lb1; return 0; }
+    }
+    if (sB32) {
+        // FP32 screening: E32 = fl32(D) fl32(B^-1) accumulated in FP32.  With
+        // u = 2^-24, |E32 - D B^-1| <= (p+3) u |D| |B^-1| entrywise, so
+        // ||E32 - E||_2 <= err32 below; FP32 norms are widened for their own
+        // rounding.  Conclusive tests here give the same decision as the FP64
+        // path; the rest fall through.
+        const double u32 = 0x1p-24;
+        const double err32 = 1.01 * (double)(p + 3) * u32 * dF * binv_fro;
+        const float up = 1.0f + 4.0f * (float)(p + 2) * 0x1p-24f;
+        const float dn = 1.0f - 4.0f * (float)(p + 2) * 0x1p-24f;
+        float* E32 = reinterpret_cast<float*>(ws.E);
+        float* v32 = reinterpret_cast<float*>(ws.v);
+        float* w32 = reinterpret_cast<float*>(ws.w);
+        float f[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) f[j] = 0.f;
+        if (act) {
+            for (int k = 0; k < p; ++k) {
+                const float dk = (float)(sAc[lane * ld + k] - Ai[lane * p + k]);
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (j < p) f[j] = fmaf(dk, sB32[k * ld + j], f[j]);
+            }
+        }
+        float fr2 = 0.f, ra = 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (j < p) { fr2 = fmaf(f[j], f[j], fr2); ra += fabsf(f[j]); }
+        const float rn = sqrtf(fr2);
+        fr2 = warp_sumf(fr2);
+        float ni = act ? ra : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ni = fmaxf(ni, __shfl_xor_sync(0xffffffffu, ni, o));
+        if (act) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (j < p) E32[lane * ld + j] = f[j];
+        }
+        __syncwarp();
+        float ca = 0.f;
+        if (act)
+            for (int r = 0; r < p; ++r) ca += fabsf(E32[r * ld + lane]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ca = fmaxf(ca, __shfl_xor_sync(0xffffffffu, ca, o));
+        const double ub32 = (double)(fminf(sqrtf(fr2), sqrtf(ca * ni)) * up);
+        if (ub32 + err32 < tol) { *dv = ub32 + err32; return 1; }
+        float bst = act ? rn : -1.f;
+        int bri = lane;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, bst, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bri, o);
+            if (ob > bst || (ob == bst && oi < bri)) { bst = ob; bri = oi; }
+        }
+        double lb32 = (double)(bst * dn);
+        if (lb32 - err32 >= tol) { *dv = lb32 - err32; return 0; }
+        if (bst > 0.f) {
+            if (act) v32[lane] = E32[bri * ld + lane] / bst;
+            __syncwarp();
+            for (int it = 0; it < 12; ++it) {
+                float wr = 0.f;
+                if (act) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (j < p) wr = fmaf(f[j], v32[j], wr);
+                }
+                const float nw = sqrtf(warp_sumf(wr * wr));
+                lb32 = fmax(lb32, (double)(nw * dn));
+                if (lb32 - err32 >= tol) { *dv = lb32 - err32; return 0; }
+                if (!(nw > 0.f)) break;
+                if (act) w32[lane] = wr;
+                __syncwarp();
+                float uj = 0.f;
+                if (act)
+                    for (int r = 0; r < p; ++r) uj = fmaf(E32[r * ld + lane], w32[r], uj);
+                const float nu = sqrtf(warp_sumf(uj * uj));
+                lb32 = fmax(lb32, (double)(nu / nw * dn));
+                if (lb32 - err32 >= tol) { *dv = lb32 - err32; return 0; }
+                if (!(nu > 0.f)) break;
+                __syncwarp();
+                if (act) v32[lane] = uj / nu;
+                __syncwarp();
+            }
+        }
+        __syncwarp();
     }
     // pass 2: E row = D row * B^-1
     double e[32];
@@ -175,9 +262,14 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
 }
 
 // ---------------------------------------------------------------- rounds
+// block part: A_c, B^-1 (FP64), probe (32), B^-1 in FP32; then per warp E + v + w
+__host__ __device__ inline int eval_block_doubles(int p) {
+    const int ld = p + 1;
+    return 2 * p * ld + 32 + (p * ld + 1) / 2;
+}
 __host__ __device__ inline size_t eval_smem_bytes(int p, int wpb) {
     const int ld = p + 1;
-    return (size_t)(2 * p * ld + 32) * 8 + (size_t)wpb * ((size_t)p * ld + 64) * 8;
+    return (size_t)eval_block_doubles(p) * 8 + (size_t)wpb * ((size_t)p * ld + 64) * 8;
 }
 
 // Entry database of one size group: patch matrices A_c, inverses B_c^{-1},
@@ -278,13 +370,16 @@ __global__ void __launch_bounds__(256, 2) k_round(RoundDev* st, int32_t* __restr
     double* sAc = reinterpret_cast<double*>(smem);
     double* sB = sAc + p * ld;
     double* sw = sB + p * ld;
-    double* wbase = sw + 32 + (size_t)wid * (p * ld + 64);
+    float* sB32 = reinterpret_cast<float*>(sw + 32);
+    double* wbase = reinterpret_cast<double*>(smem) + eval_block_doubles(p) + (size_t)wid * (p * ld + 64);
     WarpScratch ws{wbase, wbase + p * ld, wbase + p * ld + 32};
     const double* a = Ag + (int64_t)i0 * p * p;
     const double* bm = Ball + (int64_t)i0 * p * p;
     for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
         sAc[(t / p) * ld + (t % p)] = a[t];
-        sB[(t / p) * ld + (t % p)] = bm[t];
+        const double b = bm[t];
+        sB[(t / p) * ld + (t % p)] = b;
+        sB32[(t / p) * ld + (t % p)] = (float)b;
     }
     if (threadIdx.x < 32) sw[threadIdx.x] = w_all[(int64_t)i0 * 32 + threadIdx.x];
     const double bfro = fro_all[i0];
@@ -295,9 +390,9 @@ __global__ void __launch_bounds__(256, 2) k_round(RoundDev* st, int32_t* __restr
     for (int cand = i0 + 1 + blockIdx.x * wpb + wid; cand < count; cand += nw) {
         if (phi[cand] != -1) continue;                 // warp-uniform
         double dv;
-        int dec = decide_pair(Ag + (int64_t)cand * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, false, sw);
+        int dec = decide_pair(Ag + (int64_t)cand * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, false, sw, sB32);
         if (dec < 0) {
-            dec = decide_pair(Ag + (int64_t)cand * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, true, sw);
+            dec = decide_pair(Ag + (int64_t)cand * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, true, sw, nullptr);
             ++my_exact;
         }
         ++my_evals;
@@ -347,9 +442,12 @@ __global__ void __launch_bounds__(256, 2) k_seed_pass(RoundDev* st, int32_t* __r
     double* sAc = reinterpret_cast<double*>(smem);
     double* sB = sAc + p * ld;
     double* sw = sB + p * ld;
-    double* wbase = sw + 32 + (size_t)wid * (p * ld + 64);
+    float* sB32 = reinterpret_cast<float*>(sw + 32);
+    double* wbase = reinterpret_cast<double*>(smem) + eval_block_doubles(p) + (size_t)wid * (p * ld + 64);
     WarpScratch ws{wbase, wbase + p * ld, wbase + p * ld + 32};
     stage_seed(db, p, e, sAc, sB, sw);
+    for (int t = threadIdx.x; t < p * p; t += blockDim.x)
+        sB32[(t / p) * ld + (t % p)] = (float)db.Binv[(int64_t)e * p * p + t];
     const double bfro = db.fro[e];
     __syncthreads();
     unsigned long long my_evals = 0, my_exact = 0;
@@ -357,9 +455,9 @@ __global__ void __launch_bounds__(256, 2) k_seed_pass(RoundDev* st, int32_t* __r
     for (int cand = blockIdx.x * wpb + wid; cand < count; cand += nw) {
         if (phi[cand] != -1) continue;
         double dv;
-        int dec = decide_pair(Ag + (int64_t)cand * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, false, sw);
+        int dec = decide_pair(Ag + (int64_t)cand * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, false, sw, sB32);
         if (dec < 0) {
-            dec = decide_pair(Ag + (int64_t)cand * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, true, sw);
+            dec = decide_pair(Ag + (int64_t)cand * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, true, sw, nullptr);
             ++my_exact;
         }
         ++my_evals;
@@ -628,12 +726,14 @@ __global__ void k_criterion_batch(const double* __restrict__ A_i, int32_t batch,
     const int wpb = blockDim.x >> 5;
     double* sAc = reinterpret_cast<double*>(smem);
     double* sB = sAc + p * ld;
-    double* wbase = sB + p * ld + (size_t)wid * (p * ld + 64);
+    float* sB32 = reinterpret_cast<float*>(sB + p * ld + 32);
+    double* wbase = reinterpret_cast<double*>(smem) + eval_block_doubles(p) + (size_t)wid * (p * ld + 64);
     WarpScratch ws{wbase, wbase + p * ld, wbase + p * ld + 32};
     double bf = 0.0;
     for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
         sAc[(e / p) * ld + (e % p)] = A_c[e];
         sB[(e / p) * ld + (e % p)] = Binv_c[e];
+        sB32[(e / p) * ld + (e % p)] = (float)Binv_c[e];
     }
     __syncthreads();
     for (int e = lane; e < p * p; e += 32) bf = fma(Binv_c[e], Binv_c[e], bf);
@@ -642,7 +742,8 @@ __global__ void k_criterion_batch(const double* __restrict__ A_i, int32_t batch,
     for (int u = blockIdx.x * wpb + wid; u < total; u += gridDim.x * wpb) {
         const int b = (phase == 0) ? u : undec[u];
         double dv;
-        const int dec = decide_pair(A_i + (int64_t)b * p * p, sAc, sB, p, ld, bf, tol, ws, &dv, phase == 1);
+        const int dec = decide_pair(A_i + (int64_t)b * p * p, sAc, sB, p, ld, bf, tol, ws, &dv, phase == 1,
+                                    nullptr, phase == 0 ? sB32 : nullptr);
         if (lane == 0) {
             if (dec >= 0) {
                 accept[b] = dec;
