@@ -63,6 +63,9 @@ extern "C" {
 #define PSR_SWEEP_AUTO     0       /* library chooses                         */
 #define PSR_SWEEP_GROUPED  1       /* one persistent launch over all size groups */
 #define PSR_SWEEP_PERGROUP 2       /* one launch per patch-size group         */
+#define PSR_SWEEP_TENSOR   3       /* per group; BF16 clustered groups always on the
+                                      tensor cores (AUTO uses them only when their
+                                      128-patch tiles are at least 1/4 full) */
 
 typedef struct psr_ctx psr_ctx;    /* opaque, library-owned */
 
@@ -90,7 +93,7 @@ typedef struct {
     int32_t store_prec;   /* PSR_PREC_*                                           */
     int32_t weighting;    /* PSR_WEIGHT_*                                         */
     int32_t krylov;       /* PSR_KRYLOV_*                                         */
-    int32_t restart;      /* FGMRES restart length m (1..64)                      */
+    int32_t restart;      /* FGMRES restart length m (1..32)                      */
     double  rtol;         /* relative residual target                             */
     int32_t maxit;        /* outer iteration cap                                  */
     int32_t use_graph;    /* 1: capture Krylov cycles in CUDA graphs              */
@@ -165,6 +168,9 @@ typedef struct {
     double  t_extract, t_rounds, t_invert, t_convert, t_autotune; /* setup seconds */
     int32_t first_singular;       /* patch index or -1                          */
     int32_t rounds;               /* Alg. 1 rounds (= m_p when tol > 0)         */
+    int32_t tc_groups;            /* size groups applied on the tensor cores (BF16
+                                     storage, 128-patch tiles at least 1/4 full) */
+    int32_t reserved;
 } psr_stats;
 
 int psr_get_stats(psr_ctx* ctx, psr_stats* st);
@@ -178,6 +184,36 @@ void psr_destroy(psr_ctx* ctx);
  * process so far (a graph launch counts its kernel nodes).  Host-only, never
  * fails; used by benchmarks to state how many kernels a timed region ran. */
 int64_t psr_kernel_launches(void);
+
+/* Instrumentation (the paper has no counterpart): per-kernel device time of
+ * the outer solve.  Classes of the per-iteration kernels: */
+#define PSR_KT_SWEEP 0   /* preconditioner application z = M^-1 r (Eq. 1 / Eq. 3) */
+#define PSR_KT_SPMV 1    /* A z inside the iteration (CSR, FP64) */
+#define PSR_KT_MDOT 2    /* FGMRES projections h = V^T w (both Gram-Schmidt passes) */
+#define PSR_KT_MAXPY 3   /* FGMRES w -= V h (both passes; the second ends the Arnoldi step) */
+#define PSR_KT_VEC 4     /* remaining vector kernels (FGMRES scale; CG updates and dots) */
+#define PSR_KT_COUNT 5
+
+/* enable != 0: from the next psr_solve on, every per-iteration kernel launch
+ * of the solve is bracketed by two CUDA event records on the solve's stream
+ * (inside the captured graph when graphs are on), and after each CG block /
+ * FGMRES cycle the elapsed times of the launches that did work (iterations
+ * that ran, not ones skipped by the stop flag) are added to per-class totals,
+ * with their algorithmic bytes.  Enabling resets the totals; enabling or
+ * disabling drops the captured graph (re-captured by the next solve).  The
+ * events add a little time per launch: take the solve's own timing from a
+ * run with timing disabled.  Returns PSR_OK or PSR_ERR_INVALID_ARG (ctx NULL). */
+int psr_set_kernel_timing(psr_ctx* ctx, int enable);
+
+/* Copies the totals since the last enable for classes 0 .. count-1
+ * (count <= PSR_KT_COUNT): ms = summed event durations in milliseconds,
+ * launches = timed launches, bytes = summed algorithmic bytes of those
+ * launches (SpMV: 12 nnz + 4 (n+1) + 16 n; V^T w with j+1 basis vectors:
+ * 8 (j+2) n; w -= V h: 8 (j+3) n; sweep: 24 n + 4 sum(p_k) + 4 n_patches +
+ * stored factor bytes; FGMRES scale 16 n; CG kernels their vector reads and
+ * writes).  Any pointer may be NULL.  Host-only; PSR_ERR_INVALID_ARG for a
+ * NULL ctx or count outside 1 .. PSR_KT_COUNT. */
+int psr_get_kernel_timing(psr_ctx* ctx, double* ms, int64_t* launches, double* bytes, int count);
 
 /* ---- single steps of the path (stateless; for testing and reuse) ------- */
 

@@ -24,14 +24,16 @@ ERRORS = {
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
 WEIGHT = {"left": 0, "sym": 1}
 KRYLOV = {"cg": 0, "fgmres": 1}
-SWEEP = {"auto": 0, "grouped": 1, "pergroup": 2}
+SWEEP = {"auto": 0, "grouped": 1, "pergroup": 2, "tensor": 3}
 
 EXPORTS = ["psr_default_opts", "psr_setup", "psr_apply", "psr_solve", "psr_get_history",
            "psr_get_assignment", "psr_get_stats", "psr_last_error", "psr_destroy", "psr_extract",
            "psr_batched_inverse", "psr_criterion", "psr_spectral_norm", "psr_kernel_launches",
            "psr_setup_seeded", "psr_features", "psr_mlp_create", "psr_mlp_num_params", "psr_mlp_set_params",
            "psr_mlp_get_params", "psr_mlp_loss_grad", "psr_mlp_train_step", "psr_mlp_predict", "psr_mlp_destroy",
-           "psr_criterion_noalloc"]
+           "psr_criterion_noalloc", "psr_set_kernel_timing", "psr_get_kernel_timing"]
+
+KT_CLASSES = ("sweep", "spmv", "mdot", "maxpy", "vec")   # PSR_KT_* in order
 
 
 class PsrError(RuntimeError):
@@ -68,7 +70,8 @@ class psr_stats(C.Structure):
                 ("factor_bytes", C.c_int64), ("index_bytes", C.c_int64),
                 ("t_extract", C.c_double), ("t_rounds", C.c_double), ("t_invert", C.c_double),
                 ("t_convert", C.c_double), ("t_autotune", C.c_double),
-                ("first_singular", C.c_int32), ("rounds", C.c_int32)]
+                ("first_singular", C.c_int32), ("rounds", C.c_int32), ("tc_groups", C.c_int32),
+                ("reserved", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -104,6 +107,8 @@ def load(path: str = LIB_PATH):
     lib.psr_spectral_norm.argtypes = [vp, i32, i32, vp, vp]
     lib.psr_criterion_noalloc.argtypes = [vp, i32, i32, vp, vp, d, vp, vp, vp]
     lib.psr_kernel_launches.argtypes = []
+    lib.psr_set_kernel_timing.argtypes = [vp, i32]
+    lib.psr_get_kernel_timing.argtypes = [vp, vp, vp, vp, i32]
     lib.psr_setup_seeded.argtypes = [C.POINTER(psr_csr), C.POINTER(psr_patches), C.POINTER(psr_opts), vp, i32, vp,
                                      vp, C.POINTER(vp)]
     lib.psr_features.argtypes = [vp, i32, i32, vp, vp, vp]
@@ -247,6 +252,17 @@ class Context:
         st = psr_stats()
         _check(load().psr_get_stats(self.h, C.byref(st)), self.h)
         return st.as_dict()
+
+    def set_kernel_timing(self, enable: bool):
+        _check(load().psr_set_kernel_timing(self.h, int(bool(enable))), self.h)
+
+    def kernel_timing(self) -> dict:
+        """Per-class totals of psr_get_kernel_timing: {class: (ms, launches, bytes)}."""
+        k = len(KT_CLASSES)
+        ms, nl, by = (C.c_double * k)(), (C.c_int64 * k)(), (C.c_double * k)()
+        _check(load().psr_get_kernel_timing(self.h, C.cast(ms, C.c_void_p), C.cast(nl, C.c_void_p),
+                                             C.cast(by, C.c_void_p), k), self.h)
+        return {name: (ms[i], int(nl[i]), by[i]) for i, name in enumerate(KT_CLASSES)}
 
     def destroy(self):
         if self.h:

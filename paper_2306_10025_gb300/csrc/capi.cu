@@ -91,7 +91,8 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
     if (o) ctx->opts = *o; else psr_default_opts(&ctx->opts);
     psr_opts& op = ctx->opts;
     if (op.restart < 1 || op.restart > 32 || op.maxit < 1 || !(op.rtol > 0.0) || op.tol < 0.0 ||
-        op.store_prec < 0 || op.store_prec > 2 || op.weighting < 0 || op.weighting > 1 || op.krylov < 0 || op.krylov > 1) {
+        op.store_prec < 0 || op.store_prec > 2 || op.weighting < 0 || op.weighting > 1 || op.krylov < 0 || op.krylov > 1 ||
+        op.sweep_kernel < PSR_SWEEP_AUTO || op.sweep_kernel > PSR_SWEEP_TENSOR) {
         set_error(ctx, "invalid option value");
         destroy_ctx(ctx);
         return PSR_ERR_INVALID_ARG;
@@ -404,6 +405,27 @@ const char* psr_last_error(psr_ctx* ctx) {
 void psr_destroy(psr_ctx* ctx) { destroy_ctx(ctx); }
 
 int64_t psr_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int psr_set_kernel_timing(psr_ctx* ctx, int enable) {
+    if (!ctx) {
+        set_error(nullptr, "ctx is NULL");
+        return PSR_ERR_INVALID_ARG;
+    }
+    return kernel_timing_enable(ctx, enable != 0);
+}
+
+int psr_get_kernel_timing(psr_ctx* ctx, double* ms, int64_t* launches, double* bytes, int count) {
+    if (!ctx || count < 1 || count > PSR_KT_COUNT) {
+        set_error(ctx, "ctx is NULL or count outside 1 .. PSR_KT_COUNT");
+        return PSR_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < count; ++k) {
+        if (ms) ms[k] = ctx->kt_ms[k];
+        if (launches) launches[k] = ctx->kt_n[k];
+        if (bytes) bytes[k] = ctx->kt_bytes[k];
+    }
+    return PSR_OK;
+}
 
 int psr_extract(const psr_csr* A, const psr_patches* P, double* A_out, int32_t* mult_out, double* W_out, void* stream) {
     if (!A || !P || A->n <= 0 || P->n_patches <= 0 || !P->dofs || (P->uniform_size <= 0 && !P->offsets)) {

@@ -32,6 +32,9 @@
 namespace psr {
 
 static constexpr double U64 = 0x1p-53;
+// Probe storage per entry: w_1 at [0, 32), w_2 at [PROBE_W2, PROBE_W2 + 32).
+static constexpr int PROBE_W2 = 32;
+static constexpr int PROBE_STRIDE = 64;
 
 struct RoundDev {
     int next;          // patch that becomes the next entry (smallest unassigned)
@@ -50,8 +53,9 @@ struct WarpScratch {  // per-warp shared memory layout for p <= 32
 };
 
 // Decides d(A_i, B_c) < tol for one candidate.  sAc, sB: shared p x ld.
-// probe (may be NULL): w = B_c^{-1} v / ||v|| for a unit-ish v, so that
-// ||D w|| = ||E v|| / ||v|| <= sigma_max(E) is an O(p^2) lower bound.
+// probe (may be NULL): two vectors w_k = B_c^{-1} v_k / ||v_k|| (at probe and
+// probe + 32), so that ||D w_k|| = ||E v_k|| / ||v_k|| <= sigma_max(E) are
+// O(p^2) lower bounds.
 // Returns 1 accept, 0 reject, -1 undecided (needs the exact path).  *dv gets
 // the deciding value.  All lanes call; lane r handles row r.
 __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, const double* sB,
@@ -61,12 +65,15 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
     const int lane = threadIdx.x & 31;
     const bool act = lane < p;
     // pass 1: D = A_c - A_i, ||D||_F and (D w)_lane
-    double dn2 = 0.0, dw = 0.0;
+    double dn2 = 0.0, dw = 0.0, dw2 = 0.0;
     if (act) {
         for (int j = 0; j < p; ++j) {
             const double d = sAc[lane * ld + j] - Ai[lane * p + j];
             dn2 = fma(d, d, dn2);
-            if (probe) dw = fma(d, probe[j], dw);
+            if (probe) {
+                dw = fma(d, probe[j], dw);
+                dw2 = fma(d, probe[PROBE_W2 + j], dw2);
+            }
         }
     }
     dn2 = warp_sum(dn2);
@@ -80,7 +87,7 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
     }
     if (probe) {
         // w carries its own rounding (B^-1 v computed in FP64): widen by 2 err
-        const double lb1 = sqrt(warp_sum(dw * dw));
+        const double lb1 = fmax(sqrt(warp_sum(dw * dw)), sqrt(warp_sum(dw2 * dw2)));
         if (lb1 * shrink - 2.0 * err >= tol) { *dv = lb1; return 0; }
     }
     if (sB32) {
@@ -262,10 +269,10 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
 }
 
 // ---------------------------------------------------------------- rounds
-// block part: A_c, B^-1 (FP64), probe (32), B^-1 in FP32; then per warp E + v + w
+// block part: A_c, B^-1 (FP64), probes (64), B^-1 in FP32; then per warp E + v + w
 __host__ __device__ inline int eval_block_doubles(int p) {
     const int ld = p + 1;
-    return 2 * p * ld + 32 + (p * ld + 1) / 2;
+    return 2 * p * ld + PROBE_STRIDE + (p * ld + 1) / 2;
 }
 __host__ __device__ inline size_t eval_smem_bytes(int p, int wpb) {
     const int ld = p + 1;
@@ -282,44 +289,74 @@ struct EntryDB {
     double* w;
 };
 
-// Probe vector of an entry: v ~ the dominant right singular vector of B^{-1}
-// (power iteration on B^-T B^-1 from the all-ones vector), w = B^{-1} v / ||v||.
-// Any v gives a valid lower bound ||E v|| <= sigma_max(E); the dominant one
-// makes it tight where B^{-1} amplifies most.  One warp, p <= 32, B with row
-// stride ld (shared or global memory).
-__device__ void probe_vector_warp(const double* B, int p, int ld, double* w_out) {
+// Dominant right singular vector of a p x p matrix M (row stride ld) by power
+// iteration on M^T M from the all-ones vector; lane k returns v_k (unit, or 0
+// when M v vanishes).  One warp, p <= 32: lane r keeps row r of M, the
+// transposed products read M directly, so each step is p fused multiply-adds
+// per lane and no warp reductions besides the normalisation.
+__device__ double dominant_right_sv_warp(const double* M, int p, int ld, int iters) {
     const int lane = threadIdx.x & 31;
     const bool act = lane < p;
-    // lane r keeps row r of B; column sums read B directly (row stride ld), so
-    // each product is p fused multiply-adds per lane and no warp reductions
     double row[32];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) row[k] = (act && k < p) ? B[lane * ld + k] : 0.0;
-    double v = act ? 1.0 : 0.0;                        // lane k holds v_k
-    for (int it = 0; it < 10; ++it) {
-        double t = 0.0;                                // t_lane = (B v)_lane
+    for (int k = 0; k < 32; ++k) row[k] = (act && k < p) ? M[lane * ld + k] : 0.0;
+    double v = act ? 1.0 : 0.0;
+    for (int it = 0; it < iters; ++it) {
+        double t = 0.0;                                // t_lane = (M v)_lane
 #pragma unroll
         for (int k = 0; k < 32; ++k) t = fma(row[k], __shfl_sync(0xffffffffu, v, k), t);
-        double u = 0.0;                                // u_lane = (B^T t)_lane
+        double u = 0.0;                                // u_lane = (M^T t)_lane
         for (int r = 0; r < p; ++r) {
             const double tr = __shfl_sync(0xffffffffu, t, r);
-            if (act) u = fma(B[r * ld + lane], tr, u);
+            if (act) u = fma(M[r * ld + lane], tr, u);
         }
         const double nu = sqrt(warp_sum(u * u));
-        if (!(nu > 0.0)) break;
+        if (!(nu > 0.0)) return 0.0;
         v = u / nu;
     }
-    const double nv = sqrt(warp_sum(v * v));
-    double t = 0.0;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) t = fma(row[k], __shfl_sync(0xffffffffu, v, k), t);
-    w_out[lane] = (act && nv > 0.0) ? t / nv : 0.0;
+    return v;
 }
 
-// ||B^{-1}||_F and the probe vector of every matrix of a batch of inverses
-// (one warp each); flags (any_bad, may be NULL) when a singular one is among them.
-__global__ void k_entry_fro(const double* __restrict__ Binv, int m, int p, double* __restrict__ fro,
-                            double* __restrict__ w, const int32_t* __restrict__ sflags,
+// y_lane = (M x)_lane for a lane-held x (row stride ld); all lanes call.
+__device__ __forceinline__ double matvec_warp(const double* M, int p, int ld, double x) {
+    const int lane = threadIdx.x & 31;
+    double t = 0.0;
+    for (int k = 0; k < p; ++k) {
+        const double xk = __shfl_sync(0xffffffffu, x, k);
+        if (lane < p) t = fma(M[lane * ld + k], xk, t);
+    }
+    return t;
+}
+
+// Probe vectors of an entry, both of the form w = B^{-1} v / ||v||, so that
+// ||D w|| = ||E v|| / ||v|| <= sigma_max(E) for any v:
+//   w_1: v = the dominant right singular vector of B^{-1} (tight where B^{-1}
+//        amplifies most);
+//   w_2: v = A x / ||A x|| with x the dominant right singular vector of A, so
+//        w_2 ~ x / sigma_max(A) and ||D w_2|| ~ ||D x|| / ||A x|| (tight where
+//        D acts like a multiple of A away from A's near-kernel, e.g. a scaled
+//        coefficient, which w_1 misses when that near-kernel is D's kernel).
+__device__ void probe_vectors_warp(const double* A, const double* B, int p, int ld, double* w_out) {
+    const int lane = threadIdx.x & 31;
+    const bool act = lane < p;
+    double v = dominant_right_sv_warp(B, p, ld, 10);
+    double nv = sqrt(warp_sum(v * v));
+    double t = matvec_warp(B, p, ld, v);
+    w_out[lane] = (act && nv > 0.0) ? t / nv : 0.0;
+    const double x = dominant_right_sv_warp(A, p, ld, 10);
+    const double ax = matvec_warp(A, p, ld, x);
+    nv = sqrt(warp_sum(ax * ax));
+    t = matvec_warp(B, p, ld, nv > 0.0 ? ax / nv : 0.0);
+    v = nv > 0.0 ? ax / nv : 0.0;
+    nv = sqrt(warp_sum(v * v));
+    w_out[PROBE_W2 + lane] = (act && nv > 0.0) ? t / nv : 0.0;
+}
+
+// ||B^{-1}||_F and the probe vectors of every matrix of a batch (patch
+// matrices A, inverses Binv; one warp each); flags (any_bad, may be NULL)
+// when a singular one is among them.
+__global__ void k_entry_fro(const double* __restrict__ A, const double* __restrict__ Binv, int m, int p,
+                            double* __restrict__ fro, double* __restrict__ w, const int32_t* __restrict__ sflags,
                             int32_t* __restrict__ any_bad) {
     const int lane = threadIdx.x & 31;
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -327,7 +364,7 @@ __global__ void k_entry_fro(const double* __restrict__ Binv, int m, int p, doubl
     double s = 0.0;
     for (int e = lane; e < p * p; e += 32) s = fma(Binv[(int64_t)j * p * p + e], Binv[(int64_t)j * p * p + e], s);
     s = warp_sum(s);
-    probe_vector_warp(Binv + (int64_t)j * p * p, p, p, w + (int64_t)j * 32);
+    probe_vectors_warp(A + (int64_t)j * p * p, Binv + (int64_t)j * p * p, p, p, w + (int64_t)j * PROBE_STRIDE);
     if (lane == 0) {
         fro[j] = sqrt(s);
         if (any_bad && sflags[j]) atomicOr(any_bad, 1);
@@ -370,7 +407,7 @@ __global__ void __launch_bounds__(256, 2) k_round(RoundDev* st, int32_t* __restr
     double* sAc = reinterpret_cast<double*>(smem);
     double* sB = sAc + p * ld;
     double* sw = sB + p * ld;
-    float* sB32 = reinterpret_cast<float*>(sw + 32);
+    float* sB32 = reinterpret_cast<float*>(sw + PROBE_STRIDE);
     double* wbase = reinterpret_cast<double*>(smem) + eval_block_doubles(p) + (size_t)wid * (p * ld + 64);
     WarpScratch ws{wbase, wbase + p * ld, wbase + p * ld + 32};
     const double* a = Ag + (int64_t)i0 * p * p;
@@ -381,7 +418,7 @@ __global__ void __launch_bounds__(256, 2) k_round(RoundDev* st, int32_t* __restr
         sB[(t / p) * ld + (t % p)] = b;
         sB32[(t / p) * ld + (t % p)] = (float)b;
     }
-    if (threadIdx.x < 32) sw[threadIdx.x] = w_all[(int64_t)i0 * 32 + threadIdx.x];
+    if (threadIdx.x < PROBE_STRIDE) sw[threadIdx.x] = w_all[(int64_t)i0 * PROBE_STRIDE + threadIdx.x];
     const double bfro = fro_all[i0];
     __syncthreads();
     unsigned long long my_evals = 0, my_exact = 0;
@@ -427,7 +464,7 @@ __device__ __forceinline__ void stage_seed(EntryDB db, int p, int e, double* sAc
         sAc[(t / p) * ld + (t % p)] = a[t];
         sB[(t / p) * ld + (t % p)] = bm[t];
     }
-    if (threadIdx.x < 32) sw[threadIdx.x] = db.w[(int64_t)e * 32 + threadIdx.x];
+    if (threadIdx.x < PROBE_STRIDE) sw[threadIdx.x] = db.w[(int64_t)e * PROBE_STRIDE + threadIdx.x];
 }
 
 // Seeded Alg. 1: every still unassigned patch compared with seed entry e.
@@ -442,7 +479,7 @@ __global__ void __launch_bounds__(256, 2) k_seed_pass(RoundDev* st, int32_t* __r
     double* sAc = reinterpret_cast<double*>(smem);
     double* sB = sAc + p * ld;
     double* sw = sB + p * ld;
-    float* sB32 = reinterpret_cast<float*>(sw + 32);
+    float* sB32 = reinterpret_cast<float*>(sw + PROBE_STRIDE);
     double* wbase = reinterpret_cast<double*>(smem) + eval_block_doubles(p) + (size_t)wid * (p * ld + 64);
     WarpScratch ws{wbase, wbase + p * ld, wbase + p * ld + 32};
     stage_seed(db, p, e, sAc, sB, sw);
@@ -523,7 +560,7 @@ __global__ void k_verify_hints(RoundDev* st, int32_t* __restrict__ phi, int coun
         }
         __syncwarp();
         double dv;
-        const double* pw = db.w + (int64_t)e * 32;
+        const double* pw = db.w + (int64_t)e * PROBE_STRIDE;
         int dec = decide_pair(Ag + (int64_t)i * p * p, sAc, sB, p, ld, db.fro[e], tol, ws, &dv, false, pw);
         if (dec < 0) {
             dec = decide_pair(Ag + (int64_t)i * p * p, sAc, sB, p, ld, db.fro[e], tol, ws, &dv, true, pw);
@@ -581,7 +618,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         PSR_CUDA(ctx, cudaMalloc(&rep_l, sizeof(int32_t) * cap));
         PSR_CUDA(ctx, cudaMalloc(&sing_all, sizeof(int32_t) * count));
         PSR_CUDA(ctx, cudaMalloc(&fro_all, sizeof(double) * count));
-        PSR_CUDA(ctx, cudaMalloc(&w_all, sizeof(double) * (size_t)count * 32));
+        PSR_CUDA(ctx, cudaMalloc(&w_all, sizeof(double) * (size_t)count * PROBE_STRIDE));
         if (cudaMalloc(&Ball, sizeof(double) * (size_t)count * p * p) != cudaSuccess) {
             cudaGetLastError();
             set_error(ctx, "out of device memory for the patch inverses");
@@ -592,7 +629,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         rc = launch_batched_inverse(Ag, (int64_t)p * p, nullptr, count, p, Ball, (int64_t)p * p, sing_all, s);
         if (rc != PSR_OK) break;
         count_launch();
-        k_entry_fro<<<(count + 7) / 8, 256, 0, s>>>(Ball, count, p, fro_all, w_all, sing_all, nullptr);
+        k_entry_fro<<<(count + 7) / 8, 256, 0, s>>>(Ag, Ball, count, p, fro_all, w_all, sing_all, nullptr);
         RoundDev init{};
         init.first_singular = -1;
         init.m = m0;
@@ -612,7 +649,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
             PSR_CUDA(ctx, cudaMalloc(&db.A, sizeof(double) * (size_t)m0 * p * p));
             PSR_CUDA(ctx, cudaMalloc(&db.Binv, sizeof(double) * (size_t)m0 * p * p));
             PSR_CUDA(ctx, cudaMalloc(&db.fro, sizeof(double) * m0));
-            PSR_CUDA(ctx, cudaMalloc(&db.w, sizeof(double) * (size_t)m0 * 32));
+            PSR_CUDA(ctx, cudaMalloc(&db.w, sizeof(double) * (size_t)m0 * PROBE_STRIDE));
             PSR_CUDA(ctx, cudaMemcpyAsync(db.A, seed_A, sizeof(double) * (size_t)m0 * p * p, cudaMemcpyDeviceToDevice, s));
             int32_t* sflags = nullptr;
             PSR_CUDA(ctx, cudaMalloc(&sflags, sizeof(int32_t) * m0));
@@ -620,7 +657,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
             if (rc != PSR_OK) break;
             PSR_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
             count_launch();
-            k_entry_fro<<<(m0 + 7) / 8, 256, 0, s>>>(db.Binv, m0, p, db.fro, db.w, sflags, flag);
+            k_entry_fro<<<(m0 + 7) / 8, 256, 0, s>>>(db.A, db.Binv, m0, p, db.fro, db.w, sflags, flag);
             std::vector<int32_t> seq(m0, -1);
             PSR_CUDA(ctx, cudaMemcpyAsync(rep_l, seq.data(), sizeof(int32_t) * m0, cudaMemcpyHostToDevice, s));
             int32_t h_bad = 0;

@@ -114,7 +114,29 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ rowptr
         double s = 0.0;
         if (valid) {
             const int rs = rowptr[row], re = rowptr[row + 1];
-            for (int e = rs + sub; e < re; e += TPR) s = fma(vals[e], x[colidx[e]], s);
+            // Four entries per lane per pass with all loads issued before the
+            // first multiply: the index -> x gathers of a row overlap instead
+            // of forming one dependent chain per entry.  The per-lane
+            // summation order (e, e + TPR, e + 2 TPR, ...) is unchanged.
+            for (int e = rs + sub; e < re; e += 4 * TPR) {
+                const bool b1 = e + TPR < re, b2 = e + 2 * TPR < re, b3 = e + 3 * TPR < re;
+                const int c0 = colidx[e];
+                const int c1 = b1 ? colidx[e + TPR] : c0;
+                const int c2 = b2 ? colidx[e + 2 * TPR] : c0;
+                const int c3 = b3 ? colidx[e + 3 * TPR] : c0;
+                const double a0 = vals[e];
+                const double a1 = b1 ? vals[e + TPR] : 0.0;
+                const double a2 = b2 ? vals[e + 2 * TPR] : 0.0;
+                const double a3 = b3 ? vals[e + 3 * TPR] : 0.0;
+                const double x0 = x[c0];
+                const double x1 = b1 ? x[c1] : 0.0;
+                const double x2 = b2 ? x[c2] : 0.0;
+                const double x3 = b3 ? x[c3] : 0.0;
+                s = fma(a0, x0, s);
+                if (b1) s = fma(a1, x1, s);
+                if (b2) s = fma(a2, x2, s);
+                if (b3) s = fma(a3, x3, s);
+            }
         }
 #pragma unroll
         for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, TPR);
@@ -411,9 +433,10 @@ __global__ void k_fg_update(double* __restrict__ x, const double* __restrict__ Z
 // ---------------------------------------------------------------- host
 static int spmv_tpr(psr_ctx* ctx) {
     const double avg = ctx->n ? (double)ctx->nnz / ctx->n : 1.0;
-    if (avg <= 6) return 4;
-    if (avg <= 12) return 8;
-    if (avg <= 40) return 16;
+    // each lane loads up to four entries per pass
+    if (avg <= 16) return 4;
+    if (avg <= 32) return 8;
+    if (avg <= 64) return 16;
     return 32;
 }
 
@@ -421,9 +444,11 @@ static void launch_spmv(psr_ctx* ctx, const double* x, double* y, const double* 
                         KDims kd, int stop_check, int nb_max, cudaStream_t s) {
     const int tpr = spmv_tpr(ctx);
     const int n = ctx->n;
-    // one row per TPR-thread group, all rows in one pass when the partials fit
+    // one row per TPR-thread group; mode 0 (no reduction) covers all rows in
+    // one pass, the reducing modes keep the grid within the partial slots
     const int rows_per_block = 256 / tpr;
-    const int nb = (int)std::max(1, std::min((n + rows_per_block - 1) / rows_per_block, nb_max));
+    const int need = (n + rows_per_block - 1) / rows_per_block;
+    const int nb = std::max(1, mode == 0 ? need : std::min(need, nb_max));
     switch (tpr) {
         case 4: count_launch(); k_spmv<4><<<nb, 256, 0, s>>>(ctx->rowptr, ctx->colidx, ctx->vals, x, y, b, n, mode, kd, stop_check, fin); break;
         case 8: count_launch(); k_spmv<8><<<nb, 256, 0, s>>>(ctx->rowptr, ctx->colidx, ctx->vals, x, y, b, n, mode, kd, stop_check, fin); break;
@@ -431,6 +456,74 @@ static void launch_spmv(psr_ctx* ctx, const double* x, double* y, const double* 
         default: count_launch(); k_spmv<32><<<nb, 256, 0, s>>>(ctx->rowptr, ctx->colidx, ctx->vals, x, y, b, n, mode, kd, stop_check, fin); break;
     }
 }
+
+// ---------------------------------------------------------------- timing
+// Per-kernel event marks (psr_set_kernel_timing).  Marks are recorded while a
+// block is enqueued (or captured: the event records become graph nodes) and
+// read back after the host's per-block synchronisation.
+static double sweep_bytes(const psr_ctx* ctx) {
+    const double tot = ctx->h_offsets.empty() ? 0.0 : (double)ctx->h_offsets.back();
+    return 24.0 * ctx->n + 4.0 * tot + 4.0 * ctx->n_patches + (double)ctx->stats.factor_bytes;
+}
+static double spmv_bytes(const psr_ctx* ctx) {
+    return 12.0 * (double)ctx->nnz + 4.0 * (ctx->n + 1.0) + 16.0 * ctx->n;
+}
+
+// While the stream is captured the record becomes an event-record node of
+// the graph (external flag); otherwise it is a plain record.
+static cudaError_t kt_record(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(s, &st);
+    if (ce != cudaSuccess) return ce;
+    return st == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                                               : cudaEventRecord(e, s);
+}
+
+static int kt_begin(psr_ctx* ctx, int kind, int j, double bytes, cudaStream_t s) {
+    if (!ctx->kt_on) return PSR_OK;
+    const size_t i = ctx->kt_marks.size();
+    while (ctx->kt_ev.size() < 2 * i + 2) {
+        cudaEvent_t e;
+        PSR_CUDA(ctx, cudaEventCreate(&e));
+        ctx->kt_ev.push_back(e);
+    }
+    ctx->kt_marks.push_back(KtMark{kind, j, bytes});
+    PSR_CUDA(ctx, kt_record(ctx->kt_ev[2 * i], s));
+    return PSR_OK;
+}
+
+static int kt_end(psr_ctx* ctx, cudaStream_t s) {
+    if (!ctx->kt_on) return PSR_OK;
+    const size_t i = ctx->kt_marks.size() - 1;
+    PSR_CUDA(ctx, kt_record(ctx->kt_ev[2 * i + 1], s));
+    return PSR_OK;
+}
+
+// After a block ran `done` iterations (all its events have completed).
+static int kt_collect(psr_ctx* ctx, int done) {
+    if (!ctx->kt_on) return PSR_OK;
+    for (size_t i = 0; i < ctx->kt_marks.size(); ++i) {
+        const KtMark& mk = ctx->kt_marks[i];
+        if (mk.j >= done) continue;
+        float ms = 0.f;
+        PSR_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->kt_ev[2 * i], ctx->kt_ev[2 * i + 1]));
+        ctx->kt_ms[mk.kind] += ms;
+        ctx->kt_n[mk.kind] += 1;
+        ctx->kt_bytes[mk.kind] += mk.bytes;
+    }
+    return PSR_OK;
+}
+
+#define KT_BEGIN(kind, j, bytes)                                   \
+    do {                                                           \
+        int rk_ = kt_begin(ctx, (kind), (j), (bytes), s);          \
+        if (rk_ != PSR_OK) return rk_;                             \
+    } while (0)
+#define KT_END()                                                   \
+    do {                                                           \
+        int rk_ = kt_end(ctx, s);                                  \
+        if (rk_ != PSR_OK) return rk_;                             \
+    } while (0)
 
 int krylov_alloc(psr_ctx* ctx) {
     KrylovWS& w = ctx->ws;
@@ -468,19 +561,46 @@ void krylov_free(psr_ctx* ctx) {
     w = KrylovWS{};
     if (ctx->g_cycle) cudaGraphExecDestroy(ctx->g_cycle);
     ctx->g_cycle = nullptr;
+    for (cudaEvent_t e : ctx->kt_ev) cudaEventDestroy(e);
+    ctx->kt_ev.clear();
+    ctx->kt_marks.clear();
+}
+
+int kernel_timing_enable(psr_ctx* ctx, bool on) {
+    if (ctx->g_cycle) cudaGraphExecDestroy(ctx->g_cycle);
+    ctx->g_cycle = nullptr;
+    ctx->kt_marks.clear();
+    ctx->kt_on = on;
+    for (int k = 0; k < PSR_KT_COUNT; ++k) {
+        ctx->kt_ms[k] = 0.0;
+        ctx->kt_n[k] = 0;
+        ctx->kt_bytes[k] = 0.0;
+    }
+    return PSR_OK;
 }
 
 // One enqueued block of work that the host repeats until the stop flag is set.
 static int enqueue_cg_block(psr_ctx* ctx, KDims kd, int iters, cudaStream_t s) {
     KrylovWS& w = ctx->ws;
     const int n = ctx->n, nb = w.nblk;
+    const double vb = 8.0 * n;
     for (int t = 0; t < iters; ++t) {
+        KT_BEGIN(PSR_KT_SPMV, t, spmv_bytes(ctx));
         launch_spmv(ctx, w.p, w.q, nullptr, 2, 1, kd, 1, w.nspmv, s);
+        KT_END();
+        KT_BEGIN(PSR_KT_VEC, t, 6 * vb);
         count_launch(); k_cg_xr<<<nb, 256, 0, s>>>(w.x, w.r, w.p, w.q, n, kd);
+        KT_END();
+        KT_BEGIN(PSR_KT_SWEEP, t, sweep_bytes(ctx));
         int rc = sweep_apply_ex(ctx, w.r, w.z, kd.ictl + I_STOP, s);
         if (rc != PSR_OK) return rc;
+        KT_END();
+        KT_BEGIN(PSR_KT_VEC, t, 2 * vb);
         count_launch(); k_dot<<<nb, 256, 0, s>>>(w.r, w.z, n, kd, 2);
+        KT_END();
+        KT_BEGIN(PSR_KT_VEC, t, 3 * vb);
         count_launch(); k_cg_p<<<nb, 256, 0, s>>>(w.p, w.z, n, kd);
+        KT_END();
     }
     PSR_CHECK_LAUNCH(ctx, "CG block");
     return PSR_OK;
@@ -494,15 +614,26 @@ static int enqueue_fg_cycle(psr_ctx* ctx, KDims kd, cudaStream_t s) {
         double* Vj = w.V + (size_t)j * n;
         double* Vn = w.V + (size_t)(j + 1) * n;
         double* Zj = w.Z + (size_t)j * n;
+        const double vb = 8.0 * n;
+        KT_BEGIN(PSR_KT_SWEEP, j, sweep_bytes(ctx));
         int rc = sweep_apply_ex(ctx, Vj, Zj, kd.ictl + I_STOP, s);
         if (rc != PSR_OK) return rc;
+        KT_END();
+        KT_BEGIN(PSR_KT_SPMV, j, spmv_bytes(ctx));
         launch_spmv(ctx, Zj, Vn, nullptr, 0, 0, kd, 1, w.nspmv, s);
+        KT_END();
         const int mb = std::max(1, std::min((n + MDOT_THREADS - 1) / MDOT_THREADS, MDOT_BLOCKS));
-        count_launch(); k_mdot<<<mb, MDOT_THREADS, 0, s>>>(w.V, Vn, n, j, kd, 0);
-        count_launch(); k_maxpy<<<nb, 256, 0, s>>>(w.V, Vn, n, j, kd, 0);
-        count_launch(); k_mdot<<<mb, MDOT_THREADS, 0, s>>>(w.V, Vn, n, j, kd, 1);
-        count_launch(); k_maxpy<<<nb, 256, 0, s>>>(w.V, Vn, n, j, kd, 1);
+        for (int pass = 0; pass < 2; ++pass) {
+            KT_BEGIN(PSR_KT_MDOT, j, (j + 2) * vb);
+            count_launch(); k_mdot<<<mb, MDOT_THREADS, 0, s>>>(w.V, Vn, n, j, kd, pass);
+            KT_END();
+            KT_BEGIN(PSR_KT_MAXPY, j, (j + 3) * vb);
+            count_launch(); k_maxpy<<<nb, 256, 0, s>>>(w.V, Vn, n, j, kd, pass);
+            KT_END();
+        }
+        KT_BEGIN(PSR_KT_VEC, j, 2 * vb);
         count_launch(); k_fg_scale<<<nb, 256, 0, s>>>(Vn, n, kd);
+        KT_END();
     }
     count_launch(); k_fg_solve<<<1, 32, 0, s>>>(kd);
     count_launch(); k_fg_update<<<nb, 256, 0, s>>>(w.x, w.Z, n, kd);
@@ -547,6 +678,7 @@ int krylov_solve(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_s
         PSR_CUDA(ctx, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         cudaGraph_t g;
         PSR_CUDA(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        ctx->kt_marks.clear();
         set_capturing(true);
         int rc = cg ? enqueue_cg_block(ctx, kd, block, cs) : enqueue_fg_cycle(ctx, kd, cs);
         set_capturing(false);
@@ -572,16 +704,21 @@ int krylov_solve(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_s
     }
     const int max_blocks = cg ? (ctx->opts.maxit + block - 1) / block + 2 : ctx->opts.maxit + 2;
     int rc = PSR_OK;
+    int it_before = 0;
     for (int it = 0; it < max_blocks; ++it) {
         if (ctx->g_cycle) {
             PSR_CUDA(ctx, cudaGraphLaunch(ctx->g_cycle, s));
             count_launch(ctx->graph_block);
         } else {
+            ctx->kt_marks.clear();
             rc = cg ? enqueue_cg_block(ctx, kd, block, s) : enqueue_fg_cycle(ctx, kd, s);
             if (rc != PSR_OK) break;
         }
         PSR_CUDA(ctx, cudaMemcpyAsync(hstop, w.ictl, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         PSR_CUDA(ctx, cudaStreamSynchronize(s));
+        rc = kt_collect(ctx, hstop[I_IT] - it_before);
+        if (rc != PSR_OK) break;
+        it_before = hstop[I_IT];
         if (hstop[I_STOP]) break;
     }
     if (rc != PSR_OK) { cudaFreeHost(hstop); return rc; }

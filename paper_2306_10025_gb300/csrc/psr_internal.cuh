@@ -111,6 +111,15 @@ struct KrylovWS {
     int nspmv = 0;
 };
 
+// One timed launch of the solve: class, iteration inside the enqueued block
+// (the launch did work iff the block ran more than j iterations) and its
+// algorithmic bytes.  Events 2i and 2i+1 of psr_ctx::kt_ev bracket mark i.
+struct KtMark {
+    int kind;
+    int j;
+    double bytes;
+};
+
 }  // namespace psr
 
 struct psr_ctx {
@@ -151,6 +160,13 @@ struct psr_ctx {
     int32_t* gcounter = nullptr;  // work counter for the persistent sweep
     int sweep_mode = PSR_SWEEP_PERGROUP;
     int grouped_blocks = 0;
+    // per-kernel timing of the solve (psr_set_kernel_timing)
+    bool kt_on = false;
+    std::vector<cudaEvent_t> kt_ev;       // two per mark
+    std::vector<psr::KtMark> kt_marks;    // marks of the enqueued block / captured graph
+    double kt_ms[PSR_KT_COUNT] = {};
+    int64_t kt_n[PSR_KT_COUNT] = {};
+    double kt_bytes[PSR_KT_COUNT] = {};
 };
 
 namespace psr {
@@ -197,5 +213,6 @@ int launch_sweep_tc(const int32_t* tiles, int ntiles, int p, const __nv_bfloat16
 int krylov_alloc(psr_ctx* ctx);
 int krylov_solve(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_solve_info* info);
 void krylov_free(psr_ctx* ctx);
+int kernel_timing_enable(psr_ctx* ctx, bool on);
 
 }  // namespace psr

@@ -399,8 +399,19 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<int32_t>& h_dofs,
             factor_bytes += ne * 4;
         } else {
             // BF16: clustered groups go to the tensor cores (entries stored in
-            // the MMA operand layout); full storage stays on the SIMT path.
-            G.tc = (G.m < G.count);
+            // the MMA operand layout) when their 128-patch tiles are at least
+            // a quarter full on average: a tile costs the same MMA work
+            // whatever its fill.  Full storage and weakly clustered groups
+            // stay on the SIMT path.
+            int64_t tc_tiles = 0;
+            for (int i = 0; i < count;) {
+                int j = i;
+                while (j < count && hs[j] == hs[i]) ++j;
+                tc_tiles += (j - i + 127) / 128;
+                i = j;
+            }
+            G.tc = (G.m < G.count) &&
+                   ((int64_t)count * 4 >= tc_tiles * 128 || ctx->opts.sweep_kernel == PSR_SWEEP_TENSOR);
             if (G.tc) {
                 __nv_bfloat16* bt = nullptr;
                 int rc = convert_tc(db64, G.m, p, ctx->opts.symmetrize, &bt, s);
@@ -456,6 +467,8 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<int32_t>& h_dofs,
         PSR_CUDA(ctx, cudaMemcpy(ctx->rep_ids, rep_global.data(), sizeof(int32_t) * rep_global.size(), cudaMemcpyHostToDevice));
     ctx->stats.factor_bytes = factor_bytes;
     ctx->stats.index_bytes = index_bytes;
+    ctx->stats.tc_groups = 0;
+    for (const Group& G : ctx->groups) ctx->stats.tc_groups += G.tc ? 1 : 0;
     ctx->stats.m_p = ctx->m_p;
     int rc = build_grouped_tables(ctx);
     if (rc != PSR_OK) return rc;
@@ -464,6 +477,7 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<int32_t>& h_dofs,
     ctx->grouped_blocks = 152 * 2;
     int mode = ctx->opts.sweep_kernel;
     if (mode == PSR_SWEEP_AUTO) mode = (ctx->groups.size() > 1) ? PSR_SWEEP_GROUPED : PSR_SWEEP_PERGROUP;
+    if (mode == PSR_SWEEP_TENSOR) mode = PSR_SWEEP_PERGROUP;
     ctx->sweep_mode = mode;
     return PSR_OK;
 }

@@ -1,0 +1,93 @@
+"""Per-kernel timing of the outer solve (instrumentation): it must not change
+the solve's results, and it counts exactly the launches that did work, with
+the algorithmic bytes stated in the header."""
+import numpy as np
+import pytest
+
+import problems as P
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2306_10025_gb300 as L
+    return L
+
+
+def dev(a, dt):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+
+
+def setup_ctx(lib, pr, **kw):
+    rp, ci, va = (dev(pr.rowptr, torch.int32), dev(pr.colidx, torch.int32), dev(pr.vals, torch.float64))
+    return lib.psr_setup(rp, ci, va, dev(pr.patch_dofs, torch.int32), uniform_size=pr.uniform_size,
+                         opts=lib.make_opts(**kw))
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_fgmres_timing_counts_and_bytes(lib, graph):
+    pr = P.stokes2d_q2q1(8)
+    maxit, m = 45, 30
+    ctx = setup_ctx(lib, pr, tol=0.0, weighting="left", krylov="fgmres", restart=m, maxit=maxit, use_graph=graph)
+    b = dev(pr.rhs(0), torch.float64)
+    x0 = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
+    i0 = ctx.solve(b, x0)
+    h0 = ctx.history()
+    ctx.set_kernel_timing(True)
+    x1 = torch.zeros_like(x0)
+    i1 = ctx.solve(b, x1)
+    kt = ctx.kernel_timing()
+    # identical results with the event marks in place
+    assert i0["iterations"] == i1["iterations"] == maxit
+    assert np.array_equal(h0, ctx.history())
+    assert torch.equal(x0, x1)
+    its = i1["iterations"]
+    assert kt["sweep"][1] == its and kt["spmv"][1] == its
+    assert kt["mdot"][1] == 2 * its and kt["maxpy"][1] == 2 * its and kt["vec"][1] == its
+    for name, (ms, cnt, by) in kt.items():
+        assert ms > 0.0 and by > 0.0, name
+    n = pr.n
+    js = list(range(m)) + list(range(maxit - m))          # iterations j of each cycle
+    assert kt["mdot"][2] == pytest.approx(2 * sum(8.0 * (j + 2) * n for j in js), rel=1e-12)
+    assert kt["maxpy"][2] == pytest.approx(2 * sum(8.0 * (j + 3) * n for j in js), rel=1e-12)
+    assert kt["spmv"][2] == pytest.approx(its * (12.0 * pr.nnz + 4.0 * (n + 1) + 16.0 * n), rel=1e-12)
+    # disabling resets nothing but stops the marks; re-enabling resets
+    ctx.set_kernel_timing(False)
+    ctx.solve(b, x1)
+    assert ctx.kernel_timing()["mdot"][1] == 2 * its
+    ctx.set_kernel_timing(True)
+    assert all(v[1] == 0 for v in ctx.kernel_timing().values())
+    ctx.destroy()
+
+
+def test_cg_timing_counts(lib):
+    pr = P.poisson2d_q2(12)
+    ctx = setup_ctx(lib, pr, tol=0.0, weighting="sym", krylov="cg")
+    b = dev(pr.rhs(0), torch.float64)
+    x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
+    ctx.set_kernel_timing(True)
+    info = ctx.solve(b, x)
+    kt = ctx.kernel_timing()
+    its = info["iterations"]
+    assert info["converged"] and its > 8
+    # every iteration runs its SpMV and x/r update; the convergence test in the
+    # last one stops the sweep, dot and p update of that iteration early, but
+    # they are still launched inside the last block and counted
+    assert kt["spmv"][1] == its and kt["sweep"][1] == its and kt["vec"][1] == 3 * its
+    assert kt["mdot"][1] == 0 and kt["maxpy"][1] == 0
+    ctx.destroy()
+
+
+def test_kernel_timing_rejects_bad_args(lib):
+    pr = P.poisson2d_q2(4)
+    ctx = setup_ctx(lib, pr, tol=0.0, weighting="sym", krylov="cg")
+    L = lib.load()
+    assert L.psr_get_kernel_timing(ctx.h, None, None, None, 0) == -1
+    assert L.psr_get_kernel_timing(ctx.h, None, None, None, 6) == -1
+    assert L.psr_set_kernel_timing(None, 1) == -1
+    ctx.destroy()

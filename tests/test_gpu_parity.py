@@ -271,8 +271,12 @@ def test_apply_bf16_vs_rounded_operator(lib, case):
     else:
         pr, tol, w = P.poisson2d_q2(8), 0.0, "sym"
     st = O.setup(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d(), tol)
-    ctx = setup_ctx(lib, pr, tol=tol, store_prec="bf16", weighting=w, krylov=pr.krylov)
+    # these small clustered cases fill their 128-patch tiles too little for the
+    # automatic choice: force the tensor-core path
+    kern = "auto" if case == "full_simt" else "tensor"
+    ctx = setup_ctx(lib, pr, tol=tol, store_prec="bf16", weighting=w, krylov=pr.krylov, sweep_kernel=kern)
     assert ctx.stats()["m_p"] == len(st["reps"])
+    assert ctx.stats()["tc_groups"] == (0 if case == "full_simt" else 1)
     g = np.random.default_rng(11)
     for _ in range(2):
         r = g.standard_normal(pr.n)
@@ -286,6 +290,17 @@ def test_apply_bf16_vs_rounded_operator(lib, case):
         assert np.abs(z.cpu().numpy() - z64).max() / np.abs(z64).max() < 3e-2
 
 
+def test_bf16_auto_picks_tensor_cores_by_tile_fill(lib):
+    """AUTO puts a clustered BF16 group on the tensor cores only when its
+    128-patch tiles are at least a quarter full (poisson 32x32 at tol 1e-12:
+    9 entries, 16 tiles, fill 1/2); a weakly clustered group (Nedelec 4^3 at
+    tol 1: 31 entries for 64 patches) stays on the SIMT path."""
+    ctx = setup_ctx(lib, P.poisson2d_q2(32), tol=1e-12, store_prec="bf16", weighting="sym", krylov="cg")
+    assert ctx.stats()["m_p"] == 9 and ctx.stats()["tc_groups"] == 1
+    ctx = setup_ctx(lib, P.nedelec3d(4, seed=5), tol=1.0, store_prec="bf16", weighting="sym", krylov="cg")
+    assert ctx.stats()["tc_groups"] == 0
+
+
 def test_bf16_pcg_converges_close_to_fp64(lib):
     """CG with the BF16 tensor-core operator (a fixed SPD operator) converges;
     iteration count within a few of the FP64 form."""
@@ -293,7 +308,9 @@ def test_bf16_pcg_converges_close_to_fp64(lib):
     b = dev(pr.rhs(0), torch.float64)
     its = {}
     for prec in ("fp64", "bf16"):
-        ctx = setup_ctx(lib, pr, tol=1e-12, store_prec=prec, weighting="sym", krylov="cg")
+        ctx = setup_ctx(lib, pr, tol=1e-12, store_prec=prec, weighting="sym", krylov="cg",
+                        sweep_kernel="tensor" if prec == "bf16" else "auto")
+        assert ctx.stats()["tc_groups"] == (1 if prec == "bf16" else 0)
         x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
         info = ctx.solve(b, x)
         assert info["converged"]
