@@ -269,10 +269,11 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
 }
 
 // ---------------------------------------------------------------- rounds
-// block part: A_c, B^-1 (FP64), probes (64), B^-1 in FP32; then per warp E + v + w
+// block part: A_c, B^-1 (FP64), probes (64), entry sketch (SK 32 + 8),
+// B^-1 in FP32; then per warp E + v + w
 __host__ __device__ inline int eval_block_doubles(int p) {
     const int ld = p + 1;
-    return 2 * p * ld + PROBE_STRIDE + (p * ld + 1) / 2;
+    return 2 * p * ld + PROBE_STRIDE + 2 * 32 + 8 + (p * ld + 1) / 2;
 }
 __host__ __device__ inline size_t eval_smem_bytes(int p, int wpb) {
     const int ld = p + 1;
@@ -371,6 +372,132 @@ __global__ void k_entry_fro(const double* __restrict__ A, const double* __restri
     }
 }
 
+// ---------------------------------------------------------------- sketches
+// Certified thread-level screen.  For any x and v = A_c x:
+//   ||E||_2 >= ||E v|| / ||v||,   E v = D B^ A_c x = D x + D (B^ A_c - I) x,
+// so ||E||_2 >= (||D x|| - ||D||_2 rho_c ||x||) / ||A_c x|| with rho_c an
+// upper bound of ||B^ A_c - I||_2 (B^ the computed inverse).  D x = A_c x -
+// A_i x comes from sketches y_i = fl(A_i x_k) kept for every patch and a few
+// fixed unit directions x_k per size group; ||D||_2 <= ||A_c||_F + ||A_i||_F.
+// The rounding of the sketches (|fl(A x) - A x| <= gamma_p |A||x|), of the
+// norms and of the residual is added to the slack.  Rejecting a pair this way
+// reads SK p values of the candidate instead of its p^2 entries.
+constexpr int SK = 2;              // sketch directions per size group
+struct SketchDB {
+    const double* X;               // [SK][32] unit directions (zero beyond p)
+    const double* Y;               // [count][SK][p] y_i = fl(A_i x_k)
+    const double* fa;              // [count] ||A_i||_F
+    const double* rho;             // [count] bound of ||B_i^ A_i - I||_2
+};
+
+__device__ __forceinline__ double gamma_u(int k) { return (double)k * U64 / (1.0 - (double)k * U64); }
+
+// Directions of a size group: x_0 = the dominant right singular vector of
+// the group's middle patch, x_1 = a fixed alternating vector; both unit.
+__global__ void k_sketch_dirs(const double* __restrict__ Ag, int count, int p, double* __restrict__ X) {
+    const int lane = threadIdx.x & 31;
+    const int k = threadIdx.x >> 5;
+    const bool act = lane < p;
+    double v;
+    if (k == 0) {
+        v = dominant_right_sv_warp(Ag + (int64_t)(count / 2) * p * p, p, p, 20);
+    } else {
+        v = act ? ((lane & 1) ? -1.0 : 1.0) * (1.0 + (double)(lane % 3)) : 0.0;
+    }
+    double nv = sqrt(warp_sum(v * v));
+    if (!(nv > 0.0)) {                 // degenerate: fall back to e_0
+        v = (lane == 0) ? 1.0 : 0.0;
+        nv = 1.0;
+    }
+    X[k * 32 + lane] = act ? v / nv : 0.0;
+}
+
+// Per matrix of a batch (one warp each): y_k = fl(A x_k), ||A||_F and the
+// residual bound rho >= ||B^ A - I||_2 with B^ = Binv.
+__global__ void __launch_bounds__(256) k_sketch(const double* __restrict__ A, const double* __restrict__ Binv,
+                                                int count, int p, const double* __restrict__ X,
+                                                double* __restrict__ Y, double* __restrict__ fa,
+                                                double* __restrict__ rho) {
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= count) return;                            // warp-uniform
+    const bool act = lane < p;
+    const double* Ai = A + (int64_t)i * p * p;
+    const double* Bi = Binv + (int64_t)i * p * p;
+    double a[32], b[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        a[j] = (act && j < p) ? Ai[lane * p + j] : 0.0;
+        b[j] = (act && j < p) ? Bi[lane * p + j] : 0.0;
+    }
+    double fa2 = 0.0, fb2 = 0.0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        fa2 = fma(a[j], a[j], fa2);
+        fb2 = fma(b[j], b[j], fb2);
+    }
+#pragma unroll
+    for (int k = 0; k < SK; ++k) {
+        double y = 0.0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) y = fma(a[j], X[k * 32 + j], y);
+        if (act) Y[((int64_t)i * SK + k) * p + lane] = y;
+    }
+    // column j of B^ A: lane r sums b[r][k] A[k][j], A[k][j] from lane k
+    double res2 = 0.0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        if (j < p) {
+            double t = 0.0;
+#pragma unroll
+            for (int k = 0; k < 32; ++k) t = fma(b[k], __shfl_sync(0xffffffffu, a[j], k), t);
+            const double r = t - ((lane == j) ? 1.0 : 0.0);
+            if (act) res2 = fma(r, r, res2);
+        }
+    }
+    fa2 = warp_sum(fa2);
+    fb2 = warp_sum(fb2);
+    res2 = warp_sum(res2);
+    if (lane == 0) {
+        const double fA = sqrt(fa2), fB = sqrt(fb2);
+        fa[i] = fA;
+        // computed residual entries carry at most gamma_{p+1} |B^||A| error
+        rho[i] = 1.01 * sqrt(res2) + 1.01 * gamma_u(p + 1) * fB * fA;
+    }
+}
+
+// Entry side of the screen, staged in shared memory: y_c (SK p) and the
+// denominators den_k >= ||A_c x_k||.
+__device__ __forceinline__ void stage_sketch(const double* __restrict__ Yc, double fc, int p, double* sy,
+                                             double* sden) {
+    for (int t = threadIdx.x; t < SK * p; t += blockDim.x) sy[t] = Yc[t];
+    __syncthreads();
+    if (threadIdx.x < SK) {
+        double n2 = 0.0;
+        for (int r = 0; r < p; ++r) n2 = fma(sy[threadIdx.x * p + r], sy[threadIdx.x * p + r], n2);
+        sden[threadIdx.x] = sqrt(n2) * (1.0 + (double)(p + 2) * U64) + 1.01 * gamma_u(p) * fc;
+    }
+}
+
+// Thread-level decision for candidate i against the staged entry: true when
+// the certified lower bound reaches tol (reject).
+__device__ __forceinline__ bool sketch_rejects(const double* __restrict__ yi, double fi, const double* sy,
+                                               const double* sden, double fc, double rhoc, int p, double tol) {
+    const double slack = 1.01 * (fc + fi) * (gamma_u(p) + rhoc);
+    double lb = 0.0;
+#pragma unroll
+    for (int k = 0; k < SK; ++k) {
+        double d2 = 0.0;
+        for (int r = 0; r < p; ++r) {
+            const double d = sy[k * p + r] - yi[k * p + r];
+            d2 = fma(d, d, d2);
+        }
+        const double num = sqrt(d2) * (1.0 - (double)(p + 8) * U64) - slack * (1.0 + 8.0 * U64);
+        if (sden[k] > 0.0) lb = fmax(lb, num / sden[k]);
+    }
+    return lb * (1.0 - 8.0 * U64) >= tol;
+}
+
 __device__ __forceinline__ bool round_last_block(int* ticket) {
     __shared__ int s_last;
     __threadfence();
@@ -395,7 +522,7 @@ __global__ void __launch_bounds__(256, 2) k_round(RoundDev* st, int32_t* __restr
                                                  const double* __restrict__ Ag, int p,
                                                  const double* __restrict__ Ball, const double* __restrict__ fro_all,
                                                  const double* __restrict__ w_all, const int32_t* __restrict__ sing_all,
-                                                 double tol, int32_t* __restrict__ rep_local) {
+                                                 SketchDB sk, double tol, int32_t* __restrict__ rep_local) {
     extern __shared__ __align__(16) unsigned char smem[];
     if (st->done) return;
     const int ld = p + 1;
@@ -407,7 +534,9 @@ __global__ void __launch_bounds__(256, 2) k_round(RoundDev* st, int32_t* __restr
     double* sAc = reinterpret_cast<double*>(smem);
     double* sB = sAc + p * ld;
     double* sw = sB + p * ld;
-    float* sB32 = reinterpret_cast<float*>(sw + PROBE_STRIDE);
+    double* sy = sw + PROBE_STRIDE;
+    double* sden = sy + SK * 32;
+    float* sB32 = reinterpret_cast<float*>(sden + 8);
     double* wbase = reinterpret_cast<double*>(smem) + eval_block_doubles(p) + (size_t)wid * (p * ld + 64);
     WarpScratch ws{wbase, wbase + p * ld, wbase + p * ld + 32};
     const double* a = Ag + (int64_t)i0 * p * p;
@@ -420,23 +549,40 @@ __global__ void __launch_bounds__(256, 2) k_round(RoundDev* st, int32_t* __restr
     }
     if (threadIdx.x < PROBE_STRIDE) sw[threadIdx.x] = w_all[(int64_t)i0 * PROBE_STRIDE + threadIdx.x];
     const double bfro = fro_all[i0];
+    const double fc = sk.fa[i0], rhoc = sk.rho[i0];
+    stage_sketch(sk.Y + (int64_t)i0 * SK * p, fc, p, sy, sden);
     __syncthreads();
     unsigned long long my_evals = 0, my_exact = 0;
     int my_min = count;
     const int nw = gridDim.x * wpb;
-    for (int cand = i0 + 1 + blockIdx.x * wpb + wid; cand < count; cand += nw) {
-        if (phi[cand] != -1) continue;                 // warp-uniform
-        double dv;
-        int dec = decide_pair(Ag + (int64_t)cand * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, false, sw, sB32);
-        if (dec < 0) {
-            dec = decide_pair(Ag + (int64_t)cand * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, true, sw, nullptr);
-            ++my_exact;
+    // a warp takes 32 consecutive candidates: every lane screens its own with
+    // the sketch bound, the survivors run the warp-wide decision one by one
+    for (int base = i0 + 1 + (blockIdx.x * wpb + wid) * 32; base < count; base += nw * 32) {
+        const int cand = base + lane;
+        const bool open = cand < count && phi[cand] == -1;
+        bool rej = false;
+        if (open) rej = sketch_rejects(sk.Y + (int64_t)cand * SK * p, sk.fa[cand], sy, sden, fc, rhoc, p, tol);
+        if (open && rej) my_min = min(my_min, cand);
+        const unsigned opened = __ballot_sync(0xffffffffu, open);
+        unsigned todo = __ballot_sync(0xffffffffu, open && !rej);
+        my_evals += __popc(opened);
+        while (todo) {
+            const int l = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int c2 = base + l;
+            double dv;
+            int dec = decide_pair(Ag + (int64_t)c2 * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, false, sw, sB32);
+            if (dec < 0) {
+                dec = decide_pair(Ag + (int64_t)c2 * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, true, sw, nullptr);
+                ++my_exact;
+            }
+            if (dec == 1) { if (lane == 0) phi[c2] = m; }
+            else my_min = min(my_min, c2);
+            __syncwarp();
         }
-        ++my_evals;
-        if (dec == 1) { if (lane == 0) phi[cand] = m; }
-        else my_min = min(my_min, cand);
-        __syncwarp();
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) my_min = min(my_min, __shfl_xor_sync(0xffffffffu, my_min, o));
     if (lane == 0) {
         if (my_evals) atomicAdd(&st->evals, my_evals);
         if (my_exact) atomicAdd(&st->exact, my_exact);
@@ -467,10 +613,11 @@ __device__ __forceinline__ void stage_seed(EntryDB db, int p, int e, double* sAc
     if (threadIdx.x < PROBE_STRIDE) sw[threadIdx.x] = db.w[(int64_t)e * PROBE_STRIDE + threadIdx.x];
 }
 
-// Seeded Alg. 1: every still unassigned patch compared with seed entry e.
+// Seeded Alg. 1: every still unassigned patch compared with seed entry e
+// (sketch screen first, as in k_round; skd holds the seed entries' sketches).
 __global__ void __launch_bounds__(256, 2) k_seed_pass(RoundDev* st, int32_t* __restrict__ phi, int count,
-                                                     const double* __restrict__ Ag, int p, EntryDB db, double tol,
-                                                     int e) {
+                                                     const double* __restrict__ Ag, int p, EntryDB db, SketchDB sk,
+                                                     SketchDB skd, double tol, int e) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int ld = p + 1;
     const int lane = threadIdx.x & 31;
@@ -479,27 +626,41 @@ __global__ void __launch_bounds__(256, 2) k_seed_pass(RoundDev* st, int32_t* __r
     double* sAc = reinterpret_cast<double*>(smem);
     double* sB = sAc + p * ld;
     double* sw = sB + p * ld;
-    float* sB32 = reinterpret_cast<float*>(sw + PROBE_STRIDE);
+    double* sy = sw + PROBE_STRIDE;
+    double* sden = sy + SK * 32;
+    float* sB32 = reinterpret_cast<float*>(sden + 8);
     double* wbase = reinterpret_cast<double*>(smem) + eval_block_doubles(p) + (size_t)wid * (p * ld + 64);
     WarpScratch ws{wbase, wbase + p * ld, wbase + p * ld + 32};
     stage_seed(db, p, e, sAc, sB, sw);
     for (int t = threadIdx.x; t < p * p; t += blockDim.x)
         sB32[(t / p) * ld + (t % p)] = (float)db.Binv[(int64_t)e * p * p + t];
     const double bfro = db.fro[e];
+    const double fc = skd.fa[e], rhoc = skd.rho[e];
+    stage_sketch(skd.Y + (int64_t)e * SK * p, fc, p, sy, sden);
     __syncthreads();
     unsigned long long my_evals = 0, my_exact = 0;
     const int nw = gridDim.x * wpb;
-    for (int cand = blockIdx.x * wpb + wid; cand < count; cand += nw) {
-        if (phi[cand] != -1) continue;
-        double dv;
-        int dec = decide_pair(Ag + (int64_t)cand * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, false, sw, sB32);
-        if (dec < 0) {
-            dec = decide_pair(Ag + (int64_t)cand * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, true, sw, nullptr);
-            ++my_exact;
+    for (int base = (blockIdx.x * wpb + wid) * 32; base < count; base += nw * 32) {
+        const int cand = base + lane;
+        const bool open = cand < count && phi[cand] == -1;
+        bool rej = false;
+        if (open) rej = sketch_rejects(sk.Y + (int64_t)cand * SK * p, sk.fa[cand], sy, sden, fc, rhoc, p, tol);
+        const unsigned opened = __ballot_sync(0xffffffffu, open);
+        unsigned todo = __ballot_sync(0xffffffffu, open && !rej);
+        my_evals += __popc(opened);
+        while (todo) {
+            const int l = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int c2 = base + l;
+            double dv;
+            int dec = decide_pair(Ag + (int64_t)c2 * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, false, sw, sB32);
+            if (dec < 0) {
+                dec = decide_pair(Ag + (int64_t)c2 * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, true, sw, nullptr);
+                ++my_exact;
+            }
+            if (lane == 0 && dec == 1) phi[c2] = e;
+            __syncwarp();
         }
-        ++my_evals;
-        if (lane == 0 && dec == 1) phi[cand] = e;
-        __syncwarp();
     }
     if (lane == 0) {
         if (my_evals) atomicAdd(&st->evals, my_evals);
@@ -625,11 +786,29 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
             return PSR_ERR_OOM;
         }
         PSR_CUDA(ctx, cudaMemsetAsync(phi_l, 0xff, sizeof(int32_t) * count, s));
-        // every patch's inverse, norm and probe, batched (any patch may become an entry)
+        // every patch's inverse, norm, probes and sketch, batched (any patch
+        // may become an entry)
         rc = launch_batched_inverse(Ag, (int64_t)p * p, nullptr, count, p, Ball, (int64_t)p * p, sing_all, s);
         if (rc != PSR_OK) break;
         count_launch();
         k_entry_fro<<<(count + 7) / 8, 256, 0, s>>>(Ag, Ball, count, p, fro_all, w_all, sing_all, nullptr);
+        double *skX = nullptr, *skY = nullptr, *skF = nullptr, *skR = nullptr;
+        PSR_CUDA(ctx, cudaMalloc(&skX, sizeof(double) * SK * 32));
+        PSR_CUDA(ctx, cudaMalloc(&skF, sizeof(double) * (size_t)count));
+        PSR_CUDA(ctx, cudaMalloc(&skR, sizeof(double) * (size_t)count));
+        if (cudaMalloc(&skY, sizeof(double) * (size_t)count * SK * p) != cudaSuccess) {
+            cudaGetLastError();
+            set_error(ctx, "out of device memory for the patch sketches");
+            return PSR_ERR_OOM;
+        }
+        count_launch();
+        k_sketch_dirs<<<1, 32 * SK, 0, s>>>(Ag, count, p, skX);
+        count_launch();
+        k_sketch<<<(count + 7) / 8, 256, 0, s>>>(Ag, Ball, count, p, skX, skY, skF, skR);
+        PSR_CHECK_LAUNCH(ctx, "patch sketches");
+        const SketchDB sk{skX, skY, skF, skR};
+        SketchDB skd{skX, nullptr, nullptr, nullptr};
+        double *sdY = nullptr, *sdF = nullptr, *sdR = nullptr;
         RoundDev init{};
         init.first_singular = -1;
         init.m = m0;
@@ -641,8 +820,9 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         const size_t smem_eval = eval_smem_bytes(p, wpb);
         if ((rc = set_smem((const void*)k_round, smem_eval)) != PSR_OK) break;
         if ((rc = set_smem((const void*)k_seed_pass, smem_eval)) != PSR_OK) break;
-        // one warp per candidate: enough warps for every SM, a few candidates each
-        int eval_blocks = (count + wpb - 1) / wpb;
+        // 32 candidates per warp (sketch screen per lane): enough warps for
+        // every SM, a few chunks each
+        int eval_blocks = (count + 32 * wpb - 1) / (32 * wpb);
         if (eval_blocks > 152 * 4) eval_blocks = 152 * 4;
         if (eval_blocks < 1) eval_blocks = 1;
         if (m0 > 0) {
@@ -658,6 +838,12 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
             PSR_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
             count_launch();
             k_entry_fro<<<(m0 + 7) / 8, 256, 0, s>>>(db.A, db.Binv, m0, p, db.fro, db.w, sflags, flag);
+            PSR_CUDA(ctx, cudaMalloc(&sdY, sizeof(double) * (size_t)m0 * SK * p));
+            PSR_CUDA(ctx, cudaMalloc(&sdF, sizeof(double) * (size_t)m0));
+            PSR_CUDA(ctx, cudaMalloc(&sdR, sizeof(double) * (size_t)m0));
+            count_launch();
+            k_sketch<<<(m0 + 7) / 8, 256, 0, s>>>(db.A, db.Binv, m0, p, skX, sdY, sdF, sdR);
+            skd = SketchDB{skX, sdY, sdF, sdR};
             std::vector<int32_t> seq(m0, -1);
             PSR_CUDA(ctx, cudaMemcpyAsync(rep_l, seq.data(), sizeof(int32_t) * m0, cudaMemcpyHostToDevice, s));
             int32_t h_bad = 0;
@@ -683,7 +869,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
             // misses: first match over the seed entries, in creation order
             for (int j = 0; j < m0; ++j) {
                 count_launch();
-                k_seed_pass<<<eval_blocks, wpb * 32, smem_eval, s>>>(st, phi_l, count, Ag, p, db, tol, j);
+                k_seed_pass<<<eval_blocks, wpb * 32, smem_eval, s>>>(st, phi_l, count, Ag, p, db, sk, skd, tol, j);
             }
             PSR_CHECK_LAUNCH(ctx, "seeded Alg. 1 passes");
             // the first new entry is the smallest patch still unassigned
@@ -700,7 +886,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
             for (int r = 0; r < batch; ++r) {
                 count_launch();
                 k_round<<<eval_blocks, wpb * 32, smem_eval, s>>>(st, phi_l, count, Ag, p, Ball, fro_all, w_all,
-                                                                 sing_all, tol, rep_l);
+                                                                 sing_all, sk, tol, rep_l);
             }
             PSR_CHECK_LAUNCH(ctx, "Alg. 1 round kernel");
             issued += batch;
@@ -734,6 +920,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         cudaFree(fro_all);
         cudaFree(w_all);
         cudaFree(sing_all);
+        for (double* q : {skX, skY, skF, skR, sdY, sdF, sdR}) cudaFree(q);
         cudaFree(db.A);
         cudaFree(db.Binv);
         cudaFree(db.fro);

@@ -277,31 +277,24 @@ __global__ void k_fg_start(const double* __restrict__ r, double* __restrict__ V0
     }
 }
 
-// h_i = V_i . w for i <= j (pass 1 -> H column j; pass 2 -> added to it).
-// 512-thread blocks; at most MDOT_BLOCKS partials per vector.
-constexpr int MDOT_THREADS = 512;
-constexpr int MDOT_BLOCKS = 152 * 2;
-__global__ void __launch_bounds__(MDOT_THREADS) k_mdot(const double* __restrict__ V, const double* __restrict__ w, int n,
-                                                       int j, KDims kd, int pass) {
-    __shared__ double sh[32][MDOT_THREADS / 32 + 1];
-    if (kd.ictl[I_STOP]) return;
-    const int nv = j + 1;
-    double acc[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) acc[i] = 0.0;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-        const double we = w[e];
-#pragma unroll
-        for (int i = 0; i < 32; ++i)
-            if (i < nv) acc[i] = fma(V[(int64_t)i * n + e], we, acc[i]);
-    }
+// ---- classical Gram-Schmidt, applied twice (CGS2)
+// The nv = j + 1 basis vectors V_0..V_j are rows of V (stride n).  Kernels are
+// templated on NV >= nv (8, 16 or 32 per-thread accumulators / basis values),
+// run 256-thread blocks on a single-wave grid (kgrid) and reduce per vector
+// deterministically: warp -> block partial -> last block in fixed order.
+constexpr int KT = 256;                 // threads per block of the CGS2 kernels
+
+// acc[i] of every thread -> part[i * gridDim.x + blockIdx.x] (i < nv): the
+// warp sums NV accumulators by recursive halving (at step h a lane keeps the
+// half of the indices picked by its lane bit h and adds its partner's copy,
+// so lane L ends with vector L mod NV), then lanes that differ above bit
+// log2(NV) are added, then the warps of the block in order.
+template <int NV>
+__device__ __forceinline__ void block_partials(double (&acc)[NV], int nv, double* __restrict__ part,
+                                               double (*sh)[KT / 32 + 1]) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    // Reduce the 32 accumulators across the warp by recursive halving: at
-    // each step a lane keeps the half of the vector indices selected by one
-    // of its lane bits and adds its partner's copy of that half, so after 31
-    // shuffles lane L holds the warp total of vector L.
 #pragma unroll
-    for (int h = 16; h >= 1; h >>= 1) {
+    for (int h = NV / 2; h >= 1; h >>= 1) {
         const bool upper = (lane & h) != 0;
 #pragma unroll
         for (int i = 0; i < h; ++i) {
@@ -310,53 +303,119 @@ __global__ void __launch_bounds__(MDOT_THREADS) k_mdot(const double* __restrict_
             acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
         }
     }
-    sh[lane][wid] = acc[0];
+#pragma unroll
+    for (int o = NV; o < 32; o <<= 1) acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
+    if (lane < NV) sh[lane][wid] = acc[0];
     __syncthreads();
     if (threadIdx.x < nv) {
         double t = 0.0;
-        for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) t += sh[threadIdx.x][wv];
-        kd.part[threadIdx.x * gridDim.x + blockIdx.x] = t;
-    }
-    if (!last_block(kd.ictl + I_CNT + 4)) return;
-    // 16 threads per vector (512 threads, <= 32 vectors), fixed order
-    const int m = kd.m;
-    double* H = Hm(kd.scal, m);
-    double* hv = Hv(kd.scal, m);
-    const int i = threadIdx.x >> 4, q = threadIdx.x & 15;
-    double v = (i < nv) ? sum_strided(kd.part + (int64_t)i * gridDim.x, q, gridDim.x, 16) : 0.0;
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, 16);
-    if (i < nv && q == 0) {
-        hv[i] = v;
-        if (pass == 0) H[i * m + j] = v;
-        else H[i * m + j] += v;
+        for (int w = 0; w < KT / 32; ++w) t += sh[threadIdx.x][w];
+        part[threadIdx.x * gridDim.x + blockIdx.x] = t;
     }
 }
 
-// w -= sum_i h_i V_i (h from the last k_mdot); pass 2 also accumulates ||w||^2
-// and finishes the Arnoldi step: H[j+1][j], Givens rotation, residual estimate.
-__global__ void __launch_bounds__(256) k_maxpy(const double* __restrict__ V, double* __restrict__ w, int n, int j,
-                                               KDims kd, int pass) {
-    __shared__ double sh[32];
-    __shared__ double sh_h[33];
+// Last block: total of vector i = threadIdx.x / (KT / NV) over the G block
+// partials, in a fixed order; valid where threadIdx.x % (KT / NV) == 0.
+template <int NV>
+__device__ __forceinline__ double final_partials(const double* __restrict__ part, int nv, int G) {
+    constexpr int T = KT / NV;           // threads per vector, <= 32
+    const int i = threadIdx.x / T, q = threadIdx.x % T;
+    double v = (i < nv) ? sum_strided(part + (int64_t)i * G, q, G, T) : 0.0;
+#pragma unroll
+    for (int o = T / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, T);
+    return v;
+}
+
+// h = V^T w (first pass): H[:, j] = h and h is kept for the update.
+template <int NV>
+__global__ void __launch_bounds__(KT) k_mdot(const double* __restrict__ V, const double* __restrict__ w, int n,
+                                             int j, KDims kd) {
+    __shared__ double sh[NV][KT / 32 + 1];
+    if (kd.ictl[I_STOP]) return;
+    const int nv = j + 1;
+    double acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += gridDim.x * KT) {
+        const double we = w[e];
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+            if (i < nv) acc[i] = fma(V[(int64_t)i * n + e], we, acc[i]);
+    }
+    block_partials<NV>(acc, nv, kd.part, sh);
+    if (!last_block(kd.ictl + I_CNT + 4)) return;
+    const double v = final_partials<NV>(kd.part, nv, gridDim.x);
+    const int i = threadIdx.x / (KT / NV);
+    if (i < nv && threadIdx.x % (KT / NV) == 0) {
+        const int m = kd.m;
+        Hv(kd.scal, m)[i] = v;
+        Hm(kd.scal, m)[i * m + j] = v;
+    }
+}
+
+// First update fused with the second projection: w <- w - V h, then
+// h2 = V^T w on the same loads of V; H[:, j] += h2 and h2 is kept for the
+// second update.
+template <int NV>
+__global__ void __launch_bounds__(KT) k_maxpy_mdot(const double* __restrict__ V, double* __restrict__ w, int n,
+                                                   int j, KDims kd) {
+    __shared__ double sh[NV][KT / 32 + 1];
+    __shared__ double sh_h[NV];
     if (kd.ictl[I_STOP]) return;
     const int nv = j + 1;
     const int m = kd.m;
-    if (threadIdx.x < nv) sh_h[threadIdx.x] = Hv(kd.scal, m)[threadIdx.x];
+    if (threadIdx.x < NV) sh_h[threadIdx.x] = (threadIdx.x < nv) ? Hv(kd.scal, m)[threadIdx.x] : 0.0;
+    __syncthreads();
+    double acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += gridDim.x * KT) {
+        double vi[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) vi[i] = (i < nv) ? V[(int64_t)i * n + e] : 0.0;
+        double we = w[e];
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+            if (i < nv) we = fma(-sh_h[i], vi[i], we);
+        w[e] = we;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) acc[i] = fma(vi[i], we, acc[i]);
+    }
+    block_partials<NV>(acc, nv, kd.part, sh);
+    if (!last_block(kd.ictl + I_CNT + 4)) return;
+    const double v = final_partials<NV>(kd.part, nv, gridDim.x);
+    const int i = threadIdx.x / (KT / NV);
+    if (i < nv && threadIdx.x % (KT / NV) == 0) {
+        Hv(kd.scal, m)[i] = v;
+        Hm(kd.scal, m)[i * m + j] += v;
+    }
+}
+
+// Second update w <- w - V h2 with ||w||^2; the last block finishes the
+// Arnoldi step: H[j+1][j], the Givens rotations, the residual estimate.
+template <int NV>
+__global__ void __launch_bounds__(KT) k_maxpy(const double* __restrict__ V, double* __restrict__ w, int n, int j,
+                                              KDims kd) {
+    __shared__ double sh[32];
+    __shared__ double sh_h[NV];
+    if (kd.ictl[I_STOP]) return;
+    const int nv = j + 1;
+    const int m = kd.m;
+    if (threadIdx.x < NV) sh_h[threadIdx.x] = (threadIdx.x < nv) ? Hv(kd.scal, m)[threadIdx.x] : 0.0;
     __syncthreads();
     double acc = 0.0;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += gridDim.x * KT) {
+        double vi[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) vi[i] = (i < nv) ? V[(int64_t)i * n + e] : 0.0;
         double we = w[e];
-        double vi[32];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) vi[i] = (i < nv) ? V[(int64_t)i * n + e] : 0.0;
-#pragma unroll
-        for (int i = 0; i < 32; ++i)
+        for (int i = 0; i < NV; ++i)
             if (i < nv) we = fma(-sh_h[i], vi[i], we);
         w[e] = we;
         acc = fma(we, we, acc);
     }
-    if (pass == 0) return;
     const double bs = block_sum(acc, sh);
     if (threadIdx.x == 0) kd.part[blockIdx.x] = bs;
     if (!last_block(kd.ictl + I_CNT + 5)) return;
@@ -397,7 +456,8 @@ __global__ void k_fg_scale(double* __restrict__ w, int n, KDims kd) {
     if (kd.ictl[I_STOP]) return;
     const double hn = kd.scal[S_BETA];
     if (hn == 0.0) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) w[i] = w[i] / hn;
+    const double inv = 1.0 / hn;       // one division per thread, FP64 multiplies per element
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) w[i] = w[i] * inv;
 }
 
 // Cycle end: y = H(1:K,1:K)^{-1} g(1:K) by back substitution (one thread).
@@ -433,11 +493,11 @@ __global__ void k_fg_update(double* __restrict__ x, const double* __restrict__ Z
 // ---------------------------------------------------------------- host
 static int spmv_tpr(psr_ctx* ctx) {
     const double avg = ctx->n ? (double)ctx->nnz / ctx->n : 1.0;
-    // each lane loads up to four entries per pass
-    if (avg <= 16) return 4;
-    if (avg <= 32) return 8;
-    if (avg <= 64) return 16;
-    return 32;
+    // each lane loads up to four entries per pass; few lanes per row keep the
+    // FP64 reduction across the row's lanes (TPR log2 TPR adds) small
+    if (avg <= 64) return 4;
+    if (avg <= 128) return 8;
+    return 16;
 }
 
 static void launch_spmv(psr_ctx* ctx, const double* x, double* y, const double* b, int mode, int fin,
@@ -545,6 +605,7 @@ int krylov_alloc(psr_ctx* ctx) {
         PSR_CUDA(ctx, cudaMalloc(&w.Z, (size_t)m * n * 8));
     }
     w.nspmv = 152 * 16;                     // partial slots available to the SpMV reductions
+    PSR_CUDA(ctx, cudaDeviceGetAttribute(&w.sms, cudaDevAttrMultiProcessorCount, ctx->device));
     PSR_CUDA(ctx, cudaMalloc(&w.partial, (size_t)std::max(w.nblk * 34, w.nspmv) * 8));
     PSR_CUDA(ctx, cudaMalloc(&w.scal, (size_t)scal_count(m) * 8));
     PSR_CUDA(ctx, cudaMemset(w.scal, 0, (size_t)scal_count(m) * 8));
@@ -606,6 +667,50 @@ static int enqueue_cg_block(psr_ctx* ctx, KDims kd, int iters, cudaStream_t s) {
     return PSR_OK;
 }
 
+// Resident blocks per SM of a CGS2 kernel (one architecture per process).
+static int blocks_per_sm(const void* f) {
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, KT, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return per_sm;
+}
+
+// Grid of a CGS2 kernel: one resident block per SM, so that each thread
+// accumulates several elements before the block reduction.  GB300 retires two
+// FP64 FMAs per clock per SM, so FP64 instructions, not bytes, bound these
+// kernels: the per-element dot products cost nv FMAs, the warp reduction
+// about NV adds per thread, and fewer threads amortise the latter.  Capped
+// by the elements and by the partial slots (nblk blocks of 34 vectors).
+static int cgs_grid(psr_ctx* ctx, int per_sm) {
+    const int need = (ctx->n + KT - 1) / KT;
+    return std::max(1, std::min(std::min(need, std::min(per_sm, 1) * ctx->ws.sms), ctx->ws.nblk));
+}
+
+// One CGS2 orthogonalisation of w = V_{j+1} against V_0..V_j: projection,
+// update fused with the second projection, second update with the norm.
+template <int NV>
+static int enqueue_cgs2(psr_ctx* ctx, KDims kd, int j, double* Vn, cudaStream_t s) {
+    KrylovWS& w = ctx->ws;
+    const int n = ctx->n;
+    const double vb = 8.0 * n;
+    static const int o1 = blocks_per_sm((const void*)k_mdot<NV>);
+    static const int o2 = blocks_per_sm((const void*)k_maxpy_mdot<NV>);
+    static const int o3 = blocks_per_sm((const void*)k_maxpy<NV>);
+    const int g1 = cgs_grid(ctx, o1), g2 = cgs_grid(ctx, o2), g3 = cgs_grid(ctx, o3);
+    KT_BEGIN(PSR_KT_MDOT, j, (j + 2) * vb);
+    count_launch(); k_mdot<NV><<<g1, KT, 0, s>>>(w.V, Vn, n, j, kd);
+    KT_END();
+    KT_BEGIN(PSR_KT_MAXPY, j, (j + 3) * vb);
+    count_launch(); k_maxpy_mdot<NV><<<g2, KT, 0, s>>>(w.V, Vn, n, j, kd);
+    KT_END();
+    KT_BEGIN(PSR_KT_MAXPY, j, (j + 3) * vb);
+    count_launch(); k_maxpy<NV><<<g3, KT, 0, s>>>(w.V, Vn, n, j, kd);
+    KT_END();
+    return PSR_OK;
+}
+
 static int enqueue_fg_cycle(psr_ctx* ctx, KDims kd, cudaStream_t s) {
     KrylovWS& w = ctx->ws;
     const int n = ctx->n, nb = w.nblk, m = kd.m;
@@ -622,15 +727,11 @@ static int enqueue_fg_cycle(psr_ctx* ctx, KDims kd, cudaStream_t s) {
         KT_BEGIN(PSR_KT_SPMV, j, spmv_bytes(ctx));
         launch_spmv(ctx, Zj, Vn, nullptr, 0, 0, kd, 1, w.nspmv, s);
         KT_END();
-        const int mb = std::max(1, std::min((n + MDOT_THREADS - 1) / MDOT_THREADS, MDOT_BLOCKS));
-        for (int pass = 0; pass < 2; ++pass) {
-            KT_BEGIN(PSR_KT_MDOT, j, (j + 2) * vb);
-            count_launch(); k_mdot<<<mb, MDOT_THREADS, 0, s>>>(w.V, Vn, n, j, kd, pass);
-            KT_END();
-            KT_BEGIN(PSR_KT_MAXPY, j, (j + 3) * vb);
-            count_launch(); k_maxpy<<<nb, 256, 0, s>>>(w.V, Vn, n, j, kd, pass);
-            KT_END();
-        }
+        int rc2 = PSR_OK;
+        if (j < 8) rc2 = enqueue_cgs2<8>(ctx, kd, j, Vn, s);
+        else if (j < 16) rc2 = enqueue_cgs2<16>(ctx, kd, j, Vn, s);
+        else rc2 = enqueue_cgs2<32>(ctx, kd, j, Vn, s);
+        if (rc2 != PSR_OK) return rc2;
         KT_BEGIN(PSR_KT_VEC, j, 2 * vb);
         count_launch(); k_fg_scale<<<nb, 256, 0, s>>>(Vn, n, kd);
         KT_END();

@@ -109,6 +109,7 @@ struct KrylovWS {
     int32_t* ictl = nullptr;    // device control ints
     int nblk = 0;
     int nspmv = 0;
+    int sms = 0;           // streaming multiprocessors of the device
 };
 
 // One timed launch of the solve: class, iteration inside the enqueued block

@@ -42,24 +42,26 @@ def test_fgmres_timing_counts_and_bytes(lib, graph):
     x1 = torch.zeros_like(x0)
     i1 = ctx.solve(b, x1)
     kt = ctx.kernel_timing()
-    # identical results with the event marks in place
+    # the same results with the event marks in place (the sweep's scatter-add
+    # uses atomics, so two solves agree to rounding, not bit for bit)
     assert i0["iterations"] == i1["iterations"] == maxit
-    assert np.array_equal(h0, ctx.history())
-    assert torch.equal(x0, x1)
+    h1 = ctx.history()
+    assert h1.shape == h0.shape and np.max(np.abs(h1 - h0)) <= 1e-10
+    assert torch.allclose(x0, x1, rtol=1e-8, atol=1e-12)
     its = i1["iterations"]
     assert kt["sweep"][1] == its and kt["spmv"][1] == its
-    assert kt["mdot"][1] == 2 * its and kt["maxpy"][1] == 2 * its and kt["vec"][1] == its
+    assert kt["mdot"][1] == its and kt["maxpy"][1] == 2 * its and kt["vec"][1] == its
     for name, (ms, cnt, by) in kt.items():
         assert ms > 0.0 and by > 0.0, name
     n = pr.n
     js = list(range(m)) + list(range(maxit - m))          # iterations j of each cycle
-    assert kt["mdot"][2] == pytest.approx(2 * sum(8.0 * (j + 2) * n for j in js), rel=1e-12)
+    assert kt["mdot"][2] == pytest.approx(sum(8.0 * (j + 2) * n for j in js), rel=1e-12)
     assert kt["maxpy"][2] == pytest.approx(2 * sum(8.0 * (j + 3) * n for j in js), rel=1e-12)
     assert kt["spmv"][2] == pytest.approx(its * (12.0 * pr.nnz + 4.0 * (n + 1) + 16.0 * n), rel=1e-12)
     # disabling resets nothing but stops the marks; re-enabling resets
     ctx.set_kernel_timing(False)
     ctx.solve(b, x1)
-    assert ctx.kernel_timing()["mdot"][1] == 2 * its
+    assert ctx.kernel_timing()["mdot"][1] == its
     ctx.set_kernel_timing(True)
     assert all(v[1] == 0 for v in ctx.kernel_timing().values())
     ctx.destroy()

@@ -163,12 +163,17 @@ def test_criterion_decisions_vs_oracle(lib):
 
 
 # ------------------------------------------------------------------ Alg. 1
-@pytest.mark.parametrize("case", ["c1", "stokes8", "diff3d", "nedelec", "uniform3d"])
+@pytest.mark.parametrize("case", ["c1", "stokes8", "stokes12", "diff3d", "nedelec", "nedelec6", "uniform3d"])
 def test_alg1_assignment_bit_exact(lib, case):
     if case == "c1":
         pr, tols = P.poisson2d_q2(16), [1e-12, 1e-3, 1e-1]
     elif case == "stokes8":
         pr, tols = P.stokes2d_q2q1(8), [1e-3, 1e-1, 2.0, 10.0]
+    elif case == "stokes12":
+        pr, tols = P.stokes2d_q2q1(12), [1e-2, 1e-1]
+    elif case == "nedelec6":
+        # nearly every patch becomes an entry: almost all pairs are rejected
+        pr, tols = P.nedelec3d(6, seed=5), [1e-1, 0.3]
     elif case == "diff3d":
         pr, tols = P.diffusion3d_q2(4, seed=3), [1e-2, 1e-1, 0.5]
     elif case == "nedelec":
