@@ -32,6 +32,8 @@
 namespace psr {
 
 static constexpr double U64 = 0x1p-53;
+// gamma_k = k u / (1 - k u), the usual bound of k accumulated FP64 roundings.
+__device__ __forceinline__ double gamma_u(int k) { return (double)k * U64 / (1.0 - (double)k * U64); }
 // Probe storage per entry: w_1 at [0, 32), w_2 at [PROBE_W2, PROBE_W2 + 32).
 static constexpr int PROBE_W2 = 32;
 static constexpr int PROBE_STRIDE = 64;
@@ -248,20 +250,75 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
         __syncwarp();
     }
     if (!allow_exact_here) { *dv = lb; return -1; }
-    // exact: G = E^T E into ws.E (overwrites E; e[] still holds rows)
+    // Certified tests on X I - G with G = fl(E^T E) (E here the computed
+    // product, within err of the exact one; ||E^T E - G||_2 <= gamma_p
+    // ||E||_F^2 =: eg):
+    //   accept: the Cholesky factorisation of X I - G - c I succeeds, c
+    //     covering its own rounding (backward error <= gamma_{p+1} tr), so
+    //     lambda_max(G) < X, sigma(E) < sqrt(X + eg) + err <= tol;
+    //   reject: the factorisation of X' I - G meets a pivot <= 0 at k; then
+    //     z = [-L11^-T l; 1; 0] has z^T G z >= X' z^T z, and ||E z|| / ||z||
+    //     with its rounding and err removed is a lower bound >= tol.
+    // A near tie that neither settles goes to the Jacobi eigenvalues of G.
     __syncwarp();
     // column j of E lives in lane j after a transpose read
     double ecol[32];
 #pragma unroll
     for (int r = 0; r < 32; ++r) ecol[r] = (act && r < p) ? ws.E[r * ld + lane] : 0.0;
     __syncwarp();
-    // G[lane][k] = sum_r E[r][lane] E[r][k]; every lane runs every shuffle
-    for (int k = 0; k < p; ++k) {
-        double g = 0.0;
-        for (int r = 0; r < p; ++r) g = fma(ecol[r], __shfl_sync(0xffffffffu, ecol[r], k), g);
-        if (act) ws.E[lane * ld + k] = g;
+    // ws.E <- X I - G (neg) or G; G[lane][k] = sum_r E[r][lane] E[r][k], every
+    // lane runs every shuffle
+    auto build = [&](double X, bool neg) {
+        for (int k = 0; k < p; ++k) {
+            double g = 0.0;
+            for (int r = 0; r < p; ++r) g = fma(ecol[r], __shfl_sync(0xffffffffu, ecol[r], k), g);
+            if (act) ws.E[lane * ld + k] = neg ? ((k == lane ? X : 0.0) - g) : g;
+        }
+        __syncwarp();
+    };
+    const double eg = 1.01 * gamma_u(p) * fro2;
+    const double tl = (tol - err) * shrink;
+    if (tl > 0.0) {
+        const double X = tl * tl * (1.0 - 4.0 * U64) - eg;
+        if (X > 0.0) {
+            build(X, true);
+            const double trA = warp_sum(act ? ws.E[lane * ld + lane] : 0.0);
+            if (trA > 0.0) {
+                const double c = 2.0 * gamma_u(p + 1) * trA;
+                if (act) ws.E[lane * ld + lane] -= c;
+                __syncwarp();
+                if (cholesky_warp(ws.E, p, ld) == p) {
+                    *dv = (sqrt(X + eg) + err) * (1.0 + 8.0 * U64);
+                    return 1;
+                }
+            }
+        }
     }
-    __syncwarp();
+    {
+        const double th = (tol + err) / shrink;
+        build(th * th * (1.0 + 4.0 * U64) + eg, true);
+        const int k = cholesky_warp(ws.E, p, ld);
+        if (k < p) {
+            // L11^T y = l (row k of L), back substitution; lane i keeps y_i
+            double yl = 0.0;
+            for (int i = k - 1; i >= 0; --i) {
+                const double part = (lane > i && lane < k) ? ws.E[lane * ld + i] * yl : 0.0;
+                const double sum = warp_sum(part);
+                const double yi = (ws.E[k * ld + i] - sum) / ws.E[i * ld + i];
+                if (lane == i) yl = yi;
+            }
+            const double z = (lane < k) ? -yl : (lane == k ? 1.0 : 0.0);
+            double t = 0.0;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) t = fma(e[j], __shfl_sync(0xffffffffu, z, j), t);
+            const double nez = sqrt(warp_sum(t * t));
+            const double nz = sqrt(warp_sum(z * z));
+            const double lbz = (nez * (1.0 - (double)(p + 4) * U64) - 1.01 * gamma_u(p) * sqrt(fro2) * nz) /
+                               (nz * (1.0 + (double)(p + 2) * U64)) - err;
+            if (lbz * (1.0 - 8.0 * U64) >= tol) { *dv = lbz; return 0; }
+        }
+    }
+    build(0.0, false);
     const double lam = jacobi_lambda_max_warp(ws.E, p, ld);
     const double sig = sqrt(fmax(lam, 0.0));
     *dv = sig;
@@ -390,7 +447,6 @@ struct SketchDB {
     const double* rho;             // [count] bound of ||B_i^ A_i - I||_2
 };
 
-__device__ __forceinline__ double gamma_u(int k) { return (double)k * U64 / (1.0 - (double)k * U64); }
 
 // Directions of a size group: x_0 = the dominant right singular vector of
 // the group's middle patch, x_1 = a fixed alternating vector; both unit.

@@ -119,4 +119,29 @@ __device__ __forceinline__ double jacobi_lambda_max_warp(double* G, int p, int l
     return warp_max(lm);
 }
 
+// Cholesky A = L L^T of the symmetric p x p matrix in A (row stride ld; the
+// lower triangle is read and overwritten by L).  One warp, p <= 32; lane r
+// updates row r.  Returns p when every pivot is positive; otherwise the index
+// k of the first pivot that is not (uniform over the warp), with columns
+// 0..k-1 of L in place, so that A[k][0..k-1] holds row k of L.
+__device__ __forceinline__ int cholesky_warp(double* A, int p, int ld) {
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < p; ++k) {
+        __syncwarp();
+        const double akk = A[k * ld + k];
+        if (!(akk > 0.0)) return k;                    // also stops on NaN
+        const double lkk = sqrt(akk);
+        __syncwarp();
+        if (lane == k) A[k * ld + k] = lkk;
+        if (lane > k && lane < p) A[lane * ld + k] /= lkk;
+        __syncwarp();
+        if (lane > k && lane < p) {
+            const double lrk = A[lane * ld + k];
+            for (int j = k + 1; j <= lane; ++j) A[lane * ld + j] = fma(-lrk, A[j * ld + k], A[lane * ld + j]);
+        }
+    }
+    __syncwarp();
+    return p;
+}
+
 }  // namespace psr
