@@ -350,7 +350,7 @@ def run_gpu(args, cfg, ws, rank, local):
         "sweep_dof_per_s": n / apply_med,
         "m_p": st["m_p"], "retained_fraction": st["m_p"] / npch,
         "factor_bytes": {"clustered": st["factor_bytes"], "full": st_f["factor_bytes"]},
-        "criterion_evals": st["criterion_evals"], "criterion_exact": st["criterion_exact"],
+        "criterion_evals": st["criterion_evals"], "criterion_exact": st["criterion_exact"], "criterion_screened": st["criterion_screened"],
         "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
     }
     return out, pr, infos[-1], st

@@ -171,6 +171,8 @@ typedef struct {
     int32_t tc_groups;            /* size groups applied on the tensor cores (BF16
                                      storage, 128-patch tiles at least 1/4 full) */
     int32_t reserved;
+    int64_t criterion_screened;   /* of the evaluations, rejected by the per-patch
+                                     sketch screen without reading the candidate */
 } psr_stats;
 
 int psr_get_stats(psr_ctx* ctx, psr_stats* st);

@@ -37,6 +37,8 @@ __device__ __forceinline__ double gamma_u(int k) { return (double)k * U64 / (1.0
 // Probe storage per entry: w_1 at [0, 32), w_2 at [PROBE_W2, PROBE_W2 + 32).
 static constexpr int PROBE_W2 = 32;
 static constexpr int PROBE_STRIDE = 64;
+// Threads per block of the round kernels (one candidate per thread in the screen).
+static constexpr int EVAL_THREADS = 128;
 
 struct RoundDev {
     int next;          // patch that becomes the next entry (smallest unassigned)
@@ -45,7 +47,7 @@ struct RoundDev {
     int first_singular;
     int ticket;        // last-block counter of the round kernel
     int next_new;      // smallest candidate the current round rejected
-    unsigned long long evals, exact;
+    unsigned long long evals, exact, screened;
 };
 
 struct WarpScratch {  // per-warp shared memory layout for p <= 32
@@ -574,7 +576,7 @@ __device__ __forceinline__ bool round_last_block(int* ticket) {
 // a rejected candidate stays unassigned and bids for being the next entry
 // (atomicMin): the smallest rejected index is exactly the smallest unassigned
 // patch after the round.  The last block records the entry and the next one.
-__global__ void __launch_bounds__(256, 2) k_round(RoundDev* st, int32_t* __restrict__ phi, int count,
+__global__ void __launch_bounds__(EVAL_THREADS, 4) k_round(RoundDev* st, int32_t* __restrict__ phi, int count,
                                                  const double* __restrict__ Ag, int p,
                                                  const double* __restrict__ Ball, const double* __restrict__ fro_all,
                                                  const double* __restrict__ w_all, const int32_t* __restrict__ sing_all,
@@ -608,24 +610,33 @@ __global__ void __launch_bounds__(256, 2) k_round(RoundDev* st, int32_t* __restr
     const double fc = sk.fa[i0], rhoc = sk.rho[i0];
     stage_sketch(sk.Y + (int64_t)i0 * SK * p, fc, p, sy, sden);
     __syncthreads();
-    unsigned long long my_evals = 0, my_exact = 0;
+    unsigned long long my_evals = 0, my_exact = 0, my_screened = 0;
     int my_min = count;
-    const int nw = gridDim.x * wpb;
-    // a warp takes 32 consecutive candidates: every lane screens its own with
-    // the sketch bound, the survivors run the warp-wide decision one by one
-    for (int base = i0 + 1 + (blockIdx.x * wpb + wid) * 32; base < count; base += nw * 32) {
-        const int cand = base + lane;
+    __shared__ int s_list[EVAL_THREADS];
+    __shared__ int s_cnt;
+    // a block takes blockDim.x consecutive candidates: every thread screens
+    // its own with the sketch bound, the survivors are queued in shared
+    // memory and the block's warps run the warp-wide decision on them in turn
+    for (int base = i0 + 1 + blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
+        if (threadIdx.x == 0) s_cnt = 0;
+        __syncthreads();
+        const int cand = base + threadIdx.x;
         const bool open = cand < count && phi[cand] == -1;
         bool rej = false;
         if (open) rej = sketch_rejects(sk.Y + (int64_t)cand * SK * p, sk.fa[cand], sy, sden, fc, rhoc, p, tol);
         if (open && rej) my_min = min(my_min, cand);
         const unsigned opened = __ballot_sync(0xffffffffu, open);
-        unsigned todo = __ballot_sync(0xffffffffu, open && !rej);
+        const unsigned surv = __ballot_sync(0xffffffffu, open && !rej);
         my_evals += __popc(opened);
-        while (todo) {
-            const int l = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int c2 = base + l;
+        my_screened += __popc(opened & ~surv);
+        int wb = 0;
+        if (lane == 0 && surv) wb = atomicAdd(&s_cnt, __popc(surv));
+        wb = __shfl_sync(0xffffffffu, wb, 0);
+        if (open && !rej) s_list[wb + __popc(surv & ((1u << lane) - 1u))] = cand;
+        __syncthreads();
+        const int ns = s_cnt;
+        for (int q = wid; q < ns; q += wpb) {
+            const int c2 = s_list[q];
             double dv;
             int dec = decide_pair(Ag + (int64_t)c2 * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, false, sw, sB32);
             if (dec < 0) {
@@ -636,12 +647,14 @@ __global__ void __launch_bounds__(256, 2) k_round(RoundDev* st, int32_t* __restr
             else my_min = min(my_min, c2);
             __syncwarp();
         }
+        __syncthreads();                    // the list is rebuilt next pass
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) my_min = min(my_min, __shfl_xor_sync(0xffffffffu, my_min, o));
     if (lane == 0) {
         if (my_evals) atomicAdd(&st->evals, my_evals);
         if (my_exact) atomicAdd(&st->exact, my_exact);
+        if (my_screened) atomicAdd(&st->screened, my_screened);
         if (my_min < count) atomicMin(&st->next_new, my_min);
     }
     if (!round_last_block(&st->ticket)) return;
@@ -671,7 +684,7 @@ __device__ __forceinline__ void stage_seed(EntryDB db, int p, int e, double* sAc
 
 // Seeded Alg. 1: every still unassigned patch compared with seed entry e
 // (sketch screen first, as in k_round; skd holds the seed entries' sketches).
-__global__ void __launch_bounds__(256, 2) k_seed_pass(RoundDev* st, int32_t* __restrict__ phi, int count,
+__global__ void __launch_bounds__(EVAL_THREADS, 4) k_seed_pass(RoundDev* st, int32_t* __restrict__ phi, int count,
                                                      const double* __restrict__ Ag, int p, EntryDB db, SketchDB sk,
                                                      SketchDB skd, double tol, int e) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -694,20 +707,28 @@ __global__ void __launch_bounds__(256, 2) k_seed_pass(RoundDev* st, int32_t* __r
     const double fc = skd.fa[e], rhoc = skd.rho[e];
     stage_sketch(skd.Y + (int64_t)e * SK * p, fc, p, sy, sden);
     __syncthreads();
-    unsigned long long my_evals = 0, my_exact = 0;
-    const int nw = gridDim.x * wpb;
-    for (int base = (blockIdx.x * wpb + wid) * 32; base < count; base += nw * 32) {
-        const int cand = base + lane;
+    unsigned long long my_evals = 0, my_exact = 0, my_screened = 0;
+    __shared__ int s_list[EVAL_THREADS];
+    __shared__ int s_cnt;
+    for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
+        if (threadIdx.x == 0) s_cnt = 0;
+        __syncthreads();
+        const int cand = base + threadIdx.x;
         const bool open = cand < count && phi[cand] == -1;
         bool rej = false;
         if (open) rej = sketch_rejects(sk.Y + (int64_t)cand * SK * p, sk.fa[cand], sy, sden, fc, rhoc, p, tol);
         const unsigned opened = __ballot_sync(0xffffffffu, open);
-        unsigned todo = __ballot_sync(0xffffffffu, open && !rej);
+        const unsigned surv = __ballot_sync(0xffffffffu, open && !rej);
         my_evals += __popc(opened);
-        while (todo) {
-            const int l = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int c2 = base + l;
+        my_screened += __popc(opened & ~surv);
+        int wb = 0;
+        if (lane == 0 && surv) wb = atomicAdd(&s_cnt, __popc(surv));
+        wb = __shfl_sync(0xffffffffu, wb, 0);
+        if (open && !rej) s_list[wb + __popc(surv & ((1u << lane) - 1u))] = cand;
+        __syncthreads();
+        const int ns = s_cnt;
+        for (int q = wid; q < ns; q += wpb) {
+            const int c2 = s_list[q];
             double dv;
             int dec = decide_pair(Ag + (int64_t)c2 * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, false, sw, sB32);
             if (dec < 0) {
@@ -717,10 +738,12 @@ __global__ void __launch_bounds__(256, 2) k_seed_pass(RoundDev* st, int32_t* __r
             if (lane == 0 && dec == 1) phi[c2] = e;
             __syncwarp();
         }
+        __syncthreads();
     }
     if (lane == 0) {
         if (my_evals) atomicAdd(&st->evals, my_evals);
         if (my_exact) atomicAdd(&st->exact, my_exact);
+        if (my_screened) atomicAdd(&st->screened, my_screened);
     }
 }
 
@@ -817,7 +840,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
     int32_t* flag = nullptr;
     PSR_CUDA(ctx, cudaMalloc(&flag, sizeof(int32_t)));
     int rc = PSR_OK;
-    int64_t total_evals = 0, total_exact = 0, total_hits = 0;
+    int64_t total_evals = 0, total_exact = 0, total_hits = 0, total_screened = 0;
     int rounds_total = 0;
     int first_singular = -1;
     if (m0 > 0 && ctx->groups.size() != 1) { set_error(ctx, "a seed database needs patches of one size"); return PSR_ERR_INVALID_ARG; }
@@ -872,13 +895,13 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         init.next_new = count;
         PSR_CUDA(ctx, cudaMemcpyAsync(st, &init, sizeof(RoundDev), cudaMemcpyHostToDevice, s));
         const int ld = p + 1;
-        const int wpb = 8;
+        const int wpb = EVAL_THREADS / 32;
         const size_t smem_eval = eval_smem_bytes(p, wpb);
         if ((rc = set_smem((const void*)k_round, smem_eval)) != PSR_OK) break;
         if ((rc = set_smem((const void*)k_seed_pass, smem_eval)) != PSR_OK) break;
-        // 32 candidates per warp (sketch screen per lane): enough warps for
-        // every SM, a few chunks each
-        int eval_blocks = (count + 32 * wpb - 1) / (32 * wpb);
+        // one candidate per thread in the screen: enough blocks for every
+        // SM, a few passes each
+        int eval_blocks = (count + EVAL_THREADS - 1) / EVAL_THREADS;
         if (eval_blocks > 152 * 4) eval_blocks = 152 * 4;
         if (eval_blocks < 1) eval_blocks = 1;
         if (m0 > 0) {
@@ -956,6 +979,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         G.m = h_st->m;
         total_evals += (int64_t)h_st->evals;
         total_exact += (int64_t)h_st->exact;
+        total_screened += (int64_t)h_st->screened;
         rounds_total += h_st->m - m0;
         if (h_st->first_singular >= 0 && first_singular < 0) first_singular = G.h_gidx[h_st->first_singular];
         std::vector<int32_t> hrep(G.m);
@@ -988,6 +1012,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
     cudaFree(flag);
     ctx->stats.criterion_evals = total_evals;
     ctx->stats.criterion_exact = total_exact;
+    ctx->stats.criterion_screened = total_screened;
     ctx->stats.mlp_hits = total_hits;
     ctx->stats.rounds = rounds_total;
     ctx->stats.first_singular = first_singular;

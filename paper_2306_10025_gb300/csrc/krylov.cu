@@ -632,10 +632,12 @@ int kernel_timing_enable(psr_ctx* ctx, bool on) {
     ctx->g_cycle = nullptr;
     ctx->kt_marks.clear();
     ctx->kt_on = on;
-    for (int k = 0; k < PSR_KT_COUNT; ++k) {
-        ctx->kt_ms[k] = 0.0;
-        ctx->kt_n[k] = 0;
-        ctx->kt_bytes[k] = 0.0;
+    if (on) {
+        for (int k = 0; k < PSR_KT_COUNT; ++k) {
+            ctx->kt_ms[k] = 0.0;
+            ctx->kt_n[k] = 0;
+            ctx->kt_bytes[k] = 0.0;
+        }
     }
     return PSR_OK;
 }
