@@ -24,7 +24,7 @@ namespace psr {
 int sweep_apply_ex(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s);
 
 enum { S_RZ = 0, S_PQ, S_ALPHA, S_BETA, S_RN, S_R0, S_RTOL, S_H = 16 };
-enum { I_STOP = 0, I_CONV, I_IT, I_K, I_MAXIT, I_M, I_CNT = 8, I_NCNT = 8 };
+enum { I_STOP = 0, I_CONV, I_IT, I_K, I_MAXIT, I_M, I_REORTH, I_CNT = 8, I_NCNT = 8 };
 
 struct KDims {
     int n, m, nb;
@@ -32,6 +32,7 @@ struct KDims {
     int32_t* ictl;
     double* part;
     double* hist;
+    int32_t* rflag;        // [m] second Gram-Schmidt pass taken at step j of the cycle
 };
 
 __device__ __forceinline__ double* Hm(double* sc, int m) { return sc + S_H; }
@@ -327,46 +328,120 @@ __device__ __forceinline__ double final_partials(const double* __restrict__ part
     return v;
 }
 
-// h = V^T w (first pass): H[:, j] = h and h is kept for the update.
+// Arnoldi finish of step j (thread 0 of the last block): H[j+1][j] = ||w||,
+// the previous Givens rotations applied to column j, the new rotation, the
+// residual estimate |g_{j+1}| and the stopping tests.
+__device__ void arnoldi_finish(KDims kd, int j, double wn2) {
+    double* sc = kd.scal;
+    int32_t* ic = kd.ictl;
+    const int m = kd.m;
+    double* H = Hm(sc, m);
+    double* cs = CSv(sc, m);
+    double* sn = SNv(sc, m);
+    double* g = Gv(sc, m);
+    const double hn = sqrt(wn2);
+    H[(j + 1) * m + j] = hn;
+    for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
+        H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
+        H[i * m + j] = t;
+    }
+    const double den = hypot(H[j * m + j], H[(j + 1) * m + j]);
+    cs[j] = H[j * m + j] / den;
+    sn[j] = H[(j + 1) * m + j] / den;
+    H[j * m + j] = den;
+    sc[S_BETA] = hn;                    // keep ||w|| for the normalisation
+    H[(j + 1) * m + j] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    const int it = ic[I_IT] + 1;
+    ic[I_IT] = it;
+    ic[I_K] = j + 1;
+    const double res = fabs(g[j + 1]);
+    kd.hist[it] = res / sc[S_R0];
+    sc[S_RN] = res;
+    if (res <= sc[S_RTOL] * sc[S_R0]) { ic[I_CONV] = 1; ic[I_STOP] = 1; }
+    else if (it >= ic[I_MAXIT] || den == 0.0) ic[I_STOP] = 1;
+}
+
+// h = V^T w and ||w||^2 (first pass): H[:, j] = h, h kept for the update.
+// The last block also decides whether the step needs a second pass: by the
+// Kahan-Parlett criterion ("twice is enough"), when the projected vector
+// keeps less than half of the squared norm, ||w||^2 - ||h||^2 < ||w||^2 / 2.
 template <int NV>
 __global__ void __launch_bounds__(KT) k_mdot(const double* __restrict__ V, const double* __restrict__ w, int n,
                                              int j, KDims kd) {
     __shared__ double sh[NV][KT / 32 + 1];
+    __shared__ double shw[32];
     if (kd.ictl[I_STOP]) return;
     const int nv = j + 1;
     double acc[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    double accw = 0.0;
     for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += gridDim.x * KT) {
         const double we = w[e];
+        accw = fma(we, we, accw);
 #pragma unroll
         for (int i = 0; i < NV; ++i)
             if (i < nv) acc[i] = fma(V[(int64_t)i * n + e], we, acc[i]);
     }
     block_partials<NV>(acc, nv, kd.part, sh);
+    const double bw = block_sum(accw, shw);
+    if (threadIdx.x == 0) kd.part[(int64_t)NV * gridDim.x + blockIdx.x] = bw;
     if (!last_block(kd.ictl + I_CNT + 4)) return;
     const double v = final_partials<NV>(kd.part, nv, gridDim.x);
+    const double wn2 = sum_partials(kd.part + (int64_t)NV * gridDim.x, gridDim.x);
+    const int m = kd.m;
     const int i = threadIdx.x / (KT / NV);
     if (i < nv && threadIdx.x % (KT / NV) == 0) {
-        const int m = kd.m;
         Hv(kd.scal, m)[i] = v;
         Hm(kd.scal, m)[i * m + j] = v;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double* hv = Hv(kd.scal, m);
+        double h2 = 0.0;
+        for (int q = 0; q < nv; ++q) h2 = fma(hv[q], hv[q], h2);
+        const int rf = (wn2 - h2 < 0.5 * wn2) ? 1 : 0;
+        kd.ictl[I_REORTH] = rf;
+        kd.rflag[j] = rf;
+    }
 }
 
-// First update fused with the second projection: w <- w - V h, then
-// h2 = V^T w on the same loads of V; H[:, j] += h2 and h2 is kept for the
-// second update.
+// Update w <- w - V h.  Without a second pass it also accumulates ||w||^2
+// and its last block finishes the Arnoldi step; with one, it accumulates the
+// second projection h2 = V^T w on the same loads of V (H[:, j] += h2, h2 kept
+// for the second update).
 template <int NV>
 __global__ void __launch_bounds__(KT) k_maxpy_mdot(const double* __restrict__ V, double* __restrict__ w, int n,
                                                    int j, KDims kd) {
     __shared__ double sh[NV][KT / 32 + 1];
     __shared__ double sh_h[NV];
+    __shared__ double shw[32];
     if (kd.ictl[I_STOP]) return;
+    const bool reorth = kd.ictl[I_REORTH] != 0;
     const int nv = j + 1;
     const int m = kd.m;
     if (threadIdx.x < NV) sh_h[threadIdx.x] = (threadIdx.x < nv) ? Hv(kd.scal, m)[threadIdx.x] : 0.0;
     __syncthreads();
+    if (!reorth) {
+        double accw = 0.0;
+        for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += gridDim.x * KT) {
+            double we = w[e];
+#pragma unroll
+            for (int i = 0; i < NV; ++i)
+                if (i < nv) we = fma(-sh_h[i], V[(int64_t)i * n + e], we);
+            w[e] = we;
+            accw = fma(we, we, accw);
+        }
+        const double bs = block_sum(accw, shw);
+        if (threadIdx.x == 0) kd.part[blockIdx.x] = bs;
+        if (!last_block(kd.ictl + I_CNT + 5)) return;
+        const double tot = sum_partials(kd.part, gridDim.x);
+        if (threadIdx.x == 0) arnoldi_finish(kd, j, tot);
+        return;
+    }
     double acc[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] = 0.0;
@@ -392,27 +467,24 @@ __global__ void __launch_bounds__(KT) k_maxpy_mdot(const double* __restrict__ V,
     }
 }
 
-// Second update w <- w - V h2 with ||w||^2; the last block finishes the
-// Arnoldi step: H[j+1][j], the Givens rotations, the residual estimate.
+// Second update w <- w - V h2 with ||w||^2 and the Arnoldi finish; returns at
+// once when the step needed no second pass.
 template <int NV>
 __global__ void __launch_bounds__(KT) k_maxpy(const double* __restrict__ V, double* __restrict__ w, int n, int j,
                                               KDims kd) {
     __shared__ double sh[32];
     __shared__ double sh_h[NV];
-    if (kd.ictl[I_STOP]) return;
+    if (kd.ictl[I_STOP] || !kd.ictl[I_REORTH]) return;
     const int nv = j + 1;
     const int m = kd.m;
     if (threadIdx.x < NV) sh_h[threadIdx.x] = (threadIdx.x < nv) ? Hv(kd.scal, m)[threadIdx.x] : 0.0;
     __syncthreads();
     double acc = 0.0;
     for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += gridDim.x * KT) {
-        double vi[NV];
-#pragma unroll
-        for (int i = 0; i < NV; ++i) vi[i] = (i < nv) ? V[(int64_t)i * n + e] : 0.0;
         double we = w[e];
 #pragma unroll
         for (int i = 0; i < NV; ++i)
-            if (i < nv) we = fma(-sh_h[i], vi[i], we);
+            if (i < nv) we = fma(-sh_h[i], V[(int64_t)i * n + e], we);
         w[e] = we;
         acc = fma(we, we, acc);
     }
@@ -420,36 +492,7 @@ __global__ void __launch_bounds__(KT) k_maxpy(const double* __restrict__ V, doub
     if (threadIdx.x == 0) kd.part[blockIdx.x] = bs;
     if (!last_block(kd.ictl + I_CNT + 5)) return;
     const double tot = sum_partials(kd.part, gridDim.x);
-    if (threadIdx.x != 0) return;
-    double* sc = kd.scal;
-    int32_t* ic = kd.ictl;
-    double* H = Hm(sc, m);
-    double* cs = CSv(sc, m);
-    double* sn = SNv(sc, m);
-    double* g = Gv(sc, m);
-    const double hn = sqrt(tot);
-    H[(j + 1) * m + j] = hn;
-    for (int i = 0; i < j; ++i) {
-        const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
-        H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
-        H[i * m + j] = t;
-    }
-    const double den = hypot(H[j * m + j], H[(j + 1) * m + j]);
-    cs[j] = H[j * m + j] / den;
-    sn[j] = H[(j + 1) * m + j] / den;
-    H[j * m + j] = den;
-    sc[S_BETA] = hn;                    // keep ||w|| for the normalisation
-    H[(j + 1) * m + j] = 0.0;
-    g[j + 1] = -sn[j] * g[j];
-    g[j] = cs[j] * g[j];
-    const int it = ic[I_IT] + 1;
-    ic[I_IT] = it;
-    ic[I_K] = j + 1;
-    const double res = fabs(g[j + 1]);
-    kd.hist[it] = res / sc[S_R0];
-    sc[S_RN] = res;
-    if (res <= sc[S_RTOL] * sc[S_R0]) { ic[I_CONV] = 1; ic[I_STOP] = 1; }
-    else if (it >= ic[I_MAXIT] || den == 0.0) ic[I_STOP] = 1;
+    if (threadIdx.x == 0) arnoldi_finish(kd, j, tot);
 }
 
 __global__ void k_fg_scale(double* __restrict__ w, int n, KDims kd) {
@@ -547,7 +590,7 @@ static int kt_begin(psr_ctx* ctx, int kind, int j, double bytes, cudaStream_t s)
         PSR_CUDA(ctx, cudaEventCreate(&e));
         ctx->kt_ev.push_back(e);
     }
-    ctx->kt_marks.push_back(KtMark{kind, j, bytes});
+    ctx->kt_marks.push_back(KtMark{kind, j, bytes, false});
     PSR_CUDA(ctx, kt_record(ctx->kt_ev[2 * i], s));
     return PSR_OK;
 }
@@ -559,8 +602,10 @@ static int kt_end(psr_ctx* ctx, cudaStream_t s) {
     return PSR_OK;
 }
 
-// After a block ran `done` iterations (all its events have completed).
-static int kt_collect(psr_ctx* ctx, int done) {
+// After a block ran `done` iterations (all its events have completed);
+// rflag[j] (host copy, FGMRES only) tells whether step j took the second
+// Gram-Schmidt pass: a second update launched without it moved no bytes.
+static int kt_collect(psr_ctx* ctx, int done, const int32_t* rflag) {
     if (!ctx->kt_on) return PSR_OK;
     for (size_t i = 0; i < ctx->kt_marks.size(); ++i) {
         const KtMark& mk = ctx->kt_marks[i];
@@ -569,7 +614,7 @@ static int kt_collect(psr_ctx* ctx, int done) {
         PSR_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->kt_ev[2 * i], ctx->kt_ev[2 * i + 1]));
         ctx->kt_ms[mk.kind] += ms;
         ctx->kt_n[mk.kind] += 1;
-        ctx->kt_bytes[mk.kind] += mk.bytes;
+        if (!mk.second_pass || (rflag && rflag[mk.j])) ctx->kt_bytes[mk.kind] += mk.bytes;
     }
     return PSR_OK;
 }
@@ -611,6 +656,8 @@ int krylov_alloc(psr_ctx* ctx) {
     PSR_CUDA(ctx, cudaMemset(w.scal, 0, (size_t)scal_count(m) * 8));
     PSR_CUDA(ctx, cudaMalloc(&w.hist, (size_t)(ctx->opts.maxit + 2) * 8));
     PSR_CUDA(ctx, cudaMalloc(&w.ictl, 32 * sizeof(int32_t)));
+    PSR_CUDA(ctx, cudaMalloc(&w.rflag, 64 * sizeof(int32_t)));
+    PSR_CUDA(ctx, cudaMemset(w.rflag, 0, 64 * sizeof(int32_t)));
     PSR_CUDA(ctx, cudaMemset(w.ictl, 0, 32 * sizeof(int32_t)));
     return PSR_OK;
 }
@@ -619,6 +666,7 @@ void krylov_free(psr_ctx* ctx) {
     KrylovWS& w = ctx->ws;
     for (double* p : {w.x, w.b, w.r, w.z, w.p, w.q, w.V, w.Z, w.partial, w.scal, w.hist}) cudaFree(p);
     cudaFree(w.ictl);
+    cudaFree(w.rflag);
     w = KrylovWS{};
     if (ctx->g_cycle) cudaGraphExecDestroy(ctx->g_cycle);
     ctx->g_cycle = nullptr;
@@ -708,6 +756,7 @@ static int enqueue_cgs2(psr_ctx* ctx, KDims kd, int j, double* Vn, cudaStream_t 
     count_launch(); k_maxpy_mdot<NV><<<g2, KT, 0, s>>>(w.V, Vn, n, j, kd);
     KT_END();
     KT_BEGIN(PSR_KT_MAXPY, j, (j + 3) * vb);
+    if (ctx->kt_on && !ctx->kt_marks.empty()) ctx->kt_marks.back().second_pass = true;
     count_launch(); k_maxpy<NV><<<g3, KT, 0, s>>>(w.V, Vn, n, j, kd);
     KT_END();
     return PSR_OK;
@@ -751,7 +800,7 @@ int krylov_solve(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_s
     const int n = ctx->n, nb = w.nblk;
     const bool cg = ctx->opts.krylov == PSR_KRYLOV_CG;
     const int m = cg ? 0 : ctx->opts.restart;
-    KDims kd{n, cg ? 1 : m, nb, w.scal, w.ictl, w.partial, w.hist};
+    KDims kd{n, cg ? 1 : m, nb, w.scal, w.ictl, w.partial, w.hist, w.rflag};
     cudaEvent_t e0, e1;
     PSR_CUDA(ctx, cudaEventCreate(&e0));
     PSR_CUDA(ctx, cudaEventCreate(&e1));
@@ -773,8 +822,8 @@ int krylov_solve(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_s
         count_launch(); k_copy<<<nb, 256, 0, s>>>(w.z, w.p, n, kd);
     }
     const int block = cg ? 8 : 1;
-    int32_t* hstop = nullptr;
-    PSR_CUDA(ctx, cudaMallocHost(&hstop, 4 * sizeof(int32_t)));
+    int32_t* hstop = nullptr;                     // control ints, then the step flags
+    PSR_CUDA(ctx, cudaMallocHost(&hstop, (4 + 64) * sizeof(int32_t)));
     // capture one block / cycle into a graph (the pointers are the context's own)
     if (ctx->opts.use_graph && !ctx->g_cycle) {
         cudaStream_t cs;
@@ -818,8 +867,10 @@ int krylov_solve(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_s
             if (rc != PSR_OK) break;
         }
         PSR_CUDA(ctx, cudaMemcpyAsync(hstop, w.ictl, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        if (ctx->kt_on && !cg)
+            PSR_CUDA(ctx, cudaMemcpyAsync(hstop + 4, w.rflag, (size_t)m * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         PSR_CUDA(ctx, cudaStreamSynchronize(s));
-        rc = kt_collect(ctx, hstop[I_IT] - it_before);
+        rc = kt_collect(ctx, hstop[I_IT] - it_before, cg ? nullptr : hstop + 4);
         if (rc != PSR_OK) break;
         it_before = hstop[I_IT];
         if (hstop[I_STOP]) break;

@@ -107,6 +107,7 @@ struct KrylovWS {
     double* scal = nullptr;     // device scalars (see krylov.cu)
     double* hist = nullptr;     // [maxit + 1]
     int32_t* ictl = nullptr;    // device control ints
+    int32_t* rflag = nullptr;   // [64] FGMRES: second Gram-Schmidt pass taken at step j
     int nblk = 0;
     int nspmv = 0;
     int sms = 0;           // streaming multiprocessors of the device
@@ -119,6 +120,7 @@ struct KtMark {
     int kind;
     int j;
     double bytes;
+    bool second_pass;      // FGMRES second update: moves its bytes only when step j reorthogonalised
 };
 
 }  // namespace psr
