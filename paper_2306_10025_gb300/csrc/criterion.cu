@@ -47,6 +47,7 @@ struct RoundDev {
     int first_singular;
     int ticket;        // last-block counter of the round kernel
     int next_new;      // smallest candidate the current round rejected
+    int nsurv;         // survivors of the current round's screen
     unsigned long long evals, exact, screened;
 };
 
@@ -334,6 +335,15 @@ __host__ __device__ inline int eval_block_doubles(int p) {
     const int ld = p + 1;
     return 2 * p * ld + PROBE_STRIDE + 2 * 32 + 8 + (p * ld + 1) / 2;
 }
+// decide kernel block part: A_c, B^-1 (FP64), probes (64), B^-1 in FP32
+__host__ __device__ inline int decide_block_doubles(int p) {
+    const int ld = p + 1;
+    return 2 * p * ld + PROBE_STRIDE + (p * ld + 1) / 2;
+}
+__host__ __device__ inline size_t decide_smem_bytes(int p, int wpb) {
+    const int ld = p + 1;
+    return (size_t)decide_block_doubles(p) * 8 + (size_t)wpb * ((size_t)p * ld + 64) * 8;
+}
 __host__ __device__ inline size_t eval_smem_bytes(int p, int wpb) {
     const int ld = p + 1;
     return (size_t)eval_block_doubles(p) * 8 + (size_t)wpb * ((size_t)p * ld + 64) * 8;
@@ -570,56 +580,32 @@ __device__ __forceinline__ bool round_last_block(int* ticket) {
     return s_last != 0;
 }
 
-// One round of Alg. 1 in one kernel.  Every patch's inverse, probe vector and
-// ||A^-1||_F were computed up front in batched launches, so the new entry
-// (patch st->next) is ready to stage.  Each warp takes candidates after it;
-// a rejected candidate stays unassigned and bids for being the next entry
-// (atomicMin): the smallest rejected index is exactly the smallest unassigned
-// patch after the round.  The last block records the entry and the next one.
-__global__ void __launch_bounds__(EVAL_THREADS, 4) k_round(RoundDev* st, int32_t* __restrict__ phi, int count,
-                                                 const double* __restrict__ Ag, int p,
-                                                 const double* __restrict__ Ball, const double* __restrict__ fro_all,
-                                                 const double* __restrict__ w_all, const int32_t* __restrict__ sing_all,
-                                                 SketchDB sk, double tol, int32_t* __restrict__ rep_local) {
-    extern __shared__ __align__(16) unsigned char smem[];
+// One round of Alg. 1 in two kernels.  Every patch's inverse, probes, sketch
+// and ||A^-1||_F were computed up front in batched launches, so the new entry
+// (patch st->next) is ready to stage.
+//   k_round_screen: one thread per unassigned candidate after the entry runs
+//     the sketch screen; a rejected candidate stays unassigned and bids for
+//     being the next entry (atomicMin); the others are appended to a global
+//     survivor list.
+//   k_round_decide: the warps of the whole grid share the survivor list
+//     (accepted ones come in runs of neighbouring patches, so a per-block
+//     queue would leave most SMs idle); rejected survivors bid as well.  The
+//     last block records the entry and the smallest rejected index, which is
+//     exactly the smallest unassigned patch after the round.
+__global__ void __launch_bounds__(EVAL_THREADS) k_round_screen(RoundDev* st, const int32_t* __restrict__ phi,
+                                                               int count, int p, SketchDB sk, double tol,
+                                                               int32_t* __restrict__ surv_list) {
+    __shared__ double sy[SK * 32];
+    __shared__ double sden[SK];
     if (st->done) return;
-    const int ld = p + 1;
     const int lane = threadIdx.x & 31;
-    const int wid = threadIdx.x >> 5;
-    const int wpb = blockDim.x >> 5;
     const int i0 = st->next;
-    const int m = st->m;
-    double* sAc = reinterpret_cast<double*>(smem);
-    double* sB = sAc + p * ld;
-    double* sw = sB + p * ld;
-    double* sy = sw + PROBE_STRIDE;
-    double* sden = sy + SK * 32;
-    float* sB32 = reinterpret_cast<float*>(sden + 8);
-    double* wbase = reinterpret_cast<double*>(smem) + eval_block_doubles(p) + (size_t)wid * (p * ld + 64);
-    WarpScratch ws{wbase, wbase + p * ld, wbase + p * ld + 32};
-    const double* a = Ag + (int64_t)i0 * p * p;
-    const double* bm = Ball + (int64_t)i0 * p * p;
-    for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
-        sAc[(t / p) * ld + (t % p)] = a[t];
-        const double b = bm[t];
-        sB[(t / p) * ld + (t % p)] = b;
-        sB32[(t / p) * ld + (t % p)] = (float)b;
-    }
-    if (threadIdx.x < PROBE_STRIDE) sw[threadIdx.x] = w_all[(int64_t)i0 * PROBE_STRIDE + threadIdx.x];
-    const double bfro = fro_all[i0];
     const double fc = sk.fa[i0], rhoc = sk.rho[i0];
     stage_sketch(sk.Y + (int64_t)i0 * SK * p, fc, p, sy, sden);
     __syncthreads();
-    unsigned long long my_evals = 0, my_exact = 0, my_screened = 0;
+    unsigned long long my_evals = 0, my_screened = 0;
     int my_min = count;
-    __shared__ int s_list[EVAL_THREADS];
-    __shared__ int s_cnt;
-    // a block takes blockDim.x consecutive candidates: every thread screens
-    // its own with the sketch bound, the survivors are queued in shared
-    // memory and the block's warps run the warp-wide decision on them in turn
     for (int base = i0 + 1 + blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
-        if (threadIdx.x == 0) s_cnt = 0;
-        __syncthreads();
         const int cand = base + threadIdx.x;
         const bool open = cand < count && phi[cand] == -1;
         bool rej = false;
@@ -630,13 +616,59 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_round(RoundDev* st, int32_t
         my_evals += __popc(opened);
         my_screened += __popc(opened & ~surv);
         int wb = 0;
-        if (lane == 0 && surv) wb = atomicAdd(&s_cnt, __popc(surv));
+        if (lane == 0 && surv) wb = atomicAdd(&st->nsurv, __popc(surv));
         wb = __shfl_sync(0xffffffffu, wb, 0);
-        if (open && !rej) s_list[wb + __popc(surv & ((1u << lane) - 1u))] = cand;
+        if (open && !rej) surv_list[wb + __popc(surv & ((1u << lane) - 1u))] = cand;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) my_min = min(my_min, __shfl_xor_sync(0xffffffffu, my_min, o));
+    if (lane == 0) {
+        if (my_evals) atomicAdd(&st->evals, my_evals);
+        if (my_screened) atomicAdd(&st->screened, my_screened);
+        if (my_min < count) atomicMin(&st->next_new, my_min);
+    }
+}
+
+__global__ void __launch_bounds__(EVAL_THREADS, 4) k_round_decide(RoundDev* st, int32_t* __restrict__ phi, int count,
+                                                                  const double* __restrict__ Ag, int p,
+                                                                  const double* __restrict__ Ball,
+                                                                  const double* __restrict__ fro_all,
+                                                                  const double* __restrict__ w_all,
+                                                                  const int32_t* __restrict__ sing_all, double tol,
+                                                                  const int32_t* __restrict__ surv_list,
+                                                                  int32_t* __restrict__ rep_local) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (st->done) return;
+    const int ld = p + 1;
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const int i0 = st->next;
+    const int m = st->m;
+    const int ns = st->nsurv;
+    unsigned long long my_exact = 0;
+    int my_min = count;
+    if (blockIdx.x * wpb < ns) {                      // block-uniform: this block has survivors
+        double* sAc = reinterpret_cast<double*>(smem);
+        double* sB = sAc + p * ld;
+        double* sw = sB + p * ld;
+        float* sB32 = reinterpret_cast<float*>(sw + PROBE_STRIDE);
+        double* wbase = reinterpret_cast<double*>(smem) + decide_block_doubles(p) + (size_t)wid * (p * ld + 64);
+        WarpScratch ws{wbase, wbase + p * ld, wbase + p * ld + 32};
+        const double* a = Ag + (int64_t)i0 * p * p;
+        const double* bm = Ball + (int64_t)i0 * p * p;
+        for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+            sAc[(t / p) * ld + (t % p)] = a[t];
+            const double b = bm[t];
+            sB[(t / p) * ld + (t % p)] = b;
+            sB32[(t / p) * ld + (t % p)] = (float)b;
+        }
+        if (threadIdx.x < PROBE_STRIDE) sw[threadIdx.x] = w_all[(int64_t)i0 * PROBE_STRIDE + threadIdx.x];
+        const double bfro = fro_all[i0];
         __syncthreads();
-        const int ns = s_cnt;
-        for (int q = wid; q < ns; q += wpb) {
-            const int c2 = s_list[q];
+        const int nwarps = gridDim.x * wpb;
+        for (int q = blockIdx.x * wpb + wid; q < ns; q += nwarps) {
+            const int c2 = surv_list[q];
             double dv;
             int dec = decide_pair(Ag + (int64_t)c2 * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, false, sw, sB32);
             if (dec < 0) {
@@ -647,14 +679,9 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_round(RoundDev* st, int32_t
             else my_min = min(my_min, c2);
             __syncwarp();
         }
-        __syncthreads();                    // the list is rebuilt next pass
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) my_min = min(my_min, __shfl_xor_sync(0xffffffffu, my_min, o));
     if (lane == 0) {
-        if (my_evals) atomicAdd(&st->evals, my_evals);
         if (my_exact) atomicAdd(&st->exact, my_exact);
-        if (my_screened) atomicAdd(&st->screened, my_screened);
         if (my_min < count) atomicMin(&st->next_new, my_min);
     }
     if (!round_last_block(&st->ticket)) return;
@@ -666,6 +693,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_round(RoundDev* st, int32_t
         const int nx = st->next_new;
         st->next_new = count;
         st->next = nx;
+        st->nsurv = 0;
         if (nx >= count) st->done = 1;
     }
 }
@@ -897,13 +925,17 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         const int ld = p + 1;
         const int wpb = EVAL_THREADS / 32;
         const size_t smem_eval = eval_smem_bytes(p, wpb);
-        if ((rc = set_smem((const void*)k_round, smem_eval)) != PSR_OK) break;
+        const size_t smem_dec = decide_smem_bytes(p, wpb);
+        if ((rc = set_smem((const void*)k_round_decide, smem_dec)) != PSR_OK) break;
+        int32_t* surv_list = nullptr;
+        PSR_CUDA(ctx, cudaMalloc(&surv_list, sizeof(int32_t) * (size_t)count));
         if ((rc = set_smem((const void*)k_seed_pass, smem_eval)) != PSR_OK) break;
         // one candidate per thread in the screen: enough blocks for every
-        // SM, a few passes each
+        // SM, a few passes each; the decide grid is one wave of 4 blocks per SM
         int eval_blocks = (count + EVAL_THREADS - 1) / EVAL_THREADS;
         if (eval_blocks > 152 * 4) eval_blocks = 152 * 4;
         if (eval_blocks < 1) eval_blocks = 1;
+        const int decide_blocks = 152 * 4;
         if (m0 > 0) {
             PSR_CUDA(ctx, cudaMalloc(&db.A, sizeof(double) * (size_t)m0 * p * p));
             PSR_CUDA(ctx, cudaMalloc(&db.Binv, sizeof(double) * (size_t)m0 * p * p));
@@ -964,8 +996,10 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         for (;;) {
             for (int r = 0; r < batch; ++r) {
                 count_launch();
-                k_round<<<eval_blocks, wpb * 32, smem_eval, s>>>(st, phi_l, count, Ag, p, Ball, fro_all, w_all,
-                                                                 sing_all, sk, tol, rep_l);
+                k_round_screen<<<eval_blocks, EVAL_THREADS, 0, s>>>(st, phi_l, count, p, sk, tol, surv_list);
+                count_launch();
+                k_round_decide<<<decide_blocks, EVAL_THREADS, smem_dec, s>>>(st, phi_l, count, Ag, p, Ball, fro_all,
+                                                                            w_all, sing_all, tol, surv_list, rep_l);
             }
             PSR_CHECK_LAUNCH(ctx, "Alg. 1 round kernel");
             issued += batch;
@@ -1001,6 +1035,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         cudaFree(w_all);
         cudaFree(sing_all);
         for (double* q : {skX, skY, skF, skR, sdY, sdF, sdR}) cudaFree(q);
+        cudaFree(surv_list);
         cudaFree(db.A);
         cudaFree(db.Binv);
         cudaFree(db.fro);

@@ -95,6 +95,29 @@ __device__ __forceinline__ double sum_partials(const double* part, int nb) {
     return block_sum(sum_strided(part, threadIdx.x, nb, blockDim.x), sp);
 }
 
+// Read-only load that the compiler neither sinks into a conditional block nor
+// reorders with the other loads of its batch (volatile asm), so that a batch
+// of basis loads is in flight together before the first use.
+__device__ __forceinline__ double ldnc(const double* p) {
+    double v;
+    asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ int ldnc_i(const int32_t* p) {
+    int v;
+    asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+// Entries e of basis vectors i0 .. i0+CH-1 (row index clamped to nv-1, so
+// every address is valid; the clamped copies are never used).
+template <int CH>
+__device__ __forceinline__ void load_basis(const double* __restrict__ V, int n, int e, int i0, int nv,
+                                           double (&v)[CH]) {
+#pragma unroll
+    for (int c = 0; c < CH; ++c) v[c] = ldnc(V + (int64_t)min(i0 + c, nv - 1) * n + e);
+}
+
 // ---------------------------------------------------------------- SpMV
 // mode 0: y = A x;  mode 1: y = b - A x and ||y||^2;  mode 2: y = A x and (x . y)
 template <int TPR>
@@ -115,28 +138,22 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ rowptr
         double s = 0.0;
         if (valid) {
             const int rs = rowptr[row], re = rowptr[row + 1];
-            // Four entries per lane per pass with all loads issued before the
-            // first multiply: the index -> x gathers of a row overlap instead
-            // of forming one dependent chain per entry.  The per-lane
-            // summation order (e, e + TPR, e + 2 TPR, ...) is unchanged.
+            // Four entries per lane per pass.  The loads are unconditional
+            // (positions past the row end are clamped to its last entry and
+            // their products zeroed), so all twelve of a pass are in flight
+            // together instead of each waiting for the multiply before it.
+            // The per-lane summation order (e, e + TPR, ...) is unchanged.
             for (int e = rs + sub; e < re; e += 4 * TPR) {
                 const bool b1 = e + TPR < re, b2 = e + 2 * TPR < re, b3 = e + 3 * TPR < re;
-                const int c0 = colidx[e];
-                const int c1 = b1 ? colidx[e + TPR] : c0;
-                const int c2 = b2 ? colidx[e + 2 * TPR] : c0;
-                const int c3 = b3 ? colidx[e + 3 * TPR] : c0;
-                const double a0 = vals[e];
-                const double a1 = b1 ? vals[e + TPR] : 0.0;
-                const double a2 = b2 ? vals[e + 2 * TPR] : 0.0;
-                const double a3 = b3 ? vals[e + 3 * TPR] : 0.0;
-                const double x0 = x[c0];
-                const double x1 = b1 ? x[c1] : 0.0;
-                const double x2 = b2 ? x[c2] : 0.0;
-                const double x3 = b3 ? x[c3] : 0.0;
+                const int e1 = b1 ? e + TPR : e, e2 = b2 ? e + 2 * TPR : e, e3 = b3 ? e + 3 * TPR : e;
+                const int c0 = ldnc_i(colidx + e), c1 = ldnc_i(colidx + e1);
+                const int c2 = ldnc_i(colidx + e2), c3 = ldnc_i(colidx + e3);
+                const double a0 = ldnc(vals + e), a1 = ldnc(vals + e1), a2 = ldnc(vals + e2), a3 = ldnc(vals + e3);
+                const double x0 = ldnc(x + c0), x1 = ldnc(x + c1), x2 = ldnc(x + c2), x3 = ldnc(x + c3);
                 s = fma(a0, x0, s);
-                if (b1) s = fma(a1, x1, s);
-                if (b2) s = fma(a2, x2, s);
-                if (b3) s = fma(a3, x3, s);
+                s = fma(b1 ? a1 : 0.0, x1, s);
+                s = fma(b2 ? a2 : 0.0, x2, s);
+                s = fma(b3 ? a3 : 0.0, x3, s);
             }
         }
 #pragma unroll
@@ -379,12 +396,20 @@ __global__ void __launch_bounds__(KT) k_mdot(const double* __restrict__ V, const
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] = 0.0;
     double accw = 0.0;
+    constexpr int CH = NV < 16 ? NV : 16;
     for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += gridDim.x * KT) {
         const double we = w[e];
         accw = fma(we, we, accw);
 #pragma unroll
-        for (int i = 0; i < NV; ++i)
-            if (i < nv) acc[i] = fma(V[(int64_t)i * n + e], we, acc[i]);
+        for (int c0 = 0; c0 < NV; c0 += CH) {
+            if (c0 < nv) {
+                double v[CH];
+                load_basis<CH>(V, n, e, c0, nv, v);
+#pragma unroll
+                for (int c = 0; c < CH; ++c)
+                    if (c0 + c < nv) acc[c0 + c] = fma(v[c], we, acc[c0 + c]);
+            }
+        }
     }
     block_partials<NV>(acc, nv, kd.part, sh);
     const double bw = block_sum(accw, shw);
@@ -427,11 +452,19 @@ __global__ void __launch_bounds__(KT) k_maxpy_mdot(const double* __restrict__ V,
     __syncthreads();
     if (!reorth) {
         double accw = 0.0;
+        constexpr int CH = NV < 16 ? NV : 16;
         for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += gridDim.x * KT) {
             double we = w[e];
 #pragma unroll
-            for (int i = 0; i < NV; ++i)
-                if (i < nv) we = fma(-sh_h[i], V[(int64_t)i * n + e], we);
+            for (int c0 = 0; c0 < NV; c0 += CH) {
+                if (c0 < nv) {
+                    double v[CH];
+                    load_basis<CH>(V, n, e, c0, nv, v);
+#pragma unroll
+                    for (int c = 0; c < CH; ++c)
+                        if (c0 + c < nv) we = fma(-sh_h[c0 + c], v[c], we);
+                }
+            }
             w[e] = we;
             accw = fma(we, we, accw);
         }
@@ -445,17 +478,31 @@ __global__ void __launch_bounds__(KT) k_maxpy_mdot(const double* __restrict__ V,
     double acc[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    constexpr int CH = NV < 16 ? NV : 16;
     for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += gridDim.x * KT) {
-        double vi[NV];
-#pragma unroll
-        for (int i = 0; i < NV; ++i) vi[i] = (i < nv) ? V[(int64_t)i * n + e] : 0.0;
         double we = w[e];
 #pragma unroll
-        for (int i = 0; i < NV; ++i)
-            if (i < nv) we = fma(-sh_h[i], vi[i], we);
-        w[e] = we;
+        for (int c0 = 0; c0 < NV; c0 += CH) {
+            if (c0 < nv) {
+                double v[CH];
+                load_basis<CH>(V, n, e, c0, nv, v);
 #pragma unroll
-        for (int i = 0; i < NV; ++i) acc[i] = fma(vi[i], we, acc[i]);
+                for (int c = 0; c < CH; ++c)
+                    if (c0 + c < nv) we = fma(-sh_h[c0 + c], v[c], we);
+            }
+        }
+        w[e] = we;
+        // second projection: the chunks are read again (L1 hits)
+#pragma unroll
+        for (int c0 = 0; c0 < NV; c0 += CH) {
+            if (c0 < nv) {
+                double v[CH];
+                load_basis<CH>(V, n, e, c0, nv, v);
+#pragma unroll
+                for (int c = 0; c < CH; ++c)
+                    if (c0 + c < nv) acc[c0 + c] = fma(v[c], we, acc[c0 + c]);
+            }
+        }
     }
     block_partials<NV>(acc, nv, kd.part, sh);
     if (!last_block(kd.ictl + I_CNT + 4)) return;
@@ -480,11 +527,19 @@ __global__ void __launch_bounds__(KT) k_maxpy(const double* __restrict__ V, doub
     if (threadIdx.x < NV) sh_h[threadIdx.x] = (threadIdx.x < nv) ? Hv(kd.scal, m)[threadIdx.x] : 0.0;
     __syncthreads();
     double acc = 0.0;
+    constexpr int CH = NV < 16 ? NV : 16;
     for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += gridDim.x * KT) {
         double we = w[e];
 #pragma unroll
-        for (int i = 0; i < NV; ++i)
-            if (i < nv) we = fma(-sh_h[i], V[(int64_t)i * n + e], we);
+        for (int c0 = 0; c0 < NV; c0 += CH) {
+            if (c0 < nv) {
+                double v[CH];
+                load_basis<CH>(V, n, e, c0, nv, v);
+#pragma unroll
+                for (int c = 0; c < CH; ++c)
+                    if (c0 + c < nv) we = fma(-sh_h[c0 + c], v[c], we);
+            }
+        }
         w[e] = we;
         acc = fma(we, we, acc);
     }
