@@ -36,6 +36,20 @@ template <> struct Comp<__nv_bfloat16> { using type = float; };
 template <typename T> __device__ __forceinline__ T to_store(double v) { return (T)v; }
 template <> __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }
 
+// Read-only loads kept in the order written and never moved into a
+// conditional block (volatile asm), so that a batch of them is in flight
+// together before the first use.
+__device__ __forceinline__ double ldg_nc(const double* p) {
+    double v;
+    asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ int ldg_nc_i(const int32_t* p) {
+    int v;
+    asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
 // ------------------------------------------------------------ kernels
 // Generic: one patch per warp, lane a owns rows a, a+32, ...; p <= 128.
 template <typename T>
@@ -152,20 +166,23 @@ __global__ void __launch_bounds__(256) k_sweep_tpp(const int32_t* __restrict__ w
     for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nwt; t += nw) {
         const int c = wtiles[3 * t], start = wtiles[3 * t + 1], cnt = wtiles[3 * t + 2];
         const bool live = lane < cnt;
-        const int k = start + lane;
+        const int k = start + (live ? lane : 0);
+        // Unconditional loads (local DOF index clamped to p-1, idle lanes on
+        // the tile's first patch): the p map loads, then the p gathers of r,
+        // are each in flight together instead of one dependent pair per DOF.
         int dof[PM];
         C x[PM];
 #pragma unroll
-        for (int a = 0; a < PM; ++a) {
-            dof[a] = 0;
-            x[a] = (C)0;
-            if (live && a < p) {
-                dof[a] = sdofs_t[(int64_t)a * count + k];
-                double v = r[dof[a]];
-                if (wg) v *= wg[dof[a]];
-                x[a] = (C)v;
-            }
+        for (int a = 0; a < PM; ++a) dof[a] = ldg_nc_i(sdofs_t + (int64_t)min(a, p - 1) * count + k);
+        double rv[PM];
+#pragma unroll
+        for (int a = 0; a < PM; ++a) rv[a] = ldg_nc(r + dof[a]);
+        if (wg) {
+#pragma unroll
+            for (int a = 0; a < PM; ++a) rv[a] *= ldg_nc(wg + dof[a]);
         }
+#pragma unroll
+        for (int a = 0; a < PM; ++a) x[a] = (live && a < p) ? (C)rv[a] : (C)0;
         const T* B = rinv + (int64_t)c * p * p;
 #pragma unroll
         for (int a = 0; a < PM; ++a) {
