@@ -50,7 +50,7 @@ CONFIGS = {
 
 # kernel(s) behind each timing class of the library's per-kernel timing
 KT_KERNEL_NAMES = {"sweep": "patch sweep (k_sweep_*)", "spmv": "k_spmv (CSR SpMV, FP64)",
-                   "mdot": "k_mdot (FGMRES projections V^T w)", "maxpy": "k_maxpy (FGMRES w -= V h)",
+                   "mdot": "k_arnoldi (fused FGMRES Arnoldi step) / k_mdot", "maxpy": "k_maxpy (FGMRES w -= V h)",
                    "vec": "vector kernels (k_fg_scale / CG updates)"}
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, ncu,

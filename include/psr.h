@@ -191,7 +191,9 @@ int64_t psr_kernel_launches(void);
  * the outer solve.  Classes of the per-iteration kernels: */
 #define PSR_KT_SWEEP 0   /* preconditioner application z = M^-1 r (Eq. 1 / Eq. 3) */
 #define PSR_KT_SPMV 1    /* A z inside the iteration (CSR, FP64) */
-#define PSR_KT_MDOT 2    /* FGMRES first projection h = V^T w (with ||w||^2) */
+#define PSR_KT_MDOT 2    /* FGMRES Gram-Schmidt: the fused Arnoldi step (one cooperative
+                            launch: projection, update(s), normalisation), or without
+                            cooperative launch the first projection h = V^T w */
 #define PSR_KT_MAXPY 3   /* FGMRES updates w -= V h: the first (fused with the second
                             projection when the step reorthogonalises, else with
                             ||w|| and the Arnoldi finish), and the second update */
@@ -214,7 +216,8 @@ int psr_set_kernel_timing(psr_ctx* ctx, int enable);
  * launches = timed launches, bytes = summed algorithmic bytes of those
  * launches (SpMV: 12 nnz + 4 (n+1) + 16 n; V^T w with j+1 basis vectors:
  * 8 (j+2) n; each w -= V h: 8 (j+3) n, the second one only when step j took
- * the second Gram-Schmidt pass; sweep: 24 n + 4 sum(p_k) + 4 n_patches +
+ * the second Gram-Schmidt pass; the fused step the sum of these plus 16 n for
+ * the normalisation; sweep: 24 n + 4 sum(p_k) + 4 n_patches +
  * stored factor bytes; FGMRES scale 16 n; CG kernels their vector reads and
  * writes).  Any pointer may be NULL.  Host-only; PSR_ERR_INVALID_ARG for a
  * NULL ctx or count outside 1 .. PSR_KT_COUNT. */

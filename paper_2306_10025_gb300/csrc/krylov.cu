@@ -24,7 +24,7 @@ namespace psr {
 int sweep_apply_ex(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s);
 
 enum { S_RZ = 0, S_PQ, S_ALPHA, S_BETA, S_RN, S_R0, S_RTOL, S_H = 16 };
-enum { I_STOP = 0, I_CONV, I_IT, I_K, I_MAXIT, I_M, I_REORTH, I_CNT = 8, I_NCNT = 8 };
+enum { I_STOP = 0, I_CONV, I_IT, I_K, I_MAXIT, I_M, I_REORTH, I_ERR, I_CNT = 8, I_NCNT = 8 };
 
 struct KDims {
     int n, m, nb;
@@ -550,6 +550,157 @@ __global__ void __launch_bounds__(KT) k_maxpy(const double* __restrict__ V, doub
     if (threadIdx.x == 0) arnoldi_finish(kd, j, tot);
 }
 
+// ---------------------------------------------------------------- fused Arnoldi step
+// Grid barrier of a cooperatively launched kernel (all blocks co-resident, so
+// every wait ends); the spin is bounded all the same: past the limit the
+// error flag is set, the stop flag raised and the barrier left, so a fault
+// surfaces as PSR_ERR_TIMEOUT on the host instead of a hang.
+__device__ __forceinline__ void grid_barrier(unsigned int* bar, int32_t* ictl) {
+    __threadfence();                                  // every thread's writes before arriving
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* vgen = bar + 1;
+        const unsigned int g = *vgen;
+        const unsigned int arrived = atomicAdd(bar, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            bar[0] = 0u;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == g) {
+                if (++spins > (1ll << 24)) {
+                    atomicExch(ictl + I_ERR, 1);
+                    atomicExch(ictl + I_STOP, 1);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// w <- w - V h over the thread's elements (h in shared memory, nv entries);
+// PROJ: also acc[i] += V_i[e] w[e] (second projection), else accw += w[e]^2.
+template <int NV, bool PROJ>
+__device__ __forceinline__ void update_pass(const double* __restrict__ V, double* __restrict__ w, int n, int nv,
+                                            const double* sh_h, double (&acc)[NV], double& accw) {
+    constexpr int CH = NV < 16 ? NV : 16;
+    for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += gridDim.x * KT) {
+        double we = w[e];
+#pragma unroll
+        for (int c0 = 0; c0 < NV; c0 += CH) {
+            if (c0 < nv) {
+#pragma unroll
+                for (int c = 0; c < CH; ++c)
+                    if (c0 + c < nv) we = fma(-sh_h[c0 + c], V[(int64_t)(c0 + c) * n + e], we);
+            }
+        }
+        w[e] = we;
+        if (PROJ) {
+#pragma unroll
+            for (int i = 0; i < NV; ++i)
+                if (i < nv) acc[i] = fma(V[(int64_t)i * n + e], we, acc[i]);
+        } else {
+            accw = fma(we, we, accw);
+        }
+    }
+}
+
+// The whole orthogonalisation of step j in one cooperative launch: w = V_{j+1}
+// (on entry A z_j) is projected (h = V^T w, ||w||^2), updated, projected and
+// updated again when the Kahan-Parlett test asks for it, normalised, and the
+// Arnoldi step finished.  Grid barriers replace the kernel boundaries; every
+// block sums the block partials of a pass itself (same order everywhere, so
+// all blocks hold bitwise the same h and norms), and each pass has its own
+// partial region.
+template <int NV>
+__global__ void __launch_bounds__(KT) k_arnoldi(const double* __restrict__ V, double* __restrict__ w, int n, int j,
+                                               KDims kd, double* __restrict__ part, unsigned int* bar) {
+    __shared__ double sh[NV][KT / 32 + 1];
+    __shared__ double sh_h[NV];
+    __shared__ double shw[32];
+    __shared__ double s_w2;
+    if (kd.ictl[I_STOP]) return;                      // same value in every block
+    const int nv = j + 1;
+    const int m = kd.m;
+    const int G = gridDim.x;
+    const int T = KT / NV;
+    double* P1 = part;
+    double* P2 = part + (int64_t)(NV + 1) * G;
+    double* P3 = part + (int64_t)2 * (NV + 1) * G;
+    double acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    double accw = 0.0;
+    // pass 1: h = V^T w and ||w||^2
+    for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += G * KT) {
+        const double we = w[e];
+        accw = fma(we, we, accw);
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+            if (i < nv) acc[i] = fma(V[(int64_t)i * n + e], we, acc[i]);
+    }
+    block_partials<NV>(acc, nv, P1, sh);
+    double bs = block_sum(accw, shw);
+    if (threadIdx.x == 0) P1[(int64_t)NV * G + blockIdx.x] = bs;
+    grid_barrier(bar, kd.ictl);
+    {
+        const double v = final_partials<NV>(P1, nv, G);
+        if (threadIdx.x / T < nv && threadIdx.x % T == 0) sh_h[threadIdx.x / T] = v;
+        const double t = sum_partials(P1 + (int64_t)NV * G, G);
+        if (threadIdx.x == 0) s_w2 = t;
+        __syncthreads();
+    }
+    double h2 = 0.0;
+    for (int q = 0; q < nv; ++q) h2 = fma(sh_h[q], sh_h[q], h2);
+    const bool reorth = (s_w2 - h2 < 0.5 * s_w2);
+    if (blockIdx.x == 0) {
+        if (threadIdx.x < nv) Hm(kd.scal, m)[threadIdx.x * m + j] = sh_h[threadIdx.x];
+        if (threadIdx.x == 0) kd.rflag[j] = reorth ? 1 : 0;
+    }
+    // pass 2: w <- w - V h, with the second projection or ||w||^2
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    accw = 0.0;
+    double wn2;
+    if (reorth) {
+        update_pass<NV, true>(V, w, n, nv, sh_h, acc, accw);
+        block_partials<NV>(acc, nv, P2, sh);
+        grid_barrier(bar, kd.ictl);
+        const double v = final_partials<NV>(P2, nv, G);
+        __syncthreads();                              // sh_h of pass 2 fully read
+        if (threadIdx.x / T < nv && threadIdx.x % T == 0) sh_h[threadIdx.x / T] = v;
+        __syncthreads();
+        if (blockIdx.x == 0 && threadIdx.x < nv) Hm(kd.scal, m)[threadIdx.x * m + j] += sh_h[threadIdx.x];
+        // pass 3: w <- w - V h2 and ||w||^2
+        update_pass<NV, false>(V, w, n, nv, sh_h, acc, accw);
+        bs = block_sum(accw, shw);
+        if (threadIdx.x == 0) P3[(int64_t)NV * G + blockIdx.x] = bs;
+        grid_barrier(bar, kd.ictl);
+        const double t = sum_partials(P3 + (int64_t)NV * G, G);
+        if (threadIdx.x == 0) s_w2 = t;
+    } else {
+        update_pass<NV, false>(V, w, n, nv, sh_h, acc, accw);
+        bs = block_sum(accw, shw);
+        if (threadIdx.x == 0) P2[(int64_t)NV * G + blockIdx.x] = bs;
+        grid_barrier(bar, kd.ictl);
+        const double t = sum_partials(P2 + (int64_t)NV * G, G);
+        if (threadIdx.x == 0) s_w2 = t;
+    }
+    __syncthreads();
+    wn2 = s_w2;
+    // normalise the thread's elements; block 0 finishes the Arnoldi step
+    const double hn = sqrt(wn2);
+    if (hn != 0.0) {
+        const double inv = 1.0 / hn;
+        for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += G * KT) w[e] = w[e] * inv;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) arnoldi_finish(kd, j, wn2);
+}
+
 __global__ void k_fg_scale(double* __restrict__ w, int n, KDims kd) {
     if (kd.ictl[I_STOP]) return;
     const double hn = kd.scal[S_BETA];
@@ -645,7 +796,7 @@ static int kt_begin(psr_ctx* ctx, int kind, int j, double bytes, cudaStream_t s)
         PSR_CUDA(ctx, cudaEventCreate(&e));
         ctx->kt_ev.push_back(e);
     }
-    ctx->kt_marks.push_back(KtMark{kind, j, bytes, false});
+    ctx->kt_marks.push_back(KtMark{kind, j, bytes, 0.0});
     PSR_CUDA(ctx, kt_record(ctx->kt_ev[2 * i], s));
     return PSR_OK;
 }
@@ -659,7 +810,7 @@ static int kt_end(psr_ctx* ctx, cudaStream_t s) {
 
 // After a block ran `done` iterations (all its events have completed);
 // rflag[j] (host copy, FGMRES only) tells whether step j took the second
-// Gram-Schmidt pass: a second update launched without it moved no bytes.
+// Gram-Schmidt pass, whose bytes a mark carries separately.
 static int kt_collect(psr_ctx* ctx, int done, const int32_t* rflag) {
     if (!ctx->kt_on) return PSR_OK;
     for (size_t i = 0; i < ctx->kt_marks.size(); ++i) {
@@ -669,7 +820,7 @@ static int kt_collect(psr_ctx* ctx, int done, const int32_t* rflag) {
         PSR_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->kt_ev[2 * i], ctx->kt_ev[2 * i + 1]));
         ctx->kt_ms[mk.kind] += ms;
         ctx->kt_n[mk.kind] += 1;
-        if (!mk.second_pass || (rflag && rflag[mk.j])) ctx->kt_bytes[mk.kind] += mk.bytes;
+        ctx->kt_bytes[mk.kind] += mk.bytes + ((rflag && rflag[mk.j]) ? mk.bytes_reorth : 0.0);
     }
     return PSR_OK;
 }
@@ -713,6 +864,21 @@ int krylov_alloc(psr_ctx* ctx) {
     PSR_CUDA(ctx, cudaMalloc(&w.ictl, 32 * sizeof(int32_t)));
     PSR_CUDA(ctx, cudaMalloc(&w.rflag, 64 * sizeof(int32_t)));
     PSR_CUDA(ctx, cudaMemset(w.rflag, 0, 64 * sizeof(int32_t)));
+    // fused Arnoldi step: cooperative launches of one block per SM
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
+    w.coop = false;
+    if (coop && ctx->opts.krylov == PSR_KRYLOV_FGMRES) {
+        int b8 = 0, b16 = 0, b32 = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b8, (const void*)k_arnoldi<8>, KT, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b16, (const void*)k_arnoldi<16>, KT, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, (const void*)k_arnoldi<32>, KT, 0);
+        cudaGetLastError();
+        w.coop = b8 >= 1 && b16 >= 1 && b32 >= 1;
+    }
+    PSR_CUDA(ctx, cudaMalloc(&w.part_arn, (size_t)3 * 33 * w.sms * sizeof(double)));
+    PSR_CUDA(ctx, cudaMalloc(&w.bar, 2 * sizeof(unsigned int)));
+    PSR_CUDA(ctx, cudaMemset(w.bar, 0, 2 * sizeof(unsigned int)));
     PSR_CUDA(ctx, cudaMemset(w.ictl, 0, 32 * sizeof(int32_t)));
     return PSR_OK;
 }
@@ -722,6 +888,8 @@ void krylov_free(psr_ctx* ctx) {
     for (double* p : {w.x, w.b, w.r, w.z, w.p, w.q, w.V, w.Z, w.partial, w.scal, w.hist}) cudaFree(p);
     cudaFree(w.ictl);
     cudaFree(w.rflag);
+    cudaFree(w.part_arn);
+    cudaFree(w.bar);
     w = KrylovWS{};
     if (ctx->g_cycle) cudaGraphExecDestroy(ctx->g_cycle);
     ctx->g_cycle = nullptr;
@@ -810,9 +978,33 @@ static int enqueue_cgs2(psr_ctx* ctx, KDims kd, int j, double* Vn, cudaStream_t 
     KT_BEGIN(PSR_KT_MAXPY, j, (j + 3) * vb);
     count_launch(); k_maxpy_mdot<NV><<<g2, KT, 0, s>>>(w.V, Vn, n, j, kd);
     KT_END();
-    KT_BEGIN(PSR_KT_MAXPY, j, (j + 3) * vb);
-    if (ctx->kt_on && !ctx->kt_marks.empty()) ctx->kt_marks.back().second_pass = true;
+    KT_BEGIN(PSR_KT_MAXPY, j, 0.0);
+    if (ctx->kt_on && !ctx->kt_marks.empty()) ctx->kt_marks.back().bytes_reorth = (j + 3) * vb;
     count_launch(); k_maxpy<NV><<<g3, KT, 0, s>>>(w.V, Vn, n, j, kd);
+    KT_END();
+    return PSR_OK;
+}
+
+// The fused Arnoldi step: one cooperative launch of one block per SM.
+template <int NV>
+static int enqueue_arnoldi(psr_ctx* ctx, KDims kd, int j, double* Vn, cudaStream_t s) {
+    KrylovWS& w = ctx->ws;
+    const int n = ctx->n;
+    const double vb = 8.0 * n;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)w.sms);
+    cfg.blockDim = dim3(KT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    KT_BEGIN(PSR_KT_MDOT, j, ((j + 2) + (j + 3) + 2) * vb);
+    if (ctx->kt_on && !ctx->kt_marks.empty()) ctx->kt_marks.back().bytes_reorth = (j + 3) * vb;
+    count_launch();
+    PSR_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_arnoldi<NV>, (const double*)w.V, Vn, n, j, kd, w.part_arn, w.bar));
     KT_END();
     return PSR_OK;
 }
@@ -834,6 +1026,13 @@ static int enqueue_fg_cycle(psr_ctx* ctx, KDims kd, cudaStream_t s) {
         launch_spmv(ctx, Zj, Vn, nullptr, 0, 0, kd, 1, w.nspmv, s);
         KT_END();
         int rc2 = PSR_OK;
+        if (w.coop) {
+            if (j < 8) rc2 = enqueue_arnoldi<8>(ctx, kd, j, Vn, s);
+            else if (j < 16) rc2 = enqueue_arnoldi<16>(ctx, kd, j, Vn, s);
+            else rc2 = enqueue_arnoldi<32>(ctx, kd, j, Vn, s);
+            if (rc2 != PSR_OK) return rc2;
+            continue;
+        }
         if (j < 8) rc2 = enqueue_cgs2<8>(ctx, kd, j, Vn, s);
         else if (j < 16) rc2 = enqueue_cgs2<16>(ctx, kd, j, Vn, s);
         else rc2 = enqueue_cgs2<32>(ctx, kd, j, Vn, s);
@@ -866,6 +1065,7 @@ int krylov_solve(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_s
     hctl[I_M] = m;
     double rtol = ctx->opts.rtol;
     PSR_CUDA(ctx, cudaMemcpyAsync(w.ictl, hctl, sizeof(hctl), cudaMemcpyHostToDevice, s));
+    PSR_CUDA(ctx, cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned int), s));
     PSR_CUDA(ctx, cudaMemcpyAsync(w.scal + S_RTOL, &rtol, sizeof(double), cudaMemcpyHostToDevice, s));
     // r = b, keep a copy of b, x = 0, r0 = ||b||
     count_launch(); k_init_norm<<<nb, 256, 0, s>>>(b, w.b, w.r, n, kd, 1, w.x);
@@ -878,7 +1078,7 @@ int krylov_solve(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_s
     }
     const int block = cg ? 8 : 1;
     int32_t* hstop = nullptr;                     // control ints, then the step flags
-    PSR_CUDA(ctx, cudaMallocHost(&hstop, (4 + 64) * sizeof(int32_t)));
+    PSR_CUDA(ctx, cudaMallocHost(&hstop, (8 + 64) * sizeof(int32_t)));
     // capture one block / cycle into a graph (the pointers are the context's own)
     if (ctx->opts.use_graph && !ctx->g_cycle) {
         cudaStream_t cs;
@@ -921,11 +1121,16 @@ int krylov_solve(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_s
             rc = cg ? enqueue_cg_block(ctx, kd, block, s) : enqueue_fg_cycle(ctx, kd, s);
             if (rc != PSR_OK) break;
         }
-        PSR_CUDA(ctx, cudaMemcpyAsync(hstop, w.ictl, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        PSR_CUDA(ctx, cudaMemcpyAsync(hstop, w.ictl, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         if (ctx->kt_on && !cg)
-            PSR_CUDA(ctx, cudaMemcpyAsync(hstop + 4, w.rflag, (size_t)m * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            PSR_CUDA(ctx, cudaMemcpyAsync(hstop + 8, w.rflag, (size_t)m * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         PSR_CUDA(ctx, cudaStreamSynchronize(s));
-        rc = kt_collect(ctx, hstop[I_IT] - it_before, cg ? nullptr : hstop + 4);
+        if (hstop[I_ERR]) {
+            set_error(ctx, "a grid barrier of the Arnoldi kernel gave up waiting");
+            rc = PSR_ERR_TIMEOUT;
+            break;
+        }
+        rc = kt_collect(ctx, hstop[I_IT] - it_before, cg ? nullptr : hstop + 8);
         if (rc != PSR_OK) break;
         it_before = hstop[I_IT];
         if (hstop[I_STOP]) break;

@@ -108,6 +108,9 @@ struct KrylovWS {
     double* hist = nullptr;     // [maxit + 1]
     int32_t* ictl = nullptr;    // device control ints
     int32_t* rflag = nullptr;   // [64] FGMRES: second Gram-Schmidt pass taken at step j
+    double* part_arn = nullptr; // partials of the fused Arnoldi step, 3 passes x 33 x sms
+    unsigned int* bar = nullptr;  // grid barrier of the fused Arnoldi step (count, generation)
+    bool coop = false;          // fused Arnoldi step (cooperative launch) available
     int nblk = 0;
     int nspmv = 0;
     int sms = 0;           // streaming multiprocessors of the device
@@ -120,7 +123,7 @@ struct KtMark {
     int kind;
     int j;
     double bytes;
-    bool second_pass;      // FGMRES second update: moves its bytes only when step j reorthogonalised
+    double bytes_reorth;   // added when step j took the second Gram-Schmidt pass
 };
 
 }  // namespace psr
