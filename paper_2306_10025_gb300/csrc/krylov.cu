@@ -119,6 +119,23 @@ __device__ __forceinline__ void load_basis(const double* __restrict__ V, int n, 
 }
 
 // ---------------------------------------------------------------- SpMV
+// Last block of a reducing SpMV (thread 0): fin 1 = CG pq and alpha;
+// fin 2 = FGMRES restart, beta = ||b - A x||.
+__device__ void spmv_finish(KDims kd, int fin, double tot) {
+    double* sc = kd.scal;
+    int32_t* ic = kd.ictl;
+    if (fin == 1) {
+        sc[S_PQ] = tot;
+        sc[S_ALPHA] = sc[S_RZ] / tot;
+    } else if (fin == 2) {
+        const double beta = sqrt(tot);
+        sc[S_RN] = beta;
+        double* g = Gv(sc, ic[I_M]);
+        g[0] = beta;
+        if (beta == 0.0) { ic[I_STOP] = 1; ic[I_CONV] = 1; }
+    }
+}
+
 // mode 0: y = A x;  mode 1: y = b - A x and ||y||^2;  mode 2: y = A x and (x . y)
 template <int TPR>
 __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
@@ -175,18 +192,93 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ rowptr
     if (!last_block(kd.ictl + I_CNT + 0)) return;
     const double tot = sum_partials(kd.part, gridDim.x);
     if (threadIdx.x != 0) return;
-    double* sc = kd.scal;
-    int32_t* ic = kd.ictl;
-    if (fin == 1) {                 // CG: pq and alpha
-        sc[S_PQ] = tot;
-        sc[S_ALPHA] = sc[S_RZ] / tot;
-    } else if (fin == 2) {          // FGMRES restart: beta = ||b - A x||
-        const double beta = sqrt(tot);
-        sc[S_RN] = beta;
-        double* g = Gv(sc, ic[I_M]);
-        g[0] = beta;
-        if (beta == 0.0) { ic[I_STOP] = 1; ic[I_CONV] = 1; }
+    spmv_finish(kd, fin, tot);
+}
+
+// ---------------------------------------------------------------- SpMV (SELL-32)
+// Sliced ELL copy of A built at setup: slices of 32 consecutive rows, each
+// padded to its longest row and stored column-major (entry k of the slice's
+// lane l at slice_ptr[s] + 32 k + l), padding with value 0 and the row's own
+// column.  One thread per row: the loads of a warp are contiguous, the
+// entries of a row are summed in CSR order by one thread (no cross-lane
+// reduction, no FP64 instruction spent on another row's tail: all rows of a
+// warp share the slice width).
+__global__ void k_sell_width(const int32_t* __restrict__ rowptr, int n, int nslices, int32_t* __restrict__ width) {
+    const int lane = threadIdx.x & 31;
+    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (s >= nslices) return;
+    const int r = s * 32 + lane;
+    int len = (r < n) ? rowptr[r + 1] - rowptr[r] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
+    if (lane == 0) width[s] = len;
+}
+
+__global__ void k_sell_fill(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                            const double* __restrict__ vals, int n, int nslices, const int64_t* __restrict__ sptr,
+                            int32_t* __restrict__ scols, double* __restrict__ svals) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = r >> 5, lane = r & 31;
+    if (s >= nslices) return;
+    const int64_t base = sptr[s] + lane;
+    const int width = (int)((sptr[s + 1] - sptr[s]) >> 5);
+    const int rs = (r < n) ? rowptr[r] : 0;
+    const int len = (r < n) ? rowptr[r + 1] - rs : 0;
+    const int self = (r < n) ? r : 0;
+    for (int k = 0; k < width; ++k) {
+        const bool in = k < len;
+        scols[base + 32 * (int64_t)k] = in ? colidx[rs + k] : self;
+        svals[base + 32 * (int64_t)k] = in ? vals[rs + k] : 0.0;
     }
+}
+
+// mode 0: y = A x;  mode 1: y = b - A x and ||y||^2;  mode 2: y = A x and (x . y)
+__global__ void __launch_bounds__(256) k_spmv_sell(const int64_t* __restrict__ sptr, const int32_t* __restrict__ scols,
+                                                   const double* __restrict__ svals, const double* __restrict__ x,
+                                                   double* __restrict__ y, const double* __restrict__ b, int n,
+                                                   int nrows_pad, int mode, KDims kd, int stop_check, int fin) {
+    __shared__ double sh[32];
+    if (stop_check && kd.ictl[I_STOP]) return;
+    double acc = 0.0;
+    // block-uniform loop bound: every thread reaches the block reduction
+    for (int base = blockIdx.x * blockDim.x; base < nrows_pad; base += gridDim.x * blockDim.x) {
+        const int row = base + threadIdx.x;
+        const int s = row >> 5, lane = row & 31;
+        const bool live = row < nrows_pad;               // whole warps: slices are 32 rows
+        const int64_t o = live ? sptr[s] + lane : 0;
+        const int width = live ? (int)((sptr[s + 1] - sptr[s]) >> 5) : 0;
+        double sum = 0.0;
+        int k = 0;
+        for (; k + 4 <= width; k += 4) {
+            const int c0 = ldnc_i(scols + o + 32 * (int64_t)k), c1 = ldnc_i(scols + o + 32 * (int64_t)(k + 1));
+            const int c2 = ldnc_i(scols + o + 32 * (int64_t)(k + 2)), c3 = ldnc_i(scols + o + 32 * (int64_t)(k + 3));
+            const double a0 = ldnc(svals + o + 32 * (int64_t)k), a1 = ldnc(svals + o + 32 * (int64_t)(k + 1));
+            const double a2 = ldnc(svals + o + 32 * (int64_t)(k + 2)), a3 = ldnc(svals + o + 32 * (int64_t)(k + 3));
+            const double x0 = ldnc(x + c0), x1 = ldnc(x + c1), x2 = ldnc(x + c2), x3 = ldnc(x + c3);
+            sum = fma(a0, x0, sum);
+            sum = fma(a1, x1, sum);
+            sum = fma(a2, x2, sum);
+            sum = fma(a3, x3, sum);
+        }
+        for (; k < width; ++k) sum = fma(ldnc(svals + o + 32 * (int64_t)k), ldnc(x + ldnc_i(scols + o + 32 * (int64_t)k)), sum);
+        if (row < n) {
+            if (mode == 1) {
+                const double v = b[row] - sum;
+                y[row] = v;
+                acc = fma(v, v, acc);
+            } else {
+                y[row] = sum;
+                if (mode == 2) acc = fma(x[row], sum, acc);
+            }
+        }
+    }
+    if (mode == 0) return;
+    const double bs = block_sum(acc, sh);
+    if (threadIdx.x == 0) kd.part[blockIdx.x] = bs;
+    if (!last_block(kd.ictl + I_CNT + 0)) return;
+    const double tot = sum_partials(kd.part, gridDim.x);
+    if (threadIdx.x != 0) return;
+    spmv_finish(kd, fin, tot);
 }
 
 // ---------------------------------------------------------------- vectors
@@ -751,6 +843,16 @@ static int spmv_tpr(psr_ctx* ctx) {
 
 static void launch_spmv(psr_ctx* ctx, const double* x, double* y, const double* b, int mode, int fin,
                         KDims kd, int stop_check, int nb_max, cudaStream_t s) {
+    const KrylovWS& w = ctx->ws;
+    if (w.sell_ptr) {
+        const int nrows_pad = w.nslices * 32;
+        const int need = (nrows_pad + 255) / 256;
+        const int nb = std::max(1, mode == 0 ? need : std::min(need, nb_max));
+        count_launch();
+        k_spmv_sell<<<nb, 256, 0, s>>>(w.sell_ptr, w.sell_cols, w.sell_vals, x, y, b, ctx->n, nrows_pad, mode, kd,
+                                       stop_check, fin);
+        return;
+    }
     const int tpr = spmv_tpr(ctx);
     const int n = ctx->n;
     // one row per TPR-thread group; mode 0 (no reduction) covers all rows in
@@ -855,6 +957,29 @@ int krylov_alloc(psr_ctx* ctx) {
         PSR_CUDA(ctx, cudaMalloc(&w.V, (size_t)(m + 1) * n * 8));
         PSR_CUDA(ctx, cudaMalloc(&w.Z, (size_t)m * n * 8));
     }
+    // SELL-32 copy of A for the SpMV
+    {
+        w.nslices = (ctx->n + 31) / 32;
+        int32_t* widths = nullptr;
+        PSR_CUDA(ctx, cudaMalloc(&widths, sizeof(int32_t) * (size_t)w.nslices));
+        count_launch();
+        k_sell_width<<<(w.nslices + 7) / 8, 256>>>(ctx->rowptr, ctx->n, w.nslices, widths);
+        std::vector<int32_t> hw((size_t)w.nslices);
+        PSR_CUDA(ctx, cudaMemcpy(hw.data(), widths, sizeof(int32_t) * hw.size(), cudaMemcpyDeviceToHost));
+        cudaFree(widths);
+        std::vector<int64_t> hp((size_t)w.nslices + 1, 0);
+        for (int q = 0; q < w.nslices; ++q) hp[q + 1] = hp[q] + 32 * (int64_t)hw[q];
+        const int64_t total = std::max<int64_t>(hp.back(), 1);
+        PSR_CUDA(ctx, cudaMalloc(&w.sell_ptr, sizeof(int64_t) * hp.size()));
+        PSR_CUDA(ctx, cudaMemcpy(w.sell_ptr, hp.data(), sizeof(int64_t) * hp.size(), cudaMemcpyHostToDevice));
+        PSR_CUDA(ctx, cudaMalloc(&w.sell_cols, sizeof(int32_t) * (size_t)total));
+        PSR_CUDA(ctx, cudaMalloc(&w.sell_vals, sizeof(double) * (size_t)total));
+        count_launch();
+        k_sell_fill<<<(w.nslices * 32 + 255) / 256, 256>>>(ctx->rowptr, ctx->colidx, ctx->vals, ctx->n, w.nslices,
+                                                            w.sell_ptr, w.sell_cols, w.sell_vals);
+        PSR_CHECK_LAUNCH(ctx, "SELL build");
+        PSR_CUDA(ctx, cudaDeviceSynchronize());
+    }
     w.nspmv = 152 * 16;                     // partial slots available to the SpMV reductions
     PSR_CUDA(ctx, cudaDeviceGetAttribute(&w.sms, cudaDevAttrMultiProcessorCount, ctx->device));
     PSR_CUDA(ctx, cudaMalloc(&w.partial, (size_t)std::max(w.nblk * 34, w.nspmv) * 8));
@@ -876,7 +1001,7 @@ int krylov_alloc(psr_ctx* ctx) {
         cudaGetLastError();
         w.coop = b8 >= 1 && b16 >= 1 && b32 >= 1;
     }
-    PSR_CUDA(ctx, cudaMalloc(&w.part_arn, (size_t)3 * 33 * w.sms * sizeof(double)));
+    PSR_CUDA(ctx, cudaMalloc(&w.part_arn, (size_t)3 * 33 * 2 * w.sms * sizeof(double)));
     PSR_CUDA(ctx, cudaMalloc(&w.bar, 2 * sizeof(unsigned int)));
     PSR_CUDA(ctx, cudaMemset(w.bar, 0, 2 * sizeof(unsigned int)));
     PSR_CUDA(ctx, cudaMemset(w.ictl, 0, 32 * sizeof(int32_t)));
@@ -890,6 +1015,9 @@ void krylov_free(psr_ctx* ctx) {
     cudaFree(w.rflag);
     cudaFree(w.part_arn);
     cudaFree(w.bar);
+    cudaFree(w.sell_ptr);
+    cudaFree(w.sell_cols);
+    cudaFree(w.sell_vals);
     w = KrylovWS{};
     if (ctx->g_cycle) cudaGraphExecDestroy(ctx->g_cycle);
     ctx->g_cycle = nullptr;
@@ -985,14 +1113,17 @@ static int enqueue_cgs2(psr_ctx* ctx, KDims kd, int j, double* Vn, cudaStream_t 
     return PSR_OK;
 }
 
-// The fused Arnoldi step: one cooperative launch of one block per SM.
+// The fused Arnoldi step: one cooperative launch, one or two blocks per SM.
 template <int NV>
 static int enqueue_arnoldi(psr_ctx* ctx, KDims kd, int j, double* Vn, cudaStream_t s) {
     KrylovWS& w = ctx->ws;
     const int n = ctx->n;
     const double vb = 8.0 * n;
+    // one block per SM, two where the registers allow (more loads in flight)
+    static const int occ = blocks_per_sm((const void*)k_arnoldi<NV>);
+    const int bps = std::min(occ, 2);
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)w.sms);
+    cfg.gridDim = dim3((unsigned)(w.sms * bps));
     cfg.blockDim = dim3(KT);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;

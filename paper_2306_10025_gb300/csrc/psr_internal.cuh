@@ -108,9 +108,13 @@ struct KrylovWS {
     double* hist = nullptr;     // [maxit + 1]
     int32_t* ictl = nullptr;    // device control ints
     int32_t* rflag = nullptr;   // [64] FGMRES: second Gram-Schmidt pass taken at step j
-    double* part_arn = nullptr; // partials of the fused Arnoldi step, 3 passes x 33 x sms
+    double* part_arn = nullptr; // partials of the fused Arnoldi step, 3 passes x 33 x 2 sms
     unsigned int* bar = nullptr;  // grid barrier of the fused Arnoldi step (count, generation)
     bool coop = false;          // fused Arnoldi step (cooperative launch) available
+    int64_t* sell_ptr = nullptr;  // SELL-32 copy of A: slice offsets [nslices + 1]
+    int32_t* sell_cols = nullptr;
+    double* sell_vals = nullptr;
+    int nslices = 0;
     int nblk = 0;
     int nspmv = 0;
     int sms = 0;           // streaming multiprocessors of the device
