@@ -248,19 +248,31 @@ __global__ void __launch_bounds__(256) k_spmv_sell(const int64_t* __restrict__ s
         const int64_t o = live ? sptr[s] + lane : 0;
         const int width = live ? (int)((sptr[s + 1] - sptr[s]) >> 5) : 0;
         double sum = 0.0;
-        int k = 0;
-        for (; k + 4 <= width; k += 4) {
-            const int c0 = ldnc_i(scols + o + 32 * (int64_t)k), c1 = ldnc_i(scols + o + 32 * (int64_t)(k + 1));
-            const int c2 = ldnc_i(scols + o + 32 * (int64_t)(k + 2)), c3 = ldnc_i(scols + o + 32 * (int64_t)(k + 3));
-            const double a0 = ldnc(svals + o + 32 * (int64_t)k), a1 = ldnc(svals + o + 32 * (int64_t)(k + 1));
-            const double a2 = ldnc(svals + o + 32 * (int64_t)(k + 2)), a3 = ldnc(svals + o + 32 * (int64_t)(k + 3));
-            const double x0 = ldnc(x + c0), x1 = ldnc(x + c1), x2 = ldnc(x + c2), x3 = ldnc(x + c3);
-            sum = fma(a0, x0, sum);
-            sum = fma(a1, x1, sum);
-            sum = fma(a2, x2, sum);
-            sum = fma(a3, x3, sum);
+        // Software pipeline over groups of four entries: the indices and
+        // values of group g+1 are requested before the x gathers of group g
+        // are consumed, so each group costs about one gather latency.
+        const int ng = width >> 2;
+        int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        if (ng > 0) {
+            c0 = ldnc_i(scols + o); c1 = ldnc_i(scols + o + 32); c2 = ldnc_i(scols + o + 64); c3 = ldnc_i(scols + o + 96);
+            a0 = ldnc(svals + o); a1 = ldnc(svals + o + 32); a2 = ldnc(svals + o + 64); a3 = ldnc(svals + o + 96);
         }
-        for (; k < width; ++k) sum = fma(ldnc(svals + o + 32 * (int64_t)k), ldnc(x + ldnc_i(scols + o + 32 * (int64_t)k)), sum);
+        for (int g = 0; g < ng; ++g) {
+            const double x0 = ldnc(x + c0), x1 = ldnc(x + c1), x2 = ldnc(x + c2), x3 = ldnc(x + c3);
+            const double b0 = a0, b1 = a1, b2 = a2, b3 = a3;
+            if (g + 1 < ng) {                              // warp-uniform (one slice per warp)
+                const int64_t q = o + 128 * (int64_t)(g + 1);
+                c0 = ldnc_i(scols + q); c1 = ldnc_i(scols + q + 32); c2 = ldnc_i(scols + q + 64); c3 = ldnc_i(scols + q + 96);
+                a0 = ldnc(svals + q); a1 = ldnc(svals + q + 32); a2 = ldnc(svals + q + 64); a3 = ldnc(svals + q + 96);
+            }
+            sum = fma(b0, x0, sum);
+            sum = fma(b1, x1, sum);
+            sum = fma(b2, x2, sum);
+            sum = fma(b3, x3, sum);
+        }
+        for (int k = 4 * ng; k < width; ++k)
+            sum = fma(ldnc(svals + o + 32 * (int64_t)k), ldnc(x + ldnc_i(scols + o + 32 * (int64_t)k)), sum);
         if (row < n) {
             if (mode == 1) {
                 const double v = b[row] - sum;
@@ -1113,17 +1125,16 @@ static int enqueue_cgs2(psr_ctx* ctx, KDims kd, int j, double* Vn, cudaStream_t 
     return PSR_OK;
 }
 
-// The fused Arnoldi step: one cooperative launch, one or two blocks per SM.
+// The fused Arnoldi step: one cooperative launch of one block per SM.
 template <int NV>
 static int enqueue_arnoldi(psr_ctx* ctx, KDims kd, int j, double* Vn, cudaStream_t s) {
     KrylovWS& w = ctx->ws;
     const int n = ctx->n;
     const double vb = 8.0 * n;
-    // one block per SM, two where the registers allow (more loads in flight)
-    static const int occ = blocks_per_sm((const void*)k_arnoldi<NV>);
-    const int bps = std::min(occ, 2);
+    // one block per SM: every block sums all block partials after a barrier,
+    // so more blocks lengthen the serial part (measured: two per SM slower)
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(w.sms * bps));
+    cfg.gridDim = dim3((unsigned)w.sms);
     cfg.blockDim = dim3(KT);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
