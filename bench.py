@@ -46,6 +46,10 @@ CONFIGS = {
                       krylov="cg", desc="3D Nedelec curl-curl 64^3, 12-DOF patches"),
     "diffusion3d": dict(builder="diffusion3d_q2", kw=dict(N=32), tol=1e-1, prec="fp32", weighting="sym",
                         krylov="cg", desc="3D Q2 lognormal diffusion 32^3, 27-DOF patches"),
+    "stokes3d": dict(builder="stokes3d_q2q1", kw=dict(N=24), tol=0.0, prec="fp32", weighting="left",
+                     krylov="fgmres",
+                     desc="3D Stokes Q2-Q1 24^3 hexes, vertex jitter 0.2h, Dirichlet-trimmed Vanka patches "
+                          "{89, 62, 44, 32} in one grouped persistent sweep, full storage"),
 }
 
 # kernel(s) behind each timing class of the library's per-kernel timing
@@ -362,7 +366,7 @@ def run_gpu(args, cfg, ws, rank, local):
 
 # ------------------------------------------------------------------ CPU oracle
 SAMPLE_KW = {"stokes2d": dict(N=16, ratio=1.05), "poisson2d": dict(N=16), "nedelec3d": dict(N=8),
-             "diffusion3d": dict(N=6)}
+             "diffusion3d": dict(N=6), "stokes3d": dict(N=4)}
 
 
 def cpu_oracle_sample(args, cfg, name):
@@ -376,10 +380,21 @@ def cpu_oracle_sample(args, cfg, name):
     pr = getattr(problems, cfg["builder"])(**kw)
     tol = cfg["tol"] if args.tol is None else args.tol
     t0 = time.perf_counter()
-    st = O.setup(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d(), tol)
-    t1 = time.perf_counter()
-    x, hist, it, conv = O.solve(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.rhs(0), st, cfg["krylov"],
-                                cfg["weighting"], restart=30, rtol=1e-8, maxit=args.maxit)
+    if pr.uniform_size:
+        st = O.setup(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d(), tol)
+        t1 = time.perf_counter()
+        x, hist, it, conv = O.solve(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.rhs(0), st, cfg["krylov"],
+                                    cfg["weighting"], restart=30, rtol=1e-8, maxit=args.maxit)
+    else:
+        # patches of several sizes, full storage (the criterion path takes one size)
+        Ak = O.extract_patches_ragged(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.patch_offsets, pr.patch_dofs)
+        Binv = [O.lu_inverse(a[None])[0][0] for a in Ak]
+        W = O.weights(O.multiplicity(pr.n, pr.patch_dofs))
+        phi = np.arange(len(Ak))
+        t1 = time.perf_counter()
+        mv = lambda v: O.csr_matvec(pr.rowptr, pr.colidx, pr.vals, v)
+        pc = lambda v: O.apply_ragged(v, pr.patch_offsets, pr.patch_dofs, Binv, phi, W, cfg["weighting"])
+        x, hist, it, conv = O.fgmres(mv, pc, pr.rhs(0), restart=30, rtol=1e-8, maxit=args.maxit)
     t2 = time.perf_counter()
     return {"value": pr.n * it / (t2 - t0), "unit": "DOF/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": (f"numpy FP64 oracle, whole step (setup with Alg. 1 at tol {tol:g}: {t1 - t0:.2f} s; "

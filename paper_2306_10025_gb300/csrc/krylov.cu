@@ -758,9 +758,14 @@ __global__ void __launch_bounds__(KT) k_arnoldi(const double* __restrict__ V, do
         if (threadIdx.x == 0) s_w2 = t;
         __syncthreads();
     }
-    double h2 = 0.0;
-    for (int q = 0; q < nv; ++q) h2 = fma(sh_h[q], sh_h[q], h2);
-    const bool reorth = (s_w2 - h2 < 0.5 * s_w2);
+    __shared__ int s_reorth;
+    if (threadIdx.x == 0) {
+        double h2 = 0.0;
+        for (int q = 0; q < nv; ++q) h2 = fma(sh_h[q], sh_h[q], h2);
+        s_reorth = (s_w2 - h2 < 0.5 * s_w2) ? 1 : 0;
+    }
+    __syncthreads();
+    const bool reorth = s_reorth != 0;
     if (blockIdx.x == 0) {
         if (threadIdx.x < nv) Hm(kd.scal, m)[threadIdx.x * m + j] = sh_h[threadIdx.x];
         if (threadIdx.x == 0) kd.rflag[j] = reorth ? 1 : 0;
