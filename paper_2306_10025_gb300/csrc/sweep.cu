@@ -50,8 +50,79 @@ __device__ __forceinline__ int ldg_nc_i(const int32_t* p) {
     return v;
 }
 
+// Asynchronous global -> shared copies of one element (4 or 8 bytes): the
+// whole staged inverse is requested before the first wait instead of one
+// load latency per loop trip.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* dst, const void* src) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    if (BYTES == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" :: "r"(sa), "l"(src) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// Stage one inverse (pp entries of T) into shared memory as compute type C
+// by the whole block; the caller synchronises the block afterwards.
+template <typename T, typename C>
+__device__ __forceinline__ void stage_inverse(C* sR, const T* __restrict__ src, int pp) {
+    if constexpr (sizeof(T) == sizeof(C) && (sizeof(T) == 4 || sizeof(T) == 8)) {
+        for (int e = threadIdx.x; e < pp; e += blockDim.x) cp_async_elem<sizeof(T)>(sR + e, src + e);
+        cp_async_wait_all();
+    } else {
+        for (int e = threadIdx.x; e < pp; e += blockDim.x) sR[e] = (C)src[e];
+    }
+}
+
+// The patches of one tile (all sharing the staged inverse sR, p <= 128) as
+// work items (patch, chunk of 32 rows) dealt to the block's warps, so that a
+// tile of fewer patches than warps (full storage: one) still keeps several
+// warps busy.  The warp gathers the patch's residual into its slot sr, then
+// lane l forms row 32 q + l and scatter-adds it.
+template <typename C>
+__device__ __forceinline__ void sweep_tile_items(const C* sR, C* sr, int p, const int32_t* __restrict__ sdofs,
+                                                 int start, int cnt, const double* __restrict__ r,
+                                                 const double* __restrict__ wg, const double* __restrict__ wsc,
+                                                 double* __restrict__ z) {
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const int nrc = (p + 31) >> 5;
+    for (int it = wid; it < cnt * nrc; it += wpb) {
+        const int k = start + it / nrc, q = it % nrc;
+        const int32_t* dk = sdofs + (int64_t)k * p;
+        // map and residual loads unconditional (index clamped to p-1), so the
+        // chunks' loads are in flight together
+        int dof[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) dof[u] = ldg_nc_i(dk + min(lane + 32 * u, p - 1));
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = ldg_nc(r + dof[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int a = lane + 32 * u;
+            if (a < p) sr[a] = (C)(wg ? v[u] * wg[dof[u]] : v[u]);
+        }
+        __syncwarp();
+        const int a = lane + 32 * q;
+        if (a < p) {
+            C y = (C)0;
+            const C* row = sR + a * p;
+            for (int b = 0; b < p; ++b) y = fma(row[b], sr[b], y);
+            const int d = (q == 0) ? dof[0] : (q == 1) ? dof[1] : (q == 2) ? dof[2] : dof[3];
+            atomicAdd(&z[d], (double)y * wsc[d]);
+        }
+        __syncwarp();
+    }
+}
+
+
 // ------------------------------------------------------------ kernels
-// Generic: one patch per warp, lane a owns rows a, a+32, ...; p <= 128.
+// Generic, p <= 128: (patch, 32-row chunk) work items over the block's warps,
+// lane l of an item forms row 32 q + l of B^-1 r_k.
 template <typename T>
 __global__ void __launch_bounds__(256) k_sweep_warp(const int32_t* __restrict__ tiles, int ntiles, int p,
                                                     const T* __restrict__ rinv, const int32_t* __restrict__ sdofs,
@@ -62,43 +133,16 @@ __global__ void __launch_bounds__(256) k_sweep_warp(const int32_t* __restrict__ 
     using C = typename Comp<T>::type;
     if (stop && *stop) return;
     C* sR = reinterpret_cast<C*>(smem);
-    const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
-    const int wpb = blockDim.x >> 5;
     const int pp = p * p;
     C* sr = reinterpret_cast<C*>(smem + (((size_t)pp * sizeof(C) + 15) & ~(size_t)15)) + wid * 128;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int c = tiles[3 * t], start = tiles[3 * t + 1], cnt = tiles[3 * t + 2];
         const T* src = rinv + (int64_t)c * pp;
         __syncthreads();
-        for (int e = threadIdx.x; e < pp; e += blockDim.x) sR[e] = (C)src[e];
+        stage_inverse<T, C>(sR, src, pp);
         __syncthreads();
-        for (int k = start + wid; k < start + cnt; k += wpb) {
-            const int32_t* dk = sdofs + (int64_t)k * p;
-            int dof[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int a = lane + 32 * q;
-                dof[q] = (a < p) ? dk[a] : 0;
-                if (a < p) {
-                    double v = r[dof[q]];
-                    if (wg) v *= wg[dof[q]];
-                    sr[a] = (C)v;
-                }
-            }
-            __syncwarp();
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int a = lane + 32 * q;
-                if (a < p) {
-                    C y = (C)0;
-                    const C* row = sR + a * p;
-                    for (int b = 0; b < p; ++b) y = fma(row[b], sr[b], y);
-                    atomicAdd(&z[dof[q]], (double)y * wsc[dof[q]]);
-                }
-            }
-            __syncwarp();
-        }
+        sweep_tile_items<C>(sR, sr, p, sdofs, start, cnt, r, wg, wsc, z);
     }
 }
 
@@ -253,9 +297,7 @@ __global__ void __launch_bounds__(256) k_sweep_grouped(const int32_t* __restrict
     __shared__ int s_tile;
     if (stop && *stop) return;
     C* sR = reinterpret_cast<C*>(smem);
-    const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
-    const int wpb = blockDim.x >> 5;
     C* sr = reinterpret_cast<C*>(smem + (((size_t)pmax * pmax * sizeof(C) + 15) & ~(size_t)15)) + wid * 128;
     for (;;) {
         __syncthreads();
@@ -267,34 +309,9 @@ __global__ void __launch_bounds__(256) k_sweep_grouped(const int32_t* __restrict
         const GroupDesc gd = groups[g];
         const int p = gd.p, pp = p * p;
         const T* src = reinterpret_cast<const T*>(gd.rinv) + (int64_t)c * pp;
-        for (int e = threadIdx.x; e < pp; e += blockDim.x) sR[e] = (C)src[e];
+        stage_inverse<T, C>(sR, src, pp);
         __syncthreads();
-        for (int k = start + wid; k < start + cnt; k += wpb) {
-            const int32_t* dk = gd.sdofs + (int64_t)k * p;
-            int dof[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int a = lane + 32 * q;
-                dof[q] = (a < p) ? dk[a] : 0;
-                if (a < p) {
-                    double v = r[dof[q]];
-                    if (wg) v *= wg[dof[q]];
-                    sr[a] = (C)v;
-                }
-            }
-            __syncwarp();
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int a = lane + 32 * q;
-                if (a < p) {
-                    C y = (C)0;
-                    const C* row = sR + a * p;
-                    for (int b = 0; b < p; ++b) y = fma(row[b], sr[b], y);
-                    atomicAdd(&z[dof[q]], (double)y * wsc[dof[q]]);
-                }
-            }
-            __syncwarp();
-        }
+        sweep_tile_items<C>(sR, sr, p, gd.sdofs, start, cnt, r, wg, wsc, z);
     }
     // the last CTA to leave resets the counter for the next launch
     __syncthreads();
