@@ -457,6 +457,7 @@ struct SketchDB {
     const double* Y;               // [count][SK][p] y_i = fl(A_i x_k)
     const double* fa;              // [count] ||A_i||_F
     const double* rho;             // [count] bound of ||B_i^ A_i - I||_2
+    const float* Y32;              // [count][SK][p] y_i rounded to FP32 (the screen's operand)
 };
 
 
@@ -484,8 +485,8 @@ __global__ void k_sketch_dirs(const double* __restrict__ Ag, int count, int p, d
 // residual bound rho >= ||B^ A - I||_2 with B^ = Binv.
 __global__ void __launch_bounds__(256) k_sketch(const double* __restrict__ A, const double* __restrict__ Binv,
                                                 int count, int p, const double* __restrict__ X,
-                                                double* __restrict__ Y, double* __restrict__ fa,
-                                                double* __restrict__ rho) {
+                                                double* __restrict__ Y, float* __restrict__ Y32,
+                                                double* __restrict__ fa, double* __restrict__ rho) {
     const int lane = threadIdx.x & 31;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= count) return;                            // warp-uniform
@@ -509,7 +510,10 @@ __global__ void __launch_bounds__(256) k_sketch(const double* __restrict__ A, co
         double y = 0.0;
 #pragma unroll
         for (int j = 0; j < 32; ++j) y = fma(a[j], X[k * 32 + j], y);
-        if (act) Y[((int64_t)i * SK + k) * p + lane] = y;
+        if (act) {
+            Y[((int64_t)i * SK + k) * p + lane] = y;
+            Y32[((int64_t)i * SK + k) * p + lane] = (float)y;
+        }
     }
     // column j of B^ A: lane r sums b[r][k] A[k][j], A[k][j] from lane k
     double res2 = 0.0;
@@ -534,33 +538,53 @@ __global__ void __launch_bounds__(256) k_sketch(const double* __restrict__ A, co
     }
 }
 
-// Entry side of the screen, staged in shared memory: y_c (SK p) and the
-// denominators den_k >= ||A_c x_k||.
-__device__ __forceinline__ void stage_sketch(const double* __restrict__ Yc, double fc, int p, double* sy,
-                                             double* sden) {
-    for (int t = threadIdx.x; t < SK * p; t += blockDim.x) sy[t] = Yc[t];
-    __syncthreads();
+// Entry side of the screen, staged in shared memory: y_c in FP32 (SK x 32,
+// zero beyond p) and the denominators den_k >= ||A_c x_k|| (from the FP64
+// sketch).
+__device__ __forceinline__ void stage_sketch(const double* __restrict__ Yc, const float* __restrict__ Yc32, double fc,
+                                             int p, float* sy32, double* sden) {
+    for (int t = threadIdx.x; t < SK * 32; t += blockDim.x) {
+        const int k = t >> 5, r = t & 31;
+        sy32[t] = (r < p) ? Yc32[k * p + r] : 0.f;
+    }
     if (threadIdx.x < SK) {
         double n2 = 0.0;
-        for (int r = 0; r < p; ++r) n2 = fma(sy[threadIdx.x * p + r], sy[threadIdx.x * p + r], n2);
+        for (int r = 0; r < p; ++r) n2 = fma(Yc[threadIdx.x * p + r], Yc[threadIdx.x * p + r], n2);
         sden[threadIdx.x] = sqrt(n2) * (1.0 + (double)(p + 2) * U64) + 1.01 * gamma_u(p) * fc;
     }
 }
 
+__device__ __forceinline__ float ldg_nc_f(const float* q) {
+    float v;
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(q));
+    return v;
+}
+
 // Thread-level decision for candidate i against the staged entry: true when
-// the certified lower bound reaches tol (reject).
-__device__ __forceinline__ bool sketch_rejects(const double* __restrict__ yi, double fi, const double* sy,
+// the certified lower bound reaches tol (reject).  The distance of the
+// sketches is formed in FP32 from the FP32 copies: their rounding
+// (||y - fl32(y)|| <= 2^-24 ||y||, ||y|| <= 1.01 ||A||_F) and that of the FP32
+// norm ((p + 8) 2^-24 relative) are taken off the bound.  All SK x PM loads
+// are issued before the first use (PM >= p, indices clamped to p - 1).
+template <int PM>
+__device__ __forceinline__ bool sketch_rejects(const float* __restrict__ yi, double fi, const float* sy32,
                                                const double* sden, double fc, double rhoc, int p, double tol) {
-    const double slack = 1.01 * (fc + fi) * (gamma_u(p) + rhoc);
+    float v[SK * PM];
+#pragma unroll
+    for (int k = 0; k < SK; ++k)
+#pragma unroll
+        for (int r = 0; r < PM; ++r) v[k * PM + r] = ldg_nc_f(yi + k * p + min(r, p - 1));
+    const double slack = 1.01 * (fc + fi) * (gamma_u(p) + rhoc) + 1.01 * 0x1p-24 * (fc + fi);
     double lb = 0.0;
 #pragma unroll
     for (int k = 0; k < SK; ++k) {
-        double d2 = 0.0;
-        for (int r = 0; r < p; ++r) {
-            const double d = sy[k * p + r] - yi[k * p + r];
-            d2 = fma(d, d, d2);
+        float d2 = 0.f;
+#pragma unroll
+        for (int r = 0; r < PM; ++r) {
+            const float d = (r < p) ? sy32[k * 32 + r] - v[k * PM + r] : 0.f;
+            d2 = fmaf(d, d, d2);
         }
-        const double num = sqrt(d2) * (1.0 - (double)(p + 8) * U64) - slack * (1.0 + 8.0 * U64);
+        const double num = sqrt((double)d2) * (1.0 - (double)(p + 8) * 0x1p-24) - slack * (1.0 + 8.0 * U64);
         if (sden[k] > 0.0) lb = fmax(lb, num / sden[k]);
     }
     return lb * (1.0 - 8.0 * U64) >= tol;
@@ -592,16 +616,17 @@ __device__ __forceinline__ bool round_last_block(int* ticket) {
 //     queue would leave most SMs idle); rejected survivors bid as well.  The
 //     last block records the entry and the smallest rejected index, which is
 //     exactly the smallest unassigned patch after the round.
+template <int PM>
 __global__ void __launch_bounds__(EVAL_THREADS) k_round_screen(RoundDev* st, const int32_t* __restrict__ phi,
                                                                int count, int p, SketchDB sk, double tol,
                                                                int32_t* __restrict__ surv_list) {
-    __shared__ double sy[SK * 32];
+    __shared__ float sy[SK * 32];
     __shared__ double sden[SK];
     if (st->done) return;
     const int lane = threadIdx.x & 31;
     const int i0 = st->next;
     const double fc = sk.fa[i0], rhoc = sk.rho[i0];
-    stage_sketch(sk.Y + (int64_t)i0 * SK * p, fc, p, sy, sden);
+    stage_sketch(sk.Y + (int64_t)i0 * SK * p, sk.Y32 + (int64_t)i0 * SK * p, fc, p, sy, sden);
     __syncthreads();
     unsigned long long my_evals = 0, my_screened = 0;
     int my_min = count;
@@ -609,7 +634,7 @@ __global__ void __launch_bounds__(EVAL_THREADS) k_round_screen(RoundDev* st, con
         const int cand = base + threadIdx.x;
         const bool open = cand < count && phi[cand] == -1;
         bool rej = false;
-        if (open) rej = sketch_rejects(sk.Y + (int64_t)cand * SK * p, sk.fa[cand], sy, sden, fc, rhoc, p, tol);
+        if (open) rej = sketch_rejects<PM>(sk.Y32 + (int64_t)cand * SK * p, sk.fa[cand], sy, sden, fc, rhoc, p, tol);
         if (open && rej) my_min = min(my_min, cand);
         const unsigned opened = __ballot_sync(0xffffffffu, open);
         const unsigned surv = __ballot_sync(0xffffffffu, open && !rej);
@@ -723,8 +748,8 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_seed_pass(RoundDev* st, int
     double* sAc = reinterpret_cast<double*>(smem);
     double* sB = sAc + p * ld;
     double* sw = sB + p * ld;
-    double* sy = sw + PROBE_STRIDE;
-    double* sden = sy + SK * 32;
+    float* sy = reinterpret_cast<float*>(sw + PROBE_STRIDE);
+    double* sden = sw + PROBE_STRIDE + SK * 32;
     float* sB32 = reinterpret_cast<float*>(sden + 8);
     double* wbase = reinterpret_cast<double*>(smem) + eval_block_doubles(p) + (size_t)wid * (p * ld + 64);
     WarpScratch ws{wbase, wbase + p * ld, wbase + p * ld + 32};
@@ -733,7 +758,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_seed_pass(RoundDev* st, int
         sB32[(t / p) * ld + (t % p)] = (float)db.Binv[(int64_t)e * p * p + t];
     const double bfro = db.fro[e];
     const double fc = skd.fa[e], rhoc = skd.rho[e];
-    stage_sketch(skd.Y + (int64_t)e * SK * p, fc, p, sy, sden);
+    stage_sketch(skd.Y + (int64_t)e * SK * p, skd.Y32 + (int64_t)e * SK * p, fc, p, sy, sden);
     __syncthreads();
     unsigned long long my_evals = 0, my_exact = 0, my_screened = 0;
     __shared__ int s_list[EVAL_THREADS];
@@ -744,7 +769,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_seed_pass(RoundDev* st, int
         const int cand = base + threadIdx.x;
         const bool open = cand < count && phi[cand] == -1;
         bool rej = false;
-        if (open) rej = sketch_rejects(sk.Y + (int64_t)cand * SK * p, sk.fa[cand], sy, sden, fc, rhoc, p, tol);
+        if (open) rej = sketch_rejects<32>(sk.Y32 + (int64_t)cand * SK * p, sk.fa[cand], sy, sden, fc, rhoc, p, tol);
         const unsigned opened = __ballot_sync(0xffffffffu, open);
         const unsigned surv = __ballot_sync(0xffffffffu, open && !rej);
         my_evals += __popc(opened);
@@ -900,7 +925,9 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         count_launch();
         k_entry_fro<<<(count + 7) / 8, 256, 0, s>>>(Ag, Ball, count, p, fro_all, w_all, sing_all, nullptr);
         double *skX = nullptr, *skY = nullptr, *skF = nullptr, *skR = nullptr;
+        float *skY32 = nullptr, *sdY32 = nullptr;
         PSR_CUDA(ctx, cudaMalloc(&skX, sizeof(double) * SK * 32));
+        PSR_CUDA(ctx, cudaMalloc(&skY32, sizeof(float) * (size_t)count * SK * p));
         PSR_CUDA(ctx, cudaMalloc(&skF, sizeof(double) * (size_t)count));
         PSR_CUDA(ctx, cudaMalloc(&skR, sizeof(double) * (size_t)count));
         if (cudaMalloc(&skY, sizeof(double) * (size_t)count * SK * p) != cudaSuccess) {
@@ -911,10 +938,10 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         count_launch();
         k_sketch_dirs<<<1, 32 * SK, 0, s>>>(Ag, count, p, skX);
         count_launch();
-        k_sketch<<<(count + 7) / 8, 256, 0, s>>>(Ag, Ball, count, p, skX, skY, skF, skR);
+        k_sketch<<<(count + 7) / 8, 256, 0, s>>>(Ag, Ball, count, p, skX, skY, skY32, skF, skR);
         PSR_CHECK_LAUNCH(ctx, "patch sketches");
-        const SketchDB sk{skX, skY, skF, skR};
-        SketchDB skd{skX, nullptr, nullptr, nullptr};
+        const SketchDB sk{skX, skY, skF, skR, skY32};
+        SketchDB skd{skX, nullptr, nullptr, nullptr, nullptr};
         double *sdY = nullptr, *sdF = nullptr, *sdR = nullptr;
         RoundDev init{};
         init.first_singular = -1;
@@ -952,9 +979,10 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
             PSR_CUDA(ctx, cudaMalloc(&sdY, sizeof(double) * (size_t)m0 * SK * p));
             PSR_CUDA(ctx, cudaMalloc(&sdF, sizeof(double) * (size_t)m0));
             PSR_CUDA(ctx, cudaMalloc(&sdR, sizeof(double) * (size_t)m0));
+            PSR_CUDA(ctx, cudaMalloc(&sdY32, sizeof(float) * (size_t)m0 * SK * p));
             count_launch();
-            k_sketch<<<(m0 + 7) / 8, 256, 0, s>>>(db.A, db.Binv, m0, p, skX, sdY, sdF, sdR);
-            skd = SketchDB{skX, sdY, sdF, sdR};
+            k_sketch<<<(m0 + 7) / 8, 256, 0, s>>>(db.A, db.Binv, m0, p, skX, sdY, sdY32, sdF, sdR);
+            skd = SketchDB{skX, sdY, sdF, sdR, sdY32};
             std::vector<int32_t> seq(m0, -1);
             PSR_CUDA(ctx, cudaMemcpyAsync(rep_l, seq.data(), sizeof(int32_t) * m0, cudaMemcpyHostToDevice, s));
             int32_t h_bad = 0;
@@ -996,7 +1024,12 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         for (;;) {
             for (int r = 0; r < batch; ++r) {
                 count_launch();
-                k_round_screen<<<eval_blocks, EVAL_THREADS, 0, s>>>(st, phi_l, count, p, sk, tol, surv_list);
+                if (p <= 8)
+                    k_round_screen<8><<<eval_blocks, EVAL_THREADS, 0, s>>>(st, phi_l, count, p, sk, tol, surv_list);
+                else if (p <= 16)
+                    k_round_screen<16><<<eval_blocks, EVAL_THREADS, 0, s>>>(st, phi_l, count, p, sk, tol, surv_list);
+                else
+                    k_round_screen<32><<<eval_blocks, EVAL_THREADS, 0, s>>>(st, phi_l, count, p, sk, tol, surv_list);
                 count_launch();
                 k_round_decide<<<decide_blocks, EVAL_THREADS, smem_dec, s>>>(st, phi_l, count, Ag, p, Ball, fro_all,
                                                                             w_all, sing_all, tol, surv_list, rep_l);
@@ -1035,6 +1068,8 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         cudaFree(w_all);
         cudaFree(sing_all);
         for (double* q : {skX, skY, skF, skR, sdY, sdF, sdR}) cudaFree(q);
+        cudaFree(skY32);
+        cudaFree(sdY32);
         cudaFree(surv_list);
         cudaFree(db.A);
         cudaFree(db.Binv);
