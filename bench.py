@@ -52,6 +52,11 @@ CONFIGS = {
                           "{89, 62, 44, 32} in one grouped persistent sweep, full storage"),
 }
 
+# FP64 peak of one GB300 from its unit counts and clock: 152 SMs x 2 FP64
+# fused multiply-adds per clock x 2 flops x 2.07 GHz (no measured FP64 peak
+# is on record; a probe kernel of independent FMA chains reached 84 % of it)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
 # kernel(s) behind each timing class of the library's per-kernel timing
 KT_KERNEL_NAMES = {"sweep": "patch sweep (k_sweep_*)", "spmv": "k_spmv (CSR SpMV, FP64)",
                    "mdot": "k_arnoldi (fused FGMRES Arnoldi step) / k_mdot", "maxpy": "k_maxpy (FGMRES w -= V h)",
@@ -276,22 +281,33 @@ def run_gpu(args, cfg, ws, rank, local):
     kt = last.kernel_timing()
     last.set_kernel_timing(False)
     kernels = {}
-    for name, (ms, cnt, by) in kt.items():
+    for name, (ms, cnt, by, fl) in kt.items():
         if cnt:
             kernels[name] = {"launches": cnt, "ms": ms, "us_per_launch": 1e3 * ms / cnt,
                              "alg_bytes_per_launch": by / cnt, "achieved_gbs": by / (ms * 1e-3) / 1e9,
-                             "frac": by / (ms * 1e-3) / 1e9 / hbm}
+                             "frac": by / (ms * 1e-3) / 1e9 / hbm,
+                             "fp64_flops_per_launch": fl / cnt, "achieved_fp64_tflops": fl / (ms * 1e-3) / 1e12,
+                             "frac_fp64": fl / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
     tot_ms = sum(v["ms"] for v in kernels.values())
     for v in kernels.values():
         v["share"] = v["ms"] / tot_ms
     top = max(kernels, key=lambda k: kernels[k]["ms"])
     kd = kernels[top]
-    roofline = {"kernel": KT_KERNEL_NAMES[top], "bound": "hbm", "achieved": kd["achieved_gbs"],
-                "peak": hbm, "unit": "GB/s", "frac": kd["frac"], "traffic": TRAFFIC.get((args.config, top)),
-                "alg_bytes_per_launch": kd["alg_bytes_per_launch"], "launch_us": kd["us_per_launch"],
-                "share_of_iteration_kernels": kd["share"], "peak_source": peak_source,
-                "timing": "CUDA events on the solve stream around each launch, one extra solve after the timed steps",
-                "kernels": kernels, "sweep_alone": sweep_alone}
+    # the binding resource of the dominant class: HBM bytes or FP64 flops,
+    # whichever it uses the larger fraction of
+    if kd["frac_fp64"] > kd["frac"]:
+        bound = {"bound": "alu", "achieved": kd["achieved_fp64_tflops"], "peak": FP64_PEAK_TFLOPS,
+                 "unit": "TFLOP/s (FP64)", "frac": kd["frac_fp64"],
+                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clock x 2 flops x 2070 MHz"}
+    else:
+        bound = {"bound": "hbm", "achieved": kd["achieved_gbs"], "peak": hbm, "unit": "GB/s", "frac": kd["frac"],
+                 "peak_source": peak_source}
+    roofline = dict(kernel=KT_KERNEL_NAMES[top], **bound, traffic=TRAFFIC.get((args.config, top)),
+                    alg_bytes_per_launch=kd["alg_bytes_per_launch"], hbm_frac=kd["frac"],
+                    fp64_flops_per_launch=kd["fp64_flops_per_launch"], fp64_frac=kd["frac_fp64"],
+                    launch_us=kd["us_per_launch"], share_of_iteration_kernels=kd["share"],
+                    timing="CUDA events on the solve stream around each launch, one extra solve after the timed steps",
+                    kernels=kernels, sweep_alone=sweep_alone)
     last.destroy()
 
     # full-storage FP64 comparison (outside the timed steps)

@@ -219,9 +219,15 @@ int psr_set_kernel_timing(psr_ctx* ctx, int enable);
  * the second Gram-Schmidt pass; the fused step the sum of these plus 16 n for
  * the normalisation; sweep: 24 n + 4 sum(p_k) + 4 n_patches +
  * stored factor bytes; FGMRES scale 16 n; CG kernels their vector reads and
- * writes).  Any pointer may be NULL.  Host-only; PSR_ERR_INVALID_ARG for a
- * NULL ctx or count outside 1 .. PSR_KT_COUNT. */
-int psr_get_kernel_timing(psr_ctx* ctx, double* ms, int64_t* launches, double* bytes, int count);
+ * writes), flops = summed algorithmic FP64 flops (SpMV 2 nnz, plus 2 n for
+ * the CG dot; fused step 4 n (j+2) + n, plus 4 n (j+1) with the second pass;
+ * first projection 2 n (j+2), updates 2 n (j+2) each; sweep 2 sum(p_k) for
+ * the weighted scatter, plus 2 sum(p_k^2) with FP64 inverses; vector
+ * kernels 2 flops per element and operation).  Any pointer may be NULL.
+ * Host-only; PSR_ERR_INVALID_ARG for a NULL ctx or count outside
+ * 1 .. PSR_KT_COUNT. */
+int psr_get_kernel_timing(psr_ctx* ctx, double* ms, int64_t* launches, double* bytes, double* flops,
+                          int count);
 
 /* ---- single steps of the path (stateless; for testing and reuse) ------- */
 

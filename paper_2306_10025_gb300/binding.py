@@ -108,7 +108,7 @@ def load(path: str = LIB_PATH):
     lib.psr_criterion_noalloc.argtypes = [vp, i32, i32, vp, vp, d, vp, vp, vp]
     lib.psr_kernel_launches.argtypes = []
     lib.psr_set_kernel_timing.argtypes = [vp, i32]
-    lib.psr_get_kernel_timing.argtypes = [vp, vp, vp, vp, i32]
+    lib.psr_get_kernel_timing.argtypes = [vp, vp, vp, vp, vp, i32]
     lib.psr_setup_seeded.argtypes = [C.POINTER(psr_csr), C.POINTER(psr_patches), C.POINTER(psr_opts), vp, i32, vp,
                                      vp, C.POINTER(vp)]
     lib.psr_features.argtypes = [vp, i32, i32, vp, vp, vp]
@@ -257,12 +257,12 @@ class Context:
         _check(load().psr_set_kernel_timing(self.h, int(bool(enable))), self.h)
 
     def kernel_timing(self) -> dict:
-        """Per-class totals of psr_get_kernel_timing: {class: (ms, launches, bytes)}."""
+        """Per-class totals of psr_get_kernel_timing: {class: (ms, launches, bytes, fp64 flops)}."""
         k = len(KT_CLASSES)
-        ms, nl, by = (C.c_double * k)(), (C.c_int64 * k)(), (C.c_double * k)()
+        ms, nl, by, fl = (C.c_double * k)(), (C.c_int64 * k)(), (C.c_double * k)(), (C.c_double * k)()
         _check(load().psr_get_kernel_timing(self.h, C.cast(ms, C.c_void_p), C.cast(nl, C.c_void_p),
-                                             C.cast(by, C.c_void_p), k), self.h)
-        return {name: (ms[i], int(nl[i]), by[i]) for i, name in enumerate(KT_CLASSES)}
+                                             C.cast(by, C.c_void_p), C.cast(fl, C.c_void_p), k), self.h)
+        return {name: (ms[i], int(nl[i]), by[i], fl[i]) for i, name in enumerate(KT_CLASSES)}
 
     def destroy(self):
         if self.h:

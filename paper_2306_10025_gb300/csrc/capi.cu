@@ -414,7 +414,7 @@ int psr_set_kernel_timing(psr_ctx* ctx, int enable) {
     return kernel_timing_enable(ctx, enable != 0);
 }
 
-int psr_get_kernel_timing(psr_ctx* ctx, double* ms, int64_t* launches, double* bytes, int count) {
+int psr_get_kernel_timing(psr_ctx* ctx, double* ms, int64_t* launches, double* bytes, double* flops, int count) {
     if (!ctx || count < 1 || count > PSR_KT_COUNT) {
         set_error(ctx, "ctx is NULL or count outside 1 .. PSR_KT_COUNT");
         return PSR_ERR_INVALID_ARG;
@@ -423,6 +423,7 @@ int psr_get_kernel_timing(psr_ctx* ctx, double* ms, int64_t* launches, double* b
         if (ms) ms[k] = ctx->kt_ms[k];
         if (launches) launches[k] = ctx->kt_n[k];
         if (bytes) bytes[k] = ctx->kt_bytes[k];
+        if (flops) flops[k] = ctx->kt_flops[k];
     }
     return PSR_OK;
 }

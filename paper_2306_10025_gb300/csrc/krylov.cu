@@ -896,6 +896,16 @@ static double sweep_bytes(const psr_ctx* ctx) {
 static double spmv_bytes(const psr_ctx* ctx) {
     return 12.0 * (double)ctx->nnz + 4.0 * (ctx->n + 1.0) + 16.0 * ctx->n;
 }
+// FP64 flops of the sweep: the patch products when the inverses are FP64,
+// the weighted scatter-add of every patch DOF
+static double sweep_flops(const psr_ctx* ctx) {
+    double sp = 0.0, sp2 = 0.0;
+    for (const Group& G : ctx->groups) {
+        sp += (double)G.count * G.p;
+        sp2 += (double)G.count * G.p * G.p;
+    }
+    return (ctx->opts.store_prec == PSR_PREC_FP64 ? 2.0 * sp2 : 0.0) + 2.0 * sp;
+}
 
 // While the stream is captured the record becomes an event-record node of
 // the graph (external flag); otherwise it is a plain record.
@@ -907,7 +917,7 @@ static cudaError_t kt_record(cudaEvent_t e, cudaStream_t s) {
                                                : cudaEventRecord(e, s);
 }
 
-static int kt_begin(psr_ctx* ctx, int kind, int j, double bytes, cudaStream_t s) {
+static int kt_begin(psr_ctx* ctx, int kind, int j, double bytes, double flops, cudaStream_t s) {
     if (!ctx->kt_on) return PSR_OK;
     const size_t i = ctx->kt_marks.size();
     while (ctx->kt_ev.size() < 2 * i + 2) {
@@ -915,7 +925,7 @@ static int kt_begin(psr_ctx* ctx, int kind, int j, double bytes, cudaStream_t s)
         PSR_CUDA(ctx, cudaEventCreate(&e));
         ctx->kt_ev.push_back(e);
     }
-    ctx->kt_marks.push_back(KtMark{kind, j, bytes, 0.0});
+    ctx->kt_marks.push_back(KtMark{kind, j, bytes, 0.0, flops, 0.0});
     PSR_CUDA(ctx, kt_record(ctx->kt_ev[2 * i], s));
     return PSR_OK;
 }
@@ -939,15 +949,25 @@ static int kt_collect(psr_ctx* ctx, int done, const int32_t* rflag) {
         PSR_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->kt_ev[2 * i], ctx->kt_ev[2 * i + 1]));
         ctx->kt_ms[mk.kind] += ms;
         ctx->kt_n[mk.kind] += 1;
-        ctx->kt_bytes[mk.kind] += mk.bytes + ((rflag && rflag[mk.j]) ? mk.bytes_reorth : 0.0);
+        const bool ro = rflag && rflag[mk.j];
+        ctx->kt_bytes[mk.kind] += mk.bytes + (ro ? mk.bytes_reorth : 0.0);
+        ctx->kt_flops[mk.kind] += mk.flops + (ro ? mk.flops_reorth : 0.0);
     }
     return PSR_OK;
 }
 
-#define KT_BEGIN(kind, j, bytes)                                   \
+#define KT_BEGIN(kind, j, bytes, flops)                            \
     do {                                                           \
-        int rk_ = kt_begin(ctx, (kind), (j), (bytes), s);          \
+        int rk_ = kt_begin(ctx, (kind), (j), (bytes), (flops), s); \
         if (rk_ != PSR_OK) return rk_;                             \
+    } while (0)
+// extra bytes / FP64 flops of the mark just opened when its step reorthogonalises
+#define KT_REORTH(bytes, flops)                                    \
+    do {                                                           \
+        if (ctx->kt_on && !ctx->kt_marks.empty()) {                \
+            ctx->kt_marks.back().bytes_reorth = (bytes);           \
+            ctx->kt_marks.back().flops_reorth = (flops);           \
+        }                                                          \
     } while (0)
 #define KT_END()                                                   \
     do {                                                           \
@@ -1053,6 +1073,7 @@ int kernel_timing_enable(psr_ctx* ctx, bool on) {
             ctx->kt_ms[k] = 0.0;
             ctx->kt_n[k] = 0;
             ctx->kt_bytes[k] = 0.0;
+            ctx->kt_flops[k] = 0.0;
         }
     }
     return PSR_OK;
@@ -1064,20 +1085,20 @@ static int enqueue_cg_block(psr_ctx* ctx, KDims kd, int iters, cudaStream_t s) {
     const int n = ctx->n, nb = w.nblk;
     const double vb = 8.0 * n;
     for (int t = 0; t < iters; ++t) {
-        KT_BEGIN(PSR_KT_SPMV, t, spmv_bytes(ctx));
+        KT_BEGIN(PSR_KT_SPMV, t, spmv_bytes(ctx), 2.0 * ctx->nnz + 2.0 * n);
         launch_spmv(ctx, w.p, w.q, nullptr, 2, 1, kd, 1, w.nspmv, s);
         KT_END();
-        KT_BEGIN(PSR_KT_VEC, t, 6 * vb);
+        KT_BEGIN(PSR_KT_VEC, t, 6 * vb, 6.0 * n);
         count_launch(); k_cg_xr<<<nb, 256, 0, s>>>(w.x, w.r, w.p, w.q, n, kd);
         KT_END();
-        KT_BEGIN(PSR_KT_SWEEP, t, sweep_bytes(ctx));
+        KT_BEGIN(PSR_KT_SWEEP, t, sweep_bytes(ctx), sweep_flops(ctx));
         int rc = sweep_apply_ex(ctx, w.r, w.z, kd.ictl + I_STOP, s);
         if (rc != PSR_OK) return rc;
         KT_END();
-        KT_BEGIN(PSR_KT_VEC, t, 2 * vb);
+        KT_BEGIN(PSR_KT_VEC, t, 2 * vb, 2.0 * n);
         count_launch(); k_dot<<<nb, 256, 0, s>>>(w.r, w.z, n, kd, 2);
         KT_END();
-        KT_BEGIN(PSR_KT_VEC, t, 3 * vb);
+        KT_BEGIN(PSR_KT_VEC, t, 3 * vb, 2.0 * n);
         count_launch(); k_cg_p<<<nb, 256, 0, s>>>(w.p, w.z, n, kd);
         KT_END();
     }
@@ -1117,14 +1138,15 @@ static int enqueue_cgs2(psr_ctx* ctx, KDims kd, int j, double* Vn, cudaStream_t 
     static const int o2 = blocks_per_sm((const void*)k_maxpy_mdot<NV>);
     static const int o3 = blocks_per_sm((const void*)k_maxpy<NV>);
     const int g1 = cgs_grid(ctx, o1), g2 = cgs_grid(ctx, o2), g3 = cgs_grid(ctx, o3);
-    KT_BEGIN(PSR_KT_MDOT, j, (j + 2) * vb);
+    KT_BEGIN(PSR_KT_MDOT, j, (j + 2) * vb, 2.0 * n * (j + 2));
     count_launch(); k_mdot<NV><<<g1, KT, 0, s>>>(w.V, Vn, n, j, kd);
     KT_END();
-    KT_BEGIN(PSR_KT_MAXPY, j, (j + 3) * vb);
+    KT_BEGIN(PSR_KT_MAXPY, j, (j + 3) * vb, 2.0 * n * (j + 2));
+    KT_REORTH(0.0, 2.0 * n * j);
     count_launch(); k_maxpy_mdot<NV><<<g2, KT, 0, s>>>(w.V, Vn, n, j, kd);
     KT_END();
-    KT_BEGIN(PSR_KT_MAXPY, j, 0.0);
-    if (ctx->kt_on && !ctx->kt_marks.empty()) ctx->kt_marks.back().bytes_reorth = (j + 3) * vb;
+    KT_BEGIN(PSR_KT_MAXPY, j, 0.0, 0.0);
+    KT_REORTH((j + 3) * vb, 2.0 * n * (j + 2));
     count_launch(); k_maxpy<NV><<<g3, KT, 0, s>>>(w.V, Vn, n, j, kd);
     KT_END();
     return PSR_OK;
@@ -1148,8 +1170,8 @@ static int enqueue_arnoldi(psr_ctx* ctx, KDims kd, int j, double* Vn, cudaStream
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    KT_BEGIN(PSR_KT_MDOT, j, ((j + 2) + (j + 3) + 2) * vb);
-    if (ctx->kt_on && !ctx->kt_marks.empty()) ctx->kt_marks.back().bytes_reorth = (j + 3) * vb;
+    KT_BEGIN(PSR_KT_MDOT, j, ((j + 2) + (j + 3) + 2) * vb, 4.0 * n * (j + 2) + n);
+    KT_REORTH((j + 3) * vb, 4.0 * n * (j + 1));
     count_launch();
     PSR_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_arnoldi<NV>, (const double*)w.V, Vn, n, j, kd, w.part_arn, w.bar));
     KT_END();
@@ -1165,11 +1187,11 @@ static int enqueue_fg_cycle(psr_ctx* ctx, KDims kd, cudaStream_t s) {
         double* Vn = w.V + (size_t)(j + 1) * n;
         double* Zj = w.Z + (size_t)j * n;
         const double vb = 8.0 * n;
-        KT_BEGIN(PSR_KT_SWEEP, j, sweep_bytes(ctx));
+        KT_BEGIN(PSR_KT_SWEEP, j, sweep_bytes(ctx), sweep_flops(ctx));
         int rc = sweep_apply_ex(ctx, Vj, Zj, kd.ictl + I_STOP, s);
         if (rc != PSR_OK) return rc;
         KT_END();
-        KT_BEGIN(PSR_KT_SPMV, j, spmv_bytes(ctx));
+        KT_BEGIN(PSR_KT_SPMV, j, spmv_bytes(ctx), 2.0 * ctx->nnz);
         launch_spmv(ctx, Zj, Vn, nullptr, 0, 0, kd, 1, w.nspmv, s);
         KT_END();
         int rc2 = PSR_OK;
@@ -1184,7 +1206,7 @@ static int enqueue_fg_cycle(psr_ctx* ctx, KDims kd, cudaStream_t s) {
         else if (j < 16) rc2 = enqueue_cgs2<16>(ctx, kd, j, Vn, s);
         else rc2 = enqueue_cgs2<32>(ctx, kd, j, Vn, s);
         if (rc2 != PSR_OK) return rc2;
-        KT_BEGIN(PSR_KT_VEC, j, 2 * vb);
+        KT_BEGIN(PSR_KT_VEC, j, 2 * vb, (double)n);
         count_launch(); k_fg_scale<<<nb, 256, 0, s>>>(Vn, n, kd);
         KT_END();
     }

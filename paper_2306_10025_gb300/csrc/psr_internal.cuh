@@ -128,6 +128,8 @@ struct KtMark {
     int j;
     double bytes;
     double bytes_reorth;   // added when step j took the second Gram-Schmidt pass
+    double flops;          // algorithmic FP64 flops
+    double flops_reorth;
 };
 
 }  // namespace psr
@@ -177,6 +179,7 @@ struct psr_ctx {
     double kt_ms[PSR_KT_COUNT] = {};
     int64_t kt_n[PSR_KT_COUNT] = {};
     double kt_bytes[PSR_KT_COUNT] = {};
+    double kt_flops[PSR_KT_COUNT] = {};
 };
 
 namespace psr {

@@ -67,8 +67,15 @@ def test_fgmres_timing_counts_and_bytes(lib, graph):
         assert second * (1 - 1e-12) <= kt["maxpy"][2] <= 2 * second * (1 + 1e-12)
         classes = ("sweep", "spmv", "mdot", "maxpy", "vec")
     for name in classes:
-        ms, cnt, by = kt[name]
-        assert ms > 0.0 and by > 0.0, name
+        ms, cnt, by, fl = kt[name]
+        assert ms > 0.0 and by > 0.0 and fl > 0.0, name
+    # FP64 flops: SpMV 2 nnz per launch; the Gram-Schmidt step between its
+    # single-pass and its two-pass count
+    assert kt["spmv"][3] == pytest.approx(its * 2.0 * pr.nnz, rel=1e-12)
+    if kt["maxpy"][1] == 0:
+        lo = sum(4.0 * n * (j + 2) + n for j in js)
+        hi = lo + sum(4.0 * n * (j + 1) for j in js)
+        assert lo * (1 - 1e-12) <= kt["mdot"][3] <= hi * (1 + 1e-12)
     assert kt["spmv"][2] == pytest.approx(its * (12.0 * pr.nnz + 4.0 * (n + 1) + 16.0 * n), rel=1e-12)
     # disabling resets nothing but stops the marks; re-enabling resets
     ctx.set_kernel_timing(False)
@@ -101,7 +108,7 @@ def test_kernel_timing_rejects_bad_args(lib):
     pr = P.poisson2d_q2(4)
     ctx = setup_ctx(lib, pr, tol=0.0, weighting="sym", krylov="cg")
     L = lib.load()
-    assert L.psr_get_kernel_timing(ctx.h, None, None, None, 0) == -1
-    assert L.psr_get_kernel_timing(ctx.h, None, None, None, 6) == -1
+    assert L.psr_get_kernel_timing(ctx.h, None, None, None, None, 0) == -1
+    assert L.psr_get_kernel_timing(ctx.h, None, None, None, None, 6) == -1
     assert L.psr_set_kernel_timing(None, 1) == -1
     ctx.destroy()
