@@ -95,12 +95,14 @@ __device__ __forceinline__ void sweep_tile_items(const C* sR, C* sr, int p, cons
         const int32_t* dk = sdofs + (int64_t)k * p;
         // map and residual loads unconditional (index clamped to p-1), so the
         // chunks' loads are in flight together
-        int dof[4];
+        int dof[4] = {0, 0, 0, 0};
 #pragma unroll
-        for (int u = 0; u < 4; ++u) dof[u] = ldg_nc_i(dk + min(lane + 32 * u, p - 1));
-        double v[4];
+        for (int u = 0; u < 4; ++u)
+            if (u < nrc) dof[u] = ldg_nc_i(dk + min(lane + 32 * u, p - 1));
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = ldg_nc(r + dof[u]);
+        for (int u = 0; u < 4; ++u)
+            if (u < nrc) v[u] = ldg_nc(r + dof[u]);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int a = lane + 32 * u;
