@@ -3,10 +3,10 @@
 // ReLU network predicting the database entry of every patch, trained by
 // softmax cross-entropy with Adam, all on the GPU.
 //
-// GEMMs: one FP32 tiled kernel (64 x 64 tile, 16-deep K slices, 4 x 4
-// outputs per thread) with arbitrary operand strides, so forward (X W^T),
-// weight gradients (G^T H) and input gradients (G W) share it; the forward
-// epilogue adds the bias and writes both Z and relu(Z).
+// GEMMs: the tensor-core kernel of gemm_tc.cu (3xTF32 on tcgen05, FP32
+// accumulation in TMEM, FP32-level results) with arbitrary operand strides,
+// so forward (X W^T), weight gradients (G^T H) and input gradients (G W)
+// share it; the forward epilogue adds the bias and writes both Z and relu(Z).
 #include "psr_internal.cuh"
 
 #include <algorithm>
@@ -26,6 +26,7 @@ struct psr_mlp {
     float *G1 = nullptr, *G2 = nullptr, *G3 = nullptr;
     float* loss_part = nullptr;
     int32_t* cnt = nullptr;
+    int32_t* tc_err = nullptr;    // set when a tensor-core GEMM wait gave up
 };
 
 namespace psr {
@@ -45,6 +46,9 @@ static MlpView view(float* base, int d, int h, int m) {
     return v;
 }
 
+// C[i][j] = sum_k A(i,k) B(k,j) (+ bias[j]); A(i,k) = A[i*sai + k*sak],
+// B(k,j) = B[k*sbk + j*sbj], C row-major with ldc.  relu_out (optional)
+// receives max(C, 0).
 // C[i][j] = sum_k A(i,k) B(k,j) (+ bias[j]); A(i,k) = A[i*sai + k*sak],
 // B(k,j) = B[k*sbk + j*sbj], C row-major with ldc.  relu_out (optional)
 // receives max(C, 0).
@@ -93,11 +97,16 @@ __global__ void __launch_bounds__(256) k_gemm_f32(int M, int N, int K, const flo
     }
 }
 
+void launch_gemm_tc(int M, int N, int K, const float* A, int64_t sai, int64_t sak, const float* B, int64_t sbk,
+                    int64_t sbj, float* C, int64_t ldc, const float* bias, float* relu_out, int32_t* err,
+                    cudaStream_t s);
+int gemm_tc_prepare();
+
+static int32_t* g_tc_err = nullptr;   // set by the network that launches (one flag per network)
+
 static void gemm(int M, int N, int K, const float* A, int64_t sai, int64_t sak, const float* B, int64_t sbk,
                  int64_t sbj, float* C, int64_t ldc, const float* bias, float* relu_out, cudaStream_t s) {
-    dim3 grid((N + 63) / 64, (M + 63) / 64);
-    count_launch();
-    k_gemm_f32<<<grid, 256, 0, s>>>(M, N, K, A, sai, sak, B, sbk, sbj, C, ldc, bias, relu_out);
+    launch_gemm_tc(M, N, K, A, sai, sak, B, sbk, sbj, C, ldc, bias, relu_out, g_tc_err, s);
 }
 
 // softmax cross-entropy: G = (softmax(L) - onehot(y)) / B, loss partials
@@ -230,6 +239,7 @@ static int ensure_cap(psr_mlp* net, int Bn) {
 
 static void forward(psr_mlp* net, const float* X, int Bn, cudaStream_t s) {
     const int d = net->d, h = net->h, m = net->m;
+    g_tc_err = net->tc_err;
     MlpView P = view(net->params, d, h, m);
     gemm(Bn, h, d, X, d, 1, P.W1, 1, d, net->Z1, h, P.b1, net->H1, s);
     gemm(Bn, h, h, net->H1, h, 1, P.W2, 1, h, net->Z2, h, P.b2, net->H2, s);
@@ -238,6 +248,7 @@ static void forward(psr_mlp* net, const float* X, int Bn, cudaStream_t s) {
 
 static void backward(psr_mlp* net, const float* X, const int32_t* y, int Bn, float* loss_out, cudaStream_t s) {
     const int d = net->d, h = net->h, m = net->m;
+    g_tc_err = net->tc_err;
     MlpView P = view(net->params, d, h, m);
     MlpView G = view(net->grads, d, h, m);
     const int nb = std::min(1024, (Bn + 7) / 8);
@@ -287,6 +298,15 @@ int psr_mlp_create(int32_t in_dim, int32_t hidden, int32_t classes, psr_mlp** ou
     cudaMemset(net->params, 0, b);
     cudaMemset(net->adam_m, 0, b);
     cudaMemset(net->adam_v, 0, b);
+    if (cudaMalloc(&net->tc_err, sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        psr_mlp_destroy(net);
+        set_error(nullptr, "MLP allocation failed");
+        return PSR_ERR_OOM;
+    }
+    cudaMemset(net->tc_err, 0, sizeof(int32_t));
+    int rc = gemm_tc_prepare();
+    if (rc != PSR_OK) { psr_mlp_destroy(net); return rc; }
     *out = net;
     return PSR_OK;
 }
@@ -358,6 +378,7 @@ void psr_mlp_destroy(psr_mlp* net) {
                      net->G1, net->G2, net->G3, net->loss_part})
         cudaFree(p);
     cudaFree(net->cnt);
+    cudaFree(net->tc_err);
     delete net;
 }
 
