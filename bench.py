@@ -491,6 +491,12 @@ def run_mlp_gain(args):
     torch.cuda.synchronize()
     t_pred = time.perf_counter() - t0
     acc_train = (hints[:half] == ytr).float().mean().item()
+    # GEMM work of one training step (forward 3 GEMMs, backward 5), as
+    # FP32-equivalent flops; the tensor-core kernels do each product as three
+    # TF32 MMAs (hi*hi + hi*lo + lo*hi)
+    Bn, h = half, 256
+    step_flops = 2.0 * Bn * (d * h + h * h + h * m0) * 3
+    gemm_tflops = step_flops * args.mlp_epochs / t_train / 1e12
     res = {}
     for name, h in (("without", None), ("with", hints)):
         torch.cuda.synchronize()
@@ -507,7 +513,10 @@ def run_mlp_gain(args):
            "n_patches": pr.n_patches, "m_p_full_alg1": m, "m_seed_first_half": m0,
            "mlp": {"shape": f"{d}->256->256->{m0}", "epochs": args.mlp_epochs, "lr": args.mlp_lr,
                    "train_s": t_train, "predict_s": t_pred, "final_loss": loss.item(),
-                   "train_accuracy": acc_train},
+                   "train_accuracy": acc_train,
+                   "gemm": {"flops_per_step": step_flops, "tflops_whole_step": gemm_tflops,
+                            "note": "GEMM flops over the whole training-step time (softmax, masks, Adam included): "
+                                    "a lower bound of the GEMM rate; 3xTF32 on tcgen05"}},
            "alg1_full_evals": st_full["criterion_evals"], "seeded": res,
            "evals_saved_fraction": 1.0 - res["with"]["criterion_evals"] / max(res["without"]["criterion_evals"], 1)}
     print(json.dumps(out))
