@@ -495,7 +495,7 @@ def run_mlp_gain(args):
     # FP32-equivalent flops; the tensor-core kernels do each product as three
     # TF32 MMAs (hi*hi + hi*lo + lo*hi)
     Bn, h = half, 256
-    step_flops = 2.0 * Bn * (d * h + h * h + h * m0) * 3
+    step_flops = 2.0 * Bn * (2 * d * h + 3 * h * h + 3 * h * m0)
     gemm_tflops = step_flops * args.mlp_epochs / t_train / 1e12
     res = {}
     for name, h in (("without", None), ("with", hints)):
