@@ -48,6 +48,7 @@ struct RoundDev {
     int ticket;        // last-block counter of the round kernel
     int next_new;      // smallest candidate the current round rejected
     int nsurv;         // survivors of the current round's screen
+    int ns2[2], nn2[2];  // persistent rounds: survivors / smallest rejected, by round parity
     unsigned long long evals, exact, screened;
 };
 
@@ -723,6 +724,146 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_round_decide(RoundDev* st, 
     }
 }
 
+// ---------------------------------------------------------------- persistent rounds
+// Grid barrier of a cooperatively launched kernel (every block co-resident, so
+// every wait ends); bounded all the same: past the limit the error flag is
+// set and the barrier left, and the host reports PSR_ERR_TIMEOUT.
+__device__ __forceinline__ void rounds_barrier(unsigned int* bar, int32_t* err) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* vgen = bar + 1;
+        const unsigned int g = *vgen;
+        const unsigned int arrived = atomicAdd(bar, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            bar[0] = 0u;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == g) {
+                if (++spins > (1ll << 24)) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// All rounds of Alg. 1 in one cooperative launch: each round is the screen
+// (one thread per unassigned candidate after the entry; survivors to a
+// global list), a grid barrier, the decide phase (the grid's warps share the
+// survivors) and a second barrier after which every block derives the next
+// entry itself (the smallest rejected index), so no third barrier is needed.
+// The per-round counters are double buffered by round parity; block 0
+// resets the other parity's counters after the first barrier, when every
+// block has read them, and records the entry and the state for the host.
+template <int PM>
+__global__ void __launch_bounds__(EVAL_THREADS) k_rounds_persistent(
+    RoundDev* st, int32_t* __restrict__ phi, int count, const double* __restrict__ Ag, int p,
+    const double* __restrict__ Ball, const double* __restrict__ fro_all, const double* __restrict__ w_all,
+    const int32_t* __restrict__ sing_all, SketchDB sk, double tol, int32_t* __restrict__ surv_list,
+    int32_t* __restrict__ rep_local, unsigned int* bar, int32_t* err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ float sy[SK * 32];
+    __shared__ double sden[SK];
+    const int ld = p + 1;
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    double* sAc = reinterpret_cast<double*>(smem);
+    double* sB = sAc + p * ld;
+    double* sw = sB + p * ld;
+    float* sB32 = reinterpret_cast<float*>(sw + PROBE_STRIDE);
+    double* wbase = reinterpret_cast<double*>(smem) + decide_block_doubles(p) + (size_t)wid * (p * ld + 64);
+    WarpScratch ws{wbase, wbase + p * ld, wbase + p * ld + 32};
+    unsigned long long my_evals = 0, my_exact = 0, my_screened = 0;
+    int i0 = st->next;
+    int m = st->m;
+    bool done = st->done != 0;
+    const int gthreads = gridDim.x * blockDim.x;
+    const int gwarps = gridDim.x * wpb;
+    for (int round = 0; !done && round < count; ++round) {
+        const int par = round & 1;
+        // stage the entry: sketch for the screen, matrices for the decisions
+        const double fc = sk.fa[i0], rhoc = sk.rho[i0];
+        stage_sketch(sk.Y + (int64_t)i0 * SK * p, sk.Y32 + (int64_t)i0 * SK * p, fc, p, sy, sden);
+        const double* a = Ag + (int64_t)i0 * p * p;
+        const double* bm = Ball + (int64_t)i0 * p * p;
+        for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+            sAc[(t / p) * ld + (t % p)] = a[t];
+            const double b = bm[t];
+            sB[(t / p) * ld + (t % p)] = b;
+            sB32[(t / p) * ld + (t % p)] = (float)b;
+        }
+        if (threadIdx.x < PROBE_STRIDE) sw[threadIdx.x] = w_all[(int64_t)i0 * PROBE_STRIDE + threadIdx.x];
+        const double bfro = fro_all[i0];
+        __syncthreads();
+        int my_min = count;
+        // screen
+        for (int base = i0 + 1 + blockIdx.x * blockDim.x; base < count; base += gthreads) {
+            const int cand = base + threadIdx.x;
+            const bool open = cand < count && phi[cand] == -1;
+            bool rej = false;
+            if (open) rej = sketch_rejects<PM>(sk.Y32 + (int64_t)cand * SK * p, sk.fa[cand], sy, sden, fc, rhoc, p, tol);
+            if (open && rej) my_min = min(my_min, cand);
+            const unsigned opened = __ballot_sync(0xffffffffu, open);
+            const unsigned surv = __ballot_sync(0xffffffffu, open && !rej);
+            my_evals += __popc(opened);
+            my_screened += __popc(opened & ~surv);
+            int wb = 0;
+            if (lane == 0 && surv) wb = atomicAdd(&st->ns2[par], __popc(surv));
+            wb = __shfl_sync(0xffffffffu, wb, 0);
+            if (open && !rej) surv_list[wb + __popc(surv & ((1u << lane) - 1u))] = cand;
+        }
+        rounds_barrier(bar, err);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {        // the other parity is free again
+            st->ns2[par ^ 1] = 0;
+            st->nn2[par ^ 1] = count;
+        }
+        // decide
+        const int ns = *((volatile int*)&st->ns2[par]);
+        for (int q = blockIdx.x * wpb + wid; q < ns; q += gwarps) {
+            const int c2 = surv_list[q];
+            double dv;
+            int dec = decide_pair(Ag + (int64_t)c2 * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, false, sw, sB32);
+            if (dec < 0) {
+                dec = decide_pair(Ag + (int64_t)c2 * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, true, sw, nullptr);
+                ++my_exact;
+            }
+            if (dec == 1) { if (lane == 0) phi[c2] = m; }
+            else my_min = min(my_min, c2);
+            __syncwarp();
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) my_min = min(my_min, __shfl_xor_sync(0xffffffffu, my_min, o));
+        if (lane == 0 && my_min < count) atomicMin(&st->nn2[par], my_min);
+        rounds_barrier(bar, err);
+        if (*((volatile int*)err)) break;
+        const int nx = *((volatile int*)&st->nn2[par]);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            phi[i0] = m;
+            rep_local[m] = i0;
+            if (sing_all[i0] && st->first_singular < 0) st->first_singular = i0;
+            st->m = m + 1;
+            st->next = nx;
+            if (nx >= count) st->done = 1;
+        }
+        m += 1;
+        i0 = nx;
+        done = nx >= count;
+    }
+    if (lane == 0) {
+        if (my_evals) atomicAdd(&st->evals, my_evals);
+        if (my_exact) atomicAdd(&st->exact, my_exact);
+        if (my_screened) atomicAdd(&st->screened, my_screened);
+    }
+}
+
 // Stages seed entry e (patch matrix, inverse, probe) into shared memory.
 __device__ __forceinline__ void stage_seed(EntryDB db, int p, int e, double* sAc, double* sB, double* sw) {
     const int ld = p + 1;
@@ -948,6 +1089,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         init.m = m0;
         init.next = 0;
         init.next_new = count;
+        init.nn2[0] = init.nn2[1] = count;
         PSR_CUDA(ctx, cudaMemcpyAsync(st, &init, sizeof(RoundDev), cudaMemcpyHostToDevice, s));
         const int ld = p + 1;
         const int wpb = EVAL_THREADS / 32;
@@ -1019,9 +1161,71 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
             count_launch();
             k_finish_first<<<1, 1, 0, s>>>(st, count);
         }
+        // all rounds in one cooperative launch when every block of the grid
+        // can be co-resident; otherwise two launches per round
+        bool persistent = false;
+        {
+            int coop = 0;
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
+            const void* kf = (p <= 8) ? (const void*)k_rounds_persistent<8>
+                           : (p <= 16) ? (const void*)k_rounds_persistent<16> : (const void*)k_rounds_persistent<32>;
+            int per_sm = 0;
+            if (coop && set_smem(kf, smem_dec) == PSR_OK &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, EVAL_THREADS, smem_dec) == cudaSuccess &&
+                per_sm >= 1) {
+                int sms = 0;
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+                const int grid = sms * std::min(per_sm, 4);
+                unsigned int* bar = nullptr;
+                int32_t* perr = nullptr;
+                PSR_CUDA(ctx, cudaMalloc(&bar, 2 * sizeof(unsigned int)));
+                PSR_CUDA(ctx, cudaMalloc(&perr, sizeof(int32_t)));
+                PSR_CUDA(ctx, cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s));
+                PSR_CUDA(ctx, cudaMemsetAsync(perr, 0, sizeof(int32_t), s));
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3((unsigned)grid);
+                cfg.blockDim = dim3(EVAL_THREADS);
+                cfg.dynamicSmemBytes = smem_dec;
+                cfg.stream = s;
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeCooperative;
+                at[0].val.cooperative = 1;
+                cfg.attrs = at;
+                cfg.numAttrs = 1;
+                count_launch();
+                cudaError_t le;
+                if (p <= 8)
+                    le = cudaLaunchKernelEx(&cfg, k_rounds_persistent<8>, st, phi_l, count, Ag, p, Ball, fro_all,
+                                            w_all, (const int32_t*)sing_all, sk, tol, surv_list, rep_l, bar, perr);
+                else if (p <= 16)
+                    le = cudaLaunchKernelEx(&cfg, k_rounds_persistent<16>, st, phi_l, count, Ag, p, Ball, fro_all,
+                                            w_all, (const int32_t*)sing_all, sk, tol, surv_list, rep_l, bar, perr);
+                else
+                    le = cudaLaunchKernelEx(&cfg, k_rounds_persistent<32>, st, phi_l, count, Ag, p, Ball, fro_all,
+                                            w_all, (const int32_t*)sing_all, sk, tol, surv_list, rep_l, bar, perr);
+                if (le == cudaSuccess) {
+                    persistent = true;
+                    int32_t herr = 0;
+                    PSR_CUDA(ctx, cudaMemcpyAsync(h_st, st, sizeof(RoundDev), cudaMemcpyDeviceToHost, s));
+                    PSR_CUDA(ctx, cudaMemcpyAsync(&herr, perr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+                    PSR_CUDA(ctx, cudaStreamSynchronize(s));
+                    cudaFree(bar);
+                    cudaFree(perr);
+                    if (herr || !h_st->done) {
+                        set_error(ctx, "a grid barrier of the Alg. 1 rounds gave up waiting");
+                        rc = PSR_ERR_TIMEOUT;
+                        break;
+                    }
+                } else {
+                    cudaGetLastError();
+                    cudaFree(bar);
+                    cudaFree(perr);
+                }
+            }
+        }
         int batch = 8;
         int issued = 0;
-        for (;;) {
+        for (; !persistent;) {
             for (int r = 0; r < batch; ++r) {
                 count_launch();
                 if (p <= 8)
