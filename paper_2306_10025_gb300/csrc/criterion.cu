@@ -366,26 +366,30 @@ struct EntryDB {
 // transposed products read M directly, so each step is p fused multiply-adds
 // per lane and no warp reductions besides the normalisation.
 __device__ double dominant_right_sv_warp(const double* M, int p, int ld, int iters) {
+    // FP32: only a direction is sought (any direction gives a valid bound,
+    // the bounds themselves are formed in FP64 from it), and FP32 runs at 64x
+    // the FP64 rate on this GPU
     const int lane = threadIdx.x & 31;
     const bool act = lane < p;
-    double row[32];
+    float row[32];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) row[k] = (act && k < p) ? M[lane * ld + k] : 0.0;
-    double v = act ? 1.0 : 0.0;
+    for (int k = 0; k < 32; ++k) row[k] = (act && k < p) ? (float)M[lane * ld + k] : 0.f;
+    float col[32];                                     // column `lane` of M
+#pragma unroll
+    for (int r = 0; r < 32; ++r) col[r] = (act && r < p) ? (float)M[r * ld + lane] : 0.f;
+    float v = act ? 1.f : 0.f;
     for (int it = 0; it < iters; ++it) {
-        double t = 0.0;                                // t_lane = (M v)_lane
+        float t = 0.f;                                 // t_lane = (M v)_lane
 #pragma unroll
-        for (int k = 0; k < 32; ++k) t = fma(row[k], __shfl_sync(0xffffffffu, v, k), t);
-        double u = 0.0;                                // u_lane = (M^T t)_lane
-        for (int r = 0; r < p; ++r) {
-            const double tr = __shfl_sync(0xffffffffu, t, r);
-            if (act) u = fma(M[r * ld + lane], tr, u);
-        }
-        const double nu = sqrt(warp_sum(u * u));
-        if (!(nu > 0.0)) return 0.0;
+        for (int k = 0; k < 32; ++k) t = fmaf(row[k], __shfl_sync(0xffffffffu, v, k), t);
+        float u = 0.f;                                 // u_lane = (M^T t)_lane
+#pragma unroll
+        for (int r = 0; r < 32; ++r) u = fmaf(col[r], __shfl_sync(0xffffffffu, t, r), u);
+        const float nu = sqrtf(warp_sumf(u * u));
+        if (!(nu > 0.f) || !(nu < 3.0e38f)) return (double)v;   // keep the last finite direction
         v = u / nu;
     }
-    return v;
+    return (double)v;
 }
 
 // y_lane = (M x)_lane for a lane-held x (row stride ld); all lanes call.
@@ -484,6 +488,9 @@ __global__ void k_sketch_dirs(const double* __restrict__ Ag, int count, int p, d
 
 // Per matrix of a batch (one warp each): y_k = fl(A x_k), ||A||_F and the
 // residual bound rho >= ||B^ A - I||_2 with B^ = Binv.
+// (PM >= p: the unrolled loops stop at PM, FP64 instructions past p are not
+// issued; predicated-off lanes would still cost the FP64 pipe.)
+template <int PM>
 __global__ void __launch_bounds__(256) k_sketch(const double* __restrict__ A, const double* __restrict__ Binv,
                                                 int count, int p, const double* __restrict__ X,
                                                 double* __restrict__ Y, float* __restrict__ Y32,
@@ -494,15 +501,15 @@ __global__ void __launch_bounds__(256) k_sketch(const double* __restrict__ A, co
     const bool act = lane < p;
     const double* Ai = A + (int64_t)i * p * p;
     const double* Bi = Binv + (int64_t)i * p * p;
-    double a[32], b[32];
+    double a[PM], b[PM];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
+    for (int j = 0; j < PM; ++j) {
         a[j] = (act && j < p) ? Ai[lane * p + j] : 0.0;
         b[j] = (act && j < p) ? Bi[lane * p + j] : 0.0;
     }
     double fa2 = 0.0, fb2 = 0.0;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
+    for (int j = 0; j < PM; ++j) {
         fa2 = fma(a[j], a[j], fa2);
         fb2 = fma(b[j], b[j], fb2);
     }
@@ -510,7 +517,7 @@ __global__ void __launch_bounds__(256) k_sketch(const double* __restrict__ A, co
     for (int k = 0; k < SK; ++k) {
         double y = 0.0;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) y = fma(a[j], X[k * 32 + j], y);
+        for (int j = 0; j < PM; ++j) y = fma(a[j], X[k * 32 + j], y);
         if (act) {
             Y[((int64_t)i * SK + k) * p + lane] = y;
             Y32[((int64_t)i * SK + k) * p + lane] = (float)y;
@@ -519,11 +526,11 @@ __global__ void __launch_bounds__(256) k_sketch(const double* __restrict__ A, co
     // column j of B^ A: lane r sums b[r][k] A[k][j], A[k][j] from lane k
     double res2 = 0.0;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
+    for (int j = 0; j < PM; ++j) {
         if (j < p) {
             double t = 0.0;
 #pragma unroll
-            for (int k = 0; k < 32; ++k) t = fma(b[k], __shfl_sync(0xffffffffu, a[j], k), t);
+            for (int k = 0; k < PM; ++k) t = fma(b[k], __shfl_sync(0xffffffffu, a[j], k), t);
             const double r = t - ((lane == j) ? 1.0 : 0.0);
             if (act) res2 = fma(r, r, res2);
         }
@@ -1011,6 +1018,15 @@ __global__ void k_verify_hints(RoundDev* st, int32_t* __restrict__ phi, int coun
     }
 }
 
+static void launch_sketch(const double* A, const double* Binv, int count, int p, const double* X, double* Y,
+                          float* Y32, double* fa, double* rho, cudaStream_t s) {
+    const int blocks = (count + 7) / 8;
+    if (p <= 8) k_sketch<8><<<blocks, 256, 0, s>>>(A, Binv, count, p, X, Y, Y32, fa, rho);
+    else if (p <= 16) k_sketch<16><<<blocks, 256, 0, s>>>(A, Binv, count, p, X, Y, Y32, fa, rho);
+    else if (p <= 24) k_sketch<24><<<blocks, 256, 0, s>>>(A, Binv, count, p, X, Y, Y32, fa, rho);
+    else k_sketch<32><<<blocks, 256, 0, s>>>(A, Binv, count, p, X, Y, Y32, fa, rho);
+}
+
 static int set_smem(const void* f, size_t bytes) {
     if (bytes > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -1079,7 +1095,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         count_launch();
         k_sketch_dirs<<<1, 32 * SK, 0, s>>>(Ag, count, p, skX);
         count_launch();
-        k_sketch<<<(count + 7) / 8, 256, 0, s>>>(Ag, Ball, count, p, skX, skY, skY32, skF, skR);
+        launch_sketch(Ag, Ball, count, p, skX, skY, skY32, skF, skR, s);
         PSR_CHECK_LAUNCH(ctx, "patch sketches");
         const SketchDB sk{skX, skY, skF, skR, skY32};
         SketchDB skd{skX, nullptr, nullptr, nullptr, nullptr};
@@ -1123,7 +1139,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
             PSR_CUDA(ctx, cudaMalloc(&sdR, sizeof(double) * (size_t)m0));
             PSR_CUDA(ctx, cudaMalloc(&sdY32, sizeof(float) * (size_t)m0 * SK * p));
             count_launch();
-            k_sketch<<<(m0 + 7) / 8, 256, 0, s>>>(db.A, db.Binv, m0, p, skX, sdY, sdY32, sdF, sdR);
+            launch_sketch(db.A, db.Binv, m0, p, skX, sdY, sdY32, sdF, sdR, s);
             skd = SketchDB{skX, sdY, sdF, sdR, sdY32};
             std::vector<int32_t> seq(m0, -1);
             PSR_CUDA(ctx, cudaMemcpyAsync(rep_l, seq.data(), sizeof(int32_t) * m0, cudaMemcpyHostToDevice, s));

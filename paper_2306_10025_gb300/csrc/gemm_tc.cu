@@ -8,12 +8,13 @@
 // term is below 2^-22 |a||b| per product and lo enters the MMA truncated to
 // TF32 (relative 2^-11 of lo), so the result carries FP32-level error.
 //
-// Tiles: one CTA of 4 warps per 128 x 128 output tile, K in slices of 32.
-// Each slice is converted by the CTA into shared memory in the no-swizzle
-// K-major core-matrix layout (8 rows x 16 bytes = 8 x 4 FP32 per core
-// matrix), then one elected thread issues 4 K-steps x 3 MMAs (M = 128,
-// N = 128, K = 8) and commits to an mbarrier; all waits are bounded.  The
-// epilogue reads each warp's 32 TMEM lanes (one output row per thread).
+// Tiles: one CTA of 4 warps per 128 x 128 output tile, K in slices of 32,
+// two shared-memory stages.  Each slice is converted by the CTA into the
+// no-swizzle K-major core-matrix layout (8 rows x 16 bytes = 8 x 4 FP32 per
+// core matrix) while the tensor cores work on the previous one; one elected
+// thread issues 4 K-steps x 3 MMAs (M = 128, N = 128, K = 8) and commits to
+// the stage's mbarrier; all waits are bounded.  The epilogue reads each
+// warp's 32 TMEM lanes (one output row per thread).
 #include "psr_internal.cuh"
 #include "tcgen05.cuh"
 
@@ -54,19 +55,33 @@ __device__ __forceinline__ int core_off32(int row, int k) {
 
 // One 128 x 32 slice of a strided operand into hi / lo shared buffers:
 // op(r, k) = X[r * srow + k * sk], zero outside rows < nrow, k < nk.  The
-// element order follows the unit stride so the global loads coalesce.
+// element order follows the unit stride so the global loads coalesce; each
+// thread requests 16 elements before converting and storing any of them.
 __device__ __forceinline__ void load_slice(const float* __restrict__ X, int64_t srow, int64_t sk, int r0, int nrow,
                                            int k0, int nk, unsigned char* hi, unsigned char* lo) {
     const bool kfast = (sk == 1);
-    for (int e = threadIdx.x; e < GM * GK; e += blockDim.x) {
-        const int r = kfast ? e / GK : e % GM;
-        const int k = kfast ? e % GK : e / GM;
-        const int gr = r0 + r, gk = k0 + k;
-        const float v = (gr < nrow && gk < nk) ? X[(int64_t)gr * srow + (int64_t)gk * sk] : 0.f;
-        const float h = to_tf32(v);
-        const int off = core_off32(r, k);
-        *reinterpret_cast<float*>(hi + off) = h;
-        *reinterpret_cast<float*>(lo + off) = v - h;
+    constexpr int PER = GM * GK / 128;                   // elements per thread (128 threads)
+#pragma unroll
+    for (int g = 0; g < PER; g += 16) {
+        float v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int e = threadIdx.x + 128 * (g + u);
+            const int r = kfast ? e / GK : e % GM;
+            const int k = kfast ? e % GK : e / GM;
+            const int gr = r0 + r, gk = k0 + k;
+            v[u] = (gr < nrow && gk < nk) ? __ldg(X + (int64_t)gr * srow + (int64_t)gk * sk) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int e = threadIdx.x + 128 * (g + u);
+            const int r = kfast ? e / GK : e % GM;
+            const int k = kfast ? e % GK : e / GM;
+            const float h = to_tf32(v[u]);
+            const int off = core_off32(r, k);
+            *reinterpret_cast<float*>(hi + off) = h;
+            *reinterpret_cast<float*>(lo + off) = v[u] - h;
+        }
     }
 }
 
@@ -77,11 +92,8 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const floa
                                                  float* __restrict__ C, int64_t ldc, const float* __restrict__ bias,
                                                  float* __restrict__ relu_out, int32_t* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* sAh = smem;
-    unsigned char* sAl = smem + TILE_BYTES;
-    unsigned char* sBh = smem + 2 * TILE_BYTES;
-    unsigned char* sBl = smem + 3 * TILE_BYTES;
-    __shared__ __align__(8) uint64_t mbar;
+    // two stages of four operand slices: A hi, A lo, B hi, B lo
+    __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -92,44 +104,59 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const floa
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&mbar)), "r"(1) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&mbar[0])), "r"(1) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&mbar[1])), "r"(1) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
-    const uint32_t mbar_a = smem_u32(&mbar);
     constexpr uint32_t idesc = idesc_tf32(GM, GN);
-    uint32_t phase = 0;
+    uint32_t issued[2] = {0u, 0u}, waited[2] = {0u, 0u};   // commits per stage buffer
     bool failed = false;
-    bool first = true;
-    for (int k0 = 0; k0 < K; k0 += GK) {
-        // A slice: rows i of C, B slice: columns j of C (op(j, k) = B(k, j))
-        load_slice(A, sai, sak, i0, M, k0, K, sAh, sAl);
-        load_slice(B, sbj, sbk, j0, N, k0, K, sBh, sBl);
+    const int nslices = (K + GK - 1) / GK;
+    // Software pipeline: while the tensor cores work on slice t, the CTA
+    // converts slice t+1 into the other stage; a stage is refilled only after
+    // the MMAs that read it have committed.
+    for (int t = 0; t < nslices; ++t) {
+        const int b = t & 1;
+        unsigned char* st = smem + (size_t)b * 4 * TILE_BYTES;
+        if (issued[b] > waited[b]) {
+            const bool ok = mbar_wait_bounded(smem_u32(&mbar[b]), waited[b] & 1u);
+            ++waited[b];
+            if (__syncthreads_or(!ok)) { failed = true; break; }
+        }
+        const int k0 = t * GK;
+        load_slice(A, sai, sak, i0, M, k0, K, st, st + TILE_BYTES);
+        load_slice(B, sbj, sbk, j0, N, k0, K, st + 2 * TILE_BYTES, st + 3 * TILE_BYTES);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (tid == 0) {
-            const uint32_t ah = smem_u32(sAh), al = smem_u32(sAl), bh = smem_u32(sBh), bl = smem_u32(sBl);
+            const uint32_t ah = smem_u32(st), al = ah + TILE_BYTES, bh = ah + 2 * TILE_BYTES, bl = ah + 3 * TILE_BYTES;
 #pragma unroll
             for (int s = 0; s < GK / 8; ++s) {
                 const uint32_t o = s * 256;                   // two core matrices along K
-                mma_tf32(tmem, make_desc(ah + o, 128, GSBO), make_desc(bh + o, 128, GSBO), idesc, first ? 0u : 1u);
-                first = false;
+                mma_tf32(tmem, make_desc(ah + o, 128, GSBO), make_desc(bh + o, 128, GSBO), idesc,
+                         (t > 0 || s > 0) ? 1u : 0u);
                 mma_tf32(tmem, make_desc(ah + o, 128, GSBO), make_desc(bl + o, 128, GSBO), idesc, 1u);
                 mma_tf32(tmem, make_desc(al + o, 128, GSBO), make_desc(bh + o, 128, GSBO), idesc, 1u);
             }
-            mma_commit(mbar_a);
+            mma_commit(smem_u32(&mbar[b]));
         }
-        first = false;
-        const bool ok = mbar_wait_bounded(mbar_a, phase);
-        phase ^= 1u;
-        if (__syncthreads_or(!ok)) { failed = true; break; }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        ++issued[b];
     }
+    // wait for every outstanding commit (the last one covers all MMAs)
+    for (int b = 0; b < 2 && !failed; ++b) {
+        while (issued[b] > waited[b]) {
+            const bool ok = mbar_wait_bounded(smem_u32(&mbar[b]), waited[b] & 1u);
+            ++waited[b];
+            if (__syncthreads_or(!ok)) { failed = true; break; }
+        }
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!failed) {
         const int row = i0 + tid;                           // TMEM lane = row of the tile
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
@@ -161,7 +188,11 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const floa
         const int row = i0 + tid;
         if (row < M)
             for (int col = j0; col < min(N, j0 + GN); ++col) C[(int64_t)row * ldc + col] = __int_as_float(0x7fc00000);
-        mbar_wait_bounded(mbar_a, phase ^ 1u);      // let an MMA still in flight finish (bounded)
+        for (int b = 0; b < 2; ++b)                   // let MMAs still in flight finish (bounded)
+            while (issued[b] > waited[b]) {
+                mbar_wait_bounded(smem_u32(&mbar[b]), waited[b] & 1u);
+                ++waited[b];
+            }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -170,7 +201,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const floa
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"((uint32_t)GN) : "memory");
 }
 
-size_t gemm_tc_smem() { return (size_t)4 * TILE_BYTES; }
+size_t gemm_tc_smem() { return (size_t)2 * 4 * TILE_BYTES; }
 
 int gemm_tc_prepare() {
     cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_tc_smem());
