@@ -59,11 +59,14 @@ struct WarpScratch {  // per-warp shared memory layout for p <= 32
 };
 
 // Decides d(A_i, B_c) < tol for one candidate.  sAc, sB: shared p x ld.
+// PM >= p bounds the unrolled per-lane loops (FP64 instructions of
+// predicated-off iterations would still occupy the pipe).
 // probe (may be NULL): two vectors w_k = B_c^{-1} v_k / ||v_k|| (at probe and
 // probe + 32), so that ||D w_k|| = ||E v_k|| / ||v_k|| <= sigma_max(E) are
 // O(p^2) lower bounds.
 // Returns 1 accept, 0 reject, -1 undecided (needs the exact path).  *dv gets
 // the deciding value.  All lanes call; lane r handles row r.
+template <int PM = 32>
 __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, const double* sB,
                            int p, int ld, double binv_fro, double tol, WarpScratch ws, double* dv,
                            bool allow_exact_here, const double* probe = nullptr,
@@ -109,20 +112,20 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
         float* E32 = reinterpret_cast<float*>(ws.E);
         float* v32 = reinterpret_cast<float*>(ws.v);
         float* w32 = reinterpret_cast<float*>(ws.w);
-        float f[32];
+        float f[PM];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) f[j] = 0.f;
+        for (int j = 0; j < PM; ++j) f[j] = 0.f;
         if (act) {
             for (int k = 0; k < p; ++k) {
                 const float dk = (float)(sAc[lane * ld + k] - Ai[lane * p + k]);
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
+                for (int j = 0; j < PM; ++j)
                     if (j < p) f[j] = fmaf(dk, sB32[k * ld + j], f[j]);
             }
         }
         float fr2 = 0.f, ra = 0.f;
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
+        for (int j = 0; j < PM; ++j)
             if (j < p) { fr2 = fmaf(f[j], f[j], fr2); ra += fabsf(f[j]); }
         const float rn = sqrtf(fr2);
         fr2 = warp_sumf(fr2);
@@ -131,7 +134,7 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
         for (int o = 16; o > 0; o >>= 1) ni = fmaxf(ni, __shfl_xor_sync(0xffffffffu, ni, o));
         if (act) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
+            for (int j = 0; j < PM; ++j)
                 if (j < p) E32[lane * ld + j] = f[j];
         }
         __syncwarp();
@@ -159,7 +162,7 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
                 float wr = 0.f;
                 if (act) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
+                    for (int j = 0; j < PM; ++j)
                         if (j < p) wr = fmaf(f[j], v32[j], wr);
                 }
                 const float nw = sqrtf(warp_sumf(wr * wr));
@@ -183,20 +186,20 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
         __syncwarp();
     }
     // pass 2: E row = D row * B^-1
-    double e[32];
+    double e[PM];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) e[j] = 0.0;
+    for (int j = 0; j < PM; ++j) e[j] = 0.0;
     if (act) {
         for (int k = 0; k < p; ++k) {
             const double dk = sAc[lane * ld + k] - Ai[lane * p + k];
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
+            for (int j = 0; j < PM; ++j)
                 if (j < p) e[j] = fma(dk, sB[k * ld + j], e[j]);
         }
     }
     double fro2 = 0.0, rabs = 0.0;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
+    for (int j = 0; j < PM; ++j) {
         if (j < p) { fro2 = fma(e[j], e[j], fro2); rabs += fabs(e[j]); }
     }
     const double rown = sqrt(fro2);
@@ -204,7 +207,7 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
     const double ninf = warp_max(act ? rabs : 0.0);
     if (act) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
+        for (int j = 0; j < PM; ++j)
             if (j < p) ws.E[lane * ld + j] = e[j];
     }
     __syncwarp();
@@ -233,7 +236,7 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
         double wr = 0.0;
         if (act) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
+            for (int j = 0; j < PM; ++j)
                 if (j < p) wr = fma(e[j], ws.v[j], wr);
         }
         const double nw = sqrt(warp_sum(wr * wr));
@@ -266,9 +269,9 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
     // A near tie that neither settles goes to the Jacobi eigenvalues of G.
     __syncwarp();
     // column j of E lives in lane j after a transpose read
-    double ecol[32];
+    double ecol[PM];
 #pragma unroll
-    for (int r = 0; r < 32; ++r) ecol[r] = (act && r < p) ? ws.E[r * ld + lane] : 0.0;
+    for (int r = 0; r < PM; ++r) ecol[r] = (act && r < p) ? ws.E[r * ld + lane] : 0.0;
     __syncwarp();
     // ws.E <- X I - G (neg) or G; G[lane][k] = sum_r E[r][lane] E[r][k], every
     // lane runs every shuffle
@@ -314,7 +317,7 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
             const double z = (lane < k) ? -yl : (lane == k ? 1.0 : 0.0);
             double t = 0.0;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) t = fma(e[j], __shfl_sync(0xffffffffu, z, j), t);
+            for (int j = 0; j < PM; ++j) t = fma(e[j], __shfl_sync(0xffffffffu, z, j), t);
             const double nez = sqrt(warp_sum(t * t));
             const double nz = sqrt(warp_sum(z * z));
             const double lbz = (nez * (1.0 - (double)(p + 4) * U64) - 1.01 * gamma_u(p) * sqrt(fro2) * nz) /
@@ -837,9 +840,9 @@ __global__ void __launch_bounds__(EVAL_THREADS) k_rounds_persistent(
         for (int q = blockIdx.x * wpb + wid; q < ns; q += gwarps) {
             const int c2 = surv_list[q];
             double dv;
-            int dec = decide_pair(Ag + (int64_t)c2 * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, false, sw, sB32);
+            int dec = decide_pair<PM>(Ag + (int64_t)c2 * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, false, sw, sB32);
             if (dec < 0) {
-                dec = decide_pair(Ag + (int64_t)c2 * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, true, sw, nullptr);
+                dec = decide_pair<PM>(Ag + (int64_t)c2 * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, true, sw, nullptr);
                 ++my_exact;
             }
             if (dec == 1) { if (lane == 0) phi[c2] = m; }
@@ -1184,7 +1187,8 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
             int coop = 0;
             cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
             const void* kf = (p <= 8) ? (const void*)k_rounds_persistent<8>
-                           : (p <= 16) ? (const void*)k_rounds_persistent<16> : (const void*)k_rounds_persistent<32>;
+                           : (p <= 16) ? (const void*)k_rounds_persistent<16>
+                           : (p <= 24) ? (const void*)k_rounds_persistent<24> : (const void*)k_rounds_persistent<32>;
             int per_sm = 0;
             if (coop && set_smem(kf, smem_dec) == PSR_OK &&
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, EVAL_THREADS, smem_dec) == cudaSuccess &&
@@ -1215,6 +1219,9 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
                                             w_all, (const int32_t*)sing_all, sk, tol, surv_list, rep_l, bar, perr);
                 else if (p <= 16)
                     le = cudaLaunchKernelEx(&cfg, k_rounds_persistent<16>, st, phi_l, count, Ag, p, Ball, fro_all,
+                                            w_all, (const int32_t*)sing_all, sk, tol, surv_list, rep_l, bar, perr);
+                else if (p <= 24)
+                    le = cudaLaunchKernelEx(&cfg, k_rounds_persistent<24>, st, phi_l, count, Ag, p, Ball, fro_all,
                                             w_all, (const int32_t*)sing_all, sk, tol, surv_list, rep_l, bar, perr);
                 else
                     le = cudaLaunchKernelEx(&cfg, k_rounds_persistent<32>, st, phi_l, count, Ag, p, Ball, fro_all,
