@@ -90,6 +90,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--apply-reps", type=int, default=200)
     ap.add_argument("--mlp", action="store_true", help="learned-assignment gain on the 3D lognormal workload")
+    ap.add_argument("--tol-sweep", action="store_true",
+                    help="compressibility curve: m_p, setup and residual per criterion tolerance and precision")
     ap.add_argument("--mlp-n", type=int, default=32)
     ap.add_argument("--mlp-epochs", type=int, default=300)
     ap.add_argument("--mlp-lr", type=float, default=1e-3)
@@ -526,8 +528,53 @@ def run_mlp_gain(args):
     print(json.dumps(out))
 
 
+def run_tol_sweep(args, cfg, name):
+    """Compressibility of the workload (the tolerance sweep of the 2D Stokes
+    configuration, 1e-3 .. 1e-1, FP64 and FP32 inverses): for every setting
+    the number of database entries, the retained fraction, the setup time
+    and the outer solve (fixed iteration budget) with its residual."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2306_10025_gb300 as L
+    dev = torch.device("cuda", 0)
+    pr = build_problem(cfg)
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    rp, ci, va = t(pr.rowptr, torch.int32), t(pr.colidx, torch.int32), t(pr.vals, torch.float64)
+    dofs = t(pr.patch_dofs, torch.int32)
+    offs = None if pr.uniform_size else t(pr.patch_offsets, torch.int32)
+    b = t(pr.rhs(0), torch.float64)
+    rows = []
+    for prec in ("fp64", "fp32"):
+        for tol in (0.0, 1e-3, 3e-3, 1e-2, 3e-2, 1e-1):
+            opts = L.make_opts(tol=tol, store_prec=prec, weighting=cfg["weighting"], krylov=cfg["krylov"],
+                               restart=30, rtol=1e-8, maxit=args.maxit)
+            for rep in range(2):                      # the second is timed (the first warms up)
+                x = torch.zeros_like(b)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                ctx = L.psr_setup(rp, ci, va, dofs, offsets=offs, uniform_size=pr.uniform_size, opts=opts)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                info = ctx.solve(b, x)
+                torch.cuda.synchronize()
+                t2 = time.perf_counter()
+                st = ctx.stats()
+                ctx.destroy()
+            rows.append({"store_prec": prec, "tol": tol, "m_p": st["m_p"], "retained_fraction": st["m_p"] / pr.n_patches,
+                         "factor_bytes": st["factor_bytes"], "setup_s": t1 - t0, "solve_s": t2 - t1,
+                         "iterations": info["iterations"], "relres": info["relres"],
+                         "criterion_evals": st["criterion_evals"], "criterion_screened": st["criterion_screened"]})
+    print(json.dumps({"metric": "compressibility (database entries, setup s, residual) per criterion tolerance",
+                      "workload": cfg["desc"], "n": pr.n, "n_patches": pr.n_patches, "maxit": args.maxit,
+                      "rows": rows}))
+
+
 def main():
     args = parse()
+    if args.tol_sweep:
+        run_tol_sweep(args, CONFIGS[args.config], args.config)
+        return
     if args.mlp:
         run_mlp_gain(args)
         return
