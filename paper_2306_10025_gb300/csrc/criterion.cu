@@ -1187,8 +1187,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
             int coop = 0;
             cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
             const void* kf = (p <= 8) ? (const void*)k_rounds_persistent<8>
-                           : (p <= 16) ? (const void*)k_rounds_persistent<16>
-                           : (p <= 24) ? (const void*)k_rounds_persistent<24> : (const void*)k_rounds_persistent<32>;
+                           : (p <= 16) ? (const void*)k_rounds_persistent<16> : (const void*)k_rounds_persistent<32>;
             int per_sm = 0;
             if (coop && set_smem(kf, smem_dec) == PSR_OK &&
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, EVAL_THREADS, smem_dec) == cudaSuccess &&
@@ -1220,9 +1219,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
                 else if (p <= 16)
                     le = cudaLaunchKernelEx(&cfg, k_rounds_persistent<16>, st, phi_l, count, Ag, p, Ball, fro_all,
                                             w_all, (const int32_t*)sing_all, sk, tol, surv_list, rep_l, bar, perr);
-                else if (p <= 24)
-                    le = cudaLaunchKernelEx(&cfg, k_rounds_persistent<24>, st, phi_l, count, Ag, p, Ball, fro_all,
-                                            w_all, (const int32_t*)sing_all, sk, tol, surv_list, rep_l, bar, perr);
+
                 else
                     le = cudaLaunchKernelEx(&cfg, k_rounds_persistent<32>, st, phi_l, count, Ag, p, Ball, fro_all,
                                             w_all, (const int32_t*)sing_all, sk, tol, surv_list, rep_l, bar, perr);
