@@ -545,3 +545,53 @@ def alg1_seeded(A, tol, A_seed, pred=None):
             reps.append(i)
             phi[i] = len(db_A) - 1
     return {"phi": phi, "reps": np.array(reps), "Binv": np.stack(db_B), "evals": evals, "hits": hits}
+
+
+# ---------------------------------------------------------------------------
+# Alg. 2 (section 3.2), entrywise variant: a database of m_p entries fixed
+# beforehand.  d(A_i, B_j) = ||A_i - B_j||_l1 entrywise; B_j the entrywise
+# mean of its cluster (Eq. 6); the stored inverse is the inverse of that mean.
+# The initial means are the patches init[0..m_p-1] (m_p distinct patches the
+# caller drew at random: Alg. 2 draws them with randperm).  One sweep assigns
+# every patch to its nearest mean (ties: the lowest j); when an assignment
+# changed the means are recomputed (members summed in increasing patch index;
+# a cluster left without members keeps its mean) and another sweep follows.
+# ---------------------------------------------------------------------------
+
+def kmeans_l1(A, init, max_iter=100, near_tie_rel=1e-9):
+    """Returns phi (n_p), means (m_p, p, p), Binv (inverses of the means),
+    singular flags, the number of sweeps and the near ties of the last sweep:
+    patches with another mean within near_tie_rel (relative) of the nearest,
+    where the argmin could differ between two summation orders."""
+    A = np.asarray(A, dtype=np.float64)
+    npch = A.shape[0]
+    init = np.asarray(init, dtype=np.int64)
+    m = init.size
+    B = A[init].copy()
+    phi = np.full(npch, -1, dtype=np.int64)
+    flat = A.reshape(npch, -1)
+    sweeps = 0
+    near = []
+    while sweeps < max_iter:
+        sweeps += 1
+        D = np.empty((npch, m))
+        for j in range(m):
+            D[:, j] = np.abs(flat - B[j].reshape(-1)).sum(axis=1)
+        new = np.argmin(D, axis=1)
+        best = D[np.arange(npch), new]
+        close = (D <= best[:, None] * (1.0 + near_tie_rel)) & (D > 0.0)
+        close[np.arange(npch), new] = False
+        near = [int(i) for i in np.flatnonzero(close.any(axis=1))]
+        changed = bool(np.any(new != phi))
+        phi = new
+        if not changed:
+            break
+        for j in range(m):
+            members = np.flatnonzero(phi == j)
+            if members.size:
+                acc = np.zeros(A.shape[1:])
+                for k in members:
+                    acc = acc + A[k]
+                B[j] = acc / members.size
+    Binv, singular = lu_inverse(B)
+    return {"phi": phi, "means": B, "Binv": Binv, "singular": singular, "sweeps": sweeps, "near_ties": near}

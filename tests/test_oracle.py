@@ -440,3 +440,65 @@ def test_alg1_seeded_hints_keep_assignment_valid():
     s2 = O.alg1_seeded(A, tol, seed_A, pred=bad)
     d = O.criterion(A, A[base["reps"]][s2["phi"]], s2["Binv"][s2["phi"]])
     assert np.all(d < tol)
+
+
+# ------------------------------------------------------------------ Alg. 2 (entrywise k-means)
+def test_kmeans_from_class_representatives_recovers_alg1():
+    """Started from the nine C1 class representatives, entrywise k-means
+    assigns every patch to its class at once (class members are bitwise
+    identical, so their distance to the class mean is rounding-small while
+    other classes differ in whole entries), so phi equals Alg. 1's and the
+    second sweep changes nothing."""
+    pr = P.poisson2d_q2(16)
+    A = O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d())
+    ref = O.alg1(A, 1e-12)
+    km = O.kmeans_l1(A, ref["reps"])
+    assert km["sweeps"] == 2
+    assert np.array_equal(km["phi"], ref["phi"])
+    assert km["near_ties"] == []
+
+
+def test_kmeans_two_scaled_groups():
+    """Patches s_k M with s in two separated groups: two clusters recovered
+    from one seed in each, means = (average s) M."""
+    g = np.random.default_rng(5)
+    M = np.array([[4.0, 1.0, 0.0], [1.0, 3.0, 1.0], [0.0, 1.0, 2.0]])
+    s = np.concatenate([1.0 + 0.05 * g.standard_normal(7), 5.0 + 0.05 * g.standard_normal(5)])
+    order = g.permutation(12)
+    s = s[order]
+    A = s[:, None, None] * M
+    grp = (s > 3.0).astype(int)
+    init = [int(np.flatnonzero(grp == 0)[0]), int(np.flatnonzero(grp == 1)[0])]
+    km = O.kmeans_l1(A, init)
+    assert np.array_equal(km["phi"], grp)
+    for j in range(2):
+        assert np.allclose(km["means"][j], s[grp == j].mean() * M, rtol=1e-13, atol=0)
+    assert np.allclose(km["Binv"][0] @ km["means"][0], np.eye(3), atol=1e-12)
+
+
+def test_kmeans_fixed_point_properties():
+    """At convergence (Lloyd's fixed point) every patch is assigned to its
+    nearest mean and every nonempty mean is the average of its members;
+    checked by brute force on random small patches."""
+    g = np.random.default_rng(11)
+    A = g.standard_normal((40, 3, 3)) + 3.0 * np.eye(3)
+    init = g.choice(40, 5, replace=False)
+    km = O.kmeans_l1(A, init, max_iter=200)
+    assert km["sweeps"] < 200
+    phi, B = km["phi"], km["means"]
+    for i in range(40):
+        d = [np.abs(A[i] - B[j]).sum() for j in range(5)]
+        assert d[phi[i]] == min(d)
+    for j in range(5):
+        mem = np.flatnonzero(phi == j)
+        if mem.size:
+            assert np.allclose(B[j], A[mem].mean(axis=0), rtol=1e-14, atol=1e-14)
+
+
+def test_kmeans_every_patch_its_own_mean():
+    """m_p = n_p distinct patches as seeds: every patch is nearest to itself
+    (distance 0), phi = identity after the first sweep."""
+    g = np.random.default_rng(2)
+    A = g.standard_normal((9, 4, 4)) + 4.0 * np.eye(4)
+    km = O.kmeans_l1(A, np.arange(9))
+    assert np.array_equal(km["phi"], np.arange(9)) and km["sweeps"] == 2
