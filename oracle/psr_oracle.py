@@ -581,6 +581,13 @@ def kmeans_l1(A, init, max_iter=100, near_tie_rel=1e-9):
         best = D[np.arange(npch), new]
         close = (D <= best[:, None] * (1.0 + near_tie_rel)) & (D > 0.0)
         close[np.arange(npch), new] = False
+        # a mean bitwise equal to the nearest one gives a bitwise equal
+        # distance in any summation order: that tie resolves to the lowest j
+        # everywhere and is not reported
+        for i in np.flatnonzero(close.any(axis=1)):
+            for j in np.flatnonzero(close[i]):
+                if np.array_equal(B[j], B[new[i]]):
+                    close[i, j] = False
         near = [int(i) for i in np.flatnonzero(close.any(axis=1))]
         changed = bool(np.any(new != phi))
         phi = new
