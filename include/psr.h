@@ -133,6 +133,21 @@ int psr_setup_seeded(const psr_csr* A, const psr_patches* patches, const psr_opt
                      const double* seed_A, int32_t m0, const int32_t* hints, void* stream,
                      psr_ctx** out);
 
+/* Setup whose database comes from Alg. 2 (section 3.2) in its entrywise
+ * variant instead of Alg. 1: m_p entries fixed beforehand, distance
+ * ||A_i - B_j||_l1 (entrywise), B_j the entrywise mean of its cluster
+ * (Eq. 6), the stored inverse that of the mean.  init: device, m_p distinct
+ * patch indices (drawn at random by the caller, as Alg. 2's randperm) whose
+ * patches are the initial means.  Every sweep assigns each patch to its
+ * nearest mean (ties to the lowest index); the means are recomputed (members
+ * summed in increasing patch index; an emptied cluster keeps its mean) until
+ * a sweep changes nothing or after max_iter sweeps.  opts->tol is ignored;
+ * psr_get_stats reports the sweeps in `rounds`.  Needs patches of one size
+ * p <= 128.  Errors: INVALID_ARG (arguments, seeds not distinct or out of
+ * range), SINGULAR_PATCH (a mean failed the pivot test), OOM, CUDA. */
+int psr_setup_kmeans(const psr_csr* A, const psr_patches* patches, const psr_opts* opts, int32_t m_p,
+                     const int32_t* init, int32_t max_iter, void* stream, psr_ctx** out);
+
 /* z = M~^{-1} r (Eq. 3 with the context's weighting).  r, z: device, length n,
  * must not overlap.  Stream-ordered, no host synchronisation, no allocation. */
 int psr_apply(psr_ctx* ctx, const double* r, double* z, void* stream);

@@ -31,7 +31,7 @@ EXPORTS = ["psr_default_opts", "psr_setup", "psr_apply", "psr_solve", "psr_get_h
            "psr_batched_inverse", "psr_criterion", "psr_spectral_norm", "psr_kernel_launches",
            "psr_setup_seeded", "psr_features", "psr_mlp_create", "psr_mlp_num_params", "psr_mlp_set_params",
            "psr_mlp_get_params", "psr_mlp_loss_grad", "psr_mlp_train_step", "psr_mlp_predict", "psr_mlp_destroy",
-           "psr_criterion_noalloc", "psr_set_kernel_timing", "psr_get_kernel_timing"]
+           "psr_criterion_noalloc", "psr_set_kernel_timing", "psr_get_kernel_timing", "psr_setup_kmeans"]
 
 KT_CLASSES = ("sweep", "spmv", "mdot", "maxpy", "vec")   # PSR_KT_* in order
 
@@ -112,6 +112,8 @@ def load(path: str = LIB_PATH):
     lib.psr_setup_seeded.argtypes = [C.POINTER(psr_csr), C.POINTER(psr_patches), C.POINTER(psr_opts), vp, i32, vp,
                                      vp, C.POINTER(vp)]
     lib.psr_features.argtypes = [vp, i32, i32, vp, vp, vp]
+    lib.psr_setup_kmeans.argtypes = [C.POINTER(psr_csr), C.POINTER(psr_patches), C.POINTER(psr_opts), i32, vp, i32,
+                                     vp, C.POINTER(vp)]
     lib.psr_mlp_create.argtypes = [i32, i32, i32, C.POINTER(vp)]
     lib.psr_mlp_num_params.argtypes = [vp]
     lib.psr_mlp_set_params.argtypes = [vp, vp, vp]
@@ -290,6 +292,23 @@ def psr_setup_seeded(rowptr, colidx, vals, dofs, uniform_size, seed_A, hints=Non
     o = opts if opts is not None else make_opts()
     h = C.c_void_p()
     rc = lib.psr_setup_seeded(C.byref(A), C.byref(P), C.byref(o), _ptr(seed_A), seed_A.shape[0], _ptr(hints),
+                              _stream(stream), C.byref(h))
+    _check(rc, None)
+    return Context(h, A.n, P.n_patches, o)
+
+
+def psr_setup_kmeans(rowptr, colidx, vals, dofs, uniform_size, init, max_iter=100, opts: psr_opts | None = None,
+                     stream=None) -> "Context":
+    """Database by Alg. 2, entrywise k-means, seeded with the patches init
+    (device int32, m_p distinct patch indices)."""
+    import torch
+    lib = load()
+    A = _csr(rowptr, colidx, vals)
+    P = _patches(dofs, None, uniform_size)
+    _need(init, torch.int32, "init")
+    o = opts if opts is not None else make_opts()
+    h = C.c_void_p()
+    rc = lib.psr_setup_kmeans(C.byref(A), C.byref(P), C.byref(o), init.numel(), _ptr(init), max_iter,
                               _stream(stream), C.byref(h))
     _check(rc, None)
     return Context(h, A.n, P.n_patches, o)

@@ -83,8 +83,22 @@ static int check_status(psr_ctx* ctx, cudaStream_t s) {
     return PSR_OK;
 }
 
+// Database construction of the setup: Alg. 1 (default; seeded and hinted
+// when seed_A / hints are given) or entrywise k-means (km_m > 0).
+struct AssignMode {
+    const double* seed_A = nullptr;
+    int m0 = 0;
+    const int32_t* hints = nullptr;
+    int km_m = 0;
+    const std::vector<int32_t>* km_init = nullptr;
+    int km_iter = 0;
+};
+
 static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o, cudaStream_t s, psr_ctx** out,
-                      const double* seed_A, int m0, const int32_t* hints) {
+                      const AssignMode& mode) {
+    const double* seed_A = mode.seed_A;
+    const int m0 = mode.m0;
+    const int32_t* hints = mode.hints;
     auto t_all = std::chrono::steady_clock::now();
     psr_ctx* ctx = new psr_ctx();
     *out = nullptr;
@@ -201,7 +215,10 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
         CK(cudaMalloc(&ctx->phi, sizeof(int32_t) * (size_t)np));
         CK(cudaMalloc(&ctx->rep_ids, sizeof(int32_t) * (size_t)np));
         t0 = std::chrono::steady_clock::now();
-        if (op.tol == 0.0 && m0 == 0) {
+        if (mode.km_m > 0) {
+            rc = run_kmeans(ctx, s, mode.km_m, *mode.km_init, mode.km_iter);
+            if (rc != PSR_OK) goto fail;
+        } else if (op.tol == 0.0 && m0 == 0) {
             // strict "< 0" never holds: every patch is its own entry (Eq. 1)
             int32_t* sing = nullptr;
             int32_t* first = nullptr;
@@ -321,7 +338,7 @@ int psr_setup(const psr_csr* A, const psr_patches* patches, const psr_opts* opts
         return PSR_ERR_CUDA;
     }
     try {
-        return setup_impl(A, patches, opts, (cudaStream_t)stream, out, nullptr, 0, nullptr);
+        return setup_impl(A, patches, opts, (cudaStream_t)stream, out, AssignMode{});
     } catch (const std::bad_alloc&) {
         set_error(nullptr, "host allocation failed");
         return PSR_ERR_OOM;
@@ -351,9 +368,57 @@ int psr_setup_seeded(const psr_csr* A, const psr_patches* patches, const psr_opt
     if (opts) o = *opts; else psr_default_opts(&o);
     if (!(o.tol > 0.0)) { set_error(nullptr, "a seeded setup needs tol > 0"); return PSR_ERR_INVALID_ARG; }
     try {
-        return setup_impl(A, patches, &o, (cudaStream_t)stream, out, seed_A, m0, hints);
+        AssignMode mode;
+        mode.seed_A = seed_A;
+        mode.m0 = m0;
+        mode.hints = hints;
+        return setup_impl(A, patches, &o, (cudaStream_t)stream, out, mode);
     } catch (...) {
         set_error(nullptr, "unexpected host exception in psr_setup_seeded");
+        return PSR_ERR_CUDA;
+    }
+}
+
+int psr_setup_kmeans(const psr_csr* A, const psr_patches* patches, const psr_opts* opts, int32_t m_p,
+                     const int32_t* init, int32_t max_iter, void* stream, psr_ctx** out) {
+    if (!out) { set_error(nullptr, "out is NULL"); return PSR_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (!A || !patches || !A->rowptr || !A->vals || !A->colidx || A->n <= 0 || patches->n_patches <= 0 ||
+        !patches->dofs || patches->uniform_size <= 0 || patches->uniform_size > 128 || m_p < 1 ||
+        m_p > patches->n_patches || !init || max_iter < 1) {
+        set_error(nullptr, "invalid k-means setup arguments (uniform patches of at most 128 DOFs, 1 <= m_p <= n_patches, max_iter >= 1)");
+        return PSR_ERR_INVALID_ARG;
+    }
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) {
+        cudaGetLastError();
+        set_error(nullptr, "no CUDA device: the library has no CPU fallback");
+        return PSR_ERR_CUDA;
+    }
+    try {
+        std::vector<int32_t> h_init((size_t)m_p);
+        cudaError_t e = cudaMemcpy(h_init.data(), init, sizeof(int32_t) * (size_t)m_p, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "k-means seeds");
+        std::vector<char> seen((size_t)patches->n_patches, 0);
+        for (int32_t v : h_init) {
+            if (v < 0 || v >= patches->n_patches || seen[(size_t)v]) {
+                set_error(nullptr, "k-means seeds must be distinct patch indices in [0, n_patches)");
+                return PSR_ERR_INVALID_ARG;
+            }
+            seen[(size_t)v] = 1;
+        }
+        psr_opts o;
+        if (opts) o = *opts; else psr_default_opts(&o);
+        AssignMode mode;
+        mode.km_m = m_p;
+        mode.km_init = &h_init;
+        mode.km_iter = max_iter;
+        return setup_impl(A, patches, &o, (cudaStream_t)stream, out, mode);
+    } catch (const std::bad_alloc&) {
+        set_error(nullptr, "host allocation failed");
+        return PSR_ERR_OOM;
+    } catch (...) {
+        set_error(nullptr, "unexpected host exception in psr_setup_kmeans");
         return PSR_ERR_CUDA;
     }
 }

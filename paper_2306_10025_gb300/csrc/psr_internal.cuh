@@ -222,6 +222,9 @@ int launch_sweep_tc(const int32_t* tiles, int ntiles, int p, const __nv_bfloat16
                     const double* r, const double* wg, const double* wsc, double* z, const int32_t* stop,
                     int32_t* err, cudaStream_t s);
 
+// kmeans.cu
+int run_kmeans(psr_ctx* ctx, cudaStream_t s, int m, const std::vector<int32_t>& init, int max_iter);
+
 // krylov.cu
 int krylov_alloc(psr_ctx* ctx);
 int krylov_solve(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_solve_info* info);

@@ -1,0 +1,102 @@
+"""Alg. 2 (entrywise k-means, section 3.2) on the GPU vs the CPU oracle:
+assignment and sweep count bit-exact, means' inverses within rounding, the
+preconditioner built from them equal to the oracle's Eq. (3) apply."""
+import numpy as np
+import pytest
+
+import problems as P
+from oracle import psr_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2306_10025_gb300 as L
+    return L
+
+
+def dev(a, dt):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+
+
+def kmeans_ctx(lib, pr, init, max_iter=100, **kw):
+    rp, ci, va = dev(pr.rowptr, torch.int32), dev(pr.colidx, torch.int32), dev(pr.vals, torch.float64)
+    return lib.psr_setup_kmeans(rp, ci, va, dev(pr.patch_dofs, torch.int32), pr.uniform_size,
+                                dev(np.asarray(init), torch.int32), max_iter=max_iter, opts=lib.make_opts(**kw))
+
+
+def seeds(n_p, m, seed):
+    return np.random.default_rng(seed).choice(n_p, m, replace=False).astype(np.int32)
+
+
+@pytest.mark.parametrize("case", ["c1_classes", "poisson_random", "stokes8", "diff3d", "nedelec"])
+def test_kmeans_assignment_bit_exact(lib, case):
+    if case == "c1_classes":
+        pr = P.poisson2d_q2(16)
+        init = np.array([0, 1, 15, 16, 17, 31, 240, 241, 255], dtype=np.int32)
+    elif case == "poisson_random":
+        pr = P.poisson2d_q2(12)
+        init = seeds(pr.n_patches, 12, 1)
+    elif case == "stokes8":
+        pr = P.stokes2d_q2q1(8)
+        init = seeds(pr.n_patches, 10, 2)
+    elif case == "diff3d":
+        pr = P.diffusion3d_q2(4, seed=3)
+        init = seeds(pr.n_patches, 8, 3)
+    else:
+        pr = P.nedelec3d(4, seed=5)
+        init = seeds(pr.n_patches, 16, 4)
+    A = O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d())
+    ref = O.kmeans_l1(A, init)
+    assert ref["near_ties"] == [], "oracle reports a near tie; pick other seeds"
+    ctx = kmeans_ctx(lib, pr, init, weighting=pr.weighting, krylov=pr.krylov)
+    phi, reps, m = ctx.assignment()
+    assert m == len(init)
+    assert np.array_equal(phi.cpu().numpy(), ref["phi"]), case
+    assert ctx.stats()["rounds"] == ref["sweeps"], case
+    # the preconditioner from the k-means database equals the oracle's Eq. (3)
+    g = np.random.default_rng(7)
+    r = g.standard_normal(pr.n)
+    z = torch.empty(pr.n, dtype=torch.float64, device="cuda")
+    ctx.apply(dev(r, torch.float64), z)
+    W = O.weights(O.multiplicity(pr.n, pr.patch_dofs))
+    zo = O.apply(r, pr.dofs2d(), ref["Binv"], ref["phi"], W, pr.weighting)
+    assert np.abs(z.cpu().numpy() - zo).max() <= 1e-11 * np.abs(zo).max()
+    ctx.destroy()
+
+
+def test_kmeans_max_iter_and_errors(lib):
+    pr = P.stokes2d_q2q1(8)
+    A = O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d())
+    init = seeds(pr.n_patches, 10, 2)
+    ref = O.kmeans_l1(A, init, max_iter=2)
+    ctx = kmeans_ctx(lib, pr, init, max_iter=2, weighting="left", krylov="fgmres")
+    assert ctx.stats()["rounds"] == 2 == ref["sweeps"]
+    assert np.array_equal(ctx.assignment()[0].cpu().numpy(), ref["phi"])
+    ctx.destroy()
+    with pytest.raises(lib.PsrError):                      # repeated seed
+        kmeans_ctx(lib, pr, np.array([3, 3], dtype=np.int32))
+    with pytest.raises(lib.PsrError):                      # out of range
+        kmeans_ctx(lib, pr, np.array([0, pr.n_patches], dtype=np.int32))
+
+
+def test_kmeans_solve_converges(lib):
+    """PCG with the k-means database (C1, 9 class seeds = the Alg. 1 classes)
+    reaches 1e-8 with the iteration count of the Alg. 1 database."""
+    pr = P.poisson2d_q2(16)
+    b = dev(pr.rhs(0), torch.float64)
+    init = np.array([0, 1, 15, 16, 17, 31, 240, 241, 255], dtype=np.int32)
+    ctx = kmeans_ctx(lib, pr, init, weighting="sym", krylov="cg")
+    x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
+    info = ctx.solve(b, x)
+    rp, ci, va = dev(pr.rowptr, torch.int32), dev(pr.colidx, torch.int32), dev(pr.vals, torch.float64)
+    c1 = lib.psr_setup(rp, ci, va, dev(pr.patch_dofs, torch.int32), uniform_size=pr.uniform_size,
+                       opts=lib.make_opts(tol=1e-12, weighting="sym", krylov="cg"))
+    x1 = torch.zeros_like(x)
+    info1 = c1.solve(b, x1)
+    assert info["converged"] and abs(info["iterations"] - info1["iterations"]) <= 1
