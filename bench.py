@@ -69,10 +69,6 @@ TRAFFIC = {
     # ncu --set full, one launch inside the FGMRES cycle (k_spmv_sell):
     # 89.11 MB read + 2.47 MB written
     ("stokes2d", "spmv"): 91.6e6,
-    # ncu --set full of the fused Arnoldi step at j = 20 (26.27 MB: one DRAM
-    # read of the basis, later passes from L2) scaled to the mean basis size
-    # of a step, (j+2) averaged over j = 0..29
-    ("stokes2d", "mdot"): 26.27e6 * 16.5 / 22.0,
 }
 
 

@@ -67,6 +67,13 @@ extern "C" {
                                       tensor cores (AUTO uses them only when their
                                       128-patch tiles are at least 1/4 full) */
 
+#define PSR_ORTHO_AUTO   0        /* FGMRES Gram-Schmidt: one fused cooperative launch per
+                                      step with dots and updates on FP32 pairs (about 48
+                                      significant bits; FP64 when ||w|| is outside
+                                      [2^-80, 2^60]); the FP64 kernels without cooperative launch */
+#define PSR_ORTHO_FP64   1         /* the fused launch in FP64 arithmetic                  */
+#define PSR_ORTHO_SPLIT  2         /* one launch per pass, FP64 arithmetic                 */
+
 typedef struct psr_ctx psr_ctx;    /* opaque, library-owned */
 
 /* Assembled matrix A (section 2: A x = b), CSR, device pointers. */
@@ -101,10 +108,12 @@ typedef struct {
     int32_t autotune;     /* 1: time candidate sweep tile shapes at setup         */
     int32_t symmetrize;   /* 1: store (B^-1 + B^-T)/2 before rounding to FP32/BF16 */
     int32_t use_mlp;      /* 1: verify MLP-predicted representatives first (needs psr_mlp_attach) */
+    int32_t ortho;        /* PSR_ORTHO_* (FGMRES only)                            */
 } psr_opts;
 
 /* Fill `o` with defaults: tol 0, FP64, SYM, CG, restart 30, rtol 1e-8,
- * maxit 10000, graphs on, AUTO sweep, autotune on, symmetrize on, no MLP. */
+ * maxit 10000, graphs on, AUTO sweep, autotune on, symmetrize on, no MLP,
+ * AUTO orthogonalisation. */
 void psr_default_opts(psr_opts* o);
 
 /* ---- whole method ------------------------------------------------------- */

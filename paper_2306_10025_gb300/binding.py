@@ -25,6 +25,7 @@ PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
 WEIGHT = {"left": 0, "sym": 1}
 KRYLOV = {"cg": 0, "fgmres": 1}
 SWEEP = {"auto": 0, "grouped": 1, "pergroup": 2, "tensor": 3}
+ORTHO = {"auto": 0, "fp64": 1, "split": 2}
 
 EXPORTS = ["psr_default_opts", "psr_setup", "psr_apply", "psr_solve", "psr_get_history",
            "psr_get_assignment", "psr_get_stats", "psr_last_error", "psr_destroy", "psr_extract",
@@ -56,7 +57,8 @@ class psr_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("store_prec", C.c_int32), ("weighting", C.c_int32),
                 ("krylov", C.c_int32), ("restart", C.c_int32), ("rtol", C.c_double),
                 ("maxit", C.c_int32), ("use_graph", C.c_int32), ("sweep_kernel", C.c_int32),
-                ("autotune", C.c_int32), ("symmetrize", C.c_int32), ("use_mlp", C.c_int32)]
+                ("autotune", C.c_int32), ("symmetrize", C.c_int32), ("use_mlp", C.c_int32),
+                ("ortho", C.c_int32)]
 
 
 class psr_solve_info(C.Structure):
@@ -158,7 +160,7 @@ def _need(t, dtype, name):
 
 def make_opts(tol=0.0, store_prec="fp64", weighting="sym", krylov="cg", restart=30, rtol=1e-8,
               maxit=10000, use_graph=True, sweep_kernel="auto", autotune=True, symmetrize=True,
-              use_mlp=False) -> psr_opts:
+              use_mlp=False, ortho="auto") -> psr_opts:
     o = psr_opts()
     load().psr_default_opts(C.byref(o))
     o.tol = tol
@@ -173,6 +175,7 @@ def make_opts(tol=0.0, store_prec="fp64", weighting="sym", krylov="cg", restart=
     o.autotune = int(autotune)
     o.symmetrize = int(symmetrize)
     o.use_mlp = int(use_mlp)
+    o.ortho = ORTHO[ortho]
     return o
 
 

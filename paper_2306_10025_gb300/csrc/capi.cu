@@ -106,7 +106,8 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
     psr_opts& op = ctx->opts;
     if (op.restart < 1 || op.restart > 32 || op.maxit < 1 || !(op.rtol > 0.0) || op.tol < 0.0 ||
         op.store_prec < 0 || op.store_prec > 2 || op.weighting < 0 || op.weighting > 1 || op.krylov < 0 || op.krylov > 1 ||
-        op.sweep_kernel < PSR_SWEEP_AUTO || op.sweep_kernel > PSR_SWEEP_TENSOR) {
+        op.sweep_kernel < PSR_SWEEP_AUTO || op.sweep_kernel > PSR_SWEEP_TENSOR || op.ortho < PSR_ORTHO_AUTO ||
+        op.ortho > PSR_ORTHO_SPLIT) {
         set_error(ctx, "invalid option value");
         destroy_ctx(ctx);
         return PSR_ERR_INVALID_ARG;
@@ -321,6 +322,7 @@ void psr_default_opts(psr_opts* o) {
     o->autotune = 1;
     o->symmetrize = 1;
     o->use_mlp = 0;
+    o->ortho = PSR_ORTHO_AUTO;
 }
 
 int psr_setup(const psr_csr* A, const psr_patches* patches, const psr_opts* opts, void* stream, psr_ctx** out) {

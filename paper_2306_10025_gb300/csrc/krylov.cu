@@ -202,7 +202,8 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ rowptr
 // column.  One thread per row: the loads of a warp are contiguous, the
 // entries of a row are summed in CSR order by one thread (no cross-lane
 // reduction, no FP64 instruction spent on another row's tail: all rows of a
-// warp share the slice width).
+// warp share the slice width).  Four independent accumulation chains per row
+// were measured slower on the 2D Stokes workload (27.4 against 24.9 us).
 __global__ void k_sell_width(const int32_t* __restrict__ rowptr, int n, int nslices, int32_t* __restrict__ width) {
     const int lane = threadIdx.x & 31;
     const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -384,12 +385,74 @@ __global__ void k_cg_p(double* __restrict__ p, const double* __restrict__ z, int
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = fma(beta, p[i], z[i]);
 }
 
+// ---------------------------------------------------------------- pair arithmetic
+// A value carried as an unevaluated pair of FP32 numbers hi + lo (about 48
+// significant bits).  On this GPU FP64 instructions, conversions between FP64
+// and FP32 included, issue at 2 per clock per SM and FP32 ones at 128, so the
+// fused Arnoldi step does its dot products and updates on pairs.  The error-free
+// transformations are Knuth's TwoSum, Dekker's FastTwoSum and the FMA-based
+// TwoProduct; the _rn intrinsics keep the compiler from contracting them.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+// exact when |a| >= |b| or a == 0
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// (ah, al) += (xh + xl)(yh + yl), the xl*yl term dropped (below 2^-46 of the product)
+__device__ __forceinline__ void df_fma(float& ah, float& al, float xh, float xl, float yh, float yl) {
+    const float p = __fmul_rn(xh, yh);
+    const float pe = __fmaf_rn(xh, yh, -p);
+    const float c = __fmaf_rn(xh, yl, __fmul_rn(xl, yh));
+    float t, e;
+    two_sum(ah, p, t, e);
+    ah = t;
+    al = __fadd_rn(al, __fadd_rn(e, __fadd_rn(pe, c)));
+}
+
+__device__ __forceinline__ void df_add(float& ah, float& al, float bh, float bl) {
+    float t, e;
+    two_sum(ah, bh, t, e);
+    e = __fadd_rn(e, __fadd_rn(al, bl));
+    fast_two_sum(t, e, ah, al);
+}
+
+// x = hi + lo: hi = x truncated to 24 significant bits (built from the bit
+// fields, no conversion instruction), lo = x - hi rounded to FP32 (relative
+// error 2^-47 of x).  Outside the FP32 normal range hi = 0 and lo = fl32(x).
+__device__ __forceinline__ float2 split_f64(double x) {
+    const long long b = __double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    const bool normal = ex > 896 && ex < 1151;
+    const double t = normal ? __longlong_as_double(b & (long long)0xFFFFFFFFE0000000ull) : 0.0;
+    const unsigned int hb = ((unsigned int)((unsigned long long)b >> 32) & 0x80000000u) |
+                            ((unsigned int)(ex - 896) << 23) | (unsigned int)((b >> 29) & 0x7fffff);
+    return make_float2(normal ? __uint_as_float(hb) : 0.f, __double2float_rn(x - t));
+}
+
 // ---------------------------------------------------------------- FGMRES
 // cycle start: V_0 = r / beta, g = (beta, 0, ...), K = 0
-__global__ void k_fg_start(const double* __restrict__ r, double* __restrict__ V0, int n, KDims kd) {
+// (with Vs0: the pair copy of V_0 for the fused Arnoldi step, and V_0 the
+// exact FP64 value of the pair)
+__global__ void k_fg_start(const double* __restrict__ r, double* __restrict__ V0, float2* __restrict__ Vs0, int n,
+                           KDims kd) {
     if (kd.ictl[I_STOP]) return;
     const double beta = kd.scal[S_RN];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) V0[i] = r[i] / beta;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double v = r[i] / beta;
+        if (Vs0) {
+            const float2 q = split_f64(v);
+            Vs0[i] = q;
+            V0[i] = (double)q.x + (double)q.y;
+        } else {
+            V0[i] = v;
+        }
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const int m = kd.m;
         double* g = Gv(kd.scal, m);
@@ -405,6 +468,31 @@ __global__ void k_fg_start(const double* __restrict__ r, double* __restrict__ V0
 // run 256-thread blocks on a single-wave grid (kgrid) and reduce per vector
 // deterministically: warp -> block partial -> last block in fixed order.
 constexpr int KT = 256;                 // threads per block of the CGS2 kernels
+
+// FP64 operations that depend on each other take about 64 clocks each on this
+// GPU (FP32: about 5), so the sums on the critical path of a step are trees in
+// a fixed order (the same in every block), never running chains.
+static_assert(KT / 32 == 8, "tree8 sums one value per warp of a block");
+__device__ __forceinline__ double tree8(const double* x) {
+    return ((x[0] + x[1]) + (x[2] + x[3])) + ((x[4] + x[5]) + (x[6] + x[7]));
+}
+
+// Sum over a KT-thread block, the total in every thread (fixed order).
+// sh: at least KT / 32 doubles of shared memory.
+__device__ __forceinline__ double block_sum_kt(double v, double* sh) {
+    v = warp_sum(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    return tree8(sh);
+}
+
+// Total of G block partials part[0..G) in every thread.
+__device__ __forceinline__ double norm_total(const double* __restrict__ part, int G, double* sh) {
+    double u = 0.0;
+    for (int k = threadIdx.x; k < G; k += KT) u += part[k];
+    return block_sum_kt(u, sh);
+}
 
 // acc[i] of every thread -> part[i * gridDim.x + blockIdx.x] (i < nv): the
 // warp sums NV accumulators by recursive halving (at step h a lane keeps the
@@ -429,12 +517,7 @@ __device__ __forceinline__ void block_partials(double (&acc)[NV], int nv, double
     for (int o = NV; o < 32; o <<= 1) acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
     if (lane < NV) sh[lane][wid] = acc[0];
     __syncthreads();
-    if (threadIdx.x < nv) {
-        double t = 0.0;
-#pragma unroll
-        for (int w = 0; w < KT / 32; ++w) t += sh[threadIdx.x][w];
-        part[threadIdx.x * gridDim.x + blockIdx.x] = t;
-    }
+    if (threadIdx.x < nv) part[threadIdx.x * gridDim.x + blockIdx.x] = tree8(sh[threadIdx.x]);
 }
 
 // Last block: total of vector i = threadIdx.x / (KT / NV) over the G block
@@ -443,9 +526,38 @@ template <int NV>
 __device__ __forceinline__ double final_partials(const double* __restrict__ part, int nv, int G) {
     constexpr int T = KT / NV;           // threads per vector, <= 32
     const int i = threadIdx.x / T, q = threadIdx.x % T;
-    double v = (i < nv) ? sum_strided(part + (int64_t)i * G, q, G, T) : 0.0;
+    double v = 0.0;
+    if (i < nv) {
+        if (G <= KT) {
+            // every load of the thread in flight at once (G / T <= NV of them)
+            double x[NV];
+#pragma unroll
+            for (int u = 0; u < NV; ++u) x[u] = (q + u * T < G) ? part[(int64_t)i * G + q + u * T] : 0.0;
+#pragma unroll
+            for (int h = NV / 2; h >= 1; h >>= 1)     // pairwise tree
+#pragma unroll
+                for (int u = 0; u < h; ++u) x[u] = x[u] + x[u + h];
+            v = x[0];
+        } else {
+            v = sum_strided(part + (int64_t)i * G, q, G, T);
+        }
+    }
 #pragma unroll
     for (int o = T / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, T);
+    return v;
+}
+
+// The vector totals of final_partials and, valid in thread 0, the total of
+// the G norm partials stored after them (part[NV * G ...]); the norm
+// partials are requested before the vector partials so that both are in
+// flight together.
+template <int NV>
+__device__ __forceinline__ double final_partials_w2(const double* __restrict__ part, int nv, int G, double* shw,
+                                                    double& w2) {
+    double u = 0.0;
+    for (int k = threadIdx.x; k < G; k += KT) u += part[(int64_t)NV * G + k];
+    const double v = final_partials<NV>(part, nv, G);
+    w2 = block_sum_kt(u, shw);
     return v;
 }
 
@@ -483,6 +595,61 @@ __device__ void arnoldi_finish(KDims kd, int j, double wn2) {
     sc[S_RN] = res;
     if (res <= sc[S_RTOL] * sc[S_R0]) { ic[I_CONV] = 1; ic[I_STOP] = 1; }
     else if (it >= ic[I_MAXIT] || den == 0.0) ic[I_STOP] = 1;
+}
+
+// Arnoldi finish of step j in the fused step, by warp 0 of block 0 on shared
+// copies loaded at the start of the launch: col = H[0..j][j] before the
+// rotations, rot = the previous cosines (rot[0..j-1]) and sines
+// (rot[NV..NV+j-1]), sg = {g[j], r0, rtol}, si = {iteration count, cap};
+// hn = ||w||.  The previous rotations applied in order leave entry i as
+// cs_i d_i + sn_i c_{i+1} with d_0 = c_0 and d_i = cs_{i-1} c_i - sn_{i-1} d_{i-1},
+// a first-order linear recurrence: lanes compose the affine maps
+// d -> a d + b in an inclusive scan (5 dependent steps instead of j).
+__device__ void arnoldi_finish_warp(KDims kd, int j, double hn, const double* col, const double* rot, int NV,
+                                    const double* sg, const int* si) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    double* sc = kd.scal;
+    int32_t* ic = kd.ictl;
+    const int m = kd.m;
+    double* H = Hm(sc, m);
+    const double ci = lane <= j ? col[lane] : 0.0;
+    const bool mid = lane >= 1 && lane <= j;
+    double a = mid ? -rot[NV + lane - 1] : 0.0;
+    double b = mid ? rot[lane - 1] * ci : (lane == 0 ? ci : 0.0);
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const double ap = __shfl_up_sync(full, a, off);
+        const double bp = __shfl_up_sync(full, b, off);
+        if (lane >= off) {
+            b = fma(a, bp, b);
+            a = a * ap;
+        }
+    }
+    const double cnext = __shfl_down_sync(full, ci, 1);     // c_{i+1}
+    const double dj = __shfl_sync(full, b, j);
+    const double den = hypot(dj, hn);
+    const double cj = dj / den, sj = hn / den;
+    if (lane < j) H[lane * m + j] = rot[lane] * b + rot[NV + lane] * cnext;
+    if (lane == j) H[j * m + j] = den;
+    if (lane != 0) return;
+    H[(j + 1) * m + j] = 0.0;
+    CSv(sc, m)[j] = cj;
+    SNv(sc, m)[j] = sj;
+    sc[S_BETA] = hn;
+    double* g = Gv(sc, m);
+    const double gj = sg[0];
+    const double g1 = -sj * gj;
+    g[j + 1] = g1;
+    g[j] = cj * gj;
+    const int it = si[0] + 1;
+    ic[I_IT] = it;
+    ic[I_K] = j + 1;
+    const double res = fabs(g1);
+    kd.hist[it] = res / sg[1];
+    sc[S_RN] = res;
+    if (res <= sg[2] * sg[1]) { ic[I_CONV] = 1; ic[I_STOP] = 1; }
+    else if (it >= si[1] || den == 0.0) ic[I_STOP] = 1;
 }
 
 // h = V^T w and ||w||^2 (first pass): H[:, j] = h, h kept for the update.
@@ -713,6 +880,79 @@ __device__ __forceinline__ void update_pass(const double* __restrict__ V, double
     }
 }
 
+// Pair form of block_partials: the same recursive halving on (hi, lo)
+// accumulators, one conversion to FP64 per lane, then the warps in order.
+template <int NV>
+__device__ __forceinline__ void block_partials_df(float (&ah)[NV], float (&al)[NV], int nv, double* __restrict__ part,
+                                                  double (*sh)[KT / 32 + 1]) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int h = NV / 2; h >= 1; h >>= 1) {
+        const bool upper = (lane & h) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float send_h = upper ? ah[i] : ah[i + h];
+            const float send_l = upper ? al[i] : al[i + h];
+            const float keep_h = upper ? ah[i + h] : ah[i];
+            const float keep_l = upper ? al[i + h] : al[i];
+            const float rh = __shfl_xor_sync(0xffffffffu, send_h, h);
+            const float rl = __shfl_xor_sync(0xffffffffu, send_l, h);
+            ah[i] = keep_h;
+            al[i] = keep_l;
+            df_add(ah[i], al[i], rh, rl);
+        }
+    }
+#pragma unroll
+    for (int o = NV; o < 32; o <<= 1) {
+        const float rh = __shfl_xor_sync(0xffffffffu, ah[0], o);
+        const float rl = __shfl_xor_sync(0xffffffffu, al[0], o);
+        df_add(ah[0], al[0], rh, rl);
+    }
+    if (lane < NV) sh[lane][wid] = (double)ah[0] + (double)al[0];
+    __syncthreads();
+    if (threadIdx.x < nv) part[threadIdx.x * gridDim.x + blockIdx.x] = tree8(sh[threadIdx.x]);
+}
+
+// Pair update of the scaled vector w' (pair copy Ws, multiplied on load by
+// the power of two scf): w' <- scf w' - V hs with hs the pair coefficients in
+// shared memory; PROJ: also (ah, al)_i += V_i[e] w'[e] (second projection),
+// else accw += w'[e]^2 in FP64.
+template <int NV, bool PROJ>
+__device__ __forceinline__ void pair_update(const float2* __restrict__ Vs, float2* __restrict__ Ws, int n, int nv,
+                                            const float2* hs, float scf, float (&ah)[NV], float (&al)[NV],
+                                            double& accw) {
+    for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += gridDim.x * KT) {
+        // all loads first (rows past nv read as zero, their coefficients are
+        // zero), then the arithmetic without branches
+        float2 vv[NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) vv[c] = (c < nv) ? Vs[(int64_t)c * n + e] : make_float2(0.f, 0.f);
+        float2 q = Ws[e];
+        q.x *= scf;
+        q.y *= scf;
+        // V hs in four independent chains (c mod 4), joined at the end
+        float ch[4] = {0.f, 0.f, 0.f, 0.f}, cl[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < NV; ++c) df_fma(ch[c & 3], cl[c & 3], hs[c].x, hs[c].y, vv[c].x, vv[c].y);
+        df_add(ch[0], cl[0], ch[1], cl[1]);
+        df_add(ch[2], cl[2], ch[3], cl[3]);
+        df_add(ch[0], cl[0], ch[2], cl[2]);
+        const float sh_ = ch[0], sl_ = cl[0];
+        float t, d, nh, nl;
+        two_sum(q.x, -sh_, t, d);
+        d = __fadd_rn(d, __fsub_rn(q.y, sl_));
+        fast_two_sum(t, d, nh, nl);
+        Ws[e] = make_float2(nh, nl);
+        if (PROJ) {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) df_fma(ah[i], al[i], vv[i].x, vv[i].y, nh, nl);
+        } else {
+            const double wd = (double)nh + (double)nl;
+            accw = fma(wd, wd, accw);
+        }
+    }
+}
+
 // The whole orthogonalisation of step j in one cooperative launch: w = V_{j+1}
 // (on entry A z_j) is projected (h = V^T w, ||w||^2), updated, projected and
 // updated again when the Kahan-Parlett test asks for it, normalised, and the
@@ -720,94 +960,221 @@ __device__ __forceinline__ void update_pass(const double* __restrict__ V, double
 // block sums the block partials of a pass itself (same order everywhere, so
 // all blocks hold bitwise the same h and norms), and each pass has its own
 // partial region.
+//
+// Arithmetic: the basis is read from its pair copy Vs (Vs_i = V_i exactly,
+// V_i being written as the FP64 value of its pair); w is split into a pair
+// once, dots and updates run on pairs, ||w||^2 and the partial sums in FP64.
+// After the first pass w is scaled by the power of two 2^k that brings ||w||
+// near 1 (exact), so cancellation in the updates stays far from the FP32
+// range limits; the coefficients are scaled alike and unscaled exactly.  When
+// ||w||^2 lies outside [2^-160, 2^120], or with fp64 set, the step is computed
+// in FP64 instead (the same passes on V), so the pair path never meets
+// overflow or underflow of the incoming vector.
 template <int NV>
-__global__ void __launch_bounds__(KT) k_arnoldi(const double* __restrict__ V, double* __restrict__ w, int n, int j,
-                                               KDims kd, double* __restrict__ part, unsigned int* bar) {
+__global__ void __launch_bounds__(KT) k_arnoldi(const double* __restrict__ V, double* __restrict__ w,
+                                               float2* __restrict__ Vs, int n, int j, KDims kd,
+                                               double* __restrict__ part, unsigned int* bar, int fp64) {
     __shared__ double sh[NV][KT / 32 + 1];
     __shared__ double sh_h[NV];
+    __shared__ float2 sh_hs[NV];
     __shared__ double shw[32];
     __shared__ double s_w2;
+    __shared__ int s_reorth;
+    __shared__ double s_col[NV + 1];                  // block 0: column j of H
+    __shared__ double s_rot[2 * NV];                  // block 0: previous rotations
+    __shared__ double s_g[3];
+    __shared__ int s_it[2];
     if (kd.ictl[I_STOP]) return;                      // same value in every block
     const int nv = j + 1;
     const int m = kd.m;
     const int G = gridDim.x;
     const int T = KT / NV;
+    if (blockIdx.x == 0) {                            // used by the finish at the end
+        if (threadIdx.x < j) {
+            s_rot[threadIdx.x] = CSv(kd.scal, m)[threadIdx.x];
+            s_rot[NV + threadIdx.x] = SNv(kd.scal, m)[threadIdx.x];
+        }
+        if (threadIdx.x == 0) {
+            s_g[0] = Gv(kd.scal, m)[j];
+            s_g[1] = kd.scal[S_R0];
+            s_g[2] = kd.scal[S_RTOL];
+            s_it[0] = kd.ictl[I_IT];
+            s_it[1] = kd.ictl[I_MAXIT];
+        }
+    }
     double* P1 = part;
     double* P2 = part + (int64_t)(NV + 1) * G;
     double* P3 = part + (int64_t)2 * (NV + 1) * G;
-    double acc[NV];
+    double* P4 = part + (int64_t)3 * (NV + 1) * G;
+    float2* Ws = Vs + (int64_t)nv * n;                // pair copy of w (row j+1)
+    double hv = 0.0;
+    bool pairs = false;
+    // pass 1 on pairs: h = V^T w, ||w||^2 in FP64, Ws = split(w)
+    if (!fp64) {
+        float ah[NV], al[NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
-    double accw = 0.0;
-    // pass 1: h = V^T w and ||w||^2
-    for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += G * KT) {
-        const double we = w[e];
-        accw = fma(we, we, accw);
+        for (int i = 0; i < NV; ++i) ah[i] = al[i] = 0.f;
+        double accw = 0.0;
+        for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += G * KT) {
+            const double we = w[e];
+            float2 vv[NV];
 #pragma unroll
-        for (int i = 0; i < NV; ++i)
-            if (i < nv) acc[i] = fma(V[(int64_t)i * n + e], we, acc[i]);
+            for (int i = 0; i < NV; ++i) vv[i] = (i < nv) ? Vs[(int64_t)i * n + e] : make_float2(0.f, 0.f);
+            accw = fma(we, we, accw);
+            const float2 q = split_f64(we);
+            Ws[e] = q;
+#pragma unroll
+            for (int i = 0; i < NV; ++i) df_fma(ah[i], al[i], vv[i].x, vv[i].y, q.x, q.y);
+        }
+        block_partials_df<NV>(ah, al, nv, P1, sh);
+        const double bs = block_sum_kt(accw, shw);
+        if (threadIdx.x == 0) P1[(int64_t)NV * G + blockIdx.x] = bs;
+        grid_barrier(bar, kd.ictl);
+        double t;
+        hv = final_partials_w2<NV>(P1, nv, G, shw, t);
+        if (threadIdx.x == 0) s_w2 = t;
+        __syncthreads();
+        pairs = s_w2 >= 0x1p-160 && s_w2 <= 0x1p120;  // same in every block
     }
-    block_partials<NV>(acc, nv, P1, sh);
-    double bs = block_sum(accw, shw);
-    if (threadIdx.x == 0) P1[(int64_t)NV * G + blockIdx.x] = bs;
-    grid_barrier(bar, kd.ictl);
-    {
-        const double v = final_partials<NV>(P1, nv, G);
-        if (threadIdx.x / T < nv && threadIdx.x % T == 0) sh_h[threadIdx.x / T] = v;
-        const double t = sum_partials(P1 + (int64_t)NV * G, G);
+    if (!pairs) {
+        // pass 1 in FP64
+        double acc[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+        double accw = 0.0;
+        for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += G * KT) {
+            const double we = w[e];
+            accw = fma(we, we, accw);
+#pragma unroll
+            for (int i = 0; i < NV; ++i)
+                if (i < nv) acc[i] = fma(V[(int64_t)i * n + e], we, acc[i]);
+        }
+        block_partials<NV>(acc, nv, P4, sh);
+        const double bs = block_sum_kt(accw, shw);
+        if (threadIdx.x == 0) P4[(int64_t)NV * G + blockIdx.x] = bs;
+        grid_barrier(bar, kd.ictl);
+        double t;
+        hv = final_partials_w2<NV>(P4, nv, G, shw, t);
         if (threadIdx.x == 0) s_w2 = t;
         __syncthreads();
     }
-    __shared__ int s_reorth;
-    if (threadIdx.x == 0) {
-        double h2 = 0.0;
-        for (int q = 0; q < nv; ++q) h2 = fma(sh_h[q], sh_h[q], h2);
-        s_reorth = (s_w2 - h2 < 0.5 * s_w2) ? 1 : 0;
+    // scale 2^k of the pair path: ||2^k w|| in [1, 2)
+    const int k = pairs ? -(ilogb(s_w2) >> 1) : 0;
+    if (threadIdx.x % T == 0) {                       // every slot i < NV (zero past nv)
+        sh_h[threadIdx.x / T] = hv;
+        sh_hs[threadIdx.x / T] = split_f64(ldexp(hv, k));
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {                           // ||h||^2 by warp 0 (sh_h is zero past nv)
+        const double hq = threadIdx.x < NV ? sh_h[threadIdx.x] : 0.0;
+        const double h2 = warp_sum(hq * hq);
+        if (threadIdx.x == 0) s_reorth = (s_w2 - h2 < 0.5 * s_w2) ? 1 : 0;
     }
     __syncthreads();
     const bool reorth = s_reorth != 0;
     if (blockIdx.x == 0) {
-        if (threadIdx.x < nv) Hm(kd.scal, m)[threadIdx.x * m + j] = sh_h[threadIdx.x];
+        if (threadIdx.x < nv) s_col[threadIdx.x] = sh_h[threadIdx.x];
         if (threadIdx.x == 0) kd.rflag[j] = reorth ? 1 : 0;
     }
-    // pass 2: w <- w - V h, with the second projection or ||w||^2
+    double hn_w;                                      // ||w|| for H[j+1][j]
+    if (pairs) {
+        const float scf = ldexpf(1.f, k);             // exact: k in [-60, 80]; w' = 2^k w on the first update
+        float ah[NV], al[NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
-    accw = 0.0;
-    double wn2;
-    if (reorth) {
-        update_pass<NV, true>(V, w, n, nv, sh_h, acc, accw);
-        block_partials<NV>(acc, nv, P2, sh);
-        grid_barrier(bar, kd.ictl);
-        const double v = final_partials<NV>(P2, nv, G);
-        __syncthreads();                              // sh_h of pass 2 fully read
-        if (threadIdx.x / T < nv && threadIdx.x % T == 0) sh_h[threadIdx.x / T] = v;
+        for (int i = 0; i < NV; ++i) ah[i] = al[i] = 0.f;
+        double accw = 0.0;
+        if (reorth) {
+            pair_update<NV, true>(Vs, Ws, n, nv, sh_hs, scf, ah, al, accw);
+            block_partials_df<NV>(ah, al, nv, P2, sh);
+            grid_barrier(bar, kd.ictl);
+            const double v2 = final_partials<NV>(P2, nv, G);      // 2^k h2
+            __syncthreads();                                      // sh_hs of pass 2 fully read
+            if (threadIdx.x % T == 0) {
+                sh_h[threadIdx.x / T] = ldexp(v2, -k);
+                sh_hs[threadIdx.x / T] = split_f64(v2);
+            }
+            __syncthreads();
+            if (blockIdx.x == 0 && threadIdx.x < nv) s_col[threadIdx.x] += sh_h[threadIdx.x];
+            pair_update<NV, false>(Vs, Ws, n, nv, sh_hs, 1.f, ah, al, accw);
+            const double bs = block_sum_kt(accw, shw);
+            if (threadIdx.x == 0) P3[(int64_t)NV * G + blockIdx.x] = bs;
+            grid_barrier(bar, kd.ictl);
+            const double t = norm_total(P3 + (int64_t)NV * G, G, shw);
+            if (threadIdx.x == 0) s_w2 = t;
+        } else {
+            pair_update<NV, false>(Vs, Ws, n, nv, sh_hs, scf, ah, al, accw);
+            const double bs = block_sum_kt(accw, shw);
+            if (threadIdx.x == 0) P2[(int64_t)NV * G + blockIdx.x] = bs;
+            grid_barrier(bar, kd.ictl);
+            const double t = norm_total(P2 + (int64_t)NV * G, G, shw);
+            if (threadIdx.x == 0) s_w2 = t;
+        }
         __syncthreads();
-        if (blockIdx.x == 0 && threadIdx.x < nv) Hm(kd.scal, m)[threadIdx.x * m + j] += sh_h[threadIdx.x];
-        // pass 3: w <- w - V h2 and ||w||^2
-        update_pass<NV, false>(V, w, n, nv, sh_h, acc, accw);
-        bs = block_sum(accw, shw);
-        if (threadIdx.x == 0) P3[(int64_t)NV * G + blockIdx.x] = bs;
-        grid_barrier(bar, kd.ictl);
-        const double t = sum_partials(P3 + (int64_t)NV * G, G);
-        if (threadIdx.x == 0) s_w2 = t;
+        const double ws2 = s_w2;                      // ||w'||^2
+        // normalise: v = w' / ||w'|| on pairs (inverse within FP32 range), else in FP64
+        const double hn = sqrt(ws2);
+        hn_w = ldexp(hn, -k);                         // exact: sqrt(2^2k x) = 2^k sqrt(x)
+        const double inv = hn != 0.0 ? 1.0 / hn : 1.0;
+        if (inv <= 0x1p100) {
+            const float2 is = split_f64(inv);
+            for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += G * KT) {
+                const float2 q = Ws[e];
+                const float p = __fmul_rn(q.x, is.x);
+                const float pe = __fmaf_rn(q.x, is.x, -p);
+                const float c = __fmaf_rn(q.x, is.y, __fmul_rn(q.y, is.x));
+                float vh, vl;
+                fast_two_sum(p, __fadd_rn(pe, c), vh, vl);
+                Ws[e] = make_float2(vh, vl);
+                w[e] = (double)vh + (double)vl;
+            }
+        } else {
+            for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += G * KT) {
+                const float2 q = Ws[e];
+                const float2 v = split_f64(((double)q.x + (double)q.y) * inv);
+                Ws[e] = v;
+                w[e] = (double)v.x + (double)v.y;
+            }
+        }
     } else {
-        update_pass<NV, false>(V, w, n, nv, sh_h, acc, accw);
-        bs = block_sum(accw, shw);
-        if (threadIdx.x == 0) P2[(int64_t)NV * G + blockIdx.x] = bs;
-        grid_barrier(bar, kd.ictl);
-        const double t = sum_partials(P2 + (int64_t)NV * G, G);
-        if (threadIdx.x == 0) s_w2 = t;
+        // FP64 passes on V and w; the pair copy written by the normalisation
+        double acc[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+        double accw = 0.0;
+        if (reorth) {
+            update_pass<NV, true>(V, w, n, nv, sh_h, acc, accw);
+            block_partials<NV>(acc, nv, P2, sh);
+            grid_barrier(bar, kd.ictl);
+            const double v2 = final_partials<NV>(P2, nv, G);
+            __syncthreads();
+            if (threadIdx.x / T < nv && threadIdx.x % T == 0) sh_h[threadIdx.x / T] = v2;
+            __syncthreads();
+            if (blockIdx.x == 0 && threadIdx.x < nv) s_col[threadIdx.x] += sh_h[threadIdx.x];
+            update_pass<NV, false>(V, w, n, nv, sh_h, acc, accw);
+            const double bs = block_sum_kt(accw, shw);
+            if (threadIdx.x == 0) P3[(int64_t)NV * G + blockIdx.x] = bs;
+            grid_barrier(bar, kd.ictl);
+            const double t = norm_total(P3 + (int64_t)NV * G, G, shw);
+            if (threadIdx.x == 0) s_w2 = t;
+        } else {
+            update_pass<NV, false>(V, w, n, nv, sh_h, acc, accw);
+            const double bs = block_sum_kt(accw, shw);
+            if (threadIdx.x == 0) P2[(int64_t)NV * G + blockIdx.x] = bs;
+            grid_barrier(bar, kd.ictl);
+            const double t = norm_total(P2 + (int64_t)NV * G, G, shw);
+            if (threadIdx.x == 0) s_w2 = t;
+        }
+        __syncthreads();
+        const double hn = sqrt(s_w2);
+        hn_w = hn;
+        const double inv = hn != 0.0 ? 1.0 / hn : 1.0;
+        for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += G * KT) {
+            const float2 v = split_f64(w[e] * inv);
+            Ws[e] = v;
+            w[e] = (double)v.x + (double)v.y;
+        }
     }
-    __syncthreads();
-    wn2 = s_w2;
-    // normalise the thread's elements; block 0 finishes the Arnoldi step
-    const double hn = sqrt(wn2);
-    if (hn != 0.0) {
-        const double inv = 1.0 / hn;
-        for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += G * KT) w[e] = w[e] * inv;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) arnoldi_finish(kd, j, wn2);
+    if (blockIdx.x == 0 && threadIdx.x < 32) arnoldi_finish_warp(kd, j, hn_w, s_col, s_rot, NV, s_g, s_it);
 }
 
 __global__ void k_fg_scale(double* __restrict__ w, int n, KDims kd) {
@@ -1038,7 +1405,8 @@ int krylov_alloc(psr_ctx* ctx) {
         cudaGetLastError();
         w.coop = b8 >= 1 && b16 >= 1 && b32 >= 1;
     }
-    PSR_CUDA(ctx, cudaMalloc(&w.part_arn, (size_t)3 * 33 * 2 * w.sms * sizeof(double)));
+    if (w.coop) PSR_CUDA(ctx, cudaMalloc(&w.Vs, (size_t)(m + 1) * n * sizeof(float2)));
+    PSR_CUDA(ctx, cudaMalloc(&w.part_arn, (size_t)4 * 33 * w.sms * sizeof(double)));
     PSR_CUDA(ctx, cudaMalloc(&w.bar, 2 * sizeof(unsigned int)));
     PSR_CUDA(ctx, cudaMemset(w.bar, 0, 2 * sizeof(unsigned int)));
     PSR_CUDA(ctx, cudaMemset(w.ictl, 0, 32 * sizeof(int32_t)));
@@ -1051,6 +1419,7 @@ void krylov_free(psr_ctx* ctx) {
     cudaFree(w.ictl);
     cudaFree(w.rflag);
     cudaFree(w.part_arn);
+    cudaFree(w.Vs);
     cudaFree(w.bar);
     cudaFree(w.sell_ptr);
     cudaFree(w.sell_cols);
@@ -1170,10 +1539,25 @@ static int enqueue_arnoldi(psr_ctx* ctx, KDims kd, int j, double* Vn, cudaStream
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    KT_BEGIN(PSR_KT_MDOT, j, ((j + 2) + (j + 3) + 2) * vb, 4.0 * n * (j + 2) + n);
-    KT_REORTH((j + 3) * vb, 4.0 * n * (j + 1));
+    // bytes: pass 1 reads w and j+1 pair rows and writes the pair of w, each
+    // update reads and writes that pair and reads j+1 rows, the normalisation
+    // reads the pair and writes it and V_{j+1}.  FP64 flops of the pair path
+    // (the dots and updates run on FP32 pairs): ||w||^2 and the split in
+    // pass 1, the FP64 value and its square in the last update, the FP64
+    // value of the normalised pair.
+    // In FP64 (PSR_ORTHO_FP64): the projection reads w and j+1 rows, each
+    // update j+1 rows and w twice, the normalisation writes w and its pair.
+    const int fp64 = ctx->opts.ortho == PSR_ORTHO_FP64 ? 1 : 0;
+    if (fp64) {
+        KT_BEGIN(PSR_KT_MDOT, j, ((j + 2) + (j + 3) + 3) * vb, 4.0 * n * (j + 2) + 3.0 * n);
+        KT_REORTH((j + 3) * vb, 4.0 * n * (j + 1));
+    } else {
+        KT_BEGIN(PSR_KT_MDOT, j, ((j + 3) + (j + 3) + 3) * vb, 7.0 * n);
+        KT_REORTH((j + 3) * vb, 0.0);
+    }
     count_launch();
-    PSR_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_arnoldi<NV>, (const double*)w.V, Vn, n, j, kd, w.part_arn, w.bar));
+    PSR_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_arnoldi<NV>, (const double*)w.V, Vn, w.Vs, n, j, kd, w.part_arn, w.bar,
+                                     fp64));
     KT_END();
     return PSR_OK;
 }
@@ -1181,7 +1565,8 @@ static int enqueue_arnoldi(psr_ctx* ctx, KDims kd, int j, double* Vn, cudaStream
 static int enqueue_fg_cycle(psr_ctx* ctx, KDims kd, cudaStream_t s) {
     KrylovWS& w = ctx->ws;
     const int n = ctx->n, nb = w.nblk, m = kd.m;
-    count_launch(); k_fg_start<<<nb, 256, 0, s>>>(w.r, w.V, n, kd);
+    float2* Vs0 = (w.coop && ctx->opts.ortho != PSR_ORTHO_SPLIT) ? w.Vs : nullptr;
+    count_launch(); k_fg_start<<<nb, 256, 0, s>>>(w.r, w.V, Vs0, n, kd);
     for (int j = 0; j < m; ++j) {
         double* Vj = w.V + (size_t)j * n;
         double* Vn = w.V + (size_t)(j + 1) * n;
@@ -1195,7 +1580,7 @@ static int enqueue_fg_cycle(psr_ctx* ctx, KDims kd, cudaStream_t s) {
         launch_spmv(ctx, Zj, Vn, nullptr, 0, 0, kd, 1, w.nspmv, s);
         KT_END();
         int rc2 = PSR_OK;
-        if (w.coop) {
+        if (w.coop && ctx->opts.ortho != PSR_ORTHO_SPLIT) {
             if (j < 8) rc2 = enqueue_arnoldi<8>(ctx, kd, j, Vn, s);
             else if (j < 16) rc2 = enqueue_arnoldi<16>(ctx, kd, j, Vn, s);
             else rc2 = enqueue_arnoldi<32>(ctx, kd, j, Vn, s);

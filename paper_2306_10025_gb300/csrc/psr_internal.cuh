@@ -108,7 +108,8 @@ struct KrylovWS {
     double* hist = nullptr;     // [maxit + 1]
     int32_t* ictl = nullptr;    // device control ints
     int32_t* rflag = nullptr;   // [64] FGMRES: second Gram-Schmidt pass taken at step j
-    double* part_arn = nullptr; // partials of the fused Arnoldi step, 3 passes x 33 x 2 sms
+    double* part_arn = nullptr; // partials of the fused Arnoldi step, 4 regions x 33 x sms
+    float2* Vs = nullptr;       // pair copy (hi, lo FP32) of the FGMRES basis, (m+1) x n, fused step only
     unsigned int* bar = nullptr;  // grid barrier of the fused Arnoldi step (count, generation)
     bool coop = false;          // fused Arnoldi step (cooperative launch) available
     int64_t* sell_ptr = nullptr;  // SELL-32 copy of A: slice offsets [nslices + 1]

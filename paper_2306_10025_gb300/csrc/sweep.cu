@@ -148,6 +148,94 @@ __global__ void __launch_bounds__(256) k_sweep_warp(const int32_t* __restrict__ 
     }
 }
 
+// Generic, p <= 128, staged: per tile the inverse and the DOF lists of up to
+// `sub` patches at a time are copied into shared memory (cp.async), then r,
+// the output weight and (SYM) the input weight at those DOFs are gathered
+// into shared memory the same way, so a tile costs two memory round trips
+// instead of two per patch and warp; the weighted residual is rounded to the
+// compute type once per entry, and every thread forms one (patch, row) of
+// B^-1 r_k (two accumulation chains) and scatter-adds it.
+__host__ __device__ inline size_t staged_align(size_t b) { return (b + 15) & ~(size_t)15; }
+template <typename C>
+__host__ __device__ inline size_t staged_smem(int p, int sub, bool sym) {
+    const size_t ne = (size_t)sub * p;
+    return staged_align((size_t)p * p * sizeof(C)) + staged_align(ne * 4) + 2 * staged_align(ne * 8) +
+           (sym ? staged_align(ne * 8) : 0) + staged_align(ne * sizeof(C));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep_staged(const int32_t* __restrict__ tiles, int ntiles, int p, int sub,
+                                                      const T* __restrict__ rinv, const int32_t* __restrict__ sdofs,
+                                                      const double* __restrict__ r, const double* __restrict__ wg,
+                                                      const double* __restrict__ wsc, double* __restrict__ z,
+                                                      const int32_t* __restrict__ stop) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    using C = typename Comp<T>::type;
+    if (stop && *stop) return;
+    const int pp = p * p;
+    const size_t ne_max = (size_t)sub * p;
+    size_t off = staged_align((size_t)pp * sizeof(C));
+    C* sR = reinterpret_cast<C*>(smem);
+    int32_t* sd = reinterpret_cast<int32_t*>(smem + off);
+    off += staged_align(ne_max * 4);
+    double* sx = reinterpret_cast<double*>(smem + off);
+    off += staged_align(ne_max * 8);
+    double* sw = reinterpret_cast<double*>(smem + off);
+    off += staged_align(ne_max * 8);
+    double* sg = nullptr;
+    if (wg) {
+        sg = reinterpret_cast<double*>(smem + off);
+        off += staged_align(ne_max * 8);
+    }
+    C* sc = reinterpret_cast<C*>(smem + off);
+    const int nt = blockDim.x;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int c = tiles[3 * t], start = tiles[3 * t + 1], cnt = tiles[3 * t + 2];
+        const T* src = rinv + (int64_t)c * pp;
+        for (int k0 = 0; k0 < cnt; k0 += sub) {
+            const int kc = min(sub, cnt - k0);
+            const int ne = kc * p;
+            const int32_t* dk = sdofs + (int64_t)(start + k0) * p;
+            __syncthreads();                          // the previous sub-tile's readers are done
+            // round trip 1: the inverse (first sub-tile only) and the DOF lists
+            if (k0 == 0) {
+                if constexpr (sizeof(T) == sizeof(C)) {
+                    for (int e = threadIdx.x; e < pp; e += nt) cp_async_elem<sizeof(T)>(sR + e, src + e);
+                } else {
+                    for (int e = threadIdx.x; e < pp; e += nt) sR[e] = (C)src[e];
+                }
+            }
+            for (int e = threadIdx.x; e < ne; e += nt) cp_async_elem<4>(sd + e, dk + e);
+            cp_async_wait_all();
+            __syncthreads();
+            // round trip 2: gathers at the DOFs
+            for (int e = threadIdx.x; e < ne; e += nt) {
+                const int d = sd[e];
+                cp_async_elem<8>(sx + e, r + d);
+                cp_async_elem<8>(sw + e, wsc + d);
+                if (wg) cp_async_elem<8>(sg + e, wg + d);
+            }
+            cp_async_wait_all();
+            __syncthreads();
+            for (int e = threadIdx.x; e < ne; e += nt) sc[e] = (C)(wg ? sx[e] * sg[e] : sx[e]);
+            __syncthreads();
+            for (int it = threadIdx.x; it < ne; it += nt) {
+                const int k = it / p, a = it - k * p;
+                const C* row = sR + a * p;
+                const C* x = sc + k * p;
+                C y0 = (C)0, y1 = (C)0;
+                int b = 0;
+                for (; b + 1 < p; b += 2) {
+                    y0 = fma(row[b], x[b], y0);
+                    y1 = fma(row[b + 1], x[b + 1], y1);
+                }
+                if (b < p) y0 = fma(row[b], x[b], y0);
+                atomicAdd(&z[sd[it]], (double)(y0 + y1) * sw[it]);
+            }
+        }
+    }
+}
+
 // Small patches (p <= 16): two patches per warp, one per half-warp, r values
 // exchanged with width-16 shuffles.
 template <typename T>
@@ -638,6 +726,9 @@ int autotune_sweep(psr_ctx* ctx, cudaStream_t s) {
     return rc;
 }
 
+// Shared memory of one staged sweep block (two blocks per SM fit).
+constexpr size_t STAGED_SMEM_MAX = 96 * 1024;
+
 template <typename T>
 static int launch_group(psr_ctx* ctx, const Group& G, const double* r, double* z, const int32_t* stop,
                         cudaStream_t s) {
@@ -673,7 +764,17 @@ static int launch_group(psr_ctx* ctx, const Group& G, const double* r, double* z
     } else if (G.p <= 16) {
         count_launch(); k_sweep_half<T><<<blocks, warps * 32, sm, s>>>(G.tiles, G.ntiles, G.p, rinv, G.sdofs, r, ctx->Wg, ctx->W, z, stop);
     } else {
-        count_launch(); k_sweep_warp<T><<<blocks, warps * 32, sm, s>>>(G.tiles, G.ntiles, G.p, rinv, G.sdofs, r, ctx->Wg, ctx->W, z, stop);
+        // staged tiles: as many patches per staging as fit the budget
+        using C = typename Comp<T>::type;
+        const bool sym = ctx->Wg != nullptr;
+        int sub = G.tile_patches;
+        while (sub > 1 && staged_smem<C>(G.p, sub, sym) > STAGED_SMEM_MAX) sub >>= 1;
+        const size_t ssm = staged_smem<C>(G.p, sub, sym);
+        if (ssm <= STAGED_SMEM_MAX) {
+            count_launch(); k_sweep_staged<T><<<blocks, warps * 32, ssm, s>>>(G.tiles, G.ntiles, G.p, sub, rinv, G.sdofs, r, ctx->Wg, ctx->W, z, stop);
+        } else {
+            count_launch(); k_sweep_warp<T><<<blocks, warps * 32, sm, s>>>(G.tiles, G.ntiles, G.p, rinv, G.sdofs, r, ctx->Wg, ctx->W, z, stop);
+        }
     }
     PSR_CHECK_LAUNCH(ctx, "sweep kernel");
     return PSR_OK;
@@ -714,6 +815,9 @@ int sweep_prepare(psr_ctx* ctx) {
     PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_grouped<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_grouped<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_warp<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_staged<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_staged<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_staged<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_full<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     {
         int rc = tc_prepare();

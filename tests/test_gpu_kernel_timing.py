@@ -29,11 +29,12 @@ def setup_ctx(lib, pr, **kw):
                          opts=lib.make_opts(**kw))
 
 
-@pytest.mark.parametrize("graph", [True, False])
-def test_fgmres_timing_counts_and_bytes(lib, graph):
+@pytest.mark.parametrize("graph,ortho", [(True, "auto"), (False, "auto"), (True, "fp64"), (True, "split")])
+def test_fgmres_timing_counts_and_bytes(lib, graph, ortho):
     pr = P.stokes2d_q2q1(8)
     maxit, m = 45, 30
-    ctx = setup_ctx(lib, pr, tol=0.0, weighting="left", krylov="fgmres", restart=m, maxit=maxit, use_graph=graph)
+    ctx = setup_ctx(lib, pr, tol=0.0, weighting="left", krylov="fgmres", restart=m, maxit=maxit, use_graph=graph,
+                    ortho=ortho)
     b = dev(pr.rhs(0), torch.float64)
     x0 = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
     i0 = ctx.solve(b, x0)
@@ -53,11 +54,15 @@ def test_fgmres_timing_counts_and_bytes(lib, graph):
     js = list(range(m)) + list(range(maxit - m))          # iterations j of each cycle
     assert kt["sweep"][1] == its and kt["spmv"][1] == its
     second = sum(8.0 * (j + 3) * n for j in js)            # bytes of the second passes, if all taken
+    if ortho == "split":
+        assert kt["maxpy"][1] > 0
     if kt["maxpy"][1] == 0:
         # fused Arnoldi step (cooperative launch): projection, update(s) and
-        # normalisation in one kernel per step
+        # normalisation in one kernel per step; on pairs it reads the pair
+        # copy of the basis and keeps w as a pair between the passes
         assert kt["mdot"][1] == its and kt["vec"][1] == 0
-        base = sum(8.0 * ((j + 2) + (j + 3) + 2) * n for j in js)
+        first = 2 if ortho == "fp64" else 3
+        base = sum(8.0 * ((j + first) + (j + 3) + 3) * n for j in js)
         assert base * (1 - 1e-12) <= kt["mdot"][2] <= (base + second) * (1 + 1e-12)
         classes = ("sweep", "spmv", "mdot")
     else:
@@ -72,10 +77,14 @@ def test_fgmres_timing_counts_and_bytes(lib, graph):
     # FP64 flops: SpMV 2 nnz per launch; the Gram-Schmidt step between its
     # single-pass and its two-pass count
     assert kt["spmv"][3] == pytest.approx(its * 2.0 * pr.nnz, rel=1e-12)
-    if kt["maxpy"][1] == 0:
-        lo = sum(4.0 * n * (j + 2) + n for j in js)
+    if kt["maxpy"][1] == 0 and ortho == "fp64":
+        lo = sum(4.0 * n * (j + 2) + 3.0 * n for j in js)
         hi = lo + sum(4.0 * n * (j + 1) for j in js)
         assert lo * (1 - 1e-12) <= kt["mdot"][3] <= hi * (1 + 1e-12)
+    elif kt["maxpy"][1] == 0:
+        # the fused step runs its dots and updates on FP32 pairs: 7 FP64
+        # flops per entry (norm and split of w, last norm, FP64 copy of v)
+        assert kt["mdot"][3] == pytest.approx(its * 7.0 * n, rel=1e-12)
     assert kt["spmv"][2] == pytest.approx(its * (12.0 * pr.nnz + 4.0 * (n + 1) + 16.0 * n), rel=1e-12)
     # disabling resets nothing but stops the marks; re-enabling resets
     ctx.set_kernel_timing(False)
