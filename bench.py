@@ -58,14 +58,19 @@ CONFIGS = {
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 # kernel(s) behind each timing class of the library's per-kernel timing
-KT_KERNEL_NAMES = {"sweep": "patch sweep (k_sweep_*)", "spmv": "k_spmv (CSR SpMV, FP64)",
-                   "mdot": "k_arnoldi (fused FGMRES Arnoldi step) / k_mdot", "maxpy": "k_maxpy (FGMRES w -= V h)",
+KT_KERNEL_NAMES = {"sweep": "patch sweep (k_sweep_staged / k_sweep_*)", "spmv": "k_spmv_sell (SELL SpMV, FP64)",
+                   "mdot": "k_arnoldi (fused FGMRES Gram-Schmidt step on FP32 pairs) / k_mdot", "maxpy": "k_maxpy (FGMRES w -= V h)",
                    "vec": "vector kernels (k_fg_scale / CG updates)"}
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, ncu,
 # averaged over the captured launches) for (config, class), valid only for
 # the kernel source they were taken on; None until captured.
 TRAFFIC = {
+    # ncu --set full of the fused Gram-Schmidt step on pairs at j = 20
+    # (26.33 MB: one DRAM read of the 21 pair rows and of w, later passes
+    # from L2) scaled to the mean basis size of a step, (j+2) averaged over
+    # j = 0..29
+    ("stokes2d", "mdot"): 26.33e6 * 16.5 / 22.0,
     # ncu --set full, one launch inside the FGMRES cycle (k_spmv_sell):
     # 89.11 MB read + 2.47 MB written
     ("stokes2d", "spmv"): 91.6e6,

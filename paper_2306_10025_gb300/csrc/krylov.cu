@@ -971,7 +971,7 @@ __device__ __forceinline__ void pair_update(const float2* __restrict__ Vs, float
 // in FP64 instead (the same passes on V), so the pair path never meets
 // overflow or underflow of the incoming vector.
 template <int NV>
-__global__ void __launch_bounds__(KT) k_arnoldi(const double* __restrict__ V, double* __restrict__ w,
+__global__ void __launch_bounds__(KT, 1) k_arnoldi(const double* __restrict__ V, double* __restrict__ w,
                                                float2* __restrict__ Vs, int n, int j, KDims kd,
                                                double* __restrict__ part, unsigned int* bar, int fp64) {
     __shared__ double sh[NV][KT / 32 + 1];
