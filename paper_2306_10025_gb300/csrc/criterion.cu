@@ -73,6 +73,15 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
                            const float* sB32 = nullptr) {
     const int lane = threadIdx.x & 31;
     const bool act = lane < p;
+    // D = 0 when the patches are bitwise equal: integer compares, no FP64
+    // instruction (the common accept of uniform meshes)
+    {
+        bool same = true;
+        if (act)
+            for (int j = 0; j < p; ++j)
+                same &= __double_as_longlong(sAc[lane * ld + j]) == __double_as_longlong(Ai[lane * p + j]);
+        if (__all_sync(0xffffffffu, same)) { *dv = 0.0; return 1; }
+    }
     // pass 1: D = A_c - A_i, ||D||_F and (D w)_lane
     double dn2 = 0.0, dw = 0.0, dw2 = 0.0;
     if (act) {
@@ -462,7 +471,7 @@ __global__ void k_entry_fro(const double* __restrict__ A, const double* __restri
 constexpr int SK = 2;              // sketch directions per size group
 struct SketchDB {
     const double* X;               // [SK][32] unit directions (zero beyond p)
-    const double* Y;               // [count][SK][p] y_i = fl(A_i x_k)
+    const double* den;             // [count][SK] den_k >= ||A_i x_k|| (norm of the FP64 sketch, widened)
     const double* fa;              // [count] ||A_i||_F
     const double* rho;             // [count] bound of ||B_i^ A_i - I||_2
     const float* Y32;              // [count][SK][p] y_i rounded to FP32 (the screen's operand)
@@ -496,7 +505,7 @@ __global__ void k_sketch_dirs(const double* __restrict__ Ag, int count, int p, d
 template <int PM>
 __global__ void __launch_bounds__(256) k_sketch(const double* __restrict__ A, const double* __restrict__ Binv,
                                                 int count, int p, const double* __restrict__ X,
-                                                double* __restrict__ Y, float* __restrict__ Y32,
+                                                double* __restrict__ den, float* __restrict__ Y32,
                                                 double* __restrict__ fa, double* __restrict__ rho) {
     const int lane = threadIdx.x & 31;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -516,15 +525,14 @@ __global__ void __launch_bounds__(256) k_sketch(const double* __restrict__ A, co
         fa2 = fma(a[j], a[j], fa2);
         fb2 = fma(b[j], b[j], fb2);
     }
+    double yn2[SK];
 #pragma unroll
     for (int k = 0; k < SK; ++k) {
         double y = 0.0;
 #pragma unroll
         for (int j = 0; j < PM; ++j) y = fma(a[j], X[k * 32 + j], y);
-        if (act) {
-            Y[((int64_t)i * SK + k) * p + lane] = y;
-            Y32[((int64_t)i * SK + k) * p + lane] = (float)y;
-        }
+        if (act) Y32[((int64_t)i * SK + k) * p + lane] = (float)y;
+        yn2[k] = act ? y * y : 0.0;
     }
     // column j of B^ A: lane r sums b[r][k] A[k][j], A[k][j] from lane k
     double res2 = 0.0;
@@ -541,28 +549,31 @@ __global__ void __launch_bounds__(256) k_sketch(const double* __restrict__ A, co
     fa2 = warp_sum(fa2);
     fb2 = warp_sum(fb2);
     res2 = warp_sum(res2);
+#pragma unroll
+    for (int k = 0; k < SK; ++k) yn2[k] = warp_sum(yn2[k]);
     if (lane == 0) {
         const double fA = sqrt(fa2), fB = sqrt(fb2);
         fa[i] = fA;
         // computed residual entries carry at most gamma_{p+1} |B^||A| error
         rho[i] = 1.01 * sqrt(res2) + 1.01 * gamma_u(p + 1) * fB * fA;
+        // den_k >= ||A x_k||: the computed sketch norm widened for its own
+        // rounding and for that of the sketch (gamma_p |A||x_k|)
+#pragma unroll
+        for (int k = 0; k < SK; ++k)
+            den[(int64_t)i * SK + k] = sqrt(yn2[k]) * (1.0 + (double)(p + 2) * U64) + 1.01 * gamma_u(p) * fA;
     }
 }
 
 // Entry side of the screen, staged in shared memory: y_c in FP32 (SK x 32,
-// zero beyond p) and the denominators den_k >= ||A_c x_k|| (from the FP64
-// sketch).
-__device__ __forceinline__ void stage_sketch(const double* __restrict__ Yc, const float* __restrict__ Yc32, double fc,
-                                             int p, float* sy32, double* sden) {
+// zero beyond p) and the denominators den_k >= ||A_c x_k|| (precomputed with
+// the sketches).
+__device__ __forceinline__ void stage_sketch(const double* __restrict__ denc, const float* __restrict__ Yc32, int p,
+                                             float* sy32, double* sden) {
     for (int t = threadIdx.x; t < SK * 32; t += blockDim.x) {
         const int k = t >> 5, r = t & 31;
         sy32[t] = (r < p) ? Yc32[k * p + r] : 0.f;
     }
-    if (threadIdx.x < SK) {
-        double n2 = 0.0;
-        for (int r = 0; r < p; ++r) n2 = fma(Yc[threadIdx.x * p + r], Yc[threadIdx.x * p + r], n2);
-        sden[threadIdx.x] = sqrt(n2) * (1.0 + (double)(p + 2) * U64) + 1.01 * gamma_u(p) * fc;
-    }
+    if (threadIdx.x < SK) sden[threadIdx.x] = denc[threadIdx.x];
 }
 
 __device__ __forceinline__ float ldg_nc_f(const float* q) {
@@ -575,18 +586,24 @@ __device__ __forceinline__ float ldg_nc_f(const float* q) {
 // the certified lower bound reaches tol (reject).  The distance of the
 // sketches is formed in FP32 from the FP32 copies: their rounding
 // (||y - fl32(y)|| <= 2^-24 ||y||, ||y|| <= 1.01 ||A||_F) and that of the FP32
-// norm ((p + 8) 2^-24 relative) are taken off the bound.  All SK x PM loads
-// are issued before the first use (PM >= p, indices clamped to p - 1).
+// norm and of its correctly rounded FP32 square root ((p + 9) 2^-24
+// relative) are taken off the bound, and the test num_k >= tol den_k is made
+// without a division.  sketch_load issues all SK x PM loads of the candidate
+// (indices clamped to p - 1) so that they are in flight with the caller's
+// other loads of that candidate.
 template <int PM>
-__device__ __forceinline__ bool sketch_rejects(const float* __restrict__ yi, double fi, const float* sy32,
-                                               const double* sden, double fc, double rhoc, int p, double tol) {
-    float v[SK * PM];
+__device__ __forceinline__ void sketch_load(const float* __restrict__ yi, int p, float (&v)[SK * PM]) {
 #pragma unroll
     for (int k = 0; k < SK; ++k)
 #pragma unroll
         for (int r = 0; r < PM; ++r) v[k * PM + r] = ldg_nc_f(yi + k * p + min(r, p - 1));
+}
+
+template <int PM>
+__device__ __forceinline__ bool sketch_bound_rejects(const float (&v)[SK * PM], double fi, const float* sy32,
+                                                     const double* sden, double fc, double rhoc, int p, double tol) {
     const double slack = 1.01 * (fc + fi) * (gamma_u(p) + rhoc) + 1.01 * 0x1p-24 * (fc + fi);
-    double lb = 0.0;
+    bool rej = false;
 #pragma unroll
     for (int k = 0; k < SK; ++k) {
         float d2 = 0.f;
@@ -595,10 +612,10 @@ __device__ __forceinline__ bool sketch_rejects(const float* __restrict__ yi, dou
             const float d = (r < p) ? sy32[k * 32 + r] - v[k * PM + r] : 0.f;
             d2 = fmaf(d, d, d2);
         }
-        const double num = sqrt((double)d2) * (1.0 - (double)(p + 8) * 0x1p-24) - slack * (1.0 + 8.0 * U64);
-        if (sden[k] > 0.0) lb = fmax(lb, num / sden[k]);
+        const double num = (double)sqrtf(d2) * (1.0 - (double)(p + 9) * 0x1p-24) - slack * (1.0 + 8.0 * U64);
+        if (sden[k] > 0.0 && num * (1.0 - 8.0 * U64) >= tol * sden[k] * (1.0 + 4.0 * U64)) rej = true;
     }
-    return lb * (1.0 - 8.0 * U64) >= tol;
+    return rej;
 }
 
 __device__ __forceinline__ bool round_last_block(int* ticket) {
@@ -637,15 +654,18 @@ __global__ void __launch_bounds__(EVAL_THREADS) k_round_screen(RoundDev* st, con
     const int lane = threadIdx.x & 31;
     const int i0 = st->next;
     const double fc = sk.fa[i0], rhoc = sk.rho[i0];
-    stage_sketch(sk.Y + (int64_t)i0 * SK * p, sk.Y32 + (int64_t)i0 * SK * p, fc, p, sy, sden);
+    stage_sketch(sk.den + (int64_t)i0 * SK, sk.Y32 + (int64_t)i0 * SK * p, p, sy, sden);
     __syncthreads();
     unsigned long long my_evals = 0, my_screened = 0;
     int my_min = count;
     for (int base = i0 + 1 + blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
         const int cand = base + threadIdx.x;
-        const bool open = cand < count && phi[cand] == -1;
-        bool rej = false;
-        if (open) rej = sketch_rejects<PM>(sk.Y32 + (int64_t)cand * SK * p, sk.fa[cand], sy, sden, fc, rhoc, p, tol);
+        const int cc = min(cand, count - 1);
+        float v[SK * PM];
+        sketch_load<PM>(sk.Y32 + (int64_t)cc * SK * p, p, v);
+        const double fi = sk.fa[cc];
+        const bool open = cand < count && phi[cc] == -1;
+        const bool rej = open && sketch_bound_rejects<PM>(v, fi, sy, sden, fc, rhoc, p, tol);
         if (open && rej) my_min = min(my_min, cand);
         const unsigned opened = __ballot_sync(0xffffffffu, open);
         const unsigned surv = __ballot_sync(0xffffffffu, open && !rej);
@@ -801,7 +821,7 @@ __global__ void __launch_bounds__(EVAL_THREADS) k_rounds_persistent(
         const int par = round & 1;
         // stage the entry: sketch for the screen, matrices for the decisions
         const double fc = sk.fa[i0], rhoc = sk.rho[i0];
-        stage_sketch(sk.Y + (int64_t)i0 * SK * p, sk.Y32 + (int64_t)i0 * SK * p, fc, p, sy, sden);
+        stage_sketch(sk.den + (int64_t)i0 * SK, sk.Y32 + (int64_t)i0 * SK * p, p, sy, sden);
         const double* a = Ag + (int64_t)i0 * p * p;
         const double* bm = Ball + (int64_t)i0 * p * p;
         for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
@@ -817,9 +837,12 @@ __global__ void __launch_bounds__(EVAL_THREADS) k_rounds_persistent(
         // screen
         for (int base = i0 + 1 + blockIdx.x * blockDim.x; base < count; base += gthreads) {
             const int cand = base + threadIdx.x;
-            const bool open = cand < count && phi[cand] == -1;
-            bool rej = false;
-            if (open) rej = sketch_rejects<PM>(sk.Y32 + (int64_t)cand * SK * p, sk.fa[cand], sy, sden, fc, rhoc, p, tol);
+            const int cc = min(cand, count - 1);
+            float v[SK * PM];
+            sketch_load<PM>(sk.Y32 + (int64_t)cc * SK * p, p, v);
+            const double fi = sk.fa[cc];
+            const bool open = cand < count && phi[cc] == -1;
+            const bool rej = open && sketch_bound_rejects<PM>(v, fi, sy, sden, fc, rhoc, p, tol);
             if (open && rej) my_min = min(my_min, cand);
             const unsigned opened = __ballot_sync(0xffffffffu, open);
             const unsigned surv = __ballot_sync(0xffffffffu, open && !rej);
@@ -909,7 +932,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_seed_pass(RoundDev* st, int
         sB32[(t / p) * ld + (t % p)] = (float)db.Binv[(int64_t)e * p * p + t];
     const double bfro = db.fro[e];
     const double fc = skd.fa[e], rhoc = skd.rho[e];
-    stage_sketch(skd.Y + (int64_t)e * SK * p, skd.Y32 + (int64_t)e * SK * p, fc, p, sy, sden);
+    stage_sketch(skd.den + (int64_t)e * SK, skd.Y32 + (int64_t)e * SK * p, p, sy, sden);
     __syncthreads();
     unsigned long long my_evals = 0, my_exact = 0, my_screened = 0;
     __shared__ int s_list[EVAL_THREADS];
@@ -918,9 +941,12 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_seed_pass(RoundDev* st, int
         if (threadIdx.x == 0) s_cnt = 0;
         __syncthreads();
         const int cand = base + threadIdx.x;
-        const bool open = cand < count && phi[cand] == -1;
-        bool rej = false;
-        if (open) rej = sketch_rejects<32>(sk.Y32 + (int64_t)cand * SK * p, sk.fa[cand], sy, sden, fc, rhoc, p, tol);
+        const int cc = min(cand, count - 1);
+        float v[SK * 32];
+        sketch_load<32>(sk.Y32 + (int64_t)cc * SK * p, p, v);
+        const double fi = sk.fa[cc];
+        const bool open = cand < count && phi[cc] == -1;
+        const bool rej = open && sketch_bound_rejects<32>(v, fi, sy, sden, fc, rhoc, p, tol);
         const unsigned opened = __ballot_sync(0xffffffffu, open);
         const unsigned surv = __ballot_sync(0xffffffffu, open && !rej);
         my_evals += __popc(opened);
@@ -1021,13 +1047,13 @@ __global__ void k_verify_hints(RoundDev* st, int32_t* __restrict__ phi, int coun
     }
 }
 
-static void launch_sketch(const double* A, const double* Binv, int count, int p, const double* X, double* Y,
+static void launch_sketch(const double* A, const double* Binv, int count, int p, const double* X, double* den,
                           float* Y32, double* fa, double* rho, cudaStream_t s) {
     const int blocks = (count + 7) / 8;
-    if (p <= 8) k_sketch<8><<<blocks, 256, 0, s>>>(A, Binv, count, p, X, Y, Y32, fa, rho);
-    else if (p <= 16) k_sketch<16><<<blocks, 256, 0, s>>>(A, Binv, count, p, X, Y, Y32, fa, rho);
-    else if (p <= 24) k_sketch<24><<<blocks, 256, 0, s>>>(A, Binv, count, p, X, Y, Y32, fa, rho);
-    else k_sketch<32><<<blocks, 256, 0, s>>>(A, Binv, count, p, X, Y, Y32, fa, rho);
+    if (p <= 8) k_sketch<8><<<blocks, 256, 0, s>>>(A, Binv, count, p, X, den, Y32, fa, rho);
+    else if (p <= 16) k_sketch<16><<<blocks, 256, 0, s>>>(A, Binv, count, p, X, den, Y32, fa, rho);
+    else if (p <= 24) k_sketch<24><<<blocks, 256, 0, s>>>(A, Binv, count, p, X, den, Y32, fa, rho);
+    else k_sketch<32><<<blocks, 256, 0, s>>>(A, Binv, count, p, X, den, Y32, fa, rho);
 }
 
 static int set_smem(const void* f, size_t bytes) {
@@ -1084,13 +1110,13 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         if (rc != PSR_OK) break;
         count_launch();
         k_entry_fro<<<(count + 7) / 8, 256, 0, s>>>(Ag, Ball, count, p, fro_all, w_all, sing_all, nullptr);
-        double *skX = nullptr, *skY = nullptr, *skF = nullptr, *skR = nullptr;
+        double *skX = nullptr, *skDen = nullptr, *skF = nullptr, *skR = nullptr;
         float *skY32 = nullptr, *sdY32 = nullptr;
         PSR_CUDA(ctx, cudaMalloc(&skX, sizeof(double) * SK * 32));
         PSR_CUDA(ctx, cudaMalloc(&skY32, sizeof(float) * (size_t)count * SK * p));
         PSR_CUDA(ctx, cudaMalloc(&skF, sizeof(double) * (size_t)count));
         PSR_CUDA(ctx, cudaMalloc(&skR, sizeof(double) * (size_t)count));
-        if (cudaMalloc(&skY, sizeof(double) * (size_t)count * SK * p) != cudaSuccess) {
+        if (cudaMalloc(&skDen, sizeof(double) * (size_t)count * SK) != cudaSuccess) {
             cudaGetLastError();
             set_error(ctx, "out of device memory for the patch sketches");
             return PSR_ERR_OOM;
@@ -1098,11 +1124,11 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         count_launch();
         k_sketch_dirs<<<1, 32 * SK, 0, s>>>(Ag, count, p, skX);
         count_launch();
-        launch_sketch(Ag, Ball, count, p, skX, skY, skY32, skF, skR, s);
+        launch_sketch(Ag, Ball, count, p, skX, skDen, skY32, skF, skR, s);
         PSR_CHECK_LAUNCH(ctx, "patch sketches");
-        const SketchDB sk{skX, skY, skF, skR, skY32};
+        const SketchDB sk{skX, skDen, skF, skR, skY32};
         SketchDB skd{skX, nullptr, nullptr, nullptr, nullptr};
-        double *sdY = nullptr, *sdF = nullptr, *sdR = nullptr;
+        double *sdDen = nullptr, *sdF = nullptr, *sdR = nullptr;
         RoundDev init{};
         init.first_singular = -1;
         init.m = m0;
@@ -1137,13 +1163,13 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
             PSR_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
             count_launch();
             k_entry_fro<<<(m0 + 7) / 8, 256, 0, s>>>(db.A, db.Binv, m0, p, db.fro, db.w, sflags, flag);
-            PSR_CUDA(ctx, cudaMalloc(&sdY, sizeof(double) * (size_t)m0 * SK * p));
+            PSR_CUDA(ctx, cudaMalloc(&sdDen, sizeof(double) * (size_t)m0 * SK));
             PSR_CUDA(ctx, cudaMalloc(&sdF, sizeof(double) * (size_t)m0));
             PSR_CUDA(ctx, cudaMalloc(&sdR, sizeof(double) * (size_t)m0));
             PSR_CUDA(ctx, cudaMalloc(&sdY32, sizeof(float) * (size_t)m0 * SK * p));
             count_launch();
-            launch_sketch(db.A, db.Binv, m0, p, skX, sdY, sdY32, sdF, sdR, s);
-            skd = SketchDB{skX, sdY, sdF, sdR, sdY32};
+            launch_sketch(db.A, db.Binv, m0, p, skX, sdDen, sdY32, sdF, sdR, s);
+            skd = SketchDB{skX, sdDen, sdF, sdR, sdY32};
             std::vector<int32_t> seq(m0, -1);
             PSR_CUDA(ctx, cudaMemcpyAsync(rep_l, seq.data(), sizeof(int32_t) * m0, cudaMemcpyHostToDevice, s));
             int32_t h_bad = 0;
@@ -1194,7 +1220,10 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
                 per_sm >= 1) {
                 int sms = 0;
                 cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-                const int grid = sms * std::min(per_sm, 4);
+                // as few blocks as give every candidate a screening thread
+                // (each grid barrier costs an arrival per block), at most 4 per SM
+                const int want = (int)((count + (int64_t)sms * EVAL_THREADS - 1) / ((int64_t)sms * EVAL_THREADS));
+                const int grid = sms * std::max(1, std::min(want, std::min(per_sm, 4)));
                 unsigned int* bar = nullptr;
                 int32_t* perr = nullptr;
                 PSR_CUDA(ctx, cudaMalloc(&bar, 2 * sizeof(unsigned int)));
@@ -1291,7 +1320,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         cudaFree(fro_all);
         cudaFree(w_all);
         cudaFree(sing_all);
-        for (double* q : {skX, skY, skF, skR, sdY, sdF, sdR}) cudaFree(q);
+        for (double* q : {skX, skDen, skF, skR, sdDen, sdF, sdR}) cudaFree(q);
         cudaFree(skY32);
         cudaFree(sdY32);
         cudaFree(surv_list);
