@@ -645,23 +645,27 @@ int autotune_sweep(psr_ctx* ctx, cudaStream_t s) {
     double* z = ctx->ws.z;
     if (!r || !z) return PSR_OK;
     PSR_CUDA(ctx, cudaMemsetAsync(r, 0, sizeof(double) * (size_t)ctx->n, s));
-    cudaEvent_t e0, e1;
-    PSR_CUDA(ctx, cudaEventCreate(&e0));
-    PSR_CUDA(ctx, cudaEventCreate(&e1));
+    // five back-to-back timed applies between six events, one host wait per
+    // candidate (a wait per apply cost more than the applies)
+    constexpr int NT = 5;
+    cudaEvent_t ev[NT + 1];
+    for (auto& e : ev) PSR_CUDA(ctx, cudaEventCreate(&e));
     auto time_apply = [&](float* out_ms) -> int {
         for (int w = 0; w < 2; ++w) {
             int rc = sweep_apply_ex(ctx, r, z, nullptr, s);
             if (rc != PSR_OK) return rc;
         }
-        std::vector<float> ts;
-        for (int it = 0; it < 5; ++it) {
-            cudaEventRecord(e0, s);
+        cudaEventRecord(ev[0], s);
+        for (int it = 0; it < NT; ++it) {
             int rc = sweep_apply_ex(ctx, r, z, nullptr, s);
             if (rc != PSR_OK) return rc;
-            cudaEventRecord(e1, s);
-            cudaEventSynchronize(e1);
+            cudaEventRecord(ev[it + 1], s);
+        }
+        cudaEventSynchronize(ev[NT]);
+        std::vector<float> ts;
+        for (int it = 0; it < NT; ++it) {
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
+            cudaEventElapsedTime(&ms, ev[it], ev[it + 1]);
             ts.push_back(ms);
         }
         std::sort(ts.begin(), ts.end());
@@ -721,8 +725,7 @@ int autotune_sweep(psr_ctx* ctx, cudaStream_t s) {
         }
         if (rc == PSR_OK) rc = build_grouped_tables(ctx);
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    for (auto& e : ev) cudaEventDestroy(e);
     return rc;
 }
 
