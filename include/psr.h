@@ -182,6 +182,17 @@ int psr_get_history(psr_ctx* ctx, double* hist, int32_t cap, int32_t* len);
  * order, or NULL) and *m_p (host). */
 int psr_get_assignment(psr_ctx* ctx, int32_t* phi, int32_t* rep_ids, int32_t* m_p);
 
+/* The database of a finished setup, for reuse in a later setup of a related
+ * matrix (section 3.2, linear problem sequences: a database initialised from
+ * the previous setup; pass the entries as seed_A of psr_setup_seeded and the
+ * previous phi, from psr_get_assignment, as hints).  entries: device,
+ * m_p x p x p FP64, row-major per entry, in creation order: the patch matrix
+ * of each entry's representative, a seed entry's matrix, or an Alg. 2 mean.
+ * Setups with patches of one size built by Alg. 1 (tol > 0), seeded Alg. 1
+ * or Alg. 2 only; INVALID_ARG otherwise (tol = 0 keeps no database copy).
+ * Blocks the host until the copy is done. */
+int psr_export_database(psr_ctx* ctx, double* entries, void* stream);
+
 typedef struct {
     int32_t n, n_patches, m_p, n_groups;
     int64_t criterion_evals;      /* d(A_i, B_j) evaluations in Alg. 1 order   */

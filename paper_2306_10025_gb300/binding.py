@@ -32,7 +32,8 @@ EXPORTS = ["psr_default_opts", "psr_setup", "psr_apply", "psr_solve", "psr_get_h
            "psr_batched_inverse", "psr_criterion", "psr_spectral_norm", "psr_kernel_launches",
            "psr_setup_seeded", "psr_features", "psr_mlp_create", "psr_mlp_num_params", "psr_mlp_set_params",
            "psr_mlp_get_params", "psr_mlp_loss_grad", "psr_mlp_train_step", "psr_mlp_predict", "psr_mlp_destroy",
-           "psr_criterion_noalloc", "psr_set_kernel_timing", "psr_get_kernel_timing", "psr_setup_kmeans"]
+           "psr_criterion_noalloc", "psr_set_kernel_timing", "psr_get_kernel_timing", "psr_setup_kmeans",
+           "psr_export_database"]
 
 KT_CLASSES = ("sweep", "spmv", "mdot", "maxpy", "vec")   # PSR_KT_* in order
 
@@ -99,6 +100,7 @@ def load(path: str = LIB_PATH):
     lib.psr_get_history.argtypes = [vp, vp, i32, C.POINTER(i32)]
     lib.psr_get_assignment.argtypes = [vp, vp, vp, C.POINTER(i32)]
     lib.psr_get_stats.argtypes = [vp, C.POINTER(psr_stats)]
+    lib.psr_export_database.argtypes = [vp, vp, vp]
     lib.psr_last_error.argtypes = [vp]
     lib.psr_last_error.restype = C.c_char_p
     lib.psr_destroy.argtypes = [vp]
@@ -208,17 +210,18 @@ def psr_setup(rowptr, colidx, vals, dofs, offsets=None, uniform_size=0, opts: ps
     h = C.c_void_p()
     rc = lib.psr_setup(C.byref(A), C.byref(P), C.byref(o), _stream(stream), C.byref(h))
     _check(rc, None)
-    return Context(h, A.n, P.n_patches, o)
+    return Context(h, A.n, P.n_patches, o, P.uniform_size)
 
 
 class Context:
     """Owns a psr_ctx (library-owned device storage)."""
 
-    def __init__(self, handle, n, n_patches, opts):
+    def __init__(self, handle, n, n_patches, opts, p=0):
         self.h = handle
         self.n = n
         self.n_patches = n_patches
         self.opts = opts
+        self.p = p                     # patch size when uniform, else 0
 
     def apply(self, r, z, stream=None):
         import torch
@@ -252,6 +255,18 @@ class Context:
         reps = torch.empty(max(m.value, 1), dtype=torch.int32, device="cuda")
         _check(load().psr_get_assignment(self.h, _ptr(phi), _ptr(reps), C.byref(m)), self.h)
         return phi, reps[: m.value], m.value
+
+    def export_database(self, stream=None):
+        """psr_export_database: the entries' patch matrices (m_p x p x p, FP64)
+        of a one-size setup, for psr_setup_seeded of a related matrix."""
+        import torch
+        m = C.c_int32()
+        _check(load().psr_get_assignment(self.h, None, None, C.byref(m)), self.h)
+        if self.p <= 0:
+            raise ValueError("export_database needs patches of one size")
+        out = torch.empty((m.value, self.p, self.p), dtype=torch.float64, device="cuda")
+        _check(load().psr_export_database(self.h, _ptr(out), _stream(stream)), self.h)
+        return out
 
     def stats(self) -> dict:
         st = psr_stats()
@@ -297,7 +312,7 @@ def psr_setup_seeded(rowptr, colidx, vals, dofs, uniform_size, seed_A, hints=Non
     rc = lib.psr_setup_seeded(C.byref(A), C.byref(P), C.byref(o), _ptr(seed_A), seed_A.shape[0], _ptr(hints),
                               _stream(stream), C.byref(h))
     _check(rc, None)
-    return Context(h, A.n, P.n_patches, o)
+    return Context(h, A.n, P.n_patches, o, P.uniform_size)
 
 
 def psr_setup_kmeans(rowptr, colidx, vals, dofs, uniform_size, init, max_iter=100, opts: psr_opts | None = None,
@@ -314,7 +329,7 @@ def psr_setup_kmeans(rowptr, colidx, vals, dofs, uniform_size, init, max_iter=10
     rc = lib.psr_setup_kmeans(C.byref(A), C.byref(P), C.byref(o), init.numel(), _ptr(init), max_iter,
                               _stream(stream), C.byref(h))
     _check(rc, None)
-    return Context(h, A.n, P.n_patches, o)
+    return Context(h, A.n, P.n_patches, o, P.uniform_size)
 
 
 def psr_features(A, coef, X, stream=None):

@@ -214,7 +214,8 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
         ctx->stats.t_extract = seconds_since(t0);
         // --- a2 / a3: database and assignment
         CK(cudaMalloc(&ctx->phi, sizeof(int32_t) * (size_t)np));
-        CK(cudaMalloc(&ctx->rep_ids, sizeof(int32_t) * (size_t)np));
+        // seed entries come on top of at most one new entry per patch
+        CK(cudaMalloc(&ctx->rep_ids, sizeof(int32_t) * ((size_t)np + (size_t)std::max(m0, 0))));
         t0 = std::chrono::steady_clock::now();
         if (mode.km_m > 0) {
             rc = run_kmeans(ctx, s, mode.km_m, *mode.km_init, mode.km_iter);
@@ -455,6 +456,19 @@ int psr_get_assignment(psr_ctx* ctx, int32_t* phi, int32_t* rep_ids, int32_t* m_
     if (phi) PSR_CUDA(ctx, cudaMemcpy(phi, ctx->phi, sizeof(int32_t) * (size_t)ctx->n_patches, cudaMemcpyDeviceToDevice));
     if (rep_ids && ctx->m_p > 0)
         PSR_CUDA(ctx, cudaMemcpy(rep_ids, ctx->rep_ids, sizeof(int32_t) * (size_t)ctx->m_p, cudaMemcpyDeviceToDevice));
+    return PSR_OK;
+}
+
+int psr_export_database(psr_ctx* ctx, double* entries, void* stream) {
+    if (!ctx || !entries) { set_error(ctx, "NULL argument"); return PSR_ERR_INVALID_ARG; }
+    if (ctx->groups.size() != 1 || !ctx->groups[0].dbA) {
+        set_error(ctx, "no database copy: export needs one patch size and an Alg. 1, seeded or Alg. 2 setup");
+        return PSR_ERR_INVALID_ARG;
+    }
+    const Group& G = ctx->groups[0];
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    PSR_CUDA(ctx, cudaMemcpyAsync(entries, G.dbA, sizeof(double) * (size_t)G.m * G.p * G.p, cudaMemcpyDeviceToDevice, s));
+    PSR_CUDA(ctx, cudaStreamSynchronize(s));
     return PSR_OK;
 }
 

@@ -1311,6 +1311,10 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
             const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 152 * 16));
             count_launch();
             k_gather_db<<<gb, 256, 0, s>>>(db.Binv, m0, Ball, rep_l, G.m, p, Bdb);
+            // the entries' patch matrices, kept for reuse by a later setup
+            PSR_CUDA(ctx, cudaMalloc(&G.dbA, sizeof(double) * (size_t)std::max(G.m, 1) * p * p));
+            count_launch();
+            k_gather_db<<<gb, 256, 0, s>>>(db.A, m0, Ag, rep_l, G.m, p, G.dbA);
         }
         PSR_CUDA(ctx, cudaStreamSynchronize(s));
         G.h_rep.assign(hrep.begin(), hrep.end());   // local patch of each entry, -1 for seed entries

@@ -131,17 +131,18 @@ int run_kmeans(psr_ctx* ctx, cudaStream_t s, int m, const std::vector<int32_t>& 
                 break;
             }
     }
-    cudaFree(B);
     cudaFree(d_init);
     cudaFree(changes);
     cudaFree(moff);
     cudaFree(mlist);
     cudaFree(sing);
     if (rc != PSR_OK) {
+        cudaFree(B);
         cudaFree(phi);
         cudaFree(Bdb);
         return rc;
     }
+    G.dbA = B;                      // the means: the entries' matrices, kept for reuse
     G.m = m;
     G.sphi = phi;
     G.rinv = Bdb;

@@ -78,6 +78,7 @@ struct Group {
     int32_t* sdofs = nullptr;      // [count * p] DOFs in sorted order
     int32_t* sphi = nullptr;       // [count] group-local entry of each sorted patch
     void* rinv = nullptr;          // [m * p * p] inverses in storage precision
+    double* dbA = nullptr;         // [m * p * p] patch matrix of each entry (Alg. 1 / seeded / Alg. 2), for reuse
     int64_t mat_off = 0;           // offset of the group's patches in A_ext (doubles)
     // tiles: (entry, first sorted patch, count)
     int32_t* tiles = nullptr;      // [ntiles * 3]
@@ -152,7 +153,7 @@ struct psr_ctx {
     double* W = nullptr;          // scale applied at the scatter
     double* Wg = nullptr;         // scale applied at the gather (SYM) or nullptr
     int32_t* phi = nullptr;       // device n_patches
-    int32_t* rep_ids = nullptr;   // device n_patches (first m_p used)
+    int32_t* rep_ids = nullptr;   // device n_patches + seed entries (first m_p used)
     int32_t m_p = 0;
     std::vector<int32_t> h_rep_ids;
     std::vector<psr::Group> groups;

@@ -843,6 +843,7 @@ void free_sweep(psr_ctx* ctx) {
         cudaFree(G.tiles);
         cudaFree(G.sdofs_t);
         cudaFree(G.wtiles);
+        cudaFree(G.dbA);
         if (G.rinv && !(ctx->A_ext && reinterpret_cast<double*>(G.rinv) >= ctx->A_ext &&
                          reinterpret_cast<double*>(G.rinv) < ctx->A_ext + ctx->A_ext_len))
             cudaFree(G.rinv);
