@@ -920,7 +920,7 @@ __device__ __forceinline__ void block_partials_df(float (&ah)[NV], float (&al)[N
 template <int NV, bool PROJ>
 __device__ __forceinline__ void pair_update(const float2* __restrict__ Vs, float2* __restrict__ Ws, int n, int nv,
                                             const float2* hs, float scf, float (&ah)[NV], float (&al)[NV],
-                                            double& accw) {
+                                            double& accw, float* nh2 = nullptr) {
     for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += gridDim.x * KT) {
         // all loads first (rows past nv read as zero, their coefficients are
         // zero), then the arithmetic without branches
@@ -946,10 +946,50 @@ __device__ __forceinline__ void pair_update(const float2* __restrict__ Vs, float
         if (PROJ) {
 #pragma unroll
             for (int i = 0; i < NV; ++i) df_fma(ah[i], al[i], vv[i].x, vv[i].y, nh, nl);
+            if (nh2) df_fma(nh2[0], nh2[1], nh, nl, nh, nl);     // ||w'||^2 on pairs
         } else {
             const double wd = (double)nh + (double)nl;
             accw = fma(wd, wd, accw);
         }
+    }
+}
+
+// The last update fused with the normalisation when ||w'|| is known before it:
+// w' <- (scf w' - V hs) * inv, written as the pair Ws and the FP64 w.  The
+// product by inv on pairs when pair_scale, else in FP64.
+template <int NV>
+__device__ __forceinline__ void pair_update_normalize(const float2* __restrict__ Vs, float2* __restrict__ Ws,
+                                                      double* __restrict__ w, int n, int nv, const float2* hs,
+                                                      float scf, double inv, bool pair_scale) {
+    const float2 is = split_f64(pair_scale ? inv : 1.0);
+    for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += gridDim.x * KT) {
+        float2 vv[NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) vv[c] = (c < nv) ? Vs[(int64_t)c * n + e] : make_float2(0.f, 0.f);
+        float2 q = Ws[e];
+        q.x *= scf;
+        q.y *= scf;
+        float ch[4] = {0.f, 0.f, 0.f, 0.f}, cl[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < NV; ++c) df_fma(ch[c & 3], cl[c & 3], hs[c].x, hs[c].y, vv[c].x, vv[c].y);
+        df_add(ch[0], cl[0], ch[1], cl[1]);
+        df_add(ch[2], cl[2], ch[3], cl[3]);
+        df_add(ch[0], cl[0], ch[2], cl[2]);
+        float t, d, nh, nl;
+        two_sum(q.x, -ch[0], t, d);
+        d = __fadd_rn(d, __fsub_rn(q.y, cl[0]));
+        fast_two_sum(t, d, nh, nl);
+        float2 v;
+        if (pair_scale) {
+            const float p = __fmul_rn(nh, is.x);
+            const float pe = __fmaf_rn(nh, is.x, -p);
+            const float c2 = __fmaf_rn(nh, is.y, __fmul_rn(nl, is.x));
+            fast_two_sum(p, __fadd_rn(pe, c2), v.x, v.y);
+        } else {
+            v = split_f64(((double)nh + (double)nl) * inv);
+        }
+        Ws[e] = v;
+        w[e] = (double)v.x + (double)v.y;
     }
 }
 
@@ -979,6 +1019,7 @@ __global__ void __launch_bounds__(KT, 1) k_arnoldi(const double* __restrict__ V,
     __shared__ float2 sh_hs[NV];
     __shared__ double shw[32];
     __shared__ double s_w2;
+    __shared__ double s_h2;
     __shared__ int s_reorth;
     __shared__ double s_col[NV + 1];                  // block 0: column j of H
     __shared__ double s_rot[2 * NV];                  // block 0: previous rotations
@@ -1068,7 +1109,10 @@ __global__ void __launch_bounds__(KT, 1) k_arnoldi(const double* __restrict__ V,
     if (threadIdx.x < 32) {                           // ||h||^2 by warp 0 (sh_h is zero past nv)
         const double hq = threadIdx.x < NV ? sh_h[threadIdx.x] : 0.0;
         const double h2 = warp_sum(hq * hq);
-        if (threadIdx.x == 0) s_reorth = (s_w2 - h2 < 0.5 * s_w2) ? 1 : 0;
+        if (threadIdx.x == 0) {
+            s_reorth = (s_w2 - h2 < 0.5 * s_w2) ? 1 : 0;
+            s_h2 = h2;
+        }
     }
     __syncthreads();
     const bool reorth = s_reorth != 0;
@@ -1083,11 +1127,27 @@ __global__ void __launch_bounds__(KT, 1) k_arnoldi(const double* __restrict__ V,
 #pragma unroll
         for (int i = 0; i < NV; ++i) ah[i] = al[i] = 0.f;
         double accw = 0.0;
+        // ||w'||^2 of the vector left by the last update.  It is known before
+        // that update from ||x||^2 - ||V^T x||^2 (x the vector it starts
+        // from, V orthonormal): without a second pass because the
+        // Kahan-Parlett test kept more than half of ||w||^2, with one when
+        // the second coefficients are below a tenth of ||x|| (the usual
+        // case: twice is enough).  Then the last update and the
+        // normalisation are one pass and the step saves a grid barrier.
+        double ws2 = 0.0;
+        bool known = false;
+        float last_scf = scf;
         if (reorth) {
-            pair_update<NV, true>(Vs, Ws, n, nv, sh_hs, scf, ah, al, accw);
+            float n2[2] = {0.f, 0.f};
+            pair_update<NV, true>(Vs, Ws, n, nv, sh_hs, scf, ah, al, accw, n2);
             block_partials_df<NV>(ah, al, nv, P2, sh);
+            {
+                const double bs = block_sum_kt((double)n2[0] + (double)n2[1], shw);
+                if (threadIdx.x == 0) P2[(int64_t)NV * G + blockIdx.x] = bs;
+            }
             grid_barrier(bar, kd.ictl);
-            const double v2 = final_partials<NV>(P2, nv, G);      // 2^k h2
+            double x2;                                            // ||w1'||^2
+            const double v2 = final_partials_w2<NV>(P2, nv, G, shw, x2);      // 2^k h2
             __syncthreads();                                      // sh_hs of pass 2 fully read
             if (threadIdx.x % T == 0) {
                 sh_h[threadIdx.x / T] = ldexp(v2, -k);
@@ -1095,27 +1155,35 @@ __global__ void __launch_bounds__(KT, 1) k_arnoldi(const double* __restrict__ V,
             }
             __syncthreads();
             if (blockIdx.x == 0 && threadIdx.x < nv) s_col[threadIdx.x] += sh_h[threadIdx.x];
-            pair_update<NV, false>(Vs, Ws, n, nv, sh_hs, 1.f, ah, al, accw);
-            const double bs = block_sum_kt(accw, shw);
-            if (threadIdx.x == 0) P3[(int64_t)NV * G + blockIdx.x] = bs;
-            grid_barrier(bar, kd.ictl);
-            const double t = norm_total(P3 + (int64_t)NV * G, G, shw);
-            if (threadIdx.x == 0) s_w2 = t;
+            if (threadIdx.x < 32) {                               // ||2^k h2||^2 by warp 0
+                const double hq = threadIdx.x < NV ? sh_h[threadIdx.x] : 0.0;
+                const double q2 = warp_sum(hq * hq);
+                if (threadIdx.x == 0) s_h2 = ldexp(q2, 2 * k);
+            }
+            __syncthreads();
+            last_scf = 1.f;
+            // pairs carry ||w1'||^2 accurately only well inside the FP32 range
+            if (x2 >= 0x1p-60 && s_h2 <= 0.01 * x2) {
+                ws2 = x2 - s_h2;
+                known = true;
+            } else {
+                pair_update<NV, false>(Vs, Ws, n, nv, sh_hs, 1.f, ah, al, accw);
+                const double bs = block_sum_kt(accw, shw);
+                if (threadIdx.x == 0) P3[(int64_t)NV * G + blockIdx.x] = bs;
+                grid_barrier(bar, kd.ictl);
+                ws2 = norm_total(P3 + (int64_t)NV * G, G, shw);
+            }
         } else {
-            pair_update<NV, false>(Vs, Ws, n, nv, sh_hs, scf, ah, al, accw);
-            const double bs = block_sum_kt(accw, shw);
-            if (threadIdx.x == 0) P2[(int64_t)NV * G + blockIdx.x] = bs;
-            grid_barrier(bar, kd.ictl);
-            const double t = norm_total(P2 + (int64_t)NV * G, G, shw);
-            if (threadIdx.x == 0) s_w2 = t;
+            ws2 = ldexp(s_w2 - s_h2, 2 * k);              // > ||w'||^2 / 2 by the test
+            known = true;
         }
-        __syncthreads();
-        const double ws2 = s_w2;                      // ||w'||^2
         // normalise: v = w' / ||w'|| on pairs (inverse within FP32 range), else in FP64
         const double hn = sqrt(ws2);
         hn_w = ldexp(hn, -k);                         // exact: sqrt(2^2k x) = 2^k sqrt(x)
         const double inv = hn != 0.0 ? 1.0 / hn : 1.0;
-        if (inv <= 0x1p100) {
+        if (known) {
+            pair_update_normalize<NV>(Vs, Ws, w, n, nv, sh_hs, last_scf, inv, inv <= 0x1p100);
+        } else if (inv <= 0x1p100) {
             const float2 is = split_f64(inv);
             for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += G * KT) {
                 const float2 q = Ws[e];
@@ -1539,12 +1607,12 @@ static int enqueue_arnoldi(psr_ctx* ctx, KDims kd, int j, double* Vn, cudaStream
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    // bytes: pass 1 reads w and j+1 pair rows and writes the pair of w, each
-    // update reads and writes that pair and reads j+1 rows, the normalisation
-    // reads the pair and writes it and V_{j+1}.  FP64 flops of the pair path
-    // (the dots and updates run on FP32 pairs): ||w||^2 and the split in
-    // pass 1, the FP64 value and its square in the last update, the FP64
-    // value of the normalised pair.
+    // bytes: pass 1 reads w and j+1 pair rows and writes the pair of w; the
+    // second pass (when taken) reads and writes that pair and reads j+1 rows;
+    // the last update, fused with the normalisation, reads the pair and j+1
+    // rows and writes the pair and V_{j+1}.  FP64 flops of the pair path (the
+    // dots and updates run on FP32 pairs): ||w||^2 and the split in pass 1,
+    // the FP64 value of the normalised pair.
     // In FP64 (PSR_ORTHO_FP64): the projection reads w and j+1 rows, each
     // update j+1 rows and w twice, the normalisation writes w and its pair.
     const int fp64 = ctx->opts.ortho == PSR_ORTHO_FP64 ? 1 : 0;
@@ -1552,7 +1620,7 @@ static int enqueue_arnoldi(psr_ctx* ctx, KDims kd, int j, double* Vn, cudaStream
         KT_BEGIN(PSR_KT_MDOT, j, ((j + 2) + (j + 3) + 3) * vb, 4.0 * n * (j + 2) + 3.0 * n);
         KT_REORTH((j + 3) * vb, 4.0 * n * (j + 1));
     } else {
-        KT_BEGIN(PSR_KT_MDOT, j, ((j + 3) + (j + 3) + 3) * vb, 7.0 * n);
+        KT_BEGIN(PSR_KT_MDOT, j, ((j + 3) + (j + 4)) * vb, 4.0 * n);
         KT_REORTH((j + 3) * vb, 0.0);
     }
     count_launch();
