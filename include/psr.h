@@ -116,6 +116,18 @@ typedef struct {
  * AUTO orthogonalisation. */
 void psr_default_opts(psr_opts* o);
 
+/* A rectangular CSR matrix (the interpolation P0 of Eq. 2), device pointers. */
+typedef struct {
+    int32_t        n_rows;
+    int32_t        n_cols;
+    int64_t        nnz;
+    const int32_t* rowptr;   /* device, n_rows+1 */
+    const int32_t* colidx;   /* device, nnz, in [0, n_cols) */
+    const double*  vals;     /* device, nnz */
+} psr_csr_rect;
+
+#define PSR_COARSE_MAX 16384       /* coarse dimension n0 (A0^-1 is kept dense) */
+
 /* ---- whole method ------------------------------------------------------- */
 
 /* Setup of M~^{-1} (Eq. 3): validate the CSR and map, extract every A_k,
@@ -181,6 +193,18 @@ int psr_get_history(psr_ctx* ctx, double* hist, int32_t cap, int32_t* len);
  * rep_ids (device, m_p, patch index of each database entry in creation
  * order, or NULL) and *m_p (host). */
 int psr_get_assignment(psr_ctx* ctx, int32_t* phi, int32_t* rep_ids, int32_t* m_p);
+
+/* Two-level combination preconditioner (Eq. 2): after this call psr_apply
+ * and psr_solve use M_combo^-1 = M^-1 + P0 A0^-1 R0 with M^-1 the patch method
+ * (Eq. 3), R0 = P0^T and A0 = R0 A P0 formed here and inverted (a direct
+ * coarse solve in place of the first-order AMG, as in Experiment 1).
+ * P0: device CSR, n x n0 (n0 <= PSR_COARSE_MAX), copied; for Experiment 1
+ * the bilinear interpolation from the mesh vertices to the high-order nodes.
+ * A0 must be symmetric positive definite (A SPD, P0 of full rank): its
+ * Gauss-Jordan inverse takes no pivots.  The coarse term is added after the
+ * patch sweep without a weight.  Errors: INVALID_ARG (shape, indices), OOM,
+ * CUDA.  Replaces an earlier coarse space; blocks the host. */
+int psr_set_coarse(psr_ctx* ctx, const psr_csr_rect* P0, void* stream);
 
 /* The database of a finished setup, for reuse in a later setup of a related
  * matrix (section 3.2, linear problem sequences: a database initialised from

@@ -602,3 +602,30 @@ def kmeans_l1(A, init, max_iter=100, near_tie_rel=1e-9):
                 B[j] = acc / members.size
     Binv, singular = lu_inverse(B)
     return {"phi": phi, "means": B, "Binv": Binv, "singular": singular, "sweeps": sweeps, "near_ties": near}
+
+
+# ---------------------------------------------------------------------------
+# Two-level combination preconditioner (Eq. 2, Experiment 1):
+#   M_combo^{-1} = M^{-1} + P0 A0^{-1} R0,  R0 = P0^T,  A0 = R0 A P0,
+# M^{-1} the patch method of Eq. (3), P0 the interpolation from the
+# low-order representation, and a direct solve with A0 in place of AMG (as
+# in Experiment 1).  A0 is formed with library sparse products and inverted
+# with LAPACK (np.linalg.inv) once; the apply follows Eq. (2) term by term.
+# ---------------------------------------------------------------------------
+
+def coarse_operator(rowptr, colidx, vals, n, P0):
+    """A0 = P0^T A P0 (dense n0 x n0) with P0 = (rowptr, colidx, vals, n0)
+    an n x n0 CSR."""
+    import scipy.sparse as sp
+    A = sp.csr_matrix((vals, colidx, rowptr), shape=(n, n))
+    prow, pcol, pval, n0 = P0
+    Pm = sp.csr_matrix((pval, pcol, prow), shape=(n, n0))
+    return np.asarray((Pm.T @ (A @ Pm)).todense(), dtype=np.float64)
+
+
+def combo_apply(r, dofs, Binv, phi, W, weighting, P0, A0inv):
+    """Eq. (2): z = M^{-1} r + P0 (A0^{-1} (P0^T r))."""
+    import scipy.sparse as sp
+    prow, pcol, pval, n0 = P0
+    Pm = sp.csr_matrix((pval, pcol, prow), shape=(len(r), n0))
+    return apply(r, dofs, Binv, phi, W, weighting) + Pm @ (A0inv @ (Pm.T @ np.asarray(r, dtype=np.float64)))

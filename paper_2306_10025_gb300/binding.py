@@ -33,7 +33,7 @@ EXPORTS = ["psr_default_opts", "psr_setup", "psr_apply", "psr_solve", "psr_get_h
            "psr_setup_seeded", "psr_features", "psr_mlp_create", "psr_mlp_num_params", "psr_mlp_set_params",
            "psr_mlp_get_params", "psr_mlp_loss_grad", "psr_mlp_train_step", "psr_mlp_predict", "psr_mlp_destroy",
            "psr_criterion_noalloc", "psr_set_kernel_timing", "psr_get_kernel_timing", "psr_setup_kmeans",
-           "psr_export_database"]
+           "psr_export_database", "psr_set_coarse"]
 
 KT_CLASSES = ("sweep", "spmv", "mdot", "maxpy", "vec")   # PSR_KT_* in order
 
@@ -60,6 +60,11 @@ class psr_opts(C.Structure):
                 ("maxit", C.c_int32), ("use_graph", C.c_int32), ("sweep_kernel", C.c_int32),
                 ("autotune", C.c_int32), ("symmetrize", C.c_int32), ("use_mlp", C.c_int32),
                 ("ortho", C.c_int32)]
+
+
+class psr_csr_rect(C.Structure):
+    _fields_ = [("n_rows", C.c_int32), ("n_cols", C.c_int32), ("nnz", C.c_int64), ("rowptr", C.c_void_p),
+                ("colidx", C.c_void_p), ("vals", C.c_void_p)]
 
 
 class psr_solve_info(C.Structure):
@@ -101,6 +106,7 @@ def load(path: str = LIB_PATH):
     lib.psr_get_assignment.argtypes = [vp, vp, vp, C.POINTER(i32)]
     lib.psr_get_stats.argtypes = [vp, C.POINTER(psr_stats)]
     lib.psr_export_database.argtypes = [vp, vp, vp]
+    lib.psr_set_coarse.argtypes = [vp, C.POINTER(psr_csr_rect), vp]
     lib.psr_last_error.argtypes = [vp]
     lib.psr_last_error.restype = C.c_char_p
     lib.psr_destroy.argtypes = [vp]
@@ -255,6 +261,16 @@ class Context:
         reps = torch.empty(max(m.value, 1), dtype=torch.int32, device="cuda")
         _check(load().psr_get_assignment(self.h, _ptr(phi), _ptr(reps), C.byref(m)), self.h)
         return phi, reps[: m.value], m.value
+
+    def set_coarse(self, rowptr, colidx, vals, n0, stream=None):
+        """psr_set_coarse: the two-level term P0 A0^-1 P0^T of Eq. (2) with
+        P0 an n x n0 CSR (device int32 rowptr / colidx, float64 vals)."""
+        import torch
+        _need(rowptr, torch.int32, "rowptr")
+        _need(colidx, torch.int32, "colidx")
+        _need(vals, torch.float64, "vals")
+        P0 = psr_csr_rect(self.n, int(n0), colidx.numel(), _ptr(rowptr), _ptr(colidx), _ptr(vals))
+        _check(load().psr_set_coarse(self.h, C.byref(P0), _stream(stream)), self.h)
 
     def export_database(self, stream=None):
         """psr_export_database: the entries' patch matrices (m_p x p x p, FP64)

@@ -56,6 +56,7 @@ static void destroy_ctx(psr_ctx* ctx) {
     cudaGetDevice(&cur);
     if (cur != ctx->device) cudaSetDevice(ctx->device);
     free_sweep(ctx);
+    coarse_free(ctx);
     krylov_free(ctx);
     cudaFree(ctx->rowptr);
     cudaFree(ctx->colidx);

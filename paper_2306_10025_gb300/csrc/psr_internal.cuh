@@ -136,6 +136,10 @@ struct KtMark {
 
 }  // namespace psr
 
+namespace psr {
+struct Coarse;
+}
+
 struct psr_ctx {
     int device = 0;
     psr_opts opts{};
@@ -165,6 +169,7 @@ struct psr_ctx {
     std::string err;
     // graphs
     cudaGraphExec_t g_cycle = nullptr;   // one FGMRES cycle / CG block
+    psr::Coarse* coarse = nullptr;       // two-level term of Eq. (2), psr_set_coarse
     cudaStream_t g_stream = nullptr;
     int graph_block = 0;
     // grouped persistent sweep
@@ -215,6 +220,8 @@ int autotune_sweep(psr_ctx* ctx, cudaStream_t s);
 int sweep_apply_ex(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s);
 int build_grouped_tables(psr_ctx* ctx);
 void free_sweep(psr_ctx* ctx);
+int coarse_apply(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s);
+void coarse_free(psr_ctx* ctx);
 
 // sweep_tc.cu (BF16 entries on tcgen05 tensor cores)
 int tc_pad(int p);

@@ -145,6 +145,100 @@ def poisson2d_q2(N: int = 16, rho: float = 1.0) -> Problem:
                    meta={"N": N, "p_s": 9, "dirichlet": bnd})
 
 
+def _qp_cell_nodes_2d(N: int, p: int) -> np.ndarray:
+    """(N*N, (p+1)^2) node ids of Q_p cells on the (Np+1)^2 node grid; cells
+    x-fastest, local nodes x-fastest."""
+    cx, cy = np.meshgrid(np.arange(N), np.arange(N), indexing="xy")
+    cx = cx.reshape(-1)
+    cy = cy.reshape(-1)
+    stride = N * p + 1
+    n1 = p + 1
+    out = np.zeros((N * N, n1 * n1), dtype=np.int64)
+    for b in range(n1):
+        for a in range(n1):
+            out[:, a + n1 * b] = (p * cx + a) + stride * (p * cy + b)
+    return out
+
+
+def smooth2d_qp(N: int = 60, p: int = 2) -> Problem:
+    """Experiment 1 of the paper (section 4): -div(rho grad u) = f on the unit
+    square, rho = sin^2(pi x) sin^2(pi y) + 0.1 (evaluated at the quadrature
+    points), f such that u = sin(pi x) sin(pi y), homogeneous Dirichlet
+    (identity rows), Q_p elements (equispaced nodes) on a uniform N x N mesh;
+    one patch per cell ((p+1)^2 DOFs).
+
+    meta["P0"]: the linear (bilinear) interpolation from the (N+1)^2 mesh
+    vertices to the (Np+1)^2 nodes, which the paper's two-level preconditioner
+    uses with R0 = P0^T, as (rowptr, colidx, vals, n0) of an n x n0 CSR;
+    meta["b"]: the load vector of f (0 on Dirichlet rows); meta["u_nodes"]:
+    the exact solution at the nodes."""
+    nq = p + 2
+    xq, wq = fem.gauss_legendre_01(nq)
+    phi, dphi, w = fem.tensor_basis(p, 2, nq)
+    h = 1.0 / N
+    nb = (p + 1) ** 2
+    nqt = nq * nq
+    qx = np.array([xq[q % nq] for q in range(nqt)])
+    qy = np.array([xq[q // nq] for q in range(nqt)])
+    edofs = _qp_cell_nodes_2d(N, p)
+    cx = np.tile(np.arange(N), N)
+    cy = np.repeat(np.arange(N), N)
+    X = (cx[:, None] + qx[None, :]) * h                 # (nc, nqt) physical points
+    Y = (cy[:, None] + qy[None, :]) * h
+    sx, sy = np.sin(np.pi * X), np.sin(np.pi * Y)
+    kx, ky = np.cos(np.pi * X), np.cos(np.pi * Y)
+    rho = sx ** 2 * sy ** 2 + 0.1
+    # f = -(grad rho . grad u + rho lap u), u = sin sin, lap u = -2 pi^2 u
+    drx = 2.0 * np.pi * sx * kx * sy ** 2
+    dry = 2.0 * np.pi * sx ** 2 * sy * ky
+    ux = np.pi * kx * sy
+    uy = np.pi * sx * ky
+    f = -(drx * ux + dry * uy) + rho * 2.0 * np.pi ** 2 * sx * sy
+    # element matrices: sum_q w_q rho_q (dphi_x dphi_x + dphi_y dphi_y) (h^2 / h^2)
+    wr = rho * w[None, :]
+    Ke = np.einsum("cq,aq,bq->cab", wr, dphi[0], dphi[0]) + np.einsum("cq,aq,bq->cab", wr, dphi[1], dphi[1])
+    Ke = 0.5 * (Ke + np.transpose(Ke, (0, 2, 1)))
+    fe = np.einsum("cq,aq->ca", f * w[None, :], phi) * (h * h)
+    nn = N * p + 1
+    n = nn * nn
+    bnd = _boundary_nodes_2d(nn, nn)
+    rowptr, colidx, vals = fem.assemble_csr(n, edofs, Ke, bnd)
+    b = np.zeros(n)
+    np.add.at(b, edofs.reshape(-1), fe.reshape(-1))
+    b[bnd] = 0.0
+    off, flat = _uniform_patches(edofs)
+    # P0: node (i, j) of the fine grid from the vertices of the coarse cell
+    # holding it, bilinear weights; exact zeros dropped
+    ii, jj = np.meshgrid(np.arange(nn), np.arange(nn), indexing="xy")
+    ii, jj = ii.reshape(-1), jj.reshape(-1)
+    ci = np.minimum(ii // p, N - 1)
+    cj = np.minimum(jj // p, N - 1)
+    s_ = (ii - ci * p) / p
+    t_ = (jj - cj * p) / p
+    nv = N + 1
+    cols = [ci + nv * cj, ci + 1 + nv * cj, ci + nv * (cj + 1), ci + 1 + nv * (cj + 1)]
+    wts = [(1 - s_) * (1 - t_), s_ * (1 - t_), (1 - s_) * t_, s_ * t_]
+    rows_l, cols_l, vals_l = [], [], []
+    for cc, ww in zip(cols, wts):
+        m = ww != 0.0
+        rows_l.append(np.flatnonzero(m))
+        cols_l.append(cc[m])
+        vals_l.append(ww[m])
+    r_ = np.concatenate(rows_l)
+    c_ = np.concatenate(cols_l)
+    v_ = np.concatenate(vals_l)
+    order = np.lexsort((c_, r_))
+    r_, c_, v_ = r_[order], c_[order], v_[order]
+    prow = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(prow, r_ + 1, 1)
+    prow = np.cumsum(prow)
+    u_nodes = np.sin(np.pi * ii / (nn - 1)) * np.sin(np.pi * jj / (nn - 1))
+    return Problem(f"smooth2d_q{p}_N{N}", n, rowptr, colidx, vals, off, flat, ~bnd,
+                   symmetric=True, krylov="fgmres", weighting="left",
+                   meta={"N": N, "p": p, "p_s": nb, "dirichlet": bnd, "b": b, "u_nodes": u_nodes,
+                         "P0": (prow.astype(np.int32), c_.astype(np.int32), v_.astype(np.float64), nv * nv)})
+
+
 def stokes2d_q2q1(N: int = 128, ratio: float = 1.05) -> Problem:
     """2D Taylor-Hood Stokes [K B^T; B 0] on an N x N mesh graded in y."""
     Kdir, _ = fem.reference_matrices(2, 2, 3)
@@ -379,4 +473,5 @@ BUILDERS = {
     "stokes2d_q2q1": stokes2d_q2q1,
     "nedelec3d": nedelec3d,
     "diffusion3d_q2": diffusion3d_q2,
+    "smooth2d_qp": smooth2d_qp,
 }

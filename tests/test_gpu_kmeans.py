@@ -100,3 +100,27 @@ def test_kmeans_solve_converges(lib):
     x1 = torch.zeros_like(x)
     info1 = c1.solve(b, x1)
     assert info["converged"] and abs(info["iterations"] - info1["iterations"]) <= 1
+
+
+def test_kmeans_bootstrapped_from_alg1(lib):
+    """Bootstrapping (section 3.2): the representatives of Alg. 1 are the
+    initial means of Alg. 2; here 48 of 216 patches change cluster over
+    three sweeps, bit for bit as in the oracle."""
+    pr = P.diffusion3d_q2(6, sigma=0.5, corr_len=3.0, seed=3)
+    A = O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d())
+    r1 = O.alg1(A, 0.2)
+    assert r1["near_ties"] == []
+    rp, ci, va = dev(pr.rowptr, torch.int32), dev(pr.colidx, torch.int32), dev(pr.vals, torch.float64)
+    c1 = lib.psr_setup(rp, ci, va, dev(pr.patch_dofs, torch.int32), uniform_size=pr.uniform_size,
+                       opts=lib.make_opts(tol=0.2, weighting="sym", krylov="cg"))
+    _, reps, m = c1.assignment()
+    assert np.array_equal(reps.cpu().numpy(), r1["reps"])
+    ref = O.kmeans_l1(A, r1["reps"])
+    assert ref["near_ties"] == [] and ref["sweeps"] == 3
+    ctx = kmeans_ctx(lib, pr, reps.cpu().numpy().astype(np.int32), weighting="sym", krylov="cg")
+    phi, _, mk = ctx.assignment()
+    assert mk == m and np.array_equal(phi.cpu().numpy(), ref["phi"])
+    assert ctx.stats()["rounds"] == ref["sweeps"]
+    assert int((ref["phi"] != r1["phi"]).sum()) == 48
+    for c in (c1, ctx):
+        c.destroy()
