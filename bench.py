@@ -91,6 +91,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--apply-reps", type=int, default=200)
     ap.add_argument("--mlp", action="store_true", help="learned-assignment gain on the 3D lognormal workload")
+    ap.add_argument("--exp1", action="store_true",
+                    help="Experiment 1: iterations of FGMRES(20) + M_combo for Q2..Q5 (Table 1 of the paper)")
     ap.add_argument("--tol-sweep", action="store_true",
                     help="compressibility curve: m_p, setup and residual per criterion tolerance and precision")
     ap.add_argument("--mlp-n", type=int, default=32)
@@ -571,8 +573,60 @@ def run_tol_sweep(args, cfg, name):
                       "rows": rows}))
 
 
+def run_exp1(args):
+    """Experiment 1 of the paper (section 4): 60 x 60 mesh, Q_p for p = 2..5,
+    rho = sin^2(pi x) sin^2(pi y) + 0.1, FGMRES(20) with the two-level
+    M_combo (Eq. 2, direct coarse solve), x0 = 0, 1e-8.  For every p the full
+    storage and Alg. 1 at a few tolerances: database entries, iterations,
+    setup (with the coarse operator) and solve times.  The paper's Table 1
+    (Matlab GMRES(20)): 11, 12, 14, 15 iterations with full storage for
+    p = 2..5; 12, 12, 14, 16 with its best algorithms at 34-35 entries."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2306_10025_gb300 as L
+    dev = torch.device("cuda", 0)
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    rows = []
+    for pdeg in (2, 3, 4, 5):
+        pr = build_problem({"builder": "smooth2d_qp", "kw": {"N": 60, "p": pdeg}})
+        rp, ci, va = t(pr.rowptr, torch.int32), t(pr.colidx, torch.int32), t(pr.vals, torch.float64)
+        dofs = t(pr.patch_dofs, torch.int32)
+        prow, pcol, pval, n0 = pr.meta["P0"]
+        P0 = (t(prow, torch.int32), t(pcol, torch.int32), t(pval, torch.float64), n0)
+        b = t(pr.meta["b"], torch.float64)
+        tols = (0.0,) if pr.uniform_size > 32 else (0.0, 0.02, 0.05, 0.1, 0.2)
+        for tol in tols:
+            opts = L.make_opts(tol=tol, store_prec="fp64", weighting="left", krylov="fgmres", restart=20,
+                               rtol=1e-8, maxit=1000)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx = L.psr_setup(rp, ci, va, dofs, uniform_size=pr.uniform_size, opts=opts)
+            ctx.set_coarse(*P0)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            x = torch.zeros_like(b)
+            info = ctx.solve(b, x)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            st = ctx.stats()
+            err = float((x.cpu() - torch.as_tensor(pr.meta["u_nodes"])).abs().max())
+            rows.append({"p": pdeg, "tol": tol, "m_p": st["m_p"], "iterations": info["iterations"],
+                         "converged": info["converged"], "setup_s": t1 - t0, "solve_s": t2 - t1,
+                         "max_error_vs_exact_solution": err})
+            ctx.destroy()
+    print(json.dumps({"metric": "Experiment 1: FGMRES(20) + M_combo iterations to 1e-8 (60 x 60 mesh, Q_p)",
+                      "workload": "smooth2d_qp N=60, p=2..5, rho = sin^2 sin^2 + 0.1, u = sin sin",
+                      "paper_table1": {"full": {"2": 11, "3": 12, "4": 14, "5": 15},
+                                       "best_compressed_34_35_entries": {"2": 12, "3": 12, "4": 14, "5": 16}},
+                      "rows": rows}))
+
+
 def main():
     args = parse()
+    if args.exp1:
+        run_exp1(args)
+        return
     if args.tol_sweep:
         run_tol_sweep(args, CONFIGS[args.config], args.config)
         return
