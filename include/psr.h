@@ -67,6 +67,9 @@ extern "C" {
                                       tensor cores (AUTO uses them only when their
                                       128-patch tiles are at least 1/4 full) */
 
+#define PSR_CRITERION_SPECTRAL 0   /* Alg. 1 with ||I - A_i B_j^-1||_2 < tol (Eq. 4)        */
+#define PSR_CRITERION_L1       1   /* Alg. 1 with ||A_i - A_j||_l1 < tol (entrywise, Exp. 3) */
+
 #define PSR_ORTHO_AUTO   0        /* FGMRES Gram-Schmidt: one fused cooperative launch per
                                       step with dots and updates on FP32 pairs (about 48
                                       significant bits; FP64 when ||w|| is outside
@@ -109,11 +112,12 @@ typedef struct {
     int32_t symmetrize;   /* 1: store (B^-1 + B^-T)/2 before rounding to FP32/BF16 */
     int32_t use_mlp;      /* 1: verify MLP-predicted representatives first (needs psr_mlp_attach) */
     int32_t ortho;        /* PSR_ORTHO_* (FGMRES only)                            */
+    int32_t criterion;    /* PSR_CRITERION_* of Alg. 1 (L1: psr_setup only)        */
 } psr_opts;
 
 /* Fill `o` with defaults: tol 0, FP64, SYM, CG, restart 30, rtol 1e-8,
  * maxit 10000, graphs on, AUTO sweep, autotune on, symmetrize on, no MLP,
- * AUTO orthogonalisation. */
+ * AUTO orthogonalisation, spectral criterion. */
 void psr_default_opts(psr_opts* o);
 
 /* A rectangular CSR matrix (the interpolation P0 of Eq. 2), device pointers. */
@@ -193,6 +197,13 @@ int psr_get_history(psr_ctx* ctx, double* hist, int32_t cap, int32_t* len);
  * rep_ids (device, m_p, patch index of each database entry in creation
  * order, or NULL) and *m_p (host). */
 int psr_get_assignment(psr_ctx* ctx, int32_t* phi, int32_t* rep_ids, int32_t* m_p);
+
+/* Smoothing iteration of Experiment 3: `sweeps` times
+ * x <- x + omega M^-1 (b - A x), M^-1 as in psr_apply (the patch method of
+ * Eq. 3, plus the coarse term of Eq. 2 when set).  b, x: device, n FP64; x
+ * is updated in place.  sweeps = 0 leaves x unchanged.  Errors:
+ * INVALID_ARG (NULL, sweeps < 0, omega NaN), CUDA.  Blocks the host. */
+int psr_smooth(psr_ctx* ctx, const double* b, double* x, double omega, int32_t sweeps, void* stream);
 
 /* Two-level combination preconditioner (Eq. 2): after this call psr_apply
  * and psr_solve use M_combo^-1 = M^-1 + P0 A0^-1 R0 with M^-1 the patch method

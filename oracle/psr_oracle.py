@@ -629,3 +629,51 @@ def combo_apply(r, dofs, Binv, phi, W, weighting, P0, A0inv):
     prow, pcol, pval, n0 = P0
     Pm = sp.csr_matrix((pval, pcol, prow), shape=(len(r), n0))
     return apply(r, dofs, Binv, phi, W, weighting) + Pm @ (A0inv @ (Pm.T @ np.asarray(r, dtype=np.float64)))
+
+
+# ---------------------------------------------------------------------------
+# Smoothing iteration of Experiment 3: x <- x + omega M^{-1} (b - A x),
+# repeated `sweeps` times (M^{-1} any preconditioner callable).
+# ---------------------------------------------------------------------------
+
+def richardson(rowptr, colidx, vals, n, b, x0, prec, omega, sweeps):
+    import scipy.sparse as sp
+    A = sp.csr_matrix((vals, colidx, rowptr), shape=(n, n))
+    x = np.array(x0, dtype=np.float64, copy=True)
+    for _ in range(sweeps):
+        x = x + omega * prec(np.asarray(b, dtype=np.float64) - A @ x)
+    return x
+
+
+# ---------------------------------------------------------------------------
+# Alg. 1 with the entrywise l1 test of Experiment 3: patch i takes the first
+# entry j (creation order) with ||A_i - A_{rep_j}||_l1 < tol (sum of the
+# absolute entrywise differences), else it becomes a new entry.  No inverse
+# is needed to decide; the database holds the inverses of the entries.
+# ---------------------------------------------------------------------------
+
+def alg1_l1(A, tol, near_tie_rel=1e-9):
+    A = np.asarray(A, dtype=np.float64)
+    npch, p, _ = A.shape
+    phi = np.full(npch, -1, dtype=np.int64)
+    reps: list[int] = []
+    evals = 0
+    near = []
+    for i in range(npch):
+        j_hit = -1
+        if reps:
+            d = np.abs(A[reps] - A[i][None]).sum(axis=(1, 2))
+            hits = np.flatnonzero(d < tol)
+            j_hit = int(hits[0]) if hits.size else -1
+            upto = j_hit + 1 if j_hit >= 0 else len(reps)
+            evals += upto
+            close = np.flatnonzero(np.abs(d[:upto] - tol) <= near_tie_rel * tol)
+            near.extend((i, int(j), float(d[j])) for j in close)
+        if j_hit >= 0:
+            phi[i] = j_hit
+        else:
+            reps.append(i)
+            phi[i] = len(reps) - 1
+    Binv, singular = lu_inverse(A[reps]) if reps else (np.zeros((0, p, p)), np.zeros(0, dtype=bool))
+    return {"phi": phi, "reps": np.array(reps, dtype=np.int64), "Binv": Binv, "evals": evals,
+            "near_ties": near, "singular": [reps[k] for k in np.flatnonzero(singular)]}

@@ -26,6 +26,7 @@ WEIGHT = {"left": 0, "sym": 1}
 KRYLOV = {"cg": 0, "fgmres": 1}
 SWEEP = {"auto": 0, "grouped": 1, "pergroup": 2, "tensor": 3}
 ORTHO = {"auto": 0, "fp64": 1, "split": 2}
+CRITERION = {"spectral": 0, "l1": 1}
 
 EXPORTS = ["psr_default_opts", "psr_setup", "psr_apply", "psr_solve", "psr_get_history",
            "psr_get_assignment", "psr_get_stats", "psr_last_error", "psr_destroy", "psr_extract",
@@ -33,7 +34,7 @@ EXPORTS = ["psr_default_opts", "psr_setup", "psr_apply", "psr_solve", "psr_get_h
            "psr_setup_seeded", "psr_features", "psr_mlp_create", "psr_mlp_num_params", "psr_mlp_set_params",
            "psr_mlp_get_params", "psr_mlp_loss_grad", "psr_mlp_train_step", "psr_mlp_predict", "psr_mlp_destroy",
            "psr_criterion_noalloc", "psr_set_kernel_timing", "psr_get_kernel_timing", "psr_setup_kmeans",
-           "psr_export_database", "psr_set_coarse"]
+           "psr_export_database", "psr_set_coarse", "psr_smooth"]
 
 KT_CLASSES = ("sweep", "spmv", "mdot", "maxpy", "vec")   # PSR_KT_* in order
 
@@ -59,7 +60,7 @@ class psr_opts(C.Structure):
                 ("krylov", C.c_int32), ("restart", C.c_int32), ("rtol", C.c_double),
                 ("maxit", C.c_int32), ("use_graph", C.c_int32), ("sweep_kernel", C.c_int32),
                 ("autotune", C.c_int32), ("symmetrize", C.c_int32), ("use_mlp", C.c_int32),
-                ("ortho", C.c_int32)]
+                ("ortho", C.c_int32), ("criterion", C.c_int32)]
 
 
 class psr_csr_rect(C.Structure):
@@ -107,6 +108,7 @@ def load(path: str = LIB_PATH):
     lib.psr_get_stats.argtypes = [vp, C.POINTER(psr_stats)]
     lib.psr_export_database.argtypes = [vp, vp, vp]
     lib.psr_set_coarse.argtypes = [vp, C.POINTER(psr_csr_rect), vp]
+    lib.psr_smooth.argtypes = [vp, vp, vp, d, i32, vp]
     lib.psr_last_error.argtypes = [vp]
     lib.psr_last_error.restype = C.c_char_p
     lib.psr_destroy.argtypes = [vp]
@@ -168,7 +170,7 @@ def _need(t, dtype, name):
 
 def make_opts(tol=0.0, store_prec="fp64", weighting="sym", krylov="cg", restart=30, rtol=1e-8,
               maxit=10000, use_graph=True, sweep_kernel="auto", autotune=True, symmetrize=True,
-              use_mlp=False, ortho="auto") -> psr_opts:
+              use_mlp=False, ortho="auto", criterion="spectral") -> psr_opts:
     o = psr_opts()
     load().psr_default_opts(C.byref(o))
     o.tol = tol
@@ -184,6 +186,7 @@ def make_opts(tol=0.0, store_prec="fp64", weighting="sym", krylov="cg", restart=
     o.symmetrize = int(symmetrize)
     o.use_mlp = int(use_mlp)
     o.ortho = ORTHO[ortho]
+    o.criterion = CRITERION[criterion]
     return o
 
 
@@ -261,6 +264,13 @@ class Context:
         reps = torch.empty(max(m.value, 1), dtype=torch.int32, device="cuda")
         _check(load().psr_get_assignment(self.h, _ptr(phi), _ptr(reps), C.byref(m)), self.h)
         return phi, reps[: m.value], m.value
+
+    def smooth(self, b, x, omega=1.0, sweeps=1, stream=None):
+        """psr_smooth: sweeps of x <- x + omega M^-1 (b - A x), x in place."""
+        import torch
+        _need(b, torch.float64, "b")
+        _need(x, torch.float64, "x")
+        _check(load().psr_smooth(self.h, _ptr(b), _ptr(x), float(omega), int(sweeps), _stream(stream)), self.h)
 
     def set_coarse(self, rowptr, colidx, vals, n0, stream=None):
         """psr_set_coarse: the two-level term P0 A0^-1 P0^T of Eq. (2) with

@@ -108,7 +108,7 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
     if (op.restart < 1 || op.restart > 32 || op.maxit < 1 || !(op.rtol > 0.0) || op.tol < 0.0 ||
         op.store_prec < 0 || op.store_prec > 2 || op.weighting < 0 || op.weighting > 1 || op.krylov < 0 || op.krylov > 1 ||
         op.sweep_kernel < PSR_SWEEP_AUTO || op.sweep_kernel > PSR_SWEEP_TENSOR || op.ortho < PSR_ORTHO_AUTO ||
-        op.ortho > PSR_ORTHO_SPLIT) {
+        op.ortho > PSR_ORTHO_SPLIT || op.criterion < PSR_CRITERION_SPECTRAL || op.criterion > PSR_CRITERION_L1) {
         set_error(ctx, "invalid option value");
         destroy_ctx(ctx);
         return PSR_ERR_INVALID_ARG;
@@ -250,6 +250,10 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
             cudaFree(first);
             ctx->stats.rounds = 0;
             ctx->stats.criterion_evals = 0;
+        } else if (op.criterion == PSR_CRITERION_L1) {
+            if (m0 > 0 || hints) { set_error(ctx, "the l1 criterion takes no seed database or hints"); FAIL(PSR_ERR_INVALID_ARG); }
+            rc = run_alg1_l1(ctx, s);
+            if (rc != PSR_OK) goto fail;
         } else {
             for (auto& G : ctx->groups)
                 if (G.p > 32) { set_error(ctx, "the criterion kernel handles patches of at most 32 DOFs"); FAIL(PSR_ERR_INVALID_ARG); }
@@ -325,6 +329,7 @@ void psr_default_opts(psr_opts* o) {
     o->symmetrize = 1;
     o->use_mlp = 0;
     o->ortho = PSR_ORTHO_AUTO;
+    o->criterion = PSR_CRITERION_SPECTRAL;
 }
 
 int psr_setup(const psr_csr* A, const psr_patches* patches, const psr_opts* opts, void* stream, psr_ctx** out) {

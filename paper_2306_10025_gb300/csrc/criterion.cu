@@ -1505,3 +1505,142 @@ extern "C" int psr_criterion_noalloc(const double* A_i, int32_t batch, int32_t p
     return launch_criterion_batch(A_i, batch, p, A_c, Binv_c, tol, accept, dval,
                                   reinterpret_cast<int32_t*>(scratch), (cudaStream_t)stream);
 }
+
+namespace psr {
+
+// ---------------------------------------------------------------- Alg. 1, entrywise l1 test
+// Experiment 3's variant of Alg. 1: patch i joins the first entry (creation
+// order) with ||A_i - A_c||_l1 < tol.  Rounds as in the spectral form: round
+// r takes the smallest unassigned patch c as entry r and compares every
+// unassigned patch after it (one warp each, lanes over the p^2 entries).  The
+// next entry is the smallest patch rejected in the round; it goes through
+// three device slots (round r reads slot r%3, bids into slot (r+1)%3 with
+// atomicMin, resets slot (r+2)%3 for round r+1), so rounds are enqueued back
+// to back and the host reads the state once per batch.  Decisions need no
+// inverse: the inverses of the entries alone are formed afterwards.
+struct L1State {
+    int32_t slot[3];
+    int32_t rounds;
+};
+
+__global__ void k_l1_round(const double* __restrict__ Ag, int count, int p, double tol, int r, L1State* st,
+                           int32_t* __restrict__ phi, int32_t* __restrict__ rep,
+                           unsigned long long* __restrict__ evals) {
+    const int c = st->slot[r % 3];
+    if (c >= count) {                                // Alg. 1 finished in an earlier round:
+        if (blockIdx.x == 0 && threadIdx.x == 0) st->slot[(r + 1) % 3] = count;   // so is the next
+        return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        phi[c] = r;
+        rep[r] = c;
+        st->slot[(r + 2) % 3] = count;
+        st->rounds = r + 1;
+    }
+    const int lane = threadIdx.x & 31;
+    const int pp = p * p;
+    const double* a = Ag + (int64_t)c * pp;
+    unsigned long long my_evals = 0;
+    int my_min = count;
+    for (int i = c + 1 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); i < count;
+         i += (gridDim.x * blockDim.x) >> 5) {
+        if (phi[i] != -1) continue;                  // uniform over the warp
+        const double* b = Ag + (int64_t)i * pp;
+        double s0 = 0.0, s1 = 0.0;
+        for (int e = lane; e < pp; e += 64) {
+            s0 += fabs(a[e] - b[e]);
+            if (e + 32 < pp) s1 += fabs(a[e + 32] - b[e + 32]);
+        }
+        const double d = warp_sum(s0 + s1);
+        ++my_evals;
+        if (d < tol) {
+            if (lane == 0) phi[i] = r;
+        } else {
+            my_min = min(my_min, i);
+        }
+    }
+    if (lane == 0) {
+        if (my_evals) atomicAdd(evals, my_evals);
+        if (my_min < count) atomicMin(&st->slot[(r + 1) % 3], my_min);
+    }
+}
+
+int run_alg1_l1(psr_ctx* ctx, cudaStream_t s) {
+    const double tol = ctx->opts.tol;
+    int64_t total_evals = 0;
+    int rounds_total = 0;
+    int first_singular = -1;
+    L1State* st = nullptr;
+    unsigned long long* evals = nullptr;
+    PSR_CUDA(ctx, cudaMalloc(&st, sizeof(L1State)));
+    PSR_CUDA(ctx, cudaMalloc(&evals, sizeof(unsigned long long)));
+    int rc = PSR_OK;
+    for (size_t g = 0; g < ctx->groups.size() && rc == PSR_OK; ++g) {
+        Group& G = ctx->groups[g];
+        const int p = G.p, count = G.count;
+        const int64_t pp = (int64_t)p * p;
+        const double* Ag = ctx->A_ext + G.mat_off;
+        int32_t *phi_l = nullptr, *rep_l = nullptr, *sing = nullptr;
+        PSR_CUDA(ctx, cudaMalloc(&phi_l, sizeof(int32_t) * count));
+        PSR_CUDA(ctx, cudaMalloc(&rep_l, sizeof(int32_t) * count));
+        PSR_CUDA(ctx, cudaMemsetAsync(phi_l, 0xff, sizeof(int32_t) * count, s));
+        PSR_CUDA(ctx, cudaMemsetAsync(evals, 0, sizeof(unsigned long long), s));
+        L1State init{{0, count, count}, 0};
+        L1State h{};
+        PSR_CUDA(ctx, cudaMemcpyAsync(st, &init, sizeof(L1State), cudaMemcpyHostToDevice, s));
+        const int blocks = std::max(1, std::min((count + 7) / 8, 152 * 16));
+        constexpr int BATCH = 64;
+        for (int r0 = 0; r0 < count; r0 += BATCH) {
+            const int r1 = std::min(count, r0 + BATCH);
+            for (int r = r0; r < r1; ++r) {
+                count_launch();
+                k_l1_round<<<blocks, 256, 0, s>>>(Ag, count, p, tol, r, st, phi_l, rep_l, evals);
+            }
+            PSR_CHECK_LAUNCH(ctx, "Alg. 1 rounds (l1)");
+            PSR_CUDA(ctx, cudaMemcpyAsync(&h, st, sizeof(L1State), cudaMemcpyDeviceToHost, s));
+            PSR_CUDA(ctx, cudaStreamSynchronize(s));
+            if (h.rounds < r1) break;                 // a round of this batch found no patch left
+        }
+        const int m = h.rounds;
+        unsigned long long h_evals = 0;
+        PSR_CUDA(ctx, cudaMemcpy(&h_evals, evals, sizeof(h_evals), cudaMemcpyDeviceToHost));
+        // the entries' matrices and their inverses
+        PSR_CUDA(ctx, cudaMalloc(&G.dbA, sizeof(double) * (size_t)std::max(m, 1) * pp));
+        double* Bdb = nullptr;
+        PSR_CUDA(ctx, cudaMalloc(&Bdb, sizeof(double) * (size_t)std::max(m, 1) * pp));
+        PSR_CUDA(ctx, cudaMalloc(&sing, sizeof(int32_t) * std::max(m, 1)));
+        {
+            const int64_t tot = (int64_t)m * pp;
+            const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 152 * 16));
+            count_launch();
+            k_gather_db<<<gb, 256, 0, s>>>(nullptr, 0, Ag, rep_l, m, p, G.dbA);
+        }
+        rc = launch_batched_inverse(G.dbA, pp, nullptr, m, p, Bdb, pp, sing, s);
+        std::vector<int32_t> hrep((size_t)m), hs((size_t)m);
+        if (rc == PSR_OK) {
+            PSR_CUDA(ctx, cudaMemcpyAsync(hrep.data(), rep_l, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s));
+            PSR_CUDA(ctx, cudaMemcpyAsync(hs.data(), sing, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s));
+            PSR_CUDA(ctx, cudaStreamSynchronize(s));
+            for (int j = 0; j < m && first_singular < 0; ++j)
+                if (hs[j]) first_singular = G.h_gidx[hrep[j]];
+        }
+        cudaFree(sing);
+        cudaFree(rep_l);
+        G.m = m;
+        G.sphi = phi_l;
+        G.rinv = Bdb;
+        G.h_rep.assign(hrep.begin(), hrep.end());
+        total_evals += (int64_t)h_evals;
+        rounds_total += m;
+    }
+    cudaFree(st);
+    cudaFree(evals);
+    ctx->stats.first_singular = first_singular;
+    ctx->stats.criterion_evals = total_evals;
+    ctx->stats.criterion_exact = 0;
+    ctx->stats.criterion_screened = 0;
+    ctx->stats.rounds = rounds_total;
+    return rc;
+}
+
+}  // namespace psr

@@ -221,6 +221,7 @@ int sweep_apply_ex(psr_ctx* ctx, const double* r, double* z, const int32_t* stop
 int build_grouped_tables(psr_ctx* ctx);
 void free_sweep(psr_ctx* ctx);
 int coarse_apply(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s);
+int run_alg1_l1(psr_ctx* ctx, cudaStream_t s);
 void coarse_free(psr_ctx* ctx);
 
 // sweep_tc.cu (BF16 entries on tcgen05 tensor cores)

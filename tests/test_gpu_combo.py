@@ -96,3 +96,33 @@ def test_set_coarse_errors(lib):
     with pytest.raises(lib.PsrError):
         ctx.set_coarse(dev(prow, torch.int32), dev(pcol, torch.int32), dev(pval, torch.float64), 20000)
     ctx.destroy()
+
+
+@pytest.mark.parametrize("coarse", [False, True])
+def test_smoothing_iteration_vs_oracle(lib, coarse):
+    """Experiment 3's smoother x <- x + omega M^-1 (b - A x): three sweeps
+    with the patch method (tol 0.1), and with M_combo."""
+    pr = P.smooth2d_qp(8, 2)
+    tol, omega, sweeps = 0.1, 0.8, 3
+    st = O.setup(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d(), tol)
+    if coarse:
+        A0inv = np.linalg.inv(O.coarse_operator(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.meta["P0"]))
+        pc = lambda r: O.combo_apply(r, pr.dofs2d(), st["Binv"], st["phi"], st["W"], "left", pr.meta["P0"], A0inv)
+        ctx = combo_ctx(lib, pr, tol)
+    else:
+        pc = lambda r: O.apply(r, pr.dofs2d(), st["Binv"], st["phi"], st["W"], "left")
+        rp, ci, va = dev(pr.rowptr, torch.int32), dev(pr.colidx, torch.int32), dev(pr.vals, torch.float64)
+        ctx = lib.psr_setup(rp, ci, va, dev(pr.patch_dofs, torch.int32), uniform_size=pr.uniform_size,
+                            opts=lib.make_opts(tol=tol, weighting="left", krylov="fgmres"))
+    b = pr.meta["b"]
+    x0 = np.random.default_rng(4).standard_normal(pr.n)
+    xo = O.richardson(pr.rowptr, pr.colidx, pr.vals, pr.n, b, x0, pc, omega, sweeps)
+    x = dev(x0, torch.float64)
+    ctx.smooth(dev(b, torch.float64), x, omega=omega, sweeps=sweeps)
+    assert np.abs(x.cpu().numpy() - xo).max() <= 1e-11 * np.abs(xo).max()
+    # the error against the discrete solution shrinks
+    xs = np.linalg.solve(pr.to_scipy().toarray(), b)
+    assert np.abs(x.cpu().numpy() - xs).max() < np.abs(x0 - xs).max()
+    with pytest.raises(lib.PsrError):
+        ctx.smooth(dev(b, torch.float64), x, sweeps=-1)
+    ctx.destroy()

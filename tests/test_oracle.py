@@ -502,3 +502,27 @@ def test_kmeans_every_patch_its_own_mean():
     A = g.standard_normal((9, 4, 4)) + 4.0 * np.eye(4)
     km = O.kmeans_l1(A, np.arange(9))
     assert np.array_equal(km["phi"], np.arange(9)) and km["sweeps"] == 2
+
+
+def test_alg1_l1_pins():
+    """Alg. 1 with Experiment 3's entrywise l1 test: equal patches merge at any
+    tol > 0, a scaled copy s A is within tol exactly when |1 - s| ||A||_l1 <
+    tol, the first match in creation order wins, and on the uniform Q2 mesh
+    the 9 boundary classes come out (Alg. 1's classes)."""
+    g = np.random.default_rng(0)
+    B = g.standard_normal((4, 4)) + 4 * np.eye(4)
+    l1 = np.abs(B).sum()
+    A = np.stack([B, 1.1 * B, B, 0.95 * B])
+    r = O.alg1_l1(A, 0.08 * l1)                      # 1.1 B: 0.1 l1 > tol; 0.95 B: 0.05 l1 < tol
+    assert list(r["phi"]) == [0, 1, 0, 0] and list(r["reps"]) == [0, 1]
+    assert r["evals"] == 3                           # 1.1B vs B; B and 0.95B match entry 0 first
+    r2 = O.alg1_l1(A, 0.06 * l1)                     # 0.95 B: 0.05 l1 < 0.06 l1 still matches entry 0
+    assert list(r2["phi"]) == [0, 1, 0, 0]
+    r3 = O.alg1_l1(A, 0.04 * l1)
+    assert list(r3["phi"]) == [0, 1, 0, 2]
+    pr = P.poisson2d_q2(16)
+    Ap = O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d())
+    rc = O.alg1_l1(Ap, 1e-3)
+    ra = O.alg1(Ap, 1e-3)
+    assert len(rc["reps"]) == 9 and np.array_equal(rc["phi"], ra["phi"])
+    assert np.allclose(np.einsum("kab,kbc->kac", rc["Binv"], Ap[rc["reps"]]), np.eye(9), atol=1e-12)

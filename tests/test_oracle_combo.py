@@ -84,3 +84,25 @@ def test_combo_with_identity_interpolation():
     r = A @ x
     z = O.combo_apply(r, pr.dofs2d(), st["Binv"], st["phi"], W, "left", I0, np.linalg.inv(A0))
     assert np.abs(z - (O.apply(r, pr.dofs2d(), st["Binv"], st["phi"], W, "left") + x)).max() < 1e-9 * np.abs(x).max()
+
+
+def test_richardson_special_cases():
+    # M^-1 = A^-1, omega = 1: one sweep solves A x = b from any x0
+    pr = P.smooth2d_qp(4, 2)
+    A = pr.to_scipy().toarray()
+    b = pr.meta["b"]
+    x0 = np.random.default_rng(2).standard_normal(pr.n)
+    x1 = O.richardson(pr.rowptr, pr.colidx, pr.vals, pr.n, b, x0, lambda r: np.linalg.solve(A, r), 1.0, 1)
+    assert np.abs(A @ x1 - b).max() < 1e-10 * np.abs(b).max()
+    # damped Jacobi on [[2, -1], [-1, 2]]: the error contracts by the known
+    # factors 1 - omega (1 +- 1/2) per sweep along the eigenvectors (1, +-1)
+    rp = np.array([0, 2, 4], dtype=np.int32)
+    ci = np.array([0, 1, 0, 1], dtype=np.int32)
+    va = np.array([2.0, -1.0, -1.0, 2.0])
+    xs = np.array([1.0, 2.0])
+    b2 = np.array([0.0, 3.0])                              # A xs
+    e0 = np.array([1.0, 1.0]) + np.array([1.0, -1.0])      # eigen-components 1 and 1
+    w = 0.6
+    x = O.richardson(rp, ci, va, 2, b2, xs + e0, lambda r: r / 2.0, w, 3)
+    expect = xs + (1 - w * 0.5) ** 3 * np.array([1.0, 1.0]) + (1 - w * 1.5) ** 3 * np.array([1.0, -1.0])
+    assert np.abs(x - expect).max() < 1e-14
