@@ -158,10 +158,11 @@ int psr_setup_seeded(const psr_csr* A, const psr_patches* patches, const psr_opt
                      const double* seed_A, int32_t m0, const int32_t* hints, void* stream,
                      psr_ctx** out);
 
-/* Setup whose database comes from Alg. 2 (section 3.2) in its entrywise
- * variant instead of Alg. 1: m_p entries fixed beforehand, distance
- * ||A_i - B_j||_l1 (entrywise), B_j the entrywise mean of its cluster
- * (Eq. 6), the stored inverse that of the mean.  init: device, m_p distinct
+/* Setup whose database comes from Alg. 2 (section 3.2) instead of Alg. 1:
+ * m_p entries fixed beforehand, B_j the entrywise mean of its cluster
+ * (Eq. 6), the stored inverse that of the mean; the distance by
+ * opts->criterion: PSR_CRITERION_L1 the entrywise ||A_i - B_j||_l1,
+ * PSR_CRITERION_SPECTRAL the 2-norm ||A_i - B_j||_2 (p <= 32).  init: device, m_p distinct
  * patch indices (drawn at random by the caller, as Alg. 2's randperm) whose
  * patches are the initial means.  Every sweep assigns each patch to its
  * nearest mean (ties to the lowest index); the means are recomputed (members

@@ -677,3 +677,48 @@ def alg1_l1(A, tol, near_tie_rel=1e-9):
     Binv, singular = lu_inverse(A[reps]) if reps else (np.zeros((0, p, p)), np.zeros(0, dtype=bool))
     return {"phi": phi, "reps": np.array(reps, dtype=np.int64), "Binv": Binv, "evals": evals,
             "near_ties": near, "singular": [reps[k] for k in np.flatnonzero(singular)]}
+
+
+# ---------------------------------------------------------------------------
+# Alg. 2 (section 3.2), spectral variant: the same iteration as kmeans_l1
+# with d(A_i, B_j) = ||A_i - B_j||_2 (largest singular value, LAPACK SVD).
+# The means, their order of summation, the tie rule and the stopping rule
+# are those of the entrywise variant.
+# ---------------------------------------------------------------------------
+
+def kmeans_spectral(A, init, max_iter=100, near_tie_rel=1e-9):
+    A = np.asarray(A, dtype=np.float64)
+    npch = A.shape[0]
+    init = np.asarray(init, dtype=np.int64)
+    m = init.size
+    B = A[init].copy()
+    phi = np.full(npch, -1, dtype=np.int64)
+    sweeps = 0
+    near = []
+    while sweeps < max_iter:
+        sweeps += 1
+        D = np.empty((npch, m))
+        for j in range(m):
+            D[:, j] = np.linalg.norm(A - B[j][None], ord=2, axis=(1, 2))
+        new = np.argmin(D, axis=1)
+        best = D[np.arange(npch), new]
+        close = (D <= best[:, None] * (1.0 + near_tie_rel)) & (D > 0.0)
+        close[np.arange(npch), new] = False
+        for i in np.flatnonzero(close.any(axis=1)):
+            for j in np.flatnonzero(close[i]):
+                if np.array_equal(B[j], B[new[i]]):
+                    close[i, j] = False
+        near = [int(i) for i in np.flatnonzero(close.any(axis=1))]
+        changed = bool(np.any(new != phi))
+        phi = new
+        if not changed:
+            break
+        for j in range(m):
+            members = np.flatnonzero(phi == j)
+            if members.size:
+                acc = np.zeros(A.shape[1:])
+                for k in members:
+                    acc = acc + A[k]
+                B[j] = acc / members.size
+    Binv, singular = lu_inverse(B)
+    return {"phi": phi, "means": B, "Binv": Binv, "singular": singular, "sweeps": sweeps, "near_ties": near}

@@ -1,6 +1,7 @@
-// Alg. 2 of section 3.2, entrywise variant: the database size m_p is fixed
-// beforehand, d(A_i, B_j) = ||A_i - B_j||_l1 (entrywise), B_j the entrywise
-// mean of its cluster (Eq. 6), the stored inverse that of the mean.
+// Alg. 2 of section 3.2: the database size m_p is fixed beforehand, B_j the
+// entrywise mean of its cluster (Eq. 6), the stored inverse that of the
+// mean; d(A_i, B_j) = ||A_i - B_j||_l1 (entrywise variant) or ||A_i - B_j||_2
+// (spectral variant), chosen by psr_opts.criterion.
 //
 // Starts from the means B_j = A_{init[j]} (the caller draws the m_p distinct
 // patches).  A sweep assigns every patch to its nearest mean in parallel
@@ -11,6 +12,7 @@
 // are bitwise those of a sequential loop; a cluster left empty keeps its
 // mean.
 #include "psr_internal.cuh"
+#include "dense.cuh"
 
 #include <algorithm>
 #include <vector>
@@ -44,6 +46,49 @@ __global__ void k_kmeans_assign(const double* __restrict__ A, int count, int pp,
     }
 }
 
+// Spectral variant: d(A_i, B_j) = ||A_i - B_j||_2 = sqrt(lambda_max(D^T D)),
+// D = A_i - B_j.  One warp per patch (p <= 32): lane k holds column k of D,
+// G = D^T D is built with shuffles into the warp's shared scratch and its
+// largest eigenvalue taken by the cyclic Jacobi of the criterion's exact
+// path; strict minimum (the lowest j wins ties).
+__global__ void __launch_bounds__(128) k_kmeans_assign_spectral(const double* __restrict__ A, int count, int p,
+                                                                 const double* __restrict__ B, int m,
+                                                                 int32_t* __restrict__ phi,
+                                                                 int32_t* __restrict__ changes) {
+    extern __shared__ double kscratch[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const int ld = p + 1, pp = p * p;
+    double* G = kscratch + (size_t)wid * p * ld;
+    for (int i = blockIdx.x * wpb + wid; i < count; i += gridDim.x * wpb) {
+        const double* a = A + (int64_t)i * pp;
+        double best = 0.0;
+        int arg = 0;
+        for (int j = 0; j < m; ++j) {
+            const double* b = B + (int64_t)j * pp;
+            double dcol[32];
+#pragma unroll
+            for (int r = 0; r < 32; ++r) dcol[r] = (lane < p && r < p) ? a[r * p + lane] - b[r * p + lane] : 0.0;
+            for (int k = 0; k < p; ++k) {
+                double g = 0.0;
+#pragma unroll
+                for (int r = 0; r < 32; ++r) g = fma(dcol[r], __shfl_sync(0xffffffffu, dcol[r], k), g);
+                if (lane < p) G[lane * ld + k] = g;
+            }
+            __syncwarp();
+            const double sig = sqrt(fmax(jacobi_lambda_max_warp(G, p, ld), 0.0));
+            __syncwarp();
+            if (j == 0 || sig < best) {
+                best = sig;
+                arg = j;
+            }
+        }
+        if (lane == 0 && phi[i] != arg) {
+            phi[i] = arg;
+            atomicAdd(changes, 1);
+        }
+    }
+}
+
 // Means of Eq. (6): thread (j, e) sums entry e over the members of cluster
 // j (member list in increasing patch index), empty clusters keep theirs.
 __global__ void k_kmeans_means(const double* __restrict__ A, int pp, const int32_t* __restrict__ moff,
@@ -73,6 +118,11 @@ __global__ void k_kmeans_init(const double* __restrict__ A, int pp, const int32_
 int run_kmeans(psr_ctx* ctx, cudaStream_t s, int m, const std::vector<int32_t>& init, int max_iter) {
     Group& G = ctx->groups[0];
     const int p = G.p, pp = p * p, count = G.count;
+    const bool spectral = ctx->opts.criterion == PSR_CRITERION_SPECTRAL;
+    if (spectral && p > 32) {
+        set_error(ctx, "spectral k-means handles patches of at most 32 DOFs");
+        return PSR_ERR_INVALID_ARG;
+    }
     const double* Ag = ctx->A_ext + G.mat_off;
     double* B = nullptr;
     int32_t *phi = nullptr, *d_init = nullptr, *changes = nullptr, *moff = nullptr, *mlist = nullptr;
@@ -94,7 +144,13 @@ int run_kmeans(psr_ctx* ctx, cudaStream_t s, int m, const std::vector<int32_t>& 
         ++sweeps;
         PSR_CUDA(ctx, cudaMemsetAsync(changes, 0, sizeof(int32_t), s));
         count_launch();
-        k_kmeans_assign<<<(count + 7) / 8, 256, 0, s>>>(Ag, count, pp, B, m, phi, changes);
+        if (spectral) {
+            const int kb = std::max(1, std::min((count + 3) / 4, 152 * 16));
+            k_kmeans_assign_spectral<<<kb, 128, sizeof(double) * 4 * p * (p + 1), s>>>(Ag, count, p, B, m, phi,
+                                                                                       changes);
+        } else {
+            k_kmeans_assign<<<(count + 7) / 8, 256, 0, s>>>(Ag, count, pp, B, m, phi, changes);
+        }
         int32_t h_changes = 0;
         PSR_CUDA(ctx, cudaMemcpyAsync(&h_changes, changes, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         PSR_CUDA(ctx, cudaMemcpyAsync(hphi.data(), phi, sizeof(int32_t) * (size_t)count, cudaMemcpyDeviceToHost, s));

@@ -33,6 +33,10 @@ struct GroupDesc {          // device copy for the grouped persistent kernel
 template <typename T> struct Comp { using type = T; };
 template <> struct Comp<__nv_bfloat16> { using type = float; };
 
+template <typename C> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
 template <typename T> __device__ __forceinline__ T to_store(double v) { return (T)v; }
 template <> __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }
 
@@ -224,12 +228,25 @@ __global__ void __launch_bounds__(256) k_sweep_staged(const int32_t* __restrict_
                 const C* row = sR + a * p;
                 const C* x = sc + k * p;
                 C y0 = (C)0, y1 = (C)0;
-                int b = 0;
-                for (; b + 1 < p; b += 2) {
+                if ((p & 1) == 0) {
+                    // even p: rows and residual slots start on 2-element
+                    // boundaries, so both are read as element pairs
+                    using V2 = typename Vec2<C>::type;
+                    const V2* r2 = reinterpret_cast<const V2*>(row);
+                    const V2* x2 = reinterpret_cast<const V2*>(x);
+                    for (int b2 = 0; b2 < (p >> 1); ++b2) {
+                        const V2 rv = r2[b2], xv = x2[b2];
+                        y0 = fma(rv.x, xv.x, y0);
+                        y1 = fma(rv.y, xv.y, y1);
+                    }
+                } else {
+                    int b = 0;
+                    for (; b + 1 < p; b += 2) {
+                        y0 = fma(row[b], x[b], y0);
+                        y1 = fma(row[b + 1], x[b + 1], y1);
+                    }
                     y0 = fma(row[b], x[b], y0);
-                    y1 = fma(row[b + 1], x[b + 1], y1);
                 }
-                if (b < p) y0 = fma(row[b], x[b], y0);
                 atomicAdd(&z[sd[it]], (double)(y0 + y1) * sw[it]);
             }
         }

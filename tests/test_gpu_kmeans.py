@@ -1,4 +1,4 @@
-"""Alg. 2 (entrywise k-means, section 3.2) on the GPU vs the CPU oracle:
+"""Alg. 2 (k-means, section 3.2; entrywise and spectral variants) on the GPU vs the CPU oracle:
 assignment and sweep count bit-exact, means' inverses within rounding, the
 preconditioner built from them equal to the oracle's Eq. (3) apply."""
 import numpy as np
@@ -24,10 +24,11 @@ def dev(a, dt):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
 
 
-def kmeans_ctx(lib, pr, init, max_iter=100, **kw):
+def kmeans_ctx(lib, pr, init, max_iter=100, criterion="l1", **kw):
     rp, ci, va = dev(pr.rowptr, torch.int32), dev(pr.colidx, torch.int32), dev(pr.vals, torch.float64)
     return lib.psr_setup_kmeans(rp, ci, va, dev(pr.patch_dofs, torch.int32), pr.uniform_size,
-                                dev(np.asarray(init), torch.int32), max_iter=max_iter, opts=lib.make_opts(**kw))
+                                dev(np.asarray(init), torch.int32), max_iter=max_iter,
+                                opts=lib.make_opts(criterion=criterion, **kw))
 
 
 def seeds(n_p, m, seed):
@@ -124,3 +125,30 @@ def test_kmeans_bootstrapped_from_alg1(lib):
     assert int((ref["phi"] != r1["phi"]).sum()) == 48
     for c in (c1, ctx):
         c.destroy()
+
+
+@pytest.mark.parametrize("case", ["c1_classes", "diff3d_random"])
+def test_kmeans_spectral_bit_exact(lib, case):
+    """Spectral variant: d = ||A_i - B_j||_2 (Jacobi eigenvalues of D^T D on
+    the GPU, LAPACK SVD in the oracle)."""
+    if case == "c1_classes":
+        pr = P.poisson2d_q2(16)
+        init = np.array([0, 1, 15, 16, 17, 31, 240, 241, 255], dtype=np.int32)
+    else:
+        pr = P.diffusion3d_q2(4, sigma=0.5, corr_len=3.0, seed=1)
+        init = seeds(pr.n_patches, 6, 5)
+    A = O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d())
+    ref = O.kmeans_spectral(A, init)
+    assert ref["near_ties"] == []
+    ctx = kmeans_ctx(lib, pr, init, criterion="spectral", weighting=pr.weighting, krylov=pr.krylov)
+    phi, _, m = ctx.assignment()
+    assert np.array_equal(phi.cpu().numpy(), ref["phi"]) and ctx.stats()["rounds"] == ref["sweeps"]
+    assert np.array_equal(ctx.export_database().cpu().numpy(), ref["means"])
+    g = np.random.default_rng(9)
+    r = g.standard_normal(pr.n)
+    z = torch.empty(pr.n, dtype=torch.float64, device="cuda")
+    ctx.apply(dev(r, torch.float64), z)
+    W = O.weights(O.multiplicity(pr.n, pr.patch_dofs))
+    zo = O.apply(r, pr.dofs2d(), ref["Binv"], ref["phi"], W, pr.weighting)
+    assert np.abs(z.cpu().numpy() - zo).max() <= 1e-11 * np.abs(zo).max()
+    ctx.destroy()

@@ -80,7 +80,7 @@ def test_export_after_kmeans_and_refusals(lib):
     A = O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d())
     ref = O.kmeans_l1(A, init)
     ctx = lib.psr_setup_kmeans(*csr(pr), dev(pr.patch_dofs, torch.int32), pr.uniform_size,
-                               dev(init, torch.int32), opts=lib.make_opts(weighting="sym", krylov="cg"))
+                               dev(init, torch.int32), opts=lib.make_opts(weighting="sym", krylov="cg", criterion="l1"))
     means = ctx.export_database().cpu().numpy()
     assert np.array_equal(means, ref["means"])        # Alg. 2 entries: the means
     ctx.destroy()

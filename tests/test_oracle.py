@@ -526,3 +526,33 @@ def test_alg1_l1_pins():
     ra = O.alg1(Ap, 1e-3)
     assert len(rc["reps"]) == 9 and np.array_equal(rc["phi"], ra["phi"])
     assert np.allclose(np.einsum("kab,kbc->kac", rc["Binv"], Ap[rc["reps"]]), np.eye(9), atol=1e-12)
+
+
+def test_kmeans_spectral_pins():
+    """Spectral Alg. 2: class seeds on C1 reproduce Alg. 1; the final state is
+    a Lloyd fixed point for the 2-norm distance, checked with singular values
+    computed independently (full SVD); two groups of scaled copies split by
+    the 2-norm; seeding with every patch gives phi = id (a second sweep
+    confirms it)."""
+    pr = P.poisson2d_q2(16)
+    A = O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d())
+    seeds = np.array([0, 1, 15, 16, 17, 31, 240, 241, 255])
+    r = O.kmeans_spectral(A, seeds)
+    assert np.array_equal(r["phi"], O.alg1(A, 1e-3)["phi"]) and r["sweeps"] == 2   # assign, then no change
+    g = np.random.default_rng(3)
+    pd = P.diffusion3d_q2(4, sigma=0.5, corr_len=3.0, seed=1)
+    A3 = O.extract_patches(pd.rowptr, pd.colidx, pd.vals, pd.n, pd.dofs2d())
+    r3 = O.kmeans_spectral(A3, g.choice(len(A3), 6, replace=False))
+    sv = np.array([[np.linalg.svd(A3[i] - r3["means"][j], compute_uv=False)[0] for j in range(6)] for i in range(len(A3))])
+    assert np.array_equal(np.argmin(sv, axis=1), r3["phi"])
+    for j in range(6):
+        mem = np.flatnonzero(r3["phi"] == j)
+        if mem.size:
+            assert np.allclose(r3["means"][j], A3[mem].mean(axis=0), rtol=0, atol=1e-14 * np.abs(A3).max())
+    B = g.standard_normal((5, 5)) + 5 * np.eye(5)
+    C = g.standard_normal((5, 5)) + 5 * np.eye(5)
+    As = np.stack([B, 1.01 * B, C, 0.99 * C, 1.02 * B])
+    rs = O.kmeans_spectral(As, np.array([0, 2]))
+    assert list(rs["phi"]) == [0, 0, 1, 1, 0]
+    ri = O.kmeans_spectral(As, np.arange(5))
+    assert list(ri["phi"]) == [0, 1, 2, 3, 4] and ri["sweeps"] == 2
