@@ -681,9 +681,11 @@ def alg1_l1(A, tol, near_tie_rel=1e-9):
 
 # ---------------------------------------------------------------------------
 # Alg. 2 (section 3.2), spectral variant: the same iteration as kmeans_l1
-# with d(A_i, B_j) = ||A_i - B_j||_2 (largest singular value, LAPACK SVD).
-# The means, their order of summation, the tie rule and the stopping rule
-# are those of the entrywise variant.
+# with d(A_i, B_j) = ||I - A_i B_j^{-1}||_2, B_j^{-1} the inverse of the
+# entrywise mean (recomputed after every update of the means), evaluated in
+# the difference form of `criterion` (LAPACK SVD).  The means, their order of
+# summation, the tie rule and the stopping rule are those of the entrywise
+# variant.
 # ---------------------------------------------------------------------------
 
 def kmeans_spectral(A, init, max_iter=100, near_tie_rel=1e-9):
@@ -698,8 +700,9 @@ def kmeans_spectral(A, init, max_iter=100, near_tie_rel=1e-9):
     while sweeps < max_iter:
         sweeps += 1
         D = np.empty((npch, m))
+        Bi, _ = lu_inverse(B)
         for j in range(m):
-            D[:, j] = np.linalg.norm(A - B[j][None], ord=2, axis=(1, 2))
+            D[:, j] = criterion(A, B[j][None], Bi[j][None])
         new = np.argmin(D, axis=1)
         best = D[np.arange(npch), new]
         close = (D <= best[:, None] * (1.0 + near_tie_rel)) & (D > 0.0)

@@ -1,7 +1,7 @@
 // Alg. 2 of section 3.2: the database size m_p is fixed beforehand, B_j the
 // entrywise mean of its cluster (Eq. 6), the stored inverse that of the
-// mean; d(A_i, B_j) = ||A_i - B_j||_l1 (entrywise variant) or ||A_i - B_j||_2
-// (spectral variant), chosen by psr_opts.criterion.
+// mean; d(A_i, B_j) = ||A_i - B_j||_l1 (entrywise variant) or
+// ||I - A_i B_j^-1||_2 (spectral variant), chosen by psr_opts.criterion.
 //
 // Starts from the means B_j = A_{init[j]} (the caller draws the m_p distinct
 // patches).  A sweep assigns every patch to its nearest mean in parallel
@@ -46,13 +46,16 @@ __global__ void k_kmeans_assign(const double* __restrict__ A, int count, int pp,
     }
 }
 
-// Spectral variant: d(A_i, B_j) = ||A_i - B_j||_2 = sqrt(lambda_max(D^T D)),
-// D = A_i - B_j.  One warp per patch (p <= 32): lane k holds column k of D,
-// G = D^T D is built with shuffles into the warp's shared scratch and its
-// largest eigenvalue taken by the cyclic Jacobi of the criterion's exact
-// path; strict minimum (the lowest j wins ties).
+// Spectral variant: d(A_i, B_j) = ||I - A_i B_j^-1||_2, evaluated in the
+// difference form ||(B_j - A_i) B_j^-1||_2 = sqrt(lambda_max(E^T E)) with
+// Bi = the inverses of the current means.  One warp per patch (p <= 32):
+// lane r forms row r of E into the warp's shared scratch, then holds column
+// r of E, G = E^T E is built with shuffles over the scratch and its largest
+// eigenvalue taken by the cyclic Jacobi of the criterion's exact path;
+// strict minimum (the lowest j wins ties).
 __global__ void __launch_bounds__(128) k_kmeans_assign_spectral(const double* __restrict__ A, int count, int p,
-                                                                 const double* __restrict__ B, int m,
+                                                                 const double* __restrict__ B,
+                                                                 const double* __restrict__ Bi, int m,
                                                                  int32_t* __restrict__ phi,
                                                                  int32_t* __restrict__ changes) {
     extern __shared__ double kscratch[];
@@ -65,13 +68,27 @@ __global__ void __launch_bounds__(128) k_kmeans_assign_spectral(const double* __
         int arg = 0;
         for (int j = 0; j < m; ++j) {
             const double* b = B + (int64_t)j * pp;
-            double dcol[32];
+            const double* bi = Bi + (int64_t)j * pp;
+            double drow[32];
 #pragma unroll
-            for (int r = 0; r < 32; ++r) dcol[r] = (lane < p && r < p) ? a[r * p + lane] - b[r * p + lane] : 0.0;
+            for (int l = 0; l < 32; ++l) drow[l] = (lane < p && l < p) ? b[lane * p + l] - a[lane * p + l] : 0.0;
+            if (lane < p)
+                for (int k = 0; k < p; ++k) {
+                    double e = 0.0;
+#pragma unroll
+                    for (int l = 0; l < 32; ++l)
+                        if (l < p) e = fma(drow[l], bi[l * p + k], e);
+                    G[lane * ld + k] = e;
+                }
+            __syncwarp();
+            double ecol[32];
+#pragma unroll
+            for (int r = 0; r < 32; ++r) ecol[r] = (lane < p && r < p) ? G[r * ld + lane] : 0.0;
+            __syncwarp();
             for (int k = 0; k < p; ++k) {
                 double g = 0.0;
 #pragma unroll
-                for (int r = 0; r < 32; ++r) g = fma(dcol[r], __shfl_sync(0xffffffffu, dcol[r], k), g);
+                for (int r = 0; r < 32; ++r) g = fma(ecol[r], __shfl_sync(0xffffffffu, ecol[r], k), g);
                 if (lane < p) G[lane * ld + k] = g;
             }
             __syncwarp();
@@ -132,6 +149,12 @@ int run_kmeans(psr_ctx* ctx, cudaStream_t s, int m, const std::vector<int32_t>& 
     PSR_CUDA(ctx, cudaMalloc(&changes, sizeof(int32_t)));
     PSR_CUDA(ctx, cudaMalloc(&moff, sizeof(int32_t) * (size_t)(m + 1)));
     PSR_CUDA(ctx, cudaMalloc(&mlist, sizeof(int32_t) * (size_t)count));
+    double* Bcur = nullptr;                   // spectral: inverses of the current means
+    int32_t* sing_cur = nullptr;
+    if (spectral) {
+        PSR_CUDA(ctx, cudaMalloc(&Bcur, sizeof(double) * (size_t)m * pp));
+        PSR_CUDA(ctx, cudaMalloc(&sing_cur, sizeof(int32_t) * (size_t)m));
+    }
     PSR_CUDA(ctx, cudaMemcpyAsync(d_init, init.data(), sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
     PSR_CUDA(ctx, cudaMemsetAsync(phi, 0xff, sizeof(int32_t) * (size_t)count, s));
     const int eb = (int)std::max<int64_t>(1, ((int64_t)m * pp + 255) / 256);
@@ -143,12 +166,16 @@ int run_kmeans(psr_ctx* ctx, cudaStream_t s, int m, const std::vector<int32_t>& 
     while (sweeps < max_iter) {
         ++sweeps;
         PSR_CUDA(ctx, cudaMemsetAsync(changes, 0, sizeof(int32_t), s));
-        count_launch();
         if (spectral) {
+            // inverses of the current means (a singular mean is reported after the loop)
+            int rci = launch_batched_inverse(B, pp, nullptr, m, p, Bcur, pp, sing_cur, s);
+            if (rci != PSR_OK) { rc = rci; break; }
+            count_launch();
             const int kb = std::max(1, std::min((count + 3) / 4, 152 * 16));
-            k_kmeans_assign_spectral<<<kb, 128, sizeof(double) * 4 * p * (p + 1), s>>>(Ag, count, p, B, m, phi,
-                                                                                       changes);
+            k_kmeans_assign_spectral<<<kb, 128, sizeof(double) * 4 * p * (p + 1), s>>>(Ag, count, p, B, Bcur, m,
+                                                                                       phi, changes);
         } else {
+            count_launch();
             k_kmeans_assign<<<(count + 7) / 8, 256, 0, s>>>(Ag, count, pp, B, m, phi, changes);
         }
         int32_t h_changes = 0;
@@ -175,7 +202,7 @@ int run_kmeans(psr_ctx* ctx, cudaStream_t s, int m, const std::vector<int32_t>& 
     int32_t* sing = nullptr;
     PSR_CUDA(ctx, cudaMalloc(&Bdb, sizeof(double) * (size_t)m * pp));
     PSR_CUDA(ctx, cudaMalloc(&sing, sizeof(int32_t) * (size_t)m));
-    rc = launch_batched_inverse(B, pp, nullptr, m, p, Bdb, pp, sing, s);
+    if (rc == PSR_OK) rc = launch_batched_inverse(B, pp, nullptr, m, p, Bdb, pp, sing, s);
     std::vector<int32_t> hs((size_t)m);
     if (rc == PSR_OK) {
         PSR_CUDA(ctx, cudaMemcpyAsync(hs.data(), sing, sizeof(int32_t) * (size_t)m, cudaMemcpyDeviceToHost, s));
@@ -188,6 +215,8 @@ int run_kmeans(psr_ctx* ctx, cudaStream_t s, int m, const std::vector<int32_t>& 
             }
     }
     cudaFree(d_init);
+    cudaFree(Bcur);
+    cudaFree(sing_cur);
     cudaFree(changes);
     cudaFree(moff);
     cudaFree(mlist);

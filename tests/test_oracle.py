@@ -529,11 +529,12 @@ def test_alg1_l1_pins():
 
 
 def test_kmeans_spectral_pins():
-    """Spectral Alg. 2: class seeds on C1 reproduce Alg. 1; the final state is
-    a Lloyd fixed point for the 2-norm distance, checked with singular values
-    computed independently (full SVD); two groups of scaled copies split by
-    the 2-norm; seeding with every patch gives phi = id (a second sweep
-    confirms it)."""
+    """Spectral Alg. 2 (d = ||I - A_i B_j^-1||_2, B_j the cluster mean): class
+    seeds on C1 reproduce Alg. 1; the final state is a Lloyd fixed point for
+    the distance evaluated independently in its naive form (explicit inverse
+    and ||I - A B^-1||_2 by SVD); for scaled copies d(sB, B) = |1 - s|, so the
+    groups split as the closed form says; seeding with every patch gives
+    phi = id (a second sweep confirms it)."""
     pr = P.poisson2d_q2(16)
     A = O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d())
     seeds = np.array([0, 1, 15, 16, 17, 31, 240, 241, 255])
@@ -543,8 +544,10 @@ def test_kmeans_spectral_pins():
     pd = P.diffusion3d_q2(4, sigma=0.5, corr_len=3.0, seed=1)
     A3 = O.extract_patches(pd.rowptr, pd.colidx, pd.vals, pd.n, pd.dofs2d())
     r3 = O.kmeans_spectral(A3, g.choice(len(A3), 6, replace=False))
-    sv = np.array([[np.linalg.svd(A3[i] - r3["means"][j], compute_uv=False)[0] for j in range(6)] for i in range(len(A3))])
-    assert np.array_equal(np.argmin(sv, axis=1), r3["phi"])
+    I = np.eye(A3.shape[1])
+    dn = np.array([[np.linalg.svd(I - A3[i] @ np.linalg.inv(r3["means"][j]), compute_uv=False)[0]
+                    for j in range(6)] for i in range(len(A3))])
+    assert np.array_equal(np.argmin(dn, axis=1), r3["phi"])
     for j in range(6):
         mem = np.flatnonzero(r3["phi"] == j)
         if mem.size:
@@ -552,6 +555,7 @@ def test_kmeans_spectral_pins():
     B = g.standard_normal((5, 5)) + 5 * np.eye(5)
     C = g.standard_normal((5, 5)) + 5 * np.eye(5)
     As = np.stack([B, 1.01 * B, C, 0.99 * C, 1.02 * B])
+    assert abs(O.criterion(1.02 * B, B, np.linalg.inv(B)) - 0.02) < 1e-14
     rs = O.kmeans_spectral(As, np.array([0, 2]))
     assert list(rs["phi"]) == [0, 0, 1, 1, 0]
     ri = O.kmeans_spectral(As, np.arange(5))
