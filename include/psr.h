@@ -69,6 +69,8 @@ extern "C" {
 
 #define PSR_CRITERION_SPECTRAL 0   /* Alg. 1 with ||I - A_i B_j^-1||_2 < tol (Eq. 4)        */
 #define PSR_CRITERION_L1       1   /* Alg. 1 with ||A_i - A_j||_l1 < tol (entrywise, Exp. 3) */
+#define PSR_CRITERION_VARMIN   2   /* Alg. 2 only: spectral distance, representatives the
+                                      members of least in-cluster variance (section 3.2) */
 
 #define PSR_ORTHO_AUTO   0        /* FGMRES Gram-Schmidt: one fused cooperative launch per
                                       step with dots and updates on FP32 pairs (about 48
@@ -162,7 +164,10 @@ int psr_setup_seeded(const psr_csr* A, const psr_patches* patches, const psr_opt
  * m_p entries fixed beforehand, B_j the entrywise mean of its cluster
  * (Eq. 6), the stored inverse that of the mean; the distance by
  * opts->criterion: PSR_CRITERION_L1 the entrywise ||A_i - B_j||_l1,
- * PSR_CRITERION_SPECTRAL the 2-norm ||A_i - B_j||_2 (p <= 32).  init: device, m_p distinct
+ * PSR_CRITERION_SPECTRAL ||I - A_i B_j^-1||_2 (p <= 32).  With
+ * PSR_CRITERION_VARMIN (p <= 32) B_j is instead the member of cluster j with
+ * the least sum over the cluster of d(A_k, B_j)^2 (d spectral), stored with
+ * its own inverse (variance-minimising clustering).  init: device, m_p distinct
  * patch indices (drawn at random by the caller, as Alg. 2's randperm) whose
  * patches are the initial means.  Every sweep assigns each patch to its
  * nearest mean (ties to the lowest index); the means are recomputed (members

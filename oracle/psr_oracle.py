@@ -725,3 +725,54 @@ def kmeans_spectral(A, init, max_iter=100, near_tie_rel=1e-9):
                 B[j] = acc / members.size
     Binv, singular = lu_inverse(B)
     return {"phi": phi, "means": B, "Binv": Binv, "singular": singular, "sweeps": sweeps, "near_ties": near}
+
+
+# ---------------------------------------------------------------------------
+# Alg. 2 (section 3.2), variance-minimising variant: d(A_i, B_j) =
+# ||I - A_i B_j^{-1}||_2 as in the spectral variant, but B_j is a member of
+# its cluster: the member m minimising the in-cluster variance
+# sum_{k in C_j} d(A_k, A_m)^2 (sum in increasing k; the lowest m on ties);
+# the stored inverse is that member's.  Starts from the patches init as the
+# representatives; a cluster left empty keeps its representative.
+# ---------------------------------------------------------------------------
+
+def kmeans_varmin(A, init, max_iter=100, near_tie_rel=1e-9):
+    A = np.asarray(A, dtype=np.float64)
+    npch = A.shape[0]
+    reps = np.asarray(init, dtype=np.int64).copy()
+    m = reps.size
+    Ainv, singular_all = lu_inverse(A)
+    phi = np.full(npch, -1, dtype=np.int64)
+    sweeps = 0
+    near = []
+    while sweeps < max_iter:
+        sweeps += 1
+        D = np.empty((npch, m))
+        for j in range(m):
+            D[:, j] = criterion(A, A[reps[j]][None], Ainv[reps[j]][None])
+        new = np.argmin(D, axis=1)
+        best = D[np.arange(npch), new]
+        close = (D <= best[:, None] * (1.0 + near_tie_rel)) & (D > 0.0)
+        close[np.arange(npch), new] = False
+        near = [int(i) for i in np.flatnonzero(close.any(axis=1))]
+        changed = bool(np.any(new != phi))
+        phi = new
+        if not changed:
+            break
+        for j in range(m):
+            members = np.flatnonzero(phi == j)
+            if members.size == 0:
+                continue
+            V = np.zeros(members.size)
+            for t, mm in enumerate(members):
+                d = criterion(A[members], A[mm][None], Ainv[mm][None])
+                acc = 0.0
+                for x in d:
+                    acc = acc + x * x
+                V[t] = acc
+            t_best = int(np.argmin(V))
+            vclose = np.flatnonzero((V <= V[t_best] * (1.0 + near_tie_rel) + 1e-300) & (np.arange(V.size) != t_best))
+            near.extend(int(members[t]) for t in vclose)
+            reps[j] = members[t_best]
+    return {"phi": phi, "reps": reps, "Binv": Ainv[reps], "singular": singular_all[reps], "sweeps": sweeps,
+            "near_ties": near}

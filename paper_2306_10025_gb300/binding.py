@@ -26,7 +26,7 @@ WEIGHT = {"left": 0, "sym": 1}
 KRYLOV = {"cg": 0, "fgmres": 1}
 SWEEP = {"auto": 0, "grouped": 1, "pergroup": 2, "tensor": 3}
 ORTHO = {"auto": 0, "fp64": 1, "split": 2}
-CRITERION = {"spectral": 0, "l1": 1}
+CRITERION = {"spectral": 0, "l1": 1, "varmin": 2}
 
 EXPORTS = ["psr_default_opts", "psr_setup", "psr_apply", "psr_solve", "psr_get_history",
            "psr_get_assignment", "psr_get_stats", "psr_last_error", "psr_destroy", "psr_extract",

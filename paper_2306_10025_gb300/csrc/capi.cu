@@ -108,7 +108,7 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
     if (op.restart < 1 || op.restart > 32 || op.maxit < 1 || !(op.rtol > 0.0) || op.tol < 0.0 ||
         op.store_prec < 0 || op.store_prec > 2 || op.weighting < 0 || op.weighting > 1 || op.krylov < 0 || op.krylov > 1 ||
         op.sweep_kernel < PSR_SWEEP_AUTO || op.sweep_kernel > PSR_SWEEP_TENSOR || op.ortho < PSR_ORTHO_AUTO ||
-        op.ortho > PSR_ORTHO_SPLIT || op.criterion < PSR_CRITERION_SPECTRAL || op.criterion > PSR_CRITERION_L1) {
+        op.ortho > PSR_ORTHO_SPLIT || op.criterion < PSR_CRITERION_SPECTRAL || op.criterion > PSR_CRITERION_VARMIN) {
         set_error(ctx, "invalid option value");
         destroy_ctx(ctx);
         return PSR_ERR_INVALID_ARG;
@@ -218,6 +218,10 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
         // seed entries come on top of at most one new entry per patch
         CK(cudaMalloc(&ctx->rep_ids, sizeof(int32_t) * ((size_t)np + (size_t)std::max(m0, 0))));
         t0 = std::chrono::steady_clock::now();
+        if (mode.km_m == 0 && op.criterion == PSR_CRITERION_VARMIN) {
+            set_error(ctx, "the variance-minimising criterion is an Alg. 2 variant (psr_setup_kmeans)");
+            FAIL(PSR_ERR_INVALID_ARG);
+        }
         if (mode.km_m > 0) {
             rc = run_kmeans(ctx, s, mode.km_m, *mode.km_init, mode.km_iter);
             if (rc != PSR_OK) goto fail;

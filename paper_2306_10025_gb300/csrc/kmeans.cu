@@ -46,13 +46,46 @@ __global__ void k_kmeans_assign(const double* __restrict__ A, int count, int pp,
     }
 }
 
-// Spectral variant: d(A_i, B_j) = ||I - A_i B_j^-1||_2, evaluated in the
-// difference form ||(B_j - A_i) B_j^-1||_2 = sqrt(lambda_max(E^T E)) with
-// Bi = the inverses of the current means.  One warp per patch (p <= 32):
-// lane r forms row r of E into the warp's shared scratch, then holds column
-// r of E, G = E^T E is built with shuffles over the scratch and its largest
-// eigenvalue taken by the cyclic Jacobi of the criterion's exact path;
-// strict minimum (the lowest j wins ties).
+// d(A_i, B) = ||I - A_i B^-1||_2 in the difference form ||(B - A_i) B^-1||_2
+// = sqrt(lambda_max(E^T E)), by one warp (p <= 32): lane r forms row r of E
+// into the warp's shared scratch G (p x (p+1)), then holds column r of E;
+// G = E^T E is built with shuffles and its largest eigenvalue taken by the
+// cyclic Jacobi of the criterion's exact path.  Every lane gets the value.
+__device__ double spectral_dist_warp(const double* __restrict__ a, const double* __restrict__ b,
+                                     const double* __restrict__ bi, int p, double* G) {
+    const int lane = threadIdx.x & 31;
+    const int ld = p + 1;
+    double drow[32];
+#pragma unroll
+    for (int l = 0; l < 32; ++l) drow[l] = (lane < p && l < p) ? b[lane * p + l] - a[lane * p + l] : 0.0;
+    if (lane < p)
+        for (int k = 0; k < p; ++k) {
+            double e = 0.0;
+#pragma unroll
+            for (int l = 0; l < 32; ++l)
+                if (l < p) e = fma(drow[l], bi[l * p + k], e);
+            G[lane * ld + k] = e;
+        }
+    __syncwarp();
+    double ecol[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) ecol[r] = (lane < p && r < p) ? G[r * ld + lane] : 0.0;
+    __syncwarp();
+    for (int k = 0; k < p; ++k) {
+        double g = 0.0;
+#pragma unroll
+        for (int r = 0; r < 32; ++r) g = fma(ecol[r], __shfl_sync(0xffffffffu, ecol[r], k), g);
+        if (lane < p) G[lane * ld + k] = g;
+    }
+    __syncwarp();
+    const double sig = sqrt(fmax(jacobi_lambda_max_warp(G, p, ld), 0.0));
+    __syncwarp();
+    return sig;
+}
+
+// Spectral and variance-minimising variants: d(A_i, B_j) = ||I - A_i B_j^-1||_2
+// with Bi the inverses of the current representatives (the means, or the
+// chosen members).  One warp per patch; strict minimum (the lowest j wins ties).
 __global__ void __launch_bounds__(128) k_kmeans_assign_spectral(const double* __restrict__ A, int count, int p,
                                                                  const double* __restrict__ B,
                                                                  const double* __restrict__ Bi, int m,
@@ -60,40 +93,13 @@ __global__ void __launch_bounds__(128) k_kmeans_assign_spectral(const double* __
                                                                  int32_t* __restrict__ changes) {
     extern __shared__ double kscratch[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    const int ld = p + 1, pp = p * p;
-    double* G = kscratch + (size_t)wid * p * ld;
+    const int pp = p * p;
+    double* G = kscratch + (size_t)wid * p * (p + 1);
     for (int i = blockIdx.x * wpb + wid; i < count; i += gridDim.x * wpb) {
-        const double* a = A + (int64_t)i * pp;
         double best = 0.0;
         int arg = 0;
         for (int j = 0; j < m; ++j) {
-            const double* b = B + (int64_t)j * pp;
-            const double* bi = Bi + (int64_t)j * pp;
-            double drow[32];
-#pragma unroll
-            for (int l = 0; l < 32; ++l) drow[l] = (lane < p && l < p) ? b[lane * p + l] - a[lane * p + l] : 0.0;
-            if (lane < p)
-                for (int k = 0; k < p; ++k) {
-                    double e = 0.0;
-#pragma unroll
-                    for (int l = 0; l < 32; ++l)
-                        if (l < p) e = fma(drow[l], bi[l * p + k], e);
-                    G[lane * ld + k] = e;
-                }
-            __syncwarp();
-            double ecol[32];
-#pragma unroll
-            for (int r = 0; r < 32; ++r) ecol[r] = (lane < p && r < p) ? G[r * ld + lane] : 0.0;
-            __syncwarp();
-            for (int k = 0; k < p; ++k) {
-                double g = 0.0;
-#pragma unroll
-                for (int r = 0; r < 32; ++r) g = fma(ecol[r], __shfl_sync(0xffffffffu, ecol[r], k), g);
-                if (lane < p) G[lane * ld + k] = g;
-            }
-            __syncwarp();
-            const double sig = sqrt(fmax(jacobi_lambda_max_warp(G, p, ld), 0.0));
-            __syncwarp();
+            const double sig = spectral_dist_warp(A + (int64_t)i * pp, B + (int64_t)j * pp, Bi + (int64_t)j * pp, p, G);
             if (j == 0 || sig < best) {
                 best = sig;
                 arg = j;
@@ -103,6 +109,29 @@ __global__ void __launch_bounds__(128) k_kmeans_assign_spectral(const double* __
             phi[i] = arg;
             atomicAdd(changes, 1);
         }
+    }
+}
+
+// Variance-minimising variant: V[m] = sum over the members k of m's cluster
+// (in increasing k) of d(A_k, A_m)^2, one warp per patch m.
+__global__ void __launch_bounds__(128) k_kmeans_variance(const double* __restrict__ A,
+                                                          const double* __restrict__ Ainv, int count, int p,
+                                                          const int32_t* __restrict__ phi,
+                                                          const int32_t* __restrict__ moff,
+                                                          const int32_t* __restrict__ mlist, double* __restrict__ V) {
+    extern __shared__ double kscratch[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const int pp = p * p;
+    double* G = kscratch + (size_t)wid * p * (p + 1);
+    for (int mm = blockIdx.x * wpb + wid; mm < count; mm += gridDim.x * wpb) {
+        const int j = phi[mm];
+        double acc = 0.0;
+        for (int q = moff[j]; q < moff[j + 1]; ++q) {
+            const int k = mlist[q];
+            const double d = spectral_dist_warp(A + (int64_t)k * pp, A + (int64_t)mm * pp, Ainv + (int64_t)mm * pp, p, G);
+            acc = acc + d * d;
+        }
+        if (lane == 0) V[mm] = acc;
     }
 }
 
@@ -132,7 +161,124 @@ __global__ void k_kmeans_init(const double* __restrict__ A, int pp, const int32_
 // init: host, m distinct local patch indices.  Leaves G.m, G.sphi (device,
 // local phi), G.rinv (FP64 inverses of the means, m x p x p), G.h_rep (-1:
 // no entry is a patch), and the number of sweeps in ctx->stats.rounds.
+// out[j] = src[idx[j]] for matrices of pp entries
+__global__ void k_kmeans_gather(const double* __restrict__ src, const int32_t* __restrict__ idx, int m, int pp,
+                                double* __restrict__ out) {
+    const int64_t total = (int64_t)m * pp;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / pp);
+        out[e] = src[(int64_t)idx[j] * pp + (e - (int64_t)j * pp)];
+    }
+}
+
+// Variance-minimising variant of Alg. 2 (section 3.2): representatives are
+// members (init the first ones); a sweep assigns every patch to the nearest
+// representative by ||I - A_i B_j^-1||_2, then every cluster takes the
+// member with the smallest variance sum_k d(A_k, A_m)^2 (sums in member
+// order on the device, the lowest member on ties chosen on the host).  The
+// inverses of all patches are formed once; the database keeps the
+// representatives' patches and inverses.
+static int run_kmeans_varmin(psr_ctx* ctx, cudaStream_t s, int m, const std::vector<int32_t>& init, int max_iter) {
+    Group& G = ctx->groups[0];
+    const int p = G.p, pp = p * p, count = G.count;
+    if (p > 32) {
+        set_error(ctx, "variance-minimising k-means handles patches of at most 32 DOFs");
+        return PSR_ERR_INVALID_ARG;
+    }
+    const double* Ag = ctx->A_ext + G.mat_off;
+    double *Ainv = nullptr, *B = nullptr, *Bcur = nullptr, *V = nullptr;
+    int32_t *sing_all = nullptr, *phi = nullptr, *changes = nullptr, *moff = nullptr, *mlist = nullptr,
+            *d_reps = nullptr;
+    PSR_CUDA(ctx, cudaMalloc(&Ainv, sizeof(double) * (size_t)count * pp));
+    PSR_CUDA(ctx, cudaMalloc(&sing_all, sizeof(int32_t) * (size_t)count));
+    PSR_CUDA(ctx, cudaMalloc(&B, sizeof(double) * (size_t)m * pp));
+    PSR_CUDA(ctx, cudaMalloc(&Bcur, sizeof(double) * (size_t)m * pp));
+    PSR_CUDA(ctx, cudaMalloc(&V, sizeof(double) * (size_t)count));
+    PSR_CUDA(ctx, cudaMalloc(&phi, sizeof(int32_t) * (size_t)count));
+    PSR_CUDA(ctx, cudaMalloc(&changes, sizeof(int32_t)));
+    PSR_CUDA(ctx, cudaMalloc(&moff, sizeof(int32_t) * (size_t)(m + 1)));
+    PSR_CUDA(ctx, cudaMalloc(&mlist, sizeof(int32_t) * (size_t)count));
+    PSR_CUDA(ctx, cudaMalloc(&d_reps, sizeof(int32_t) * (size_t)m));
+    int rc = launch_batched_inverse(Ag, pp, nullptr, count, p, Ainv, pp, sing_all, s);
+    std::vector<int32_t> reps(init.begin(), init.end());
+    std::vector<int32_t> hphi((size_t)count), hoff((size_t)m + 1), hlist((size_t)count);
+    std::vector<double> hV((size_t)count);
+    PSR_CUDA(ctx, cudaMemsetAsync(phi, 0xff, sizeof(int32_t) * (size_t)count, s));
+    const int gb = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)m * pp + 255) / 256, 152 * 16));
+    const int kb = std::max(1, std::min((count + 3) / 4, 152 * 16));
+    const size_t scratch = sizeof(double) * 4 * p * (p + 1);
+    int sweeps = 0;
+    while (rc == PSR_OK && sweeps < max_iter) {
+        ++sweeps;
+        PSR_CUDA(ctx, cudaMemcpyAsync(d_reps, reps.data(), sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
+        count_launch(); k_kmeans_gather<<<gb, 256, 0, s>>>(Ag, d_reps, m, pp, B);
+        count_launch(); k_kmeans_gather<<<gb, 256, 0, s>>>(Ainv, d_reps, m, pp, Bcur);
+        PSR_CUDA(ctx, cudaMemsetAsync(changes, 0, sizeof(int32_t), s));
+        count_launch();
+        k_kmeans_assign_spectral<<<kb, 128, scratch, s>>>(Ag, count, p, B, Bcur, m, phi, changes);
+        int32_t h_changes = 0;
+        PSR_CUDA(ctx, cudaMemcpyAsync(&h_changes, changes, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        PSR_CUDA(ctx, cudaMemcpyAsync(hphi.data(), phi, sizeof(int32_t) * (size_t)count, cudaMemcpyDeviceToHost, s));
+        PSR_CUDA(ctx, cudaStreamSynchronize(s));
+        if (h_changes == 0) break;
+        std::fill(hoff.begin(), hoff.end(), 0);
+        for (int i = 0; i < count; ++i) ++hoff[(size_t)hphi[i] + 1];
+        for (int j = 0; j < m; ++j) hoff[(size_t)j + 1] += hoff[j];
+        std::vector<int32_t> fill(hoff.begin(), hoff.end() - 1);
+        for (int i = 0; i < count; ++i) hlist[(size_t)fill[hphi[i]]++] = i;
+        PSR_CUDA(ctx, cudaMemcpyAsync(moff, hoff.data(), sizeof(int32_t) * hoff.size(), cudaMemcpyHostToDevice, s));
+        PSR_CUDA(ctx, cudaMemcpyAsync(mlist, hlist.data(), sizeof(int32_t) * hlist.size(), cudaMemcpyHostToDevice, s));
+        count_launch();
+        k_kmeans_variance<<<kb, 128, scratch, s>>>(Ag, Ainv, count, p, phi, moff, mlist, V);
+        PSR_CHECK_LAUNCH(ctx, "k-means variances");
+        PSR_CUDA(ctx, cudaMemcpyAsync(hV.data(), V, sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost, s));
+        PSR_CUDA(ctx, cudaStreamSynchronize(s));
+        for (int j = 0; j < m; ++j) {
+            int best = -1;
+            for (int q = hoff[j]; q < hoff[j + 1]; ++q)
+                if (best < 0 || hV[hlist[q]] < hV[best]) best = hlist[q];
+            if (best >= 0) reps[j] = best;         // an empty cluster keeps its representative
+        }
+    }
+    // the database: the representatives' patches and inverses
+    double* Bdb = nullptr;
+    std::vector<int32_t> hsing((size_t)count);
+    if (rc == PSR_OK) {
+        PSR_CUDA(ctx, cudaMemcpyAsync(d_reps, reps.data(), sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
+        PSR_CUDA(ctx, cudaMalloc(&Bdb, sizeof(double) * (size_t)m * pp));
+        count_launch(); k_kmeans_gather<<<gb, 256, 0, s>>>(Ag, d_reps, m, pp, B);
+        count_launch(); k_kmeans_gather<<<gb, 256, 0, s>>>(Ainv, d_reps, m, pp, Bdb);
+        PSR_CUDA(ctx, cudaMemcpyAsync(hsing.data(), sing_all, sizeof(int32_t) * (size_t)count, cudaMemcpyDeviceToHost, s));
+        PSR_CUDA(ctx, cudaStreamSynchronize(s));
+        for (int j = 0; j < m; ++j)
+            if (hsing[reps[j]]) {
+                set_error(ctx, "representative patch " + std::to_string(G.h_gidx[reps[j]]) +
+                                   " failed the pivot test (singular)");
+                rc = PSR_ERR_SINGULAR_PATCH;
+                break;
+            }
+    }
+    for (void* q : {(void*)Ainv, (void*)sing_all, (void*)Bcur, (void*)V, (void*)changes, (void*)moff, (void*)mlist,
+                    (void*)d_reps})
+        cudaFree(q);
+    if (rc != PSR_OK) {
+        cudaFree(B);
+        cudaFree(phi);
+        cudaFree(Bdb);
+        return rc;
+    }
+    G.dbA = B;
+    G.m = m;
+    G.sphi = phi;
+    G.rinv = Bdb;
+    G.h_rep.assign(reps.begin(), reps.end());
+    ctx->stats.rounds = sweeps;
+    ctx->stats.criterion_evals = 0;
+    return PSR_OK;
+}
+
 int run_kmeans(psr_ctx* ctx, cudaStream_t s, int m, const std::vector<int32_t>& init, int max_iter) {
+    if (ctx->opts.criterion == PSR_CRITERION_VARMIN) return run_kmeans_varmin(ctx, s, m, init, max_iter);
     Group& G = ctx->groups[0];
     const int p = G.p, pp = p * p, count = G.count;
     const bool spectral = ctx->opts.criterion == PSR_CRITERION_SPECTRAL;

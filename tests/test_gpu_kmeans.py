@@ -152,3 +152,34 @@ def test_kmeans_spectral_bit_exact(lib, case):
     zo = O.apply(r, pr.dofs2d(), ref["Binv"], ref["phi"], W, pr.weighting)
     assert np.abs(z.cpu().numpy() - zo).max() <= 1e-11 * np.abs(zo).max()
     ctx.destroy()
+
+
+@pytest.mark.parametrize("case", ["c1_classes", "diff3d_random"])
+def test_kmeans_varmin_bit_exact(lib, case):
+    """Variance-minimising variant: representatives are the members of least
+    in-cluster variance (spectral distance), stored with their own inverses."""
+    if case == "c1_classes":
+        pr = P.poisson2d_q2(16)
+        init = np.array([0, 1, 15, 16, 17, 31, 240, 241, 255], dtype=np.int32)
+    else:
+        pr = P.diffusion3d_q2(4, sigma=0.5, corr_len=3.0, seed=1)
+        init = np.random.default_rng(6).choice(pr.n_patches, 5, replace=False).astype(np.int32)
+    A = O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d())
+    ref = O.kmeans_varmin(A, init)
+    assert ref["near_ties"] == []
+    ctx = kmeans_ctx(lib, pr, init, criterion="varmin", weighting=pr.weighting, krylov=pr.krylov)
+    phi, reps, m = ctx.assignment()
+    assert np.array_equal(phi.cpu().numpy(), ref["phi"]) and np.array_equal(reps.cpu().numpy(), ref["reps"])
+    assert ctx.stats()["rounds"] == ref["sweeps"]
+    assert np.array_equal(ctx.export_database().cpu().numpy(), A[ref["reps"]])
+    r = np.random.default_rng(10).standard_normal(pr.n)
+    z = torch.empty(pr.n, dtype=torch.float64, device="cuda")
+    ctx.apply(dev(r, torch.float64), z)
+    W = O.weights(O.multiplicity(pr.n, pr.patch_dofs))
+    zo = O.apply(r, pr.dofs2d(), ref["Binv"], ref["phi"], W, pr.weighting)
+    assert np.abs(z.cpu().numpy() - zo).max() <= 1e-11 * np.abs(zo).max()
+    ctx.destroy()
+    rp, ci, va = dev(pr.rowptr, torch.int32), dev(pr.colidx, torch.int32), dev(pr.vals, torch.float64)
+    with pytest.raises(lib.PsrError):                      # Alg. 1 has no variance-minimising form
+        lib.psr_setup(rp, ci, va, dev(pr.patch_dofs, torch.int32), uniform_size=pr.uniform_size,
+                      opts=lib.make_opts(tol=0.1, criterion="varmin"))

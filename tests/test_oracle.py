@@ -560,3 +560,37 @@ def test_kmeans_spectral_pins():
     assert list(rs["phi"]) == [0, 0, 1, 1, 0]
     ri = O.kmeans_spectral(As, np.arange(5))
     assert list(ri["phi"]) == [0, 1, 2, 3, 4] and ri["sweeps"] == 2
+
+
+def test_kmeans_varmin_pins():
+    """Variance-minimising Alg. 2: on C1 with class seeds the representatives
+    stay the seeds (all members of a class are equal: every variance is 0 and
+    the lowest index wins); for scaled copies d(s_k B, s_m B) = |1 - s_k/s_m|,
+    so the medoid is the closed-form minimiser; the final state is a fixed
+    point checked by brute force."""
+    pr = P.poisson2d_q2(16)
+    A = O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d())
+    seeds = np.array([0, 1, 15, 16, 17, 31, 240, 241, 255])
+    r = O.kmeans_varmin(A, seeds)
+    assert np.array_equal(r["phi"], O.alg1(A, 1e-3)["phi"]) and list(r["reps"]) == list(seeds)
+    g = np.random.default_rng(4)
+    B = g.standard_normal((5, 5)) + 5 * np.eye(5)
+    C = g.standard_normal((5, 5)) + 5 * np.eye(5)
+    s = np.array([1.0, 1.01, 1.03, 1.06])
+    As = np.concatenate([s[:, None, None] * B[None], np.stack([C, 1.02 * C])])
+    rs = O.kmeans_varmin(As, np.array([0, 4]))
+    assert list(rs["phi"]) == [0, 0, 0, 0, 1, 1]
+    V = [sum((1 - sk / sm) ** 2 for sk in s) for sm in s]
+    assert rs["reps"][0] == int(np.argmin(V))
+    pd = P.diffusion3d_q2(4, sigma=0.5, corr_len=3.0, seed=1)
+    A3 = O.extract_patches(pd.rowptr, pd.colidx, pd.vals, pd.n, pd.dofs2d())
+    r3 = O.kmeans_varmin(A3, np.random.default_rng(6).choice(len(A3), 5, replace=False))
+    I = np.eye(A3.shape[1])
+    dn = lambda i, m: np.linalg.svd(I - A3[i] @ np.linalg.inv(A3[m]), compute_uv=False)[0]
+    for i in range(len(A3)):
+        assert r3["phi"][i] == int(np.argmin([dn(i, m) for m in r3["reps"]]))
+    for j, m in enumerate(r3["reps"]):
+        mem = np.flatnonzero(r3["phi"] == j)
+        if mem.size:
+            Vm = [sum(dn(k, c) ** 2 for k in mem) for c in mem]
+            assert m == mem[int(np.argmin(Vm))]
