@@ -957,11 +957,11 @@ __device__ __forceinline__ void pair_update(const float2* __restrict__ Vs, float
 // The last update fused with the normalisation when ||w'|| is known before it:
 // w' <- (scf w' - V hs) * inv, written as the pair Ws and the FP64 w.  The
 // product by inv on pairs when pair_scale, else in FP64.
-template <int NV>
+template <int NV, bool PAIR_SCALE>
 __device__ __forceinline__ void pair_update_normalize(const float2* __restrict__ Vs, float2* __restrict__ Ws,
                                                       double* __restrict__ w, int n, int nv, const float2* hs,
-                                                      float scf, double inv, bool pair_scale) {
-    const float2 is = split_f64(pair_scale ? inv : 1.0);
+                                                      float scf, double inv) {
+    const float2 is = split_f64(PAIR_SCALE ? inv : 1.0);
     for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += gridDim.x * KT) {
         float2 vv[NV];
 #pragma unroll
@@ -980,7 +980,7 @@ __device__ __forceinline__ void pair_update_normalize(const float2* __restrict__
         d = __fadd_rn(d, __fsub_rn(q.y, cl[0]));
         fast_two_sum(t, d, nh, nl);
         float2 v;
-        if (pair_scale) {
+        if (PAIR_SCALE) {
             const float p = __fmul_rn(nh, is.x);
             const float pe = __fmaf_rn(nh, is.x, -p);
             const float c2 = __fmaf_rn(nh, is.y, __fmul_rn(nl, is.x));
@@ -991,6 +991,135 @@ __device__ __forceinline__ void pair_update_normalize(const float2* __restrict__
         Ws[e] = v;
         w[e] = (double)v.x + (double)v.y;
     }
+}
+
+// Rare forms of the pair path, out of line like the FP64 form below: the
+// last update with the product by inv in FP64 (inv beyond the FP32 range)...
+template <int NV>
+__device__ __noinline__ void pair_update_normalize_wide(const float2* __restrict__ Vs, float2* __restrict__ Ws,
+                                                        double* __restrict__ w, int n, int nv, const float2* hs,
+                                                        float scf, double inv) {
+    pair_update_normalize<NV, false>(Vs, Ws, w, n, nv, hs, scf, inv);
+}
+
+// ... the second update with an explicit norm (when ||x||^2 - ||h2||^2 may
+// cancel), returning ||w'||^2 ...
+template <int NV>
+__device__ __noinline__ double pair_pass3_norm(const float2* __restrict__ Vs, float2* __restrict__ Ws, int n, int nv,
+                                               const float2* hs, double* shw, double* __restrict__ P3,
+                                               unsigned int* bar, int32_t* ictl) {
+    float ah[NV], al[NV];
+    double accw = 0.0;
+    pair_update<NV, false>(Vs, Ws, n, nv, hs, 1.f, ah, al, accw);
+    const double bs = block_sum_kt(accw, shw);
+    if (threadIdx.x == 0) P3[(int64_t)NV * gridDim.x + blockIdx.x] = bs;
+    grid_barrier(bar, ictl);
+    return norm_total(P3 + (int64_t)NV * gridDim.x, gridDim.x, shw);
+}
+
+// ... and the normalisation after it.
+__device__ __noinline__ void pair_normalize(float2* __restrict__ Ws, double* __restrict__ w, int n, double inv) {
+    if (inv <= 0x1p100) {
+        const float2 is = split_f64(inv);
+        for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += gridDim.x * KT) {
+            const float2 q = Ws[e];
+            const float p = __fmul_rn(q.x, is.x);
+            const float pe = __fmaf_rn(q.x, is.x, -p);
+            const float c = __fmaf_rn(q.x, is.y, __fmul_rn(q.y, is.x));
+            float vh, vl;
+            fast_two_sum(p, __fadd_rn(pe, c), vh, vl);
+            Ws[e] = make_float2(vh, vl);
+            w[e] = (double)vh + (double)vl;
+        }
+    } else {
+        for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += gridDim.x * KT) {
+            const float2 q = Ws[e];
+            const float2 v = split_f64(((double)q.x + (double)q.y) * inv);
+            Ws[e] = v;
+            w[e] = (double)v.x + (double)v.y;
+        }
+    }
+}
+
+// The FP64 form of the step (PSR_ORTHO_FP64, or w outside the pair range),
+// kept out of line so that the pair path's code stays contiguous.  All
+// threads of the block call them; sh, shw, s_w2, sh_h and s_col are the
+// kernel's shared arrays.
+// Pass 1 in FP64: h = V^T w (returned where the vector's lane group holds
+// it) and ||w||^2 into *s_w2.
+template <int NV>
+__device__ __noinline__ double fp64_pass1(const double* __restrict__ V, const double* __restrict__ w, int n, int nv,
+                                          double* __restrict__ P4, double (*sh)[KT / 32 + 1], double* shw,
+                                          double* s_w2, unsigned int* bar, int32_t* ictl) {
+    const int G = gridDim.x;
+    double acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    double accw = 0.0;
+    for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += G * KT) {
+        const double we = w[e];
+        accw = fma(we, we, accw);
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+            if (i < nv) acc[i] = fma(V[(int64_t)i * n + e], we, acc[i]);
+    }
+    block_partials<NV>(acc, nv, P4, sh);
+    const double bs = block_sum_kt(accw, shw);
+    if (threadIdx.x == 0) P4[(int64_t)NV * G + blockIdx.x] = bs;
+    grid_barrier(bar, ictl);
+    double t;
+    const double hv = final_partials_w2<NV>(P4, nv, G, shw, t);
+    if (threadIdx.x == 0) *s_w2 = t;
+    __syncthreads();
+    return hv;
+}
+
+// The FP64 updates (the second projection when reorth), the norm and the
+// normalisation (with the pair copy); returns ||w||.
+template <int NV>
+__device__ __noinline__ double fp64_rest(const double* __restrict__ V, double* __restrict__ w,
+                                         float2* __restrict__ Ws, int n, int nv, bool reorth, double* sh_h,
+                                         double (*sh)[KT / 32 + 1], double* shw, double* s_col, double* s_w2,
+                                         double* __restrict__ P2, double* __restrict__ P3, unsigned int* bar,
+                                         int32_t* ictl) {
+    const int G = gridDim.x;
+    constexpr int T = KT / NV;
+    double acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    double accw = 0.0;
+    if (reorth) {
+        update_pass<NV, true>(V, w, n, nv, sh_h, acc, accw);
+        block_partials<NV>(acc, nv, P2, sh);
+        grid_barrier(bar, ictl);
+        const double v2 = final_partials<NV>(P2, nv, G);
+        __syncthreads();
+        if (threadIdx.x / T < nv && threadIdx.x % T == 0) sh_h[threadIdx.x / T] = v2;
+        __syncthreads();
+        if (blockIdx.x == 0 && threadIdx.x < nv) s_col[threadIdx.x] += sh_h[threadIdx.x];
+        update_pass<NV, false>(V, w, n, nv, sh_h, acc, accw);
+        const double bs = block_sum_kt(accw, shw);
+        if (threadIdx.x == 0) P3[(int64_t)NV * G + blockIdx.x] = bs;
+        grid_barrier(bar, ictl);
+        const double t = norm_total(P3 + (int64_t)NV * G, G, shw);
+        if (threadIdx.x == 0) *s_w2 = t;
+    } else {
+        update_pass<NV, false>(V, w, n, nv, sh_h, acc, accw);
+        const double bs = block_sum_kt(accw, shw);
+        if (threadIdx.x == 0) P2[(int64_t)NV * G + blockIdx.x] = bs;
+        grid_barrier(bar, ictl);
+        const double t = norm_total(P2 + (int64_t)NV * G, G, shw);
+        if (threadIdx.x == 0) *s_w2 = t;
+    }
+    __syncthreads();
+    const double hn = sqrt(*s_w2);
+    const double inv = hn != 0.0 ? 1.0 / hn : 1.0;
+    for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += G * KT) {
+        const float2 v = split_f64(w[e] * inv);
+        Ws[e] = v;
+        w[e] = (double)v.x + (double)v.y;
+    }
+    return hn;
 }
 
 // The whole orthogonalisation of step j in one cooperative launch: w = V_{j+1}
@@ -1077,28 +1206,7 @@ __global__ void __launch_bounds__(KT, 1) k_arnoldi(const double* __restrict__ V,
         __syncthreads();
         pairs = s_w2 >= 0x1p-160 && s_w2 <= 0x1p120;  // same in every block
     }
-    if (!pairs) {
-        // pass 1 in FP64
-        double acc[NV];
-#pragma unroll
-        for (int i = 0; i < NV; ++i) acc[i] = 0.0;
-        double accw = 0.0;
-        for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += G * KT) {
-            const double we = w[e];
-            accw = fma(we, we, accw);
-#pragma unroll
-            for (int i = 0; i < NV; ++i)
-                if (i < nv) acc[i] = fma(V[(int64_t)i * n + e], we, acc[i]);
-        }
-        block_partials<NV>(acc, nv, P4, sh);
-        const double bs = block_sum_kt(accw, shw);
-        if (threadIdx.x == 0) P4[(int64_t)NV * G + blockIdx.x] = bs;
-        grid_barrier(bar, kd.ictl);
-        double t;
-        hv = final_partials_w2<NV>(P4, nv, G, shw, t);
-        if (threadIdx.x == 0) s_w2 = t;
-        __syncthreads();
-    }
+    if (!pairs) hv = fp64_pass1<NV>(V, w, n, nv, P4, sh, shw, &s_w2, bar, kd.ictl);
     // scale 2^k of the pair path: ||2^k w|| in [1, 2)
     const int k = pairs ? -(ilogb(s_w2) >> 1) : 0;
     if (threadIdx.x % T == 0) {                       // every slot i < NV (zero past nv)
@@ -1167,11 +1275,7 @@ __global__ void __launch_bounds__(KT, 1) k_arnoldi(const double* __restrict__ V,
                 ws2 = x2 - s_h2;
                 known = true;
             } else {
-                pair_update<NV, false>(Vs, Ws, n, nv, sh_hs, 1.f, ah, al, accw);
-                const double bs = block_sum_kt(accw, shw);
-                if (threadIdx.x == 0) P3[(int64_t)NV * G + blockIdx.x] = bs;
-                grid_barrier(bar, kd.ictl);
-                ws2 = norm_total(P3 + (int64_t)NV * G, G, shw);
+                ws2 = pair_pass3_norm<NV>(Vs, Ws, n, nv, sh_hs, shw, P3, bar, kd.ictl);
             }
         } else {
             ws2 = ldexp(s_w2 - s_h2, 2 * k);              // > ||w'||^2 / 2 by the test
@@ -1181,66 +1285,15 @@ __global__ void __launch_bounds__(KT, 1) k_arnoldi(const double* __restrict__ V,
         const double hn = sqrt(ws2);
         hn_w = ldexp(hn, -k);                         // exact: sqrt(2^2k x) = 2^k sqrt(x)
         const double inv = hn != 0.0 ? 1.0 / hn : 1.0;
-        if (known) {
-            pair_update_normalize<NV>(Vs, Ws, w, n, nv, sh_hs, last_scf, inv, inv <= 0x1p100);
-        } else if (inv <= 0x1p100) {
-            const float2 is = split_f64(inv);
-            for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += G * KT) {
-                const float2 q = Ws[e];
-                const float p = __fmul_rn(q.x, is.x);
-                const float pe = __fmaf_rn(q.x, is.x, -p);
-                const float c = __fmaf_rn(q.x, is.y, __fmul_rn(q.y, is.x));
-                float vh, vl;
-                fast_two_sum(p, __fadd_rn(pe, c), vh, vl);
-                Ws[e] = make_float2(vh, vl);
-                w[e] = (double)vh + (double)vl;
-            }
+        if (known && inv <= 0x1p100) {
+            pair_update_normalize<NV, true>(Vs, Ws, w, n, nv, sh_hs, last_scf, inv);
+        } else if (known) {
+            pair_update_normalize_wide<NV>(Vs, Ws, w, n, nv, sh_hs, last_scf, inv);
         } else {
-            for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += G * KT) {
-                const float2 q = Ws[e];
-                const float2 v = split_f64(((double)q.x + (double)q.y) * inv);
-                Ws[e] = v;
-                w[e] = (double)v.x + (double)v.y;
-            }
+            pair_normalize(Ws, w, n, inv);
         }
     } else {
-        // FP64 passes on V and w; the pair copy written by the normalisation
-        double acc[NV];
-#pragma unroll
-        for (int i = 0; i < NV; ++i) acc[i] = 0.0;
-        double accw = 0.0;
-        if (reorth) {
-            update_pass<NV, true>(V, w, n, nv, sh_h, acc, accw);
-            block_partials<NV>(acc, nv, P2, sh);
-            grid_barrier(bar, kd.ictl);
-            const double v2 = final_partials<NV>(P2, nv, G);
-            __syncthreads();
-            if (threadIdx.x / T < nv && threadIdx.x % T == 0) sh_h[threadIdx.x / T] = v2;
-            __syncthreads();
-            if (blockIdx.x == 0 && threadIdx.x < nv) s_col[threadIdx.x] += sh_h[threadIdx.x];
-            update_pass<NV, false>(V, w, n, nv, sh_h, acc, accw);
-            const double bs = block_sum_kt(accw, shw);
-            if (threadIdx.x == 0) P3[(int64_t)NV * G + blockIdx.x] = bs;
-            grid_barrier(bar, kd.ictl);
-            const double t = norm_total(P3 + (int64_t)NV * G, G, shw);
-            if (threadIdx.x == 0) s_w2 = t;
-        } else {
-            update_pass<NV, false>(V, w, n, nv, sh_h, acc, accw);
-            const double bs = block_sum_kt(accw, shw);
-            if (threadIdx.x == 0) P2[(int64_t)NV * G + blockIdx.x] = bs;
-            grid_barrier(bar, kd.ictl);
-            const double t = norm_total(P2 + (int64_t)NV * G, G, shw);
-            if (threadIdx.x == 0) s_w2 = t;
-        }
-        __syncthreads();
-        const double hn = sqrt(s_w2);
-        hn_w = hn;
-        const double inv = hn != 0.0 ? 1.0 / hn : 1.0;
-        for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += G * KT) {
-            const float2 v = split_f64(w[e] * inv);
-            Ws[e] = v;
-            w[e] = (double)v.x + (double)v.y;
-        }
+        hn_w = fp64_rest<NV>(V, w, Ws, n, nv, reorth, sh_h, sh, shw, s_col, &s_w2, P2, P3, bar, kd.ictl);
     }
     if (blockIdx.x == 0 && threadIdx.x < 32) arnoldi_finish_warp(kd, j, hn_w, s_col, s_rot, NV, s_g, s_it);
 }
