@@ -67,10 +67,10 @@ KT_KERNEL_NAMES = {"sweep": "patch sweep (k_sweep_staged / k_sweep_*)", "spmv": 
 # the kernel source they were taken on; None until captured.
 TRAFFIC = {
     # ncu --set full of the fused Gram-Schmidt step on pairs at j = 20
-    # (26.32 MB: one DRAM read of the 21 pair rows and of w, later passes
+    # (26.30 MB: one DRAM read of the 21 pair rows and of w, later passes
     # from L2) scaled to the mean basis size of a step, (j+2) averaged over
     # j = 0..29
-    ("stokes2d", "mdot"): 26.32e6 * 16.5 / 22.0,
+    ("stokes2d", "mdot"): 26.30e6 * 16.5 / 22.0,
     # ncu --set full, one launch inside the FGMRES cycle (k_spmv_sell):
     # 89.11 MB read + 2.47 MB written
     ("stokes2d", "spmv"): 91.6e6,
