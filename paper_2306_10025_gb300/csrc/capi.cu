@@ -33,8 +33,7 @@ int cuda_fail(psr_ctx* ctx, cudaError_t e, const char* what) {
     return (e == cudaErrorMemoryAllocation) ? PSR_ERR_OOM : PSR_ERR_CUDA;
 }
 
-int build_sweep_layout(psr_ctx* ctx, const std::vector<int32_t>& h_dofs,
-                       const std::vector<std::vector<int32_t>>& gidx, cudaStream_t s);
+int build_sweep_layout(psr_ctx* ctx, const std::vector<std::vector<int32_t>>& gidx, cudaStream_t s);
 int sweep_prepare(psr_ctx* ctx);
 
 __global__ void k_iota(int32_t* a, int n) {
@@ -149,8 +148,6 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
         CK(cudaMemcpyAsync(ctx->offsets, ctx->h_offsets.data(), sizeof(int32_t) * (size_t)(np + 1), cudaMemcpyHostToDevice, s));
         CK(cudaMalloc(&ctx->dofs, sizeof(int32_t) * (size_t)total));
         CK(cudaMemcpyAsync(ctx->dofs, P->dofs, sizeof(int32_t) * (size_t)total, cudaMemcpyDeviceToDevice, s));
-        std::vector<int32_t> h_dofs((size_t)total);
-        CK(cudaMemcpyAsync(h_dofs.data(), P->dofs, sizeof(int32_t) * (size_t)total, cudaMemcpyDeviceToHost, s));
         // --- validation
         rc = validate_inputs(ctx, A, ctx->offsets, ctx->dofs, np, total, ctx->status, s);
         if (rc != PSR_OK) goto fail;
@@ -272,7 +269,7 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
             FAIL(PSR_ERR_SINGULAR_PATCH);
         }
         t0 = std::chrono::steady_clock::now();
-        rc = build_sweep_layout(ctx, h_dofs, gidx, s);
+        rc = build_sweep_layout(ctx, gidx, s);
         if (rc != PSR_OK) goto fail;
         rc = sweep_prepare(ctx);
         if (rc != PSR_OK) goto fail;

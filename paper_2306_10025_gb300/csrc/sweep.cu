@@ -452,13 +452,18 @@ static size_t sweep_smem(int p, int prec, int warps) {
     return ((p * p * es + 15) & ~(size_t)15) + (size_t)warps * 128 * es;
 }
 
-static int make_tiles(psr_ctx* ctx, Group& G, const std::vector<int32_t>& sorted_phi, int T) {
+static int cuda_fail_if(psr_ctx* ctx, cudaError_t e, const char* what) {
+    return e == cudaSuccess ? PSR_OK : cuda_fail(ctx, e, what);
+}
+
+// Tiles (entry, first sorted patch, count <= T) of a group's sweep order.
+static std::vector<int32_t> tiles_host(const std::vector<int32_t>& sorted_phi, int count, int T) {
     std::vector<int32_t> t;
     int i = 0;
-    while (i < G.count) {
+    while (i < count) {
         const int c = sorted_phi[i];
         int j = i;
-        while (j < G.count && sorted_phi[j] == c) ++j;
+        while (j < count && sorted_phi[j] == c) ++j;
         for (int s = i; s < j; s += T) {
             t.push_back(c);
             t.push_back(s);
@@ -466,6 +471,11 @@ static int make_tiles(psr_ctx* ctx, Group& G, const std::vector<int32_t>& sorted
         }
         i = j;
     }
+    return t;
+}
+
+static int make_tiles(psr_ctx* ctx, Group& G, const std::vector<int32_t>& sorted_phi, int T) {
+    const std::vector<int32_t> t = tiles_host(sorted_phi, G.count, T);
     if (G.tiles) cudaFree(G.tiles);
     G.tiles = nullptr;
     G.ntiles = (int)(t.size() / 3);
@@ -475,11 +485,35 @@ static int make_tiles(psr_ctx* ctx, Group& G, const std::vector<int32_t>& sorted
     return PSR_OK;
 }
 
+// Sweep-order DOF list of a group, gathered from the flat DOF map: sorted
+// patch i is patch[i], its DOFs go to sdofs[i * p .. i * p + p).
+__global__ void k_gather_sdofs(const int32_t* __restrict__ patch, int count, int p,
+                               const int32_t* __restrict__ offsets, const int32_t* __restrict__ dofs,
+                               int32_t* __restrict__ sdofs) {
+    const int64_t total = (int64_t)count * p;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / p);
+        sdofs[e] = dofs[offsets[patch[i]] + (int)(e - (int64_t)i * p)];
+    }
+}
+
+// Local-DOF-major copy for the thread-per-patch kernel: sdofs_t[a * count + i].
+__global__ void k_transpose_sdofs(const int32_t* __restrict__ sdofs, int count, int p, int32_t* __restrict__ sdofs_t) {
+    const int64_t total = (int64_t)count * p;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(e / count);
+        const int i = (int)(e - (int64_t)a * count);
+        sdofs_t[e] = sdofs[(int64_t)i * p + a];
+    }
+}
+
+static int gather_grid(int64_t total) { return (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 8)); }
+
 // Build the sweep layout from the Alg. 1 output left in every group
 // (G.sphi = local phi in original order, G.rinv = FP64 database), and the
-// global phi / rep_ids.  h_dofs: host copy of the flat DOF map.
-int build_sweep_layout(psr_ctx* ctx, const std::vector<int32_t>& h_dofs,
-                       const std::vector<std::vector<int32_t>>& gidx, cudaStream_t s) {
+// global phi / rep_ids.  The DOF lists in sweep order are gathered on the
+// device from the flat DOF map (ctx->offsets, ctx->dofs).
+int build_sweep_layout(psr_ctx* ctx, const std::vector<std::vector<int32_t>>& gidx, cudaStream_t s) {
     const int prec = ctx->opts.store_prec;
     std::vector<int32_t> phi_global(ctx->n_patches, -1);
     std::vector<int32_t> rep_global;
@@ -493,14 +527,12 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<int32_t>& h_dofs,
         std::vector<int32_t> order(count);
         std::iota(order.begin(), order.end(), 0);
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lphi[a] < lphi[b]; });
-        std::vector<int32_t> hp(count), hs(count), hd((size_t)count * p);
+        std::vector<int32_t> hp(count), hs(count);
         for (int i = 0; i < count; ++i) {
             const int l = order[i];
             const int k = gidx[g][l];
             hp[i] = k;
             hs[i] = lphi[l];
-            const int off = ctx->h_offsets[k];
-            for (int a = 0; a < p; ++a) hd[(size_t)i * p + a] = h_dofs[off + a];
             phi_global[k] = entry_base + lphi[l];
         }
         for (int j = 0; j < G.m; ++j) rep_global.push_back(G.h_rep[j] >= 0 ? gidx[g][G.h_rep[j]] : -1);
@@ -509,9 +541,13 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<int32_t>& h_dofs,
         PSR_CUDA(ctx, cudaMalloc(&G.patch, sizeof(int32_t) * count));
         PSR_CUDA(ctx, cudaMalloc(&G.sphi, sizeof(int32_t) * count));
         PSR_CUDA(ctx, cudaMalloc(&G.sdofs, sizeof(int32_t) * (size_t)count * p));
-        PSR_CUDA(ctx, cudaMemcpy(G.patch, hp.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice));
-        PSR_CUDA(ctx, cudaMemcpy(G.sphi, hs.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice));
-        PSR_CUDA(ctx, cudaMemcpy(G.sdofs, hd.data(), sizeof(int32_t) * (size_t)count * p, cudaMemcpyHostToDevice));
+        // on the stream of the gather below (a pageable source is staged
+        // before the call returns)
+        PSR_CUDA(ctx, cudaMemcpyAsync(G.patch, hp.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, s));
+        PSR_CUDA(ctx, cudaMemcpyAsync(G.sphi, hs.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, s));
+        count_launch();
+        k_gather_sdofs<<<gather_grid((int64_t)count * p), 256, 0, s>>>(G.patch, count, p, ctx->offsets, ctx->dofs, G.sdofs);
+        PSR_CHECK_LAUNCH(ctx, "k_gather_sdofs");
         // storage precision
         double* db64 = reinterpret_cast<double*>(G.rinv);
         const int64_t ne = (int64_t)G.m * p * p;
@@ -574,11 +610,11 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<int32_t>& h_dofs,
         }
         G.h_sorted_phi = hs;
         if (!G.tc && G.m < G.count && p <= 32) {
-            std::vector<int32_t> ht((size_t)count * p), wt;
-            for (int i = 0; i < count; ++i)
-                for (int a = 0; a < p; ++a) ht[(size_t)a * count + i] = hd[(size_t)i * p + a];
+            std::vector<int32_t> wt;
             PSR_CUDA(ctx, cudaMalloc(&G.sdofs_t, sizeof(int32_t) * (size_t)count * p));
-            PSR_CUDA(ctx, cudaMemcpy(G.sdofs_t, ht.data(), sizeof(int32_t) * ht.size(), cudaMemcpyHostToDevice));
+            count_launch();
+            k_transpose_sdofs<<<gather_grid((int64_t)count * p), 256, 0, s>>>(G.sdofs, count, p, G.sdofs_t);
+            PSR_CHECK_LAUNCH(ctx, "k_transpose_sdofs");
             int i = 0;
             while (i < count) {
                 int j = i;
@@ -652,45 +688,46 @@ int build_grouped_tables(psr_ctx* ctx) {
 }
 
 // Project-written autotuner: times candidate tile shapes of the sweep on the
-// caller's stream (CUDA events, median of 5 after 2 warm-up launches) and
-// keeps the fastest.  Per size group for the per-group kernels (patches per
-// tile x warps per CTA); tiles per group x persistent grid size for the
-// grouped kernel.  Tensor-core tiles are fixed at 128 patches (M = 128).
+// caller's stream (CUDA events) and keeps the fastest.  Per size group for
+// the per-group kernels (patches per tile x warps per CTA, and the
+// thread-per-patch kernel where it applies): every candidate's tiles go to
+// the device in one copy, all candidates run back to back (one warm-up and
+// three timed applies each, median kept) and the host waits once per group.
+// Tiles per group x persistent grid size for the grouped kernel.
+// Tensor-core tiles are fixed at 128 patches (M = 128).
 int autotune_sweep(psr_ctx* ctx, cudaStream_t s) {
     if (!ctx->opts.autotune) return PSR_OK;
     double* r = ctx->ws.r;
     double* z = ctx->ws.z;
     if (!r || !z) return PSR_OK;
     PSR_CUDA(ctx, cudaMemsetAsync(r, 0, sizeof(double) * (size_t)ctx->n, s));
-    // five back-to-back timed applies between six events, one host wait per
-    // candidate (a wait per apply cost more than the applies)
-    constexpr int NT = 5;
-    cudaEvent_t ev[NT + 1];
-    for (auto& e : ev) PSR_CUDA(ctx, cudaEventCreate(&e));
-    auto time_apply = [&](float* out_ms) -> int {
-        for (int w = 0; w < 2; ++w) {
-            int rc = sweep_apply_ex(ctx, r, z, nullptr, s);
-            if (rc != PSR_OK) return rc;
-        }
-        cudaEventRecord(ev[0], s);
-        for (int it = 0; it < NT; ++it) {
-            int rc = sweep_apply_ex(ctx, r, z, nullptr, s);
-            if (rc != PSR_OK) return rc;
-            cudaEventRecord(ev[it + 1], s);
-        }
-        cudaEventSynchronize(ev[NT]);
-        std::vector<float> ts;
-        for (int it = 0; it < NT; ++it) {
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, ev[it], ev[it + 1]);
-            ts.push_back(ms);
-        }
-        std::sort(ts.begin(), ts.end());
-        *out_ms = ts[ts.size() / 2];
-        return PSR_OK;
-    };
     int rc = PSR_OK;
     if (ctx->sweep_mode == PSR_SWEEP_GROUPED && ctx->opts.store_prec != PSR_PREC_BF16) {
+        constexpr int NT = 5;
+        cudaEvent_t ev[NT + 1];
+        for (auto& e : ev) PSR_CUDA(ctx, cudaEventCreate(&e));
+        auto time_apply = [&](float* out_ms) -> int {
+            for (int w = 0; w < 2; ++w) {
+                int rc2 = sweep_apply_ex(ctx, r, z, nullptr, s);
+                if (rc2 != PSR_OK) return rc2;
+            }
+            cudaEventRecord(ev[0], s);
+            for (int it = 0; it < NT; ++it) {
+                int rc2 = sweep_apply_ex(ctx, r, z, nullptr, s);
+                if (rc2 != PSR_OK) return rc2;
+                cudaEventRecord(ev[it + 1], s);
+            }
+            cudaEventSynchronize(ev[NT]);
+            std::vector<float> ts;
+            for (int it = 0; it < NT; ++it) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev[it], ev[it + 1]);
+                ts.push_back(ms);
+            }
+            std::sort(ts.begin(), ts.end());
+            *out_ms = ts[ts.size() / 2];
+            return PSR_OK;
+        };
         const int Ts[] = {16, 32, 64, 128};
         const int Bs[] = {152 * 2, 152 * 4, 152 * 8};
         float best = 1e30f;
@@ -713,36 +750,72 @@ int autotune_sweep(psr_ctx* ctx, cudaStream_t s) {
             if (rc == PSR_OK) rc = build_grouped_tables(ctx);
             ctx->grouped_blocks = bB;
         }
-    } else {
-        for (auto& G : ctx->groups) {
-            if (G.tc || (G.m == G.count && G.p <= 32)) continue;   // fixed shapes
-            const int cand[][2] = {{8, 8}, {16, 8}, {16, 4}, {32, 4}, {64, 4}, {32, 8}, {64, 8}, {128, 8}};
-            float best = 1e30f;
-            int bT = G.tile_patches, bW = G.warps;
-            const bool has_tpp = G.tpp;
-            bool b_tpp = false;
-            if (has_tpp) {
-                float ms;
-                if ((rc = time_apply(&ms)) != PSR_OK) break;
-                best = ms;
-                b_tpp = true;
-                G.tpp = false;
-            }
-            for (auto& c : cand) {
-                if ((rc = make_tiles(ctx, G, G.h_sorted_phi, c[0])) != PSR_OK) break;
-                G.warps = c[1];
-                float ms;
-                if ((rc = time_apply(&ms)) != PSR_OK) break;
-                if (ms < best) { best = ms; bT = c[0]; bW = c[1]; b_tpp = false; }
-            }
-            if (rc != PSR_OK) break;
-            G.warps = bW;
-            G.tpp = b_tpp;
-            if ((rc = make_tiles(ctx, G, G.h_sorted_phi, bT)) != PSR_OK) break;
-        }
-        if (rc == PSR_OK) rc = build_grouped_tables(ctx);
+        for (auto& e : ev) cudaEventDestroy(e);
+        return rc;
     }
-    for (auto& e : ev) cudaEventDestroy(e);
+    constexpr int NT = 3;
+    struct Cand { int T, W; bool tpp; size_t off, len; };
+    for (auto& G : ctx->groups) {
+        if (G.tc || (G.m == G.count && G.p <= 32)) continue;   // fixed shapes
+        const int shapes[][2] = {{8, 8}, {16, 8}, {16, 4}, {32, 4}, {64, 4}, {32, 8}, {64, 8}, {128, 8}};
+        std::vector<Cand> cand;
+        std::vector<int32_t> all;
+        if (G.tpp) cand.push_back(Cand{G.tile_patches, G.warps, true, 0, 0});
+        for (auto& sh : shapes) {
+            const std::vector<int32_t> t = tiles_host(G.h_sorted_phi, G.count, sh[0]);
+            cand.push_back(Cand{sh[0], sh[1], false, all.size(), t.size()});
+            all.insert(all.end(), t.begin(), t.end());
+        }
+        int32_t* d_all = nullptr;
+        std::vector<cudaEvent_t> ev(cand.size() * (NT + 1), nullptr);
+        PSR_CUDA(ctx, cudaMalloc(&d_all, sizeof(int32_t) * std::max<size_t>(all.size(), 3)));
+        rc = cuda_fail_if(ctx, cudaMemcpyAsync(d_all, all.data(), sizeof(int32_t) * all.size(), cudaMemcpyHostToDevice, s),
+                          "autotune tiles");
+        for (size_t e = 0; rc == PSR_OK && e < ev.size(); ++e)
+            rc = cuda_fail_if(ctx, cudaEventCreate(&ev[e]), "autotune events");
+        // the group's own tiles stay owned by G; candidates point into d_all
+        int32_t* own = G.tiles;
+        const int own_n = G.ntiles, own_T = G.tile_patches, own_W = G.warps;
+        for (size_t c = 0; rc == PSR_OK && c < cand.size(); ++c) {
+            G.tpp = cand[c].tpp;
+            if (!cand[c].tpp) {
+                G.tiles = d_all + cand[c].off;
+                G.ntiles = (int)(cand[c].len / 3);
+                G.tile_patches = cand[c].T;
+                G.warps = cand[c].W;
+            }
+            cudaEvent_t* e = &ev[c * (NT + 1)];
+            if ((rc = sweep_apply_ex(ctx, r, z, nullptr, s)) != PSR_OK) break;
+            cudaEventRecord(e[0], s);
+            for (int it = 0; it < NT && rc == PSR_OK; ++it) {
+                rc = sweep_apply_ex(ctx, r, z, nullptr, s);
+                cudaEventRecord(e[it + 1], s);
+            }
+            G.tiles = own;
+            G.ntiles = own_n;
+            G.tile_patches = own_T;
+            G.warps = own_W;
+        }
+        if (rc == PSR_OK) rc = cuda_fail_if(ctx, cudaEventSynchronize(ev.back()), "autotune wait");
+        float best = 1e30f;
+        size_t bc = 0;
+        for (size_t c = 0; rc == PSR_OK && c < cand.size(); ++c) {
+            float ts[NT];
+            for (int it = 0; it < NT; ++it) cudaEventElapsedTime(&ts[it], ev[c * (NT + 1) + it], ev[c * (NT + 1) + it + 1]);
+            std::sort(ts, ts + NT);
+            if (ts[NT / 2] < best) { best = ts[NT / 2]; bc = c; }
+        }
+        for (auto e : ev)
+            if (e) cudaEventDestroy(e);
+        if (rc != PSR_OK) { cudaStreamSynchronize(s); cudaFree(d_all); break; }
+        cudaFree(d_all);
+        G.tpp = cand[bc].tpp;
+        if (!cand[bc].tpp) {
+            G.warps = cand[bc].W;
+            if ((rc = make_tiles(ctx, G, G.h_sorted_phi, cand[bc].T)) != PSR_OK) break;
+        }
+    }
+    if (rc == PSR_OK) rc = build_grouped_tables(ctx);
     return rc;
 }
 
