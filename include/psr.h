@@ -258,6 +258,16 @@ const char* psr_last_error(psr_ctx* ctx);
 
 void psr_destroy(psr_ctx* ctx);
 
+/* Memory: the library keeps the device and pinned host blocks that a destroy
+ * (or a setup's temporaries) frees and hands them out again to later
+ * allocations of a similar size (1x to 1.25x), after one device
+ * synchronisation when they were freed since the last; at most 16 GiB per
+ * device is kept, and on out-of-memory the cache is released and the
+ * allocation retried.  This call synchronises every device the library
+ * allocated on and returns all cached blocks to the driver (blocks still in
+ * use by live contexts are not touched).  Returns PSR_OK or PSR_ERR_CUDA. */
+int psr_release_cached_memory(void);
+
 /* Instrumentation: number of CUDA kernels this library has launched in the
  * process so far (a graph launch counts its kernel nodes).  Host-only, never
  * fails; used by benchmarks to state how many kernels a timed region ran. */

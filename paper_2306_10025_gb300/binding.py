@@ -34,7 +34,7 @@ EXPORTS = ["psr_default_opts", "psr_setup", "psr_apply", "psr_solve", "psr_get_h
            "psr_setup_seeded", "psr_features", "psr_mlp_create", "psr_mlp_num_params", "psr_mlp_set_params",
            "psr_mlp_get_params", "psr_mlp_loss_grad", "psr_mlp_train_step", "psr_mlp_predict", "psr_mlp_destroy",
            "psr_criterion_noalloc", "psr_set_kernel_timing", "psr_get_kernel_timing", "psr_setup_kmeans",
-           "psr_export_database", "psr_set_coarse", "psr_smooth"]
+           "psr_export_database", "psr_set_coarse", "psr_smooth", "psr_release_cached_memory"]
 
 KT_CLASSES = ("sweep", "spmv", "mdot", "maxpy", "vec")   # PSR_KT_* in order
 
@@ -119,6 +119,7 @@ def load(path: str = LIB_PATH):
     lib.psr_spectral_norm.argtypes = [vp, i32, i32, vp, vp]
     lib.psr_criterion_noalloc.argtypes = [vp, i32, i32, vp, vp, d, vp, vp, vp]
     lib.psr_kernel_launches.argtypes = []
+    lib.psr_release_cached_memory.argtypes = []
     lib.psr_set_kernel_timing.argtypes = [vp, i32]
     lib.psr_get_kernel_timing.argtypes = [vp, vp, vp, vp, vp, i32]
     lib.psr_setup_seeded.argtypes = [C.POINTER(psr_csr), C.POINTER(psr_patches), C.POINTER(psr_opts), vp, i32, vp,
@@ -460,6 +461,11 @@ def psr_spectral_norm(E, sigma, stream=None):
 
 def psr_kernel_launches() -> int:
     return int(load().psr_kernel_launches())
+
+
+def psr_release_cached_memory() -> None:
+    """Return the library's cached device and pinned host blocks to the driver."""
+    _check(load().psr_release_cached_memory())
 
 
 def exported_symbols(path: str = LIB_PATH) -> list[str]:

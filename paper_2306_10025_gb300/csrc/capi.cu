@@ -57,18 +57,18 @@ static void destroy_ctx(psr_ctx* ctx) {
     free_sweep(ctx);
     coarse_free(ctx);
     krylov_free(ctx);
-    cudaFree(ctx->rowptr);
-    cudaFree(ctx->colidx);
-    cudaFree(ctx->vals);
-    cudaFree(ctx->offsets);
-    cudaFree(ctx->dofs);
-    cudaFree(ctx->mat_off);
-    cudaFree(ctx->A_ext);
-    cudaFree(ctx->W);
-    if (ctx->Wg && ctx->Wg != ctx->W) cudaFree(ctx->Wg);
-    cudaFree(ctx->phi);
-    cudaFree(ctx->rep_ids);
-    cudaFree(ctx->status);
+    psr::dev_free(ctx->rowptr);
+    psr::dev_free(ctx->colidx);
+    psr::dev_free(ctx->vals);
+    psr::dev_free(ctx->offsets);
+    psr::dev_free(ctx->dofs);
+    psr::dev_free(ctx->mat_off);
+    psr::dev_free(ctx->A_ext);
+    psr::dev_free(ctx->W);
+    if (ctx->Wg && ctx->Wg != ctx->W) psr::dev_free(ctx->Wg);
+    psr::dev_free(ctx->phi);
+    psr::dev_free(ctx->rep_ids);
+    psr::dev_free(ctx->status);
     if (cur != ctx->device) cudaSetDevice(cur);
     delete ctx;
 }
@@ -123,11 +123,11 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
 #define CK(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { rc = cuda_fail(ctx, e_, #call); goto fail; } } while (0)
     {
         // --- copies of the inputs
-        CK(cudaMalloc(&ctx->status, sizeof(int32_t)));
+        CK(psr::dev_alloc(&ctx->status, sizeof(int32_t)));
         CK(cudaMemsetAsync(ctx->status, 0, sizeof(int32_t), s));
-        CK(cudaMalloc(&ctx->rowptr, sizeof(int32_t) * (size_t)(n + 1)));
-        CK(cudaMalloc(&ctx->colidx, sizeof(int32_t) * (size_t)std::max<int64_t>(A->nnz, 1)));
-        CK(cudaMalloc(&ctx->vals, sizeof(double) * (size_t)std::max<int64_t>(A->nnz, 1)));
+        CK(psr::dev_alloc(&ctx->rowptr, sizeof(int32_t) * (size_t)(n + 1)));
+        CK(psr::dev_alloc(&ctx->colidx, sizeof(int32_t) * (size_t)std::max<int64_t>(A->nnz, 1)));
+        CK(psr::dev_alloc(&ctx->vals, sizeof(double) * (size_t)std::max<int64_t>(A->nnz, 1)));
         CK(cudaMemcpyAsync(ctx->rowptr, A->rowptr, sizeof(int32_t) * (size_t)(n + 1), cudaMemcpyDeviceToDevice, s));
         CK(cudaMemcpyAsync(ctx->colidx, A->colidx, sizeof(int32_t) * (size_t)A->nnz, cudaMemcpyDeviceToDevice, s));
         CK(cudaMemcpyAsync(ctx->vals, A->vals, sizeof(double) * (size_t)A->nnz, cudaMemcpyDeviceToDevice, s));
@@ -144,9 +144,9 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
                 if (ctx->h_offsets[k + 1] <= ctx->h_offsets[k]) { set_error(ctx, "patch sizes must be positive"); FAIL(PSR_ERR_INVALID_ARG); }
         }
         const int64_t total = ctx->h_offsets[np];
-        CK(cudaMalloc(&ctx->offsets, sizeof(int32_t) * (size_t)(np + 1)));
+        CK(psr::dev_alloc(&ctx->offsets, sizeof(int32_t) * (size_t)(np + 1)));
         CK(cudaMemcpyAsync(ctx->offsets, ctx->h_offsets.data(), sizeof(int32_t) * (size_t)(np + 1), cudaMemcpyHostToDevice, s));
-        CK(cudaMalloc(&ctx->dofs, sizeof(int32_t) * (size_t)total));
+        CK(psr::dev_alloc(&ctx->dofs, sizeof(int32_t) * (size_t)total));
         CK(cudaMemcpyAsync(ctx->dofs, P->dofs, sizeof(int32_t) * (size_t)total, cudaMemcpyDeviceToDevice, s));
         // --- validation
         rc = validate_inputs(ctx, A, ctx->offsets, ctx->dofs, np, total, ctx->status, s);
@@ -174,10 +174,10 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
         }
         h_mat_off[np] = off;
         ctx->A_ext_len = off;
-        CK(cudaMalloc(&ctx->mat_off, sizeof(int64_t) * (size_t)(np + 1)));
+        CK(psr::dev_alloc(&ctx->mat_off, sizeof(int64_t) * (size_t)(np + 1)));
         CK(cudaMemcpyAsync(ctx->mat_off, h_mat_off.data(), sizeof(int64_t) * (size_t)(np + 1), cudaMemcpyHostToDevice, s));
         {
-            cudaError_t ea = cudaMalloc(&ctx->A_ext, sizeof(double) * (size_t)off);
+            cudaError_t ea = psr::dev_alloc(&ctx->A_ext, sizeof(double) * (size_t)off);
             if (ea != cudaSuccess) { cudaGetLastError(); set_error(ctx, "out of device memory for the patch matrices"); FAIL(PSR_ERR_OOM); }
         }
         // --- a1: extraction
@@ -190,19 +190,19 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
             int32_t* mult = nullptr;
             double* w1 = nullptr;
             double* w2 = nullptr;
-            CK(cudaMalloc(&mult, sizeof(int32_t) * (size_t)n));
-            CK(cudaMalloc(&w1, sizeof(double) * (size_t)n));
-            CK(cudaMalloc(&w2, sizeof(double) * (size_t)n));
+            CK(psr::dev_alloc(&mult, sizeof(int32_t) * (size_t)n));
+            CK(psr::dev_alloc(&w1, sizeof(double) * (size_t)n));
+            CK(psr::dev_alloc(&w2, sizeof(double) * (size_t)n));
             rc = launch_multiplicity(ctx->dofs, total, n, mult, w1, w2, ctx->status, s);
-            if (rc != PSR_OK) { cudaFree(mult); cudaFree(w1); cudaFree(w2); goto fail; }
+            if (rc != PSR_OK) { psr::dev_free(mult); psr::dev_free(w1); psr::dev_free(w2); goto fail; }
             CK(cudaStreamSynchronize(s));
-            cudaFree(mult);
+            psr::dev_free(mult);
             if (op.weighting == PSR_WEIGHT_SYM) {
-                cudaFree(w1);
+                psr::dev_free(w1);
                 ctx->W = w2;
                 ctx->Wg = w2;
             } else {
-                cudaFree(w2);
+                psr::dev_free(w2);
                 ctx->W = w1;
                 ctx->Wg = nullptr;
             }
@@ -211,9 +211,9 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
         if (rc != PSR_OK) goto fail;
         ctx->stats.t_extract = seconds_since(t0);
         // --- a2 / a3: database and assignment
-        CK(cudaMalloc(&ctx->phi, sizeof(int32_t) * (size_t)np));
+        CK(psr::dev_alloc(&ctx->phi, sizeof(int32_t) * (size_t)np));
         // seed entries come on top of at most one new entry per patch
-        CK(cudaMalloc(&ctx->rep_ids, sizeof(int32_t) * ((size_t)np + (size_t)std::max(m0, 0))));
+        CK(psr::dev_alloc(&ctx->rep_ids, sizeof(int32_t) * ((size_t)np + (size_t)std::max(m0, 0))));
         t0 = std::chrono::steady_clock::now();
         if (mode.km_m == 0 && op.criterion == PSR_CRITERION_VARMIN) {
             set_error(ctx, "the variance-minimising criterion is an Alg. 2 variant (psr_setup_kmeans)");
@@ -226,13 +226,13 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
             // strict "< 0" never holds: every patch is its own entry (Eq. 1)
             int32_t* sing = nullptr;
             int32_t* first = nullptr;
-            CK(cudaMalloc(&sing, sizeof(int32_t) * (size_t)np));
-            CK(cudaMalloc(&first, sizeof(int32_t)));
+            CK(psr::dev_alloc(&sing, sizeof(int32_t) * (size_t)np));
+            CK(psr::dev_alloc(&first, sizeof(int32_t)));
             for (auto& G : ctx->groups) {
                 double* base = ctx->A_ext + G.mat_off;
                 rc = launch_batched_inverse(base, (int64_t)G.p * G.p, nullptr, G.count, G.p, base,
                                             (int64_t)G.p * G.p, sing, s);
-                if (rc != PSR_OK) { cudaFree(sing); cudaFree(first); goto fail; }
+                if (rc != PSR_OK) { psr::dev_free(sing); psr::dev_free(first); goto fail; }
                 int32_t big = 0x7fffffff;
                 CK(cudaMemcpyAsync(first, &big, sizeof(int32_t), cudaMemcpyHostToDevice, s));
                 count_launch(); k_any<<<std::max(1, std::min(G.count / 256 + 1, 1024)), 256, 0, s>>>(sing, G.count, first);
@@ -241,14 +241,14 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
                 CK(cudaStreamSynchronize(s));
                 G.m = G.count;
                 G.rinv = base;
-                CK(cudaMalloc(&G.sphi, sizeof(int32_t) * (size_t)G.count));
+                CK(psr::dev_alloc(&G.sphi, sizeof(int32_t) * (size_t)G.count));
                 count_launch(); k_iota<<<std::max(1, std::min(G.count / 256 + 1, 1024)), 256, 0, s>>>(G.sphi, G.count);
                 G.h_rep.resize(G.count);
                 for (int l = 0; l < G.count; ++l) G.h_rep[l] = l;
                 if (h_first != 0x7fffffff && ctx->stats.first_singular < 0) ctx->stats.first_singular = gidx[&G - &ctx->groups[0]][h_first];
             }
-            cudaFree(sing);
-            cudaFree(first);
+            psr::dev_free(sing);
+            psr::dev_free(first);
             ctx->stats.rounds = 0;
             ctx->stats.criterion_evals = 0;
         } else if (op.criterion == PSR_CRITERION_L1) {
@@ -282,7 +282,7 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
                     reinterpret_cast<double*>(G.rinv) < ctx->A_ext + std::max<int64_t>(ctx->A_ext_len, 1))
                     in_use = true;
             if (!in_use) {
-                cudaFree(ctx->A_ext);
+                psr::dev_free(ctx->A_ext);
                 ctx->A_ext = nullptr;
                 ctx->A_ext_len = 0;
             }
@@ -532,7 +532,7 @@ int psr_extract(const psr_csr* A, const psr_patches* P, double* A_out, int32_t* 
     }
     const int64_t total = ho[np];
     int32_t* status = nullptr;
-    PSR_CUDA(nullptr, cudaMalloc(&status, sizeof(int32_t)));
+    PSR_CUDA(nullptr, psr::dev_alloc(&status, sizeof(int32_t)));
     PSR_CUDA(nullptr, cudaMemsetAsync(status, 0, sizeof(int32_t), s));
     int rc = validate_inputs(nullptr, A, P->uniform_size > 0 ? nullptr : P->offsets, P->dofs, np, total, status, s);
     int32_t st = 0;
@@ -553,7 +553,7 @@ int psr_extract(const psr_csr* A, const psr_patches* P, double* A_out, int32_t* 
                 const int64_t pk = ho[k + 1] - ho[k];
                 hm[k + 1] = hm[k] + pk * pk;
             }
-            if (cudaMalloc(&mo, sizeof(int64_t) * (size_t)(np + 1)) != cudaSuccess) rc = PSR_ERR_OOM;
+            if (psr::dev_alloc(&mo, sizeof(int64_t) * (size_t)(np + 1)) != cudaSuccess) rc = PSR_ERR_OOM;
             else {
                 cudaMemcpyAsync(mo, hm.data(), sizeof(int64_t) * (size_t)(np + 1), cudaMemcpyHostToDevice, s);
                 rc = launch_extract(A->rowptr, A->colidx, A->vals, P->offsets, P->dofs, mo, np, 0, total, A_out, s);
@@ -562,18 +562,18 @@ int psr_extract(const psr_csr* A, const psr_patches* P, double* A_out, int32_t* 
     }
     if (rc == PSR_OK && (mult_out || W_out)) {
         int32_t* mult = mult_out;
-        if (!mult && cudaMalloc(&mult, sizeof(int32_t) * (size_t)A->n) != cudaSuccess) rc = PSR_ERR_OOM;
+        if (!mult && psr::dev_alloc(&mult, sizeof(int32_t) * (size_t)A->n) != cudaSuccess) rc = PSR_ERR_OOM;
         if (rc == PSR_OK) rc = launch_multiplicity(P->dofs, total, A->n, mult, W_out, nullptr, status, s);
         if (rc == PSR_OK && W_out) {
             cudaMemcpyAsync(&st, status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
             cudaStreamSynchronize(s);
             if (st & ST_UNCOVERED) { rc = PSR_ERR_UNCOVERED_DOF; set_error(nullptr, "a DOF belongs to no patch"); }
         }
-        if (mult && !mult_out) { cudaStreamSynchronize(s); cudaFree(mult); }
+        if (mult && !mult_out) { cudaStreamSynchronize(s); psr::dev_free(mult); }
     }
     cudaStreamSynchronize(s);
-    cudaFree(mo);
-    cudaFree(status);
+    psr::dev_free(mo);
+    psr::dev_free(status);
     return rc;
 }
 

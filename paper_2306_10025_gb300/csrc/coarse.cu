@@ -117,7 +117,7 @@ void coarse_free(psr_ctx* ctx) {
     if (!c) return;
     for (void* p : {(void*)c->prow, (void*)c->pcol, (void*)c->pval, (void*)c->rrow, (void*)c->rcol, (void*)c->rval,
                     (void*)c->Minv, (void*)c->rc, (void*)c->yc, (void*)c->col})
-        cudaFree(p);
+        psr::dev_free(p);
     delete c;
     ctx->coarse = nullptr;
 }
@@ -190,7 +190,7 @@ extern "C" int psr_set_coarse(psr_ctx* ctx, const psr_csr_rect* P0, void* stream
     }
     auto up = [&](auto** dst, const auto& src) -> int {
         using T = typename std::remove_reference<decltype(src)>::type::value_type;
-        PSR_CUDA(ctx, cudaMalloc(dst, sizeof(T) * std::max<size_t>(src.size(), 1)));
+        PSR_CUDA(ctx, psr::dev_alloc(dst, sizeof(T) * std::max<size_t>(src.size(), 1)));
         if (!src.empty()) PSR_CUDA(ctx, cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice));
         return PSR_OK;
     };
@@ -201,15 +201,15 @@ extern "C" int psr_set_coarse(psr_ctx* ctx, const psr_csr_rect* P0, void* stream
         return rc;
     }
     const size_t mbytes = sizeof(double) * (size_t)n0 * n0;
-    if (cudaMalloc(&c->Minv, mbytes) != cudaSuccess) {
+    if (psr::dev_alloc(&c->Minv, mbytes) != cudaSuccess) {
         cudaGetLastError();
         coarse_free(ctx);
         set_error(ctx, "out of device memory for the coarse inverse");
         return PSR_ERR_OOM;
     }
-    PSR_CUDA(ctx, cudaMalloc(&c->rc, sizeof(double) * n0));
-    PSR_CUDA(ctx, cudaMalloc(&c->yc, sizeof(double) * n0));
-    PSR_CUDA(ctx, cudaMalloc(&c->col, sizeof(double) * n0));
+    PSR_CUDA(ctx, psr::dev_alloc(&c->rc, sizeof(double) * n0));
+    PSR_CUDA(ctx, psr::dev_alloc(&c->yc, sizeof(double) * n0));
+    PSR_CUDA(ctx, psr::dev_alloc(&c->col, sizeof(double) * n0));
     PSR_CUDA(ctx, cudaMemsetAsync(c->Minv, 0, mbytes, s));
     count_launch();
     k_galerkin<<<std::max(1, std::min((n + 255) / 256, 152 * 8)), 256, 0, s>>>(ctx->rowptr, ctx->colidx, ctx->vals, n,

@@ -1074,10 +1074,10 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
     const double tol = ctx->opts.tol;
     RoundDev* st = nullptr;
     RoundDev* h_st = nullptr;
-    PSR_CUDA(ctx, cudaMalloc(&st, sizeof(RoundDev)));
-    PSR_CUDA(ctx, cudaMallocHost(&h_st, sizeof(RoundDev)));
+    PSR_CUDA(ctx, psr::dev_alloc(&st, sizeof(RoundDev)));
+    PSR_CUDA(ctx, psr::host_alloc(&h_st, sizeof(RoundDev)));
     int32_t* flag = nullptr;
-    PSR_CUDA(ctx, cudaMalloc(&flag, sizeof(int32_t)));
+    PSR_CUDA(ctx, psr::dev_alloc(&flag, sizeof(int32_t)));
     int rc = PSR_OK;
     int64_t total_evals = 0, total_exact = 0, total_hits = 0, total_screened = 0;
     int rounds_total = 0;
@@ -1093,12 +1093,12 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         double *Ball = nullptr, *fro_all = nullptr, *w_all = nullptr;
         EntryDB db{nullptr, nullptr, nullptr, nullptr};
         const int cap = count + m0;
-        PSR_CUDA(ctx, cudaMalloc(&phi_l, sizeof(int32_t) * count));
-        PSR_CUDA(ctx, cudaMalloc(&rep_l, sizeof(int32_t) * cap));
-        PSR_CUDA(ctx, cudaMalloc(&sing_all, sizeof(int32_t) * count));
-        PSR_CUDA(ctx, cudaMalloc(&fro_all, sizeof(double) * count));
-        PSR_CUDA(ctx, cudaMalloc(&w_all, sizeof(double) * (size_t)count * PROBE_STRIDE));
-        if (cudaMalloc(&Ball, sizeof(double) * (size_t)count * p * p) != cudaSuccess) {
+        PSR_CUDA(ctx, psr::dev_alloc(&phi_l, sizeof(int32_t) * count));
+        PSR_CUDA(ctx, psr::dev_alloc(&rep_l, sizeof(int32_t) * cap));
+        PSR_CUDA(ctx, psr::dev_alloc(&sing_all, sizeof(int32_t) * count));
+        PSR_CUDA(ctx, psr::dev_alloc(&fro_all, sizeof(double) * count));
+        PSR_CUDA(ctx, psr::dev_alloc(&w_all, sizeof(double) * (size_t)count * PROBE_STRIDE));
+        if (psr::dev_alloc(&Ball, sizeof(double) * (size_t)count * p * p) != cudaSuccess) {
             cudaGetLastError();
             set_error(ctx, "out of device memory for the patch inverses");
             return PSR_ERR_OOM;
@@ -1112,11 +1112,11 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         k_entry_fro<<<(count + 7) / 8, 256, 0, s>>>(Ag, Ball, count, p, fro_all, w_all, sing_all, nullptr);
         double *skX = nullptr, *skDen = nullptr, *skF = nullptr, *skR = nullptr;
         float *skY32 = nullptr, *sdY32 = nullptr;
-        PSR_CUDA(ctx, cudaMalloc(&skX, sizeof(double) * SK * 32));
-        PSR_CUDA(ctx, cudaMalloc(&skY32, sizeof(float) * (size_t)count * SK * p));
-        PSR_CUDA(ctx, cudaMalloc(&skF, sizeof(double) * (size_t)count));
-        PSR_CUDA(ctx, cudaMalloc(&skR, sizeof(double) * (size_t)count));
-        if (cudaMalloc(&skDen, sizeof(double) * (size_t)count * SK) != cudaSuccess) {
+        PSR_CUDA(ctx, psr::dev_alloc(&skX, sizeof(double) * SK * 32));
+        PSR_CUDA(ctx, psr::dev_alloc(&skY32, sizeof(float) * (size_t)count * SK * p));
+        PSR_CUDA(ctx, psr::dev_alloc(&skF, sizeof(double) * (size_t)count));
+        PSR_CUDA(ctx, psr::dev_alloc(&skR, sizeof(double) * (size_t)count));
+        if (psr::dev_alloc(&skDen, sizeof(double) * (size_t)count * SK) != cudaSuccess) {
             cudaGetLastError();
             set_error(ctx, "out of device memory for the patch sketches");
             return PSR_ERR_OOM;
@@ -1142,7 +1142,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         const size_t smem_dec = decide_smem_bytes(p, wpb);
         if ((rc = set_smem((const void*)k_round_decide, smem_dec)) != PSR_OK) break;
         int32_t* surv_list = nullptr;
-        PSR_CUDA(ctx, cudaMalloc(&surv_list, sizeof(int32_t) * (size_t)count));
+        PSR_CUDA(ctx, psr::dev_alloc(&surv_list, sizeof(int32_t) * (size_t)count));
         if ((rc = set_smem((const void*)k_seed_pass, smem_eval)) != PSR_OK) break;
         // one candidate per thread in the screen: enough blocks for every
         // SM, a few passes each; the decide grid is one wave of 4 blocks per SM
@@ -1151,22 +1151,22 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         if (eval_blocks < 1) eval_blocks = 1;
         const int decide_blocks = 152 * 4;
         if (m0 > 0) {
-            PSR_CUDA(ctx, cudaMalloc(&db.A, sizeof(double) * (size_t)m0 * p * p));
-            PSR_CUDA(ctx, cudaMalloc(&db.Binv, sizeof(double) * (size_t)m0 * p * p));
-            PSR_CUDA(ctx, cudaMalloc(&db.fro, sizeof(double) * m0));
-            PSR_CUDA(ctx, cudaMalloc(&db.w, sizeof(double) * (size_t)m0 * PROBE_STRIDE));
+            PSR_CUDA(ctx, psr::dev_alloc(&db.A, sizeof(double) * (size_t)m0 * p * p));
+            PSR_CUDA(ctx, psr::dev_alloc(&db.Binv, sizeof(double) * (size_t)m0 * p * p));
+            PSR_CUDA(ctx, psr::dev_alloc(&db.fro, sizeof(double) * m0));
+            PSR_CUDA(ctx, psr::dev_alloc(&db.w, sizeof(double) * (size_t)m0 * PROBE_STRIDE));
             PSR_CUDA(ctx, cudaMemcpyAsync(db.A, seed_A, sizeof(double) * (size_t)m0 * p * p, cudaMemcpyDeviceToDevice, s));
             int32_t* sflags = nullptr;
-            PSR_CUDA(ctx, cudaMalloc(&sflags, sizeof(int32_t) * m0));
+            PSR_CUDA(ctx, psr::dev_alloc(&sflags, sizeof(int32_t) * m0));
             rc = launch_batched_inverse(db.A, (int64_t)p * p, nullptr, m0, p, db.Binv, (int64_t)p * p, sflags, s);
             if (rc != PSR_OK) break;
             PSR_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
             count_launch();
             k_entry_fro<<<(m0 + 7) / 8, 256, 0, s>>>(db.A, db.Binv, m0, p, db.fro, db.w, sflags, flag);
-            PSR_CUDA(ctx, cudaMalloc(&sdDen, sizeof(double) * (size_t)m0 * SK));
-            PSR_CUDA(ctx, cudaMalloc(&sdF, sizeof(double) * (size_t)m0));
-            PSR_CUDA(ctx, cudaMalloc(&sdR, sizeof(double) * (size_t)m0));
-            PSR_CUDA(ctx, cudaMalloc(&sdY32, sizeof(float) * (size_t)m0 * SK * p));
+            PSR_CUDA(ctx, psr::dev_alloc(&sdDen, sizeof(double) * (size_t)m0 * SK));
+            PSR_CUDA(ctx, psr::dev_alloc(&sdF, sizeof(double) * (size_t)m0));
+            PSR_CUDA(ctx, psr::dev_alloc(&sdR, sizeof(double) * (size_t)m0));
+            PSR_CUDA(ctx, psr::dev_alloc(&sdY32, sizeof(float) * (size_t)m0 * SK * p));
             count_launch();
             launch_sketch(db.A, db.Binv, m0, p, skX, sdDen, sdY32, sdF, sdR, s);
             skd = SketchDB{skX, sdDen, sdF, sdR, sdY32};
@@ -1175,11 +1175,11 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
             int32_t h_bad = 0;
             PSR_CUDA(ctx, cudaMemcpyAsync(&h_bad, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
             PSR_CUDA(ctx, cudaStreamSynchronize(s));
-            cudaFree(sflags);
+            psr::dev_free(sflags);
             if (h_bad) { set_error(ctx, "a seed database entry is singular"); rc = PSR_ERR_SINGULAR_PATCH; break; }
             if (hints) {
                 int32_t* hits = nullptr;
-                PSR_CUDA(ctx, cudaMalloc(&hits, sizeof(int32_t)));
+                PSR_CUDA(ctx, psr::dev_alloc(&hits, sizeof(int32_t)));
                 PSR_CUDA(ctx, cudaMemsetAsync(hits, 0, sizeof(int32_t), s));
                 const size_t smem_h = (size_t)wpb * (3 * p * ld + 64) * 8;
                 if ((rc = set_smem((const void*)k_verify_hints, smem_h)) != PSR_OK) break;
@@ -1190,7 +1190,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
                 PSR_CUDA(ctx, cudaMemcpyAsync(&h_hits, hits, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
                 PSR_CUDA(ctx, cudaStreamSynchronize(s));
                 total_hits += h_hits;
-                cudaFree(hits);
+                psr::dev_free(hits);
             }
             // misses: first match over the seed entries, in creation order
             for (int j = 0; j < m0; ++j) {
@@ -1226,8 +1226,8 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
                 const int grid = sms * std::max(1, std::min(want, std::min(per_sm, 4)));
                 unsigned int* bar = nullptr;
                 int32_t* perr = nullptr;
-                PSR_CUDA(ctx, cudaMalloc(&bar, 2 * sizeof(unsigned int)));
-                PSR_CUDA(ctx, cudaMalloc(&perr, sizeof(int32_t)));
+                PSR_CUDA(ctx, psr::dev_alloc(&bar, 2 * sizeof(unsigned int)));
+                PSR_CUDA(ctx, psr::dev_alloc(&perr, sizeof(int32_t)));
                 PSR_CUDA(ctx, cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s));
                 PSR_CUDA(ctx, cudaMemsetAsync(perr, 0, sizeof(int32_t), s));
                 cudaLaunchConfig_t cfg = {};
@@ -1258,8 +1258,8 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
                     PSR_CUDA(ctx, cudaMemcpyAsync(h_st, st, sizeof(RoundDev), cudaMemcpyDeviceToHost, s));
                     PSR_CUDA(ctx, cudaMemcpyAsync(&herr, perr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
                     PSR_CUDA(ctx, cudaStreamSynchronize(s));
-                    cudaFree(bar);
-                    cudaFree(perr);
+                    psr::dev_free(bar);
+                    psr::dev_free(perr);
                     if (herr || !h_st->done) {
                         set_error(ctx, "a grid barrier of the Alg. 1 rounds gave up waiting");
                         rc = PSR_ERR_TIMEOUT;
@@ -1267,8 +1267,8 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
                     }
                 } else {
                     cudaGetLastError();
-                    cudaFree(bar);
-                    cudaFree(perr);
+                    psr::dev_free(bar);
+                    psr::dev_free(perr);
                 }
             }
         }
@@ -1305,14 +1305,14 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         std::vector<int32_t> hrep(G.m);
         PSR_CUDA(ctx, cudaMemcpyAsync(hrep.data(), rep_l, sizeof(int32_t) * G.m, cudaMemcpyDeviceToHost, s));
         double* Bdb = nullptr;
-        PSR_CUDA(ctx, cudaMalloc(&Bdb, sizeof(double) * (size_t)std::max(G.m, 1) * p * p));
+        PSR_CUDA(ctx, psr::dev_alloc(&Bdb, sizeof(double) * (size_t)std::max(G.m, 1) * p * p));
         {
             const int64_t tot = (int64_t)G.m * p * p;
             const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 152 * 16));
             count_launch();
             k_gather_db<<<gb, 256, 0, s>>>(db.Binv, m0, Ball, rep_l, G.m, p, Bdb);
             // the entries' patch matrices, kept for reuse by a later setup
-            PSR_CUDA(ctx, cudaMalloc(&G.dbA, sizeof(double) * (size_t)std::max(G.m, 1) * p * p));
+            PSR_CUDA(ctx, psr::dev_alloc(&G.dbA, sizeof(double) * (size_t)std::max(G.m, 1) * p * p));
             count_launch();
             k_gather_db<<<gb, 256, 0, s>>>(db.A, m0, Ag, rep_l, G.m, p, G.dbA);
         }
@@ -1320,23 +1320,23 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         G.h_rep.assign(hrep.begin(), hrep.end());   // local patch of each entry, -1 for seed entries
         G.sphi = phi_l;             // local phi in original (unsorted) order
         G.rinv = Bdb;               // FP64 database, converted in the sweep builder
-        cudaFree(Ball);
-        cudaFree(fro_all);
-        cudaFree(w_all);
-        cudaFree(sing_all);
-        for (double* q : {skX, skDen, skF, skR, sdDen, sdF, sdR}) cudaFree(q);
-        cudaFree(skY32);
-        cudaFree(sdY32);
-        cudaFree(surv_list);
-        cudaFree(db.A);
-        cudaFree(db.Binv);
-        cudaFree(db.fro);
-        cudaFree(db.w);
-        cudaFree(rep_l);
+        psr::dev_free(Ball);
+        psr::dev_free(fro_all);
+        psr::dev_free(w_all);
+        psr::dev_free(sing_all);
+        for (double* q : {skX, skDen, skF, skR, sdDen, sdF, sdR}) psr::dev_free(q);
+        psr::dev_free(skY32);
+        psr::dev_free(sdY32);
+        psr::dev_free(surv_list);
+        psr::dev_free(db.A);
+        psr::dev_free(db.Binv);
+        psr::dev_free(db.fro);
+        psr::dev_free(db.w);
+        psr::dev_free(rep_l);
     }
-    cudaFree(st);
-    cudaFreeHost(h_st);
-    cudaFree(flag);
+    psr::dev_free(st);
+    psr::host_free(h_st);
+    psr::dev_free(flag);
     ctx->stats.criterion_evals = total_evals;
     ctx->stats.criterion_exact = total_exact;
     ctx->stats.criterion_screened = total_screened;
@@ -1572,8 +1572,8 @@ int run_alg1_l1(psr_ctx* ctx, cudaStream_t s) {
     int first_singular = -1;
     L1State* st = nullptr;
     unsigned long long* evals = nullptr;
-    PSR_CUDA(ctx, cudaMalloc(&st, sizeof(L1State)));
-    PSR_CUDA(ctx, cudaMalloc(&evals, sizeof(unsigned long long)));
+    PSR_CUDA(ctx, psr::dev_alloc(&st, sizeof(L1State)));
+    PSR_CUDA(ctx, psr::dev_alloc(&evals, sizeof(unsigned long long)));
     int rc = PSR_OK;
     for (size_t g = 0; g < ctx->groups.size() && rc == PSR_OK; ++g) {
         Group& G = ctx->groups[g];
@@ -1581,8 +1581,8 @@ int run_alg1_l1(psr_ctx* ctx, cudaStream_t s) {
         const int64_t pp = (int64_t)p * p;
         const double* Ag = ctx->A_ext + G.mat_off;
         int32_t *phi_l = nullptr, *rep_l = nullptr, *sing = nullptr;
-        PSR_CUDA(ctx, cudaMalloc(&phi_l, sizeof(int32_t) * count));
-        PSR_CUDA(ctx, cudaMalloc(&rep_l, sizeof(int32_t) * count));
+        PSR_CUDA(ctx, psr::dev_alloc(&phi_l, sizeof(int32_t) * count));
+        PSR_CUDA(ctx, psr::dev_alloc(&rep_l, sizeof(int32_t) * count));
         PSR_CUDA(ctx, cudaMemsetAsync(phi_l, 0xff, sizeof(int32_t) * count, s));
         PSR_CUDA(ctx, cudaMemsetAsync(evals, 0, sizeof(unsigned long long), s));
         L1State init{{0, count, count}, 0};
@@ -1605,10 +1605,10 @@ int run_alg1_l1(psr_ctx* ctx, cudaStream_t s) {
         unsigned long long h_evals = 0;
         PSR_CUDA(ctx, cudaMemcpy(&h_evals, evals, sizeof(h_evals), cudaMemcpyDeviceToHost));
         // the entries' matrices and their inverses
-        PSR_CUDA(ctx, cudaMalloc(&G.dbA, sizeof(double) * (size_t)std::max(m, 1) * pp));
+        PSR_CUDA(ctx, psr::dev_alloc(&G.dbA, sizeof(double) * (size_t)std::max(m, 1) * pp));
         double* Bdb = nullptr;
-        PSR_CUDA(ctx, cudaMalloc(&Bdb, sizeof(double) * (size_t)std::max(m, 1) * pp));
-        PSR_CUDA(ctx, cudaMalloc(&sing, sizeof(int32_t) * std::max(m, 1)));
+        PSR_CUDA(ctx, psr::dev_alloc(&Bdb, sizeof(double) * (size_t)std::max(m, 1) * pp));
+        PSR_CUDA(ctx, psr::dev_alloc(&sing, sizeof(int32_t) * std::max(m, 1)));
         {
             const int64_t tot = (int64_t)m * pp;
             const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 152 * 16));
@@ -1624,8 +1624,8 @@ int run_alg1_l1(psr_ctx* ctx, cudaStream_t s) {
             for (int j = 0; j < m && first_singular < 0; ++j)
                 if (hs[j]) first_singular = G.h_gidx[hrep[j]];
         }
-        cudaFree(sing);
-        cudaFree(rep_l);
+        psr::dev_free(sing);
+        psr::dev_free(rep_l);
         G.m = m;
         G.sphi = phi_l;
         G.rinv = Bdb;
@@ -1633,8 +1633,8 @@ int run_alg1_l1(psr_ctx* ctx, cudaStream_t s) {
         total_evals += (int64_t)h_evals;
         rounds_total += m;
     }
-    cudaFree(st);
-    cudaFree(evals);
+    psr::dev_free(st);
+    psr::dev_free(evals);
     ctx->stats.first_singular = first_singular;
     ctx->stats.criterion_evals = total_evals;
     ctx->stats.criterion_exact = 0;

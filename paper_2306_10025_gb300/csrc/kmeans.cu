@@ -189,16 +189,16 @@ static int run_kmeans_varmin(psr_ctx* ctx, cudaStream_t s, int m, const std::vec
     double *Ainv = nullptr, *B = nullptr, *Bcur = nullptr, *V = nullptr;
     int32_t *sing_all = nullptr, *phi = nullptr, *changes = nullptr, *moff = nullptr, *mlist = nullptr,
             *d_reps = nullptr;
-    PSR_CUDA(ctx, cudaMalloc(&Ainv, sizeof(double) * (size_t)count * pp));
-    PSR_CUDA(ctx, cudaMalloc(&sing_all, sizeof(int32_t) * (size_t)count));
-    PSR_CUDA(ctx, cudaMalloc(&B, sizeof(double) * (size_t)m * pp));
-    PSR_CUDA(ctx, cudaMalloc(&Bcur, sizeof(double) * (size_t)m * pp));
-    PSR_CUDA(ctx, cudaMalloc(&V, sizeof(double) * (size_t)count));
-    PSR_CUDA(ctx, cudaMalloc(&phi, sizeof(int32_t) * (size_t)count));
-    PSR_CUDA(ctx, cudaMalloc(&changes, sizeof(int32_t)));
-    PSR_CUDA(ctx, cudaMalloc(&moff, sizeof(int32_t) * (size_t)(m + 1)));
-    PSR_CUDA(ctx, cudaMalloc(&mlist, sizeof(int32_t) * (size_t)count));
-    PSR_CUDA(ctx, cudaMalloc(&d_reps, sizeof(int32_t) * (size_t)m));
+    PSR_CUDA(ctx, psr::dev_alloc(&Ainv, sizeof(double) * (size_t)count * pp));
+    PSR_CUDA(ctx, psr::dev_alloc(&sing_all, sizeof(int32_t) * (size_t)count));
+    PSR_CUDA(ctx, psr::dev_alloc(&B, sizeof(double) * (size_t)m * pp));
+    PSR_CUDA(ctx, psr::dev_alloc(&Bcur, sizeof(double) * (size_t)m * pp));
+    PSR_CUDA(ctx, psr::dev_alloc(&V, sizeof(double) * (size_t)count));
+    PSR_CUDA(ctx, psr::dev_alloc(&phi, sizeof(int32_t) * (size_t)count));
+    PSR_CUDA(ctx, psr::dev_alloc(&changes, sizeof(int32_t)));
+    PSR_CUDA(ctx, psr::dev_alloc(&moff, sizeof(int32_t) * (size_t)(m + 1)));
+    PSR_CUDA(ctx, psr::dev_alloc(&mlist, sizeof(int32_t) * (size_t)count));
+    PSR_CUDA(ctx, psr::dev_alloc(&d_reps, sizeof(int32_t) * (size_t)m));
     int rc = launch_batched_inverse(Ag, pp, nullptr, count, p, Ainv, pp, sing_all, s);
     std::vector<int32_t> reps(init.begin(), init.end());
     std::vector<int32_t> hphi((size_t)count), hoff((size_t)m + 1), hlist((size_t)count);
@@ -245,7 +245,7 @@ static int run_kmeans_varmin(psr_ctx* ctx, cudaStream_t s, int m, const std::vec
     std::vector<int32_t> hsing((size_t)count);
     if (rc == PSR_OK) {
         PSR_CUDA(ctx, cudaMemcpyAsync(d_reps, reps.data(), sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
-        PSR_CUDA(ctx, cudaMalloc(&Bdb, sizeof(double) * (size_t)m * pp));
+        PSR_CUDA(ctx, psr::dev_alloc(&Bdb, sizeof(double) * (size_t)m * pp));
         count_launch(); k_kmeans_gather<<<gb, 256, 0, s>>>(Ag, d_reps, m, pp, B);
         count_launch(); k_kmeans_gather<<<gb, 256, 0, s>>>(Ainv, d_reps, m, pp, Bdb);
         PSR_CUDA(ctx, cudaMemcpyAsync(hsing.data(), sing_all, sizeof(int32_t) * (size_t)count, cudaMemcpyDeviceToHost, s));
@@ -260,11 +260,11 @@ static int run_kmeans_varmin(psr_ctx* ctx, cudaStream_t s, int m, const std::vec
     }
     for (void* q : {(void*)Ainv, (void*)sing_all, (void*)Bcur, (void*)V, (void*)changes, (void*)moff, (void*)mlist,
                     (void*)d_reps})
-        cudaFree(q);
+        psr::dev_free(q);
     if (rc != PSR_OK) {
-        cudaFree(B);
-        cudaFree(phi);
-        cudaFree(Bdb);
+        psr::dev_free(B);
+        psr::dev_free(phi);
+        psr::dev_free(Bdb);
         return rc;
     }
     G.dbA = B;
@@ -289,17 +289,17 @@ int run_kmeans(psr_ctx* ctx, cudaStream_t s, int m, const std::vector<int32_t>& 
     const double* Ag = ctx->A_ext + G.mat_off;
     double* B = nullptr;
     int32_t *phi = nullptr, *d_init = nullptr, *changes = nullptr, *moff = nullptr, *mlist = nullptr;
-    PSR_CUDA(ctx, cudaMalloc(&B, sizeof(double) * (size_t)m * pp));
-    PSR_CUDA(ctx, cudaMalloc(&phi, sizeof(int32_t) * (size_t)count));
-    PSR_CUDA(ctx, cudaMalloc(&d_init, sizeof(int32_t) * (size_t)m));
-    PSR_CUDA(ctx, cudaMalloc(&changes, sizeof(int32_t)));
-    PSR_CUDA(ctx, cudaMalloc(&moff, sizeof(int32_t) * (size_t)(m + 1)));
-    PSR_CUDA(ctx, cudaMalloc(&mlist, sizeof(int32_t) * (size_t)count));
+    PSR_CUDA(ctx, psr::dev_alloc(&B, sizeof(double) * (size_t)m * pp));
+    PSR_CUDA(ctx, psr::dev_alloc(&phi, sizeof(int32_t) * (size_t)count));
+    PSR_CUDA(ctx, psr::dev_alloc(&d_init, sizeof(int32_t) * (size_t)m));
+    PSR_CUDA(ctx, psr::dev_alloc(&changes, sizeof(int32_t)));
+    PSR_CUDA(ctx, psr::dev_alloc(&moff, sizeof(int32_t) * (size_t)(m + 1)));
+    PSR_CUDA(ctx, psr::dev_alloc(&mlist, sizeof(int32_t) * (size_t)count));
     double* Bcur = nullptr;                   // spectral: inverses of the current means
     int32_t* sing_cur = nullptr;
     if (spectral) {
-        PSR_CUDA(ctx, cudaMalloc(&Bcur, sizeof(double) * (size_t)m * pp));
-        PSR_CUDA(ctx, cudaMalloc(&sing_cur, sizeof(int32_t) * (size_t)m));
+        PSR_CUDA(ctx, psr::dev_alloc(&Bcur, sizeof(double) * (size_t)m * pp));
+        PSR_CUDA(ctx, psr::dev_alloc(&sing_cur, sizeof(int32_t) * (size_t)m));
     }
     PSR_CUDA(ctx, cudaMemcpyAsync(d_init, init.data(), sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
     PSR_CUDA(ctx, cudaMemsetAsync(phi, 0xff, sizeof(int32_t) * (size_t)count, s));
@@ -346,8 +346,8 @@ int run_kmeans(psr_ctx* ctx, cudaStream_t s, int m, const std::vector<int32_t>& 
     // inverses of the means (FP64 Gauss-Jordan with partial pivoting)
     double* Bdb = nullptr;
     int32_t* sing = nullptr;
-    PSR_CUDA(ctx, cudaMalloc(&Bdb, sizeof(double) * (size_t)m * pp));
-    PSR_CUDA(ctx, cudaMalloc(&sing, sizeof(int32_t) * (size_t)m));
+    PSR_CUDA(ctx, psr::dev_alloc(&Bdb, sizeof(double) * (size_t)m * pp));
+    PSR_CUDA(ctx, psr::dev_alloc(&sing, sizeof(int32_t) * (size_t)m));
     if (rc == PSR_OK) rc = launch_batched_inverse(B, pp, nullptr, m, p, Bdb, pp, sing, s);
     std::vector<int32_t> hs((size_t)m);
     if (rc == PSR_OK) {
@@ -360,17 +360,17 @@ int run_kmeans(psr_ctx* ctx, cudaStream_t s, int m, const std::vector<int32_t>& 
                 break;
             }
     }
-    cudaFree(d_init);
-    cudaFree(Bcur);
-    cudaFree(sing_cur);
-    cudaFree(changes);
-    cudaFree(moff);
-    cudaFree(mlist);
-    cudaFree(sing);
+    psr::dev_free(d_init);
+    psr::dev_free(Bcur);
+    psr::dev_free(sing_cur);
+    psr::dev_free(changes);
+    psr::dev_free(moff);
+    psr::dev_free(mlist);
+    psr::dev_free(sing);
     if (rc != PSR_OK) {
-        cudaFree(B);
-        cudaFree(phi);
-        cudaFree(Bdb);
+        psr::dev_free(B);
+        psr::dev_free(phi);
+        psr::dev_free(Bdb);
         return rc;
     }
     G.dbA = B;                      // the means: the entries' matrices, kept for reuse

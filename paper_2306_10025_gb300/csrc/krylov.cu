@@ -1471,34 +1471,34 @@ int krylov_alloc(psr_ctx* ctx) {
     if (m > 32) m = 32;
     ctx->opts.restart = m;
     w.nblk = (int)std::min<size_t>(std::max<size_t>((n + 255) / 256, 1), 152 * 4);
-    PSR_CUDA(ctx, cudaMalloc(&w.x, n * 8));
-    PSR_CUDA(ctx, cudaMalloc(&w.b, n * 8));
-    PSR_CUDA(ctx, cudaMalloc(&w.r, n * 8));
-    PSR_CUDA(ctx, cudaMalloc(&w.z, n * 8));
+    PSR_CUDA(ctx, psr::dev_alloc(&w.x, n * 8));
+    PSR_CUDA(ctx, psr::dev_alloc(&w.b, n * 8));
+    PSR_CUDA(ctx, psr::dev_alloc(&w.r, n * 8));
+    PSR_CUDA(ctx, psr::dev_alloc(&w.z, n * 8));
     if (ctx->opts.krylov == PSR_KRYLOV_CG) {
-        PSR_CUDA(ctx, cudaMalloc(&w.p, n * 8));
-        PSR_CUDA(ctx, cudaMalloc(&w.q, n * 8));
+        PSR_CUDA(ctx, psr::dev_alloc(&w.p, n * 8));
+        PSR_CUDA(ctx, psr::dev_alloc(&w.q, n * 8));
     } else {
-        PSR_CUDA(ctx, cudaMalloc(&w.V, (size_t)(m + 1) * n * 8));
-        PSR_CUDA(ctx, cudaMalloc(&w.Z, (size_t)m * n * 8));
+        PSR_CUDA(ctx, psr::dev_alloc(&w.V, (size_t)(m + 1) * n * 8));
+        PSR_CUDA(ctx, psr::dev_alloc(&w.Z, (size_t)m * n * 8));
     }
     // SELL-32 copy of A for the SpMV
     {
         w.nslices = (ctx->n + 31) / 32;
         int32_t* widths = nullptr;
-        PSR_CUDA(ctx, cudaMalloc(&widths, sizeof(int32_t) * (size_t)w.nslices));
+        PSR_CUDA(ctx, psr::dev_alloc(&widths, sizeof(int32_t) * (size_t)w.nslices));
         count_launch();
         k_sell_width<<<(w.nslices + 7) / 8, 256>>>(ctx->rowptr, ctx->n, w.nslices, widths);
         std::vector<int32_t> hw((size_t)w.nslices);
         PSR_CUDA(ctx, cudaMemcpy(hw.data(), widths, sizeof(int32_t) * hw.size(), cudaMemcpyDeviceToHost));
-        cudaFree(widths);
+        psr::dev_free(widths);
         std::vector<int64_t> hp((size_t)w.nslices + 1, 0);
         for (int q = 0; q < w.nslices; ++q) hp[q + 1] = hp[q] + 32 * (int64_t)hw[q];
         const int64_t total = std::max<int64_t>(hp.back(), 1);
-        PSR_CUDA(ctx, cudaMalloc(&w.sell_ptr, sizeof(int64_t) * hp.size()));
+        PSR_CUDA(ctx, psr::dev_alloc(&w.sell_ptr, sizeof(int64_t) * hp.size()));
         PSR_CUDA(ctx, cudaMemcpy(w.sell_ptr, hp.data(), sizeof(int64_t) * hp.size(), cudaMemcpyHostToDevice));
-        PSR_CUDA(ctx, cudaMalloc(&w.sell_cols, sizeof(int32_t) * (size_t)total));
-        PSR_CUDA(ctx, cudaMalloc(&w.sell_vals, sizeof(double) * (size_t)total));
+        PSR_CUDA(ctx, psr::dev_alloc(&w.sell_cols, sizeof(int32_t) * (size_t)total));
+        PSR_CUDA(ctx, psr::dev_alloc(&w.sell_vals, sizeof(double) * (size_t)total));
         count_launch();
         k_sell_fill<<<(w.nslices * 32 + 255) / 256, 256>>>(ctx->rowptr, ctx->colidx, ctx->vals, ctx->n, w.nslices,
                                                             w.sell_ptr, w.sell_cols, w.sell_vals);
@@ -1507,12 +1507,12 @@ int krylov_alloc(psr_ctx* ctx) {
     }
     w.nspmv = 152 * 16;                     // partial slots available to the SpMV reductions
     PSR_CUDA(ctx, cudaDeviceGetAttribute(&w.sms, cudaDevAttrMultiProcessorCount, ctx->device));
-    PSR_CUDA(ctx, cudaMalloc(&w.partial, (size_t)std::max(w.nblk * 34, w.nspmv) * 8));
-    PSR_CUDA(ctx, cudaMalloc(&w.scal, (size_t)scal_count(m) * 8));
+    PSR_CUDA(ctx, psr::dev_alloc(&w.partial, (size_t)std::max(w.nblk * 34, w.nspmv) * 8));
+    PSR_CUDA(ctx, psr::dev_alloc(&w.scal, (size_t)scal_count(m) * 8));
     PSR_CUDA(ctx, cudaMemset(w.scal, 0, (size_t)scal_count(m) * 8));
-    PSR_CUDA(ctx, cudaMalloc(&w.hist, (size_t)(ctx->opts.maxit + 2) * 8));
-    PSR_CUDA(ctx, cudaMalloc(&w.ictl, 32 * sizeof(int32_t)));
-    PSR_CUDA(ctx, cudaMalloc(&w.rflag, 64 * sizeof(int32_t)));
+    PSR_CUDA(ctx, psr::dev_alloc(&w.hist, (size_t)(ctx->opts.maxit + 2) * 8));
+    PSR_CUDA(ctx, psr::dev_alloc(&w.ictl, 32 * sizeof(int32_t)));
+    PSR_CUDA(ctx, psr::dev_alloc(&w.rflag, 64 * sizeof(int32_t)));
     PSR_CUDA(ctx, cudaMemset(w.rflag, 0, 64 * sizeof(int32_t)));
     // fused Arnoldi step: cooperative launches of one block per SM
     int coop = 0;
@@ -1526,9 +1526,9 @@ int krylov_alloc(psr_ctx* ctx) {
         cudaGetLastError();
         w.coop = b8 >= 1 && b16 >= 1 && b32 >= 1;
     }
-    if (w.coop) PSR_CUDA(ctx, cudaMalloc(&w.Vs, (size_t)(m + 1) * n * sizeof(float2)));
-    PSR_CUDA(ctx, cudaMalloc(&w.part_arn, (size_t)4 * 33 * w.sms * sizeof(double)));
-    PSR_CUDA(ctx, cudaMalloc(&w.bar, 2 * sizeof(unsigned int)));
+    if (w.coop) PSR_CUDA(ctx, psr::dev_alloc(&w.Vs, (size_t)(m + 1) * n * sizeof(float2)));
+    PSR_CUDA(ctx, psr::dev_alloc(&w.part_arn, (size_t)4 * 33 * w.sms * sizeof(double)));
+    PSR_CUDA(ctx, psr::dev_alloc(&w.bar, 2 * sizeof(unsigned int)));
     PSR_CUDA(ctx, cudaMemset(w.bar, 0, 2 * sizeof(unsigned int)));
     PSR_CUDA(ctx, cudaMemset(w.ictl, 0, 32 * sizeof(int32_t)));
     return PSR_OK;
@@ -1536,15 +1536,15 @@ int krylov_alloc(psr_ctx* ctx) {
 
 void krylov_free(psr_ctx* ctx) {
     KrylovWS& w = ctx->ws;
-    for (double* p : {w.x, w.b, w.r, w.z, w.p, w.q, w.V, w.Z, w.partial, w.scal, w.hist}) cudaFree(p);
-    cudaFree(w.ictl);
-    cudaFree(w.rflag);
-    cudaFree(w.part_arn);
-    cudaFree(w.Vs);
-    cudaFree(w.bar);
-    cudaFree(w.sell_ptr);
-    cudaFree(w.sell_cols);
-    cudaFree(w.sell_vals);
+    for (double* p : {w.x, w.b, w.r, w.z, w.p, w.q, w.V, w.Z, w.partial, w.scal, w.hist}) psr::dev_free(p);
+    psr::dev_free(w.ictl);
+    psr::dev_free(w.rflag);
+    psr::dev_free(w.part_arn);
+    psr::dev_free(w.Vs);
+    psr::dev_free(w.bar);
+    psr::dev_free(w.sell_ptr);
+    psr::dev_free(w.sell_cols);
+    psr::dev_free(w.sell_vals);
     w = KrylovWS{};
     if (ctx->g_cycle) cudaGraphExecDestroy(ctx->g_cycle);
     ctx->g_cycle = nullptr;
@@ -1753,7 +1753,7 @@ int krylov_solve(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_s
     }
     const int block = cg ? 8 : 1;
     int32_t* hstop = nullptr;                     // control ints, then the step flags
-    PSR_CUDA(ctx, cudaMallocHost(&hstop, (8 + 64) * sizeof(int32_t)));
+    PSR_CUDA(ctx, psr::host_alloc(&hstop, (8 + 64) * sizeof(int32_t)));
     // capture one block / cycle into a graph (the pointers are the context's own)
     if (ctx->opts.use_graph && !ctx->g_cycle) {
         cudaStream_t cs;
@@ -1777,12 +1777,12 @@ int krylov_solve(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_s
             }
             ctx->graph_block = kn;
         }
-        if (rc != PSR_OK) { cudaStreamDestroy(cs); cudaFreeHost(hstop); return rc; }
-        if (ce != cudaSuccess) { cudaStreamDestroy(cs); cudaFreeHost(hstop); return cuda_fail(ctx, ce, "graph capture"); }
+        if (rc != PSR_OK) { cudaStreamDestroy(cs); psr::host_free(hstop); return rc; }
+        if (ce != cudaSuccess) { cudaStreamDestroy(cs); psr::host_free(hstop); return cuda_fail(ctx, ce, "graph capture"); }
         ce = cudaGraphInstantiate(&ctx->g_cycle, g, 0);
         cudaGraphDestroy(g);
         cudaStreamDestroy(cs);
-        if (ce != cudaSuccess) { cudaFreeHost(hstop); ctx->g_cycle = nullptr; return cuda_fail(ctx, ce, "graph instantiate"); }
+        if (ce != cudaSuccess) { psr::host_free(hstop); ctx->g_cycle = nullptr; return cuda_fail(ctx, ce, "graph instantiate"); }
     }
     const int max_blocks = cg ? (ctx->opts.maxit + block - 1) / block + 2 : ctx->opts.maxit + 2;
     int rc = PSR_OK;
@@ -1810,7 +1810,7 @@ int krylov_solve(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_s
         it_before = hstop[I_IT];
         if (hstop[I_STOP]) break;
     }
-    if (rc != PSR_OK) { cudaFreeHost(hstop); return rc; }
+    if (rc != PSR_OK) { psr::host_free(hstop); return rc; }
     PSR_CUDA(ctx, cudaMemcpyAsync(x, w.x, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
     PSR_CUDA(ctx, cudaEventRecord(e1, s));
     PSR_CUDA(ctx, cudaEventSynchronize(e1));
@@ -1820,7 +1820,7 @@ int krylov_solve(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_s
     cudaEventDestroy(e1);
     const int iters = hstop[I_IT];
     const int conv = hstop[I_CONV];
-    cudaFreeHost(hstop);
+    psr::host_free(hstop);
     ctx->last_iters = iters;
     ctx->h_hist.assign((size_t)iters + 1, 0.0);
     PSR_CUDA(ctx, cudaMemcpy(ctx->h_hist.data(), w.hist, sizeof(double) * (iters + 1), cudaMemcpyDeviceToHost));

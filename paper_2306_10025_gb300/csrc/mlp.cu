@@ -220,13 +220,13 @@ __global__ void k_features(const double* __restrict__ A, int npch, int p, const 
 
 static int ensure_cap(psr_mlp* net, int Bn) {
     if (Bn <= net->cap) return PSR_OK;
-    for (float* p : {net->Z1, net->H1, net->Z2, net->H2, net->L, net->G1, net->G2, net->G3, net->loss_part}) cudaFree(p);
-    cudaFree(net->cnt);
+    for (float* p : {net->Z1, net->H1, net->Z2, net->H2, net->L, net->G1, net->G2, net->G3, net->loss_part}) psr::dev_free(p);
+    psr::dev_free(net->cnt);
     const size_t bh = (size_t)Bn * net->h, bm = (size_t)Bn * net->m;
-    if (cudaMalloc(&net->Z1, bh * 4) || cudaMalloc(&net->H1, bh * 4) || cudaMalloc(&net->Z2, bh * 4) ||
-        cudaMalloc(&net->H2, bh * 4) || cudaMalloc(&net->L, bm * 4) || cudaMalloc(&net->G1, bh * 4) ||
-        cudaMalloc(&net->G2, bh * 4) || cudaMalloc(&net->G3, bm * 4) || cudaMalloc(&net->loss_part, 1024 * 4) ||
-        cudaMalloc(&net->cnt, 4)) {
+    if (psr::dev_alloc(&net->Z1, bh * 4) || psr::dev_alloc(&net->H1, bh * 4) || psr::dev_alloc(&net->Z2, bh * 4) ||
+        psr::dev_alloc(&net->H2, bh * 4) || psr::dev_alloc(&net->L, bm * 4) || psr::dev_alloc(&net->G1, bh * 4) ||
+        psr::dev_alloc(&net->G2, bh * 4) || psr::dev_alloc(&net->G3, bm * 4) || psr::dev_alloc(&net->loss_part, 1024 * 4) ||
+        psr::dev_alloc(&net->cnt, 4)) {
         cudaGetLastError();
         net->cap = 0;
         set_error(nullptr, "MLP activation allocation failed");
@@ -287,10 +287,10 @@ int psr_mlp_create(int32_t in_dim, int32_t hidden, int32_t classes, psr_mlp** ou
     net->m = classes;
     net->np = (int64_t)hidden * in_dim + hidden + (int64_t)hidden * hidden + hidden + (int64_t)classes * hidden + classes;
     const size_t b = (size_t)net->np * 4;
-    if (cudaMalloc(&net->params, b) || cudaMalloc(&net->grads, b) || cudaMalloc(&net->adam_m, b) ||
-        cudaMalloc(&net->adam_v, b)) {
+    if (psr::dev_alloc(&net->params, b) || psr::dev_alloc(&net->grads, b) || psr::dev_alloc(&net->adam_m, b) ||
+        psr::dev_alloc(&net->adam_v, b)) {
         cudaGetLastError();
-        cudaFree(net->params); cudaFree(net->grads); cudaFree(net->adam_m); cudaFree(net->adam_v);
+        psr::dev_free(net->params); psr::dev_free(net->grads); psr::dev_free(net->adam_m); psr::dev_free(net->adam_v);
         delete net;
         set_error(nullptr, "MLP parameter allocation failed");
         return PSR_ERR_OOM;
@@ -298,7 +298,7 @@ int psr_mlp_create(int32_t in_dim, int32_t hidden, int32_t classes, psr_mlp** ou
     cudaMemset(net->params, 0, b);
     cudaMemset(net->adam_m, 0, b);
     cudaMemset(net->adam_v, 0, b);
-    if (cudaMalloc(&net->tc_err, sizeof(int32_t)) != cudaSuccess) {
+    if (psr::dev_alloc(&net->tc_err, sizeof(int32_t)) != cudaSuccess) {
         cudaGetLastError();
         psr_mlp_destroy(net);
         set_error(nullptr, "MLP allocation failed");
@@ -376,9 +376,9 @@ void psr_mlp_destroy(psr_mlp* net) {
     if (!net) return;
     for (float* p : {net->params, net->grads, net->adam_m, net->adam_v, net->Z1, net->H1, net->Z2, net->H2, net->L,
                      net->G1, net->G2, net->G3, net->loss_part})
-        cudaFree(p);
-    cudaFree(net->cnt);
-    cudaFree(net->tc_err);
+        psr::dev_free(p);
+    psr::dev_free(net->cnt);
+    psr::dev_free(net->tc_err);
     delete net;
 }
 

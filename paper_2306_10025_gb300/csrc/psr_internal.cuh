@@ -35,6 +35,18 @@ void set_capturing(bool on);
         if (e_ != cudaSuccess) return psr::cuda_fail((ctx), e_, what); \
     } while (0)
 
+// Device and pinned host memory of the library go through a caching
+// allocator (memory.cu): freed blocks are kept and handed out again, after a
+// device synchronisation when they were freed since the last one.
+cudaError_t dev_alloc(void** p, size_t bytes);
+cudaError_t dev_free(void* p);
+cudaError_t host_alloc(void** p, size_t bytes);
+cudaError_t host_free(void* p);
+template <class T>
+inline cudaError_t dev_alloc(T** p, size_t bytes) { return dev_alloc(reinterpret_cast<void**>(p), bytes); }
+template <class T>
+inline cudaError_t host_alloc(T** p, size_t bytes) { return host_alloc(reinterpret_cast<void**>(p), bytes); }
+
 // ------------------------------------------------------- device helpers
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

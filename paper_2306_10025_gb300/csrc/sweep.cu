@@ -476,10 +476,10 @@ static std::vector<int32_t> tiles_host(const std::vector<int32_t>& sorted_phi, i
 
 static int make_tiles(psr_ctx* ctx, Group& G, const std::vector<int32_t>& sorted_phi, int T) {
     const std::vector<int32_t> t = tiles_host(sorted_phi, G.count, T);
-    if (G.tiles) cudaFree(G.tiles);
+    if (G.tiles) psr::dev_free(G.tiles);
     G.tiles = nullptr;
     G.ntiles = (int)(t.size() / 3);
-    PSR_CUDA(ctx, cudaMalloc(&G.tiles, sizeof(int32_t) * std::max<size_t>(t.size(), 3)));
+    PSR_CUDA(ctx, psr::dev_alloc(&G.tiles, sizeof(int32_t) * std::max<size_t>(t.size(), 3)));
     PSR_CUDA(ctx, cudaMemcpy(G.tiles, t.data(), sizeof(int32_t) * t.size(), cudaMemcpyHostToDevice));
     G.tile_patches = T;
     return PSR_OK;
@@ -536,11 +536,11 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<std::vector<int32_t>>& gi
             phi_global[k] = entry_base + lphi[l];
         }
         for (int j = 0; j < G.m; ++j) rep_global.push_back(G.h_rep[j] >= 0 ? gidx[g][G.h_rep[j]] : -1);
-        cudaFree(G.sphi);
+        psr::dev_free(G.sphi);
         G.sphi = nullptr;
-        PSR_CUDA(ctx, cudaMalloc(&G.patch, sizeof(int32_t) * count));
-        PSR_CUDA(ctx, cudaMalloc(&G.sphi, sizeof(int32_t) * count));
-        PSR_CUDA(ctx, cudaMalloc(&G.sdofs, sizeof(int32_t) * (size_t)count * p));
+        PSR_CUDA(ctx, psr::dev_alloc(&G.patch, sizeof(int32_t) * count));
+        PSR_CUDA(ctx, psr::dev_alloc(&G.sphi, sizeof(int32_t) * count));
+        PSR_CUDA(ctx, psr::dev_alloc(&G.sdofs, sizeof(int32_t) * (size_t)count * p));
         // on the stream of the gather below (a pageable source is staged
         // before the call returns)
         PSR_CUDA(ctx, cudaMemcpyAsync(G.patch, hp.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, s));
@@ -557,21 +557,21 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<std::vector<int32_t>>& gi
                 G.rinv = db64;              // full storage: inverses live where the patches were
             } else {                        // shrink the round buffer to m entries
                 double* keep = nullptr;
-                PSR_CUDA(ctx, cudaMalloc(&keep, sizeof(double) * std::max<int64_t>(ne, 1)));
+                PSR_CUDA(ctx, psr::dev_alloc(&keep, sizeof(double) * std::max<int64_t>(ne, 1)));
                 PSR_CUDA(ctx, cudaMemcpyAsync(keep, db64, sizeof(double) * ne, cudaMemcpyDeviceToDevice, s));
                 PSR_CUDA(ctx, cudaStreamSynchronize(s));
-                cudaFree(db64);
+                psr::dev_free(db64);
                 G.rinv = keep;
             }
             factor_bytes += ne * 8;
         } else if (prec == PSR_PREC_FP32) {
             float* f = nullptr;
-            PSR_CUDA(ctx, cudaMalloc(&f, sizeof(float) * std::max<int64_t>(ne, 1)));
+            PSR_CUDA(ctx, psr::dev_alloc(&f, sizeof(float) * std::max<int64_t>(ne, 1)));
             int blocks = (int)std::min<int64_t>((ne + 255) / 256, 152 * 16);
             count_launch(); k_convert<float><<<std::max(blocks, 1), 256, 0, s>>>(db64, G.m, p, ctx->opts.symmetrize, f);
             PSR_CHECK_LAUNCH(ctx, "k_convert fp32");
             PSR_CUDA(ctx, cudaStreamSynchronize(s));
-            if (!in_place) cudaFree(db64);
+            if (!in_place) psr::dev_free(db64);
             G.rinv = f;
             factor_bytes += ne * 4;
         } else {
@@ -598,7 +598,7 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<std::vector<int32_t>>& gi
                 G.rinv = bt;
             } else {
                 __nv_bfloat16* bt = nullptr;
-                PSR_CUDA(ctx, cudaMalloc(&bt, sizeof(__nv_bfloat16) * std::max<int64_t>(ne, 1)));
+                PSR_CUDA(ctx, psr::dev_alloc(&bt, sizeof(__nv_bfloat16) * std::max<int64_t>(ne, 1)));
                 int blocks = (int)std::min<int64_t>((ne + 255) / 256, 152 * 16);
                 count_launch(); k_convert<__nv_bfloat16><<<std::max(blocks, 1), 256, 0, s>>>(db64, G.m, p, ctx->opts.symmetrize, bt);
                 PSR_CHECK_LAUNCH(ctx, "k_convert bf16");
@@ -606,12 +606,12 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<std::vector<int32_t>>& gi
                 G.rinv = bt;
             }
             PSR_CUDA(ctx, cudaStreamSynchronize(s));
-            if (!in_place) cudaFree(db64);
+            if (!in_place) psr::dev_free(db64);
         }
         G.h_sorted_phi = hs;
         if (!G.tc && G.m < G.count && p <= 32) {
             std::vector<int32_t> wt;
-            PSR_CUDA(ctx, cudaMalloc(&G.sdofs_t, sizeof(int32_t) * (size_t)count * p));
+            PSR_CUDA(ctx, psr::dev_alloc(&G.sdofs_t, sizeof(int32_t) * (size_t)count * p));
             count_launch();
             k_transpose_sdofs<<<gather_grid((int64_t)count * p), 256, 0, s>>>(G.sdofs, count, p, G.sdofs_t);
             PSR_CHECK_LAUNCH(ctx, "k_transpose_sdofs");
@@ -627,7 +627,7 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<std::vector<int32_t>>& gi
                 i = j;
             }
             G.nwt = (int)(wt.size() / 3);
-            PSR_CUDA(ctx, cudaMalloc(&G.wtiles, sizeof(int32_t) * wt.size()));
+            PSR_CUDA(ctx, psr::dev_alloc(&G.wtiles, sizeof(int32_t) * wt.size()));
             PSR_CUDA(ctx, cudaMemcpy(G.wtiles, wt.data(), sizeof(int32_t) * wt.size(), cudaMemcpyHostToDevice));
             G.tpp = true;
         }
@@ -649,7 +649,7 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<std::vector<int32_t>>& gi
     ctx->stats.m_p = ctx->m_p;
     int rc = build_grouped_tables(ctx);
     if (rc != PSR_OK) return rc;
-    PSR_CUDA(ctx, cudaMalloc(&ctx->gcounter, sizeof(int32_t) * 2));
+    PSR_CUDA(ctx, psr::dev_alloc(&ctx->gcounter, sizeof(int32_t) * 2));
     PSR_CUDA(ctx, cudaMemset(ctx->gcounter, 0, sizeof(int32_t) * 2));
     ctx->grouped_blocks = 152 * 2;
     int mode = ctx->opts.sweep_kernel;
@@ -677,12 +677,12 @@ int build_grouped_tables(psr_ctx* ctx) {
             gt.push_back(ht[3 * t + 2]);
         }
     }
-    cudaFree(ctx->gtiles);
-    cudaFree(ctx->gdesc);
+    psr::dev_free(ctx->gtiles);
+    psr::dev_free(ctx->gdesc);
     ctx->gntiles = (int)(gt.size() / 4);
-    PSR_CUDA(ctx, cudaMalloc(&ctx->gtiles, sizeof(int32_t) * std::max<size_t>(gt.size(), 4)));
+    PSR_CUDA(ctx, psr::dev_alloc(&ctx->gtiles, sizeof(int32_t) * std::max<size_t>(gt.size(), 4)));
     PSR_CUDA(ctx, cudaMemcpy(ctx->gtiles, gt.data(), sizeof(int32_t) * gt.size(), cudaMemcpyHostToDevice));
-    PSR_CUDA(ctx, cudaMalloc(&ctx->gdesc, sizeof(GroupDesc) * std::max<size_t>(gd.size(), 1)));
+    PSR_CUDA(ctx, psr::dev_alloc(&ctx->gdesc, sizeof(GroupDesc) * std::max<size_t>(gd.size(), 1)));
     PSR_CUDA(ctx, cudaMemcpy(ctx->gdesc, gd.data(), sizeof(GroupDesc) * gd.size(), cudaMemcpyHostToDevice));
     return PSR_OK;
 }
@@ -768,7 +768,7 @@ int autotune_sweep(psr_ctx* ctx, cudaStream_t s) {
         }
         int32_t* d_all = nullptr;
         std::vector<cudaEvent_t> ev(cand.size() * (NT + 1), nullptr);
-        PSR_CUDA(ctx, cudaMalloc(&d_all, sizeof(int32_t) * std::max<size_t>(all.size(), 3)));
+        PSR_CUDA(ctx, psr::dev_alloc(&d_all, sizeof(int32_t) * std::max<size_t>(all.size(), 3)));
         rc = cuda_fail_if(ctx, cudaMemcpyAsync(d_all, all.data(), sizeof(int32_t) * all.size(), cudaMemcpyHostToDevice, s),
                           "autotune tiles");
         for (size_t e = 0; rc == PSR_OK && e < ev.size(); ++e)
@@ -807,8 +807,8 @@ int autotune_sweep(psr_ctx* ctx, cudaStream_t s) {
         }
         for (auto e : ev)
             if (e) cudaEventDestroy(e);
-        if (rc != PSR_OK) { cudaStreamSynchronize(s); cudaFree(d_all); break; }
-        cudaFree(d_all);
+        if (rc != PSR_OK) { cudaStreamSynchronize(s); psr::dev_free(d_all); break; }
+        psr::dev_free(d_all);
         G.tpp = cand[bc].tpp;
         if (!cand[bc].tpp) {
             G.warps = cand[bc].W;
@@ -936,21 +936,21 @@ int sweep_apply(psr_ctx* ctx, const double* r, double* z, cudaStream_t s) {
 
 void free_sweep(psr_ctx* ctx) {
     for (auto& G : ctx->groups) {
-        cudaFree(G.patch);
-        cudaFree(G.sdofs);
-        cudaFree(G.sphi);
-        cudaFree(G.tiles);
-        cudaFree(G.sdofs_t);
-        cudaFree(G.wtiles);
-        cudaFree(G.dbA);
+        psr::dev_free(G.patch);
+        psr::dev_free(G.sdofs);
+        psr::dev_free(G.sphi);
+        psr::dev_free(G.tiles);
+        psr::dev_free(G.sdofs_t);
+        psr::dev_free(G.wtiles);
+        psr::dev_free(G.dbA);
         if (G.rinv && !(ctx->A_ext && reinterpret_cast<double*>(G.rinv) >= ctx->A_ext &&
                          reinterpret_cast<double*>(G.rinv) < ctx->A_ext + ctx->A_ext_len))
-            cudaFree(G.rinv);
+            psr::dev_free(G.rinv);
         G = Group{};
     }
-    cudaFree(ctx->gtiles);
-    cudaFree(ctx->gdesc);
-    cudaFree(ctx->gcounter);
+    psr::dev_free(ctx->gtiles);
+    psr::dev_free(ctx->gdesc);
+    psr::dev_free(ctx->gcounter);
     ctx->gtiles = nullptr;
     ctx->gdesc = nullptr;
     ctx->gcounter = nullptr;

@@ -180,7 +180,7 @@ static size_t tc_smem(int P, int p) { return (size_t)2 * 128 * P * 2 + (size_t)P
 int convert_tc(const double* src, int m, int p, int sym, __nv_bfloat16** out, cudaStream_t s) {
     const int P = tc_pad(p);
     const size_t bytes = sizeof(__nv_bfloat16) * (size_t)std::max(m, 1) * P * P;
-    cudaError_t e = cudaMalloc(out, bytes);
+    cudaError_t e = psr::dev_alloc(out, bytes);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "bf16 database");
     const int64_t total = (int64_t)m * P * P;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 16));
