@@ -371,6 +371,7 @@ def run_gpu(args, cfg, ws, rank, local):
                    "krylov": cfg["krylov"] + ("(30)" if cfg["krylov"] == "fgmres" else ""),
                    "weighting": cfg["weighting"], "maxit": args.maxit, "rhs": "uniform(-1,1) seed 0",
                    "l2": "flushed (256 MB write) before every timed step",
+                   "allocations": "library caching allocator, filled by the warm-up steps",
                    "value_def": "n x preconditioner applications / step time (setup + solve)",
                    "parallelism": f"replicas x{ws}"},
         "setup_s": {"clustered": st["t_extract"] + st["t_rounds"] + st["t_convert"],
