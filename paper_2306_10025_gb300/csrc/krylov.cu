@@ -1307,27 +1307,34 @@ __global__ void k_fg_scale(double* __restrict__ w, int n, KDims kd) {
 }
 
 // Cycle end: y = H(1:K,1:K)^{-1} g(1:K) by back substitution (one thread).
-__global__ void k_fg_solve(KDims kd) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const int m = kd.m;
-    const int K = kd.ictl[I_K];
-    double* H = Hm(kd.scal, m);
-    double* g = Gv(kd.scal, m);
-    double* y = Yv(kd.scal, m);
-    for (int i = K - 1; i >= 0; --i) {
-        double s = g[i];
-        for (int l = i + 1; l < K; ++l) s -= H[i * m + l] * y[l];
-        y[i] = s / H[i * m + i];
-    }
-}
-
-// x += sum_{i<K} y_i Z_i ; then K = 0 (the update is consumed)
+// End of an FGMRES cycle: y = R^-1 g with R the K x K upper triangle left in
+// H by the Givens rotations (K <= 32), then x += sum_{i<K} y_i Z_i; every
+// block solves the small system itself.  The block stages R in shared
+// memory; warp 0 takes the reciprocals of the diagonal at once, then y_i
+// for i = K-1 .. 0, each followed by the update of the remaining right-hand
+// sides below it (lane l subtracts R[l][i] y_i), so a step costs a
+// multiply, a shuffle and an FMA instead of a division and a row dot.
 __global__ void k_fg_update(double* __restrict__ x, const double* __restrict__ Z, int n, KDims kd) {
-    __shared__ double sy[64];
+    __shared__ double sy[32];
+    __shared__ double sR[32][33];
     const int K = kd.ictl[I_K];
     if (K == 0) return;
-    const double* y = Yv(kd.scal, kd.m);
-    if (threadIdx.x < K) sy[threadIdx.x] = y[threadIdx.x];
+    const int m = kd.m;
+    const double* H = Hm(kd.scal, m);
+    for (int e = threadIdx.x; e < K * K; e += blockDim.x) sR[e / K][e % K] = H[(e / K) * m + e % K];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int l = threadIdx.x;
+        double sl = l < K ? Gv(kd.scal, m)[l] : 0.0;
+        const double rinv = l < K ? 1.0 / sR[l][l] : 0.0;
+        double yl = 0.0;
+        for (int i = K - 1; i >= 0; --i) {
+            const double yi = __shfl_sync(0xffffffffu, sl * rinv, i);
+            if (l == i) yl = yi;
+            if (l < i) sl = fma(-sR[l][i], yi, sl);
+        }
+        sy[l] = yl;
+    }
     __syncthreads();
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         double xe = x[e];
@@ -1716,7 +1723,6 @@ static int enqueue_fg_cycle(psr_ctx* ctx, KDims kd, cudaStream_t s) {
         count_launch(); k_fg_scale<<<nb, 256, 0, s>>>(Vn, n, kd);
         KT_END();
     }
-    count_launch(); k_fg_solve<<<1, 32, 0, s>>>(kd);
     count_launch(); k_fg_update<<<nb, 256, 0, s>>>(w.x, w.Z, n, kd);
     // restart residual r = b - A x (skipped once stopped)
     launch_spmv(ctx, w.x, w.r, w.b, 1, 2, kd, 1, w.nspmv, s);
@@ -1755,17 +1761,18 @@ int krylov_solve(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_s
     int32_t* hstop = nullptr;                     // control ints, then the step flags
     PSR_CUDA(ctx, psr::host_alloc(&hstop, (8 + 64) * sizeof(int32_t)));
     // capture one block / cycle into a graph (the pointers are the context's own)
-    if (ctx->opts.use_graph && !ctx->g_cycle) {
+    auto capture_graph = [&]() -> int {
         cudaStream_t cs;
         PSR_CUDA(ctx, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         cudaGraph_t g;
-        PSR_CUDA(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (ce != cudaSuccess) { cudaStreamDestroy(cs); return cuda_fail(ctx, ce, "graph capture"); }
         ctx->kt_marks.clear();
         set_capturing(true);
-        int rc = cg ? enqueue_cg_block(ctx, kd, block, cs) : enqueue_fg_cycle(ctx, kd, cs);
+        int rc2 = cg ? enqueue_cg_block(ctx, kd, block, cs) : enqueue_fg_cycle(ctx, kd, cs);
         set_capturing(false);
-        cudaError_t ce = cudaStreamEndCapture(cs, &g);
-        if (ce == cudaSuccess && rc == PSR_OK) {
+        ce = cudaStreamEndCapture(cs, &g);
+        if (ce == cudaSuccess && rc2 == PSR_OK) {
             size_t nn = 0;
             cudaGraphGetNodes(g, nullptr, &nn);
             std::vector<cudaGraphNode_t> nodes(nn);
@@ -1777,12 +1784,22 @@ int krylov_solve(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_s
             }
             ctx->graph_block = kn;
         }
-        if (rc != PSR_OK) { cudaStreamDestroy(cs); psr::host_free(hstop); return rc; }
-        if (ce != cudaSuccess) { cudaStreamDestroy(cs); psr::host_free(hstop); return cuda_fail(ctx, ce, "graph capture"); }
+        if (rc2 != PSR_OK) { if (ce == cudaSuccess) cudaGraphDestroy(g); cudaStreamDestroy(cs); return rc2; }
+        if (ce != cudaSuccess) { cudaStreamDestroy(cs); return cuda_fail(ctx, ce, "graph capture"); }
         ce = cudaGraphInstantiate(&ctx->g_cycle, g, 0);
         cudaGraphDestroy(g);
         cudaStreamDestroy(cs);
-        if (ce != cudaSuccess) { psr::host_free(hstop); ctx->g_cycle = nullptr; return cuda_fail(ctx, ce, "graph instantiate"); }
+        if (ce != cudaSuccess) { ctx->g_cycle = nullptr; return cuda_fail(ctx, ce, "graph instantiate"); }
+        return PSR_OK;
+    };
+    // Without per-kernel timing the first block / cycle is enqueued directly
+    // and the graph is captured and instantiated while the device runs it;
+    // with timing the graph comes first (the marks of a block are those of
+    // the graph).
+    const bool capture_behind = ctx->opts.use_graph && !ctx->g_cycle && !ctx->kt_on;
+    if (ctx->opts.use_graph && !ctx->g_cycle && !capture_behind) {
+        int rc0 = capture_graph();
+        if (rc0 != PSR_OK) { psr::host_free(hstop); return rc0; }
     }
     const int max_blocks = cg ? (ctx->opts.maxit + block - 1) / block + 2 : ctx->opts.maxit + 2;
     int rc = PSR_OK;
@@ -1795,6 +1812,7 @@ int krylov_solve(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_s
             ctx->kt_marks.clear();
             rc = cg ? enqueue_cg_block(ctx, kd, block, s) : enqueue_fg_cycle(ctx, kd, s);
             if (rc != PSR_OK) break;
+            if (it == 0 && capture_behind && (rc = capture_graph()) != PSR_OK) break;
         }
         PSR_CUDA(ctx, cudaMemcpyAsync(hstop, w.ictl, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         if (ctx->kt_on && !cg)
