@@ -21,7 +21,6 @@
 
 namespace psr {
 
-int sweep_apply_ex(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s);
 
 enum { S_RZ = 0, S_PQ, S_ALPHA, S_BETA, S_RN, S_R0, S_RTOL, S_H = 16 };
 enum { I_STOP = 0, I_CONV, I_IT, I_K, I_MAXIT, I_M, I_REORTH, I_ERR, I_CNT = 8, I_NCNT = 8 };
@@ -439,11 +438,14 @@ __device__ __forceinline__ float2 split_f64(double x) {
 // cycle start: V_0 = r / beta, g = (beta, 0, ...), K = 0
 // (with Vs0: the pair copy of V_0 for the fused Arnoldi step, and V_0 the
 // exact FP64 value of the pair)
+// Z0 (may be null): cleared for the first sweep of the cycle, which adds
+// into it.
 __global__ void k_fg_start(const double* __restrict__ r, double* __restrict__ V0, float2* __restrict__ Vs0, int n,
-                           KDims kd) {
+                           KDims kd, double* __restrict__ Z0) {
     if (kd.ictl[I_STOP]) return;
     const double beta = kd.scal[S_RN];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (Z0) Z0[i] = 0.0;
         const double v = r[i] / beta;
         if (Vs0) {
             const float2 q = split_f64(v);
@@ -1142,7 +1144,8 @@ __device__ __noinline__ double fp64_rest(const double* __restrict__ V, double* _
 template <int NV>
 __global__ void __launch_bounds__(KT, 1) k_arnoldi(const double* __restrict__ V, double* __restrict__ w,
                                                float2* __restrict__ Vs, int n, int j, KDims kd,
-                                               double* __restrict__ part, unsigned int* bar, int fp64) {
+                                               double* __restrict__ part, unsigned int* bar, int fp64,
+                                               double* __restrict__ zn) {
     __shared__ double sh[NV][KT / 32 + 1];
     __shared__ double sh_h[NV];
     __shared__ float2 sh_hs[NV];
@@ -1158,6 +1161,10 @@ __global__ void __launch_bounds__(KT, 1) k_arnoldi(const double* __restrict__ V,
     const int nv = j + 1;
     const int m = kd.m;
     const int G = gridDim.x;
+    // the next sweep's output (it adds into a cleared vector); plain stores
+    // that no pass of this step waits for
+    if (zn)
+        for (int e = blockIdx.x * KT + threadIdx.x; e < n; e += G * KT) zn[e] = 0.0;
     const int T = KT / NV;
     if (blockIdx.x == 0) {                            // used by the finish at the end
         if (threadIdx.x < j) {
@@ -1675,6 +1682,8 @@ static int enqueue_arnoldi(psr_ctx* ctx, KDims kd, int j, double* Vn, cudaStream
     // the FP64 value of the normalised pair.
     // In FP64 (PSR_ORTHO_FP64): the projection reads w and j+1 rows, each
     // update j+1 rows and w twice, the normalisation writes w and its pair.
+    // Not counted: the clearing of Z_{j+1} for the next sweep (zn), which an
+    // ideal sweep would not need.
     const int fp64 = ctx->opts.ortho == PSR_ORTHO_FP64 ? 1 : 0;
     if (fp64) {
         KT_BEGIN(PSR_KT_MDOT, j, ((j + 2) + (j + 3) + 3) * vb, 4.0 * n * (j + 2) + 3.0 * n);
@@ -1684,8 +1693,9 @@ static int enqueue_arnoldi(psr_ctx* ctx, KDims kd, int j, double* Vn, cudaStream
         KT_REORTH((j + 3) * vb, 0.0);
     }
     count_launch();
+    double* zn = (j + 1 < kd.m) ? w.Z + (size_t)(j + 1) * n : nullptr;
     PSR_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_arnoldi<NV>, (const double*)w.V, Vn, w.Vs, n, j, kd, w.part_arn, w.bar,
-                                     fp64));
+                                     fp64, zn));
     KT_END();
     return PSR_OK;
 }
@@ -1693,22 +1703,25 @@ static int enqueue_arnoldi(psr_ctx* ctx, KDims kd, int j, double* Vn, cudaStream
 static int enqueue_fg_cycle(psr_ctx* ctx, KDims kd, cudaStream_t s) {
     KrylovWS& w = ctx->ws;
     const int n = ctx->n, nb = w.nblk, m = kd.m;
-    float2* Vs0 = (w.coop && ctx->opts.ortho != PSR_ORTHO_SPLIT) ? w.Vs : nullptr;
-    count_launch(); k_fg_start<<<nb, 256, 0, s>>>(w.r, w.V, Vs0, n, kd);
+    // The fused step clears the next sweep's output Z_{j+1} (k_fg_start
+    // clears Z_0), so the sweeps of the cycle skip their own memset.
+    const bool fused = w.coop && ctx->opts.ortho != PSR_ORTHO_SPLIT;
+    float2* Vs0 = fused ? w.Vs : nullptr;
+    count_launch(); k_fg_start<<<nb, 256, 0, s>>>(w.r, w.V, Vs0, n, kd, fused ? w.Z : nullptr);
     for (int j = 0; j < m; ++j) {
         double* Vj = w.V + (size_t)j * n;
         double* Vn = w.V + (size_t)(j + 1) * n;
         double* Zj = w.Z + (size_t)j * n;
         const double vb = 8.0 * n;
         KT_BEGIN(PSR_KT_SWEEP, j, sweep_bytes(ctx), sweep_flops(ctx));
-        int rc = sweep_apply_ex(ctx, Vj, Zj, kd.ictl + I_STOP, s);
+        int rc = sweep_apply_ex(ctx, Vj, Zj, kd.ictl + I_STOP, s, fused);
         if (rc != PSR_OK) return rc;
         KT_END();
         KT_BEGIN(PSR_KT_SPMV, j, spmv_bytes(ctx), 2.0 * ctx->nnz);
         launch_spmv(ctx, Zj, Vn, nullptr, 0, 0, kd, 1, w.nspmv, s);
         KT_END();
         int rc2 = PSR_OK;
-        if (w.coop && ctx->opts.ortho != PSR_ORTHO_SPLIT) {
+        if (fused) {
             if (j < 8) rc2 = enqueue_arnoldi<8>(ctx, kd, j, Vn, s);
             else if (j < 16) rc2 = enqueue_arnoldi<16>(ctx, kd, j, Vn, s);
             else rc2 = enqueue_arnoldi<32>(ctx, kd, j, Vn, s);

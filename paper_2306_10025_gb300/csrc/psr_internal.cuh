@@ -229,7 +229,9 @@ int launch_spectral_norm(const double* E, int32_t batch, int32_t p, double* sigm
 int build_sweep(psr_ctx* ctx, cudaStream_t s);
 int sweep_apply(psr_ctx* ctx, const double* r, double* z, cudaStream_t s);
 int autotune_sweep(psr_ctx* ctx, cudaStream_t s);
-int sweep_apply_ex(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s);
+// z_zeroed: z is already zero (the caller cleared it), the sweep skips its memset
+int sweep_apply_ex(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s,
+                   bool z_zeroed = false);
 int build_grouped_tables(psr_ctx* ctx);
 void free_sweep(psr_ctx* ctx);
 int coarse_apply(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s);

@@ -6,7 +6,6 @@
 
 namespace psr {
 
-int sweep_apply_ex(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s);
 
 // r = b - A x (SELL-32: one thread per row, all rows of a warp in one slice)
 __global__ void __launch_bounds__(256) k_residual_sell(const int64_t* __restrict__ sptr,

@@ -874,16 +874,17 @@ static int launch_group(psr_ctx* ctx, const Group& G, const double* r, double* z
 }
 
 // z = M^-1 r (Eq. 3), plus P0 A0^-1 R0 r when a coarse space is set (Eq. 2)
-static int sweep_patches(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s);
+static int sweep_patches(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s, bool z_zeroed);
 
-int sweep_apply_ex(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s) {
-    const int rc = sweep_patches(ctx, r, z, stop, s);
+int sweep_apply_ex(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s, bool z_zeroed) {
+    const int rc = sweep_patches(ctx, r, z, stop, s, z_zeroed);
     if (rc != PSR_OK) return rc;
     return coarse_apply(ctx, r, z, stop, s);
 }
 
-static int sweep_patches(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s) {
-    PSR_CUDA(ctx, cudaMemsetAsync(z, 0, sizeof(double) * (size_t)ctx->n, s));
+static int sweep_patches(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s,
+                         bool z_zeroed) {
+    if (!z_zeroed) PSR_CUDA(ctx, cudaMemsetAsync(z, 0, sizeof(double) * (size_t)ctx->n, s));
     const int prec = ctx->opts.store_prec;
     if (ctx->sweep_mode == PSR_SWEEP_GROUPED && prec != PSR_PREC_BF16) {
         int pmax = 0;
