@@ -51,3 +51,5 @@ def test_compute_without_gpu_fails_loudly():
     rc = lib.psr_setup(C.byref(A), C.byref(P_), C.byref(o), None, C.byref(h))
     assert rc == -5 and not h.value
     assert b"CUDA" in lib.psr_last_error(None)
+    # the allocator's release has nothing to return and reports the missing device
+    assert lib.psr_release_cached_memory() == -5
