@@ -776,3 +776,28 @@ def kmeans_varmin(A, init, max_iter=100, near_tie_rel=1e-9):
             reps[j] = members[t_best]
     return {"phi": phi, "reps": reps, "Binv": Ainv[reps], "singular": singular_all[reps], "sweeps": sweeps,
             "near_ties": near}
+
+
+# ---------------------------------------------------------------------------
+# Patch detection from the matrix alone (section 2, after Figure 1: cell-
+# restricted patches are found as the rows with q (p+1)^d stored entries)
+# ---------------------------------------------------------------------------
+
+def detect_patches(rowptr, colidx, n, row_nnz):
+    """A row with exactly row_nnz = q (p+1)^d stored entries (q components,
+    tensor-product cells of degree p in d dimensions) couples only with the
+    DOFs of one cell, so its column set is that cell's DOF set.  Returns one
+    patch per distinct column set, in the order of the smallest row that has
+    it, each patch's DOFs ascending: an int32 array [patches, row_nnz]."""
+    seen = set()
+    out = []
+    for r in range(n):
+        a, b = int(rowptr[r]), int(rowptr[r + 1])
+        if b - a != row_nnz:
+            continue
+        key = tuple(sorted(int(c) for c in colidx[a:b]))
+        if key in seen:
+            continue
+        seen.add(key)
+        out.append(key)
+    return np.array(out, dtype=np.int32).reshape(-1, row_nnz)

@@ -129,8 +129,9 @@ def graded_sizes(n: int, ratio: float) -> np.ndarray:
     return h0 * ratio ** np.arange(n)
 
 
-def poisson2d_q2(N: int = 16, rho: float = 1.0) -> Problem:
-    """2D Q2 diffusion on a uniform N x N mesh with Dirichlet identity rows."""
+def poisson2d_q2(N: int = 16, rho: float = 1.0, keep_pattern: bool = False) -> Problem:
+    """2D Q2 diffusion on a uniform N x N mesh with Dirichlet identity rows
+    (keep_pattern: their couplings stay stored as zeros)."""
     Kdir, _ = fem.reference_matrices(2, 2, 3)
     nc = N * N
     h = np.full((nc, 2), 1.0 / N)
@@ -138,7 +139,7 @@ def poisson2d_q2(N: int = 16, rho: float = 1.0) -> Problem:
     edofs = _q2_cell_nodes_2d(N, N)
     n = (2 * N + 1) ** 2
     bnd = _boundary_nodes_2d(2 * N + 1, 2 * N + 1)
-    rowptr, colidx, vals = fem.assemble_csr(n, edofs, Ke, bnd)
+    rowptr, colidx, vals = fem.assemble_csr(n, edofs, Ke, bnd, keep_pattern=keep_pattern)
     off, flat = _uniform_patches(edofs)
     return Problem(f"poisson2d_q2_N{N}", n, rowptr, colidx, vals, off, flat, ~bnd,
                    symmetric=True, krylov="cg", weighting="sym",
@@ -239,8 +240,9 @@ def smooth2d_qp(N: int = 60, p: int = 2) -> Problem:
                          "P0": (prow.astype(np.int32), c_.astype(np.int32), v_.astype(np.float64), nv * nv)})
 
 
-def stokes2d_q2q1(N: int = 128, ratio: float = 1.05) -> Problem:
-    """2D Taylor-Hood Stokes [K B^T; B 0] on an N x N mesh graded in y."""
+def stokes2d_q2q1(N: int = 128, ratio: float = 1.05, keep_pattern: bool = False) -> Problem:
+    """2D Taylor-Hood Stokes [K B^T; B 0] on an N x N mesh graded in y
+    (keep_pattern: Dirichlet couplings stay stored as zeros)."""
     Kdir, _ = fem.reference_matrices(2, 2, 3)
     Bref = fem.reference_divergence(2, 1, 2, 3)          # (2, 4, 9)
     hx = np.full(N, 1.0 / N)
@@ -270,7 +272,7 @@ def stokes2d_q2q1(N: int = 128, ratio: float = 1.05) -> Problem:
     dirichlet[:nv] = bnd
     dirichlet[nv:2 * nv] = bnd
     dirichlet[2 * nv] = True            # pressure pin at vertex (0, 0)
-    rowptr, colidx, vals = fem.assemble_csr(n, edofs, E, dirichlet)
+    rowptr, colidx, vals = fem.assemble_csr(n, edofs, E, dirichlet, keep_pattern=keep_pattern)
     rhs_mask = np.zeros(n, dtype=bool)
     rhs_mask[:2 * nv] = ~dirichlet[:2 * nv]
     off, flat = _uniform_patches(edofs)
@@ -338,7 +340,7 @@ def gaussian_random_field(N: int, corr_len: float, seed: int) -> np.ndarray:
 
 
 def diffusion3d_q2(N: int = 32, sigma: float = 1.0, corr_len: float = 8.0, seed: int = 0,
-                   uniform: bool = False) -> Problem:
+                   uniform: bool = False, keep_pattern: bool = False) -> Problem:
     """3D Q2 diffusion with a lognormal cell coefficient (or rho = 1 when
     uniform=True), Dirichlet identity rows; 27-DOF patches."""
     Kdir, _ = fem.reference_matrices(2, 3, 3)
@@ -353,7 +355,7 @@ def diffusion3d_q2(N: int = 32, sigma: float = 1.0, corr_len: float = 8.0, seed:
     m = 2 * N + 1
     n = m ** 3
     bnd = _boundary_nodes_3d(m)
-    rowptr, colidx, vals = fem.assemble_csr(n, edofs, Ke, bnd)
+    rowptr, colidx, vals = fem.assemble_csr(n, edofs, Ke, bnd, keep_pattern=keep_pattern)
     off, flat = _uniform_patches(edofs)
     return Problem(f"diffusion3d_q2_N{N}", n, rowptr, colidx, vals, off, flat, ~bnd,
                    symmetric=True, krylov="cg", weighting="sym",

@@ -125,7 +125,7 @@ def rect_diffusion_element(Kdir: np.ndarray, h: np.ndarray, rho: np.ndarray):
     return out
 
 
-def assemble_csr(n: int, edofs: np.ndarray, Ke: np.ndarray, dirichlet: np.ndarray):
+def assemble_csr(n: int, edofs: np.ndarray, Ke: np.ndarray, dirichlet: np.ndarray, keep_pattern: bool = False):
     """Assemble element matrices into CSR with symmetric Dirichlet identity
     rows.
 
@@ -135,7 +135,9 @@ def assemble_csr(n: int, edofs: np.ndarray, Ke: np.ndarray, dirichlet: np.ndarra
       increasing cell order (so translation-equivalent cells give bitwise
       equal sums).
     * Rows and columns of Dirichlet DOFs are removed and a unit diagonal is
-      put in their place ("a row with only one nonzero").
+      put in their place ("a row with only one nonzero"); with keep_pattern
+      their entries stay in the sparsity pattern as stored zeros (unit
+      diagonal), so every row keeps the symbolic nonzeros of its cells.
     Returns (rowptr int32, colidx int32, vals float64); columns sorted and
     unique in every row.
     """
@@ -144,8 +146,12 @@ def assemble_csr(n: int, edofs: np.ndarray, Ke: np.ndarray, dirichlet: np.ndarra
     rows = np.repeat(e64, ne, axis=1).reshape(-1)
     cols = np.tile(e64, (1, ne)).reshape(-1)
     vals = np.ascontiguousarray(Ke, dtype=np.float64).reshape(-1)
-    keep = ~(dirichlet[rows] | dirichlet[cols])
-    rows, cols, vals = rows[keep], cols[keep], vals[keep]
+    drop = dirichlet[rows] | dirichlet[cols]
+    if keep_pattern:
+        vals = np.where(drop, 0.0, vals)
+    else:
+        keep = ~drop
+        rows, cols, vals = rows[keep], cols[keep], vals[keep]
     key = rows * n + cols
     order = np.argsort(key, kind="stable")  # keeps cell order inside a key
     key = key[order]
@@ -164,8 +170,11 @@ def assemble_csr(n: int, edofs: np.ndarray, Ke: np.ndarray, dirichlet: np.ndarra
         sums[grp[m]] += vals[m]  # one contribution per entry per pass
     ukey = key[starts]
     dd = np.flatnonzero(dirichlet).astype(np.int64)
-    ukey = np.concatenate([ukey, dd * n + dd])
-    sums = np.concatenate([sums, np.ones(dd.size)])
+    if keep_pattern:
+        sums[np.isin(ukey, dd * n + dd)] = 1.0
+    else:
+        ukey = np.concatenate([ukey, dd * n + dd])
+        sums = np.concatenate([sums, np.ones(dd.size)])
     o2 = np.argsort(ukey, kind="stable")
     ukey = ukey[o2]
     sums = sums[o2]
