@@ -258,6 +258,28 @@ const char* psr_last_error(psr_ctx* ctx);
 
 void psr_destroy(psr_ctx* ctx);
 
+/* Patch detection (section 2, after Figure 1): cell-restricted patches found
+ * from the matrix alone.  A row with exactly row_nnz = q (p+1)^d stored
+ * entries (q components, tensor-product cells of degree p in d dimensions)
+ * couples only with the DOFs of its own cell, so its column set is that
+ * cell's DOF set; every distinct set of such rows is one patch.  The stored
+ * pattern must be the symbolic one (boundary conditions that remove entries
+ * hide the boundary cells).
+ *   A:           device CSR (vals unused); only rows of length row_nnz are
+ *                read, and their columns must be sorted, unique, in range.
+ *   row_nnz:     1..1024.
+ *   dofs:        device int32 [max_patches * row_nnz], or NULL to only count.
+ *                Patch k (ordered by the smallest row having its set) is
+ *                dofs[k * row_nnz .. k * row_nnz + row_nnz), ascending, and
+ *                goes to psr_setup as a uniform-size patch map.
+ *   n_patches:   host; the number of patches found (also when dofs is NULL
+ *                or too small).
+ * Errors: INVALID_ARG (bad argument, more patches than max_patches, or two
+ * different column sets with equal 64-bit hashes), UNSORTED_CSR, CUDA.
+ * Blocks the host until done. */
+int psr_detect_patches(const psr_csr* A, int32_t row_nnz, int32_t* dofs, int32_t max_patches,
+                       int32_t* n_patches, void* stream);
+
 /* Memory: the library keeps the device and pinned host blocks that a destroy
  * (or a setup's temporaries) frees and hands them out again to later
  * allocations of a similar size (1x to 1.25x), after one device

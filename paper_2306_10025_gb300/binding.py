@@ -34,7 +34,8 @@ EXPORTS = ["psr_default_opts", "psr_setup", "psr_apply", "psr_solve", "psr_get_h
            "psr_setup_seeded", "psr_features", "psr_mlp_create", "psr_mlp_num_params", "psr_mlp_set_params",
            "psr_mlp_get_params", "psr_mlp_loss_grad", "psr_mlp_train_step", "psr_mlp_predict", "psr_mlp_destroy",
            "psr_criterion_noalloc", "psr_set_kernel_timing", "psr_get_kernel_timing", "psr_setup_kmeans",
-           "psr_export_database", "psr_set_coarse", "psr_smooth", "psr_release_cached_memory"]
+           "psr_export_database", "psr_set_coarse", "psr_smooth", "psr_release_cached_memory",
+           "psr_detect_patches"]
 
 KT_CLASSES = ("sweep", "spmv", "mdot", "maxpy", "vec")   # PSR_KT_* in order
 
@@ -120,6 +121,7 @@ def load(path: str = LIB_PATH):
     lib.psr_criterion_noalloc.argtypes = [vp, i32, i32, vp, vp, d, vp, vp, vp]
     lib.psr_kernel_launches.argtypes = []
     lib.psr_release_cached_memory.argtypes = []
+    lib.psr_detect_patches.argtypes = [C.POINTER(psr_csr), i32, vp, i32, C.POINTER(i32), vp]
     lib.psr_set_kernel_timing.argtypes = [vp, i32]
     lib.psr_get_kernel_timing.argtypes = [vp, vp, vp, vp, vp, i32]
     lib.psr_setup_seeded.argtypes = [C.POINTER(psr_csr), C.POINTER(psr_patches), C.POINTER(psr_opts), vp, i32, vp,
@@ -461,6 +463,24 @@ def psr_spectral_norm(E, sigma, stream=None):
 
 def psr_kernel_launches() -> int:
     return int(load().psr_kernel_launches())
+
+
+def psr_detect_patches(rowptr, colidx, row_nnz: int, stream=None):
+    """Cell-restricted patches of the rows with row_nnz stored entries:
+    a device int32 tensor [patches, row_nnz], DOFs ascending, patches in the
+    order of their smallest row (psr_detect_patches)."""
+    import torch
+    _need(rowptr, torch.int32, "rowptr")
+    _need(colidx, torch.int32, "colidx")
+    A = psr_csr(rowptr.numel() - 1, colidx.numel(), rowptr.data_ptr(), colidx.data_ptr(), 0)
+    cnt = C.c_int32(0)
+    _check(load().psr_detect_patches(C.byref(A), int(row_nnz), None, 0, C.byref(cnt), _stream(stream)))
+    out = torch.empty((max(cnt.value, 0), int(row_nnz)), dtype=torch.int32, device=rowptr.device)
+    if cnt.value > 0:
+        got = C.c_int32(0)
+        _check(load().psr_detect_patches(C.byref(A), int(row_nnz), _ptr(out), cnt.value, C.byref(got),
+                                         _stream(stream)))
+    return out
 
 
 def psr_release_cached_memory() -> None:

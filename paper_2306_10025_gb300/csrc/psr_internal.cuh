@@ -76,6 +76,7 @@ enum : int {
     ST_UNCOVERED = 4,
     ST_SINGULAR = 8,
     ST_NAN = 16,
+    ST_HASH = 32,       // patch detection: two column sets with one hash
 };
 
 // ------------------------------------------------------------ size group
