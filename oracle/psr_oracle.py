@@ -558,11 +558,13 @@ def alg1_seeded(A, tol, A_seed, pred=None):
 # a cluster left without members keeps its mean) and another sweep follows.
 # ---------------------------------------------------------------------------
 
-def kmeans_l1(A, init, max_iter=100, near_tie_rel=1e-9):
+def kmeans_l1(A, init, max_iter=100, near_tie_rel=1e-9, classes=None):
     """Returns phi (n_p), means (m_p, p, p), Binv (inverses of the means),
     singular flags, the number of sweeps and the near ties of the last sweep:
     patches with another mean within near_tie_rel (relative) of the nearest,
-    where the argmin could differ between two summation orders."""
+    where the argmin could differ between two summation orders.
+    classes (per patch, e.g. boundary_classes): each partition is clustered
+    on its own -- a patch is assigned only to means seeded in its class."""
     A = np.asarray(A, dtype=np.float64)
     npch = A.shape[0]
     init = np.asarray(init, dtype=np.int64)
@@ -570,6 +572,11 @@ def kmeans_l1(A, init, max_iter=100, near_tie_rel=1e-9):
     B = A[init].copy()
     phi = np.full(npch, -1, dtype=np.int64)
     flat = A.reshape(npch, -1)
+    other = None
+    if classes is not None:
+        classes = np.asarray(classes)
+        other = classes[:, None] != classes[init][None, :]
+        assert not other.all(axis=1).any(), "a class without a seed"
     sweeps = 0
     near = []
     while sweeps < max_iter:
@@ -577,6 +584,8 @@ def kmeans_l1(A, init, max_iter=100, near_tie_rel=1e-9):
         D = np.empty((npch, m))
         for j in range(m):
             D[:, j] = np.abs(flat - B[j].reshape(-1)).sum(axis=1)
+        if other is not None:
+            D[other] = np.inf
         new = np.argmin(D, axis=1)
         best = D[np.arange(npch), new]
         close = (D <= best[:, None] * (1.0 + near_tie_rel)) & (D > 0.0)
@@ -801,3 +810,31 @@ def detect_patches(rowptr, colidx, n, row_nnz):
         seen.add(key)
         out.append(key)
     return np.array(out, dtype=np.int32).reshape(-1, row_nnz)
+
+
+# ---------------------------------------------------------------------------
+# Boundary partition of the patch matrices (section 3.2, after the Alg. 2
+# variants): boundary conditions show as patch rows with one nonzero entry
+# ---------------------------------------------------------------------------
+
+def boundary_classes(A):
+    """Class of every patch: the set of its rows with exactly one nonzero
+    entry (a boundary condition); patches with the same set form one
+    partition.  Classes are numbered in the order of their first patch.
+    Returns (class per patch, number of classes)."""
+    A = np.asarray(A)
+    ids = {}
+    cls = np.empty(A.shape[0], dtype=np.int32)
+    for k in range(A.shape[0]):
+        key = tuple(np.flatnonzero(np.count_nonzero(A[k], axis=1) == 1))
+        cls[k] = ids.setdefault(key, len(ids))
+    return cls, len(ids)
+
+
+def proportional_split(classes, m_total):
+    """Clusters per class in proportion to the class sizes (section 3.2: the
+    number of clusters divided between boundary types by patch count):
+    round(m_total n_c / n), at least 1 and at most n_c."""
+    sizes = np.bincount(np.asarray(classes))
+    n = sizes.sum()
+    return np.array([min(int(c), max(1, int(np.floor(m_total * c / n + 0.5)))) for c in sizes], dtype=np.int64)
