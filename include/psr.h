@@ -174,10 +174,28 @@ int psr_setup_seeded(const psr_csr* A, const psr_patches* patches, const psr_opt
  * summed in increasing patch index; an emptied cluster keeps its mean) until
  * a sweep changes nothing or after max_iter sweeps.  opts->tol is ignored;
  * psr_get_stats reports the sweeps in `rounds`.  Needs patches of one size
- * p <= 128.  Errors: INVALID_ARG (arguments, seeds not distinct or out of
- * range), SINGULAR_PATCH (a mean failed the pivot test), OOM, CUDA. */
+ * p <= 128.  patch_class (device, n_patches int32, or NULL): the boundary
+ * partition of psr_boundary_classes -- a patch is then assigned only among
+ * the means seeded in its class, every class needing a seed.  Errors:
+ * INVALID_ARG (arguments, seeds not distinct or out of range, a class
+ * without a seed), SINGULAR_PATCH (a mean failed the pivot test), OOM, CUDA. */
 int psr_setup_kmeans(const psr_csr* A, const psr_patches* patches, const psr_opts* opts, int32_t m_p,
-                     const int32_t* init, int32_t max_iter, void* stream, psr_ctx** out);
+                     const int32_t* init, int32_t max_iter, const int32_t* patch_class, void* stream,
+                     psr_ctx** out);
+
+/* Boundary partition for Alg. 2 (section 3.2): boundary conditions appear in
+ * a patch matrix as rows with exactly one nonzero entry, and averaging a
+ * patch that has them with one that has not destroys them, so the patches
+ * are partitioned by the set of such rows and each partition is clustered
+ * on its own (9 partitions on a square, 27 on a cube).  patch_class (device,
+ * n_patches int32, written) gets the partition of every patch, numbered in
+ * the order of its first patch; n_classes (host) their number.  Pass the
+ * classes as psr_setup_kmeans's patch_class, with init holding at least one
+ * seed of every class (the paper divides the clusters in proportion to the
+ * partition sizes).  Patches of at most 64 DOFs.  Errors: INVALID_ARG,
+ * UNSORTED_CSR, OOM, CUDA.  Blocks the host until done. */
+int psr_boundary_classes(const psr_csr* A, const psr_patches* patches, int32_t* patch_class,
+                         int32_t* n_classes, void* stream);
 
 /* z = M~^{-1} r (Eq. 3 with the context's weighting).  r, z: device, length n,
  * must not overlap.  Stream-ordered, no host synchronisation, no allocation. */

@@ -697,13 +697,18 @@ def alg1_l1(A, tol, near_tie_rel=1e-9):
 # variant.
 # ---------------------------------------------------------------------------
 
-def kmeans_spectral(A, init, max_iter=100, near_tie_rel=1e-9):
+def kmeans_spectral(A, init, max_iter=100, near_tie_rel=1e-9, classes=None):
     A = np.asarray(A, dtype=np.float64)
     npch = A.shape[0]
     init = np.asarray(init, dtype=np.int64)
     m = init.size
     B = A[init].copy()
     phi = np.full(npch, -1, dtype=np.int64)
+    other = None
+    if classes is not None:                  # boundary partition, as in kmeans_l1
+        classes = np.asarray(classes)
+        other = classes[:, None] != classes[init][None, :]
+        assert not other.all(axis=1).any(), "a class without a seed"
     sweeps = 0
     near = []
     while sweeps < max_iter:
@@ -712,6 +717,8 @@ def kmeans_spectral(A, init, max_iter=100, near_tie_rel=1e-9):
         Bi, _ = lu_inverse(B)
         for j in range(m):
             D[:, j] = criterion(A, B[j][None], Bi[j][None])
+        if other is not None:
+            D[other] = np.inf
         new = np.argmin(D, axis=1)
         best = D[np.arange(npch), new]
         close = (D <= best[:, None] * (1.0 + near_tie_rel)) & (D > 0.0)

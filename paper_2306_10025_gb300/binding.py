@@ -35,7 +35,7 @@ EXPORTS = ["psr_default_opts", "psr_setup", "psr_apply", "psr_solve", "psr_get_h
            "psr_mlp_get_params", "psr_mlp_loss_grad", "psr_mlp_train_step", "psr_mlp_predict", "psr_mlp_destroy",
            "psr_criterion_noalloc", "psr_set_kernel_timing", "psr_get_kernel_timing", "psr_setup_kmeans",
            "psr_export_database", "psr_set_coarse", "psr_smooth", "psr_release_cached_memory",
-           "psr_detect_patches"]
+           "psr_detect_patches", "psr_boundary_classes"]
 
 KT_CLASSES = ("sweep", "spmv", "mdot", "maxpy", "vec")   # PSR_KT_* in order
 
@@ -128,7 +128,8 @@ def load(path: str = LIB_PATH):
                                      vp, C.POINTER(vp)]
     lib.psr_features.argtypes = [vp, i32, i32, vp, vp, vp]
     lib.psr_setup_kmeans.argtypes = [C.POINTER(psr_csr), C.POINTER(psr_patches), C.POINTER(psr_opts), i32, vp, i32,
-                                     vp, C.POINTER(vp)]
+                                     vp, vp, C.POINTER(vp)]
+    lib.psr_boundary_classes.argtypes = [C.POINTER(psr_csr), C.POINTER(psr_patches), vp, C.POINTER(i32), vp]
     lib.psr_mlp_create.argtypes = [i32, i32, i32, C.POINTER(vp)]
     lib.psr_mlp_num_params.argtypes = [vp]
     lib.psr_mlp_set_params.argtypes = [vp, vp, vp]
@@ -345,18 +346,22 @@ def psr_setup_seeded(rowptr, colidx, vals, dofs, uniform_size, seed_A, hints=Non
 
 
 def psr_setup_kmeans(rowptr, colidx, vals, dofs, uniform_size, init, max_iter=100, opts: psr_opts | None = None,
-                     stream=None) -> "Context":
+                     stream=None, patch_class=None) -> "Context":
     """Database by Alg. 2, entrywise k-means, seeded with the patches init
-    (device int32, m_p distinct patch indices)."""
+    (device int32, m_p distinct patch indices); patch_class (device int32 per
+    patch, from psr_boundary_classes) restricts every patch to the means of
+    its class."""
     import torch
     lib = load()
     A = _csr(rowptr, colidx, vals)
     P = _patches(dofs, None, uniform_size)
     _need(init, torch.int32, "init")
+    if patch_class is not None:
+        _need(patch_class, torch.int32, "patch_class")
     o = opts if opts is not None else make_opts()
     h = C.c_void_p()
     rc = lib.psr_setup_kmeans(C.byref(A), C.byref(P), C.byref(o), init.numel(), _ptr(init), max_iter,
-                              _stream(stream), C.byref(h))
+                              _ptr(patch_class), _stream(stream), C.byref(h))
     _check(rc, None)
     return Context(h, A.n, P.n_patches, o, P.uniform_size)
 
@@ -481,6 +486,18 @@ def psr_detect_patches(rowptr, colidx, row_nnz: int, stream=None):
         _check(load().psr_detect_patches(C.byref(A), int(row_nnz), _ptr(out), cnt.value, C.byref(got),
                                          _stream(stream)))
     return out
+
+
+def psr_boundary_classes(rowptr, colidx, vals, dofs, offsets=None, uniform_size=0, stream=None):
+    """Boundary partition of the patches (psr_boundary_classes): (device int32
+    class per patch, number of classes)."""
+    import torch
+    A = _csr(rowptr, colidx, vals)
+    P = _patches(dofs, offsets, uniform_size)
+    out = torch.empty(P.n_patches, dtype=torch.int32, device=rowptr.device)
+    k = C.c_int32(0)
+    _check(load().psr_boundary_classes(C.byref(A), C.byref(P), _ptr(out), C.byref(k), _stream(stream)))
+    return out, k.value
 
 
 def psr_release_cached_memory() -> None:

@@ -92,6 +92,7 @@ struct AssignMode {
     int km_m = 0;
     const std::vector<int32_t>* km_init = nullptr;
     int km_iter = 0;
+    const std::vector<int32_t>* km_cls = nullptr;   // class of every patch (boundary partition) or null
 };
 
 static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o, cudaStream_t s, psr_ctx** out,
@@ -220,7 +221,7 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
             FAIL(PSR_ERR_INVALID_ARG);
         }
         if (mode.km_m > 0) {
-            rc = run_kmeans(ctx, s, mode.km_m, *mode.km_init, mode.km_iter);
+            rc = run_kmeans(ctx, s, mode.km_m, *mode.km_init, mode.km_iter, mode.km_cls);
             if (rc != PSR_OK) goto fail;
         } else if (op.tol == 0.0 && m0 == 0) {
             // strict "< 0" never holds: every patch is its own entry (Eq. 1)
@@ -390,7 +391,8 @@ int psr_setup_seeded(const psr_csr* A, const psr_patches* patches, const psr_opt
 }
 
 int psr_setup_kmeans(const psr_csr* A, const psr_patches* patches, const psr_opts* opts, int32_t m_p,
-                     const int32_t* init, int32_t max_iter, void* stream, psr_ctx** out) {
+                     const int32_t* init, int32_t max_iter, const int32_t* patch_class, void* stream,
+                     psr_ctx** out) {
     if (!out) { set_error(nullptr, "out is NULL"); return PSR_ERR_INVALID_ARG; }
     *out = nullptr;
     if (!A || !patches || !A->rowptr || !A->vals || !A->colidx || A->n <= 0 || patches->n_patches <= 0 ||
@@ -417,12 +419,36 @@ int psr_setup_kmeans(const psr_csr* A, const psr_patches* patches, const psr_opt
             }
             seen[(size_t)v] = 1;
         }
+        // boundary partition: every class needs at least one seed
+        std::vector<int32_t> h_cls;
+        if (patch_class) {
+            h_cls.resize((size_t)patches->n_patches);
+            e = cudaMemcpy(h_cls.data(), patch_class, sizeof(int32_t) * h_cls.size(), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(nullptr, e, "k-means patch classes");
+            int32_t cmax = -1;
+            for (int32_t c : h_cls) {
+                if (c < 0 || c >= patches->n_patches) {
+                    set_error(nullptr, "patch classes must lie in [0, n_patches)");
+                    return PSR_ERR_INVALID_ARG;
+                }
+                cmax = std::max(cmax, c);
+            }
+            std::vector<char> has((size_t)cmax + 1, 0), used((size_t)cmax + 1, 0);
+            for (int32_t c : h_cls) used[(size_t)c] = 1;
+            for (int32_t v : h_init) has[(size_t)h_cls[(size_t)v]] = 1;
+            for (int32_t c = 0; c <= cmax; ++c)
+                if (used[(size_t)c] && !has[(size_t)c]) {
+                    set_error(nullptr, "patch class " + std::to_string(c) + " has no k-means seed");
+                    return PSR_ERR_INVALID_ARG;
+                }
+        }
         psr_opts o;
         if (opts) o = *opts; else psr_default_opts(&o);
         AssignMode mode;
         mode.km_m = m_p;
         mode.km_init = &h_init;
         mode.km_iter = max_iter;
+        mode.km_cls = patch_class ? &h_cls : nullptr;
         return setup_impl(A, patches, &o, (cudaStream_t)stream, out, mode);
     } catch (const std::bad_alloc&) {
         set_error(nullptr, "host allocation failed");

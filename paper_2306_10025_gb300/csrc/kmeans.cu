@@ -15,6 +15,7 @@
 #include "dense.cuh"
 
 #include <algorithm>
+#include <map>
 #include <vector>
 
 namespace psr {
@@ -22,24 +23,31 @@ namespace psr {
 // One warp per patch: entrywise l1 distance to every mean (lanes over the
 // p^2 entries, warp sum), strict minimum (the lowest j wins ties); counts the
 // patches whose assignment changed.
+// pcls / mcls (both null, or both set): class of every patch and of every
+// mean; a patch is assigned only among the means of its class (the boundary
+// partition of section 3.2).
 __global__ void k_kmeans_assign(const double* __restrict__ A, int count, int pp, const double* __restrict__ B,
-                                int m, int32_t* __restrict__ phi, int32_t* __restrict__ changes) {
+                                int m, int32_t* __restrict__ phi, int32_t* __restrict__ changes,
+                                const int32_t* __restrict__ pcls, const int32_t* __restrict__ mcls) {
     const int lane = threadIdx.x & 31;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= count) return;                                   // warp-uniform
     const double* a = A + (int64_t)i * pp;
+    const int ci = pcls ? pcls[i] : 0;
     double best = 0.0;
-    int arg = 0;
+    int arg = -1;
     for (int j = 0; j < m; ++j) {
+        if (pcls && mcls[j] != ci) continue;                  // warp-uniform
         const double* b = B + (int64_t)j * pp;
         double s = 0.0;
         for (int e = lane; e < pp; e += 32) s += fabs(a[e] - b[e]);
         s = warp_sum(s);
-        if (j == 0 || s < best) {
+        if (arg < 0 || s < best) {
             best = s;
             arg = j;
         }
     }
+    if (arg < 0) arg = 0;                                     // every class has a mean (checked on the host)
     if (lane == 0 && phi[i] != arg) {
         phi[i] = arg;
         atomicAdd(changes, 1);
@@ -90,21 +98,26 @@ __global__ void __launch_bounds__(128) k_kmeans_assign_spectral(const double* __
                                                                  const double* __restrict__ B,
                                                                  const double* __restrict__ Bi, int m,
                                                                  int32_t* __restrict__ phi,
-                                                                 int32_t* __restrict__ changes) {
+                                                                 int32_t* __restrict__ changes,
+                                                                 const int32_t* __restrict__ pcls,
+                                                                 const int32_t* __restrict__ mcls) {
     extern __shared__ double kscratch[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     const int pp = p * p;
     double* G = kscratch + (size_t)wid * p * (p + 1);
     for (int i = blockIdx.x * wpb + wid; i < count; i += gridDim.x * wpb) {
+        const int ci = pcls ? pcls[i] : 0;
         double best = 0.0;
-        int arg = 0;
+        int arg = -1;
         for (int j = 0; j < m; ++j) {
+            if (pcls && mcls[j] != ci) continue;              // warp-uniform
             const double sig = spectral_dist_warp(A + (int64_t)i * pp, B + (int64_t)j * pp, Bi + (int64_t)j * pp, p, G);
-            if (j == 0 || sig < best) {
+            if (arg < 0 || sig < best) {
                 best = sig;
                 arg = j;
             }
         }
+        if (arg < 0) arg = 0;                                 // every class has a mean (checked on the host)
         if (lane == 0 && phi[i] != arg) {
             phi[i] = arg;
             atomicAdd(changes, 1);
@@ -178,7 +191,29 @@ __global__ void k_kmeans_gather(const double* __restrict__ src, const int32_t* _
 // order on the device, the lowest member on ties chosen on the host).  The
 // inverses of all patches are formed once; the database keeps the
 // representatives' patches and inverses.
-static int run_kmeans_varmin(psr_ctx* ctx, cudaStream_t s, int m, const std::vector<int32_t>& init, int max_iter) {
+// Device copies of the class of every patch and of every mean (the class of
+// its seed) for the partitioned assignment; nothing when cls is null.
+struct ClassFilter {
+    int32_t* pcls = nullptr;
+    int32_t* mcls = nullptr;
+    ~ClassFilter() {
+        dev_free(pcls);
+        dev_free(mcls);
+    }
+    int upload(psr_ctx* ctx, const std::vector<int32_t>* cls, const std::vector<int32_t>& init, cudaStream_t s) {
+        if (!cls) return PSR_OK;
+        std::vector<int32_t> hm(init.size());
+        for (size_t j = 0; j < init.size(); ++j) hm[j] = (*cls)[(size_t)init[j]];
+        PSR_CUDA(ctx, dev_alloc(&pcls, sizeof(int32_t) * std::max<size_t>(cls->size(), 1)));
+        PSR_CUDA(ctx, dev_alloc(&mcls, sizeof(int32_t) * std::max<size_t>(hm.size(), 1)));
+        PSR_CUDA(ctx, cudaMemcpyAsync(pcls, cls->data(), sizeof(int32_t) * cls->size(), cudaMemcpyHostToDevice, s));
+        PSR_CUDA(ctx, cudaMemcpyAsync(mcls, hm.data(), sizeof(int32_t) * hm.size(), cudaMemcpyHostToDevice, s));
+        return PSR_OK;
+    }
+};
+
+static int run_kmeans_varmin(psr_ctx* ctx, cudaStream_t s, int m, const std::vector<int32_t>& init, int max_iter,
+                             const std::vector<int32_t>* cls) {
     Group& G = ctx->groups[0];
     const int p = G.p, pp = p * p, count = G.count;
     if (p > 32) {
@@ -186,6 +221,8 @@ static int run_kmeans_varmin(psr_ctx* ctx, cudaStream_t s, int m, const std::vec
         return PSR_ERR_INVALID_ARG;
     }
     const double* Ag = ctx->A_ext + G.mat_off;
+    ClassFilter cf;
+    if (int rcf = cf.upload(ctx, cls, init, s)) return rcf;
     double *Ainv = nullptr, *B = nullptr, *Bcur = nullptr, *V = nullptr;
     int32_t *sing_all = nullptr, *phi = nullptr, *changes = nullptr, *moff = nullptr, *mlist = nullptr,
             *d_reps = nullptr;
@@ -215,7 +252,7 @@ static int run_kmeans_varmin(psr_ctx* ctx, cudaStream_t s, int m, const std::vec
         count_launch(); k_kmeans_gather<<<gb, 256, 0, s>>>(Ainv, d_reps, m, pp, Bcur);
         PSR_CUDA(ctx, cudaMemsetAsync(changes, 0, sizeof(int32_t), s));
         count_launch();
-        k_kmeans_assign_spectral<<<kb, 128, scratch, s>>>(Ag, count, p, B, Bcur, m, phi, changes);
+        k_kmeans_assign_spectral<<<kb, 128, scratch, s>>>(Ag, count, p, B, Bcur, m, phi, changes, cf.pcls, cf.mcls);
         int32_t h_changes = 0;
         PSR_CUDA(ctx, cudaMemcpyAsync(&h_changes, changes, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         PSR_CUDA(ctx, cudaMemcpyAsync(hphi.data(), phi, sizeof(int32_t) * (size_t)count, cudaMemcpyDeviceToHost, s));
@@ -277,8 +314,9 @@ static int run_kmeans_varmin(psr_ctx* ctx, cudaStream_t s, int m, const std::vec
     return PSR_OK;
 }
 
-int run_kmeans(psr_ctx* ctx, cudaStream_t s, int m, const std::vector<int32_t>& init, int max_iter) {
-    if (ctx->opts.criterion == PSR_CRITERION_VARMIN) return run_kmeans_varmin(ctx, s, m, init, max_iter);
+int run_kmeans(psr_ctx* ctx, cudaStream_t s, int m, const std::vector<int32_t>& init, int max_iter,
+               const std::vector<int32_t>* cls) {
+    if (ctx->opts.criterion == PSR_CRITERION_VARMIN) return run_kmeans_varmin(ctx, s, m, init, max_iter, cls);
     Group& G = ctx->groups[0];
     const int p = G.p, pp = p * p, count = G.count;
     const bool spectral = ctx->opts.criterion == PSR_CRITERION_SPECTRAL;
@@ -287,6 +325,8 @@ int run_kmeans(psr_ctx* ctx, cudaStream_t s, int m, const std::vector<int32_t>& 
         return PSR_ERR_INVALID_ARG;
     }
     const double* Ag = ctx->A_ext + G.mat_off;
+    ClassFilter cf;
+    if (int rcf = cf.upload(ctx, cls, init, s)) return rcf;
     double* B = nullptr;
     int32_t *phi = nullptr, *d_init = nullptr, *changes = nullptr, *moff = nullptr, *mlist = nullptr;
     PSR_CUDA(ctx, psr::dev_alloc(&B, sizeof(double) * (size_t)m * pp));
@@ -319,10 +359,10 @@ int run_kmeans(psr_ctx* ctx, cudaStream_t s, int m, const std::vector<int32_t>& 
             count_launch();
             const int kb = std::max(1, std::min((count + 3) / 4, 152 * 16));
             k_kmeans_assign_spectral<<<kb, 128, sizeof(double) * 4 * p * (p + 1), s>>>(Ag, count, p, B, Bcur, m,
-                                                                                       phi, changes);
+                                                                                       phi, changes, cf.pcls, cf.mcls);
         } else {
             count_launch();
-            k_kmeans_assign<<<(count + 7) / 8, 256, 0, s>>>(Ag, count, pp, B, m, phi, changes);
+            k_kmeans_assign<<<(count + 7) / 8, 256, 0, s>>>(Ag, count, pp, B, m, phi, changes, cf.pcls, cf.mcls);
         }
         int32_t h_changes = 0;
         PSR_CUDA(ctx, cudaMemcpyAsync(&h_changes, changes, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -383,4 +423,104 @@ int run_kmeans(psr_ctx* ctx, cudaStream_t s, int m, const std::vector<int32_t>& 
     return PSR_OK;
 }
 
+// Boundary partition (section 3.2): bit a of mask[k] is set when row a of the
+// patch matrix A_k has exactly one nonzero entry (a boundary condition);
+// one warp per patch, p <= 64.
+__global__ void k_bc_mask(const double* __restrict__ Aext, const int64_t* __restrict__ mat_off,
+                          const int32_t* __restrict__ offsets, int np, int pu,
+                          unsigned long long* __restrict__ mask) {
+    const int lane = threadIdx.x & 31;
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (k >= np) return;                                      // warp-uniform
+    const int p = pu > 0 ? pu : offsets[k + 1] - offsets[k];
+    const double* a = Aext + (pu > 0 ? (int64_t)k * p * p : mat_off[k]);
+    unsigned lo = 0u, hi = 0u;
+    for (int r = lane; r < p; r += 32) {
+        int nz = 0;
+        for (int c = 0; c < p; ++c) nz += a[(int64_t)r * p + c] != 0.0;
+        if (nz == 1) {
+            if (r < 32) lo |= 1u << r;
+            else hi |= 1u << (r - 32);
+        }
+    }
+    lo = __reduce_or_sync(0xffffffffu, lo);
+    hi = __reduce_or_sync(0xffffffffu, hi);
+    if (lane == 0) mask[k] = ((unsigned long long)hi << 32) | lo;
+}
+
 }  // namespace psr
+
+extern "C" int psr_boundary_classes(const psr_csr* A, const psr_patches* P, int32_t* patch_class,
+                                    int32_t* n_classes, void* stream) {
+    using namespace psr;
+    if (!A || !P || !patch_class || !n_classes || A->n <= 0 || P->n_patches <= 0 || !P->dofs ||
+        (P->uniform_size <= 0 && !P->offsets) || P->uniform_size > 64) {
+        set_error(nullptr, "psr_boundary_classes: invalid argument (patches of at most 64 DOFs)");
+        return PSR_ERR_INVALID_ARG;
+    }
+    *n_classes = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int np = P->n_patches;
+    std::vector<int32_t> ho((size_t)np + 1);
+    std::vector<int64_t> hm((size_t)np + 1, 0);
+    if (P->uniform_size > 0) {
+        for (int k = 0; k <= np; ++k) ho[(size_t)k] = k * P->uniform_size;
+    } else {
+        PSR_CUDA(nullptr, cudaMemcpyAsync(ho.data(), P->offsets, sizeof(int32_t) * (size_t)(np + 1),
+                                          cudaMemcpyDeviceToHost, s));
+        PSR_CUDA(nullptr, cudaStreamSynchronize(s));
+    }
+    for (int k = 0; k < np; ++k) {
+        const int64_t pk = ho[(size_t)k + 1] - ho[(size_t)k];
+        if (pk < 1 || pk > 64) {
+            set_error(nullptr, "psr_boundary_classes: patch sizes must lie in 1..64");
+            return PSR_ERR_INVALID_ARG;
+        }
+        hm[(size_t)k + 1] = hm[(size_t)k] + pk * pk;
+    }
+    double* Aext = nullptr;
+    int64_t* mo = nullptr;
+    unsigned long long* mask = nullptr;
+    int rc = PSR_OK;
+    if (dev_alloc(&Aext, sizeof(double) * (size_t)std::max<int64_t>(hm[(size_t)np], 1)) != cudaSuccess ||
+        dev_alloc(&mo, sizeof(int64_t) * (size_t)(np + 1)) != cudaSuccess ||
+        dev_alloc(&mask, sizeof(unsigned long long) * (size_t)np) != cudaSuccess) {
+        cudaGetLastError();
+        set_error(nullptr, "psr_boundary_classes: out of device memory");
+        rc = PSR_ERR_OOM;
+    }
+    // the patch matrices (validates the CSR and the map)
+    if (rc == PSR_OK) rc = psr_extract(A, P, Aext, nullptr, nullptr, stream);
+    std::vector<unsigned long long> hmask((size_t)np);
+    if (rc == PSR_OK) {
+        cudaError_t e = cudaMemcpyAsync(mo, hm.data(), sizeof(int64_t) * (size_t)(np + 1), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) {
+            count_launch();
+            k_bc_mask<<<(np + 7) / 8, 256, 0, s>>>(Aext, mo, P->uniform_size > 0 ? nullptr : P->offsets, np,
+                                                   P->uniform_size, mask);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(hmask.data(), mask, sizeof(unsigned long long) * (size_t)np, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_fail(nullptr, e, "psr_boundary_classes");
+    }
+    if (rc == PSR_OK) {
+        // classes numbered in the order of their first patch
+        std::map<unsigned long long, int32_t> ids;
+        std::vector<int32_t> hc((size_t)np);
+        for (int k = 0; k < np; ++k) {
+            auto it = ids.emplace(hmask[(size_t)k], (int32_t)ids.size()).first;
+            hc[(size_t)k] = it->second;
+        }
+        cudaError_t e = cudaMemcpyAsync(patch_class, hc.data(), sizeof(int32_t) * (size_t)np, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_fail(nullptr, e, "psr_boundary_classes");
+        else *n_classes = (int32_t)ids.size();
+    }
+    cudaStreamSynchronize(s);
+    dev_free(Aext);
+    dev_free(mo);
+    dev_free(mask);
+    return rc;
+}

@@ -248,7 +248,9 @@ int launch_sweep_tc(const int32_t* tiles, int ntiles, int p, const __nv_bfloat16
                     int32_t* err, cudaStream_t s);
 
 // kmeans.cu
-int run_kmeans(psr_ctx* ctx, cudaStream_t s, int m, const std::vector<int32_t>& init, int max_iter);
+// cls: class of every patch (boundary partition) or null
+int run_kmeans(psr_ctx* ctx, cudaStream_t s, int m, const std::vector<int32_t>& init, int max_iter,
+               const std::vector<int32_t>* cls);
 
 // krylov.cu
 int krylov_alloc(psr_ctx* ctx);

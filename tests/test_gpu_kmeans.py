@@ -24,11 +24,11 @@ def dev(a, dt):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
 
 
-def kmeans_ctx(lib, pr, init, max_iter=100, criterion="l1", **kw):
+def kmeans_ctx(lib, pr, init, max_iter=100, criterion="l1", patch_class=None, **kw):
     rp, ci, va = dev(pr.rowptr, torch.int32), dev(pr.colidx, torch.int32), dev(pr.vals, torch.float64)
     return lib.psr_setup_kmeans(rp, ci, va, dev(pr.patch_dofs, torch.int32), pr.uniform_size,
                                 dev(np.asarray(init), torch.int32), max_iter=max_iter,
-                                opts=lib.make_opts(criterion=criterion, **kw))
+                                opts=lib.make_opts(criterion=criterion, **kw), patch_class=patch_class)
 
 
 def seeds(n_p, m, seed):
@@ -183,3 +183,55 @@ def test_kmeans_varmin_bit_exact(lib, case):
     with pytest.raises(lib.PsrError):                      # Alg. 1 has no variance-minimising form
         lib.psr_setup(rp, ci, va, dev(pr.patch_dofs, torch.int32), uniform_size=pr.uniform_size,
                       opts=lib.make_opts(tol=0.1, criterion="varmin"))
+
+
+@pytest.mark.parametrize("case,k", [("poisson", 9), ("diff3d", 27), ("stokes", 9)])
+def test_boundary_classes_equal_oracle(lib, case, k):
+    """The boundary partition (section 3.2): rows of a patch with one nonzero
+    entry; 9 classes on a square, 27 on a cube; equal to the oracle's."""
+    pr = {"poisson": lambda: P.poisson2d_q2(10), "diff3d": lambda: P.diffusion3d_q2(4, seed=2),
+          "stokes": lambda: P.stokes2d_q2q1(8)}[case]()
+    rp, ci, va = dev(pr.rowptr, torch.int32), dev(pr.colidx, torch.int32), dev(pr.vals, torch.float64)
+    cls, kg = lib.psr_boundary_classes(rp, ci, va, dev(pr.patch_dofs, torch.int32), uniform_size=pr.uniform_size)
+    ref, kr = O.boundary_classes(O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d()))
+    assert kg == kr == k and np.array_equal(cls.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("criterion", ["l1", "spectral"])
+@pytest.mark.parametrize("partition", ["boundary", "mod3"])
+def test_partitioned_kmeans_bit_exact(lib, criterion, partition):
+    """Each partition clustered on its own: the assignment and sweep count
+    equal the oracle's, and no patch leaves its class.  The boundary
+    partition takes the proportional split (40 clusters over 27 classes);
+    the arbitrary mod-3 partition moves 45 patches away from the
+    unpartitioned result, so the class filter is exercised."""
+    pr = P.diffusion3d_q2(4, sigma=0.5, corr_len=3.0, seed=4)
+    A = O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d())
+    if partition == "boundary":
+        cls, k = O.boundary_classes(A)
+        split = O.proportional_split(cls, 40)
+        g = np.random.default_rng(3)
+        init = np.concatenate([g.choice(np.flatnonzero(cls == c), split[c], replace=False)
+                               for c in range(k)]).astype(np.int32)
+        rp, ci, va = dev(pr.rowptr, torch.int32), dev(pr.colidx, torch.int32), dev(pr.vals, torch.float64)
+        cls_d, _ = lib.psr_boundary_classes(rp, ci, va, dev(pr.patch_dofs, torch.int32),
+                                            uniform_size=pr.uniform_size)
+    else:
+        cls = (np.arange(pr.n_patches) % 3).astype(np.int32)
+        init = np.random.default_rng(7).choice(pr.n_patches, 9, replace=False).astype(np.int32)
+        cls_d = dev(cls, torch.int32)
+    ref = (O.kmeans_l1 if criterion == "l1" else O.kmeans_spectral)(A, init, classes=cls)
+    assert ref["near_ties"] == []
+    ctx = kmeans_ctx(lib, pr, init, criterion=criterion, patch_class=cls_d, weighting=pr.weighting,
+                     krylov=pr.krylov)
+    phi = ctx.assignment()[0].cpu().numpy()
+    assert np.array_equal(phi, ref["phi"]) and ctx.stats()["rounds"] == ref["sweeps"]
+    assert np.array_equal(cls[init][phi], cls)
+    ctx.destroy()
+
+
+def test_partition_needs_a_seed_per_class(lib):
+    pr = P.poisson2d_q2(8)
+    cls = dev((np.arange(pr.n_patches) % 2).astype(np.int32), torch.int32)
+    with pytest.raises(lib.PsrError):                      # every seed in class 0
+        kmeans_ctx(lib, pr, np.array([0, 2, 4], dtype=np.int32), patch_class=cls)
