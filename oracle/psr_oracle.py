@@ -845,3 +845,85 @@ def proportional_split(classes, m_total):
     sizes = np.bincount(np.asarray(classes))
     n = sizes.sum()
     return np.array([min(int(c), max(1, int(np.floor(m_total * c / n + 0.5)))) for c in sizes], dtype=np.int64)
+
+
+# ---------------------------------------------------------------------------
+# Faster / less order-sensitive forms of Alg. 1 (section 3.1, after Alg. 1)
+# ---------------------------------------------------------------------------
+
+def alg1_closest_match(A, tol, near_tie_rel=1e-9):
+    """Alg. 1 in which A_i joins the closest of the entries that pass the
+    test (d < tol) instead of the first one; lowest j on ties.  An entry is
+    still created exactly when no entry passes, so the representatives are
+    those of alg1; only phi can differ.  near_ties: patches whose two best
+    passing distances lie within near_tie_rel of each other."""
+    A = np.asarray(A, dtype=np.float64)
+    npch, p, _ = A.shape
+    phi = np.full(npch, -1, dtype=np.int64)
+    reps: list[int] = []
+    Binv = np.zeros((0, p, p))
+    near = []
+    for i in range(npch):
+        j_hit = -1
+        if reps:
+            d = criterion(A[i][None], A[reps], Binv)
+            ok = np.flatnonzero(d < tol)
+            if ok.size:
+                j_hit = int(ok[np.argmin(d[ok])])
+                ds = np.sort(d[ok])
+                if ds.size > 1 and ds[1] - ds[0] <= near_tie_rel * max(ds[1], 1e-300):
+                    near.append(i)
+        if j_hit >= 0:
+            phi[i] = j_hit
+        else:
+            inv, _ = lu_inverse(A[i][None])
+            reps.append(i)
+            Binv = np.concatenate([Binv, inv], axis=0)
+            phi[i] = len(reps) - 1
+    return {"phi": phi, "reps": np.array(reps, dtype=np.int64), "Binv": Binv, "near_ties": near}
+
+
+def alg1_sorted(A, tol):
+    """Alg. 1 with the entries kept sorted by ||B_j||_2 (the O(n_p log m_p)
+    search the paper suggests).  Since d = ||(B_j - A_i) B_j^{-1}||_2 >=
+    ||B_j - A_i||_2 / ||B_j||_2 >= | ||B_j||_2 - ||A_i||_2 | / ||B_j||_2,
+    an entry can pass only if ||A_i||_2 / (1 + tol) < ||B_j||_2 <
+    ||A_i||_2 / (1 - tol) (tol < 1): a binary search finds that window and
+    only its entries are tested, in creation order.  The result equals
+    alg1's; evals counts the tests made."""
+    A = np.asarray(A, dtype=np.float64)
+    npch, p, _ = A.shape
+    phi = np.full(npch, -1, dtype=np.int64)
+    reps: list[int] = []
+    Binv = np.zeros((0, p, p))
+    norms = np.array([np.linalg.svd(A[k], compute_uv=False)[0] for k in range(npch)])
+    keys: list[float] = []          # ||B_j||_2, sorted
+    order: list[int] = []           # entry j of each sorted key
+    evals = 0
+    for i in range(npch):
+        a = norms[i]
+        lo = a / (1.0 + tol)
+        hi = a / (1.0 - tol) if tol < 1.0 else np.inf
+        # widened by the rounding of the norms (the window must not lose a match)
+        s0 = np.searchsorted(keys, lo * (1 - 1e-12), side="left")
+        s1 = np.searchsorted(keys, hi * (1 + 1e-12), side="right")
+        cand = sorted(order[s0:s1])
+        j_hit = -1
+        if cand:
+            d = criterion(A[i][None], A[[reps[j] for j in cand]], Binv[cand])
+            for c, dj in zip(cand, d):
+                evals += 1
+                if dj < tol:
+                    j_hit = c
+                    break
+        if j_hit >= 0:
+            phi[i] = j_hit
+        else:
+            inv, _ = lu_inverse(A[i][None])
+            reps.append(i)
+            Binv = np.concatenate([Binv, inv], axis=0)
+            phi[i] = len(reps) - 1
+            pos = int(np.searchsorted(keys, norms[i], side="right"))
+            keys.insert(pos, float(norms[i]))
+            order.insert(pos, len(reps) - 1)
+    return {"phi": phi, "reps": np.array(reps, dtype=np.int64), "Binv": Binv, "evals": evals}
