@@ -53,3 +53,11 @@ def test_compute_without_gpu_fails_loudly():
     assert b"CUDA" in lib.psr_last_error(None)
     # the allocator's release has nothing to return and reports the missing device
     assert lib.psr_release_cached_memory() == -5
+    # argument checks come before any device work
+    cnt = C.c_int32(7)
+    assert lib.psr_detect_patches(None, 9, None, 0, C.byref(cnt), None) == -1
+    assert lib.psr_detect_patches(C.byref(A), 0, None, 0, C.byref(cnt), None) == -1
+    assert lib.psr_detect_patches(C.byref(A), 2000, None, 0, C.byref(cnt), None) == -1
+    assert lib.psr_boundary_classes(None, C.byref(P_), None, C.byref(cnt), None) == -1
+    big = L.binding.psr_patches(1, 65, None, 8)               # more than 64 DOFs per patch
+    assert lib.psr_boundary_classes(C.byref(A), C.byref(big), C.c_void_p(8), C.byref(cnt), None) == -1
