@@ -11,9 +11,10 @@ Vanka cell patches (input generator; none of the method's arithmetic).
 * Global numbering: u_x of the free Q2 nodes (lexicographic, x fastest), then
   u_y, u_z, then the (N+1)^3 pressure vertices.  Patch local order: free nodes
   of the cell in tensor order for u_x, u_y, u_z, then the 8 vertices.
-* Assembly runs in slabs of cell layers (rows of one slab of node layers are
-  summed from the cells that touch them, in increasing cell order) so the
-  48^3 case (about 4e8 nonzeros) fits in host memory.
+* Element blocks (velocity stiffness, divergence) are formed per cell with
+  batched products; the CSR assembly runs in native code (_assemble.c), row
+  by row, each entry the sum of its cell contributions in increasing cell
+  order, so the 48^3 case (about 4e8 stored entries) takes seconds.
 """
 from __future__ import annotations
 
@@ -53,13 +54,20 @@ def _cell_mats(Xc, ref):
     # grad_x phi_a = J^{-T} grad_xi phi_a : G[c,q,a,i] = sum_j Jinv[c,q,j,i] dphi[j,a,q]
     G = np.einsum("cqji,jaq->cqai", Jinv, dphi)
     wd = w[None, :] * np.abs(det)
-    K = np.einsum("cq,cqai,cqbi->cab", wd, G, G)
+    nc, nq = wd.shape
+    # K[c] = sum_{q,i} wd G G^T as one product per cell: H[c] = (sqrt(wd) G) laid
+    # out (27 basis, nq * 3) so K[c] = H[c] H[c]^T
+    H = np.ascontiguousarray(np.transpose(G * np.sqrt(wd)[:, :, None, None], (0, 2, 1, 3))).reshape(nc, 27, nq * 3)
+    K = np.matmul(H, np.transpose(H, (0, 2, 1)))
     K = 0.5 * (K + np.transpose(K, (0, 2, 1)))
-    B = -np.einsum("cq,pq,cqak->ckpa", wd, psi, G)
-    return K, B
+    # B[c, k, p, a] = -sum_q wd psi_p (G)_{a,k}: (8 x nq) @ (nq x 27*3) per cell
+    Pw = psi[None, :, :] * wd[:, None, :]                       # (nc, 8, nq)
+    B = -np.matmul(Pw, G.reshape(nc, nq, 27 * 3)).reshape(nc, 8, 27, 3)
+    return K, np.ascontiguousarray(np.transpose(B, (0, 3, 1, 2)))
 
 
-def stokes3d_q2q1(N: int = 48, jitter: float = 0.2, seed: int = 0, chunk_layers: int = 4) -> Problem:
+def stokes3d_q2q1(N: int = 48, jitter: float = 0.2, seed: int = 0, chunk_cells: int = 8192) -> Problem:
+    from . import _native
     ref = _ref3d()
     V = _jittered_vertices(N, jitter, seed)
     m = 2 * N + 1                                   # Q2 nodes per direction
@@ -88,7 +96,7 @@ def stokes3d_q2q1(N: int = 48, jitter: float = 0.2, seed: int = 0, chunk_layers:
             for a in range(2):
                 verts[:, a + 2 * b + 4 * c] = (cx + a) + (N + 1) * ((cy + b) + (N + 1) * (cz + c))
     vel = [np.where(fnodes >= 0, k * nfree + fnodes, -1) for k in range(3)]
-    edofs = np.concatenate(vel + [3 * nfree + verts], axis=1)       # (nc, 89), -1 = eliminated
+    edofs = np.ascontiguousarray(np.concatenate(vel + [3 * nfree + verts], axis=1))  # (nc, 89), -1 = eliminated
     pin = 3 * nfree                                                   # pressure vertex 0
     # patches: the cell's kept DOFs in element order
     keep = edofs >= 0
@@ -96,71 +104,28 @@ def stokes3d_q2q1(N: int = 48, jitter: float = 0.2, seed: int = 0, chunk_layers:
     offsets = np.zeros(nc + 1, dtype=np.int64)
     np.cumsum(sizes, out=offsets[1:])
     flat = edofs[keep]
-    # --- chunked assembly by slabs of cell layers
-    rows_out, cols_out, vals_out = [], [], []
-    layer_rows = []
-    for z0 in range(0, N, chunk_layers):
-        z1 = min(N, z0 + chunk_layers)
-        # rows owned by this slab: velocity nodes with node-z in [2 z0, 2 z1) (last slab: up to m)
-        # pressure vertices with z in [z0, z1) (last: up to N+1)
-        nz_lo, nz_hi = 2 * z0, (2 * z1 if z1 < N else m)
-        vz_lo, vz_hi = z0, (z1 if z1 < N else N + 1)
-        cells = np.flatnonzero((cz >= max(z0 - 1, 0)) & (cz <= min(z1, N - 1)))
-        Xc = V[verts[cells]]
-        K, B = _cell_mats(Xc, ref)
-        ncs = cells.size
-        E = np.zeros((ncs, 89, 89))
-        for k in range(3):
-            E[:, 27 * k:27 * k + 27, 27 * k:27 * k + 27] = K
-            E[:, 81:89, 27 * k:27 * k + 27] = B[:, k]
-            E[:, 27 * k:27 * k + 27, 81:89] = np.transpose(B[:, k], (0, 2, 1))
-        ed = edofs[cells]
-        r = np.repeat(ed, 89, axis=1).reshape(-1)
-        c = np.tile(ed, (1, 89)).reshape(-1)
-        v = E.reshape(-1)
-        del E
-        ok = (r >= 0) & (c >= 0) & (r != pin) & (c != pin)
-        # row ownership
-        rv = np.where(r < 3 * nfree, r % nfree, 0)
-        rnz = 1 + rv // (nf * nf)                          # node z of a free node
-        own_v = (r < 3 * nfree) & (rnz >= nz_lo) & (rnz < nz_hi)
-        rp = r - 3 * nfree
-        own_p = (r >= 3 * nfree) & ((rp // ((N + 1) ** 2)) >= vz_lo) & ((rp // ((N + 1) ** 2)) < vz_hi)
-        sel = ok & (own_v | own_p)
-        r, c, v = r[sel], c[sel], v[sel]
-        key = r * n + c
-        order = np.argsort(key, kind="stable")      # cell order kept inside a key
-        key = key[order]
-        v = v[order]
-        newg = np.empty(key.size, dtype=bool)
-        if key.size:
-            newg[0] = True
-            np.not_equal(key[1:], key[:-1], out=newg[1:])
-        starts = np.flatnonzero(newg)
-        grp = np.cumsum(newg) - 1
-        rank = np.arange(key.size) - starts[grp]
-        sums = np.zeros(starts.size)
-        for rr in range(int(rank.max()) + 1 if key.size else 0):
-            mm = rank == rr
-            sums[grp[mm]] += v[mm]
-        uk = key[starts]
-        rows_out.append(uk // n)
-        cols_out.append(uk % n)
-        vals_out.append(sums)
-        del key, v, r, c, order, newg, grp, rank
-    rows = np.concatenate(rows_out + [np.array([pin])])
-    cols = np.concatenate(cols_out + [np.array([pin])])
-    vals = np.concatenate(vals_out + [np.array([1.0])])
-    o = np.lexsort((cols, rows))
-    rows, cols, vals = rows[o], cols[o], vals[o]
-    counts = np.bincount(rows, minlength=n)
+    # element blocks of every cell (in chunks), then CSR assembly in native
+    # code: row by row, cell contributions summed in increasing cell order
+    K = np.empty((nc, 27, 27))
+    B = np.empty((nc, 3, 8, 27))
+    for c0 in range(0, nc, chunk_cells):
+        c1 = min(nc, c0 + chunk_cells)
+        K[c0:c1], B[c0:c1] = _cell_mats(V[verts[c0:c1]], ref)
+    lib = _native.lib()
     rowptr = np.zeros(n + 1, dtype=np.int64)
-    np.cumsum(counts, out=rowptr[1:])
+    if lib.stokes3d_pattern_count(n, nc, edofs.ctypes.data, pin, rowptr.ctypes.data) != 0:
+        raise MemoryError("stokes3d assembly: out of host memory (pattern)")
     if rowptr[-1] >= 2 ** 31:
         raise ValueError("nnz exceeds int32")
+    cols = np.empty(int(rowptr[-1]), dtype=np.int32)
+    vals = np.empty(int(rowptr[-1]), dtype=np.float64)
+    if lib.stokes3d_fill(n, nc, edofs.ctypes.data, pin, rowptr.ctypes.data, K.ctypes.data, B.ctypes.data,
+                         cols.ctypes.data, vals.ctypes.data) != 0:
+        raise MemoryError("stokes3d assembly: out of host memory (values)")
+    del K, B
     rhs_mask = np.zeros(n, dtype=bool)
     rhs_mask[:3 * nfree] = True
-    return Problem(f"stokes3d_q2q1_N{N}", n, rowptr.astype(np.int32), cols.astype(np.int32), vals,
+    return Problem(f"stokes3d_q2q1_N{N}", n, rowptr.astype(np.int32), cols, vals,
                    offsets.astype(np.int32), flat.astype(np.int32), rhs_mask,
                    symmetric=True, krylov="fgmres", weighting="left",
                    meta={"N": N, "jitter": jitter, "seed": seed, "sizes": sorted(set(sizes.tolist()))})
