@@ -392,7 +392,10 @@ int psr_criterion(const double* A_i, int32_t batch, int32_t p, const double* A_c
  *   - batch > PSR_CRITERION_NOALLOC_MAX returns PSR_ERR_INVALID_ARG.
  *   - The first call on a device looks up the array's device address (a
  *     one-time set-up per device, done with that device current); make that
- *     first call before any stream capture on the device.
+ *     first call before any stream capture on the device.  The address is
+ *     kept for the life of the process: after a cudaDeviceReset of that
+ *     device it is stale, so a process that resets a device must not call
+ *     this entry point on it again.
  *   - All calls share the array (it keeps the last call's contents; the
  *     counter is cleared at the start of every call), so calls whose work
  *     overlaps on the GPU race: order them on one stream or synchronise.
