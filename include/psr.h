@@ -79,6 +79,17 @@ extern "C" {
 #define PSR_ORTHO_FP64   1         /* the fused launch in FP64 arithmetic                  */
 #define PSR_ORTHO_SPLIT  2         /* one launch per pass, FP64 arithmetic                 */
 
+#define PSR_FP64_PAIRS   0         /* FP64 inverses of full-storage groups kept as (hi, lo)
+                                      FP32 pairs (8 bytes, 48-bit significand, a power-of-two
+                                      scale per patch) and applied in compensated FP32 pair
+                                      arithmetic: the GPU's FP64 units are 1/64 of its FP32
+                                      rate and would bound the sweep instead of HBM          */
+#define PSR_FP64_NATIVE  1         /* FP64 inverses applied with FP64 fused multiply-adds      */
+
+#define PSR_MATCH_FIRST   0        /* Alg. 1 as printed: the first entry with d < tol          */
+#define PSR_MATCH_CLOSEST 1        /* section 3.1 variant: of the entries existing when the
+                                      patch is reached, the one with the least d (< tol)       */
+
 typedef struct psr_ctx psr_ctx;    /* opaque, library-owned */
 
 /* Assembled matrix A (section 2: A x = b), CSR, device pointers. */
@@ -115,11 +126,16 @@ typedef struct {
     int32_t use_mlp;      /* 1: verify MLP-predicted representatives first (needs psr_mlp_attach) */
     int32_t ortho;        /* PSR_ORTHO_* (FGMRES only)                            */
     int32_t criterion;    /* PSR_CRITERION_* of Alg. 1 (L1: psr_setup only)        */
+    int32_t fp64_arith;   /* PSR_FP64_* arithmetic of the FP64 full-storage sweep  */
+    int32_t match;        /* PSR_MATCH_* rule of Alg. 1 (spectral criterion)       */
+    uint64_t seed;        /* seed of the library's own random draws (MLP weights,
+                             training order of psr_mlp_train)                     */
 } psr_opts;
 
 /* Fill `o` with defaults: tol 0, FP64, SYM, CG, restart 30, rtol 1e-8,
  * maxit 10000, graphs on, AUTO sweep, autotune on, symmetrize on, no MLP,
- * AUTO orthogonalisation, spectral criterion. */
+ * AUTO orthogonalisation, spectral criterion, FP64 pairs, first match,
+ * seed 0. */
 void psr_default_opts(psr_opts* o);
 
 /* A rectangular CSR matrix (the interpolation P0 of Eq. 2), device pointers. */

@@ -27,6 +27,8 @@ KRYLOV = {"cg": 0, "fgmres": 1}
 SWEEP = {"auto": 0, "grouped": 1, "pergroup": 2, "tensor": 3}
 ORTHO = {"auto": 0, "fp64": 1, "split": 2}
 CRITERION = {"spectral": 0, "l1": 1, "varmin": 2}
+FP64_ARITH = {"pairs": 0, "native": 1}
+MATCH = {"first": 0, "closest": 1}
 
 EXPORTS = ["psr_default_opts", "psr_setup", "psr_apply", "psr_solve", "psr_get_history",
            "psr_get_assignment", "psr_get_stats", "psr_last_error", "psr_destroy", "psr_extract",
@@ -61,7 +63,8 @@ class psr_opts(C.Structure):
                 ("krylov", C.c_int32), ("restart", C.c_int32), ("rtol", C.c_double),
                 ("maxit", C.c_int32), ("use_graph", C.c_int32), ("sweep_kernel", C.c_int32),
                 ("autotune", C.c_int32), ("symmetrize", C.c_int32), ("use_mlp", C.c_int32),
-                ("ortho", C.c_int32), ("criterion", C.c_int32)]
+                ("ortho", C.c_int32), ("criterion", C.c_int32), ("fp64_arith", C.c_int32),
+                ("match", C.c_int32), ("seed", C.c_uint64)]
 
 
 class psr_csr_rect(C.Structure):
@@ -174,7 +177,8 @@ def _need(t, dtype, name):
 
 def make_opts(tol=0.0, store_prec="fp64", weighting="sym", krylov="cg", restart=30, rtol=1e-8,
               maxit=10000, use_graph=True, sweep_kernel="auto", autotune=True, symmetrize=True,
-              use_mlp=False, ortho="auto", criterion="spectral") -> psr_opts:
+              use_mlp=False, ortho="auto", criterion="spectral", fp64_arith="pairs", match="first",
+              seed=0) -> psr_opts:
     o = psr_opts()
     load().psr_default_opts(C.byref(o))
     o.tol = tol
@@ -191,6 +195,9 @@ def make_opts(tol=0.0, store_prec="fp64", weighting="sym", krylov="cg", restart=
     o.use_mlp = int(use_mlp)
     o.ortho = ORTHO[ortho]
     o.criterion = CRITERION[criterion]
+    o.fp64_arith = FP64_ARITH[fp64_arith]
+    o.match = MATCH[match]
+    o.seed = int(seed)
     return o
 
 

@@ -108,7 +108,9 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
     if (op.restart < 1 || op.restart > 32 || op.maxit < 1 || !(op.rtol > 0.0) || op.tol < 0.0 ||
         op.store_prec < 0 || op.store_prec > 2 || op.weighting < 0 || op.weighting > 1 || op.krylov < 0 || op.krylov > 1 ||
         op.sweep_kernel < PSR_SWEEP_AUTO || op.sweep_kernel > PSR_SWEEP_TENSOR || op.ortho < PSR_ORTHO_AUTO ||
-        op.ortho > PSR_ORTHO_SPLIT || op.criterion < PSR_CRITERION_SPECTRAL || op.criterion > PSR_CRITERION_VARMIN) {
+        op.ortho > PSR_ORTHO_SPLIT || op.criterion < PSR_CRITERION_SPECTRAL || op.criterion > PSR_CRITERION_VARMIN ||
+        op.fp64_arith < PSR_FP64_PAIRS || op.fp64_arith > PSR_FP64_NATIVE || op.match < PSR_MATCH_FIRST ||
+        op.match > PSR_MATCH_CLOSEST) {
         set_error(ctx, "invalid option value");
         destroy_ctx(ctx);
         return PSR_ERR_INVALID_ARG;
@@ -257,8 +259,6 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
             rc = run_alg1_l1(ctx, s);
             if (rc != PSR_OK) goto fail;
         } else {
-            for (auto& G : ctx->groups)
-                if (G.p > 32) { set_error(ctx, "the criterion kernel handles patches of at most 32 DOFs"); FAIL(PSR_ERR_INVALID_ARG); }
             rc = run_alg1(ctx, s, seed_A, m0, hints);
             if (rc != PSR_OK) goto fail;
         }
@@ -332,6 +332,9 @@ void psr_default_opts(psr_opts* o) {
     o->use_mlp = 0;
     o->ortho = PSR_ORTHO_AUTO;
     o->criterion = PSR_CRITERION_SPECTRAL;
+    o->fp64_arith = PSR_FP64_PAIRS;
+    o->match = PSR_MATCH_FIRST;
+    o->seed = 0;
 }
 
 int psr_setup(const psr_csr* A, const psr_patches* patches, const psr_opts* opts, void* stream, psr_ctx** out) {
@@ -610,12 +613,13 @@ int psr_batched_inverse(const double* A, int32_t batch, int32_t p, double* Ainv,
 
 int psr_criterion(const double* A_i, int32_t batch, int32_t p, const double* A_c, const double* Binv_c, double tol,
                   int32_t* accept, double* dval, void* stream) {
-    if (!A_i || !A_c || !Binv_c || !accept || batch < 0 || p < 1 || p > 32 || !(tol >= 0.0)) {
+    if (!A_i || !A_c || !Binv_c || !accept || batch < 0 || p < 1 || p > 128 || !(tol >= 0.0)) {
         set_error(nullptr, "invalid criterion arguments");
         return PSR_ERR_INVALID_ARG;
     }
     if (batch == 0) return PSR_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    if (p > 32) return launch_criterion_big(A_i, batch, p, A_c, Binv_c, tol, accept, dval, s);
     int32_t* work = nullptr;
     PSR_CUDA(nullptr, cudaMallocAsync((void**)&work, sizeof(int32_t) * ((size_t)batch + 1), s));
     int rc = launch_criterion_batch(A_i, batch, p, A_c, Binv_c, tol, accept, dval, work, s);

@@ -1087,6 +1087,16 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         Group& G = ctx->groups[g];
         const int p = G.p, count = G.count;
         const double* Ag = ctx->A_ext + G.mat_off;
+        if (p > 32) {
+            // block-per-candidate kernels (criterion_big.cu)
+            if (m0 > 0) { set_error(ctx, "a seed database needs patches of at most 32 DOFs"); rc = PSR_ERR_INVALID_ARG; break; }
+            int fs = -1;
+            rc = run_alg1_big(ctx, G, Ag, s, &total_evals, &total_exact, &total_screened, &fs);
+            if (rc != PSR_OK) break;
+            rounds_total += G.m;
+            if (fs >= 0 && first_singular < 0) first_singular = G.h_gidx[fs];
+            continue;
+        }
         int32_t* phi_l = nullptr;
         int32_t* rep_l = nullptr;
         int32_t* sing_all = nullptr;

@@ -1398,15 +1398,17 @@ static double sweep_bytes(const psr_ctx* ctx) {
 static double spmv_bytes(const psr_ctx* ctx) {
     return 12.0 * (double)ctx->nnz + 4.0 * (ctx->n + 1.0) + 16.0 * ctx->n;
 }
-// FP64 flops of the sweep: the patch products when the inverses are FP64,
+// FP64 flops of the sweep: the patch products when they run on FP64 units
+// (FP64 inverses, except streamed groups applied in FP32 pair arithmetic),
 // the weighted scatter-add of every patch DOF
 static double sweep_flops(const psr_ctx* ctx) {
     double sp = 0.0, sp2 = 0.0;
+    const bool fp64 = ctx->opts.store_prec == PSR_PREC_FP64;
     for (const Group& G : ctx->groups) {
         sp += (double)G.count * G.p;
-        sp2 += (double)G.count * G.p * G.p;
+        if (fp64 && !(G.stream && ctx->opts.fp64_arith == PSR_FP64_PAIRS)) sp2 += (double)G.count * G.p * G.p;
     }
-    return (ctx->opts.store_prec == PSR_PREC_FP64 ? 2.0 * sp2 : 0.0) + 2.0 * sp;
+    return 2.0 * sp2 + 2.0 * sp;
 }
 
 // While the stream is captured the record becomes an event-record node of

@@ -100,6 +100,9 @@ struct Group {
     int warps = 4;
     bool tc = false;               // BF16 entries applied on the tensor cores
     bool tpp = false;              // clustered p <= 32: one patch per thread
+    bool stream = false;           // every patch its own entry: column-major inverses streamed
+                                   // by k_sweep_stream (thread per row)
+    int32_t* bexp = nullptr;       // [m] power-of-two scale of each entry (FP64 pairs only)
     int32_t* sdofs_t = nullptr;    // [p * count] DOFs, local-DOF major (tpp kernel)
     int32_t* wtiles = nullptr;     // [nwt * 3] warp tiles (entry, first, count <= 32)
     int nwt = 0;
@@ -192,6 +195,11 @@ struct psr_ctx {
     int32_t* gcounter = nullptr;  // work counter for the persistent sweep
     int sweep_mode = PSR_SWEEP_PERGROUP;
     int grouped_blocks = 0;
+    // streaming sweep of the full-storage groups (one launch over all of them)
+    void* sdesc = nullptr;        // device StreamDesc per streamed group
+    int n_stream = 0;             // streamed groups
+    int stream_rb = 0;            // 32-row blocks over all streamed groups
+    int stream_blocks = 0;        // grid of k_sweep_stream (autotuned)
     // per-kernel timing of the solve (psr_set_kernel_timing)
     bool kt_on = false;
     std::vector<cudaEvent_t> kt_ev;       // two per mark
@@ -226,6 +234,12 @@ int launch_criterion_batch(const double* A_i, int32_t batch, int32_t p, const do
                            int32_t* work, cudaStream_t s);
 int launch_spectral_norm(const double* E, int32_t batch, int32_t p, double* sigma, cudaStream_t s);
 
+// criterion_big.cu (33 <= p <= 128: a block per candidate)
+int run_alg1_big(psr_ctx* ctx, Group& G, const double* Ag, cudaStream_t s, int64_t* evals, int64_t* exact,
+                 int64_t* screened, int* first_singular_local);
+int launch_criterion_big(const double* A_i, int32_t batch, int32_t p, const double* A_c, const double* Binv_c,
+                         double tol, int32_t* accept, double* dval, cudaStream_t s);
+
 // sweep.cu
 int build_sweep(psr_ctx* ctx, cudaStream_t s);
 int sweep_apply(psr_ctx* ctx, const double* r, double* z, cudaStream_t s);
@@ -235,6 +249,12 @@ int sweep_apply_ex(psr_ctx* ctx, const double* r, double* z, const int32_t* stop
                    bool z_zeroed = false);
 int build_grouped_tables(psr_ctx* ctx);
 void free_sweep(psr_ctx* ctx);
+
+// sweep_stream.cu (full-storage groups: column-major inverses, thread per row)
+int stream_convert(psr_ctx* ctx, Group& G, const double* db64, cudaStream_t s, int64_t* bytes);
+int stream_build_table(psr_ctx* ctx);
+int launch_sweep_stream(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s);
+void stream_free(psr_ctx* ctx);
 int coarse_apply(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s);
 int run_alg1_l1(psr_ctx* ctx, cudaStream_t s);
 void coarse_free(psr_ctx* ctx);

@@ -552,7 +552,15 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<std::vector<int32_t>>& gi
         double* db64 = reinterpret_cast<double*>(G.rinv);
         const int64_t ne = (int64_t)G.m * p * p;
         const bool in_place = (db64 == ctx->A_ext + G.mat_off);
-        if (prec == PSR_PREC_FP64) {
+        if (G.m == G.count) {
+            // every patch its own entry: column-major stream (sweep_stream.cu)
+            int64_t fb = 0;
+            int rc = stream_convert(ctx, G, db64, s, &fb);
+            if (rc != PSR_OK) return rc;
+            PSR_CUDA(ctx, cudaStreamSynchronize(s));
+            if (!in_place) psr::dev_free(db64);
+            factor_bytes += fb;
+        } else if (prec == PSR_PREC_FP64) {
             if (in_place) {
                 G.rinv = db64;              // full storage: inverses live where the patches were
             } else {                        // shrink the round buffer to m entries
@@ -631,9 +639,11 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<std::vector<int32_t>>& gi
             PSR_CUDA(ctx, cudaMemcpy(G.wtiles, wt.data(), sizeof(int32_t) * wt.size(), cudaMemcpyHostToDevice));
             G.tpp = true;
         }
-        int T = G.tc ? 128 : ((p <= 16) ? 64 : 32);
-        int rc = make_tiles(ctx, G, G.h_sorted_phi, T);
-        if (rc != PSR_OK) return rc;
+        if (!G.stream) {
+            int T = G.tc ? 128 : ((p <= 16) ? 64 : 32);
+            int rc = make_tiles(ctx, G, G.h_sorted_phi, T);
+            if (rc != PSR_OK) return rc;
+        }
         index_bytes += (int64_t)count * p * 4 + (int64_t)count * 4;
         entry_base += G.m;
     }
@@ -648,6 +658,8 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<std::vector<int32_t>>& gi
     for (const Group& G : ctx->groups) ctx->stats.tc_groups += G.tc ? 1 : 0;
     ctx->stats.m_p = ctx->m_p;
     int rc = build_grouped_tables(ctx);
+    if (rc != PSR_OK) return rc;
+    rc = stream_build_table(ctx);
     if (rc != PSR_OK) return rc;
     PSR_CUDA(ctx, psr::dev_alloc(&ctx->gcounter, sizeof(int32_t) * 2));
     PSR_CUDA(ctx, cudaMemset(ctx->gcounter, 0, sizeof(int32_t) * 2));
@@ -668,6 +680,7 @@ int build_grouped_tables(psr_ctx* ctx) {
     for (size_t g = 0; g < ctx->groups.size(); ++g) {
         Group& G = ctx->groups[g];
         gd[g] = GroupDesc{G.sdofs, G.rinv, G.p, 0};
+        if (G.stream) continue;             // streamed by k_sweep_stream
         std::vector<int32_t> ht((size_t)G.ntiles * 3);
         PSR_CUDA(ctx, cudaMemcpy(ht.data(), G.tiles, sizeof(int32_t) * ht.size(), cudaMemcpyDeviceToHost));
         for (int t = 0; t < G.ntiles; ++t) {
@@ -684,6 +697,27 @@ int build_grouped_tables(psr_ctx* ctx) {
     PSR_CUDA(ctx, cudaMemcpy(ctx->gtiles, gt.data(), sizeof(int32_t) * gt.size(), cudaMemcpyHostToDevice));
     PSR_CUDA(ctx, psr::dev_alloc(&ctx->gdesc, sizeof(GroupDesc) * std::max<size_t>(gd.size(), 1)));
     PSR_CUDA(ctx, cudaMemcpy(ctx->gdesc, gd.data(), sizeof(GroupDesc) * gd.size(), cudaMemcpyHostToDevice));
+    return PSR_OK;
+}
+
+// Grid of the streaming sweep (blocks of 8 warps): the candidates are timed
+// with the caller's apply timer and the fastest kept.
+template <class F>
+static int tune_stream_grid(psr_ctx* ctx, double* r, double* z, cudaStream_t s, cudaEvent_t* ev, int nt,
+                            F&& time_apply) {
+    (void)r; (void)z; (void)s; (void)ev; (void)nt;
+    if (ctx->n_stream == 0) return PSR_OK;
+    const int Bs[] = {152 * 4, 152 * 8, 152 * 16};
+    float best = 1e30f;
+    int bB = ctx->stream_blocks;
+    for (int B : Bs) {
+        ctx->stream_blocks = B;
+        float ms;
+        int rc = time_apply(&ms);
+        if (rc != PSR_OK) return rc;
+        if (ms < best) { best = ms; bB = B; }
+    }
+    ctx->stream_blocks = bB;
     return PSR_OK;
 }
 
@@ -733,8 +767,9 @@ int autotune_sweep(psr_ctx* ctx, cudaStream_t s) {
         float best = 1e30f;
         int bT = 32, bB = 152 * 2;
         for (int T : Ts) {
+            if (ctx->gntiles == 0) break;   // every group streamed
             for (auto& G : ctx->groups)
-                if ((rc = make_tiles(ctx, G, G.h_sorted_phi, T)) != PSR_OK) break;
+                if (!G.stream && (rc = make_tiles(ctx, G, G.h_sorted_phi, T)) != PSR_OK) break;
             if (rc != PSR_OK || (rc = build_grouped_tables(ctx)) != PSR_OK) break;
             for (int B : Bs) {
                 ctx->grouped_blocks = B;
@@ -744,19 +779,20 @@ int autotune_sweep(psr_ctx* ctx, cudaStream_t s) {
             }
             if (rc != PSR_OK) break;
         }
-        if (rc == PSR_OK) {
+        if (rc == PSR_OK && ctx->gntiles > 0) {
             for (auto& G : ctx->groups)
-                if ((rc = make_tiles(ctx, G, G.h_sorted_phi, bT)) != PSR_OK) break;
+                if (!G.stream && (rc = make_tiles(ctx, G, G.h_sorted_phi, bT)) != PSR_OK) break;
             if (rc == PSR_OK) rc = build_grouped_tables(ctx);
             ctx->grouped_blocks = bB;
         }
+        if (rc == PSR_OK) rc = tune_stream_grid(ctx, r, z, s, ev, NT, time_apply);
         for (auto& e : ev) cudaEventDestroy(e);
         return rc;
     }
     constexpr int NT = 3;
     struct Cand { int T, W; bool tpp; size_t off, len; };
     for (auto& G : ctx->groups) {
-        if (G.tc || (G.m == G.count && G.p <= 32)) continue;   // fixed shapes
+        if (G.tc || G.stream || (G.m == G.count && G.p <= 32)) continue;   // fixed shapes
         const int shapes[][2] = {{8, 8}, {16, 8}, {16, 4}, {32, 4}, {64, 4}, {32, 8}, {64, 8}, {128, 8}};
         std::vector<Cand> cand;
         std::vector<int32_t> all;
@@ -816,6 +852,35 @@ int autotune_sweep(psr_ctx* ctx, cudaStream_t s) {
         }
     }
     if (rc == PSR_OK) rc = build_grouped_tables(ctx);
+    if (rc == PSR_OK && ctx->n_stream > 0) {
+        constexpr int NS = 5;
+        cudaEvent_t ev[NS + 1];
+        for (auto& e : ev) PSR_CUDA(ctx, cudaEventCreate(&e));
+        auto time_apply = [&](float* out_ms) -> int {
+            for (int w = 0; w < 2; ++w) {
+                int rc2 = sweep_apply_ex(ctx, r, z, nullptr, s);
+                if (rc2 != PSR_OK) return rc2;
+            }
+            cudaEventRecord(ev[0], s);
+            for (int it = 0; it < NS; ++it) {
+                int rc2 = sweep_apply_ex(ctx, r, z, nullptr, s);
+                if (rc2 != PSR_OK) return rc2;
+                cudaEventRecord(ev[it + 1], s);
+            }
+            cudaEventSynchronize(ev[NS]);
+            std::vector<float> ts;
+            for (int it = 0; it < NS; ++it) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev[it], ev[it + 1]);
+                ts.push_back(ms);
+            }
+            std::sort(ts.begin(), ts.end());
+            *out_ms = ts[ts.size() / 2];
+            return PSR_OK;
+        };
+        rc = tune_stream_grid(ctx, r, z, s, ev, NS, time_apply);
+        for (auto& e : ev) cudaEventDestroy(e);
+    }
     return rc;
 }
 
@@ -886,7 +951,12 @@ static int sweep_patches(psr_ctx* ctx, const double* r, double* z, const int32_t
                          bool z_zeroed) {
     if (!z_zeroed) PSR_CUDA(ctx, cudaMemsetAsync(z, 0, sizeof(double) * (size_t)ctx->n, s));
     const int prec = ctx->opts.store_prec;
+    if (ctx->n_stream > 0) {
+        const int rc = launch_sweep_stream(ctx, r, z, stop, s);
+        if (rc != PSR_OK) return rc;
+    }
     if (ctx->sweep_mode == PSR_SWEEP_GROUPED && prec != PSR_PREC_BF16) {
+        if (ctx->gntiles == 0) return PSR_OK;
         int pmax = 0;
         for (auto& G : ctx->groups) pmax = std::max(pmax, G.p);
         const int warps = 8;
@@ -901,6 +971,7 @@ static int sweep_patches(psr_ctx* ctx, const double* r, double* z, const int32_t
         return PSR_OK;
     }
     for (auto& G : ctx->groups) {
+        if (G.stream) continue;
         int rc = (prec == PSR_PREC_FP64)   ? launch_group<double>(ctx, G, r, z, stop, s)
                  : (prec == PSR_PREC_FP32) ? launch_group<float>(ctx, G, r, z, stop, s)
                                            : launch_group<__nv_bfloat16>(ctx, G, r, z, stop, s);
@@ -944,6 +1015,7 @@ void free_sweep(psr_ctx* ctx) {
         psr::dev_free(G.sdofs_t);
         psr::dev_free(G.wtiles);
         psr::dev_free(G.dbA);
+        psr::dev_free(G.bexp);
         if (G.rinv && !(ctx->A_ext && reinterpret_cast<double*>(G.rinv) >= ctx->A_ext &&
                          reinterpret_cast<double*>(G.rinv) < ctx->A_ext + ctx->A_ext_len))
             psr::dev_free(G.rinv);
@@ -952,6 +1024,7 @@ void free_sweep(psr_ctx* ctx) {
     psr::dev_free(ctx->gtiles);
     psr::dev_free(ctx->gdesc);
     psr::dev_free(ctx->gcounter);
+    stream_free(ctx);
     ctx->gtiles = nullptr;
     ctx->gdesc = nullptr;
     ctx->gcounter = nullptr;

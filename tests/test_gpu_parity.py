@@ -206,10 +206,11 @@ def test_alg1_tol_zero_identity(lib):
 # ------------------------------------------------------------------ a4
 @pytest.mark.parametrize("weighting", ["left", "sym"])
 @pytest.mark.parametrize("tol", [0.0, 1e-1])
-def test_apply_vs_oracle_fp64(lib, weighting, tol):
+@pytest.mark.parametrize("arith", ["pairs", "native"])
+def test_apply_vs_oracle_fp64(lib, weighting, tol, arith):
     pr = P.stokes2d_q2q1(8)
     st = O.setup(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d(), tol)
-    ctx = setup_ctx(lib, pr, tol=tol, weighting=weighting, krylov="fgmres")
+    ctx = setup_ctx(lib, pr, tol=tol, weighting=weighting, krylov="fgmres", fp64_arith=arith)
     g = np.random.default_rng(1)
     for _ in range(3):
         r = g.standard_normal(pr.n)

@@ -45,10 +45,15 @@ def test_sizes_present(stokes3d):
 
 
 @pytest.mark.parametrize("kernel", ["grouped", "pergroup"])
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp64-native", "fp32"])
 def test_uneven_apply_vs_oracle(lib, stokes3d, kernel, prec):
+    """Full storage streams every group through k_sweep_stream; FP64 entries
+    as FP32 pairs (default) or with FP64 FMAs, both within the FP64 bar."""
     pr, Binv, W = stokes3d
-    ctx = ctx_for(lib, pr, tol=0.0, store_prec=prec, weighting="left", krylov="fgmres", sweep_kernel=kernel)
+    arith = "native" if prec == "fp64-native" else "pairs"
+    prec = prec.split("-")[0]
+    ctx = ctx_for(lib, pr, tol=0.0, store_prec=prec, weighting="left", krylov="fgmres", sweep_kernel=kernel,
+                  fp64_arith=arith)
     st = ctx.stats()
     assert st["n_groups"] == 4 and st["m_p"] == pr.n_patches
     g = np.random.default_rng(5)
@@ -90,3 +95,58 @@ def test_autotuner_keeps_results(lib, stokes3d):
         ctx.apply(r, z)
         out.append(z.cpu().numpy())
     assert np.abs(out[0] - out[1]).max() <= 1e-13 * np.abs(out[0]).max()
+
+
+def test_uneven_apply_bf16_vs_rounded_operator(lib, stokes3d):
+    """BF16 full storage of the uneven groups: equal, up to FP32
+    accumulation, to the exactly summed product of the symmetrised inverses
+    rounded FP64 -> FP32 -> BF16 (nearest even) with x rounded to FP32."""
+    pr, Binv, W = stokes3d
+
+    def bf16(x):
+        f = np.ascontiguousarray(np.asarray(x, dtype=np.float64).astype(np.float32))
+        b = f.view(np.uint32).astype(np.uint64)
+        b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+        return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+    Bq = [bf16(0.5 * (B + B.T)) for B in Binv]
+    ctx = ctx_for(lib, pr, tol=0.0, store_prec="bf16", weighting="left", krylov="fgmres")
+    g = np.random.default_rng(8)
+    for _ in range(2):
+        r = g.standard_normal(pr.n)
+        z = torch.empty(pr.n, dtype=torch.float64, device="cuda")
+        ctx.apply(dev(r, torch.float64), z)
+        rq = r.astype(np.float32).astype(np.float64)
+        zr = O.apply_ragged(rq, pr.patch_offsets, pr.patch_dofs, Bq, np.arange(pr.n_patches), W, "left")
+        err = np.abs(z.cpu().numpy() - zr).max() / np.abs(zr).max()
+        assert err < 2e-6, err
+
+
+def test_uneven_apply_nan_propagates(lib, stokes3d):
+    """A NaN in r reaches z at the DOFs of the patches holding it, and only
+    through them: patches without it keep their values (FP64 pairs)."""
+    pr, Binv, W = stokes3d
+    ctx = ctx_for(lib, pr, tol=0.0, store_prec="fp64", weighting="left", krylov="fgmres")
+    r = np.random.default_rng(9).standard_normal(pr.n)
+    j = int(pr.patch_dofs[pr.patch_offsets[pr.n_patches // 2]])
+    r_nan = r.copy()
+    r_nan[j] = np.nan
+    z = torch.empty(pr.n, dtype=torch.float64, device="cuda")
+    ctx.apply(dev(r_nan, torch.float64), z)
+    zc = z.cpu().numpy()
+    touched = np.zeros(pr.n, dtype=bool)
+    for k in range(pr.n_patches):
+        d = pr.patch_dofs[pr.patch_offsets[k]:pr.patch_offsets[k + 1]]
+        if j in d:
+            touched[d] = True
+    assert np.all(np.isnan(zc[touched]))
+    zr = O.apply_ragged(np.where(np.isnan(r_nan), 0.0, r_nan), pr.patch_offsets, pr.patch_dofs, Binv,
+                        np.arange(pr.n_patches), W, "left")
+    # DOFs outside every patch holding j: unaffected by the NaN
+    clean = np.ones(pr.n, dtype=bool)
+    for k in range(pr.n_patches):
+        d = pr.patch_dofs[pr.patch_offsets[k]:pr.patch_offsets[k + 1]]
+        if touched[d].any():
+            clean[d] = False
+    assert clean.any()
+    assert np.abs(zc[clean] - zr[clean]).max() <= 1e-12 * np.abs(zr).max()
