@@ -156,7 +156,11 @@ typedef struct {
  * compute W, build B and phi with Alg. 1 at opts->tol (tol = 0 stores every
  * patch, Eq. 1), invert the representatives (FP64 LU-equivalent Gauss-Jordan
  * with partial pivoting), convert them to opts->store_prec and lay out the
- * sweep.  The CSR and map are copied; the caller may free them afterwards.
+ * sweep.  Patches of up to 128 DOFs; every size forms its own group (the
+ * remark after Eq. 1) with its own database, numbered group after group,
+ * larger sizes first.  Groups in which every patch is its own entry are
+ * stored column-major and streamed (one launch over all of them).  The CSR
+ * and map are copied; the caller may free them afterwards.
  * On success *out owns all derived storage.  Errors: INVALID_ARG,
  * UNSORTED_CSR, UNCOVERED_DOF, SINGULAR_PATCH (psr_last_error names the
  * patch), OOM, CUDA.  Blocks the host. */
@@ -393,7 +397,11 @@ int psr_batched_inverse(const double* A, int32_t batch, int32_t p, double* Ainv,
  * dval (device, batch, may be NULL) <- the value that decided: 0 for an
  * exactly equal patch, a certified upper bound below tol for an accept, a
  * certified lower bound >= tol for a reject, or sigma_max from the exact
- * path.  A_i, A_c, Binv_c: device, row-major p x p FP64.  1 <= p <= 32. */
+ * path (p <= 32: Jacobi eigenvalues of E^T E; 33 <= p <= 128: the power-
+ * iteration estimate, the decision taken by one Cholesky of tol^2 I - E^T E
+ * for the near ties no certificate settles).  A_i, A_c, Binv_c: device,
+ * row-major p x p FP64.  1 <= p <= 128 (p > 32: one block per candidate;
+ * the call allocates scratch and blocks the host until done). */
 int psr_criterion(const double* A_i, int32_t batch, int32_t p, const double* A_c,
                   const double* Binv_c, double tol, int32_t* accept, double* dval,
                   void* stream);

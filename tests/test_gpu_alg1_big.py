@@ -1,0 +1,175 @@
+"""Alg. 1 and the criterion for patches of 33..128 DOFs (block-per-candidate
+kernels): the Dirichlet-trimmed 3D Stokes Vanka groups (89 / 62 / 44 DOFs,
+the 32-DOF corners take the warp kernels) and the Q5 cells of Experiment 1
+(36 DOFs), against the oracle's Alg. 1 per size group (remark after Eq. 1)."""
+import numpy as np
+import pytest
+
+import problems as P
+from oracle import psr_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2306_10025_gb300 as L
+    return L
+
+
+def dev(a, dt):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+
+
+def ctx_for(lib, pr, **kw):
+    rp, ci, va = dev(pr.rowptr, torch.int32), dev(pr.colidx, torch.int32), dev(pr.vals, torch.float64)
+    if pr.uniform_size:
+        return lib.psr_setup(rp, ci, va, dev(pr.patch_dofs, torch.int32), uniform_size=pr.uniform_size,
+                             opts=lib.make_opts(**kw))
+    return lib.psr_setup(rp, ci, va, dev(pr.patch_dofs, torch.int32), offsets=dev(pr.patch_offsets, torch.int32),
+                         opts=lib.make_opts(**kw))
+
+
+@pytest.mark.parametrize("p", [36, 62, 89, 128])
+def test_criterion_big_vs_exact_norm(lib, p):
+    """psr_criterion at p > 32: the decision equals sigma_max(E) < tol (numpy
+    SVD of the difference form) away from near ties; an accepted value bounds
+    d from above, a rejected one from below."""
+    g = np.random.default_rng(p)
+    batch = 300
+    Ac = g.standard_normal((p, p)) + p * np.eye(p)
+    Binv = np.linalg.inv(Ac)
+    scale = 10.0 ** g.uniform(-7, 0.5, (batch, 1, 1))
+    Ai = Ac[None] + scale * g.standard_normal((batch, p, p))
+    Ai[0] = Ac
+    Ai[1] = 1.01 * Ac                                  # a scaled copy: d = 0.01 / 1.01
+    d = np.linalg.norm(np.matmul(Ac[None] - Ai, Binv[None]), ord=2, axis=(1, 2))
+    for tol in (float(np.median(d)), 1e-3, 0.05):
+        acc = torch.full((batch,), -7, dtype=torch.int32, device="cuda")
+        dv = torch.full((batch,), np.nan, dtype=torch.float64, device="cuda")
+        lib.psr_criterion(dev(Ai, torch.float64), dev(Ac, torch.float64), dev(Binv, torch.float64), tol, acc, dv)
+        a = acc.cpu().numpy().astype(bool)
+        dvh = dv.cpu().numpy()
+        far = np.abs(d - tol) > 1e-9 * tol
+        assert np.array_equal(a[far], d[far] < tol), (p, tol)
+        assert a[0] and dvh[0] == 0.0
+        ok = far
+        assert np.all(dvh[a & ok] >= d[a & ok] * (1 - 1e-12))
+        assert np.all(dvh[~a & ok] <= d[~a & ok] * (1 + 1e-12))
+
+
+def test_criterion_big_near_tie_goes_exact(lib):
+    """tol equal to one candidate's sigma_max: no bound can decide it; the
+    others still match the exact norm."""
+    p, batch = 62, 64
+    g = np.random.default_rng(3)
+    Ac = g.standard_normal((p, p)) + p * np.eye(p)
+    Binv = np.linalg.inv(Ac)
+    Ai = Ac[None] + 10.0 ** g.uniform(-4, -1, (batch, 1, 1)) * g.standard_normal((batch, p, p))
+    d = np.linalg.norm(np.matmul(Ac[None] - Ai, Binv[None]), ord=2, axis=(1, 2))
+    tol = float(d[7])
+    acc = torch.full((batch,), -7, dtype=torch.int32, device="cuda")
+    lib.psr_criterion(dev(Ai, torch.float64), dev(Ac, torch.float64), dev(Binv, torch.float64), tol, acc)
+    a = acc.cpu().numpy()
+    assert a[7] in (0, 1)
+    far = np.abs(d - tol) > 1e-9 * tol
+    assert np.array_equal(a[far].astype(bool), d[far] < tol)
+
+
+def _groups(pr):
+    """Patch indices of each size group, larger sizes first (the library's
+    group order), and the patch matrices of each group in patch order."""
+    Alist = O.extract_patches_ragged(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.patch_offsets, pr.patch_dofs)
+    sizes = pr.patch_sizes
+    out = []
+    for s in sorted(set(sizes.tolist()), reverse=True):
+        idx = np.flatnonzero(sizes == s)
+        out.append((s, idx, np.stack([Alist[k] for k in idx])))
+    return out
+
+
+@pytest.mark.parametrize("case", ["jitter4", "jitter5", "uniform4"])
+def test_alg1_big_groups_bit_exact(lib, case):
+    """phi, the representatives and the evaluation counts of Alg. 1 per size
+    group equal the oracle's (the GPU numbers entries group after group,
+    larger patches first)."""
+    if case == "jitter4":
+        pr, tols = P.stokes3d_q2q1(4, seed=3), [15.0, 22.0, 40.0]
+    elif case == "jitter5":
+        pr, tols = P.stokes3d_q2q1(5, seed=1), [18.0, 30.0]
+    else:
+        pr, tols = P.stokes3d_q2q1(4, jitter=0.0), [1e-10, 0.5]
+    groups = _groups(pr)
+    for tol in tols:
+        refs = [O.alg1(A, tol) for _, _, A in groups]
+        for r in refs:
+            assert r["near_ties"] == [], "oracle reports a near tie; pick another tol"
+        ctx = ctx_for(lib, pr, tol=tol, weighting="left", krylov="fgmres")
+        phi, reps, m = ctx.assignment()
+        phi = phi.cpu().numpy()
+        reps = reps.cpu().numpy()
+        assert m == sum(len(r["reps"]) for r in refs), (case, tol)
+        base = 0
+        for (s, idx, _), r in zip(groups, refs):
+            mg = len(r["reps"])
+            assert np.array_equal(phi[idx] - base, r["phi"]), (case, tol, s)
+            assert np.array_equal(reps[base:base + mg], idx[r["reps"]]), (case, tol, s)
+            base += mg
+        st = ctx.stats()
+        assert st["criterion_evals"] == sum(r["evals"] for r in refs), (case, tol)
+        ctx.destroy()
+
+
+def test_alg1_big_uniform_classes():
+    """Sanity of the uniform case itself: with no jitter the interior cells'
+    patches are bitwise equal, so each size group keeps one entry per
+    boundary class (interior 1, faces 6, edges 12, corners 8)."""
+    pr = P.stokes3d_q2q1(4, jitter=0.0)
+    counts = {s: len(O.alg1(A, 1e-10)["reps"]) for s, _, A in _groups(pr)}
+    assert counts == {89: 1, 62: 6, 44: 12, 32: 8}
+
+
+def test_exp1_q5_alg1_bit_exact(lib):
+    """Q5 cells (36 DOFs) of Experiment 1's problem on a 10 x 10 mesh."""
+    pr = P.smooth2d_qp(N=10, p=5)
+    A = O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d())
+    for tol in (0.05, 0.2, 0.5, 2.0):
+        ref = O.alg1(A, tol)
+        assert ref["near_ties"] == []
+        ctx = ctx_for(lib, pr, tol=tol, weighting="left", krylov="fgmres")
+        phi, reps, m = ctx.assignment()
+        assert m == len(ref["reps"])
+        assert np.array_equal(phi.cpu().numpy(), ref["phi"])
+        assert np.array_equal(reps.cpu().numpy(), ref["reps"])
+        assert ctx.stats()["criterion_evals"] == ref["evals"]
+        ctx.destroy()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_clustered_big_apply_vs_oracle(lib, prec):
+    """Eq. 3 with the clustered 3D Stokes database (every group at tol 22):
+    the apply equals the oracle's apply_ragged with the oracle's databases."""
+    pr = P.stokes3d_q2q1(4, seed=3)
+    tol = 22.0
+    groups = _groups(pr)
+    phi = np.empty(pr.n_patches, dtype=np.int64)
+    db = []
+    for s, idx, A in groups:
+        r = O.alg1(A, tol)
+        phi[idx] = len(db) + r["phi"]
+        db.extend(list(r["Binv"]))
+    W = O.weights(O.multiplicity(pr.n, pr.patch_dofs))
+    ctx = ctx_for(lib, pr, tol=tol, store_prec=prec, weighting="left", krylov="fgmres")
+    assert ctx.stats()["m_p"] < pr.n_patches
+    g = np.random.default_rng(4)
+    for _ in range(2):
+        rv = g.standard_normal(pr.n)
+        z = torch.empty(pr.n, dtype=torch.float64, device="cuda")
+        ctx.apply(dev(rv, torch.float64), z)
+        zr = O.apply_ragged(rv, pr.patch_offsets, pr.patch_dofs, db, phi, W, "left")
+        err = np.abs(z.cpu().numpy() - zr).max() / np.abs(zr).max()
+        assert err < (1e-12 if prec == "fp64" else 2e-5), err
