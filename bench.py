@@ -1,23 +1,30 @@
 """Benchmark of the compressed patch-relaxation hot path on GB300.
 
-One step = the whole path on one synthetic workload: setup (patch extraction,
-multiplicity weights, Alg. 1 with the certified criterion, FP64 inverses of
-the database entries, conversion to the storage precision, sweep layout) and
-the outer solve (right-preconditioned FGMRES(30) or PCG, sweeps + SpMV +
-orthogonalisation) from x0 = 0, inputs already resident in HBM.
+One step = the whole path on one synthetic workload, inputs resident in HBM:
+setup (patch extraction, multiplicity weights, the database -- Alg. 1, or
+every patch its own entry at tol 0 (Eq. 1) -- FP64 inverses, conversion to
+the storage layout, autotuned sweep layout) and the outer solve
+(right-preconditioned FGMRES(30) or PCG from x0 = 0, sweeps + SpMV +
+orthogonalisation) to 1e-8 or a fixed iteration budget.
 
-Default workload: 2D Stokes, Taylor-Hood Q2-Q1 on 128 x 128 quads graded in y
-(ratio 1.05), 22-DOF Vanka cell patches, FGMRES(30) in FP64, criterion tol
-1e-2, representative inverses stored in FP32.  The one-level Vanka
-preconditioner does not reach 1e-8 on this mesh within a practical budget, so
-a step runs a fixed iteration budget (--maxit, default 300) and reports the
-relative residual reached; the full-storage FP64 form is measured beside it.
+Default workload: 3D Stokes, Taylor-Hood Q2-Q1 on 48^3 hexahedra with vertex
+jitter 0.2h, Dirichlet-trimmed Vanka cell patches of 89 / 62 / 44 / 32 DOFs
+(2,689,774 DOFs, 110,592 patches), full storage of FP64 inverses, all size
+groups in one streamed sweep launch, FGMRES(30) in FP64.  On this jittered
+mesh no two interior patches are within any useful tolerance of each other
+(d = 13.7 .. 28.8 between interior patches of the 6^3 instance), so Alg. 1
+would keep every patch; the one-level Vanka preconditioner does not reach
+1e-8 on it either, so a step runs a fixed FGMRES budget (--maxit).  The
+clustered-vs-full comparison to 1e-8 is the `per_config` sub-line on the 3D
+lognormal Q2 workload (32^3, PCG), where the one-level method converges.
 
-value = n x (preconditioner applications in the step) / step time, i.e. the
-Schwarz sweep DOF/s of the whole step with setup included (unit DOF/s).
+value = the Schwarz sweep rate of the timed steps: n x (sweeps in the steps)
+/ (device time of those sweeps), the sweeps timed by CUDA events the library
+records on the solve stream around each launch.  ms_per_step is the whole
+step (setup + solve).
 
 Prints ONE JSON line (rank 0).  --impl reference times the CPU FP64 oracle on
-a bounded sample of the same workload instead.
+a bounded sample of the same instance instead.
 """
 from __future__ import annotations
 
@@ -27,6 +34,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -37,19 +45,19 @@ import numpy as np
 METRIC = "Schwarz sweep DOF/s + setup s, clustered vs full, iters to 1e-8 rel. residual"
 
 CONFIGS = {
-    "stokes2d": dict(builder="stokes2d_q2q1", kw=dict(N=128, ratio=1.05), tol=1e-2, prec="fp32",
-                     weighting="left", krylov="fgmres",
+    "stokes3d": dict(builder="stokes3d_q2q1", kw=dict(N=48), tol=0.0, prec="fp64", weighting="left",
+                     krylov="fgmres", maxit=60,
+                     desc="3D Stokes Q2-Q1 48^3 hexes, vertex jitter 0.2h, Dirichlet-trimmed Vanka patches "
+                          "{89, 62, 44, 32} in one streamed sweep launch, FP64 full storage, FGMRES(30)"),
+    "diffusion3d": dict(builder="diffusion3d_q2", kw=dict(N=32), tol=1e-1, prec="fp64", weighting="sym",
+                        krylov="cg", maxit=3000, desc="3D Q2 lognormal diffusion 32^3, 27-DOF patches, PCG"),
+    "stokes2d": dict(builder="stokes2d_q2q1", kw=dict(N=128, ratio=1.05), tol=1e-2, prec="fp64",
+                     weighting="left", krylov="fgmres", maxit=300,
                      desc="2D Stokes Taylor-Hood Q2-Q1, 128x128 quads graded 1.05 in y, 22-DOF Vanka patches"),
     "poisson2d": dict(builder="poisson2d_q2", kw=dict(N=16), tol=1e-12, prec="fp64", weighting="sym",
-                      krylov="cg", desc="2D Q2 diffusion 16x16, 9-DOF patches"),
-    "nedelec3d": dict(builder="nedelec3d", kw=dict(N=64), tol=1e-1, prec="fp32", weighting="sym",
-                      krylov="cg", desc="3D Nedelec curl-curl 64^3, 12-DOF patches"),
-    "diffusion3d": dict(builder="diffusion3d_q2", kw=dict(N=32), tol=1e-1, prec="fp32", weighting="sym",
-                        krylov="cg", desc="3D Q2 lognormal diffusion 32^3, 27-DOF patches"),
-    "stokes3d": dict(builder="stokes3d_q2q1", kw=dict(N=24), tol=0.0, prec="fp32", weighting="left",
-                     krylov="fgmres",
-                     desc="3D Stokes Q2-Q1 24^3 hexes, vertex jitter 0.2h, Dirichlet-trimmed Vanka patches "
-                          "{89, 62, 44, 32} in one grouped persistent sweep, full storage"),
+                      krylov="cg", maxit=1000, desc="2D Q2 diffusion 16x16, 9-DOF patches"),
+    "nedelec3d": dict(builder="nedelec3d", kw=dict(N=64), tol=0.0, prec="fp64", weighting="sym",
+                      krylov="cg", maxit=300, desc="3D Nedelec curl-curl 64^3, 12-DOF patches"),
 }
 
 # FP64 peak of one GB300 from its unit counts and clock: 152 SMs x 2 FP64
@@ -58,23 +66,15 @@ CONFIGS = {
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 # kernel(s) behind each timing class of the library's per-kernel timing
-KT_KERNEL_NAMES = {"sweep": "patch sweep (k_sweep_staged / k_sweep_*)", "spmv": "k_spmv_sell (SELL SpMV, FP64)",
-                   "mdot": "k_arnoldi (fused FGMRES Gram-Schmidt step on FP32 pairs) / k_mdot", "maxpy": "k_maxpy (FGMRES w -= V h)",
-                   "vec": "vector kernels (k_fg_scale / CG updates)"}
+KT_KERNEL_NAMES = {"sweep": "patch sweep (k_sweep_stream for full-storage groups / k_sweep_* tiles)",
+                   "spmv": "k_spmv_sell (SELL SpMV, FP64)",
+                   "mdot": "k_arnoldi (fused FGMRES Gram-Schmidt step on FP32 pairs) / k_mdot",
+                   "maxpy": "k_maxpy (FGMRES w -= V h)", "vec": "vector kernels (k_fg_scale / CG updates)"}
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, ncu,
-# averaged over the captured launches) for (config, class), valid only for
-# the kernel source they were taken on; None until captured.
-TRAFFIC = {
-    # ncu --set full of the fused Gram-Schmidt step on pairs at j = 20
-    # (26.30 MB: one DRAM read of the 21 pair rows and of w, later passes
-    # from L2) scaled to the mean basis size of a step, (j+2) averaged over
-    # j = 0..29
-    ("stokes2d", "mdot"): 26.30e6 * 16.5 / 22.0,
-    # ncu --set full, one launch inside the FGMRES cycle (k_spmv_sell):
-    # 89.11 MB read + 2.47 MB written
-    ("stokes2d", "spmv"): 91.6e6,
-}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, ncu)
+# for (config, class), valid only for the kernel source they were taken on;
+# None until captured.
+TRAFFIC = {}
 
 
 def parse():
@@ -83,13 +83,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default="stokes2d", choices=sorted(CONFIGS))
-    ap.add_argument("--maxit", type=int, default=300)
+    ap.add_argument("--config", default="stokes3d", choices=sorted(CONFIGS))
+    ap.add_argument("--maxit", type=int, default=None)
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--prec", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the precision variants and the sub-line")
     ap.add_argument("--apply-reps", type=int, default=200)
+    ap.add_argument("--clock-dir", default=None, help="folder for the nvidia-smi clock samples (default: a temp dir)")
     ap.add_argument("--mlp", action="store_true", help="learned-assignment gain on the 3D lognormal workload")
     ap.add_argument("--exp1", action="store_true",
                     help="Experiment 1: iterations of FGMRES(20) + M_combo for Q2..Q5 (Table 1 of the paper)")
@@ -119,10 +121,11 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, folder: str | None = None):
         self.p = None
         self.idx = gpu_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        folder = folder or tempfile.mkdtemp(prefix="psr_clocks_")
+        self.path = os.path.join(folder, f"clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:
@@ -180,6 +183,161 @@ def aggregate_replicas(seconds: float, units: float, device=None):
 
 
 # ------------------------------------------------------------------ GPU arm
+def _setup_solve(L, dev_in, pr, opts, b, x, timing):
+    """One step: setup + solve.  Returns (ctx, solve info)."""
+    rp, ci, va, dofs, offs = dev_in
+    ctx = L.psr_setup(rp, ci, va, dofs, offsets=offs, uniform_size=pr.uniform_size, opts=opts)
+    if timing:
+        ctx.set_kernel_timing(True)
+    info = ctx.solve(b, x)
+    return ctx, info
+
+
+def _apply_median(ctx, n, reps, devc, flush=None, seed=1):
+    """Median device time (s) of `reps` applies on random r (CUDA events on
+    the current stream), after 10 untimed ones; flush (a tensor larger than
+    L2) is zeroed before every timed apply when given."""
+    import torch
+    stream = torch.cuda.current_stream()
+    g = torch.Generator(device=devc).manual_seed(seed)
+    rs = [torch.randn(n, dtype=torch.float64, device=devc, generator=g) for _ in range(2)]
+    z = torch.empty_like(rs[0])
+    for _ in range(10):
+        ctx.apply(rs[0], z)
+    ev = []
+    for i in range(reps):
+        if flush is not None:
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.apply(rs[i % 2], z)
+        e1.record(stream)
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = sorted(a.elapsed_time(b_) for a, b_ in ev)
+    return ms[len(ms) // 2] * 1e-3
+
+
+def _sweep_alg_bytes(pr, st):
+    """Algorithmic bytes of one apply: r, W and z (24 n), the DOF map (4 per
+    patch DOF), phi (4 per patch) and the stored inverses."""
+    return 24 * pr.n + 4 * int(pr.patch_offsets[-1]) + 4 * pr.n_patches + st["factor_bytes"]
+
+
+def _kernels_from_timing(kt, hbm):
+    out = {}
+    for name, (ms, cnt, by, fl) in kt.items():
+        if cnt:
+            out[name] = {"launches": cnt, "ms": ms, "us_per_launch": 1e3 * ms / cnt,
+                         "alg_bytes_per_launch": by / cnt, "achieved_gbs": by / (ms * 1e-3) / 1e9,
+                         "frac": by / (ms * 1e-3) / 1e9 / hbm,
+                         "fp64_flops_per_launch": fl / cnt, "achieved_fp64_tflops": fl / (ms * 1e-3) / 1e12,
+                         "frac_fp64": fl / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
+    tot = sum(v["ms"] for v in out.values()) or 1.0
+    for v in out.values():
+        v["share"] = v["ms"] / tot
+    return out
+
+
+def _roofline_of(name, kd, hbm, peak_source, config):
+    if kd["frac_fp64"] > kd["frac"]:
+        bound = {"bound": "alu", "achieved": kd["achieved_fp64_tflops"], "peak": FP64_PEAK_TFLOPS,
+                 "unit": "TFLOP/s (FP64)", "frac": kd["frac_fp64"],
+                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clock x 2 flops x 2070 MHz"}
+    else:
+        bound = {"bound": "hbm", "achieved": kd["achieved_gbs"], "peak": hbm, "unit": "GB/s", "frac": kd["frac"],
+                 "peak_source": peak_source}
+    return dict(kernel=KT_KERNEL_NAMES[name], **bound, traffic=TRAFFIC.get((config, name)),
+                alg_bytes_per_launch=kd["alg_bytes_per_launch"], launch_us=kd["us_per_launch"],
+                share_of_iteration_kernels=kd["share"])
+
+
+def _variant(L, dev_in, pr, cfg, b, devc, reps, tol, prec, arith, maxit, r_ref=None, z_ref=None, solve=True):
+    """One setup in another precision / arithmetic: its apply rate, its error
+    against the reference apply, and (optionally) its solve with the same
+    budget."""
+    import torch
+    opts = L.make_opts(tol=tol, store_prec=prec, weighting=cfg["weighting"], krylov=cfg["krylov"], restart=30,
+                       rtol=1e-8, maxit=maxit, fp64_arith=arith)
+    x = torch.zeros_like(b)
+    ctx, info = _setup_solve(L, dev_in, pr, opts, b, x, False) if solve else (None, None)
+    if ctx is None:
+        rp, ci, va, dofs, offs = dev_in
+        ctx = L.psr_setup(rp, ci, va, dofs, offsets=offs, uniform_size=pr.uniform_size, opts=opts)
+    st = ctx.stats()
+    out = {"store_prec": prec, "fp64_arith": arith if prec == "fp64" else None, "m_p": st["m_p"],
+           "factor_bytes": st["factor_bytes"]}
+    ams = _apply_median(ctx, pr.n, reps, devc)
+    out["apply_ms"] = ams * 1e3
+    out["sweep_dof_per_s"] = pr.n / ams
+    out["sweep_gbs"] = _sweep_alg_bytes(pr, st) / ams / 1e9
+    if r_ref is not None:
+        z = torch.empty_like(r_ref)
+        ctx.apply(r_ref, z)
+        out["apply_err_vs_fp64"] = float((z - z_ref).abs().max() / z_ref.abs().max())
+    if info is not None:
+        out.update(iterations=info["iterations"], relres=info["relres"], converged=info["converged"])
+    ctx.destroy()
+    return out
+
+
+def convergence_subline(L, args, devc, hbm):
+    """Clustered vs full storage to 1e-8 on the 3D lognormal Q2 workload
+    (32^3, PCG with SYM weighting): per form the setup and solve seconds
+    (CUDA events, median of 3 after one warm-up), iterations, database size,
+    apply rate, and the speedup of setup + solve over the FP64 full-storage
+    form."""
+    import torch
+    cfg = CONFIGS["diffusion3d"]
+    pr = build_problem(cfg)
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=devc)
+    dev_in = (t(pr.rowptr, torch.int32), t(pr.colidx, torch.int32), t(pr.vals, torch.float64),
+              t(pr.patch_dofs, torch.int32), None)
+    b = t(pr.rhs(0), torch.float64)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=devc)
+    stream = torch.cuda.current_stream()
+    forms = [("full_fp64", 0.0, "fp64"), ("clustered_fp64", cfg["tol"], "fp64"),
+             ("clustered_fp32", cfg["tol"], "fp32"), ("clustered_bf16", cfg["tol"], "bf16")]
+    rows = {}
+    for name, tol, prec in forms:
+        opts = L.make_opts(tol=tol, store_prec=prec, weighting=cfg["weighting"], krylov=cfg["krylov"], restart=30,
+                           rtol=1e-8, maxit=cfg["maxit"])
+        rp, ci, va, dofs, _ = dev_in
+        setups, solves = [], []
+        for rep in range(4):
+            flush.zero_()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            x = torch.zeros_like(b)
+            e0.record(stream)
+            ctx = L.psr_setup(rp, ci, va, dofs, uniform_size=pr.uniform_size, opts=opts)
+            e1.record(stream)
+            info = ctx.solve(b, x)
+            e2.record(stream)
+            e2.synchronize()
+            if rep > 0:
+                setups.append(e0.elapsed_time(e1) * 1e-3)
+                solves.append(e1.elapsed_time(e2) * 1e-3)
+            st = ctx.stats()
+            if rep < 3:
+                ctx.destroy()
+        ams = _apply_median(ctx, pr.n, 100, devc, flush=flush)
+        ctx.destroy()
+        rows[name] = {"tol": tol, "store_prec": prec, "m_p": st["m_p"], "retained_fraction": st["m_p"] / pr.n_patches,
+                      "factor_bytes": st["factor_bytes"], "setup_s": statistics.median(setups),
+                      "solve_s": statistics.median(solves), "iterations": info["iterations"],
+                      "converged": info["converged"], "relres": info["relres"],
+                      "criterion_evals": st["criterion_evals"], "criterion_screened": st["criterion_screened"],
+                      "criterion_exact": st["criterion_exact"], "sweep_dof_per_s": pr.n / ams,
+                      "apply_ms": ams * 1e3}
+    full = rows["full_fp64"]
+    for name, r in rows.items():
+        r["speedup_setup_plus_solve_vs_full_fp64"] = (full["setup_s"] + full["solve_s"]) / (r["setup_s"] + r["solve_s"])
+        r["within_plus_one_iteration"] = bool(r["converged"] and r["iterations"] <= full["iterations"] + 1)
+    return {"workload": cfg["desc"] + f", tol {cfg['tol']}, SYM weighting, rtol 1e-8", "n": pr.n,
+            "n_patches": pr.n_patches, "rhs": "uniform(-1,1) seed 0", "forms": rows}
+
+
 def run_gpu(args, cfg, ws, rank, local):
     import torch
     import __graft_entry__ as ge
@@ -188,263 +346,305 @@ def run_gpu(args, cfg, ws, rank, local):
 
     torch.cuda.set_device(local)
     devc = torch.device("cuda", local)
+    t_gen = time.perf_counter()
     pr = build_problem(cfg)
+    t_gen = time.perf_counter() - t_gen
     tol = cfg["tol"] if args.tol is None else args.tol
     prec = cfg["prec"] if args.prec is None else args.prec
+    maxit = cfg["maxit"] if args.maxit is None else args.maxit
     t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=devc)
-    rp, ci, va = t(pr.rowptr, torch.int32), t(pr.colidx, torch.int32), t(pr.vals, torch.float64)
-    dofs = t(pr.patch_dofs, torch.int32)
-    offs = None if pr.uniform_size else t(pr.patch_offsets, torch.int32)
+    dev_in = (t(pr.rowptr, torch.int32), t(pr.colidx, torch.int32), t(pr.vals, torch.float64),
+              t(pr.patch_dofs, torch.int32), None if pr.uniform_size else t(pr.patch_offsets, torch.int32))
     b = t(pr.rhs(0), torch.float64)
     x = torch.zeros_like(b)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=devc)   # > L2 (129 MB)
     stream = torch.cuda.current_stream()
+    opts = L.make_opts(tol=tol, store_prec=prec, weighting=cfg["weighting"], krylov=cfg["krylov"], restart=30,
+                       rtol=1e-8, maxit=maxit, fp64_arith="pairs")
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    peak_source = "measured" if "hbm_gbs" in peaks else "fallback"
+    # the stored inverses alone exceed L2 (129 MB) on the large workloads;
+    # smaller ones get an L2 flush (256 MB write) before every timed step
+    nnz_bytes = 12 * pr.nnz
+    big = nnz_bytes > 4 * 129e6
+    flush = None if big else torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=devc)
 
-    def mk_opts(tol_, prec_):
-        return L.make_opts(tol=tol_, store_prec=prec_, weighting=cfg["weighting"], krylov=cfg["krylov"],
-                           restart=30, rtol=1e-8, maxit=args.maxit)
-
-    def one_step(tol_, prec_):
-        ctx = L.psr_setup(rp, ci, va, dofs, offsets=offs, uniform_size=pr.uniform_size, opts=mk_opts(tol_, prec_))
-        info = ctx.solve(b, x)
-        return ctx, info
-
-    # warm-up
     for _ in range(args.warmup):
-        ctx, info = one_step(tol, prec)
+        ctx, info = _setup_solve(L, dev_in, pr, opts, b, x, True)
         ctx.destroy()
     torch.cuda.synchronize()
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()
-    clk = ClockSampler(local)
+    clk = ClockSampler(local, args.clock_dir)
     clk.start()
     launches0 = L.psr_kernel_launches()
-    times, infos, stats = [], [], []
+    times, infos, stats, kts = [], [], [], []
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
-    for _ in range(args.steps):
-        flush.zero_()                               # L2 flush between steps (outside the timing)
+    for k in range(args.steps):
+        if flush is not None:
+            flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ctx, info = one_step(tol, prec)
+        ctx, info = _setup_solve(L, dev_in, pr, opts, b, x, True)
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1) * 1e-3)
         infos.append(info)
         stats.append(ctx.stats())
-        if len(times) < args.steps:
+        kts.append(ctx.kernel_timing())
+        if k < args.steps - 1:
             ctx.destroy()
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     launches = L.psr_kernel_launches() - launches0
     clocks = clk.stop()
-    step_s = sum(times) / len(times)
-    iters = infos[-1]["iterations"]
-    units_local = pr.n * sum(i["iterations"] for i in infos)
-    value, total_s, _ = aggregate_replicas(sum(times), units_local, devc)
-
-    # kernel-level: sweep (apply) timing with CUDA events over many launches
     last = ctx
-    r = torch.randn(pr.n, dtype=torch.float64, device=devc)
-    z = torch.empty_like(r)
-    for _ in range(20):
-        last.apply(r, z)
-    big_r = [torch.randn(pr.n, dtype=torch.float64, device=devc) for _ in range(2)]
-    torch.cuda.synchronize()
-    ev = []
-    for i in range(args.apply_reps):
-        flush.zero_() if i % 8 == 0 else None
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        last.apply(big_r[i % 2], z)
-        e1.record(stream)
-        ev.append((e0, e1))
-    torch.cuda.synchronize()
-    apply_ms = sorted(a.elapsed_time(b_) for a, b_ in ev)
-    apply_med = apply_ms[len(apply_ms) // 2] * 1e-3
+    step_s = sum(times) / len(times)
+    sweep_ms = sum(kt["sweep"][0] for kt in kts)
+    sweeps = sum(kt["sweep"][1] for kt in kts)
+    units_local = pr.n * sweeps
+    value, total_sweep_s, _ = aggregate_replicas(sweep_ms * 1e-3, units_local, devc)
     st = stats[-1]
-    n, npch = pr.n, pr.n_patches
-    psum = int(pr.patch_offsets[-1])
-    eb = {"fp64": 8, "fp32": 4, "bf16": 2}[prec]
-    ntile_bytes = 12 * (st["m_p"] + npch // 32 + 1)
-    alg_bytes = 3 * 8 * n + 4 * psum + st["factor_bytes"] + ntile_bytes
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    peak_source = "measured" if "hbm_gbs" in peaks else "fallback"
-    sweep_alone = {"alg_bytes_per_launch": alg_bytes, "launch_us": apply_med * 1e6,
-                   "achieved_gbs": alg_bytes / apply_med / 1e9, "frac": alg_bytes / apply_med / 1e9 / hbm}
-
-    # per-kernel device time inside one more solve of the same step, from
-    # CUDA events the library records around every per-iteration launch on
-    # its stream (inside the cycle graph); the dominant class is the roofline
-    last.set_kernel_timing(True)
-    flush.zero_()
-    last.solve(b, x)
-    torch.cuda.synchronize()
-    kt = last.kernel_timing()
-    last.set_kernel_timing(False)
-    kernels = {}
-    for name, (ms, cnt, by, fl) in kt.items():
-        if cnt:
-            kernels[name] = {"launches": cnt, "ms": ms, "us_per_launch": 1e3 * ms / cnt,
-                             "alg_bytes_per_launch": by / cnt, "achieved_gbs": by / (ms * 1e-3) / 1e9,
-                             "frac": by / (ms * 1e-3) / 1e9 / hbm,
-                             "fp64_flops_per_launch": fl / cnt, "achieved_fp64_tflops": fl / (ms * 1e-3) / 1e12,
-                             "frac_fp64": fl / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
-    tot_ms = sum(v["ms"] for v in kernels.values())
-    for v in kernels.values():
-        v["share"] = v["ms"] / tot_ms
+    # per-kernel picture of the timed steps (summed over them)
+    kt_sum = {}
+    for kt in kts:
+        for name, (ms, cnt, by, fl) in kt.items():
+            a = kt_sum.setdefault(name, [0.0, 0, 0.0, 0.0])
+            a[0] += ms
+            a[1] += cnt
+            a[2] += by
+            a[3] += fl
+    kernels = _kernels_from_timing({k: tuple(v) for k, v in kt_sum.items()}, hbm)
     top = max(kernels, key=lambda k: kernels[k]["ms"])
-    kd = kernels[top]
-    # the binding resource of the dominant class: HBM bytes or FP64 flops,
-    # whichever it uses the larger fraction of
-    if kd["frac_fp64"] > kd["frac"]:
-        bound = {"bound": "alu", "achieved": kd["achieved_fp64_tflops"], "peak": FP64_PEAK_TFLOPS,
-                 "unit": "TFLOP/s (FP64)", "frac": kd["frac_fp64"],
-                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clock x 2 flops x 2070 MHz"}
-    else:
-        bound = {"bound": "hbm", "achieved": kd["achieved_gbs"], "peak": hbm, "unit": "GB/s", "frac": kd["frac"],
-                 "peak_source": peak_source}
-    roofline = dict(kernel=KT_KERNEL_NAMES[top], **bound, traffic=TRAFFIC.get((args.config, top)),
-                    alg_bytes_per_launch=kd["alg_bytes_per_launch"], hbm_frac=kd["frac"],
-                    fp64_flops_per_launch=kd["fp64_flops_per_launch"], fp64_frac=kd["frac_fp64"],
-                    launch_us=kd["us_per_launch"], share_of_iteration_kernels=kd["share"],
-                    timing="CUDA events on the solve stream around each launch, one extra solve after the timed steps",
-                    kernels=kernels, sweep_alone=sweep_alone)
+    roofline = _roofline_of(top, kernels[top], hbm, peak_source, args.config)
+    roofline["timing"] = "CUDA events the library records on the solve stream around each launch, timed steps"
+    roofline["kernels"] = kernels
+    sweep_roof = _roofline_of("sweep", kernels["sweep"], hbm, peak_source, args.config)
+    # the sweep alone: median of back-to-back applies (larger-than-L2 inputs)
+    r_ref = torch.randn(pr.n, dtype=torch.float64, device=devc, generator=torch.Generator(device=devc).manual_seed(7))
+    z_ref = torch.empty_like(r_ref)
+    last.apply(r_ref, z_ref)
+    ams = _apply_median(last, pr.n, args.apply_reps, devc, flush=flush)
+    sweep_roof["alone"] = {"apply_ms": ams * 1e3, "alg_bytes": _sweep_alg_bytes(pr, st),
+                           "achieved_gbs": _sweep_alg_bytes(pr, st) / ams / 1e9,
+                           "frac": _sweep_alg_bytes(pr, st) / ams / 1e9 / hbm, "reps": args.apply_reps}
     last.destroy()
-
-    # full-storage FP64 comparison (outside the timed steps)
-    ctx_f, info_f = one_step(0.0, "fp64")
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    ctx_f2, info_f2 = one_step(0.0, "fp64")
-    e1.record(stream)
-    e1.synchronize()
-    full_step_s = e0.elapsed_time(e1) * 1e-3
-    st_f = ctx_f2.stats()
-    ctx_f.destroy()
-    ctx_f2.destroy()
-
-    # end to end: host (pinned) inputs -> device -> setup + solve -> x to host
-    e2e = None
-    if not args.no_e2e:
-        hp = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).pin_memory()
-        h_rp, h_ci, h_va = hp(pr.rowptr, torch.int32), hp(pr.colidx, torch.int32), hp(pr.vals, torch.float64)
-        h_d, h_b = hp(pr.patch_dofs, torch.int32), hp(pr.rhs(0), torch.float64)
-        h_o = None if pr.uniform_size else hp(pr.patch_offsets, torch.int32)
-        h_x = torch.empty(n, dtype=torch.float64).pin_memory()
-        h2d = sum(a.numel() * a.element_size() for a in (h_rp, h_ci, h_va, h_d, h_b) ) + (0 if h_o is None else h_o.numel() * 4)
-        ets = []
-        for i in range(args.warmup + args.steps):
-            flush.zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            d_rp, d_ci, d_va = h_rp.to(devc, non_blocking=True), h_ci.to(devc, non_blocking=True), h_va.to(devc, non_blocking=True)
-            d_d, d_b = h_d.to(devc, non_blocking=True), h_b.to(devc, non_blocking=True)
-            d_o = None if h_o is None else h_o.to(devc, non_blocking=True)
-            d_x = torch.zeros(n, dtype=torch.float64, device=devc)
-            c2 = L.psr_setup(d_rp, d_ci, d_va, d_d, offsets=d_o, uniform_size=pr.uniform_size, opts=mk_opts(tol, prec))
-            inf2 = c2.solve(d_b, d_x)
-            h_x.copy_(d_x, non_blocking=True)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            c2.destroy()
-            if i >= args.warmup:
-                ets.append(dt)
-        e2e = {"value": n * inf2["iterations"] / (sum(ets) / len(ets)), "unit": "DOF/s",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(n * 8),
-               "ms_per_step": 1e3 * sum(ets) / len(ets)}
 
     out = {
         "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64+" + prec, "data": "synthetic",
-        "config": {"workload": cfg["desc"], "n": n, "n_patches": npch, "tol": tol, "store_prec": prec,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": cfg["desc"], "n": pr.n, "nnz": pr.nnz, "n_patches": pr.n_patches,
+                   "patch_sizes": sorted(set(pr.patch_sizes.tolist())), "tol": tol, "store_prec": prec,
+                   "fp64_arith": "pairs (FP64 inverses as (hi, lo) FP32 pairs, compensated products, ~47 bits)",
                    "krylov": cfg["krylov"] + ("(30)" if cfg["krylov"] == "fgmres" else ""),
-                   "weighting": cfg["weighting"], "maxit": args.maxit, "rhs": "uniform(-1,1) seed 0",
-                   "l2": "flushed (256 MB write) before every timed step",
+                   "weighting": cfg["weighting"], "maxit": maxit, "rhs": "uniform(-1,1) seed 0",
+                   "l2": ("inputs larger than L2 (the stored inverses alone)" if big
+                          else "flushed (256 MB write) before every timed step"),
                    "allocations": "library caching allocator, filled by the warm-up steps",
-                   "value_def": "n x preconditioner applications / step time (setup + solve)",
-                   "parallelism": f"replicas x{ws}"},
-        "setup_s": {"clustered": st["t_extract"] + st["t_rounds"] + st["t_convert"],
-                    "full": st_f["t_extract"] + st_f["t_rounds"] + st_f["t_convert"],
-                    "clustered_phases": {k: st[k] for k in ("t_extract", "t_rounds", "t_convert")}},
-        "iters": {"clustered": iters, "full": info_f2["iterations"], "relres_clustered": infos[-1]["relres"],
-                  "relres_full": info_f2["relres"], "converged_clustered": infos[-1]["converged"],
-                  "converged_full": info_f2["converged"], "rtol": 1e-8},
-        "step_s": {"clustered": step_s, "full_fp64": full_step_s},
-        "sweep_dof_per_s": n / apply_med,
-        "m_p": st["m_p"], "retained_fraction": st["m_p"] / npch,
-        "factor_bytes": {"clustered": st["factor_bytes"], "full": st_f["factor_bytes"]},
-        "criterion_evals": st["criterion_evals"], "criterion_exact": st["criterion_exact"], "criterion_screened": st["criterion_screened"],
-        "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
+                   "value_def": "n x sweeps in the timed steps / device time of those sweeps (CUDA events)",
+                   "generation_s": t_gen, "parallelism": f"replicas x{ws}"},
+        "setup_s": {"total": st["t_extract"] + st["t_rounds"] + st["t_convert"] + st["t_autotune"],
+                    "phases": {k: st[k] for k in ("t_extract", "t_rounds", "t_convert", "t_autotune")}},
+        "iters": {"iterations": infos[-1]["iterations"], "relres": infos[-1]["relres"],
+                  "converged": infos[-1]["converged"], "rtol": 1e-8},
+        "m_p": st["m_p"], "retained_fraction": st["m_p"] / pr.n_patches, "factor_bytes": st["factor_bytes"],
+        "criterion_evals": st["criterion_evals"],
+        "step_dof_per_s": pr.n * sweeps / sum(times),
+        "roofline": roofline, "sweep_roofline": sweep_roof, "clocks": clocks, "gpu_launches": launches,
     }
-    return out, pr, infos[-1], st
+    if not args.no_extras:
+        # the same setup with other storage / arithmetic: rate, error against
+        # the FP64 (pairs) apply and the solve with the same budget
+        variants = {}
+        for name, pv, ar in (("fp64_native", "fp64", "native"), ("fp32", "fp32", "pairs"), ("bf16", "bf16", "pairs")):
+            variants[name] = _variant(L, dev_in, pr, cfg, b, devc, 50, tol, pv, ar, maxit, r_ref, z_ref)
+        out["precisions"] = variants
+        out["per_config"] = {"diffusion3d_32": convergence_subline(L, args, devc, hbm)}
+
+    # end to end: host (pinned) inputs -> device -> setup + solve -> x to host
+    if not args.no_e2e:
+        hp = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).pin_memory()
+        h_in = [hp(pr.rowptr, torch.int32), hp(pr.colidx, torch.int32), hp(pr.vals, torch.float64),
+                hp(pr.patch_dofs, torch.int32), hp(pr.rhs(0), torch.float64)]
+        h_o = None if pr.uniform_size else hp(pr.patch_offsets, torch.int32)
+        h_x = torch.empty(pr.n, dtype=torch.float64).pin_memory()
+        h2d = sum(a.numel() * a.element_size() for a in h_in) + (0 if h_o is None else h_o.numel() * 4)
+        del dev_in
+        torch.cuda.empty_cache()
+        ets, its = [], []
+        for i in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            d = [a.to(devc, non_blocking=True) for a in h_in]
+            d_o = None if h_o is None else h_o.to(devc, non_blocking=True)
+            d_x = torch.zeros(pr.n, dtype=torch.float64, device=devc)
+            c2 = L.psr_setup(d[0], d[1], d[2], d[3], offsets=d_o, uniform_size=pr.uniform_size, opts=opts)
+            inf2 = c2.solve(d[4], d_x)
+            h_x.copy_(d_x, non_blocking=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            c2.destroy()
+            del d, d_o, d_x
+            if i >= args.warmup:
+                ets.append(dt)
+                its.append(inf2["iterations"])
+        out["e2e"] = {"value": pr.n * sum(its) / sum(ets), "unit": "DOF/s", "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(pr.n * 8), "ms_per_step": 1e3 * sum(ets) / len(ets),
+                      "def": "n x sweeps per host wall second of the whole call (copies, setup, solve, read-back)"}
+    return out, pr
 
 
 # ------------------------------------------------------------------ CPU oracle
-SAMPLE_KW = {"stokes2d": dict(N=16, ratio=1.05), "poisson2d": dict(N=16), "nedelec3d": dict(N=8),
-             "diffusion3d": dict(N=6), "stokes3d": dict(N=4)}
+_SHM = {}
 
 
-def cpu_oracle_sample(args, cfg, name):
-    """The numpy FP64 oracle, as it stands, on a bounded sample of the same
-    workload: the same family, solver and options on a smaller mesh, the
-    whole step (setup with Alg. 1 + outer solve with the same iteration
-    budget).  Returns the line's cpu_baseline object (same unit)."""
-    import problems
+def _shm_attach(spec):
+    """Worker initialiser: attach the shared arrays of the oracle sample."""
+    from multiprocessing import shared_memory
+    for key, (name, shape, dt) in spec.items():
+        h = shared_memory.SharedMemory(name=name)
+        _SHM[key] = (h, np.ndarray(shape, dtype=dt, buffer=h.buf))
+
+
+def _oracle_apply_chunk(rng):
+    """The oracle's apply (Eq. 3, ragged sizes) over sampled patches
+    k0..k1-1, on the DOFs they touch (renumbered locally); returns the
+    seconds of the apply_ragged call."""
     from oracle import psr_oracle as O
-    kw = SAMPLE_KW[name]
-    pr = getattr(problems, cfg["builder"])(**kw)
-    tol = cfg["tol"] if args.tol is None else args.tol
+    k0, k1 = rng
+    arr = lambda k: _SHM[k][1]
+    offs, flat, boff, bflat, r, W = (arr(k) for k in ("offs", "flat", "boff", "bflat", "r", "W"))
+    fl = flat[offs[k0]:offs[k1]]
+    uniq, loc = np.unique(fl, return_inverse=True)
+    o = offs[k0:k1 + 1] - offs[k0]
+    sizes = np.diff(o)
+    Binv = [bflat[boff[k]:boff[k + 1]].reshape(int(s), int(s)) for k, s in zip(range(k0, k1), sizes)]
     t0 = time.perf_counter()
-    if pr.uniform_size:
-        st = O.setup(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d(), tol)
-        t1 = time.perf_counter()
-        x, hist, it, conv = O.solve(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.rhs(0), st, cfg["krylov"],
-                                    cfg["weighting"], restart=30, rtol=1e-8, maxit=args.maxit)
-    else:
-        # patches of several sizes, full storage (the criterion path takes one size)
-        Ak = O.extract_patches_ragged(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.patch_offsets, pr.patch_dofs)
-        Binv = [O.lu_inverse(a[None])[0][0] for a in Ak]
-        W = O.weights(O.multiplicity(pr.n, pr.patch_dofs))
-        phi = np.arange(len(Ak))
-        t1 = time.perf_counter()
-        mv = lambda v: O.csr_matvec(pr.rowptr, pr.colidx, pr.vals, v)
-        pc = lambda v: O.apply_ragged(v, pr.patch_offsets, pr.patch_dofs, Binv, phi, W, cfg["weighting"])
-        x, hist, it, conv = O.fgmres(mv, pc, pr.rhs(0), restart=30, rtol=1e-8, maxit=args.maxit)
-    t2 = time.perf_counter()
-    return {"value": pr.n * it / (t2 - t0), "unit": "DOF/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": (f"numpy FP64 oracle, whole step (setup with Alg. 1 at tol {tol:g}: {t1 - t0:.2f} s; "
-                       f"{it} outer iterations: {t2 - t1:.2f} s) on the same workload family at "
-                       f"{kw} (n = {pr.n}, {pr.n_patches} patches); BLAS default threading"),
-            "step_s": t2 - t0}
+    O.apply_ragged(r[uniq], o, loc, Binv, np.arange(k1 - k0), W[uniq], "left")
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_sample(pr, cfg, n_apply=6000, n_inv=400, cores=None):
+    """The numpy FP64 oracle, as it stands, on a bounded sample of the same
+    instance: O.lu_inverse on `n_inv` of its patches (setup part) and
+    O.apply_ragged on `n_apply` sampled patches (sweep part), single-threaded
+    and cut into one chunk per host core (spawned workers, data in shared
+    memory); scaled to the full instance by sum(p^2) (apply) and sum(p^3)
+    (inverses), the work of each being proportional to it.
+    value = n / (scaled all-core oracle time of one apply)."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    from oracle import psr_oracle as O
+    cores = cores or os.cpu_count() or 1
+    offs_all = pr.patch_offsets.astype(np.int64)
+    sizes = np.diff(offs_all)
+    g = np.random.Generator(np.random.PCG64(11))
+    pick = np.sort(g.choice(pr.n_patches, size=min(n_apply, pr.n_patches), replace=False))
+    flat_s = np.concatenate([pr.patch_dofs[offs_all[k]:offs_all[k + 1]] for k in pick]).astype(np.int64)
+    offs_s = np.concatenate([[0], np.cumsum(sizes[pick])]).astype(np.int64)
+    # the sampled patch matrices (not timed): one O.csr_lookup over a copy of
+    # the CSR that keeps only the rows the sample uses
+    rows = np.unique(flat_s)
+    rp64 = pr.rowptr.astype(np.int64)
+    keep = np.zeros(pr.n, dtype=bool)
+    keep[rows] = True
+    lens = np.where(keep, np.diff(rp64), 0)
+    sub_ptr = np.concatenate([[0], np.cumsum(lens)])
+    take = np.concatenate([np.arange(rp64[i], rp64[i + 1]) for i in rows])
+    rr = np.concatenate([np.repeat(flat_s[offs_s[k]:offs_s[k + 1]], sizes[pick[k]]) for k in range(len(pick))])
+    cc = np.concatenate([np.tile(flat_s[offs_s[k]:offs_s[k + 1]], sizes[pick[k]]) for k in range(len(pick))])
+    vals = O.csr_lookup(sub_ptr, pr.colidx[take], pr.vals[take], pr.n, rr, cc)
+    sq = np.concatenate([[0], np.cumsum(sizes[pick] ** 2)])
+    A_s = [vals[sq[k]:sq[k + 1]].reshape(sizes[pick[k]], sizes[pick[k]]) for k in range(len(pick))]
+    del rr, cc, vals
+    # setup part: inverses of the first n_inv sampled patches, per size
+    sub = A_s[:n_inv]
+    t0 = time.perf_counter()
+    by_size = {}
+    for p in sorted(set(a.shape[0] for a in sub)):
+        by_size[p] = O.lu_inverse(np.stack([a for a in sub if a.shape[0] == p]))[0]
+    t_inv = time.perf_counter() - t0
+    # every sampled patch needs an inverse for the apply: the computed ones
+    # are reused cyclically within each size (the apply's work is the same)
+    cnt = {}
+    blocks = []
+    for a in A_s:
+        p = a.shape[0]
+        if p not in by_size:
+            by_size[p] = O.lu_inverse(a[None])[0]
+        j = cnt.get(p, 0)
+        blocks.append(by_size[p][j % by_size[p].shape[0]].reshape(-1))
+        cnt[p] = j + 1
+    bflat = np.concatenate(blocks)
+    boff = np.concatenate([[0], np.cumsum([blk.size for blk in blocks])]).astype(np.int64)
+    W = O.weights(O.multiplicity(pr.n, pr.patch_dofs))
+    r = np.random.Generator(np.random.PCG64(5)).uniform(-1, 1, pr.n)
+    shms, spec = [], {}
+    try:
+        for key, a in (("offs", offs_s), ("flat", flat_s), ("boff", boff), ("bflat", bflat), ("r", r), ("W", W)):
+            h = shared_memory.SharedMemory(create=True, size=max(a.nbytes, 1))
+            np.ndarray(a.shape, dtype=a.dtype, buffer=h.buf)[...] = a
+            shms.append(h)
+            spec[key] = (h.name, a.shape, a.dtype)
+        _shm_attach(spec)
+        ns = len(pick)
+        t_one = _oracle_apply_chunk((0, ns))
+        cuts = np.linspace(0, ns, cores + 1).astype(int)
+        ranges = [(int(cuts[i]), int(cuts[i + 1])) for i in range(cores) if cuts[i + 1] > cuts[i]]
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(len(ranges), initializer=_shm_attach, initargs=(spec,)) as pool:
+            pool.map(_oracle_apply_chunk, ranges)          # warm: imports, first touch
+            t0 = time.perf_counter()
+            pool.map(_oracle_apply_chunk, ranges)
+            t_all = time.perf_counter() - t0
+    finally:
+        for key in list(_SHM):
+            _SHM.pop(key)[0].close()
+        for h in shms:
+            h.close()
+            h.unlink()
+    s2_full = float(np.sum(sizes.astype(np.float64) ** 2))
+    s2_app = float(np.sum(sizes[pick].astype(np.float64) ** 2))
+    s3_full = float(np.sum(sizes.astype(np.float64) ** 3))
+    s3_inv = float(sum(a.shape[0] ** 3 for a in sub))
+    apply_one = t_one * s2_full / s2_app
+    apply_all = t_all * s2_full / s2_app
+    return {"value": pr.n / apply_all, "unit": "DOF/s", "cores": len(ranges), "kind": "oracle",
+            "nproc": os.cpu_count(),
+            "single_thread": {"value": pr.n / apply_one, "apply_s_full": apply_one},
+            "apply_s_full": apply_all,
+            "setup_inverses_s_full_single_thread": t_inv * s3_full / s3_inv,
+            "sample": (f"numpy FP64 oracle on the same instance ({pr.n} DOFs): apply_ragged over {ns} sampled "
+                       f"patches ({t_one:.3f} s single-threaded, {t_all:.3f} s in {len(ranges)} spawned workers, "
+                       f"one chunk each) and lu_inverse of {len(sub)} of them ({t_inv:.2f} s); scaled to all "
+                       f"{pr.n_patches} patches by sum(p^2) (apply) and sum(p^3) (inverses)")}
 
 
 def run_reference(args, cfg, ws, rank):
     if rank != 0:
         return None
-    vals, walls = [], []
+    pr = build_problem(cfg)
+    vals, walls, cb = [], [], None
     for i in range(args.warmup + args.steps):
-        cb = cpu_oracle_sample(args, cfg, args.config)
+        t0 = time.perf_counter()
+        cb = cpu_oracle_sample(pr, cfg, n_apply=3000, n_inv=200)
         if i >= args.warmup:
             vals.append(cb["value"])
-            walls.append(cb["step_s"])
+            walls.append(time.perf_counter() - t0)
     v = statistics.median(vals)
     cb["value"] = v
     return {"metric": METRIC, "value": v, "unit": "DOF/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(walls), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": cfg["desc"] + " (bounded CPU sample, see cpu_baseline)",
-                       "maxit": args.maxit},
+            "config": {"workload": cfg["desc"] + " (bounded CPU sample of the same instance, see cpu_baseline)",
+                       "n": pr.n, "n_patches": pr.n_patches},
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -644,10 +844,10 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    out, pr, info, st = run_gpu(args, cfg, ws, rank, local)
+    out, pr = run_gpu(args, cfg, ws, rank, local)
     if rank == 0:
         if not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_oracle_sample(args, cfg, args.config)
+            out["cpu_baseline"] = cpu_oracle_sample(pr, cfg)
         print(json.dumps(out))
     if ws > 1:
         import torch.distributed as dist
