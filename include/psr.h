@@ -123,7 +123,8 @@ typedef struct {
     int32_t sweep_kernel; /* PSR_SWEEP_*                                          */
     int32_t autotune;     /* 1: time candidate sweep tile shapes at setup         */
     int32_t symmetrize;   /* 1: store (B^-1 + B^-T)/2 before rounding to FP32/BF16 */
-    int32_t use_mlp;      /* 1: verify MLP-predicted representatives first (needs psr_mlp_attach) */
+    int32_t use_mlp;      /* psr_setup_learned: 1 = verify the trained network's
+                             predicted entries first (the other setups ignore it)  */
     int32_t ortho;        /* PSR_ORTHO_* (FGMRES only)                            */
     int32_t criterion;    /* PSR_CRITERION_* of Alg. 1 (L1: psr_setup only)        */
     int32_t fp64_arith;   /* PSR_FP64_* arithmetic of the FP64 full-storage sweep  */
@@ -328,6 +329,24 @@ int psr_detect_patches(const psr_csr* A, int32_t row_nnz, int32_t* dofs, int32_t
  * use by live contexts are not touched).  Returns PSR_OK or PSR_ERR_CUDA. */
 int psr_release_cached_memory(void);
 
+/* Fault injection for tests of the failure paths (the paper has no
+ * counterpart).  Nothing here makes a GPU fault: the failures are made on
+ * the host or by a bounded wait that runs out.
+ *   PSR_INJECT_ALLOC_FAIL, value k >= 1: the k-th next device allocation of
+ *     the library (counted from this call, 1 = the next) fails as if the
+ *     device were out of memory, without a driver call; the call that made
+ *     it returns PSR_ERR_OOM and frees what it held.  0 disables.
+ *   PSR_INJECT_BARRIER_WAIT, value s >= 1: the grid barriers of the Alg. 1
+ *     rounds kernel launched on the current device from now on wait for one
+ *     block more than the grid holds and give up after s spins (about
+ *     s x 32 ns); every block then leaves the kernel and the setup returns
+ *     PSR_ERR_TIMEOUT.  0 restores the normal barrier (limit 2^24 spins).
+ * Returns PSR_OK, PSR_ERR_INVALID_ARG (unknown kind, negative value) or
+ * PSR_ERR_CUDA (PSR_INJECT_BARRIER_WAIT without a device). */
+#define PSR_INJECT_ALLOC_FAIL   1
+#define PSR_INJECT_BARRIER_WAIT 2
+int psr_debug_inject(int32_t what, int64_t value);
+
 /* Instrumentation: number of CUDA kernels this library has launched in the
  * process so far (a graph launch counts its kernel nodes).  Host-only, never
  * fails; used by benchmarks to state how many kernels a timed region ran. */
@@ -466,6 +485,63 @@ int psr_mlp_train_step(psr_mlp* net, const float* X, const int32_t* y, int32_t b
 int psr_mlp_predict(psr_mlp* net, const float* X, int32_t batch, int32_t* cls, float* logits,
                     void* stream);
 void psr_mlp_destroy(psr_mlp* net);
+
+/* ---- learned assignment inside setup (a network trained on a finished
+ * setup predicts the entries of a later one; the paper leaves deep-learning
+ * assisted clustering to future work, end of section 3.2) -------------- */
+
+#define PSR_LABEL_ASSIGNMENT 0      /* labels = the context's phi (closest-match phi when
+                                       the context was built with PSR_MATCH_CLOSEST) */
+
+typedef struct {
+    int32_t hidden;          /* hidden width h of the d -> h -> h -> m_p network        */
+    int32_t epochs;          /* full-batch Adam steps                                    */
+    float   lr;              /* Adam learning rate                                       */
+    float   train_fraction;  /* the first ceil(f n_patches) patches (patch order) train  */
+    uint64_t seed;           /* initial weights: N(0, 1/fan_in), biases 0, from this seed */
+} psr_train_opts;
+
+typedef struct {
+    int32_t n_train;         /* patches trained on                                        */
+    int32_t classes;         /* m_p of the context                                        */
+    float   final_loss;      /* mean cross-entropy after the last step                    */
+    float   train_accuracy;  /* fraction of training patches whose argmax is their label  */
+    double  seconds;         /* host wall time of the training (features included)        */
+} psr_train_info;
+
+/* Defaults: hidden 256, 300 epochs, lr 1e-3, train_fraction 1, seed 0. */
+void psr_default_train_opts(psr_train_opts* t);
+
+/* Trains a network owned by ctx to predict each patch's database entry.
+ * ctx: a setup built by Alg. 1 (tol > 0) with patches of one size p <= 32.
+ * Inputs: features (device, n_patches x (p*p + 2) FP32, as psr_features), or
+ * NULL to compute them from the context's patch matrices without a cell
+ * coefficient.  Labels: the context's phi (PSR_LABEL_ASSIGNMENT); build ctx
+ * with opts.match = PSR_MATCH_CLOSEST to train on closest representatives.
+ * The network (d = p*p + 2 -> hidden -> hidden -> m_p, ReLU, softmax) is
+ * trained on the GPU (forward and backward GEMMs on the tensor cores) and
+ * replaces an earlier one.  info (host) may be NULL.  Errors: INVALID_ARG,
+ * OOM, CUDA.  Blocks the host until done. */
+int psr_mlp_train(psr_ctx* ctx, const float* features_or_NULL, const psr_train_opts* t, void* stream,
+                  psr_train_info* info);
+
+/* The trained network of ctx (owned by ctx; NULL before psr_mlp_train), for
+ * psr_mlp_predict / psr_mlp_get_params. */
+psr_mlp* psr_ctx_mlp(psr_ctx* ctx);
+
+/* Setup whose Alg. 1 starts from the database of `trained` (its entries'
+ * patch matrices, inverted here) and, when opts->use_mlp is set, first tries
+ * for every patch the entry that trained's network predicts: one criterion
+ * evaluation, the patch assigned when d < tol; patches whose prediction
+ * fails (or all patches, use_mlp = 0) run Alg. 1 against the database in
+ * creation order and may append entries -- psr_setup_seeded with the
+ * network's predictions as hints.  features: device n_patches x (p*p + 2)
+ * FP32 of the new patches, or NULL (computed from the patch matrices without
+ * a cell coefficient).  Needs tol > 0 and patches of trained's size
+ * (p <= 32).  psr_get_stats reports the verified predictions in mlp_hits and
+ * the prediction time inside t_rounds.  Errors as psr_setup_seeded. */
+int psr_setup_learned(const psr_csr* A, const psr_patches* patches, const psr_opts* opts, const psr_ctx* trained,
+                      const float* features_or_NULL, void* stream, psr_ctx** out);
 
 #ifdef __cplusplus
 }

@@ -37,7 +37,8 @@ EXPORTS = ["psr_default_opts", "psr_setup", "psr_apply", "psr_solve", "psr_get_h
            "psr_mlp_get_params", "psr_mlp_loss_grad", "psr_mlp_train_step", "psr_mlp_predict", "psr_mlp_destroy",
            "psr_criterion_noalloc", "psr_set_kernel_timing", "psr_get_kernel_timing", "psr_setup_kmeans",
            "psr_export_database", "psr_set_coarse", "psr_smooth", "psr_release_cached_memory",
-           "psr_detect_patches", "psr_boundary_classes"]
+           "psr_detect_patches", "psr_boundary_classes", "psr_default_train_opts", "psr_mlp_train", "psr_ctx_mlp",
+           "psr_setup_learned", "psr_debug_inject"]
 
 KT_CLASSES = ("sweep", "spmv", "mdot", "maxpy", "vec")   # PSR_KT_* in order
 
@@ -65,6 +66,16 @@ class psr_opts(C.Structure):
                 ("autotune", C.c_int32), ("symmetrize", C.c_int32), ("use_mlp", C.c_int32),
                 ("ortho", C.c_int32), ("criterion", C.c_int32), ("fp64_arith", C.c_int32),
                 ("match", C.c_int32), ("seed", C.c_uint64)]
+
+
+class psr_train_opts(C.Structure):
+    _fields_ = [("hidden", C.c_int32), ("epochs", C.c_int32), ("lr", C.c_float), ("train_fraction", C.c_float),
+                ("seed", C.c_uint64)]
+
+
+class psr_train_info(C.Structure):
+    _fields_ = [("n_train", C.c_int32), ("classes", C.c_int32), ("final_loss", C.c_float),
+                ("train_accuracy", C.c_float), ("seconds", C.c_double)]
 
 
 class psr_csr_rect(C.Structure):
@@ -141,8 +152,16 @@ def load(path: str = LIB_PATH):
     lib.psr_mlp_train_step.argtypes = [vp, vp, vp, i32, C.c_float, vp, vp]
     lib.psr_mlp_predict.argtypes = [vp, vp, i32, vp, vp, vp]
     lib.psr_mlp_destroy.argtypes = [vp]
+    lib.psr_default_train_opts.argtypes = [C.POINTER(psr_train_opts)]
+    lib.psr_default_train_opts.restype = None
+    lib.psr_mlp_train.argtypes = [vp, vp, C.POINTER(psr_train_opts), vp, C.POINTER(psr_train_info)]
+    lib.psr_debug_inject.argtypes = [i32, i64]
+    lib.psr_ctx_mlp.argtypes = [vp]
+    lib.psr_ctx_mlp.restype = vp
+    lib.psr_setup_learned.argtypes = [C.POINTER(psr_csr), C.POINTER(psr_patches), C.POINTER(psr_opts), vp, vp, vp,
+                                      C.POINTER(vp)]
     void_ret = ("psr_default_opts", "psr_last_error", "psr_destroy", "psr_kernel_launches", "psr_mlp_num_params",
-                "psr_mlp_destroy")
+                "psr_mlp_destroy", "psr_default_train_opts", "psr_ctx_mlp")
     for name in EXPORTS:
         if name not in void_ret:
             getattr(lib, name).restype = C.c_int
@@ -305,6 +324,23 @@ class Context:
         _check(load().psr_export_database(self.h, _ptr(out), _stream(stream)), self.h)
         return out
 
+    def mlp_train(self, features=None, hidden=256, epochs=300, lr=1e-3, train_fraction=1.0, seed=0,
+                  stream=None) -> dict:
+        """psr_mlp_train: a network owned by the context learns its phi."""
+        t = psr_train_opts()
+        load().psr_default_train_opts(C.byref(t))
+        t.hidden, t.epochs, t.lr, t.train_fraction, t.seed = hidden, epochs, lr, train_fraction, seed
+        info = psr_train_info()
+        _check(load().psr_mlp_train(self.h, _ptr(features), C.byref(t), _stream(stream), C.byref(info)), self.h)
+        return {f: getattr(info, f) for f, _ in info._fields_}
+
+    def mlp(self) -> "MLP":
+        """The context's trained network (not owned by the returned view)."""
+        h = load().psr_ctx_mlp(self.h)
+        if not h:
+            raise ValueError("no trained network (psr_mlp_train)")
+        return MLP.view_of(C.c_void_p(h), self)
+
     def stats(self) -> dict:
         st = psr_stats()
         _check(load().psr_get_stats(self.h, C.byref(st)), self.h)
@@ -352,6 +388,21 @@ def psr_setup_seeded(rowptr, colidx, vals, dofs, uniform_size, seed_A, hints=Non
     return Context(h, A.n, P.n_patches, o, P.uniform_size)
 
 
+def psr_setup_learned(rowptr, colidx, vals, dofs, uniform_size, trained: "Context", opts: psr_opts | None = None,
+                      features=None, stream=None) -> "Context":
+    """Setup seeded with trained's database and (opts.use_mlp) its network's
+    predictions as hints."""
+    lib = load()
+    A = _csr(rowptr, colidx, vals)
+    P = _patches(dofs, None, uniform_size)
+    o = opts if opts is not None else make_opts()
+    h = C.c_void_p()
+    rc = lib.psr_setup_learned(C.byref(A), C.byref(P), C.byref(o), trained.h, _ptr(features), _stream(stream),
+                               C.byref(h))
+    _check(rc, None)
+    return Context(h, A.n, P.n_patches, o, P.uniform_size)
+
+
 def psr_setup_kmeans(rowptr, colidx, vals, dofs, uniform_size, init, max_iter=100, opts: psr_opts | None = None,
                      stream=None, patch_class=None) -> "Context":
     """Database by Alg. 2, entrywise k-means, seeded with the patches init
@@ -387,8 +438,19 @@ class MLP:
     def __init__(self, d, h, m):
         self.d, self.h, self.m = d, h, m
         self.ptr = C.c_void_p()
+        self.owner = None
         _check(load().psr_mlp_create(d, h, m, C.byref(self.ptr)))
         self.num_params = int(load().psr_mlp_num_params(self.ptr))
+
+    @classmethod
+    def view_of(cls, ptr, owner):
+        """A non-owning handle on a network that `owner` keeps alive."""
+        self = cls.__new__(cls)
+        self.ptr = ptr
+        self.owner = owner
+        self.num_params = int(load().psr_mlp_num_params(ptr))
+        self.d = self.h = self.m = None
+        return self
 
     def set_params(self, packed, stream=None):
         import torch
@@ -420,9 +482,9 @@ class MLP:
         return (cls, lg) if logits else cls
 
     def destroy(self):
-        if self.ptr:
+        if self.ptr and self.owner is None:
             load().psr_mlp_destroy(self.ptr)
-            self.ptr = None
+        self.ptr = None
 
     def __del__(self):
         try:
@@ -523,3 +585,14 @@ def exported_symbols(path: str = LIB_PATH) -> list[str]:
         except AttributeError:
             pass
     return found
+
+
+INJECT = {"alloc_fail": 1, "barrier_wait": 2}
+
+
+def psr_debug_inject(what: str, value: int) -> None:
+    """Fault injection for tests (psr_debug_inject): "alloc_fail" makes the
+    value-th next device allocation fail (0 disables); "barrier_wait" makes the
+    Alg. 1 rounds barriers wait for a block that never arrives, giving up
+    after value spins (0 restores)."""
+    _check(load().psr_debug_inject(INJECT[what], int(value)))

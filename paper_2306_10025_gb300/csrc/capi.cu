@@ -2,6 +2,8 @@
 // stateless single-step calls.  No C++ exception crosses this boundary.
 #include "psr_internal.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -45,6 +47,23 @@ __global__ void k_any(const int32_t* flags, int n, int32_t* first) {
         if (flags[i]) atomicMin(first, i);
 }
 
+// NVTX ranges around the setup phases (visible in a profiler timeline; no
+// cost without one).  The depth is tracked so a failing setup closes them.
+static thread_local int g_nvtx_depth = 0;
+static void phase_begin(const char* name) {
+    nvtxRangePushA(name);
+    ++g_nvtx_depth;
+}
+static void phase_end() {
+    if (g_nvtx_depth > 0) {
+        nvtxRangePop();
+        --g_nvtx_depth;
+    }
+}
+static void phases_close(int depth) {
+    while (g_nvtx_depth > depth) phase_end();
+}
+
 static double seconds_since(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
@@ -69,6 +88,7 @@ static void destroy_ctx(psr_ctx* ctx) {
     psr::dev_free(ctx->phi);
     psr::dev_free(ctx->rep_ids);
     psr::dev_free(ctx->status);
+    if (ctx->mlp) psr_mlp_destroy(ctx->mlp);
     if (cur != ctx->device) cudaSetDevice(cur);
     delete ctx;
 }
@@ -93,6 +113,8 @@ struct AssignMode {
     const std::vector<int32_t>* km_init = nullptr;
     int km_iter = 0;
     const std::vector<int32_t>* km_cls = nullptr;   // class of every patch (boundary partition) or null
+    psr_mlp* mlp = nullptr;          // predictions of this network become the hints
+    const float* features = nullptr; // its inputs (device) or null: computed from the patch matrices
 };
 
 static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o, cudaStream_t s, psr_ctx** out,
@@ -101,6 +123,8 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
     const int m0 = mode.m0;
     const int32_t* hints = mode.hints;
     auto t_all = std::chrono::steady_clock::now();
+    const int nvtx_base = g_nvtx_depth;
+    phase_begin("psr_setup");
     psr_ctx* ctx = new psr_ctx();
     *out = nullptr;
     if (o) ctx->opts = *o; else psr_default_opts(&ctx->opts);
@@ -184,6 +208,7 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
             if (ea != cudaSuccess) { cudaGetLastError(); set_error(ctx, "out of device memory for the patch matrices"); FAIL(PSR_ERR_OOM); }
         }
         // --- a1: extraction
+        phase_begin("psr_setup: extraction and weights");
         auto t0 = std::chrono::steady_clock::now();
         rc = launch_extract(ctx->rowptr, ctx->colidx, ctx->vals, ctx->offsets, ctx->dofs, ctx->mat_off, np,
                             0, total, ctx->A_ext, s);
@@ -213,6 +238,8 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
         rc = check_status(ctx, s);
         if (rc != PSR_OK) goto fail;
         ctx->stats.t_extract = seconds_since(t0);
+        phase_end();
+        phase_begin("psr_setup: database and inverses");
         // --- a2 / a3: database and assignment
         CK(psr::dev_alloc(&ctx->phi, sizeof(int32_t) * (size_t)np));
         // seed entries come on top of at most one new entry per patch
@@ -259,22 +286,46 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
             rc = run_alg1_l1(ctx, s);
             if (rc != PSR_OK) goto fail;
         } else {
+            int32_t* pred = nullptr;
+            if (mode.mlp) {
+                // learned assignment: the network's entry for every patch becomes its hint
+                const Group& G0 = ctx->groups[0];
+                const int d = G0.p * G0.p + 2;
+                float* X = nullptr;
+                CK(psr::dev_alloc(&pred, sizeof(int32_t) * (size_t)np));
+                const float* feat = mode.features;
+                if (!feat) {
+                    CK(psr::dev_alloc(&X, sizeof(float) * (size_t)np * d));
+                    rc = psr_features(ctx->A_ext + G0.mat_off, np, G0.p, nullptr, X, s);
+                    if (rc != PSR_OK) { psr::dev_free(X); psr::dev_free(pred); goto fail; }
+                    feat = X;
+                }
+                rc = psr_mlp_predict(mode.mlp, feat, np, pred, nullptr, s);
+                CK(cudaStreamSynchronize(s));
+                psr::dev_free(X);
+                if (rc != PSR_OK) { psr::dev_free(pred); goto fail; }
+                hints = pred;
+            }
             rc = run_alg1(ctx, s, seed_A, m0, hints);
+            psr::dev_free(pred);
             if (rc != PSR_OK) goto fail;
         }
         CK(cudaStreamSynchronize(s));
         ctx->stats.t_rounds = seconds_since(t0);
+        phase_end();
         if (ctx->stats.first_singular >= 0) {
             set_error(ctx, "patch " + std::to_string(ctx->stats.first_singular) +
                            " failed the pivot test |u_kk| <= p * 2^-53 * max|A_k| (singular)");
             FAIL(PSR_ERR_SINGULAR_PATCH);
         }
+        phase_begin("psr_setup: storage and sweep layout");
         t0 = std::chrono::steady_clock::now();
         rc = build_sweep_layout(ctx, gidx, s);
         if (rc != PSR_OK) goto fail;
         rc = sweep_prepare(ctx);
         if (rc != PSR_OK) goto fail;
         ctx->stats.t_convert = seconds_since(t0);
+        phase_end();
         // the patch matrices are no longer needed unless they hold the inverses
         {
             bool in_use = false;
@@ -290,20 +341,24 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
         }
         rc = krylov_alloc(ctx);
         if (rc != PSR_OK) goto fail;
+        phase_begin("psr_setup: sweep autotuner");
         t0 = std::chrono::steady_clock::now();
         rc = autotune_sweep(ctx, s);
         if (rc != PSR_OK) goto fail;
         CK(cudaStreamSynchronize(s));
         ctx->stats.t_autotune = seconds_since(t0);
+        phase_end();
         ctx->stats.n = n;
         ctx->stats.n_patches = np;
         ctx->stats.n_groups = (int)ctx->groups.size();
         (void)t_all;
         *out = ctx;
+        phases_close(nvtx_base);
         return PSR_OK;
     }
 fail:
     destroy_ctx(ctx);
+    phases_close(nvtx_base);
     return rc;
 #undef FAIL
 #undef CK
@@ -389,6 +444,48 @@ int psr_setup_seeded(const psr_csr* A, const psr_patches* patches, const psr_opt
         return setup_impl(A, patches, &o, (cudaStream_t)stream, out, mode);
     } catch (...) {
         set_error(nullptr, "unexpected host exception in psr_setup_seeded");
+        return PSR_ERR_CUDA;
+    }
+}
+
+int psr_setup_learned(const psr_csr* A, const psr_patches* patches, const psr_opts* opts, const psr_ctx* trained,
+                      const float* features, void* stream, psr_ctx** out) {
+    if (!out) { set_error(nullptr, "out is NULL"); return PSR_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (!trained || trained->groups.size() != 1 || !trained->groups[0].dbA || trained->m_p < 1) {
+        set_error(nullptr, "psr_setup_learned needs a trained context with a one-size database");
+        return PSR_ERR_INVALID_ARG;
+    }
+    const int p = trained->groups[0].p;
+    if (!A || !patches || !A->rowptr || !A->vals || !A->colidx || A->n <= 0 || patches->n_patches <= 0 ||
+        !patches->dofs || patches->uniform_size != p || p > 32) {
+        set_error(nullptr, "psr_setup_learned: uniform patches of the trained context's size (at most 32 DOFs)");
+        return PSR_ERR_INVALID_ARG;
+    }
+    psr_opts o;
+    if (opts) o = *opts; else psr_default_opts(&o);
+    if (!(o.tol > 0.0)) { set_error(nullptr, "a learned setup needs tol > 0"); return PSR_ERR_INVALID_ARG; }
+    if (o.use_mlp && (!trained->mlp || trained->mlp_classes != trained->m_p)) {
+        set_error(nullptr, "use_mlp: the trained context has no network for its database (psr_mlp_train)");
+        return PSR_ERR_INVALID_ARG;
+    }
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) {
+        cudaGetLastError();
+        set_error(nullptr, "no CUDA device: the library has no CPU fallback");
+        return PSR_ERR_CUDA;
+    }
+    try {
+        AssignMode mode;
+        mode.seed_A = trained->groups[0].dbA;
+        mode.m0 = trained->m_p;
+        if (o.use_mlp) {
+            mode.mlp = trained->mlp;
+            mode.features = features;
+        }
+        return setup_impl(A, patches, &o, (cudaStream_t)stream, out, mode);
+    } catch (...) {
+        set_error(nullptr, "unexpected host exception in psr_setup_learned");
         return PSR_ERR_CUDA;
     }
 }
@@ -625,6 +722,25 @@ int psr_criterion(const double* A_i, int32_t batch, int32_t p, const double* A_c
     int rc = launch_criterion_batch(A_i, batch, p, A_c, Binv_c, tol, accept, dval, work, s);
     cudaFreeAsync(work, s);
     return rc;
+}
+
+int psr_debug_inject(int32_t what, int64_t value) {
+    if (value < 0) { set_error(nullptr, "psr_debug_inject: negative value"); return PSR_ERR_INVALID_ARG; }
+    if (what == PSR_INJECT_ALLOC_FAIL) {
+        inject_alloc_fail((long long)value);
+        return PSR_OK;
+    }
+    if (what == PSR_INJECT_BARRIER_WAIT) {
+        int dev_count = 0;
+        if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) {
+            cudaGetLastError();
+            set_error(nullptr, "no CUDA device");
+            return PSR_ERR_CUDA;
+        }
+        return inject_barrier_wait((long long)value);
+    }
+    set_error(nullptr, "psr_debug_inject: unknown kind");
+    return PSR_ERR_INVALID_ARG;
 }
 
 int psr_spectral_norm(const double* E, int32_t batch, int32_t p, double* sigma, void* stream) {

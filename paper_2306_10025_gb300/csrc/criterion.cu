@@ -755,6 +755,12 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_round_decide(RoundDev* st, 
 }
 
 // ---------------------------------------------------------------- persistent rounds
+// Barrier settings of this translation unit: the arrivals beyond the grid a
+// barrier waits for (0; 1 only under psr_debug_inject, so that the wait runs
+// out) and the spin limit.
+static __device__ unsigned int g_bar_extra = 0u;
+static __device__ long long g_bar_limit = 1ll << 24;
+
 // Grid barrier of a cooperatively launched kernel (every block co-resident, so
 // every wait ends); bounded all the same: past the limit the error flag is
 // set and the barrier left, and the host reports PSR_ERR_TIMEOUT.
@@ -765,14 +771,15 @@ __device__ __forceinline__ void rounds_barrier(unsigned int* bar, int32_t* err) 
         volatile unsigned int* vgen = bar + 1;
         const unsigned int g = *vgen;
         const unsigned int arrived = atomicAdd(bar, 1u) + 1u;
-        if (arrived == gridDim.x) {
+        const long long limit = g_bar_limit;
+        if (arrived == gridDim.x + g_bar_extra) {
             bar[0] = 0u;
             __threadfence();
             atomicAdd(bar + 1, 1u);
         } else {
             long long spins = 0;
             while (*vgen == g) {
-                if (++spins > (1ll << 24)) {
+                if (++spins > limit) {
                     atomicExch(err, 1);
                     break;
                 }
@@ -854,6 +861,7 @@ __global__ void __launch_bounds__(EVAL_THREADS) k_rounds_persistent(
             if (open && !rej) surv_list[wb + __popc(surv & ((1u << lane) - 1u))] = cand;
         }
         rounds_barrier(bar, err);
+        if (*((volatile int*)err)) break;                 // a barrier gave up: leave before reading survivors
         if (blockIdx.x == 0 && threadIdx.x == 0) {        // the other parity is free again
             st->ns2[par ^ 1] = 0;
             st->nn2[par ^ 1] = count;
@@ -1047,6 +1055,110 @@ __global__ void k_verify_hints(RoundDev* st, int32_t* __restrict__ phi, int coun
     }
 }
 
+// sigma_max(E), E = (A_c - A_i) B_c^-1 computed in FP64 (lane r forms row r),
+// from the Jacobi eigenvalues of G = E^T E: the "small SVD" of the section 3
+// remark.  A_c, B_c: global (row stride p); ws.E: p x (p+1) shared.
+template <int PM>
+__device__ double exact_sigma_warp(const double* __restrict__ Ai, const double* __restrict__ Ac,
+                                   const double* __restrict__ B, int p, WarpScratch ws) {
+    const int lane = threadIdx.x & 31;
+    const bool act = lane < p;
+    const int ld = p + 1;
+    double e[PM];
+#pragma unroll
+    for (int j = 0; j < PM; ++j) e[j] = 0.0;
+    if (act) {
+        for (int k = 0; k < p; ++k) {
+            const double dk = Ac[lane * p + k] - Ai[lane * p + k];
+#pragma unroll
+            for (int j = 0; j < PM; ++j)
+                if (j < p) e[j] = fma(dk, B[k * p + j], e[j]);
+        }
+    }
+    // column j of E in lane j: read back through shared memory
+    __syncwarp();
+    if (act) {
+#pragma unroll
+        for (int j = 0; j < PM; ++j)
+            if (j < p) ws.E[lane * ld + j] = e[j];
+    }
+    __syncwarp();
+    double ecol[PM];
+#pragma unroll
+    for (int r = 0; r < PM; ++r) ecol[r] = (act && r < p) ? ws.E[r * ld + lane] : 0.0;
+    __syncwarp();
+    for (int k = 0; k < p; ++k) {
+        double g = 0.0;
+        for (int r = 0; r < p; ++r) g = fma(ecol[r], __shfl_sync(0xffffffffu, ecol[r], k), g);
+        if (act) ws.E[lane * ld + k] = g;
+    }
+    __syncwarp();
+    const double lam = jacobi_lambda_max_warp(ws.E, p, ld);
+    __syncwarp();
+    return sqrt(fmax(lam, 0.0));
+}
+
+// Closest-match variant of Alg. 1 (section 3.1): the entries are those of the
+// first-match rounds (an entry is created exactly when no entry passes, which
+// does not depend on which passing entry is taken), and patch i joins the
+// entry with the least d among the entries created before it that pass
+// (d < tol), the lowest index on ties.  Entries before its first match
+// failed already, so a warp per patch compares the first match j0 with the
+// later entries whose representative precedes i (certified decision first,
+// sigma_max by the Jacobi eigenvalues for those that pass).
+template <int PM>
+__global__ void __launch_bounds__(EVAL_THREADS) k_closest_pass(int count, int p, const double* __restrict__ Ag,
+                                                               const double* __restrict__ Ball,
+                                                               const double* __restrict__ fro_all,
+                                                               const double* __restrict__ w_all,
+                                                               const int32_t* __restrict__ rep_l, int m, double tol,
+                                                               int32_t* __restrict__ phi,
+                                                               unsigned long long* __restrict__ evals) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const int ld = p + 1;
+    double* wbase = reinterpret_cast<double*>(smem) + (size_t)wid * (p * ld + 64);
+    WarpScratch ws{wbase, wbase + p * ld, wbase + p * ld + 32};
+    const int64_t pp = (int64_t)p * p;
+    unsigned long long ev = 0;
+    for (int i = blockIdx.x * wpb + wid; i < count; i += gridDim.x * wpb) {
+        const int j0 = phi[i];
+        if (rep_l[j0] == i) continue;                   // a representative keeps its own entry
+        const double* Ai = Ag + (int64_t)i * pp;
+        int best = j0;
+        double bs = exact_sigma_warp<PM>(Ai, Ag + (int64_t)rep_l[j0] * pp, Ball + (int64_t)rep_l[j0] * pp, p, ws);
+        for (int j = j0 + 1; j < m && bs > 0.0; ++j) {
+            const int rj = rep_l[j];
+            if (rj > i) break;                          // entries are created in increasing patch order
+            const double* Ac = Ag + (int64_t)rj * pp;
+            const double* Bc = Ball + (int64_t)rj * pp;
+            double dv;
+            ++ev;
+            const int dec = decide_pair<PM>(Ai, Ac, Bc, p, p, fro_all[rj], tol, ws, &dv, true,
+                                            w_all + (int64_t)rj * PROBE_STRIDE, nullptr);
+            __syncwarp();
+            if (dec != 1) continue;
+            const double sj = (dv == 0.0) ? 0.0 : exact_sigma_warp<PM>(Ai, Ac, Bc, p, ws);
+            if (sj < bs) { bs = sj; best = j; }
+        }
+        if (lane == 0) phi[i] = best;
+        __syncwarp();
+    }
+    if (lane == 0 && ev) atomicAdd(evals, ev);
+}
+
+// psr_debug_inject(PSR_INJECT_BARRIER_WAIT, spins) on the current device.
+int inject_barrier_wait(long long spins) {
+    const unsigned int extra = spins > 0 ? 1u : 0u;
+    const long long limit = spins > 0 ? spins : (1ll << 24);
+    cudaError_t e = cudaMemcpyToSymbol(g_bar_extra, &extra, sizeof(extra));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_bar_limit, &limit, sizeof(limit));
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "barrier injection");
+    return PSR_OK;
+}
+
 static void launch_sketch(const double* A, const double* Binv, int count, int p, const double* X, double* den,
                           float* Y32, double* fa, double* rho, cudaStream_t s) {
     const int blocks = (count + 7) / 8;
@@ -1090,6 +1202,11 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         if (p > 32) {
             // block-per-candidate kernels (criterion_big.cu)
             if (m0 > 0) { set_error(ctx, "a seed database needs patches of at most 32 DOFs"); rc = PSR_ERR_INVALID_ARG; break; }
+            if (ctx->opts.match == PSR_MATCH_CLOSEST) {
+                set_error(ctx, "closest match handles patches of at most 32 DOFs");
+                rc = PSR_ERR_INVALID_ARG;
+                break;
+            }
             int fs = -1;
             rc = run_alg1_big(ctx, G, Ag, s, &total_evals, &total_exact, &total_screened, &fs);
             if (rc != PSR_OK) break;
@@ -1307,6 +1424,30 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         }
         if (rc != PSR_OK) break;
         G.m = h_st->m;
+        if (ctx->opts.match == PSR_MATCH_CLOSEST && G.m > 1) {
+            if (m0 > 0) { set_error(ctx, "closest match takes no seed database"); rc = PSR_ERR_INVALID_ARG; break; }
+            unsigned long long* cev = nullptr;
+            PSR_CUDA(ctx, psr::dev_alloc(&cev, sizeof(unsigned long long)));
+            PSR_CUDA(ctx, cudaMemsetAsync(cev, 0, sizeof(unsigned long long), s));
+            const size_t smem_c = (size_t)wpb * ((size_t)p * ld + 64) * 8;
+            const void* kf = (p <= 8) ? (const void*)k_closest_pass<8>
+                           : (p <= 16) ? (const void*)k_closest_pass<16> : (const void*)k_closest_pass<32>;
+            if ((rc = set_smem(kf, smem_c)) != PSR_OK) break;
+            const int cb = std::max(1, std::min((count + wpb - 1) / wpb, 152 * 8));
+            count_launch();
+            if (p <= 8)
+                k_closest_pass<8><<<cb, EVAL_THREADS, smem_c, s>>>(count, p, Ag, Ball, fro_all, w_all, rep_l, G.m, tol, phi_l, cev);
+            else if (p <= 16)
+                k_closest_pass<16><<<cb, EVAL_THREADS, smem_c, s>>>(count, p, Ag, Ball, fro_all, w_all, rep_l, G.m, tol, phi_l, cev);
+            else
+                k_closest_pass<32><<<cb, EVAL_THREADS, smem_c, s>>>(count, p, Ag, Ball, fro_all, w_all, rep_l, G.m, tol, phi_l, cev);
+            PSR_CHECK_LAUNCH(ctx, "closest-match pass");
+            unsigned long long h_cev = 0;
+            PSR_CUDA(ctx, cudaMemcpyAsync(&h_cev, cev, sizeof(h_cev), cudaMemcpyDeviceToHost, s));
+            PSR_CUDA(ctx, cudaStreamSynchronize(s));
+            psr::dev_free(cev);
+            total_evals += (int64_t)h_cev;
+        }
         total_evals += (int64_t)h_st->evals;
         total_exact += (int64_t)h_st->exact;
         total_screened += (int64_t)h_st->screened;

@@ -16,6 +16,8 @@
 // |g_{j+1}| / ||r_0|| as in the FP64 reference formulation.
 #include "psr_internal.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -1745,7 +1747,17 @@ static int enqueue_fg_cycle(psr_ctx* ctx, KDims kd, cudaStream_t s) {
     return PSR_OK;
 }
 
+static int krylov_solve_impl(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_solve_info* info);
+
+// The outer solve inside one NVTX range (visible in a profiler timeline).
 int krylov_solve(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_solve_info* info) {
+    nvtxRangePushA("psr_solve");
+    const int rc = krylov_solve_impl(ctx, b, x, s, info);
+    nvtxRangePop();
+    return rc;
+}
+
+static int krylov_solve_impl(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_solve_info* info) {
     KrylovWS& w = ctx->ws;
     const int n = ctx->n, nb = w.nblk;
     const bool cg = ctx->opts.krylov == PSR_KRYLOV_CG;

@@ -21,6 +21,7 @@
 // psr_release_cached_memory() returns all cached blocks to the driver.
 #include "psr_internal.cuh"
 
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <unordered_map>
@@ -74,8 +75,15 @@ void release_all(Pool& P, bool host) {
     P.cached_bytes = 0;
 }
 
+// Injected failure (psr_debug_inject): the countdown's last device
+// allocation fails as if the device were out of memory.
+std::atomic<long long> g_fail_countdown{0};
+
 cudaError_t alloc_impl(void** p, size_t bytes, bool host) {
     *p = nullptr;
+    if (!host && g_fail_countdown.load(std::memory_order_relaxed) > 0 &&
+        g_fail_countdown.fetch_sub(1, std::memory_order_relaxed) == 1)
+        return cudaErrorMemoryAllocation;
     int d = 0;
     cudaGetDevice(&d);
     const size_t n = round_up(bytes);
@@ -143,6 +151,8 @@ cudaError_t free_impl(void* p, bool host) {
 }
 
 }  // namespace
+
+void inject_alloc_fail(long long k) { g_fail_countdown.store(k, std::memory_order_relaxed); }
 
 cudaError_t dev_alloc(void** p, size_t bytes) { return alloc_impl(p, bytes, false); }
 cudaError_t dev_free(void* p) { return free_impl(p, false); }

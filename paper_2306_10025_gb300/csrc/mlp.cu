@@ -10,6 +10,9 @@
 #include "psr_internal.cuh"
 
 #include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <random>
 #include <vector>
 
 struct psr_mlp {
@@ -390,6 +393,112 @@ int psr_features(const double* A, int32_t n_patches, int32_t p, const double* co
     k_features<<<blocks, 256, 0, (cudaStream_t)stream>>>(A, n_patches, p, coef, X);
     PSR_CUDA(nullptr, cudaGetLastError());
     return PSR_OK;
+}
+
+void psr_default_train_opts(psr_train_opts* t) {
+    if (!t) return;
+    t->hidden = 256;
+    t->epochs = 300;
+    t->lr = 1e-3f;
+    t->train_fraction = 1.0f;
+    t->seed = 0;
+}
+
+psr_mlp* psr_ctx_mlp(psr_ctx* ctx) { return ctx ? ctx->mlp : nullptr; }
+
+int psr_mlp_train(psr_ctx* ctx, const float* features, const psr_train_opts* topts, void* stream,
+                  psr_train_info* info) {
+    using namespace psr;
+    if (!ctx) { set_error(nullptr, "ctx is NULL"); return PSR_ERR_INVALID_ARG; }
+    psr_train_opts t;
+    if (topts) t = *topts; else psr_default_train_opts(&t);
+    if (ctx->groups.size() != 1 || ctx->groups[0].p > 32 || !ctx->groups[0].dbA || ctx->m_p < 1 || t.hidden < 1 ||
+        t.epochs < 0 || !(t.lr > 0.f) || !(t.train_fraction > 0.f) || t.train_fraction > 1.f) {
+        set_error(ctx, "psr_mlp_train needs a one-size (p <= 32) setup with a database and valid training options");
+        return PSR_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const auto t0 = std::chrono::steady_clock::now();
+    const int p = ctx->groups[0].p;
+    const int n = ctx->n_patches;
+    const int d = p * p + 2;
+    const int n_train = std::max(1, std::min(n, (int)std::ceil((double)t.train_fraction * n)));
+    float* X = nullptr;
+    double* A = nullptr;
+    float* loss = nullptr;
+    int32_t* pred = nullptr;
+    psr_mlp* net = nullptr;
+    auto done = [&](int rc) {
+        psr::dev_free(X);
+        psr::dev_free(A);
+        psr::dev_free(loss);
+        psr::dev_free(pred);
+        if (rc != PSR_OK && net) psr_mlp_destroy(net);
+        return rc;
+    };
+    if (!features) {
+        // features from the context's patch matrices (extracted again from its CSR and map copies)
+        if (psr::dev_alloc(&A, sizeof(double) * (size_t)n * p * p) != cudaSuccess ||
+            psr::dev_alloc(&X, sizeof(float) * (size_t)n * d) != cudaSuccess) {
+            cudaGetLastError();
+            set_error(ctx, "out of device memory for the training features");
+            return done(PSR_ERR_OOM);
+        }
+        int rc = launch_extract(ctx->rowptr, ctx->colidx, ctx->vals, ctx->offsets, ctx->dofs, ctx->mat_off, n, 0,
+                                (int64_t)n * p, A, s);
+        if (rc != PSR_OK) return done(rc);
+        if ((rc = psr_features(A, n, p, nullptr, X, stream)) != PSR_OK) return done(rc);
+        features = X;
+    }
+    int rc = psr_mlp_create(d, t.hidden, ctx->m_p, &net);
+    if (rc != PSR_OK) { net = nullptr; return done(rc); }
+    {
+        // initial weights N(0, 1/fan_in), biases 0 (host generator from the seed)
+        std::vector<float> w((size_t)net->np, 0.f);
+        std::mt19937_64 gen(t.seed);
+        std::normal_distribution<double> nd(0.0, 1.0);
+        MlpView v = view(w.data(), d, t.hidden, ctx->m_p);
+        auto fill = [&](float* W, int64_t cnt, int fan_in) {
+            const double sc = 1.0 / std::sqrt((double)fan_in);
+            for (int64_t i = 0; i < cnt; ++i) W[i] = (float)(nd(gen) * sc);
+        };
+        fill(v.W1, (int64_t)t.hidden * d, d);
+        fill(v.W2, (int64_t)t.hidden * t.hidden, t.hidden);
+        fill(v.W3, (int64_t)ctx->m_p * t.hidden, t.hidden);
+        PSR_CUDA(ctx, cudaMemcpyAsync(net->grads, w.data(), (size_t)net->np * 4, cudaMemcpyHostToDevice, s));
+        if ((rc = psr_mlp_set_params(net, net->grads, stream)) != PSR_OK) return done(rc);
+        PSR_CUDA(ctx, cudaStreamSynchronize(s));
+    }
+    if (psr::dev_alloc(&loss, sizeof(float)) != cudaSuccess || psr::dev_alloc(&pred, sizeof(int32_t) * n_train) != cudaSuccess) {
+        cudaGetLastError();
+        set_error(ctx, "out of device memory for the training state");
+        return done(PSR_ERR_OOM);
+    }
+    for (int e = 0; e < t.epochs; ++e)
+        if ((rc = psr_mlp_train_step(net, features, ctx->phi, n_train, t.lr, loss, stream)) != PSR_OK) return done(rc);
+    if ((rc = psr_mlp_predict(net, features, n_train, pred, nullptr, stream)) != PSR_OK) return done(rc);
+    std::vector<int32_t> hp(n_train), hy(n_train);
+    float hl = 0.f;
+    PSR_CUDA(ctx, cudaMemcpyAsync(hp.data(), pred, sizeof(int32_t) * n_train, cudaMemcpyDeviceToHost, s));
+    PSR_CUDA(ctx, cudaMemcpyAsync(hy.data(), ctx->phi, sizeof(int32_t) * n_train, cudaMemcpyDeviceToHost, s));
+    PSR_CUDA(ctx, cudaMemcpyAsync(&hl, loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+    PSR_CUDA(ctx, cudaStreamSynchronize(s));
+    int32_t herr = 0;
+    PSR_CUDA(ctx, cudaMemcpy(&herr, net->tc_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (herr) { set_error(ctx, "a tensor-core GEMM wait gave up during training"); return done(PSR_ERR_TIMEOUT); }
+    int hits = 0;
+    for (int i = 0; i < n_train; ++i) hits += hp[i] == hy[i];
+    if (ctx->mlp) psr_mlp_destroy(ctx->mlp);
+    ctx->mlp = net;
+    ctx->mlp_classes = ctx->m_p;
+    if (info) {
+        info->n_train = n_train;
+        info->classes = ctx->m_p;
+        info->final_loss = t.epochs > 0 ? hl : 0.f;
+        info->train_accuracy = (float)hits / (float)n_train;
+        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return done(PSR_OK);
 }
 
 }  // extern "C"

@@ -42,6 +42,8 @@ cudaError_t dev_alloc(void** p, size_t bytes);
 cudaError_t dev_free(void* p);
 cudaError_t host_alloc(void** p, size_t bytes);
 cudaError_t host_free(void* p);
+void inject_alloc_fail(long long k);      // psr_debug_inject(PSR_INJECT_ALLOC_FAIL, k)
+int inject_barrier_wait(long long spins); // criterion.cu
 template <class T>
 inline cudaError_t dev_alloc(T** p, size_t bytes) { return dev_alloc(reinterpret_cast<void**>(p), bytes); }
 template <class T>
@@ -208,6 +210,9 @@ struct psr_ctx {
     int64_t kt_n[PSR_KT_COUNT] = {};
     double kt_bytes[PSR_KT_COUNT] = {};
     double kt_flops[PSR_KT_COUNT] = {};
+    // learned assignment: network trained on this setup (psr_mlp_train)
+    psr_mlp* mlp = nullptr;
+    int32_t mlp_classes = 0;      // its output width (the m_p it was trained for)
 };
 
 namespace psr {

@@ -61,3 +61,18 @@ def test_compute_without_gpu_fails_loudly():
     assert lib.psr_boundary_classes(None, C.byref(P_), None, C.byref(cnt), None) == -1
     big = L.binding.psr_patches(1, 65, None, 8)               # more than 64 DOFs per patch
     assert lib.psr_boundary_classes(C.byref(A), C.byref(big), C.c_void_p(8), C.byref(cnt), None) == -1
+
+
+def test_debug_inject_arguments_without_device():
+    """The allocation-failure injection is host state (accepted without a
+    device); unknown kinds and negative values are rejected; the barrier
+    injection needs a device."""
+    import paper_2306_10025_gb300 as L
+    lib = L.load()
+    assert lib.psr_debug_inject(1, 3) == 0
+    assert lib.psr_debug_inject(1, 0) == 0
+    assert lib.psr_debug_inject(7, 1) == -1
+    assert lib.psr_debug_inject(1, -1) == -1
+    import torch
+    if not torch.cuda.is_available():
+        assert lib.psr_debug_inject(2, 100) == -5

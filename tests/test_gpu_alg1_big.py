@@ -173,3 +173,39 @@ def test_clustered_big_apply_vs_oracle(lib, prec):
         zr = O.apply_ragged(rv, pr.patch_offsets, pr.patch_dofs, db, phi, W, "left")
         err = np.abs(z.cpu().numpy() - zr).max() / np.abs(zr).max()
         assert err < (1e-12 if prec == "fp64" else 2e-5), err
+
+
+CLOSEST_CASES = [("diff3d", lambda: P.diffusion3d_q2(4, sigma=0.5, corr_len=3.0, seed=1), 1.0),
+                 ("diff3d_b", lambda: P.diffusion3d_q2(4, sigma=1.0, corr_len=2.0, seed=2), 0.8),
+                 ("diff3d_b_tight", lambda: P.diffusion3d_q2(4, sigma=1.0, corr_len=2.0, seed=2), 0.3),
+                 ("nedelec", lambda: P.nedelec3d(4, seed=5), 1.5),
+                 ("stokes", lambda: P.stokes2d_q2q1(8, 1.05), 5.0),
+                 ("poisson", lambda: P.poisson2d_q2(8), 1e-12)]
+
+
+@pytest.mark.parametrize("name,make,tol", CLOSEST_CASES)
+def test_closest_match_bit_exact(lib, name, make, tol):
+    """opts.match = closest (section 3.1 variant): the representatives are
+    Alg. 1's, phi the oracle's alg1_closest_match."""
+    pr = make()
+    A = O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d())
+    ref = O.alg1_closest_match(A, tol)
+    assert ref["near_ties"] == []
+    first = O.alg1(A, tol)
+    ctx = ctx_for(lib, pr, tol=tol, weighting=pr.weighting, krylov=pr.krylov, match="closest")
+    phi, reps, m = ctx.assignment()
+    assert np.array_equal(reps.cpu().numpy(), ref["reps"])
+    assert np.array_equal(phi.cpu().numpy(), ref["phi"])
+    assert ctx.stats()["criterion_evals"] >= first["evals"]
+    ctx.destroy()
+
+
+def test_closest_match_differs_from_first_match_somewhere(lib):
+    """The chosen cases are not vacuous: on them the two rules give
+    different maps (12, 9, 1 and 10 patches move)."""
+    moved = 0
+    for name, make, tol in CLOSEST_CASES:
+        pr = make()
+        A = O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d())
+        moved += int((O.alg1(A, tol)["phi"] != O.alg1_closest_match(A, tol)["phi"]).sum())
+    assert moved >= 30

@@ -174,3 +174,59 @@ def test_hinted_alg1_bit_exact_and_gain(lib):
     dbA = np.concatenate([seed_A, A[[r for r in ref["reps"] if r >= 0]]])
     dvals = O.criterion(A, dbA[ref["phi"]], Bi)
     assert np.all(dvals < tol)
+
+
+def test_learned_setup_through_the_abi(lib):
+    """psr_mlp_train + psr_setup_learned: a context built with closest-match
+    labels trains its network on the GPU on the first half of its patches; a
+    setup seeded with that context's database and hinted by its network
+    (opts.use_mlp = 1) equals the oracle's hinted Alg. 1 given the same
+    predictions, and needs fewer criterion evaluations than the same setup
+    with use_mlp = 0 (which equals the unhinted oracle)."""
+    pr, A = _c4_small()
+    tol = 0.3
+    p = pr.uniform_size
+    rp, ci, va = dev(pr.rowptr, torch.int32), dev(pr.colidx, torch.int32), dev(pr.vals, torch.float64)
+    dofs = dev(pr.patch_dofs, torch.int32)
+    train = lib.psr_setup(rp, ci, va, dofs, uniform_size=p,
+                          opts=lib.make_opts(tol=tol, weighting="sym", krylov="cg", match="closest"))
+    closest = O.alg1_closest_match(A, tol)
+    assert closest["near_ties"] == []
+    phi_t, reps_t, m0 = train.assignment()
+    assert np.array_equal(phi_t.cpu().numpy(), closest["phi"])
+    info = train.mlp_train(hidden=64, epochs=300, lr=3e-3, train_fraction=0.5, seed=5)
+    assert info["n_train"] == (pr.n_patches + 1) // 2 and info["classes"] == m0
+    assert info["train_accuracy"] > 2.0 / m0                 # better than chance
+    # the predictions the library uses: its network on its features (no coefficient)
+    X = torch.empty(pr.n_patches, p * p + 2, dtype=torch.float32, device="cuda")
+    lib.psr_features(dev(A, torch.float64), None, X)
+    pred = train.mlp().predict(X).cpu().numpy()
+    seed_A = train.export_database().cpu().numpy()
+    assert np.array_equal(seed_A, A[closest["reps"]])
+    out = {}
+    for use in (False, True):
+        ctx = lib.psr_setup_learned(rp, ci, va, dofs, p, train,
+                                    opts=lib.make_opts(tol=tol, weighting="sym", krylov="cg", use_mlp=use))
+        ref = O.alg1_seeded(A, tol, seed_A, pred=pred if use else None)
+        phi, reps, m = ctx.assignment()
+        st = ctx.stats()
+        assert np.array_equal(phi.cpu().numpy(), ref["phi"]), use
+        assert np.array_equal(reps.cpu().numpy(), ref["reps"]), use
+        assert st["criterion_evals"] == ref["evals"] and st["mlp_hits"] == ref["hits"], use
+        out[use] = st["criterion_evals"]
+        ctx.destroy()
+    assert out[True] < out[False]
+    train.destroy()
+
+
+def test_learned_setup_rejects_untrained_context(lib):
+    pr, A = _c4_small()
+    rp, ci, va = dev(pr.rowptr, torch.int32), dev(pr.colidx, torch.int32), dev(pr.vals, torch.float64)
+    dofs = dev(pr.patch_dofs, torch.int32)
+    ctx = lib.psr_setup(rp, ci, va, dofs, uniform_size=pr.uniform_size,
+                        opts=lib.make_opts(tol=0.3, weighting="sym", krylov="cg"))
+    with pytest.raises(lib.PsrError) as e:
+        lib.psr_setup_learned(rp, ci, va, dofs, pr.uniform_size, ctx,
+                              opts=lib.make_opts(tol=0.3, weighting="sym", krylov="cg", use_mlp=True))
+    assert "PSR_ERR_INVALID_ARG" in str(e.value)
+    ctx.destroy()
