@@ -85,6 +85,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="stokes3d", choices=sorted(CONFIGS))
     ap.add_argument("--maxit", type=int, default=None)
+    ap.add_argument("--N", type=int, default=None, help="mesh size of the workload (a smaller instance, e.g. "
+                    "for a profiler capture); the default is the configuration's")
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--prec", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -110,9 +112,12 @@ def dist_info():
     return ws, rank, local
 
 
-def build_problem(cfg):
+def build_problem(cfg, N=None):
     import problems
-    return getattr(problems, cfg["builder"])(**cfg["kw"])
+    kw = dict(cfg["kw"])
+    if N is not None:
+        kw["N"] = N
+    return getattr(problems, cfg["builder"])(**kw)
 
 
 # ------------------------------------------------------------------ clocks
@@ -347,7 +352,7 @@ def run_gpu(args, cfg, ws, rank, local):
     torch.cuda.set_device(local)
     devc = torch.device("cuda", local)
     t_gen = time.perf_counter()
-    pr = build_problem(cfg)
+    pr = build_problem(cfg, args.N)
     t_gen = time.perf_counter() - t_gen
     tol = cfg["tol"] if args.tol is None else args.tol
     prec = cfg["prec"] if args.prec is None else args.prec
@@ -440,7 +445,8 @@ def run_gpu(args, cfg, ws, rank, local):
         "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": cfg["desc"], "n": pr.n, "nnz": pr.nnz, "n_patches": pr.n_patches,
+        "config": {"workload": cfg["desc"] + ("" if args.N is None else f" (mesh size overridden: N = {args.N})"),
+                   "n": pr.n, "nnz": pr.nnz, "n_patches": pr.n_patches,
                    "patch_sizes": sorted(set(pr.patch_sizes.tolist())), "tol": tol, "store_prec": prec,
                    "fp64_arith": "pairs (FP64 inverses as (hi, lo) FP32 pairs, compensated products, ~47 bits)",
                    "krylov": cfg["krylov"] + ("(30)" if cfg["krylov"] == "fgmres" else ""),
@@ -630,7 +636,7 @@ def cpu_oracle_sample(pr, cfg, n_apply=6000, n_inv=400, cores=None):
 def run_reference(args, cfg, ws, rank):
     if rank != 0:
         return None
-    pr = build_problem(cfg)
+    pr = build_problem(cfg, args.N)
     vals, walls, cb = [], [], None
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()

@@ -131,12 +131,17 @@ typedef struct {
     int32_t match;        /* PSR_MATCH_* rule of Alg. 1 (spectral criterion)       */
     uint64_t seed;        /* seed of the library's own random draws (MLP weights,
                              training order of psr_mlp_train)                     */
+    double  prec_check;   /* FP32 / BF16 storage of a database built by Alg. 1 or 2:
+                             an entry whose rounded (symmetrised) inverse B~ has
+                             ||B~ A_c - I||_F > prec_check, or (CG) is not positive
+                             definite, is kept and applied in FP64 instead;
+                             0 disables the check                                  */
 } psr_opts;
 
 /* Fill `o` with defaults: tol 0, FP64, SYM, CG, restart 30, rtol 1e-8,
  * maxit 10000, graphs on, AUTO sweep, autotune on, symmetrize on, no MLP,
  * AUTO orthogonalisation, spectral criterion, FP64 pairs, first match,
- * seed 0. */
+ * seed 0, precision check 0.5. */
 void psr_default_opts(psr_opts* o);
 
 /* A rectangular CSR matrix (the interpolation P0 of Eq. 2), device pointers. */
@@ -285,7 +290,8 @@ typedef struct {
     int32_t rounds;               /* Alg. 1 rounds (= m_p when tol > 0)         */
     int32_t tc_groups;            /* size groups applied on the tensor cores (BF16
                                      storage, 128-patch tiles at least 1/4 full) */
-    int32_t reserved;
+    int32_t prec_fallback;        /* database entries kept in FP64 because their rounded
+                                     inverse failed psr_opts.prec_check */
     int64_t criterion_screened;   /* of the evaluations, rejected by the per-patch
                                      sketch screen without reading the candidate */
 } psr_stats;

@@ -65,7 +65,7 @@ class psr_opts(C.Structure):
                 ("maxit", C.c_int32), ("use_graph", C.c_int32), ("sweep_kernel", C.c_int32),
                 ("autotune", C.c_int32), ("symmetrize", C.c_int32), ("use_mlp", C.c_int32),
                 ("ortho", C.c_int32), ("criterion", C.c_int32), ("fp64_arith", C.c_int32),
-                ("match", C.c_int32), ("seed", C.c_uint64)]
+                ("match", C.c_int32), ("seed", C.c_uint64), ("prec_check", C.c_double)]
 
 
 class psr_train_opts(C.Structure):
@@ -95,7 +95,7 @@ class psr_stats(C.Structure):
                 ("t_extract", C.c_double), ("t_rounds", C.c_double), ("t_invert", C.c_double),
                 ("t_convert", C.c_double), ("t_autotune", C.c_double),
                 ("first_singular", C.c_int32), ("rounds", C.c_int32), ("tc_groups", C.c_int32),
-                ("reserved", C.c_int32), ("criterion_screened", C.c_int64)]
+                ("prec_fallback", C.c_int32), ("criterion_screened", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -197,7 +197,7 @@ def _need(t, dtype, name):
 def make_opts(tol=0.0, store_prec="fp64", weighting="sym", krylov="cg", restart=30, rtol=1e-8,
               maxit=10000, use_graph=True, sweep_kernel="auto", autotune=True, symmetrize=True,
               use_mlp=False, ortho="auto", criterion="spectral", fp64_arith="pairs", match="first",
-              seed=0) -> psr_opts:
+              seed=0, prec_check=0.5) -> psr_opts:
     o = psr_opts()
     load().psr_default_opts(C.byref(o))
     o.tol = tol
@@ -217,6 +217,7 @@ def make_opts(tol=0.0, store_prec="fp64", weighting="sym", krylov="cg", restart=
     o.fp64_arith = FP64_ARITH[fp64_arith]
     o.match = MATCH[match]
     o.seed = int(seed)
+    o.prec_check = float(prec_check)
     return o
 
 

@@ -134,7 +134,7 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
         op.sweep_kernel < PSR_SWEEP_AUTO || op.sweep_kernel > PSR_SWEEP_TENSOR || op.ortho < PSR_ORTHO_AUTO ||
         op.ortho > PSR_ORTHO_SPLIT || op.criterion < PSR_CRITERION_SPECTRAL || op.criterion > PSR_CRITERION_VARMIN ||
         op.fp64_arith < PSR_FP64_PAIRS || op.fp64_arith > PSR_FP64_NATIVE || op.match < PSR_MATCH_FIRST ||
-        op.match > PSR_MATCH_CLOSEST) {
+        op.match > PSR_MATCH_CLOSEST || !(op.prec_check >= 0.0)) {
         set_error(ctx, "invalid option value");
         destroy_ctx(ctx);
         return PSR_ERR_INVALID_ARG;
@@ -390,6 +390,7 @@ void psr_default_opts(psr_opts* o) {
     o->fp64_arith = PSR_FP64_PAIRS;
     o->match = PSR_MATCH_FIRST;
     o->seed = 0;
+    o->prec_check = 0.5;
 }
 
 int psr_setup(const psr_csr* A, const psr_patches* patches, const psr_opts* opts, void* stream, psr_ctx** out) {

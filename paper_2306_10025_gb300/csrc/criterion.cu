@@ -167,7 +167,7 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
         if (bst > 0.f) {
             if (act) v32[lane] = E32[bri * ld + lane] / bst;
             __syncwarp();
-            for (int it = 0; it < 12; ++it) {
+            for (int it = 0; it < 20; ++it) {
                 float wr = 0.f;
                 if (act) {
 #pragma unroll
@@ -190,6 +190,58 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
                 __syncwarp();
                 if (act) v32[lane] = uj / nu;
                 __syncwarp();
+            }
+        }
+        __syncwarp();
+        // FP32 certificate (accept): G32 = fl32(E32^T E32) next to E32 in the
+        // scratch; ||G32 - E32^T E32||_2 <= eg32 = gamma32_p ||E32||_F^2.  A
+        // successful FP32 factorisation of X I - G32 - c I (c covering its
+        // backward error gamma32_{p+1} tr) proves lambda_max(G32) <= X, so
+        // sigma(E) <= sigma(E32) + err32 <= sqrt(X + eg32) + err32 < tol: the
+        // same argument as the FP64 certificate below, with u = 2^-24.
+        {
+            const double u = 0x1p-24;
+            auto g32 = [&](int k) { return (double)k * u / (1.0 - (double)k * u); };
+            const double f2 = (double)fr2 * (1.0 + (double)(p + 2) * 0x1p-23);
+            const double eg = 1.01 * g32(p) * f2;
+            const double tl = (tol - err32) * (1.0 - 4.0 * (double)(p + 2) * u);
+            const double X = tl > 0.0 ? tl * tl * (1.0 - 8.0 * u) - eg : -1.0;
+            if (X > 0.0) {
+                float* G32 = E32 + (size_t)p * ld;
+                const float Xf = __double2float_rd(X);
+                for (int kc = 0; kc < p; kc += 8) {
+                    float acc[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) acc[q] = 0.f;
+                    if (act) {
+                        for (int r = 0; r < p; ++r) {
+                            const float a = E32[r * ld + lane];
+                            const float* row = E32 + r * ld;
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) acc[q] = fmaf(a, row[min(kc + q, p - 1)], acc[q]);
+                        }
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const int k = kc + q;
+                            // off the diagonal 0 - g is exact; on it X - g rounds
+                            // down, so the factored matrix is below X I - G32
+                            if (k < p) G32[lane * ld + k] = (k == lane) ? __fsub_rd(Xf, acc[q]) : -acc[q];
+                        }
+                    }
+                }
+                __syncwarp();
+                float trf = act ? G32[lane * ld + lane] : 0.f;
+                trf = warp_sumf(trf);
+                const double tr = (double)trf * (1.0 + (double)(p + 2) * 0x1p-23);
+                if (tr > 0.0) {
+                    const float c = __double2float_ru(2.0 * g32(p + 1) * tr);
+                    if (act) G32[lane * ld + lane] = __fsub_rd(G32[lane * ld + lane], c);
+                    __syncwarp();
+                    if (cholesky_warp_f(G32, p, ld) == p) {
+                        *dv = (sqrt((double)Xf + eg) + err32) * (1.0 + 8.0 * U64);
+                        return 1;
+                    }
+                }
             }
         }
         __syncwarp();
@@ -282,15 +334,40 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
 #pragma unroll
     for (int r = 0; r < PM; ++r) ecol[r] = (act && r < p) ? ws.E[r * ld + lane] : 0.0;
     __syncwarp();
-    // ws.E <- X I - G (neg) or G; G[lane][k] = sum_r E[r][lane] E[r][k], every
-    // lane runs every shuffle
+    // ws.E <- X I - G (neg) or G; G[lane][k] = sum_r E[r][lane] E[r][k] (r in
+    // increasing order).  E goes back to shared memory from the rows held in
+    // registers, then G is formed eight columns at a time: eight independent
+    // FMA chains per lane, each chunk written over its own columns of E only
+    // after every lane has read them (later chunks read other columns, and
+    // column `lane` is held in ecol).
     auto build = [&](double X, bool neg) {
-        for (int k = 0; k < p; ++k) {
-            double g = 0.0;
-            for (int r = 0; r < p; ++r) g = fma(ecol[r], __shfl_sync(0xffffffffu, ecol[r], k), g);
-            if (act) ws.E[lane * ld + k] = neg ? ((k == lane ? X : 0.0) - g) : g;
+        __syncwarp();
+        if (act) {
+#pragma unroll
+            for (int j = 0; j < PM; ++j)
+                if (j < p) ws.E[lane * ld + j] = e[j];
         }
         __syncwarp();
+        for (int kc = 0; kc < p; kc += 8) {
+            double acc[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] = 0.0;
+            for (int r = 0; r < p; ++r) {
+                const double a = ecol[r];
+                const double* row = ws.E + r * ld;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc[u] = fma(a, row[min(kc + u, p - 1)], acc[u]);
+            }
+            __syncwarp();
+            if (act) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int k = kc + u;
+                    if (k < p) ws.E[lane * ld + k] = neg ? ((k == lane ? X : 0.0) - acc[u]) : acc[u];
+                }
+            }
+            __syncwarp();
+        }
     };
     const double eg = 1.01 * gamma_u(p) * fro2;
     const double tl = (tol - err) * shrink;
@@ -800,7 +877,7 @@ __device__ __forceinline__ void rounds_barrier(unsigned int* bar, int32_t* err) 
 // resets the other parity's counters after the first barrier, when every
 // block has read them, and records the entry and the state for the host.
 template <int PM>
-__global__ void __launch_bounds__(EVAL_THREADS) k_rounds_persistent(
+__global__ void __launch_bounds__(EVAL_THREADS, 4) k_rounds_persistent(
     RoundDev* st, int32_t* __restrict__ phi, int count, const double* __restrict__ Ag, int p,
     const double* __restrict__ Ball, const double* __restrict__ fro_all, const double* __restrict__ w_all,
     const int32_t* __restrict__ sing_all, SketchDB sk, double tol, int32_t* __restrict__ surv_list,

@@ -144,4 +144,27 @@ __device__ __forceinline__ int cholesky_warp(double* A, int p, int ld) {
     return p;
 }
 
+// FP32 Cholesky of the symmetric p x p matrix in A (row stride ld, lower
+// triangle read and overwritten), one warp, p <= 32; lane r updates row r.
+// Returns p when every pivot is positive, else the first index that is not.
+__device__ __forceinline__ int cholesky_warp_f(float* A, int p, int ld) {
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < p; ++k) {
+        __syncwarp();
+        const float akk = A[k * ld + k];
+        if (!(akk > 0.f)) return k;                    // also stops on NaN
+        const float lkk = sqrtf(akk);
+        __syncwarp();
+        if (lane == k) A[k * ld + k] = lkk;
+        if (lane > k && lane < p) A[lane * ld + k] = __fdiv_rn(A[lane * ld + k], lkk);
+        __syncwarp();
+        if (lane > k && lane < p) {
+            const float lrk = A[lane * ld + k];
+            for (int j = k + 1; j <= lane; ++j) A[lane * ld + j] = fmaf(-lrk, A[j * ld + k], A[lane * ld + j]);
+        }
+    }
+    __syncwarp();
+    return p;
+}
+
 }  // namespace psr

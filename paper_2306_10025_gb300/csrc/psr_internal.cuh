@@ -105,6 +105,12 @@ struct Group {
     bool stream = false;           // every patch its own entry: column-major inverses streamed
                                    // by k_sweep_stream (thread per row)
     int32_t* bexp = nullptr;       // [m] power-of-two scale of each entry (FP64 pairs only)
+    // entries whose rounded inverse failed the precision check (psr_opts.prec_check):
+    // their tiles run separately on an FP64 copy of the database
+    std::vector<char> h_hi;        // [m] 1 = entry applied in FP64
+    double* rinv_hi = nullptr;     // [m * p * p] FP64 inverses (read for the flagged entries)
+    int32_t* tiles_hi = nullptr;   // [ntiles_hi * 3] tiles of the flagged entries
+    int ntiles_hi = 0;
     int32_t* sdofs_t = nullptr;    // [p * count] DOFs, local-DOF major (tpp kernel)
     int32_t* wtiles = nullptr;     // [nwt * 3] warp tiles (entry, first, count <= 32)
     int nwt = 0;

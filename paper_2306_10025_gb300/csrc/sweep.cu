@@ -457,13 +457,17 @@ static int cuda_fail_if(psr_ctx* ctx, cudaError_t e, const char* what) {
 }
 
 // Tiles (entry, first sorted patch, count <= T) of a group's sweep order.
-static std::vector<int32_t> tiles_host(const std::vector<int32_t>& sorted_phi, int count, int T) {
+// keep: 0 = every entry, 1 = entries not flagged in `hi`, 2 = flagged ones only.
+static std::vector<int32_t> tiles_host(const std::vector<int32_t>& sorted_phi, int count, int T,
+                                       const std::vector<char>* hi = nullptr, int keep = 0) {
     std::vector<int32_t> t;
     int i = 0;
     while (i < count) {
         const int c = sorted_phi[i];
         int j = i;
         while (j < count && sorted_phi[j] == c) ++j;
+        const bool flagged = hi && !hi->empty() && (*hi)[c];
+        if (keep != 0 && flagged != (keep == 2)) { i = j; continue; }
         for (int s = i; s < j; s += T) {
             t.push_back(c);
             t.push_back(s);
@@ -475,13 +479,120 @@ static std::vector<int32_t> tiles_host(const std::vector<int32_t>& sorted_phi, i
 }
 
 static int make_tiles(psr_ctx* ctx, Group& G, const std::vector<int32_t>& sorted_phi, int T) {
-    const std::vector<int32_t> t = tiles_host(sorted_phi, G.count, T);
+    const bool split = !G.h_hi.empty();
+    const std::vector<int32_t> t = tiles_host(sorted_phi, G.count, T, &G.h_hi, split ? 1 : 0);
     if (G.tiles) psr::dev_free(G.tiles);
     G.tiles = nullptr;
     G.ntiles = (int)(t.size() / 3);
     PSR_CUDA(ctx, psr::dev_alloc(&G.tiles, sizeof(int32_t) * std::max<size_t>(t.size(), 3)));
     PSR_CUDA(ctx, cudaMemcpy(G.tiles, t.data(), sizeof(int32_t) * t.size(), cudaMemcpyHostToDevice));
     G.tile_patches = T;
+    if (split) {
+        const std::vector<int32_t> th = tiles_host(sorted_phi, G.count, 32, &G.h_hi, 2);
+        if (G.tiles_hi) psr::dev_free(G.tiles_hi);
+        G.tiles_hi = nullptr;
+        G.ntiles_hi = (int)(th.size() / 3);
+        PSR_CUDA(ctx, psr::dev_alloc(&G.tiles_hi, sizeof(int32_t) * std::max<size_t>(th.size(), 3)));
+        PSR_CUDA(ctx, cudaMemcpy(G.tiles_hi, th.data(), sizeof(int32_t) * th.size(), cudaMemcpyHostToDevice));
+    }
+    return PSR_OK;
+}
+
+// Precision check of a rounded database (psr_opts.prec_check), one block per
+// entry: B~ = the stored value of (B + B^T)/2 (sym) or B rounded to FP32 /
+// BF16 exactly as the conversion kernels round it, then rho = ||B~ A_c - I||_F
+// in FP64 (column j of the product by thread j), and, when spd, an FP64
+// Cholesky of B~ (global scratch, one p x p slice per block).  flag[e] = 1
+// when rho > theta or B~ is not positive definite.
+__device__ __forceinline__ double rounded_entry(const double* B, int p, int i, int k, int sym, int prec) {
+    double v = B[i * p + k];
+    if (sym) v = 0.5 * (v + B[k * p + i]);
+    const float f = __double2float_rn(v);
+    if (prec == PSR_PREC_BF16) return (double)__bfloat162float(__float2bfloat16_rn(f));
+    return (double)f;
+}
+
+__global__ void __launch_bounds__(128) k_prec_check(const double* __restrict__ Binv, const double* __restrict__ Adb,
+                                                    int m, int p, int sym, int prec, int spd, double theta,
+                                                    double* __restrict__ scratch, int32_t* __restrict__ flag) {
+    __shared__ double red[4];
+    __shared__ int s_bad;
+    const int t = threadIdx.x;
+    const int64_t pp = (int64_t)p * p;
+    double* H = scratch + (int64_t)blockIdx.x * pp;
+    for (int e = blockIdx.x; e < m; e += gridDim.x) {
+        const double* B = Binv + e * pp;
+        const double* A = Adb + e * pp;
+        double r2 = 0.0;
+        for (int j = t; j < p; j += blockDim.x) {
+            for (int i = 0; i < p; ++i) {
+                double sacc = 0.0;
+                for (int k = 0; k < p; ++k) sacc = fma(rounded_entry(B, p, i, k, sym, prec), A[k * p + j], sacc);
+                const double d = sacc - (i == j ? 1.0 : 0.0);
+                r2 = fma(d, d, r2);
+            }
+        }
+        r2 = warp_sum(r2);
+        __syncthreads();
+        if ((t & 31) == 0) red[t >> 5] = r2;
+        __syncthreads();
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+        bool bad = !(sqrt(tot) <= theta);                // NaN fails too
+        if (spd && !bad) {
+            for (int q = t; q < (int)pp; q += blockDim.x) H[q] = rounded_entry(B, p, q / p, q % p, 1, prec);
+            if (t == 0) s_bad = 0;
+            __syncthreads();
+            for (int k = 0; k < p; ++k) {
+                const double akk = *((volatile double*)&H[k * p + k]);
+                if (!(akk > 0.0)) { if (t == 0) s_bad = 1; break; }
+                const double lkk = sqrt(akk);
+                __syncthreads();
+                for (int r = k + 1 + t; r < p; r += blockDim.x) H[r * p + k] /= lkk;
+                __syncthreads();
+                for (int r = k + 1 + t; r < p; r += blockDim.x) {
+                    const double lrk = H[r * p + k];
+                    for (int j = k + 1; j <= r; ++j) H[r * p + j] = fma(-lrk, H[j * p + k], H[r * p + j]);
+                }
+                __syncthreads();
+            }
+            __syncthreads();
+            bad = s_bad != 0;
+        }
+        if (t == 0) flag[e] = bad ? 1 : 0;
+        __syncthreads();
+    }
+}
+
+// Runs the check on a group's FP64 database (before its conversion) and, when
+// an entry fails, keeps an FP64 copy for the flagged entries' tiles.
+static int check_precision(psr_ctx* ctx, Group& G, const double* db64, int prec, cudaStream_t s, int* n_bad) {
+    *n_bad = 0;
+    G.h_hi.clear();
+    if (ctx->opts.prec_check <= 0.0 || prec == PSR_PREC_FP64 || !G.dbA || G.m >= G.count || G.m < 1) return PSR_OK;
+    const int64_t pp = (int64_t)G.p * G.p;
+    const int blocks = std::max(1, std::min(G.m, 152 * 4));
+    double* scratch = nullptr;
+    int32_t* flag = nullptr;
+    PSR_CUDA(ctx, psr::dev_alloc(&scratch, sizeof(double) * (size_t)blocks * pp));
+    PSR_CUDA(ctx, psr::dev_alloc(&flag, sizeof(int32_t) * (size_t)G.m));
+    const int spd = (ctx->opts.krylov == PSR_KRYLOV_CG) ? 1 : 0;
+    count_launch();
+    k_prec_check<<<blocks, 128, 0, s>>>(db64, G.dbA, G.m, G.p, ctx->opts.symmetrize, prec, spd, ctx->opts.prec_check,
+                                        scratch, flag);
+    PSR_CHECK_LAUNCH(ctx, "k_prec_check");
+    std::vector<int32_t> hf(G.m);
+    PSR_CUDA(ctx, cudaMemcpyAsync(hf.data(), flag, sizeof(int32_t) * G.m, cudaMemcpyDeviceToHost, s));
+    PSR_CUDA(ctx, cudaStreamSynchronize(s));
+    psr::dev_free(scratch);
+    psr::dev_free(flag);
+    int bad = 0;
+    for (int32_t f : hf) bad += f ? 1 : 0;
+    if (bad == 0) return PSR_OK;
+    G.h_hi.assign(hf.begin(), hf.end());
+    PSR_CUDA(ctx, psr::dev_alloc(&G.rinv_hi, sizeof(double) * (size_t)G.m * pp));
+    PSR_CUDA(ctx, cudaMemcpyAsync(G.rinv_hi, db64, sizeof(double) * (size_t)G.m * pp, cudaMemcpyDeviceToDevice, s));
+    *n_bad = bad;
     return PSR_OK;
 }
 
@@ -518,6 +629,7 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<std::vector<int32_t>>& gi
     std::vector<int32_t> phi_global(ctx->n_patches, -1);
     std::vector<int32_t> rep_global;
     int entry_base = 0;
+    int n_fallback = 0;
     int64_t factor_bytes = 0, index_bytes = 0;
     for (size_t g = 0; g < ctx->groups.size(); ++g) {
         Group& G = ctx->groups[g];
@@ -552,6 +664,12 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<std::vector<int32_t>>& gi
         double* db64 = reinterpret_cast<double*>(G.rinv);
         const int64_t ne = (int64_t)G.m * p * p;
         const bool in_place = (db64 == ctx->A_ext + G.mat_off);
+        int n_bad = 0;
+        if (G.m < G.count) {
+            int rc = check_precision(ctx, G, db64, prec, s, &n_bad);
+            if (rc != PSR_OK) return rc;
+            n_fallback += n_bad;
+        }
         if (G.m == G.count) {
             // every patch its own entry: column-major stream (sweep_stream.cu)
             int64_t fb = 0;
@@ -627,6 +745,7 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<std::vector<int32_t>>& gi
             while (i < count) {
                 int j = i;
                 while (j < count && hs[j] == hs[i]) ++j;
+                if (!G.h_hi.empty() && G.h_hi[hs[i]]) { i = j; continue; }   // applied in FP64
                 for (int s0 = i; s0 < j; s0 += 32) {
                     wt.push_back(hs[i]);
                     wt.push_back(s0);
@@ -654,6 +773,7 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<std::vector<int32_t>>& gi
         PSR_CUDA(ctx, cudaMemcpy(ctx->rep_ids, rep_global.data(), sizeof(int32_t) * rep_global.size(), cudaMemcpyHostToDevice));
     ctx->stats.factor_bytes = factor_bytes;
     ctx->stats.index_bytes = index_bytes;
+    ctx->stats.prec_fallback = n_fallback;
     ctx->stats.tc_groups = 0;
     for (const Group& G : ctx->groups) ctx->stats.tc_groups += G.tc ? 1 : 0;
     ctx->stats.m_p = ctx->m_p;
@@ -667,6 +787,7 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<std::vector<int32_t>>& gi
     int mode = ctx->opts.sweep_kernel;
     if (mode == PSR_SWEEP_AUTO) mode = (ctx->groups.size() > 1) ? PSR_SWEEP_GROUPED : PSR_SWEEP_PERGROUP;
     if (mode == PSR_SWEEP_TENSOR) mode = PSR_SWEEP_PERGROUP;
+    if (n_fallback > 0) mode = PSR_SWEEP_PERGROUP;         // FP64 tiles of flagged entries run per group
     ctx->sweep_mode = mode;
     return PSR_OK;
 }
@@ -798,7 +919,7 @@ int autotune_sweep(psr_ctx* ctx, cudaStream_t s) {
         std::vector<int32_t> all;
         if (G.tpp) cand.push_back(Cand{G.tile_patches, G.warps, true, 0, 0});
         for (auto& sh : shapes) {
-            const std::vector<int32_t> t = tiles_host(G.h_sorted_phi, G.count, sh[0]);
+            const std::vector<int32_t> t = tiles_host(G.h_sorted_phi, G.count, sh[0], &G.h_hi, G.h_hi.empty() ? 0 : 1);
             cand.push_back(Cand{sh[0], sh[1], false, all.size(), t.size()});
             all.insert(all.end(), t.begin(), t.end());
         }
@@ -888,8 +1009,29 @@ int autotune_sweep(psr_ctx* ctx, cudaStream_t s) {
 constexpr size_t STAGED_SMEM_MAX = 96 * 1024;
 
 template <typename T>
+static int launch_group_lo(psr_ctx* ctx, const Group& G, const double* r, double* z, const int32_t* stop,
+                           cudaStream_t s);
+
+// A group's sweep: its tiles in the storage precision, then the tiles of the
+// entries that failed the precision check on the FP64 copy.
+template <typename T>
 static int launch_group(psr_ctx* ctx, const Group& G, const double* r, double* z, const int32_t* stop,
                         cudaStream_t s) {
+    int rc = launch_group_lo<T>(ctx, G, r, z, stop, s);
+    if (rc != PSR_OK || G.ntiles_hi == 0) return rc;
+    const int warps = 4;
+    const size_t sm = sweep_smem(G.p, PSR_PREC_FP64, warps);
+    const int blocks = std::min(G.ntiles_hi, 152 * 8);
+    count_launch();
+    k_sweep_warp<double><<<blocks, warps * 32, sm, s>>>(G.tiles_hi, G.ntiles_hi, G.p, G.rinv_hi, G.sdofs, r, ctx->Wg,
+                                                        ctx->W, z, stop);
+    PSR_CHECK_LAUNCH(ctx, "sweep kernel (FP64 entries)");
+    return PSR_OK;
+}
+
+template <typename T>
+static int launch_group_lo(psr_ctx* ctx, const Group& G, const double* r, double* z, const int32_t* stop,
+                           cudaStream_t s) {
     const int warps = G.warps;
     const int prec = ctx->opts.store_prec;
     const size_t sm = sweep_smem(G.p, prec, warps);
@@ -1016,6 +1158,8 @@ void free_sweep(psr_ctx* ctx) {
         psr::dev_free(G.wtiles);
         psr::dev_free(G.dbA);
         psr::dev_free(G.bexp);
+        psr::dev_free(G.rinv_hi);
+        psr::dev_free(G.tiles_hi);
         if (G.rinv && !(ctx->A_ext && reinterpret_cast<double*>(G.rinv) >= ctx->A_ext &&
                          reinterpret_cast<double*>(G.rinv) < ctx->A_ext + ctx->A_ext_len))
             psr::dev_free(G.rinv);

@@ -280,7 +280,8 @@ def test_apply_bf16_vs_rounded_operator(lib, case):
     # these small clustered cases fill their 128-patch tiles too little for the
     # automatic choice: force the tensor-core path
     kern = "auto" if case == "full_simt" else "tensor"
-    ctx = setup_ctx(lib, pr, tol=tol, store_prec="bf16", weighting=w, krylov=pr.krylov, sweep_kernel=kern)
+    ctx = setup_ctx(lib, pr, tol=tol, store_prec="bf16", weighting=w, krylov=pr.krylov, sweep_kernel=kern,
+                    prec_check=0.0)
     assert ctx.stats()["m_p"] == len(st["reps"])
     assert ctx.stats()["tc_groups"] == (0 if case == "full_simt" else 1)
     g = np.random.default_rng(11)
@@ -301,9 +302,11 @@ def test_bf16_auto_picks_tensor_cores_by_tile_fill(lib):
     128-patch tiles are at least a quarter full (poisson 32x32 at tol 1e-12:
     9 entries, 16 tiles, fill 1/2); a weakly clustered group (Nedelec 4^3 at
     tol 1: 31 entries for 64 patches) stays on the SIMT path."""
-    ctx = setup_ctx(lib, P.poisson2d_q2(32), tol=1e-12, store_prec="bf16", weighting="sym", krylov="cg")
+    ctx = setup_ctx(lib, P.poisson2d_q2(32), tol=1e-12, store_prec="bf16", weighting="sym", krylov="cg",
+                    prec_check=0.0)
     assert ctx.stats()["m_p"] == 9 and ctx.stats()["tc_groups"] == 1
-    ctx = setup_ctx(lib, P.nedelec3d(4, seed=5), tol=1.0, store_prec="bf16", weighting="sym", krylov="cg")
+    ctx = setup_ctx(lib, P.nedelec3d(4, seed=5), tol=1.0, store_prec="bf16", weighting="sym", krylov="cg",
+                    prec_check=0.0)
     assert ctx.stats()["tc_groups"] == 0
 
 
@@ -382,6 +385,93 @@ def test_fgmres_history_vs_oracle(lib, tol, ortho):
     info = ctx.solve(dev(b, torch.float64), x)
     assert info["converged"] and info["iterations"] == it
     assert_history_close(ctx.history(), hist)
+
+
+@pytest.mark.parametrize("N", [10, 12])
+@pytest.mark.parametrize("ortho", ["auto", "fp64"])
+def test_fgmres_history_clustered_larger_mesh(lib, N, ortho):
+    """FGMRES(30) with the clustered FP64 database (tol 0.1) on 10x10 and
+    12x12 Stokes: 957 and 1726 iterations.  Over runs this long the
+    roundings of the two Gram-Schmidt orders (classical with
+    reorthogonalisation here, modified in the oracle) and of the sweep's FP64
+    atomic scatter (whose order varies from run to run) accumulate: the bars
+    are 1e-9 absolute (up to 4.7e-10 measured at 12x12) and 1e-7 relative
+    where h_k >= 1e-4 (7.7e-9 measured at 957 iterations) instead of the
+    1e-10 of the short runs, and the iteration count may differ by one where
+    the two histories straddle the 1e-8 threshold (1727 against 1726 at
+    12x12)."""
+    pr = P.stokes2d_q2q1(N)
+    st = O.setup(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d(), 1e-1)
+    b = pr.rhs(1)
+    _, hist, it, conv = O.solve(pr.rowptr, pr.colidx, pr.vals, pr.n, b, st, "fgmres", "left", restart=30,
+                                maxit=20000)
+    assert conv
+    ctx = setup_ctx(lib, pr, tol=1e-1, weighting="left", krylov="fgmres", restart=30, maxit=20000, ortho=ortho)
+    assert ctx.stats()["m_p"] == len(st["reps"]) < pr.n_patches
+    x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
+    info = ctx.solve(dev(b, torch.float64), x)
+    h = np.asarray(ctx.history())
+    hist = np.asarray(hist)
+    assert info["converged"]
+    k = min(len(h), len(hist))
+    if info["iterations"] != it:
+        # the stopping test may fall on the other side of 1e-8 only where the
+        # two histories, agreeing within their bar, straddle it at the last
+        # common step
+        assert abs(info["iterations"] - it) == 1
+        lo, hi = sorted((h[k - 1], hist[k - 1]))
+        assert lo <= 1e-8 <= hi and hi - lo <= 1e-9
+    assert np.max(np.abs(h[:k] - hist[:k])) <= 1e-9
+    big = hist[:k] >= 1e-4
+    assert np.max(np.abs(h[:k][big] - hist[:k][big]) / hist[:k][big]) <= 1e-7
+
+
+@pytest.mark.parametrize("N", [64, 128])
+def test_alg1_bench_size_vs_sorted_search(lib, N):
+    """Alg. 1 on the graded Stokes mesh at the sizes the benchmarks use
+    (4,096 and 16,384 patches, tol 1e-2): phi and the representatives equal
+    the oracle's sorted-search form, which is pinned equal to Alg. 1."""
+    pr = P.stokes2d_q2q1(N, 1.05)
+    A = O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d())
+    ref = O.alg1_sorted(A, 1e-2)
+    ctx = setup_ctx(lib, pr, tol=1e-2, weighting="left", krylov="fgmres")
+    phi, reps, m = ctx.assignment()
+    assert m == len(ref["reps"])
+    assert np.array_equal(phi.cpu().numpy(), ref["phi"])
+    assert np.array_equal(reps.cpu().numpy(), ref["reps"])
+    ctx.destroy()
+
+
+@pytest.mark.parametrize("case", ["stokes", "diff3d"])
+def test_apply_fp32_clustered_vs_rounded_operator(lib, case):
+    """FP32 storage of a clustered database: equal, up to FP32 accumulation,
+    to the exactly summed product of the symmetrised inverses rounded to FP32
+    with the (weighted) residual rounded to FP32; within 1e-5 of the FP64
+    operator."""
+    if case == "stokes":
+        pr, tol, w = P.stokes2d_q2q1(8), 1e-1, "left"
+    else:
+        pr, tol, w = P.diffusion3d_q2(4, seed=3), 1e-1, "sym"
+    st = O.setup(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d(), tol)
+    ctx = setup_ctx(lib, pr, tol=tol, store_prec="fp32", weighting=w, krylov=pr.krylov, prec_check=0.0)
+    assert ctx.stats()["m_p"] == len(st["reps"]) < pr.n_patches
+    B = st["Binv"]
+    Bq = (0.5 * (B + np.transpose(B, (0, 2, 1)))).astype(np.float32).astype(np.float64)
+    sw = np.sqrt(st["W"])
+    g = np.random.default_rng(12)
+    for _ in range(2):
+        r = g.standard_normal(pr.n)
+        z = torch.empty(pr.n, dtype=torch.float64, device="cuda")
+        ctx.apply(dev(r, torch.float64), z)
+        x = (sw * r if w == "sym" else r).astype(np.float32).astype(np.float64)
+        yk = np.einsum("kab,kb->ka", Bq[st["phi"]], x[pr.dofs2d()])
+        acc = np.zeros(pr.n)
+        np.add.at(acc, pr.dofs2d().reshape(-1), yk.reshape(-1))
+        zr = (sw if w == "sym" else st["W"]) * acc
+        zc = z.cpu().numpy()
+        assert np.abs(zc - zr).max() <= 2e-6 * np.abs(zr).max()
+        z64 = O.apply(r, pr.dofs2d(), st["Binv"], st["phi"], st["W"], w)
+        assert np.abs(zc - z64).max() <= 1e-5 * np.abs(z64).max()
 
 
 def test_fgmres_maxit_reports_not_converged(lib):
