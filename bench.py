@@ -89,6 +89,8 @@ def parse():
                     "for a profiler capture); the default is the configuration's")
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--prec", default=None)
+    ap.add_argument("--prec-check", type=float, default=0.5,
+                    help="psr_opts.prec_check of the main line (0 keeps every entry in the storage precision)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the precision variants and the sub-line")
@@ -266,7 +268,7 @@ def _variant(L, dev_in, pr, cfg, b, devc, reps, tol, prec, arith, maxit, r_ref=N
     opts = L.make_opts(tol=tol, store_prec=prec, weighting=cfg["weighting"], krylov=cfg["krylov"], restart=30,
                        rtol=1e-8, maxit=maxit, fp64_arith=arith)
     x = torch.zeros_like(b)
-    ctx, info = _setup_solve(L, dev_in, pr, opts, b, x, False) if solve else (None, None)
+    ctx, info = _setup_solve(L, dev_in, pr, opts, b, x, True) if solve else (None, None)
     if ctx is None:
         rp, ci, va, dofs, offs = dev_in
         ctx = L.psr_setup(rp, ci, va, dofs, offsets=offs, uniform_size=pr.uniform_size, opts=opts)
@@ -283,6 +285,8 @@ def _variant(L, dev_in, pr, cfg, b, devc, reps, tol, prec, arith, maxit, r_ref=N
         out["apply_err_vs_fp64"] = float((z - z_ref).abs().max() / z_ref.abs().max())
     if info is not None:
         out.update(iterations=info["iterations"], relres=info["relres"], converged=info["converged"])
+        kt = ctx.kernel_timing()
+        out["us_per_launch"] = {k: 1e3 * v[0] / v[1] for k, v in kt.items() if v[1]}
     ctx.destroy()
     return out
 
@@ -340,7 +344,77 @@ def convergence_subline(L, args, devc, hbm):
         r["speedup_setup_plus_solve_vs_full_fp64"] = (full["setup_s"] + full["solve_s"]) / (r["setup_s"] + r["solve_s"])
         r["within_plus_one_iteration"] = bool(r["converged"] and r["iterations"] <= full["iterations"] + 1)
     return {"workload": cfg["desc"] + f", tol {cfg['tol']}, SYM weighting, rtol 1e-8", "n": pr.n,
-            "n_patches": pr.n_patches, "rhs": "uniform(-1,1) seed 0", "forms": rows}
+            "n_patches": pr.n_patches, "rhs": "uniform(-1,1) seed 0", "forms": rows,
+            "learned": learned_subline(L, cfg, pr, dev_in, b, devc)}
+
+
+def learned_subline(L, cfg, pr, dev_in, b, devc):
+    """The learned assignment on a matrix sequence (section 3.2: a database
+    carried from one linear problem to the next): a setup of the 3D lognormal
+    workload with closest-match labels trains its network on the GPU (half of
+    its patches, 300 full-batch Adam steps); the next matrix of the sequence
+    (the coefficient field's amplitude 1.0 -> 1.02) is set up (a) by plain
+    Alg. 1, (b) seeded with the first setup's database, (c) seeded and hinted
+    by the network (psr_setup_learned, use_mlp), in FP32 storage: criterion
+    evaluations, setup seconds (prediction included; training reported
+    apart) and PCG iterations to 1e-8 against FP64 full storage of the same
+    matrix."""
+    import torch
+    tol = cfg["tol"]
+    rp, ci, va, dofs, _ = dev_in
+    p = pr.uniform_size
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - t0
+
+    train, t_setup1 = timed(lambda: L.psr_setup(rp, ci, va, dofs, uniform_size=p, opts=L.make_opts(
+        tol=tol, weighting=cfg["weighting"], krylov=cfg["krylov"], match="closest")))
+    info, t_train = timed(lambda: train.mlp_train(hidden=256, epochs=300, lr=1e-3, train_fraction=0.5, seed=1))
+    import problems
+    pr2 = problems.diffusion3d_q2(N=cfg["kw"]["N"], sigma=1.02, seed=0)
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=devc)
+    rp2, ci2, va2 = t(pr2.rowptr, torch.int32), t(pr2.colidx, torch.int32), t(pr2.vals, torch.float64)
+    d2 = t(pr2.patch_dofs, torch.int32)
+    b2 = t(pr2.rhs(0), torch.float64)
+    out = {"matrix_2": "3D Q2 lognormal 32^3, amplitude 1.02 (same noise)", "train": {
+        "setup_s": t_setup1, "m_p": train.stats()["m_p"], "train_s": t_train, **info}}
+    forms = {
+        "full_fp64": lambda: L.psr_setup(rp2, ci2, va2, d2, uniform_size=p, opts=L.make_opts(
+            tol=0.0, weighting=cfg["weighting"], krylov=cfg["krylov"], maxit=cfg["maxit"])),
+        "alg1_fp32": lambda: L.psr_setup(rp2, ci2, va2, d2, uniform_size=p, opts=L.make_opts(
+            tol=tol, store_prec="fp32", weighting=cfg["weighting"], krylov=cfg["krylov"], maxit=cfg["maxit"])),
+        "seeded_fp32": lambda: L.psr_setup_learned(rp2, ci2, va2, d2, p, train, opts=L.make_opts(
+            tol=tol, store_prec="fp32", weighting=cfg["weighting"], krylov=cfg["krylov"], maxit=cfg["maxit"],
+            use_mlp=False)),
+        "learned_fp32": lambda: L.psr_setup_learned(rp2, ci2, va2, d2, p, train, opts=L.make_opts(
+            tol=tol, store_prec="fp32", weighting=cfg["weighting"], krylov=cfg["krylov"], maxit=cfg["maxit"],
+            use_mlp=True)),
+    }
+    for name, mk in forms.items():
+        best = None
+        for rep in range(2):
+            ctx, ts = timed(mk)
+            x = torch.zeros_like(b2)
+            inf, tsol = timed(lambda: ctx.solve(b2, x))
+            st = ctx.stats()
+            ctx.destroy()
+            if best is None or ts < best[0]:
+                best = (ts, tsol, inf, st)
+        ts, tsol, inf, st = best
+        out[name] = {"setup_s": ts, "solve_s": tsol, "m_p": st["m_p"], "criterion_evals": st["criterion_evals"],
+                     "mlp_hits": st["mlp_hits"], "iterations": inf["iterations"], "converged": inf["converged"]}
+    full = out["full_fp64"]["iterations"]
+    for name in ("alg1_fp32", "seeded_fp32", "learned_fp32"):
+        out[name]["within_plus_one_iteration"] = bool(out[name]["converged"] and out[name]["iterations"] <= full + 1)
+    out["evals_saved_vs_seeded"] = 1.0 - out["learned_fp32"]["criterion_evals"] / max(out["seeded_fp32"]["criterion_evals"], 1)
+    out["evals_saved_vs_alg1"] = 1.0 - out["learned_fp32"]["criterion_evals"] / max(out["alg1_fp32"]["criterion_evals"], 1)
+    train.destroy()
+    return out
 
 
 def run_gpu(args, cfg, ws, rank, local):
@@ -364,7 +438,7 @@ def run_gpu(args, cfg, ws, rank, local):
     x = torch.zeros_like(b)
     stream = torch.cuda.current_stream()
     opts = L.make_opts(tol=tol, store_prec=prec, weighting=cfg["weighting"], krylov=cfg["krylov"], restart=30,
-                       rtol=1e-8, maxit=maxit, fp64_arith="pairs")
+                       rtol=1e-8, maxit=maxit, fp64_arith="pairs", prec_check=args.prec_check)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = peaks.get("hbm_gbs", 6800.0)

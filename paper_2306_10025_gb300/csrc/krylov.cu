@@ -1408,7 +1408,7 @@ static double sweep_flops(const psr_ctx* ctx) {
     const bool fp64 = ctx->opts.store_prec == PSR_PREC_FP64;
     for (const Group& G : ctx->groups) {
         sp += (double)G.count * G.p;
-        if (fp64 && !(G.stream && ctx->opts.fp64_arith == PSR_FP64_PAIRS)) sp2 += (double)G.count * G.p * G.p;
+        if (fp64 && !(G.stream && ctx->opts.fp64_arith != PSR_FP64_NATIVE)) sp2 += (double)G.count * G.p * G.p;
     }
     return 2.0 * sp2 + 2.0 * sp;
 }

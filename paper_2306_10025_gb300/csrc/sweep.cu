@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <numeric>
+#include <type_traits>
 
 namespace psr {
 
@@ -1012,6 +1013,36 @@ template <typename T>
 static int launch_group_lo(psr_ctx* ctx, const Group& G, const double* r, double* z, const int32_t* stop,
                            cudaStream_t s);
 
+// Tiles (entry, first, count) of one group with inverses of type T: half
+// warps per patch for p <= 16, else the staged kernel (the warp kernel when
+// a staging does not fit).
+template <typename T>
+static int launch_tiles(psr_ctx* ctx, int p, const int32_t* tiles, int ntiles, int tile_patches, int warps,
+                        const void* rinv_v, const int32_t* sdofs, const double* r, double* z, const int32_t* stop,
+                        cudaStream_t s) {
+    const int blocks = std::min(ntiles, 152 * 8);
+    if (blocks < 1) return PSR_OK;
+    const T* rinv = reinterpret_cast<const T*>(rinv_v);
+    const int prec = std::is_same<T, double>::value ? PSR_PREC_FP64 : PSR_PREC_FP32;
+    const size_t sm = sweep_smem(p, prec, warps);
+    if (p <= 16) {
+        count_launch(); k_sweep_half<T><<<blocks, warps * 32, sm, s>>>(tiles, ntiles, p, rinv, sdofs, r, ctx->Wg, ctx->W, z, stop);
+    } else {
+        using C = typename Comp<T>::type;
+        const bool sym = ctx->Wg != nullptr;
+        int sub = tile_patches;
+        while (sub > 1 && staged_smem<C>(p, sub, sym) > STAGED_SMEM_MAX) sub >>= 1;
+        const size_t ssm = staged_smem<C>(p, sub, sym);
+        if (ssm <= STAGED_SMEM_MAX) {
+            count_launch(); k_sweep_staged<T><<<blocks, warps * 32, ssm, s>>>(tiles, ntiles, p, sub, rinv, sdofs, r, ctx->Wg, ctx->W, z, stop);
+        } else {
+            count_launch(); k_sweep_warp<T><<<blocks, warps * 32, sm, s>>>(tiles, ntiles, p, rinv, sdofs, r, ctx->Wg, ctx->W, z, stop);
+        }
+    }
+    PSR_CHECK_LAUNCH(ctx, "sweep kernel");
+    return PSR_OK;
+}
+
 // A group's sweep: its tiles in the storage precision, then the tiles of the
 // entries that failed the precision check on the FP64 copy.
 template <typename T>
@@ -1019,14 +1050,7 @@ static int launch_group(psr_ctx* ctx, const Group& G, const double* r, double* z
                         cudaStream_t s) {
     int rc = launch_group_lo<T>(ctx, G, r, z, stop, s);
     if (rc != PSR_OK || G.ntiles_hi == 0) return rc;
-    const int warps = 4;
-    const size_t sm = sweep_smem(G.p, PSR_PREC_FP64, warps);
-    const int blocks = std::min(G.ntiles_hi, 152 * 8);
-    count_launch();
-    k_sweep_warp<double><<<blocks, warps * 32, sm, s>>>(G.tiles_hi, G.ntiles_hi, G.p, G.rinv_hi, G.sdofs, r, ctx->Wg,
-                                                        ctx->W, z, stop);
-    PSR_CHECK_LAUNCH(ctx, "sweep kernel (FP64 entries)");
-    return PSR_OK;
+    return launch_tiles<double>(ctx, G.p, G.tiles_hi, G.ntiles_hi, 32, 4, G.rinv_hi, G.sdofs, r, z, stop, s);
 }
 
 template <typename T>
@@ -1061,20 +1085,8 @@ static int launch_group_lo(psr_ctx* ctx, const Group& G, const double* r, double
         const int fb = std::min((G.count + wpb - 1) / wpb, 152 * 16);
         count_launch(); k_sweep_full<T><<<fb, wpb * 32, wpb * slot, s>>>(G.count, G.p, rinv, G.sphi, G.sdofs, r, ctx->Wg,
                                                           ctx->W, z, stop);
-    } else if (G.p <= 16) {
-        count_launch(); k_sweep_half<T><<<blocks, warps * 32, sm, s>>>(G.tiles, G.ntiles, G.p, rinv, G.sdofs, r, ctx->Wg, ctx->W, z, stop);
     } else {
-        // staged tiles: as many patches per staging as fit the budget
-        using C = typename Comp<T>::type;
-        const bool sym = ctx->Wg != nullptr;
-        int sub = G.tile_patches;
-        while (sub > 1 && staged_smem<C>(G.p, sub, sym) > STAGED_SMEM_MAX) sub >>= 1;
-        const size_t ssm = staged_smem<C>(G.p, sub, sym);
-        if (ssm <= STAGED_SMEM_MAX) {
-            count_launch(); k_sweep_staged<T><<<blocks, warps * 32, ssm, s>>>(G.tiles, G.ntiles, G.p, sub, rinv, G.sdofs, r, ctx->Wg, ctx->W, z, stop);
-        } else {
-            count_launch(); k_sweep_warp<T><<<blocks, warps * 32, sm, s>>>(G.tiles, G.ntiles, G.p, rinv, G.sdofs, r, ctx->Wg, ctx->W, z, stop);
-        }
+        return launch_tiles<T>(ctx, G.p, G.tiles, G.ntiles, G.tile_patches, warps, G.rinv, G.sdofs, r, z, stop, s);
     }
     PSR_CHECK_LAUNCH(ctx, "sweep kernel");
     return PSR_OK;
