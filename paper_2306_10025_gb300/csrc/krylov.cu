@@ -234,9 +234,38 @@ __global__ void k_sell_fill(const int32_t* __restrict__ rowptr, const int32_t* _
     }
 }
 
+// Length-sorted slices (SELL-C-sigma): when rows of very different lengths
+// alternate (the 3D Stokes velocity rows of vertex, edge, face and cell
+// nodes: 43 % padding in slices of consecutive rows), the rows of every
+// window of SELL_SIGMA consecutive rows are ordered by decreasing length
+// before being cut into slices, and rowmap gives each slice row its row of A.
+constexpr int SELL_SIGMA = 1024;
+
+__global__ void k_sell_fill_map(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                const double* __restrict__ vals, const int32_t* __restrict__ rowmap, int nslices,
+                                const int64_t* __restrict__ sptr, int32_t* __restrict__ scols,
+                                double* __restrict__ svals) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = r >> 5, lane = r & 31;
+    if (s >= nslices) return;
+    const int64_t base = sptr[s] + lane;
+    const int width = (int)((sptr[s + 1] - sptr[s]) >> 5);
+    const int orig = rowmap[r];
+    const int rs = (orig >= 0) ? rowptr[orig] : 0;
+    const int len = (orig >= 0) ? rowptr[orig + 1] - rs : 0;
+    const int self = (orig >= 0) ? orig : 0;
+    for (int k = 0; k < width; ++k) {
+        const bool in = k < len;
+        scols[base + 32 * (int64_t)k] = in ? colidx[rs + k] : self;
+        svals[base + 32 * (int64_t)k] = in ? vals[rs + k] : 0.0;
+    }
+}
+
 // mode 0: y = A x;  mode 1: y = b - A x and ||y||^2;  mode 2: y = A x and (x . y)
+// rowmap (or null): the row of A of every padded slice row (-1 for none).
 __global__ void __launch_bounds__(256) k_spmv_sell(const int64_t* __restrict__ sptr, const int32_t* __restrict__ scols,
-                                                   const double* __restrict__ svals, const double* __restrict__ x,
+                                                   const double* __restrict__ svals, const int32_t* __restrict__ rowmap,
+                                                   const double* __restrict__ x,
                                                    double* __restrict__ y, const double* __restrict__ b, int n,
                                                    int nrows_pad, int mode, KDims kd, int stop_check, int fin) {
     __shared__ double sh[32];
@@ -275,14 +304,15 @@ __global__ void __launch_bounds__(256) k_spmv_sell(const int64_t* __restrict__ s
         }
         for (int k = 4 * ng; k < width; ++k)
             sum = fma(ldnc(svals + o + 32 * (int64_t)k), ldnc(x + ldnc_i(scols + o + 32 * (int64_t)k)), sum);
-        if (row < n) {
+        const int orow = rowmap ? (live ? rowmap[row] : -1) : (row < n ? row : -1);
+        if (orow >= 0) {
             if (mode == 1) {
-                const double v = b[row] - sum;
-                y[row] = v;
+                const double v = b[orow] - sum;
+                y[orow] = v;
                 acc = fma(v, v, acc);
             } else {
-                y[row] = sum;
-                if (mode == 2) acc = fma(x[row], sum, acc);
+                y[orow] = sum;
+                if (mode == 2) acc = fma(x[orow], sum, acc);
             }
         }
     }
@@ -1370,8 +1400,8 @@ static void launch_spmv(psr_ctx* ctx, const double* x, double* y, const double* 
         const int need = (nrows_pad + 255) / 256;
         const int nb = std::max(1, mode == 0 ? need : std::min(need, nb_max));
         count_launch();
-        k_spmv_sell<<<nb, 256, 0, s>>>(w.sell_ptr, w.sell_cols, w.sell_vals, x, y, b, ctx->n, nrows_pad, mode, kd,
-                                       stop_check, fin);
+        k_spmv_sell<<<nb, 256, 0, s>>>(w.sell_ptr, w.sell_cols, w.sell_vals, w.sell_row, x, y, b, ctx->n, nrows_pad,
+                                       mode, kd, stop_check, fin);
         return;
     }
     const int tpr = spmv_tpr(ctx);
@@ -1510,6 +1540,33 @@ int krylov_alloc(psr_ctx* ctx) {
         std::vector<int32_t> hw((size_t)w.nslices);
         PSR_CUDA(ctx, cudaMemcpy(hw.data(), widths, sizeof(int32_t) * hw.size(), cudaMemcpyDeviceToHost));
         psr::dev_free(widths);
+        int64_t natural = 0;
+        for (int q = 0; q < w.nslices; ++q) natural += 32 * (int64_t)hw[q];
+        // more than 15 % padding on a large matrix: length-sorted windows
+        std::vector<int32_t> hmap;
+        if (ctx->nnz > 0 && (double)natural > 1.15 * (double)ctx->nnz && ctx->n >= 4 * SELL_SIGMA) {
+            std::vector<int32_t> hrp((size_t)ctx->n + 1);
+            PSR_CUDA(ctx, cudaMemcpy(hrp.data(), ctx->rowptr, sizeof(int32_t) * hrp.size(), cudaMemcpyDeviceToHost));
+            hmap.assign((size_t)w.nslices * 32, -1);
+            std::vector<int32_t> idx;
+            for (int w0 = 0; w0 < ctx->n; w0 += SELL_SIGMA) {
+                const int w1 = std::min(ctx->n, w0 + SELL_SIGMA);
+                idx.resize((size_t)(w1 - w0));
+                for (int i = w0; i < w1; ++i) idx[(size_t)(i - w0)] = i;
+                std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+                    return hrp[a + 1] - hrp[a] > hrp[b + 1] - hrp[b];
+                });
+                std::copy(idx.begin(), idx.end(), hmap.begin() + w0);
+            }
+            for (int q = 0; q < w.nslices; ++q) {
+                int mx = 0;
+                for (int l = 0; l < 32; ++l) {
+                    const int r = hmap[(size_t)q * 32 + l];
+                    if (r >= 0) mx = std::max(mx, hrp[r + 1] - hrp[r]);
+                }
+                hw[q] = mx;
+            }
+        }
         std::vector<int64_t> hp((size_t)w.nslices + 1, 0);
         for (int q = 0; q < w.nslices; ++q) hp[q + 1] = hp[q] + 32 * (int64_t)hw[q];
         const int64_t total = std::max<int64_t>(hp.back(), 1);
@@ -1518,8 +1575,15 @@ int krylov_alloc(psr_ctx* ctx) {
         PSR_CUDA(ctx, psr::dev_alloc(&w.sell_cols, sizeof(int32_t) * (size_t)total));
         PSR_CUDA(ctx, psr::dev_alloc(&w.sell_vals, sizeof(double) * (size_t)total));
         count_launch();
-        k_sell_fill<<<(w.nslices * 32 + 255) / 256, 256>>>(ctx->rowptr, ctx->colidx, ctx->vals, ctx->n, w.nslices,
-                                                            w.sell_ptr, w.sell_cols, w.sell_vals);
+        if (hmap.empty()) {
+            k_sell_fill<<<(w.nslices * 32 + 255) / 256, 256>>>(ctx->rowptr, ctx->colidx, ctx->vals, ctx->n, w.nslices,
+                                                                w.sell_ptr, w.sell_cols, w.sell_vals);
+        } else {
+            PSR_CUDA(ctx, psr::dev_alloc(&w.sell_row, sizeof(int32_t) * hmap.size()));
+            PSR_CUDA(ctx, cudaMemcpy(w.sell_row, hmap.data(), sizeof(int32_t) * hmap.size(), cudaMemcpyHostToDevice));
+            k_sell_fill_map<<<(w.nslices * 32 + 255) / 256, 256>>>(ctx->rowptr, ctx->colidx, ctx->vals, w.sell_row,
+                                                                    w.nslices, w.sell_ptr, w.sell_cols, w.sell_vals);
+        }
         PSR_CHECK_LAUNCH(ctx, "SELL build");
         PSR_CUDA(ctx, cudaDeviceSynchronize());
     }
@@ -1562,6 +1626,8 @@ void krylov_free(psr_ctx* ctx) {
     psr::dev_free(w.bar);
     psr::dev_free(w.sell_ptr);
     psr::dev_free(w.sell_cols);
+    psr::dev_free(w.sell_row);
+    w.sell_row = nullptr;
     psr::dev_free(w.sell_vals);
     w = KrylovWS{};
     if (ctx->g_cycle) cudaGraphExecDestroy(ctx->g_cycle);

@@ -140,6 +140,7 @@ struct KrylovWS {
     int64_t* sell_ptr = nullptr;  // SELL-32 copy of A: slice offsets [nslices + 1]
     int32_t* sell_cols = nullptr;
     double* sell_vals = nullptr;
+    int32_t* sell_row = nullptr;  // padded SELL row -> row of A (-1: none), or null when rows are in order
     int nslices = 0;
     int nblk = 0;
     int nspmv = 0;

@@ -10,7 +10,8 @@ namespace psr {
 // r = b - A x (SELL-32: one thread per row, all rows of a warp in one slice)
 __global__ void __launch_bounds__(256) k_residual_sell(const int64_t* __restrict__ sptr,
                                                        const int32_t* __restrict__ scols,
-                                                       const double* __restrict__ svals, const double* __restrict__ x,
+                                                       const double* __restrict__ svals,
+                                                       const int32_t* __restrict__ rowmap, const double* __restrict__ x,
                                                        const double* __restrict__ b, double* __restrict__ r, int n,
                                                        int nrows_pad) {
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
@@ -20,7 +21,8 @@ __global__ void __launch_bounds__(256) k_residual_sell(const int64_t* __restrict
     const int width = (int)((sptr[s + 1] - sptr[s]) >> 5);
     double sum = 0.0;
     for (int k = 0; k < width; ++k) sum = fma(svals[o + 32 * (int64_t)k], x[scols[o + 32 * (int64_t)k]], sum);
-    if (row < n) r[row] = b[row] - sum;
+    const int orow = rowmap ? rowmap[row] : (row < n ? row : -1);
+    if (orow >= 0) r[orow] = b[orow] - sum;
 }
 
 __global__ void k_axpy(double* __restrict__ x, double a, const double* __restrict__ z, int n) {
@@ -41,8 +43,8 @@ extern "C" int psr_smooth(psr_ctx* ctx, const double* b, double* x, double omega
     const int gb = std::max(1, std::min((n + 255) / 256, 152 * 8));
     for (int it = 0; it < sweeps; ++it) {
         count_launch();
-        k_residual_sell<<<(nrows_pad + 255) / 256, 256, 0, s>>>(w.sell_ptr, w.sell_cols, w.sell_vals, x, b, w.r, n,
-                                                                 nrows_pad);
+        k_residual_sell<<<(nrows_pad + 255) / 256, 256, 0, s>>>(w.sell_ptr, w.sell_cols, w.sell_vals, w.sell_row, x, b,
+                                                                 w.r, n, nrows_pad);
         int rc = sweep_apply_ex(ctx, w.r, w.z, nullptr, s);
         if (rc != PSR_OK) return rc;
         count_launch();

@@ -150,3 +150,35 @@ def test_uneven_apply_nan_propagates(lib, stokes3d):
             clean[d] = False
     assert clean.any()
     assert np.abs(zc[clean] - zr[clean]).max() <= 1e-12 * np.abs(zr).max()
+
+
+@pytest.fixture(scope="module")
+def stokes3d_8():
+    pr = P.stokes3d_q2q1(8, seed=2)
+    Alist = O.extract_patches_ragged(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.patch_offsets, pr.patch_dofs)
+    Binv = [O.lu_inverse(a[None])[0][0] for a in Alist]
+    W = O.weights(O.multiplicity(pr.n, pr.patch_dofs))
+    return pr, Binv, W
+
+
+def test_sorted_sell_smoother_and_fgmres(lib, stokes3d_8):
+    """3D Stokes 8^3 (10,854 rows, 69 % padding in slices of consecutive
+    rows): the SpMV runs on length-sorted slices with a row map.  Two
+    smoothing sweeps (residual b - A x on the sorted slices, Eq. 3 sweep)
+    equal the oracle's Richardson iteration, and 40 FGMRES(30) iterations
+    follow the oracle's history."""
+    pr, Binv, W = stokes3d_8
+    A = pr.to_scipy()
+    b = pr.rhs(4)
+    pc = lambda v: O.apply_ragged(v, pr.patch_offsets, pr.patch_dofs, Binv, np.arange(pr.n_patches), W, "left")
+    ctx = ctx_for(lib, pr, tol=0.0, store_prec="fp64", weighting="left", krylov="fgmres", maxit=40)
+    x = torch.zeros(pr.n, dtype=torch.float64, device="cuda")
+    ctx.smooth(dev(b, torch.float64), x, omega=0.7, sweeps=2)
+    xr = O.richardson(pr.rowptr, pr.colidx, pr.vals, pr.n, b, np.zeros(pr.n), pc, 0.7, 2)
+    assert np.abs(x.cpu().numpy() - xr).max() <= 1e-11 * np.abs(xr).max()
+    _, hist, it, conv = O.fgmres(lambda v: A @ v, pc, b, restart=30, rtol=1e-8, maxit=40)
+    x.zero_()
+    info = ctx.solve(dev(b, torch.float64), x)
+    assert info["iterations"] == it == 40
+    h = np.asarray(ctx.history())
+    assert np.max(np.abs(h - np.asarray(hist))) <= 1e-10
