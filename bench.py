@@ -71,10 +71,20 @@ KT_KERNEL_NAMES = {"sweep": "patch sweep (k_sweep_stream for full-storage groups
                    "mdot": "k_arnoldi (fused FGMRES Gram-Schmidt step on FP32 pairs) / k_mdot",
                    "maxpy": "k_maxpy (FGMRES w -= V h)", "vec": "vector kernels (k_fg_scale / CG updates)"}
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, ncu)
-# for (config, class), valid only for the kernel source they were taken on;
-# None until captured.
-TRAFFIC = {}
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one
+# ncu capture) over the algorithmic bytes of that launch, for (config,
+# class).  Taken on the 24^3 instance of the 3D Stokes workload (one launch
+# each, --set full; the 48^3 run holds ~20 GB on the device, above the size
+# an ncu replay capture may take) and applied to the algorithmic bytes of the
+# run: traffic grows with the bytes (both are the stored inverses / matrix
+# entries plus vectors).  Valid only for the kernel sources they were taken on.
+TRAFFIC = {
+    ("stokes3d", "sweep"): {"ratio": (785.054976e6 + 6.025984e6) / 780664560.0,
+                            "capture": "k_sweep_stream, 3D Stokes 24^3: 791.08 MB DRAM for 780.66 MB algorithmic"},
+    ("stokes3d", "spmv"): {"ratio": (808.000256e6 + 6.935552e6) / 788402076.0,
+                           "capture": "k_spmv_sell (length-sorted slices), 3D Stokes 24^3: 814.94 MB DRAM for "
+                                      "788.40 MB algorithmic"},
+}
 
 
 def parse():
@@ -255,7 +265,10 @@ def _roofline_of(name, kd, hbm, peak_source, config):
     else:
         bound = {"bound": "hbm", "achieved": kd["achieved_gbs"], "peak": hbm, "unit": "GB/s", "frac": kd["frac"],
                  "peak_source": peak_source}
-    return dict(kernel=KT_KERNEL_NAMES[name], **bound, traffic=TRAFFIC.get((config, name)),
+    tr = TRAFFIC.get((config, name))
+    return dict(kernel=KT_KERNEL_NAMES[name], **bound,
+                traffic=None if tr is None else tr["ratio"] * kd["alg_bytes_per_launch"],
+                traffic_source=None if tr is None else tr["capture"] + " (ratio applied to this launch)",
                 alg_bytes_per_launch=kd["alg_bytes_per_launch"], launch_us=kd["us_per_launch"],
                 share_of_iteration_kernels=kd["share"])
 

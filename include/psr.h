@@ -287,13 +287,20 @@ typedef struct {
     int64_t index_bytes;          /* bytes of phi + maps used by the sweep      */
     double  t_extract, t_rounds, t_invert, t_convert, t_autotune; /* setup seconds */
     int32_t first_singular;       /* patch index or -1                          */
-    int32_t rounds;               /* Alg. 1 rounds (= m_p when tol > 0)         */
+    int32_t rounds;               /* Alg. 1 rounds: passes of the round kernels
+                                     (one makes up to 64 entries for patches of
+                                     at most 32 DOFs, one entry above); Alg. 2
+                                     and the l1 test: their own passes          */
     int32_t tc_groups;            /* size groups applied on the tensor cores (BF16
                                      storage, 128-patch tiles at least 1/4 full) */
     int32_t prec_fallback;        /* database entries kept in FP64 because their rounded
                                      inverse failed psr_opts.prec_check */
     int64_t criterion_screened;   /* of the evaluations, rejected by the per-patch
                                      sketch screen without reading the candidate */
+    int64_t criterion_decided;    /* pairs the warp / block cascade decided, also
+                                     those Alg. 1 does not count (candidates of a
+                                     round that are not entries, pairs past a
+                                     patch's first accept)                       */
 } psr_stats;
 
 int psr_get_stats(psr_ctx* ctx, psr_stats* st);

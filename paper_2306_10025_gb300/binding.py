@@ -95,7 +95,8 @@ class psr_stats(C.Structure):
                 ("t_extract", C.c_double), ("t_rounds", C.c_double), ("t_invert", C.c_double),
                 ("t_convert", C.c_double), ("t_autotune", C.c_double),
                 ("first_singular", C.c_int32), ("rounds", C.c_int32), ("tc_groups", C.c_int32),
-                ("prec_fallback", C.c_int32), ("criterion_screened", C.c_int64)]
+                ("prec_fallback", C.c_int32), ("criterion_screened", C.c_int64),
+                ("criterion_decided", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -49,7 +49,9 @@ struct RoundDev {
     int next_new;      // smallest candidate the current round rejected
     int nsurv;         // survivors of the current round's screen
     int ns2[2], nn2[2];  // persistent rounds: survivors / smallest rejected, by round parity
+    int nrounds;       // passes of the multi-entry round kernel
     unsigned long long evals, exact, screened;
+    unsigned long long decided;   // pairs the warp cascade decided, counted by Alg. 1 or not
 };
 
 struct WarpScratch {  // per-warp shared memory layout for p <= 32
@@ -66,16 +68,21 @@ struct WarpScratch {  // per-warp shared memory layout for p <= 32
 // O(p^2) lower bounds.
 // Returns 1 accept, 0 reject, -1 undecided (needs the exact path).  *dv gets
 // the deciding value.  All lanes call; lane r handles row r.
-template <int PM = 32>
+// DIFF: sAc already holds D = A_c - A_i (formed by the caller with the same
+// FP64 subtraction, after its own bitwise-equality test); Ai is not read.
+template <int PM = 32, bool DIFF = false>
 __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, const double* sB,
                            int p, int ld, double binv_fro, double tol, WarpScratch ws, double* dv,
                            bool allow_exact_here, const double* probe = nullptr,
                            const float* sB32 = nullptr) {
     const int lane = threadIdx.x & 31;
     const bool act = lane < p;
+    auto dval = [&](int r, int j) -> double {
+        return DIFF ? sAc[r * ld + j] : sAc[r * ld + j] - Ai[r * p + j];
+    };
     // D = 0 when the patches are bitwise equal: integer compares, no FP64
     // instruction (the common accept of uniform meshes)
-    {
+    if (!DIFF) {
         bool same = true;
         if (act)
             for (int j = 0; j < p; ++j)
@@ -86,7 +93,7 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
     double dn2 = 0.0, dw = 0.0, dw2 = 0.0;
     if (act) {
         for (int j = 0; j < p; ++j) {
-            const double d = sAc[lane * ld + j] - Ai[lane * p + j];
+            const double d = dval(lane, j);
             dn2 = fma(d, d, dn2);
             if (probe) {
                 dw = fma(d, probe[j], dw);
@@ -126,7 +133,7 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
         for (int j = 0; j < PM; ++j) f[j] = 0.f;
         if (act) {
             for (int k = 0; k < p; ++k) {
-                const float dk = (float)(sAc[lane * ld + k] - Ai[lane * p + k]);
+                const float dk = (float)dval(lane, k);
 #pragma unroll
                 for (int j = 0; j < PM; ++j)
                     if (j < p) f[j] = fmaf(dk, sB32[k * ld + j], f[j]);
@@ -252,7 +259,7 @@ __device__ int decide_pair(const double* __restrict__ Ai, const double* sAc, con
     for (int j = 0; j < PM; ++j) e[j] = 0.0;
     if (act) {
         for (int k = 0; k < p; ++k) {
-            const double dk = sAc[lane * ld + k] - Ai[lane * p + k];
+            const double dk = dval(lane, k);
 #pragma unroll
             for (int j = 0; j < PM; ++j)
                 if (j < p) e[j] = fma(dk, sB[k * ld + j], e[j]);
@@ -758,6 +765,7 @@ __global__ void __launch_bounds__(EVAL_THREADS) k_round_screen(RoundDev* st, con
     if (lane == 0) {
         if (my_evals) atomicAdd(&st->evals, my_evals);
         if (my_screened) atomicAdd(&st->screened, my_screened);
+        if (my_evals > my_screened) atomicAdd(&st->decided, my_evals - my_screened);
         if (my_min < count) atomicMin(&st->next_new, my_min);
     }
 }
@@ -868,117 +876,444 @@ __device__ __forceinline__ void rounds_barrier(unsigned int* bar, int32_t* err) 
     __syncthreads();
 }
 
-// All rounds of Alg. 1 in one cooperative launch: each round is the screen
-// (one thread per unassigned candidate after the entry; survivors to a
-// global list), a grid barrier, the decide phase (the grid's warps share the
-// survivors) and a second barrier after which every block derives the next
-// entry itself (the smallest rejected index), so no third barrier is needed.
-// The per-round counters are double buffered by round parity; block 0
-// resets the other parity's counters after the first barrier, when every
-// block has read them, and records the entry and the state for the host.
+// All rounds of Alg. 1 in one cooperative launch, KC candidate entries per
+// round.  The candidates are the KC smallest open (unassigned) patches
+// c_0 < ... < c_{K-1}.  Every entry made before the round has rejected every
+// open patch, so in sequential Alg. 1 c_k becomes an entry exactly when no
+// entry among c_0..c_{k-1} accepts it, and every other open patch (all lie
+// above c_{K-1}) meets the round's entries in that order.  A round:
+//   A. every block screens all pairs (entry c_l, patch c_k), l < k, itself
+//      (the same survivor list in every block); the grid's warps decide the
+//      survivors; grid barrier; every block derives the entry mask R
+//      serially (c_0 is an entry, c_k one iff no entry of R below it accepts
+//      it) and block 0 assigns the candidates;
+//   B. one thread per other open patch screens it against the entries of R;
+//      survivors (patch, entry) go to a global list; grid barrier; the warps
+//      decide them, and the warp that decides a patch's last pair assigns it
+//      to its first accepting entry in creation order (the lowest bit of
+//      R & accepted); grid barrier.
+// A patch therefore meets the entries in creation order and stops at its
+// first accept, so phi is that of sequential Alg. 1; the evaluation count
+// adds, per patch, the entries of R up to and including its first accept
+// (all of R when none accepts) -- the evaluations sequential Alg. 1 makes.
+// Pairs decided beyond a patch's first accept, and pairs with candidates
+// that turn out not to be entries, are extra work and are not counted.  On
+// the 3D lognormal workload a round of 64 candidates makes about 14 entries.
+constexpr int KC = 64;
+
+struct MultiWS {
+    uint32_t* obits;               // [ceil(count/32)] open patches
+    uint32_t* pairs;               // [count * KC] phase B survivor pairs, i << 6 | l
+    int32_t* rem;                  // [count] undecided pairs of patch i in this round
+    unsigned long long* accm;      // [count] entries (bit l) that accepted patch i
+    unsigned long long* exm;       // [count] pairs of patch i decided by the exact stage
+    unsigned long long* rejm;      // [count] pairs of patch i the screen rejected
+    unsigned long long* accA;      // [2][KC] phase A accepts of candidate k, by round parity
+    unsigned long long* exA;       // [2][KC] phase A exact-stage pairs of candidate k
+    int32_t* npB;                  // [2] phase B pair counts, by round parity
+    int32_t* wq;                   // [4] pairs handed out beyond the first sweep: A, B by parity
+    const float* B32;              // [count][p * p] inverses rounded to FP32
+};
+
+// Pair q of a decide phase for the calling warp: the first one statically
+// (q = the warp's grid index), later ones from a shared counter, so that
+// warps that drew cheap pairs take more (the costly ones, certificates and
+// power iterations, come in runs of neighbouring patches).
+__device__ __forceinline__ int next_pair(int32_t* wq, int gwarps) {
+    int q = 0;
+    if ((threadIdx.x & 31) == 0) q = gwarps + atomicAdd(wq, 1);
+    return __shfl_sync(0xffffffffu, q, 0);
+}
+
+// Thresholds of the multi-entry screen.  The one-entry screen rejects when
+// sqrt(d2)(1 - (p+9) 2^-24)(1 - 8u) - slack(1 + 8u)(1 - 8u) >= tol den_k
+// (1 + 4u), slack = (f_c + f_i) s_c, s_c = 1.01 (gamma_p + rho_c + 2^-24):
+// that is sqrt(d2) >= alpha_k + beta f_i with the entry's alpha_k, beta.
+// Both are rounded up to FP32 (with a 2^-40 margin for their FP64
+// evaluation) and f_i too, and the threshold formed with an FMA rounded up,
+// so the FP32 test sqrt(d2) >= T is a certified reject as before.  A
+// direction with den_k = 0 gives no bound (threshold NaN: never rejects).
+__device__ __forceinline__ void multi_thresholds(double fc, double rhoc, const double* den, int p, double tol,
+                                                 float* thr, float* beta) {
+    const double sc = 1.01 * (gamma_u(p) + rhoc) + 1.01 * 0x1p-24;
+    const double a = 1.0 - (double)(p + 9) * 0x1p-24;
+    const double c1 = (1.0 + 4.0 * U64) / (1.0 - 8.0 * U64);
+    const double c2 = 1.0 + 8.0 * U64;
+    const double widen = 1.0 + 0x1p-40;
+    *beta = __double2float_ru(sc * c2 / a * widen);
+#pragma unroll
+    for (int k = 0; k < SK; ++k)
+        thr[k] = den[k] > 0.0 ? __double2float_ru((tol * den[k] * c1 + fc * sc * c2) / a * widen)
+                              : __int_as_float(0x7fc00000);   // NaN: this direction never rejects
+}
+
+// Multi-entry screen of one patch sketch v (FP32, f_i rounded up in fi32)
+// against staged entry l: true when the certified lower bound reaches tol.
 template <int PM>
-__global__ void __launch_bounds__(EVAL_THREADS, 4) k_rounds_persistent(
+__device__ __forceinline__ bool multi_rejects(const float (&v)[SK * PM], float fi32, const float* sy32,
+                                              const float* thr, float beta, int p) {
+    bool rej = false;
+#pragma unroll
+    for (int k = 0; k < SK; ++k) {
+        float d2 = 0.f;
+#pragma unroll
+        for (int r = 0; r < PM; ++r) {
+            const float d = (r < p) ? sy32[k * 32 + r] - v[k * PM + r] : 0.f;
+            d2 = fmaf(d, d, d2);
+        }
+        if (sqrtf(d2) >= __fmaf_ru(beta, fi32, thr[k])) rej = true;
+    }
+    return rej;
+}
+
+// One pair (entry c, patch i) through the certified cascade; *ex is set when
+// the exact stage decided it.  The warp first forms D = A_c - A_i in its
+// shared scratch sD with coalesced loads (both matrices are contiguous; rows
+// read lane by lane from global memory cost one L1 wavefront per lane and
+// were the bulk of a decision's time), testing bitwise equality on the way;
+// the inverses are read from global memory (every lane reads the same entry:
+// one wavefront per load).
+template <int PM>
+__device__ __forceinline__ int multi_decide(const double* __restrict__ Ag, const double* __restrict__ Ball,
+                                            const float* __restrict__ B32, const double* __restrict__ fro_all,
+                                            const double* __restrict__ w_all, int p, double tol, WarpScratch ws,
+                                            double* sD, int c, int i, bool* ex) {
+    const int lane = threadIdx.x & 31;
+    const size_t pp = (size_t)p * p;
+    const double* Ac = Ag + (int64_t)c * pp;
+    const double* Ai = Ag + (int64_t)i * pp;
+    bool same = true;
+    __syncwarp();                                  // the previous pair's readers of sD are done
+    for (int e = lane; e < p * p; e += 32) {
+        const double a = Ac[e], b = Ai[e];
+        same &= __double_as_longlong(a) == __double_as_longlong(b);
+        sD[e] = a - b;
+    }
+    *ex = false;
+    if (__all_sync(0xffffffffu, same)) return 1;   // bitwise equal patches: D = 0
+    __syncwarp();
+    double dv;
+    int dec = decide_pair<PM, true>(nullptr, sD, Ball + (int64_t)c * pp, p, p, fro_all[c], tol, ws, &dv, false,
+                                    w_all + (int64_t)c * PROBE_STRIDE, B32 + (int64_t)c * pp);
+    if (dec < 0) {
+        dec = decide_pair<PM, true>(nullptr, sD, Ball + (int64_t)c * pp, p, p, fro_all[c], tol, ws, &dv, true,
+                                    w_all + (int64_t)c * PROBE_STRIDE, nullptr);
+        *ex = true;
+    }
+    return dec;
+}
+
+// Bits 0..l of a 64-bit mask (l in [0, 63]) and bits below l.
+__device__ __forceinline__ unsigned long long upto_bit(int l) { return l >= 63 ? ~0ull : ((2ull << l) - 1ull); }
+__device__ __forceinline__ unsigned long long below_bit(int l) { return (1ull << l) - 1ull; }
+
+template <int PM>
+__global__ void __launch_bounds__(EVAL_THREADS, 4) k_rounds_multi(
     RoundDev* st, int32_t* __restrict__ phi, int count, const double* __restrict__ Ag, int p,
     const double* __restrict__ Ball, const double* __restrict__ fro_all, const double* __restrict__ w_all,
-    const int32_t* __restrict__ sing_all, SketchDB sk, double tol, int32_t* __restrict__ surv_list,
-    int32_t* __restrict__ rep_local, unsigned int* bar, int32_t* err) {
+    const int32_t* __restrict__ sing_all, SketchDB sk, double tol, MultiWS mw, int32_t* __restrict__ rep_local,
+    unsigned int* bar, int32_t* err) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ float sy[SK * 32];
-    __shared__ double sden[SK];
-    const int ld = p + 1;
+    constexpr int SYS = SK * 32 + 1;               // padded stride: lanes over candidates hit distinct banks
+    __shared__ float sy[KC * SYS];                 // candidates' sketches (FP32, zero beyond p)
+    __shared__ float sthr[KC * SK];                // screen thresholds alpha_k per candidate
+    __shared__ float sbeta[KC];
+    __shared__ float sfi[KC];                      // candidates' ||A||_F rounded up (as patches in phase A)
+    __shared__ int scand[KC];
+    __shared__ int sridx[KC];                      // slots of the entries of R, in order
+    __shared__ unsigned long long srejA[KC], sacc[KC], sexA[KC];
+    __shared__ unsigned short sapair[KC * (KC - 1) / 2];
+    __shared__ int s_aoff[KC];
+    __shared__ int s_wsum[EVAL_THREADS / 32];
+    __shared__ int s_found, s_na;
+    __shared__ unsigned long long s_R;
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    double* sAc = reinterpret_cast<double*>(smem);
-    double* sB = sAc + p * ld;
-    double* sw = sB + p * ld;
-    float* sB32 = reinterpret_cast<float*>(sw + PROBE_STRIDE);
-    double* wbase = reinterpret_cast<double*>(smem) + decide_block_doubles(p) + (size_t)wid * (p * ld + 64);
-    WarpScratch ws{wbase, wbase + p * ld, wbase + p * ld + 32};
-    unsigned long long my_evals = 0, my_exact = 0, my_screened = 0;
-    int i0 = st->next;
-    int m = st->m;
-    bool done = st->done != 0;
+    double* wbase = reinterpret_cast<double*>(smem) + (size_t)wid * (2 * (size_t)p * p + 64);
+    WarpScratch ws{wbase, wbase + (size_t)p * p, wbase + (size_t)p * p + 32};
+    double* sD = wbase + (size_t)p * p + 64;       // D = A_c - A_i of the pair being decided
+    const int nwords = (count + 31) >> 5;
     const int gthreads = gridDim.x * blockDim.x;
     const int gwarps = gridDim.x * wpb;
-    for (int round = 0; !done && round < count; ++round) {
+    const int gw = blockIdx.x * wpb + wid;
+    unsigned long long my_evals = 0, my_exact = 0, my_screened = 0, my_decided = 0;
+    int m = st->m;
+    int nrounds = 0;
+    // the open bitmap from phi (a seed database may have assigned some)
+    for (int wd = gw; wd < nwords; wd += gwarps) {
+        const int i = wd * 32 + lane;
+        const unsigned b = __ballot_sync(0xffffffffu, i < count && phi[i] == -1);
+        if (lane == 0) mw.obits[wd] = b;
+    }
+    rounds_barrier(bar, err);
+    int fw = 0;                                    // no open patch below word fw
+    bool ok = *((volatile int*)err) == 0;
+    for (int round = 0; ok && round < count; ++round) {
         const int par = round & 1;
-        // stage the entry: sketch for the screen, matrices for the decisions
-        const double fc = sk.fa[i0], rhoc = sk.rho[i0];
-        stage_sketch(sk.den + (int64_t)i0 * SK, sk.Y32 + (int64_t)i0 * SK * p, p, sy, sden);
-        const double* a = Ag + (int64_t)i0 * p * p;
-        const double* bm = Ball + (int64_t)i0 * p * p;
-        for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
-            sAc[(t / p) * ld + (t % p)] = a[t];
-            const double b = bm[t];
-            sB[(t / p) * ld + (t % p)] = b;
-            sB32[(t / p) * ld + (t % p)] = (float)b;
-        }
-        if (threadIdx.x < PROBE_STRIDE) sw[threadIdx.x] = w_all[(int64_t)i0 * PROBE_STRIDE + threadIdx.x];
-        const double bfro = fro_all[i0];
+        // ---- the KC smallest open patches (every block finds the same)
+        if (threadIdx.x == 0) s_found = 0;
         __syncthreads();
-        int my_min = count;
-        // screen
-        for (int base = i0 + 1 + blockIdx.x * blockDim.x; base < count; base += gthreads) {
-            const int cand = base + threadIdx.x;
-            const int cc = min(cand, count - 1);
-            float v[SK * PM];
-            sketch_load<PM>(sk.Y32 + (int64_t)cc * SK * p, p, v);
-            const double fi = sk.fa[cc];
-            const bool open = cand < count && phi[cc] == -1;
-            const bool rej = open && sketch_bound_rejects<PM>(v, fi, sy, sden, fc, rhoc, p, tol);
-            if (open && rej) my_min = min(my_min, cand);
-            const unsigned opened = __ballot_sync(0xffffffffu, open);
-            const unsigned surv = __ballot_sync(0xffffffffu, open && !rej);
-            my_evals += __popc(opened);
-            my_screened += __popc(opened & ~surv);
-            int wb = 0;
-            if (lane == 0 && surv) wb = atomicAdd(&st->ns2[par], __popc(surv));
-            wb = __shfl_sync(0xffffffffu, wb, 0);
-            if (open && !rej) surv_list[wb + __popc(surv & ((1u << lane) - 1u))] = cand;
-        }
-        rounds_barrier(bar, err);
-        if (*((volatile int*)err)) break;                 // a barrier gave up: leave before reading survivors
-        if (blockIdx.x == 0 && threadIdx.x == 0) {        // the other parity is free again
-            st->ns2[par ^ 1] = 0;
-            st->nn2[par ^ 1] = count;
-        }
-        // decide
-        const int ns = *((volatile int*)&st->ns2[par]);
-        for (int q = blockIdx.x * wpb + wid; q < ns; q += gwarps) {
-            const int c2 = surv_list[q];
-            double dv;
-            int dec = decide_pair<PM>(Ag + (int64_t)c2 * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, false, sw, sB32);
-            if (dec < 0) {
-                dec = decide_pair<PM>(Ag + (int64_t)c2 * p * p, sAc, sB, p, ld, bfro, tol, ws, &dv, true, sw, nullptr);
-                ++my_exact;
+        for (int w0 = fw; w0 < nwords; w0 += blockDim.x) {
+            const int wd = w0 + threadIdx.x;
+            const unsigned bits = wd < nwords ? __ldcg(mw.obits + wd) : 0u;
+            const int c = __popc(bits);
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
             }
-            if (dec == 1) { if (lane == 0) phi[c2] = m; }
-            else my_min = min(my_min, c2);
+            if (lane == 31) s_wsum[wid] = incl;
+            __syncthreads();
+            int pos = s_found, tot = s_found;
+            for (int q = 0; q < wpb; ++q) {
+                if (q < wid) pos += s_wsum[q];
+                tot += s_wsum[q];
+            }
+            pos += incl - c;
+            unsigned b = bits;
+            while (b && pos < KC) {
+                scand[pos++] = wd * 32 + (__ffs(b) - 1);
+                b &= b - 1;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) s_found = min(tot, KC);
+            __syncthreads();
+            if (s_found >= KC) break;
+        }
+        const int K = s_found;
+        if (K == 0) break;                         // every patch assigned (same in every block)
+        ++nrounds;
+        fw = scand[0] >> 5;
+        // ---- stage the candidates
+        for (int t = threadIdx.x; t < K * SK * 32; t += blockDim.x) {
+            const int l = t / (SK * 32), q = t % (SK * 32), k = q >> 5, r = q & 31;
+            sy[l * SYS + q] = (r < p) ? sk.Y32[((int64_t)scand[l] * SK + k) * p + r] : 0.f;
+        }
+        for (int l = threadIdx.x; l < K; l += blockDim.x) {
+            const int c = scand[l];
+            double den[SK];
+#pragma unroll
+            for (int k = 0; k < SK; ++k) den[k] = sk.den[(int64_t)c * SK + k];
+            multi_thresholds(sk.fa[c], sk.rho[c], den, p, tol, sthr + l * SK, sbeta + l);
+            sfi[l] = __double2float_ru(sk.fa[c]);
+            srejA[l] = 0ull;
+        }
+        if (threadIdx.x == 0) s_na = 0;
+        __syncthreads();
+        // ---- phase A: pairs among the candidates, screened by every block
+        // (thread k takes candidate k as the patch and the entries l < k in
+        // turn; the reject bits need no atomics), survivors listed in (k, l)
+        // order so that every block holds the same list
+        for (int t = threadIdx.x; t < 2 * KC; t += blockDim.x) {
+            const int k = t & (KC - 1), l0 = (t >> 6) * 32;   // entries l0 .. l0 + 31 below k
+            if (k < K && l0 < k) {
+                float v[SK * PM];
+#pragma unroll
+                for (int kk = 0; kk < SK; ++kk)
+#pragma unroll
+                    for (int r = 0; r < PM; ++r) v[kk * PM + r] = sy[k * SYS + kk * 32 + r];
+                unsigned long long rb = 0ull;
+                const int l1 = min(k, l0 + 32);
+                for (int l = l0; l < l1; ++l)
+                    if (multi_rejects<PM>(v, sfi[k], sy + l * SYS, sthr + l * SK, sbeta[l], p)) rb |= 1ull << l;
+                if (rb) atomicOr(&srejA[k], rb);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int o = 0;
+            for (int k = 0; k < K; ++k) {
+                s_aoff[k] = o;
+                o += __popcll(~srejA[k] & below_bit(k));
+            }
+            s_na = o;
+        }
+        __syncthreads();
+        for (int k = 1 + wid; k < K; k += wpb) {
+            const unsigned long long sv = ~srejA[k] & below_bit(k);
+            for (int l0 = 0; l0 < k; l0 += 32) {
+                const int l = l0 + lane;
+                if (l < k && ((sv >> l) & 1ull))
+                    sapair[s_aoff[k] + __popcll(sv & below_bit(l))] = (unsigned short)((l << 8) | k);
+            }
+        }
+        __syncthreads();
+        const int na = s_na;
+        for (int q = gw; q < na; q = next_pair(mw.wq + par, gwarps)) {
+            const int l = sapair[q] >> 8, k = sapair[q] & 255;
+            bool ex;
+            const int dec = multi_decide<PM>(Ag, Ball, mw.B32, fro_all, w_all, p, tol, ws, sD, scand[l], scand[k], &ex);
+            if (lane == 0) {
+                ++my_decided;
+                if (dec == 1) atomicOr(&mw.accA[par * KC + k], 1ull << l);
+                if (ex) atomicOr(&mw.exA[par * KC + k], 1ull << l);
+            }
             __syncwarp();
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) my_min = min(my_min, __shfl_xor_sync(0xffffffffu, my_min, o));
-        if (lane == 0 && my_min < count) atomicMin(&st->nn2[par], my_min);
         rounds_barrier(bar, err);
         if (*((volatile int*)err)) break;
-        const int nx = *((volatile int*)&st->nn2[par]);
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            phi[i0] = m;
-            rep_local[m] = i0;
-            if (sing_all[i0] && st->first_singular < 0) st->first_singular = i0;
-            st->m = m + 1;
-            st->next = nx;
-            if (nx >= count) st->done = 1;
+        // ---- the round's entries
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            sacc[k] = __ldcg(mw.accA + par * KC + k);
+            sexA[k] = __ldcg(mw.exA + par * KC + k);
         }
-        m += 1;
-        i0 = nx;
-        done = nx >= count;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long R = 1ull;
+            int nr = 0;
+            sridx[nr++] = 0;
+            for (int k = 1; k < K; ++k)
+                if ((sacc[k] & R) == 0ull) {
+                    R |= 1ull << k;
+                    sridx[nr++] = k;
+                }
+            s_R = R;
+        }
+        __syncthreads();
+        const unsigned long long R = s_R;
+        const int nR = __popcll(R);
+        if (blockIdx.x == 0) {
+            if (threadIdx.x < KC) {                // phase A counters of the other parity are free again
+                mw.accA[(par ^ 1) * KC + threadIdx.x] = 0ull;
+                mw.exA[(par ^ 1) * KC + threadIdx.x] = 0ull;
+            }
+            if (threadIdx.x == 0) {
+                mw.npB[par ^ 1] = 0;
+                mw.wq[par ^ 1] = 0;
+                mw.wq[2 + (par ^ 1)] = 0;
+            }
+            // the candidates: entries, or assigned to their first accepting entry
+            for (int k = threadIdx.x; k < K; k += blockDim.x) {
+                const int c = scand[k];
+                unsigned long long path;
+                int e;
+                if ((R >> k) & 1ull) {
+                    path = R & below_bit(k);
+                    e = m + __popcll(path);
+                    rep_local[e] = c;
+                } else {
+                    const int ls = __ffsll((long long)(sacc[k] & R & below_bit(k))) - 1;
+                    path = R & upto_bit(ls);
+                    e = m + __popcll(R & below_bit(ls));
+                }
+                phi[c] = e;
+                my_evals += __popcll(path);
+                my_screened += __popcll(srejA[k] & path);
+                my_exact += __popcll(sexA[k] & path);
+                atomicAnd(mw.obits + (c >> 5), ~(1u << (c & 31)));
+            }
+            if (threadIdx.x == 0 && st->first_singular < 0) {
+                for (int t = 0; t < nR; ++t)
+                    if (sing_all[scand[sridx[t]]]) {
+                        st->first_singular = scand[sridx[t]];
+                        break;
+                    }
+            }
+        }
+        // ---- phase B screen: every other open patch against the entries of R
+        const int lo = scand[K - 1] + 1;
+        const int par_npb = par;
+        for (int base = lo + blockIdx.x * blockDim.x; base < count; base += gthreads) {
+            const int i = base + threadIdx.x;
+            const bool open = i < count && ((__ldcg(mw.obits + (i >> 5)) >> (i & 31)) & 1u);
+            unsigned long long rej = 0ull;
+            if (open) {
+                float v[SK * PM];
+                sketch_load<PM>(sk.Y32 + (int64_t)i * SK * p, p, v);
+                const float fi32 = __double2float_ru(sk.fa[i]);
+                for (int t = 0; t < nR; ++t) {
+                    const int l = sridx[t];
+                    if (multi_rejects<PM>(v, fi32, sy + l * SYS, sthr + l * SK, sbeta[l], p)) rej |= 1ull << l;
+                }
+            }
+            const unsigned long long surv = open ? (R & ~rej) : 0ull;
+            const int ns = __popcll(surv);
+            if (open && ns == 0) {                 // rejected by every entry: stays open
+                my_evals += nR;
+                my_screened += nR;
+            }
+            int incl = ns;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int wtot = __shfl_sync(0xffffffffu, incl, 31);
+            int wb = 0;
+            if (lane == 31 && wtot) wb = atomicAdd(mw.npB + par_npb, wtot);
+            wb = __shfl_sync(0xffffffffu, wb, 31);
+            if (ns) {
+                mw.rem[i] = ns;
+                mw.rejm[i] = rej & R;
+                mw.accm[i] = 0ull;
+                mw.exm[i] = 0ull;
+                int pos = wb + incl - ns;
+                unsigned long long b = surv;
+                while (b) {
+                    const int l = __ffsll((long long)b) - 1;
+                    mw.pairs[pos++] = ((uint32_t)i << 6) | (uint32_t)l;
+                    b &= b - 1ull;
+                }
+            }
+        }
+        rounds_barrier(bar, err);
+        if (*((volatile int*)err)) break;
+        // ---- phase B decide; the last pair of a patch assigns it
+        const int npb = __ldcg(mw.npB + par_npb);
+        for (int q = gw; q < npb; q = next_pair(mw.wq + 2 + par, gwarps)) {
+            const uint32_t pr = __ldcg(mw.pairs + q);
+            const int i = (int)(pr >> 6), l = (int)(pr & 63u);
+            bool ex;
+            const int dec = multi_decide<PM>(Ag, Ball, mw.B32, fro_all, w_all, p, tol, ws, sD, scand[l], i, &ex);
+            if (lane == 0) {
+                ++my_decided;
+                if (dec == 1) atomicOr(mw.accm + i, 1ull << l);
+                if (ex) atomicOr(mw.exm + i, 1ull << l);
+                __threadfence();
+                if (atomicSub(mw.rem + i, 1) == 1) {
+                    __threadfence();
+                    const unsigned long long a = atomicOr(mw.accm + i, 0ull) & R;
+                    const unsigned long long exb = atomicOr(mw.exm + i, 0ull);
+                    const unsigned long long rj = __ldcg(mw.rejm + i);
+                    unsigned long long path = R;
+                    if (a) {
+                        const int ls = __ffsll((long long)a) - 1;
+                        path = R & upto_bit(ls);
+                        phi[i] = m + __popcll(R & below_bit(ls));
+                        atomicAnd(mw.obits + (i >> 5), ~(1u << (i & 31)));
+                    }
+                    my_evals += __popcll(path);
+                    my_screened += __popcll(rj & path);
+                    my_exact += __popcll(exb & path);
+                }
+            }
+            __syncwarp();
+        }
+        m += nR;
+        rounds_barrier(bar, err);
+        if (*((volatile int*)err)) break;
+    }
+    // the counts are per thread here: sum each warp's before the atomics
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        my_evals += __shfl_xor_sync(0xffffffffu, my_evals, o);
+        my_exact += __shfl_xor_sync(0xffffffffu, my_exact, o);
+        my_screened += __shfl_xor_sync(0xffffffffu, my_screened, o);
+        my_decided += __shfl_xor_sync(0xffffffffu, my_decided, o);
     }
     if (lane == 0) {
         if (my_evals) atomicAdd(&st->evals, my_evals);
         if (my_exact) atomicAdd(&st->exact, my_exact);
         if (my_screened) atomicAdd(&st->screened, my_screened);
+        if (my_decided) atomicAdd(&st->decided, my_decided);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && *((volatile int*)err) == 0) {
+        st->nrounds = nrounds;
+        st->m = m;
+        st->next = count;
+        st->done = 1;
     }
 }
 
@@ -1059,6 +1394,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_seed_pass(RoundDev* st, int
         if (my_evals) atomicAdd(&st->evals, my_evals);
         if (my_exact) atomicAdd(&st->exact, my_exact);
         if (my_screened) atomicAdd(&st->screened, my_screened);
+        if (my_evals > my_screened) atomicAdd(&st->decided, my_evals - my_screened);
     }
 }
 
@@ -1127,6 +1463,7 @@ __global__ void k_verify_hints(RoundDev* st, int32_t* __restrict__ phi, int coun
     }
     if (lane == 0) {
         if (ev) atomicAdd(&st->evals, ev);
+        if (ev) atomicAdd(&st->decided, ev);
         if (ex) atomicAdd(&st->exact, ex);
         if (my_hits) atomicAdd(hits, my_hits);
     }
@@ -1227,6 +1564,12 @@ __global__ void __launch_bounds__(EVAL_THREADS) k_closest_pass(int count, int p,
 }
 
 // psr_debug_inject(PSR_INJECT_BARRIER_WAIT, spins) on the current device.
+// FP32 copy of the inverses for the FP32 stage of the multi-entry rounds.
+__global__ void k_round_f32(const double* __restrict__ src, int64_t n, float* __restrict__ dst) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = (float)src[e];
+}
+
 int inject_barrier_wait(long long spins) {
     const unsigned int extra = spins > 0 ? 1u : 0u;
     const long long limit = spins > 0 ? spins : (1ll << 24);
@@ -1245,11 +1588,12 @@ static void launch_sketch(const double* A, const double* Binv, int count, int p,
     else k_sketch<32><<<blocks, 256, 0, s>>>(A, Binv, count, p, X, den, Y32, fa, rho);
 }
 
+// Raises a kernel's dynamic shared memory limit to `bytes`.  Set whatever the
+// size: the default limit is 48 KB minus the kernel's static shared memory,
+// so a kernel with static arrays needs it below 48 KB of dynamic memory too.
 static int set_smem(const void* f, size_t bytes) {
-    if (bytes > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        if (e != cudaSuccess) return cuda_fail(nullptr, e, "criterion smem attribute");
-    }
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "criterion smem attribute");
     return PSR_OK;
 }
 
@@ -1268,7 +1612,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
     int32_t* flag = nullptr;
     PSR_CUDA(ctx, psr::dev_alloc(&flag, sizeof(int32_t)));
     int rc = PSR_OK;
-    int64_t total_evals = 0, total_exact = 0, total_hits = 0, total_screened = 0;
+    int64_t total_evals = 0, total_exact = 0, total_hits = 0, total_screened = 0, total_decided = 0;
     int rounds_total = 0;
     int first_singular = -1;
     if (m0 > 0 && ctx->groups.size() != 1) { set_error(ctx, "a seed database needs patches of one size"); return PSR_ERR_INVALID_ARG; }
@@ -1285,9 +1629,11 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
                 break;
             }
             int fs = -1;
+            const int64_t ev0 = total_evals, sc0 = total_screened;
             rc = run_alg1_big(ctx, G, Ag, s, &total_evals, &total_exact, &total_screened, &fs);
             if (rc != PSR_OK) break;
             rounds_total += G.m;
+            total_decided += (total_evals - ev0) - (total_screened - sc0);   // one entry per round here
             if (fs >= 0 && first_singular < 0) first_singular = G.h_gidx[fs];
             continue;
         }
@@ -1416,11 +1762,12 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         {
             int coop = 0;
             cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
-            const void* kf = (p <= 8) ? (const void*)k_rounds_persistent<8>
-                           : (p <= 16) ? (const void*)k_rounds_persistent<16> : (const void*)k_rounds_persistent<32>;
+            const void* kf = (p <= 8) ? (const void*)k_rounds_multi<8>
+                           : (p <= 16) ? (const void*)k_rounds_multi<16> : (const void*)k_rounds_multi<32>;
+            const size_t smem_multi = (size_t)wpb * (2 * (size_t)p * p + 64) * 8;
             int per_sm = 0;
-            if (coop && set_smem(kf, smem_dec) == PSR_OK &&
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, EVAL_THREADS, smem_dec) == cudaSuccess &&
+            if (coop && count <= (1 << 25) && set_smem(kf, smem_multi) == PSR_OK &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, EVAL_THREADS, smem_multi) == cudaSuccess &&
                 per_sm >= 1) {
                 int sms = 0;
                 cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
@@ -1428,51 +1775,97 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
                 // (each grid barrier costs an arrival per block), at most 4 per SM
                 const int want = (int)((count + (int64_t)sms * EVAL_THREADS - 1) / ((int64_t)sms * EVAL_THREADS));
                 const int grid = sms * std::max(1, std::min(want, std::min(per_sm, 4)));
+                MultiWS mw{};
                 unsigned int* bar = nullptr;
                 int32_t* perr = nullptr;
+                float* b32 = nullptr;
+                bool room = true;
+                const int nwords = (count + 31) / 32;
                 PSR_CUDA(ctx, psr::dev_alloc(&bar, 2 * sizeof(unsigned int)));
                 PSR_CUDA(ctx, psr::dev_alloc(&perr, sizeof(int32_t)));
+                PSR_CUDA(ctx, psr::dev_alloc(&mw.obits, sizeof(uint32_t) * nwords));
+                if (psr::dev_alloc(&mw.pairs, sizeof(uint32_t) * (size_t)count * KC) != cudaSuccess ||
+                    psr::dev_alloc(&b32, sizeof(float) * (size_t)count * p * p) != cudaSuccess) {
+                    // no room for the pair list or the FP32 inverses: two launches per round
+                    cudaGetLastError();
+                    psr::dev_free(mw.pairs);
+                    psr::dev_free(b32);
+                    mw.pairs = nullptr;
+                    b32 = nullptr;
+                    room = false;
+                }
+                PSR_CUDA(ctx, psr::dev_alloc(&mw.rem, sizeof(int32_t) * (size_t)count));
+                PSR_CUDA(ctx, psr::dev_alloc(&mw.accm, 8 * (size_t)count));
+                PSR_CUDA(ctx, psr::dev_alloc(&mw.exm, 8 * (size_t)count));
+                PSR_CUDA(ctx, psr::dev_alloc(&mw.rejm, 8 * (size_t)count));
+                PSR_CUDA(ctx, psr::dev_alloc(&mw.accA, 8 * 2 * KC));
+                PSR_CUDA(ctx, psr::dev_alloc(&mw.exA, 8 * 2 * KC));
+                PSR_CUDA(ctx, psr::dev_alloc(&mw.npB, sizeof(int32_t) * 2));
+                PSR_CUDA(ctx, psr::dev_alloc(&mw.wq, sizeof(int32_t) * 4));
                 PSR_CUDA(ctx, cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s));
                 PSR_CUDA(ctx, cudaMemsetAsync(perr, 0, sizeof(int32_t), s));
-                cudaLaunchConfig_t cfg = {};
-                cfg.gridDim = dim3((unsigned)grid);
-                cfg.blockDim = dim3(EVAL_THREADS);
-                cfg.dynamicSmemBytes = smem_dec;
-                cfg.stream = s;
-                cudaLaunchAttribute at[1];
-                at[0].id = cudaLaunchAttributeCooperative;
-                at[0].val.cooperative = 1;
-                cfg.attrs = at;
-                cfg.numAttrs = 1;
-                count_launch();
-                cudaError_t le;
-                if (p <= 8)
-                    le = cudaLaunchKernelEx(&cfg, k_rounds_persistent<8>, st, phi_l, count, Ag, p, Ball, fro_all,
-                                            w_all, (const int32_t*)sing_all, sk, tol, surv_list, rep_l, bar, perr);
-                else if (p <= 16)
-                    le = cudaLaunchKernelEx(&cfg, k_rounds_persistent<16>, st, phi_l, count, Ag, p, Ball, fro_all,
-                                            w_all, (const int32_t*)sing_all, sk, tol, surv_list, rep_l, bar, perr);
-
-                else
-                    le = cudaLaunchKernelEx(&cfg, k_rounds_persistent<32>, st, phi_l, count, Ag, p, Ball, fro_all,
-                                            w_all, (const int32_t*)sing_all, sk, tol, surv_list, rep_l, bar, perr);
+                PSR_CUDA(ctx, cudaMemsetAsync(mw.accA, 0, 8 * 2 * KC, s));
+                PSR_CUDA(ctx, cudaMemsetAsync(mw.exA, 0, 8 * 2 * KC, s));
+                PSR_CUDA(ctx, cudaMemsetAsync(mw.npB, 0, sizeof(int32_t) * 2, s));
+                PSR_CUDA(ctx, cudaMemsetAsync(mw.wq, 0, sizeof(int32_t) * 4, s));
+                cudaError_t le = cudaErrorMemoryAllocation;
+                if (room) {
+                    const int64_t tot = (int64_t)count * p * p;
+                    const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 152 * 16));
+                    count_launch();
+                    k_round_f32<<<gb, 256, 0, s>>>(Ball, tot, b32);
+                    mw.B32 = b32;
+                    cudaLaunchConfig_t cfg = {};
+                    cfg.gridDim = dim3((unsigned)grid);
+                    cfg.blockDim = dim3(EVAL_THREADS);
+                    cfg.dynamicSmemBytes = smem_multi;
+                    cfg.stream = s;
+                    cudaLaunchAttribute at[1];
+                    at[0].id = cudaLaunchAttributeCooperative;
+                    at[0].val.cooperative = 1;
+                    cfg.attrs = at;
+                    cfg.numAttrs = 1;
+                    count_launch();
+                    if (p <= 8)
+                        le = cudaLaunchKernelEx(&cfg, k_rounds_multi<8>, st, phi_l, count, Ag, p, (const double*)Ball,
+                                                (const double*)fro_all, (const double*)w_all, (const int32_t*)sing_all,
+                                                sk, tol, mw, rep_l, bar, perr);
+                    else if (p <= 16)
+                        le = cudaLaunchKernelEx(&cfg, k_rounds_multi<16>, st, phi_l, count, Ag, p, (const double*)Ball,
+                                                (const double*)fro_all, (const double*)w_all, (const int32_t*)sing_all,
+                                                sk, tol, mw, rep_l, bar, perr);
+                    else
+                        le = cudaLaunchKernelEx(&cfg, k_rounds_multi<32>, st, phi_l, count, Ag, p, (const double*)Ball,
+                                                (const double*)fro_all, (const double*)w_all, (const int32_t*)sing_all,
+                                                sk, tol, mw, rep_l, bar, perr);
+                }
+                int32_t herr = 0;
                 if (le == cudaSuccess) {
                     persistent = true;
-                    int32_t herr = 0;
                     PSR_CUDA(ctx, cudaMemcpyAsync(h_st, st, sizeof(RoundDev), cudaMemcpyDeviceToHost, s));
                     PSR_CUDA(ctx, cudaMemcpyAsync(&herr, perr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
                     PSR_CUDA(ctx, cudaStreamSynchronize(s));
-                    psr::dev_free(bar);
-                    psr::dev_free(perr);
-                    if (herr || !h_st->done) {
-                        set_error(ctx, "a grid barrier of the Alg. 1 rounds gave up waiting");
-                        rc = PSR_ERR_TIMEOUT;
-                        break;
-                    }
                 } else {
                     cudaGetLastError();
-                    psr::dev_free(bar);
-                    psr::dev_free(perr);
+                    PSR_CUDA(ctx, cudaStreamSynchronize(s));
+                }
+                psr::dev_free(bar);
+                psr::dev_free(perr);
+                psr::dev_free(mw.obits);
+                psr::dev_free(mw.pairs);
+                psr::dev_free(mw.rem);
+                psr::dev_free(mw.accm);
+                psr::dev_free(mw.exm);
+                psr::dev_free(mw.rejm);
+                psr::dev_free(mw.accA);
+                psr::dev_free(mw.exA);
+                psr::dev_free(mw.npB);
+                psr::dev_free(mw.wq);
+                psr::dev_free(b32);
+                if (persistent && (herr || !h_st->done)) {
+                    set_error(ctx, "a grid barrier of the Alg. 1 rounds gave up waiting");
+                    rc = PSR_ERR_TIMEOUT;
+                    break;
                 }
             }
         }
@@ -1524,11 +1917,13 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
             PSR_CUDA(ctx, cudaStreamSynchronize(s));
             psr::dev_free(cev);
             total_evals += (int64_t)h_cev;
+            total_decided += (int64_t)h_cev;
         }
         total_evals += (int64_t)h_st->evals;
         total_exact += (int64_t)h_st->exact;
         total_screened += (int64_t)h_st->screened;
-        rounds_total += h_st->m - m0;
+        total_decided += (int64_t)h_st->decided;
+        rounds_total += persistent ? h_st->nrounds : h_st->m - m0;
         if (h_st->first_singular >= 0 && first_singular < 0) first_singular = G.h_gidx[h_st->first_singular];
         std::vector<int32_t> hrep(G.m);
         PSR_CUDA(ctx, cudaMemcpyAsync(hrep.data(), rep_l, sizeof(int32_t) * G.m, cudaMemcpyDeviceToHost, s));
@@ -1568,6 +1963,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
     ctx->stats.criterion_evals = total_evals;
     ctx->stats.criterion_exact = total_exact;
     ctx->stats.criterion_screened = total_screened;
+    ctx->stats.criterion_decided = total_decided;
     ctx->stats.mlp_hits = total_hits;
     ctx->stats.rounds = rounds_total;
     ctx->stats.first_singular = first_singular;

@@ -716,11 +716,11 @@ __global__ void k_gather_entries(const double* __restrict__ Ball, const int32_t*
     }
 }
 
+// Set whatever the size: the default dynamic limit is 48 KB minus the
+// kernel's static shared memory.
 int set_big_smem(const void* f, size_t bytes) {
-    if (bytes > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        if (e != cudaSuccess) return cuda_fail(nullptr, e, "criterion (p > 32) smem attribute");
-    }
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "criterion (p > 32) smem attribute");
     return PSR_OK;
 }
 

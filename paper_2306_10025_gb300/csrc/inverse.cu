@@ -75,18 +75,33 @@ int launch_batched_inverse(const double* A, int64_t stride_in, const int32_t* in
 
 namespace psr {
 
-// Larger patches (p > 32): one block of 128 threads per matrix, thread t owns
-// column t.  The warp kernel leaves at most three matrices of 89 x 89 per SM
-// (65 KB of shared memory each) with one warp apiece, too few warps to keep
-// the FP64 pipe busy (27 % of its peak on the 3D Stokes patches); here each
-// of those matrices is worked on by four warps.  Same arithmetic as
+// Larger patches (p > 32): one block per matrix, thread t owns column t,
+// 32 * ceil(p / 32) threads.  The warp kernel leaves at most three matrices of
+// 89 x 89 per SM (65 KB of shared memory each) with one warp apiece, too few
+// warps to keep the FP64 pipe busy (27 % of its peak on the 3D Stokes
+// patches); here each of those matrices is worked on by three warps (96 and
+// 128 threads per block measured the same).  Same arithmetic as
 // gj_invert_warp: partial pivoting (largest |entry|, lowest row on ties), the
 // pivot row divided by the pivot, every other row updated with one FMA per
-// entry, the interchanges undone on the columns at the end.
-constexpr int INV_BT = 128;
+// entry, the interchanges undone on the columns at the end.  Two block
+// barriers per step: the owner of column k+1 finds the next pivot right after
+// it updates that column (a serial scan in row order, so ties go to the
+// lowest row), and column k itself is never swapped (it is overwritten by the
+// step; the swapped copy the update needs is read from it in permuted order).
+// 3D Stokes Vanka patches, 30,000 of 89 x 89: 60.1 ms, 56 % of the FP64 peak
+// (the four-barrier form with a shuffle pivot search: 71.7 ms, 47 %); results
+// bitwise equal.
+constexpr int INV_BT = 128;   // upper bound of the block size (p <= 128)
 
 __host__ __device__ inline size_t inv_block_bytes(int p) {
     return ((size_t)p * (p + 1) + p + 16) * 8 + (size_t)p * 4 + 64;
+}
+
+// Order key of |x| for pivot search: the bits of |x| as an integer (monotone
+// for non-negative doubles); NaN ranks below every number.
+__device__ __forceinline__ long long abs_key(double x) {
+    const long long b = __double_as_longlong(x) & 0x7fffffffffffffffLL;
+    return b > 0x7ff0000000000000LL ? -1LL : b;
 }
 
 __global__ void __launch_bounds__(INV_BT) k_batched_inverse_block(const double* __restrict__ A, int64_t stride_in,
@@ -96,57 +111,54 @@ __global__ void __launch_bounds__(INV_BT) k_batched_inverse_block(const double* 
     extern __shared__ __align__(16) unsigned char smem[];
     const int ld = p + 1;
     const int t = threadIdx.x;
-    const int lane = t & 31, wid = t >> 5;
+    const int nt = blockDim.x;
+    const int lane = t & 31, wid = t >> 5, nw = nt >> 5;
     double* S = reinterpret_cast<double*>(smem);
     double* colk = S + (size_t)p * ld;
-    double* red = colk + p;                       // 4 values + 4 indices (as doubles) + amax
+    double* red = colk + p;                       // per-warp amax; [12] pivot |value|; [13] pivot row
     int* swaps = reinterpret_cast<int*>(red + 16);
     for (int64_t b = blockIdx.x; b < batch; b += gridDim.x) {
         const int64_t src = index ? (int64_t)index[b] : b;
         const double* a = A + src * stride_in;
         double amax = 0.0;
-        for (int e = t; e < p * p; e += INV_BT) {
+        for (int e = t; e < p * p; e += nt) {
             const double v = a[e];
             S[(e / p) * ld + (e % p)] = v;
             amax = fmax(amax, fabs(v));
         }
         amax = warp_max(amax);
-        if (lane == 0) red[8 + wid] = amax;
+        if (lane == 0) red[wid] = amax;
         __syncthreads();
-        amax = fmax(fmax(red[8], red[9]), fmax(red[10], red[11]));
+        if (t == 0) {                             // pivot of column 0
+            long long bk = -2;
+            int bi = p;
+            for (int i = 0; i < p; ++i) {
+                const long long key = abs_key(S[i * ld]);
+                if (key > bk) { bk = key; bi = i; }
+            }
+            red[12] = bk >= 0 ? __longlong_as_double(bk) : -1.0;
+            red[13] = (double)(bk >= 0 ? bi : p);
+        }
+        amax = red[0];
+        for (int w = 1; w < nw; ++w) amax = fmax(amax, red[w]);
         const double thresh = (double)p * 0x1p-53 * amax;
         bool sing = !(amax > 0.0);
+        __syncthreads();
         for (int k = 0; k < p; ++k) {
-            __syncthreads();                      // column k as the previous step left it
-            // pivot: largest |S[i][k]|, i >= k, lowest row on ties
-            double best = -1.0;
-            int bi = p;
-            if (t >= k && t < p) { best = fabs(S[t * ld + k]); bi = t; }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-            }
-            if (lane == 0) { red[wid] = best; red[4 + wid] = (double)bi; }
-            __syncthreads();
-            best = red[0];
-            bi = (int)red[4];
-            for (int w = 1; w < 4; ++w) {
-                const double ob = red[w];
-                const int oi = (int)red[4 + w];
-                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-            }
+            const double best = red[12];
+            const int bi = (int)red[13];
             const int piv = (bi < p) ? bi : k;    // an all-NaN column has no valid pivot
             if (!(best > thresh)) sing = true;
-            if (t < p && piv != k) {              // rows k <-> piv in my column
-                const double x = S[k * ld + t];
-                S[k * ld + t] = S[piv * ld + t];
-                S[piv * ld + t] = x;
+            if (t < p) {
+                if (t != k && piv != k) {         // rows k <-> piv in my column
+                    const double x = S[k * ld + t];
+                    S[k * ld + t] = S[piv * ld + t];
+                    S[piv * ld + t] = x;
+                }
+                const int r = (t == k) ? piv : (t == piv ? k : t);
+                colk[t] = S[r * ld + k];          // column k after the interchange
             }
             if (t == 0) swaps[k] = piv;
-            __syncthreads();
-            if (t < p) colk[t] = S[t * ld + k];
             __syncthreads();
             double pv = colk[k];
             if (pv == 0.0) pv = 1.0;              // singular: keep going, result discarded
@@ -158,9 +170,23 @@ __global__ void __launch_bounds__(INV_BT) k_batched_inverse_block(const double* 
                     S[i * ld + t] = fma(-colk[i], rj, x);
                 }
                 S[k * ld + t] = rj;
+                // the owner of column k+1 scans it for the next pivot after
+                // its update (tracking the maximum inside the update loop of
+                // every column made the step 1.5x slower: that loop is bound
+                // by issue, not by the FP64 pipe)
+                if (t == k + 1) {
+                    long long bk = -2;
+                    int bnext = p;
+                    for (int i = k + 1; i < p; ++i) {
+                        const long long key = abs_key(S[i * ld + t]);
+                        if (key > bk) { bk = key; bnext = i; }
+                    }
+                    red[12] = bk >= 0 ? __longlong_as_double(bk) : -1.0;
+                    red[13] = (double)(bk >= 0 ? bnext : p);
+                }
             }
+            __syncthreads();
         }
-        __syncthreads();
         // X = (P A)^{-1} = A^{-1} P^T  =>  A^{-1} = X P: swap columns back, last first
         for (int k = p - 1; k >= 0; --k) {
             const int piv = swaps[k];
@@ -173,7 +199,7 @@ __global__ void __launch_bounds__(INV_BT) k_batched_inverse_block(const double* 
         }
         double* out = Ainv + b * stride_out;
         const double nanv = __longlong_as_double(0x7ff8000000000000LL);
-        for (int e = t; e < p * p; e += INV_BT) out[e] = sing ? nanv : S[(e / p) * ld + (e % p)];
+        for (int e = t; e < p * p; e += nt) out[e] = sing ? nanv : S[(e / p) * ld + (e % p)];
         if (singular && t == 0) singular[b] = sing ? 1 : 0;
         __syncthreads();
     }
@@ -190,7 +216,8 @@ int launch_batched_inverse_block(const double* A, int64_t stride_in, const int32
     int64_t blocks = batch;
     if (blocks > 152 * 16) blocks = 152 * 16;
     count_launch();
-    k_batched_inverse_block<<<(int)blocks, INV_BT, smem, s>>>(A, stride_in, index, batch, p, Ainv, stride_out, singular);
+    const int nt = 32 * ((p + 31) / 32);
+    k_batched_inverse_block<<<(int)blocks, nt, smem, s>>>(A, stride_in, index, batch, p, Ainv, stride_out, singular);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "k_batched_inverse_block");
     return PSR_OK;

@@ -395,9 +395,12 @@ def test_fgmres_history_clustered_larger_mesh(lib, N, ortho):
     roundings of the two Gram-Schmidt orders (classical with
     reorthogonalisation here, modified in the oracle) and of the sweep's FP64
     atomic scatter (whose order varies from run to run) accumulate: the bars
-    are 1e-9 absolute (up to 4.7e-10 measured at 12x12) and 1e-7 relative
-    where h_k >= 1e-4 (7.7e-9 measured at 957 iterations) instead of the
-    1e-10 of the short runs.  The iteration count agrees within 0.5 %: near
+    are 4e-9 absolute and 1e-7 relative where h_k >= 1e-4 (7.7e-9 measured
+    at 957 iterations) instead of the 1e-10 of the short runs.  At 12x12 the
+    GPU history differed from the oracle's by 1.9e-10 .. 1.3e-9 absolute in
+    seven runs with the pair-arithmetic Gram-Schmidt step (2.9e-11 .. 9.1e-11
+    with ortho fp64), and three GPU runs differed from each other by up to
+    1.0e-9: the bar follows the run-to-run spread.  The iteration count agrees within 0.5 %: near
     1e-8 the 12x12 residual falls by under 1 % per step, so differences of a
     few 1e-11 there move the step that crosses the threshold (GPU runs ended
     at 1722 and 1727 against the oracle's 1726)."""
@@ -419,7 +422,7 @@ def test_fgmres_history_clustered_larger_mesh(lib, N, ortho):
     # of the histories there (a few 1e-11 absolute) decides the last step only
     # to within a few iterations
     assert abs(info["iterations"] - it) <= max(1, int(np.ceil(0.005 * it)))
-    assert np.max(np.abs(h[:k] - hist[:k])) <= 1e-9
+    assert np.max(np.abs(h[:k] - hist[:k])) <= 4e-9
     big = hist[:k] >= 1e-4
     assert np.max(np.abs(h[:k][big] - hist[:k][big]) / hist[:k][big]) <= 1e-7
 
@@ -437,6 +440,11 @@ def test_alg1_bench_size_vs_sorted_search(lib, N):
     assert m == len(ref["reps"])
     assert np.array_equal(phi.cpu().numpy(), ref["phi"])
     assert np.array_equal(reps.cpu().numpy(), ref["reps"])
+    st = ctx.stats()
+    # the rounds ran in the multi-entry kernel (up to 64 entries a round), and
+    # every evaluation the screen did not reject was decided by a warp
+    assert st["rounds"] < m
+    assert st["criterion_decided"] >= st["criterion_evals"] - st["criterion_screened"] > 0
     ctx.destroy()
 
 
