@@ -966,6 +966,16 @@ __device__ __forceinline__ bool multi_rejects(const float (&v)[SK * PM], float f
     return rej;
 }
 
+// Where the entries of a multi-entry pass live: the group's own patches
+// (Alg. 1 rounds) or a seed database; entry c is at A + c p^2 and so on.
+struct EntrySrc {
+    const double* A;               // [*][p * p] patch matrices of the entries
+    const double* B;               // [*][p * p] FP64 inverses
+    const float* B32;              // [*][p * p] inverses rounded to FP32
+    const double* fro;             // [*] ||B^-1||_F
+    const double* w;               // [*][PROBE_STRIDE] probe vectors
+};
+
 // One pair (entry c, patch i) through the certified cascade; *ex is set when
 // the exact stage decided it.  The warp first forms D = A_c - A_i in its
 // shared scratch sD with coalesced loads (both matrices are contiguous; rows
@@ -974,13 +984,11 @@ __device__ __forceinline__ bool multi_rejects(const float (&v)[SK * PM], float f
 // the inverses are read from global memory (every lane reads the same entry:
 // one wavefront per load).
 template <int PM>
-__device__ __forceinline__ int multi_decide(const double* __restrict__ Ag, const double* __restrict__ Ball,
-                                            const float* __restrict__ B32, const double* __restrict__ fro_all,
-                                            const double* __restrict__ w_all, int p, double tol, WarpScratch ws,
-                                            double* sD, int c, int i, bool* ex) {
+__device__ __forceinline__ int multi_decide(const EntrySrc& es, const double* __restrict__ Ag, int p, double tol,
+                                            WarpScratch ws, double* sD, int c, int i, bool* ex) {
     const int lane = threadIdx.x & 31;
     const size_t pp = (size_t)p * p;
-    const double* Ac = Ag + (int64_t)c * pp;
+    const double* Ac = es.A + (int64_t)c * pp;
     const double* Ai = Ag + (int64_t)i * pp;
     bool same = true;
     __syncwarp();                                  // the previous pair's readers of sD are done
@@ -993,11 +1001,11 @@ __device__ __forceinline__ int multi_decide(const double* __restrict__ Ag, const
     if (__all_sync(0xffffffffu, same)) return 1;   // bitwise equal patches: D = 0
     __syncwarp();
     double dv;
-    int dec = decide_pair<PM, true>(nullptr, sD, Ball + (int64_t)c * pp, p, p, fro_all[c], tol, ws, &dv, false,
-                                    w_all + (int64_t)c * PROBE_STRIDE, B32 + (int64_t)c * pp);
+    int dec = decide_pair<PM, true>(nullptr, sD, es.B + (int64_t)c * pp, p, p, es.fro[c], tol, ws, &dv, false,
+                                    es.w + (int64_t)c * PROBE_STRIDE, es.B32 + (int64_t)c * pp);
     if (dec < 0) {
-        dec = decide_pair<PM, true>(nullptr, sD, Ball + (int64_t)c * pp, p, p, fro_all[c], tol, ws, &dv, true,
-                                    w_all + (int64_t)c * PROBE_STRIDE, nullptr);
+        dec = decide_pair<PM, true>(nullptr, sD, es.B + (int64_t)c * pp, p, p, es.fro[c], tol, ws, &dv, true,
+                                    es.w + (int64_t)c * PROBE_STRIDE, nullptr);
         *ex = true;
     }
     return dec;
@@ -1010,9 +1018,8 @@ __device__ __forceinline__ unsigned long long below_bit(int l) { return (1ull <<
 template <int PM>
 __global__ void __launch_bounds__(EVAL_THREADS, 4) k_rounds_multi(
     RoundDev* st, int32_t* __restrict__ phi, int count, const double* __restrict__ Ag, int p,
-    const double* __restrict__ Ball, const double* __restrict__ fro_all, const double* __restrict__ w_all,
-    const int32_t* __restrict__ sing_all, SketchDB sk, double tol, MultiWS mw, int32_t* __restrict__ rep_local,
-    unsigned int* bar, int32_t* err) {
+    EntrySrc own, const int32_t* __restrict__ sing_all, SketchDB sk, double tol, MultiWS mw,
+    int32_t* __restrict__ rep_local, unsigned int* bar, int32_t* err, EntrySrc seed, SketchDB skd, int m0) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int SYS = SK * 32 + 1;               // padded stride: lanes over candidates hit distinct banks
     __shared__ float sy[KC * SYS];                 // candidates' sketches (FP32, zero beyond p)
@@ -1049,8 +1056,121 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_rounds_multi(
     rounds_barrier(bar, err);
     int fw = 0;                                    // no open patch below word fw
     bool ok = *((volatile int*)err) == 0;
+    int npass = 0;                                 // passes so far (seed chunks and rounds): counter parity
+    // Phase B of a pass: every open patch i >= lo screened against the staged
+    // entries of R (slots sridx[0..nR)), the surviving pairs decided by the
+    // grid's warps; the warp deciding a patch's last pair assigns it to its
+    // first accepting entry, numbered ebase + (its rank in R).  Two grid
+    // barriers; false when one gave up.
+    auto phase_b = [&](const EntrySrc& es, int ebase, unsigned long long R, int nR, int lo, int par) -> bool {
+        for (int base = lo + blockIdx.x * blockDim.x; base < count; base += gthreads) {
+            const int i = base + threadIdx.x;
+            const bool open = i < count && ((__ldcg(mw.obits + (i >> 5)) >> (i & 31)) & 1u);
+            unsigned long long rej = 0ull;
+            if (open) {
+                float v[SK * PM];
+                sketch_load<PM>(sk.Y32 + (int64_t)i * SK * p, p, v);
+                const float fi32 = __double2float_ru(sk.fa[i]);
+                for (int t = 0; t < nR; ++t) {
+                    const int l = sridx[t];
+                    if (multi_rejects<PM>(v, fi32, sy + l * SYS, sthr + l * SK, sbeta[l], p)) rej |= 1ull << l;
+                }
+            }
+            const unsigned long long surv = open ? (R & ~rej) : 0ull;
+            const int ns = __popcll(surv);
+            if (open && ns == 0) {                 // rejected by every entry: stays open
+                my_evals += nR;
+                my_screened += nR;
+            }
+            int incl = ns;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int wtot = __shfl_sync(0xffffffffu, incl, 31);
+            int wb = 0;
+            if (lane == 31 && wtot) wb = atomicAdd(mw.npB + par, wtot);
+            wb = __shfl_sync(0xffffffffu, wb, 31);
+            if (ns) {
+                mw.rem[i] = ns;
+                mw.rejm[i] = rej & R;
+                mw.accm[i] = 0ull;
+                mw.exm[i] = 0ull;
+                int pos = wb + incl - ns;
+                unsigned long long b = surv;
+                while (b) {
+                    const int l = __ffsll((long long)b) - 1;
+                    mw.pairs[pos++] = ((uint32_t)i << 6) | (uint32_t)l;
+                    b &= b - 1ull;
+                }
+            }
+        }
+        rounds_barrier(bar, err);
+        if (*((volatile int*)err)) return false;
+        const int npb = __ldcg(mw.npB + par);
+        for (int q = gw; q < npb; q = next_pair(mw.wq + 2 + par, gwarps)) {
+            const uint32_t pr = __ldcg(mw.pairs + q);
+            const int i = (int)(pr >> 6), l = (int)(pr & 63u);
+            bool ex;
+            const int dec = multi_decide<PM>(es, Ag, p, tol, ws, sD, scand[l], i, &ex);
+            if (lane == 0) {
+                ++my_decided;
+                if (dec == 1) atomicOr(mw.accm + i, 1ull << l);
+                if (ex) atomicOr(mw.exm + i, 1ull << l);
+                __threadfence();
+                if (atomicSub(mw.rem + i, 1) == 1) {
+                    __threadfence();
+                    const unsigned long long a = atomicOr(mw.accm + i, 0ull) & R;
+                    const unsigned long long exb = atomicOr(mw.exm + i, 0ull);
+                    const unsigned long long rj = __ldcg(mw.rejm + i);
+                    unsigned long long path = R;
+                    if (a) {
+                        const int ls = __ffsll((long long)a) - 1;
+                        path = R & upto_bit(ls);
+                        phi[i] = ebase + __popcll(R & below_bit(ls));
+                        atomicAnd(mw.obits + (i >> 5), ~(1u << (i & 31)));
+                    }
+                    my_evals += __popcll(path);
+                    my_screened += __popcll(rj & path);
+                    my_exact += __popcll(exb & path);
+                }
+            }
+            __syncwarp();
+        }
+        rounds_barrier(bar, err);
+        return *((volatile int*)err) == 0;
+    };
+    // Seed database first (seeded Alg. 1): its entries exist before any new
+    // one, so every open patch meets them in creation order, 64 at a time;
+    // no entry among them needs deciding.
+    for (int j0 = 0; ok && j0 < m0; j0 += KC) {
+        const int par = npass & 1;
+        ++npass;
+        const int K = min(KC, m0 - j0);
+        for (int t = threadIdx.x; t < K * SK * 32; t += blockDim.x) {
+            const int l = t / (SK * 32), q = t % (SK * 32), k = q >> 5, r = q & 31;
+            sy[l * SYS + q] = (r < p) ? skd.Y32[((int64_t)(j0 + l) * SK + k) * p + r] : 0.f;
+        }
+        for (int l = threadIdx.x; l < K; l += blockDim.x) {
+            double den[SK];
+#pragma unroll
+            for (int k = 0; k < SK; ++k) den[k] = skd.den[(int64_t)(j0 + l) * SK + k];
+            multi_thresholds(skd.fa[j0 + l], skd.rho[j0 + l], den, p, tol, sthr + l * SK, sbeta + l);
+            scand[l] = j0 + l;
+            sridx[l] = l;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) {      // counters of the other parity are free again
+            mw.npB[par ^ 1] = 0;
+            mw.wq[2 + (par ^ 1)] = 0;
+        }
+        __syncthreads();
+        const unsigned long long R = (K == KC) ? ~0ull : ((1ull << K) - 1ull);
+        ok = phase_b(seed, j0, R, K, 0, par);
+    }
     for (int round = 0; ok && round < count; ++round) {
-        const int par = round & 1;
+        const int par = npass & 1;
+        ++npass;
         // ---- the KC smallest open patches (every block finds the same)
         if (threadIdx.x == 0) s_found = 0;
         __syncthreads();
@@ -1144,7 +1264,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_rounds_multi(
         for (int q = gw; q < na; q = next_pair(mw.wq + par, gwarps)) {
             const int l = sapair[q] >> 8, k = sapair[q] & 255;
             bool ex;
-            const int dec = multi_decide<PM>(Ag, Ball, mw.B32, fro_all, w_all, p, tol, ws, sD, scand[l], scand[k], &ex);
+            const int dec = multi_decide<PM>(own, Ag, p, tol, ws, sD, scand[l], scand[k], &ex);
             if (lane == 0) {
                 ++my_decided;
                 if (dec == 1) atomicOr(&mw.accA[par * KC + k], 1ull << l);
@@ -1212,88 +1332,9 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_rounds_multi(
                     }
             }
         }
-        // ---- phase B screen: every other open patch against the entries of R
-        const int lo = scand[K - 1] + 1;
-        const int par_npb = par;
-        for (int base = lo + blockIdx.x * blockDim.x; base < count; base += gthreads) {
-            const int i = base + threadIdx.x;
-            const bool open = i < count && ((__ldcg(mw.obits + (i >> 5)) >> (i & 31)) & 1u);
-            unsigned long long rej = 0ull;
-            if (open) {
-                float v[SK * PM];
-                sketch_load<PM>(sk.Y32 + (int64_t)i * SK * p, p, v);
-                const float fi32 = __double2float_ru(sk.fa[i]);
-                for (int t = 0; t < nR; ++t) {
-                    const int l = sridx[t];
-                    if (multi_rejects<PM>(v, fi32, sy + l * SYS, sthr + l * SK, sbeta[l], p)) rej |= 1ull << l;
-                }
-            }
-            const unsigned long long surv = open ? (R & ~rej) : 0ull;
-            const int ns = __popcll(surv);
-            if (open && ns == 0) {                 // rejected by every entry: stays open
-                my_evals += nR;
-                my_screened += nR;
-            }
-            int incl = ns;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            const int wtot = __shfl_sync(0xffffffffu, incl, 31);
-            int wb = 0;
-            if (lane == 31 && wtot) wb = atomicAdd(mw.npB + par_npb, wtot);
-            wb = __shfl_sync(0xffffffffu, wb, 31);
-            if (ns) {
-                mw.rem[i] = ns;
-                mw.rejm[i] = rej & R;
-                mw.accm[i] = 0ull;
-                mw.exm[i] = 0ull;
-                int pos = wb + incl - ns;
-                unsigned long long b = surv;
-                while (b) {
-                    const int l = __ffsll((long long)b) - 1;
-                    mw.pairs[pos++] = ((uint32_t)i << 6) | (uint32_t)l;
-                    b &= b - 1ull;
-                }
-            }
-        }
-        rounds_barrier(bar, err);
-        if (*((volatile int*)err)) break;
-        // ---- phase B decide; the last pair of a patch assigns it
-        const int npb = __ldcg(mw.npB + par_npb);
-        for (int q = gw; q < npb; q = next_pair(mw.wq + 2 + par, gwarps)) {
-            const uint32_t pr = __ldcg(mw.pairs + q);
-            const int i = (int)(pr >> 6), l = (int)(pr & 63u);
-            bool ex;
-            const int dec = multi_decide<PM>(Ag, Ball, mw.B32, fro_all, w_all, p, tol, ws, sD, scand[l], i, &ex);
-            if (lane == 0) {
-                ++my_decided;
-                if (dec == 1) atomicOr(mw.accm + i, 1ull << l);
-                if (ex) atomicOr(mw.exm + i, 1ull << l);
-                __threadfence();
-                if (atomicSub(mw.rem + i, 1) == 1) {
-                    __threadfence();
-                    const unsigned long long a = atomicOr(mw.accm + i, 0ull) & R;
-                    const unsigned long long exb = atomicOr(mw.exm + i, 0ull);
-                    const unsigned long long rj = __ldcg(mw.rejm + i);
-                    unsigned long long path = R;
-                    if (a) {
-                        const int ls = __ffsll((long long)a) - 1;
-                        path = R & upto_bit(ls);
-                        phi[i] = m + __popcll(R & below_bit(ls));
-                        atomicAnd(mw.obits + (i >> 5), ~(1u << (i & 31)));
-                    }
-                    my_evals += __popcll(path);
-                    my_screened += __popcll(rj & path);
-                    my_exact += __popcll(exb & path);
-                }
-            }
-            __syncwarp();
-        }
+        // ---- phase B: every other open patch against the entries of R
+        if (!phase_b(own, m, R, nR, scand[K - 1] + 1, par)) break;
         m += nR;
-        rounds_barrier(bar, err);
-        if (*((volatile int*)err)) break;
     }
     // the counts are per thread here: sum each warp's before the atomics
 #pragma unroll
@@ -1742,7 +1783,11 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
                 total_hits += h_hits;
                 psr::dev_free(hits);
             }
-            // misses: first match over the seed entries, in creation order
+        }
+        // misses of a seed database: first match over its entries in creation
+        // order, one launch per entry (the multi-entry kernel below does the
+        // same 64 entries at a time when it runs)
+        auto seed_passes = [&]() -> int {
             for (int j = 0; j < m0; ++j) {
                 count_launch();
                 k_seed_pass<<<eval_blocks, wpb * 32, smem_eval, s>>>(st, phi_l, count, Ag, p, db, sk, skd, tol, j);
@@ -1755,7 +1800,8 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
             k_first_open<<<std::max(1, std::min((count + 255) / 256, 1024)), 256, 0, s>>>(st, phi_l, count);
             count_launch();
             k_finish_first<<<1, 1, 0, s>>>(st, count);
-        }
+            return PSR_OK;
+        };
         // all rounds in one cooperative launch when every block of the grid
         // can be co-resident; otherwise two launches per round
         bool persistent = false;
@@ -1808,13 +1854,26 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
                 PSR_CUDA(ctx, cudaMemsetAsync(mw.exA, 0, 8 * 2 * KC, s));
                 PSR_CUDA(ctx, cudaMemsetAsync(mw.npB, 0, sizeof(int32_t) * 2, s));
                 PSR_CUDA(ctx, cudaMemsetAsync(mw.wq, 0, sizeof(int32_t) * 4, s));
+                float* sb32 = nullptr;
+                if (room && m0 > 0 && psr::dev_alloc(&sb32, sizeof(float) * (size_t)m0 * p * p) != cudaSuccess) {
+                    cudaGetLastError();
+                    room = false;
+                }
                 cudaError_t le = cudaErrorMemoryAllocation;
                 if (room) {
                     const int64_t tot = (int64_t)count * p * p;
                     const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 152 * 16));
                     count_launch();
                     k_round_f32<<<gb, 256, 0, s>>>(Ball, tot, b32);
+                    if (m0 > 0) {
+                        const int64_t ts = (int64_t)m0 * p * p;
+                        count_launch();
+                        k_round_f32<<<(int)std::max<int64_t>(1, std::min<int64_t>((ts + 255) / 256, 152 * 16)), 256, 0,
+                                      s>>>(db.Binv, ts, sb32);
+                    }
                     mw.B32 = b32;
+                    const EntrySrc own{Ag, Ball, b32, fro_all, w_all};
+                    const EntrySrc seeds{db.A, db.Binv, sb32, db.fro, db.w};
                     cudaLaunchConfig_t cfg = {};
                     cfg.gridDim = dim3((unsigned)grid);
                     cfg.blockDim = dim3(EVAL_THREADS);
@@ -1827,17 +1886,17 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
                     cfg.numAttrs = 1;
                     count_launch();
                     if (p <= 8)
-                        le = cudaLaunchKernelEx(&cfg, k_rounds_multi<8>, st, phi_l, count, Ag, p, (const double*)Ball,
-                                                (const double*)fro_all, (const double*)w_all, (const int32_t*)sing_all,
-                                                sk, tol, mw, rep_l, bar, perr);
+                        le = cudaLaunchKernelEx(&cfg, k_rounds_multi<8>, st, phi_l, count, Ag, p, own,
+                                                (const int32_t*)sing_all, sk, tol, mw, rep_l, bar, perr, seeds, skd,
+                                                m0);
                     else if (p <= 16)
-                        le = cudaLaunchKernelEx(&cfg, k_rounds_multi<16>, st, phi_l, count, Ag, p, (const double*)Ball,
-                                                (const double*)fro_all, (const double*)w_all, (const int32_t*)sing_all,
-                                                sk, tol, mw, rep_l, bar, perr);
+                        le = cudaLaunchKernelEx(&cfg, k_rounds_multi<16>, st, phi_l, count, Ag, p, own,
+                                                (const int32_t*)sing_all, sk, tol, mw, rep_l, bar, perr, seeds, skd,
+                                                m0);
                     else
-                        le = cudaLaunchKernelEx(&cfg, k_rounds_multi<32>, st, phi_l, count, Ag, p, (const double*)Ball,
-                                                (const double*)fro_all, (const double*)w_all, (const int32_t*)sing_all,
-                                                sk, tol, mw, rep_l, bar, perr);
+                        le = cudaLaunchKernelEx(&cfg, k_rounds_multi<32>, st, phi_l, count, Ag, p, own,
+                                                (const int32_t*)sing_all, sk, tol, mw, rep_l, bar, perr, seeds, skd,
+                                                m0);
                 }
                 int32_t herr = 0;
                 if (le == cudaSuccess) {
@@ -1862,6 +1921,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
                 psr::dev_free(mw.npB);
                 psr::dev_free(mw.wq);
                 psr::dev_free(b32);
+                psr::dev_free(sb32);
                 if (persistent && (herr || !h_st->done)) {
                     set_error(ctx, "a grid barrier of the Alg. 1 rounds gave up waiting");
                     rc = PSR_ERR_TIMEOUT;
@@ -1869,6 +1929,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
                 }
             }
         }
+        if (!persistent && m0 > 0 && (rc = seed_passes()) != PSR_OK) break;
         int batch = 8;
         int issued = 0;
         for (; !persistent;) {

@@ -1438,7 +1438,13 @@ static double sweep_flops(const psr_ctx* ctx) {
     const bool fp64 = ctx->opts.store_prec == PSR_PREC_FP64;
     for (const Group& G : ctx->groups) {
         sp += (double)G.count * G.p;
-        if (fp64 && !(G.stream && ctx->opts.fp64_arith != PSR_FP64_NATIVE)) sp2 += (double)G.count * G.p * G.p;
+        // pair arithmetic: streamed groups, and clustered groups with a pair copy
+        // in the thread-per-patch or staged kernel (the half-warp kernel of
+        // p <= 16 and the grouped launch stay FP64)
+        const bool pairs = (G.stream || (G.rinv_pair && (G.tpp || G.p > 16) &&
+                                         ctx->sweep_mode != PSR_SWEEP_GROUPED)) &&
+                           ctx->opts.fp64_arith != PSR_FP64_NATIVE;
+        if (fp64 && !pairs) sp2 += (double)G.count * G.p * G.p;
     }
     return 2.0 * sp2 + 2.0 * sp;
 }

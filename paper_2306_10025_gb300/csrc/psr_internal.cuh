@@ -105,6 +105,8 @@ struct Group {
     bool stream = false;           // every patch its own entry: column-major inverses streamed
                                    // by k_sweep_stream (thread per row)
     int32_t* bexp = nullptr;       // [m] power-of-two scale of each entry (FP64 pairs only)
+    void* rinv_pair = nullptr;     // [m * p * p] clustered FP64 entries as scaled (hi, lo) FP32
+                                   // pairs, column-major (thread-per-patch kernel on pairs)
     // entries whose rounded inverse failed the precision check (psr_opts.prec_check):
     // their tiles run separately on an FP64 copy of the database
     std::vector<char> h_hi;        // [m] 1 = entry applied in FP64
@@ -266,6 +268,11 @@ void free_sweep(psr_ctx* ctx);
 int stream_convert(psr_ctx* ctx, Group& G, const double* db64, cudaStream_t s, int64_t* bytes);
 int stream_build_table(psr_ctx* ctx);
 int launch_sweep_stream(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s);
+// Clustered FP64 database of a group (p <= 32) as scaled FP32 pairs
+// (G.rinv_pair, G.bexp) and its thread-per-patch sweep on pair arithmetic.
+int pair_db_convert(psr_ctx* ctx, Group& G, const double* db64, cudaStream_t s);
+int launch_sweep_tpp_pair(psr_ctx* ctx, const Group& G, const double* r, double* z, const int32_t* stop,
+                          cudaStream_t s);
 void stream_free(psr_ctx* ctx);
 int coarse_apply(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s);
 int run_alg1_l1(psr_ctx* ctx, cudaStream_t s);

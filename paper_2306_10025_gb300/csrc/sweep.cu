@@ -15,6 +15,7 @@
 // Precision: FP64 storage computes in FP64; FP32 storage gathers r in FP64,
 // rounds it to FP32, multiplies in FP32 and scatters in FP64.
 #include "psr_internal.cuh"
+#include "pairs.cuh"
 
 #include <algorithm>
 #include <numeric>
@@ -249,6 +250,92 @@ __global__ void __launch_bounds__(256) k_sweep_staged(const int32_t* __restrict_
                     y0 = fma(row[b], x[b], y0);
                 }
                 atomicAdd(&z[sd[it]], (double)(y0 + y1) * sw[it]);
+            }
+        }
+    }
+}
+
+// Shared memory of the staged kernel on pairs: that of the FP64 form plus
+// one exponent per patch of the sub-tile.
+__host__ __device__ inline size_t staged_pair_smem(int p, int sub, bool sym) {
+    return staged_smem<double>(p, sub, sym) + staged_align((size_t)sub * 4);
+}
+
+// The staged kernel for FP64 entries on FP32 pair arithmetic: the entry's
+// inverse staged as scaled pairs (column-major, so the threads of a patch read
+// consecutive elements), every patch's weighted residual split into pairs
+// after a power-of-two shift that brings its largest entry into [1, 2), each
+// (patch, row) summed with compensated products and unshifted in FP64.
+__global__ void __launch_bounds__(256) k_sweep_staged_pair(const int32_t* __restrict__ tiles, int ntiles, int p,
+                                                           int sub, const float2* __restrict__ Bt,
+                                                           const int32_t* __restrict__ bexp,
+                                                           const int32_t* __restrict__ sdofs,
+                                                           const double* __restrict__ r, const double* __restrict__ wg,
+                                                           const double* __restrict__ wsc, double* __restrict__ z,
+                                                           const int32_t* __restrict__ stop) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (stop && *stop) return;
+    const int pp = p * p;
+    const size_t ne_max = (size_t)sub * p;
+    size_t off = staged_align((size_t)pp * 8);
+    float2* sR = reinterpret_cast<float2*>(smem);
+    int32_t* sd = reinterpret_cast<int32_t*>(smem + off);
+    off += staged_align(ne_max * 4);
+    double* sx = reinterpret_cast<double*>(smem + off);
+    off += staged_align(ne_max * 8);
+    double* sw = reinterpret_cast<double*>(smem + off);
+    off += staged_align(ne_max * 8);
+    double* sg = nullptr;
+    if (wg) {
+        sg = reinterpret_cast<double*>(smem + off);
+        off += staged_align(ne_max * 8);
+    }
+    float2* sc = reinterpret_cast<float2*>(smem + off);
+    off += staged_align(ne_max * 8);
+    int* sex = reinterpret_cast<int*>(smem + off);
+    const int nt = blockDim.x;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int c = tiles[3 * t], start = tiles[3 * t + 1], cnt = tiles[3 * t + 2];
+        const float2* src = Bt + (int64_t)c * pp;
+        const int bx = __ldg(bexp + c);
+        for (int k0 = 0; k0 < cnt; k0 += sub) {
+            const int kc = min(sub, cnt - k0);
+            const int ne = kc * p;
+            const int32_t* dk = sdofs + (int64_t)(start + k0) * p;
+            __syncthreads();                          // the previous sub-tile's readers are done
+            if (k0 == 0)
+                for (int e = threadIdx.x; e < pp; e += nt) cp_async_elem<8>(sR + e, src + e);
+            for (int e = threadIdx.x; e < ne; e += nt) cp_async_elem<4>(sd + e, dk + e);
+            for (int k = threadIdx.x; k < kc; k += nt) sex[k] = 0;
+            cp_async_wait_all();
+            __syncthreads();
+            for (int e = threadIdx.x; e < ne; e += nt) {
+                const int d = sd[e];
+                cp_async_elem<8>(sx + e, r + d);
+                cp_async_elem<8>(sw + e, wsc + d);
+                if (wg) cp_async_elem<8>(sg + e, wg + d);
+            }
+            cp_async_wait_all();
+            __syncthreads();
+            for (int e = threadIdx.x; e < ne; e += nt) {
+                const double v = wg ? sx[e] * sg[e] : sx[e];
+                sx[e] = v;
+                const int ex = (int)((unsigned)(__double2hiint(v) >> 20) & 0x7ffu);
+                if (ex != 0x7ff) atomicMax(&sex[e / p], ex);
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < ne; e += nt) sc[e] = split_scaled(sx[e], sex[e / p] - 1023);
+            __syncthreads();
+            for (int it = threadIdx.x; it < ne; it += nt) {
+                const int k = it / p, a = it - k * p;
+                const float2* x = sc + k * p;
+                float sh = 0.f, sl = 0.f;
+                for (int b = 0; b < p; ++b) {
+                    const float2 bv = sR[b * p + a];
+                    const float2 xv = x[b];
+                    pair_fma(sh, sl, bv.x, bv.y, xv.x, xv.y);
+                }
+                atomicAdd(&z[sd[it]], ldexp((double)sh + (double)sl, sex[k] - 1023 + bx) * sw[it]);
             }
         }
     }
@@ -759,6 +846,14 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<std::vector<int32_t>>& gi
             PSR_CUDA(ctx, cudaMemcpy(G.wtiles, wt.data(), sizeof(int32_t) * wt.size(), cudaMemcpyHostToDevice));
             G.tpp = true;
         }
+        // clustered FP64 entries on pair arithmetic: the thread-per-patch and
+        // staged kernels read a pair copy (the FP64 copy stays for the kernels
+        // without a pair form: half-warp patches, the grouped launch)
+        if (prec == PSR_PREC_FP64 && ctx->opts.fp64_arith == PSR_FP64_PAIRS && G.m < G.count && !G.stream) {
+            int rc = pair_db_convert(ctx, G, reinterpret_cast<const double*>(G.rinv), s);
+            if (rc != PSR_OK) return rc;
+            PSR_CUDA(ctx, cudaStreamSynchronize(s));
+        }
         if (!G.stream) {
             int T = G.tc ? 128 : ((p <= 16) ? 64 : 32);
             int rc = make_tiles(ctx, G, G.h_sorted_phi, T);
@@ -1019,12 +1114,26 @@ static int launch_group_lo(psr_ctx* ctx, const Group& G, const double* r, double
 template <typename T>
 static int launch_tiles(psr_ctx* ctx, int p, const int32_t* tiles, int ntiles, int tile_patches, int warps,
                         const void* rinv_v, const int32_t* sdofs, const double* r, double* z, const int32_t* stop,
-                        cudaStream_t s) {
+                        cudaStream_t s, const void* pair_db = nullptr, const int32_t* pair_exp = nullptr) {
     const int blocks = std::min(ntiles, 152 * 8);
     if (blocks < 1) return PSR_OK;
     const T* rinv = reinterpret_cast<const T*>(rinv_v);
     const int prec = std::is_same<T, double>::value ? PSR_PREC_FP64 : PSR_PREC_FP32;
     const size_t sm = sweep_smem(p, prec, warps);
+    if (pair_db && p > 16) {                      // FP64 entries on pair arithmetic, staged
+        const bool sym = ctx->Wg != nullptr;
+        int sub = tile_patches;
+        while (sub > 1 && staged_pair_smem(p, sub, sym) > STAGED_SMEM_MAX) sub >>= 1;
+        const size_t ssm = staged_pair_smem(p, sub, sym);
+        if (ssm <= STAGED_SMEM_MAX) {
+            count_launch();
+            k_sweep_staged_pair<<<blocks, warps * 32, ssm, s>>>(tiles, ntiles, p, sub,
+                                                                reinterpret_cast<const float2*>(pair_db), pair_exp,
+                                                                sdofs, r, ctx->Wg, ctx->W, z, stop);
+            PSR_CHECK_LAUNCH(ctx, "sweep kernel (staged, FP64 pairs)");
+            return PSR_OK;
+        }
+    }
     if (p <= 16) {
         count_launch(); k_sweep_half<T><<<blocks, warps * 32, sm, s>>>(tiles, ntiles, p, rinv, sdofs, r, ctx->Wg, ctx->W, z, stop);
     } else {
@@ -1068,6 +1177,7 @@ static int launch_group_lo(psr_ctx* ctx, const Group& G, const double* r, double
         if (rc != PSR_OK) set_error(ctx, "tensor-core sweep launch failed");
         return rc;
     }
+    if (G.tpp && G.rinv_pair && std::is_same<T, double>::value) return launch_sweep_tpp_pair(ctx, G, r, z, stop, s);
     if (G.tpp) {
         const int tb = std::max(1, std::min((G.nwt + 7) / 8, 152 * 16));
         if (G.p <= 16) {
@@ -1086,7 +1196,9 @@ static int launch_group_lo(psr_ctx* ctx, const Group& G, const double* r, double
         count_launch(); k_sweep_full<T><<<fb, wpb * 32, wpb * slot, s>>>(G.count, G.p, rinv, G.sphi, G.sdofs, r, ctx->Wg,
                                                           ctx->W, z, stop);
     } else {
-        return launch_tiles<T>(ctx, G.p, G.tiles, G.ntiles, G.tile_patches, warps, G.rinv, G.sdofs, r, z, stop, s);
+        const bool pairs = std::is_same<T, double>::value && G.rinv_pair != nullptr;
+        return launch_tiles<T>(ctx, G.p, G.tiles, G.ntiles, G.tile_patches, warps, G.rinv, G.sdofs, r, z, stop, s,
+                               pairs ? G.rinv_pair : nullptr, pairs ? G.bexp : nullptr);
     }
     PSR_CHECK_LAUNCH(ctx, "sweep kernel");
     return PSR_OK;
@@ -1146,6 +1258,7 @@ int sweep_prepare(psr_ctx* ctx) {
     PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_staged<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_staged<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_staged<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_staged_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     PSR_CUDA(ctx, cudaFuncSetAttribute(k_sweep_full<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     {
         int rc = tc_prepare();
@@ -1170,6 +1283,7 @@ void free_sweep(psr_ctx* ctx) {
         psr::dev_free(G.wtiles);
         psr::dev_free(G.dbA);
         psr::dev_free(G.bexp);
+        psr::dev_free(G.rinv_pair);
         psr::dev_free(G.rinv_hi);
         psr::dev_free(G.tiles_hi);
         if (G.rinv && !(ctx->A_ext && reinterpret_cast<double*>(G.rinv) >= ctx->A_ext &&

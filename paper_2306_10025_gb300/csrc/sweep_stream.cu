@@ -25,6 +25,7 @@
 // PSR_FP64_NATIVE keeps FP64 entries and FP64 FMAs.  FP32 and BF16 storage
 // multiply in FP32 with x rounded to FP32.
 #include "psr_internal.cuh"
+#include "pairs.cuh"
 
 #include <algorithm>
 
@@ -71,43 +72,6 @@ __device__ __forceinline__ float ld_stream(const __nv_bfloat16* q) {
     unsigned short h;
     asm volatile("ld.global.nc.b16 %0, [%1];" : "=h"(h) : "l"(q));
     return __uint_as_float((unsigned)h << 16);          // BF16 -> FP32 is exact
-}
-
-// v 2^-shift as a pair (hi, lo) of FP32 with integer operations only: hi is
-// v's significand truncated to 24 bits, lo the next 23 bits (truncated), so
-// |v 2^-shift - hi - lo| < 2^-46 |v 2^-shift|.  Scaled values below 2^-126
-// (hi) or 2^-103 (lo) are dropped, which the caller's choice of shift (the
-// largest exponent of the block) makes negligible; FP64 subnormals read as 0;
-// Inf and NaN give NaN.
-__device__ __forceinline__ float2 split_scaled(double v, int shift) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
-    const unsigned h32 = (unsigned)(u >> 32), l32 = (unsigned)u;
-    const unsigned sgn = h32 & 0x80000000u;
-    const int e = (int)((h32 >> 20) & 0x7ffu);
-    const int E = e - 1023 - shift;
-    const unsigned m23 = ((h32 & 0xfffffu) << 3) | (l32 >> 29);
-    const unsigned mlo = (l32 & 0x1fffffffu) >> 6;
-    const int eh = E + 127, el = E - 23 + 127;
-    float hi = (e != 0 && eh > 0) ? __uint_as_float(sgn | ((unsigned)eh << 23) | m23) : 0.f;
-    float lo = 0.f;
-    if (e != 0 && el > 0)
-        lo = __fsub_rn(__uint_as_float(sgn | ((unsigned)el << 23) | mlo), __uint_as_float(sgn | ((unsigned)el << 23)));
-    if (e == 0x7ff) { hi = __uint_as_float(0x7fc00000u); lo = 0.f; }
-    return make_float2(hi, lo);
-}
-
-// (s, c) += (bh + bl)(xh + xl): the product bh xh exactly as p + e (FMA), p
-// added to s exactly (TwoSum), the cross terms, e and the TwoSum error added
-// to c.  Intrinsics keep every operation rounded as written (no contraction).
-__device__ __forceinline__ void pair_fma(float& s, float& c, float bh, float bl, float xh, float xl) {
-    const float p = __fmul_rn(bh, xh);
-    const float e = __fmaf_rn(bh, xh, -p);
-    const float t = __fadd_rn(s, p);
-    const float z = __fsub_rn(t, s);
-    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
-    const float q = __fmaf_rn(bh, xl, __fmul_rn(bl, xh));
-    c = __fadd_rn(c, __fadd_rn(err, __fadd_rn(e, q)));
-    s = t;
 }
 
 template <int MODE>
@@ -308,6 +272,100 @@ int stream_convert(psr_ctx* ctx, Group& G, const double* db64, cudaStream_t s, i
     G.bexp = bexp;
     G.stream = true;
     *bytes = ne * (int64_t)es;
+    return PSR_OK;
+}
+
+// Clustered FP64 entries (m of them) as scaled pairs in the column-major
+// layout of the stream: the same conversion, applied to the database.
+int pair_db_convert(psr_ctx* ctx, Group& G, const double* db64, cudaStream_t s) {
+    const int64_t ne = (int64_t)G.m * G.p * G.p;
+    float2* dst = nullptr;
+    PSR_CUDA(ctx, psr::dev_alloc(&dst, sizeof(float2) * (size_t)std::max<int64_t>(ne, 1)));
+    PSR_CUDA(ctx, psr::dev_alloc(&G.bexp, sizeof(int32_t) * (size_t)std::max(G.m, 1)));
+    const int blocks = std::max(1, std::min(G.m, 152 * 8));
+    count_launch();
+    k_to_stream<SM_PAIR><<<blocks, 256, 0, s>>>(db64, G.m, G.p, 0, dst, G.bexp);
+    PSR_CHECK_LAUNCH(ctx, "pair database conversion");
+    G.rinv_pair = dst;
+    return PSR_OK;
+}
+
+// Clustered sweep, p <= 32, FP64 entries on FP32 pair arithmetic: one patch
+// per thread (warp tiles of patches sharing one entry, as k_sweep_tpp), the
+// entry read as pairs (every lane reads the same element: one transaction),
+// the patch's weighted residual split into pairs after a power-of-two shift
+// that brings its largest entry into [1, 2), each row of B^-1 r_k summed
+// with compensated products, the result unshifted in FP64.  The FP64 pipe
+// keeps the gathers' weighting, the row results and their weighting (about
+// 6p FP64 operations per patch instead of the p^2 FMAs of the FP64 form).
+template <int PM>
+__global__ void __launch_bounds__(256) k_sweep_tpp_pair(const int32_t* __restrict__ wtiles, int nwt, int p, int count,
+                                                        const float2* __restrict__ Bt, const int32_t* __restrict__ bexp,
+                                                        const int32_t* __restrict__ sdofs_t,
+                                                        const double* __restrict__ r, const double* __restrict__ wg,
+                                                        const double* __restrict__ wsc, double* __restrict__ z,
+                                                        const int32_t* __restrict__ stop) {
+    if (stop && *stop) return;
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nwt; t += nw) {
+        const int c = wtiles[3 * t], start = wtiles[3 * t + 1], cnt = wtiles[3 * t + 2];
+        const bool live = lane < cnt;
+        const int k = start + (live ? lane : 0);
+        int dof[PM];
+#pragma unroll
+        for (int a = 0; a < PM; ++a) dof[a] = __ldg(sdofs_t + (int64_t)min(a, p - 1) * count + k);
+        double rv[PM];
+#pragma unroll
+        for (int a = 0; a < PM; ++a) rv[a] = __ldg(r + dof[a]);
+        if (wg) {
+#pragma unroll
+            for (int a = 0; a < PM; ++a) rv[a] *= __ldg(wg + dof[a]);
+        }
+        unsigned emax = 0;
+#pragma unroll
+        for (int a = 0; a < PM; ++a) {
+            const unsigned ex = (unsigned)(__double2hiint(rv[a]) >> 20) & 0x7ffu;
+            if (a < p && ex != 0x7ffu) emax = max(emax, ex);
+        }
+        const int shift = (int)emax - 1023;
+        float2 x[PM];
+#pragma unroll
+        for (int a = 0; a < PM; ++a) x[a] = (live && a < p) ? split_scaled(rv[a], shift) : make_float2(0.f, 0.f);
+        const float2* B = Bt + (int64_t)c * p * p;       // B[a][b] at b * p + a
+        const int sc = shift + __ldg(bexp + c);
+#pragma unroll 1
+        for (int a = 0; a < p; ++a) {
+            float sh = 0.f, sl = 0.f;
+#pragma unroll
+            for (int b = 0; b < PM; ++b) {
+                if (b < p) {
+                    const float2 bv = __ldg(B + b * p + a);
+                    pair_fma(sh, sl, bv.x, bv.y, x[b].x, x[b].y);
+                }
+            }
+            if (live) {
+                const int d = dof[a];
+                atomicAdd(&z[d], ldexp((double)sh + (double)sl, sc) * __ldg(wsc + d));
+            }
+        }
+    }
+}
+
+int launch_sweep_tpp_pair(psr_ctx* ctx, const Group& G, const double* r, double* z, const int32_t* stop,
+                          cudaStream_t s) {
+    const int tb = std::max(1, std::min((G.nwt + 7) / 8, 152 * 16));
+    const float2* Bt = reinterpret_cast<const float2*>(G.rinv_pair);
+    if (G.p <= 16) {
+        count_launch();
+        k_sweep_tpp_pair<16><<<tb, 256, 0, s>>>(G.wtiles, G.nwt, G.p, G.count, Bt, G.bexp, G.sdofs_t, r, ctx->Wg,
+                                                ctx->W, z, stop);
+    } else {
+        count_launch();
+        k_sweep_tpp_pair<32><<<tb, 256, 0, s>>>(G.wtiles, G.nwt, G.p, G.count, Bt, G.bexp, G.sdofs_t, r, ctx->Wg,
+                                                ctx->W, z, stop);
+    }
+    PSR_CHECK_LAUNCH(ctx, "sweep kernel (thread per patch, FP64 pairs)");
     return PSR_OK;
 }
 
