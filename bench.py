@@ -304,35 +304,33 @@ def _variant(L, dev_in, pr, cfg, b, devc, reps, tol, prec, arith, maxit, r_ref=N
     return out
 
 
-def convergence_subline(L, args, devc, hbm):
-    """Clustered vs full storage to 1e-8 on the 3D lognormal Q2 workload
-    (32^3, PCG with SYM weighting): per form the setup and solve seconds
-    (CUDA events, median of 3 after one warm-up), iterations, database size,
-    apply rate, and the speedup of setup + solve over the FP64 full-storage
-    form."""
+def forms_subline(L, key, forms, devc, reps=4, learned=False):
+    """Storage forms of one workload (CONFIGS[key]) side by side: per form the
+    setup and solve seconds (CUDA events, median after one warm-up, L2
+    flushed before each), iterations, relative residual reached, database
+    size, apply rate, and the speedup of setup + solve over the first form
+    (FP64 full storage)."""
     import torch
-    cfg = CONFIGS["diffusion3d"]
+    cfg = CONFIGS[key]
     pr = build_problem(cfg)
     t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=devc)
     dev_in = (t(pr.rowptr, torch.int32), t(pr.colidx, torch.int32), t(pr.vals, torch.float64),
-              t(pr.patch_dofs, torch.int32), None)
+              t(pr.patch_dofs, torch.int32), None if pr.uniform_size else t(pr.patch_offsets, torch.int32))
     b = t(pr.rhs(0), torch.float64)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=devc)
     stream = torch.cuda.current_stream()
-    forms = [("full_fp64", 0.0, "fp64"), ("clustered_fp64", cfg["tol"], "fp64"),
-             ("clustered_fp32", cfg["tol"], "fp32"), ("clustered_bf16", cfg["tol"], "bf16")]
     rows = {}
     for name, tol, prec in forms:
         opts = L.make_opts(tol=tol, store_prec=prec, weighting=cfg["weighting"], krylov=cfg["krylov"], restart=30,
                            rtol=1e-8, maxit=cfg["maxit"])
-        rp, ci, va, dofs, _ = dev_in
+        rp, ci, va, dofs, offs = dev_in
         setups, solves = [], []
-        for rep in range(4):
+        for rep in range(reps):
             flush.zero_()
             e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             x = torch.zeros_like(b)
             e0.record(stream)
-            ctx = L.psr_setup(rp, ci, va, dofs, uniform_size=pr.uniform_size, opts=opts)
+            ctx = L.psr_setup(rp, ci, va, dofs, offsets=offs, uniform_size=pr.uniform_size, opts=opts)
             e1.record(stream)
             info = ctx.solve(b, x)
             e2.record(stream)
@@ -341,7 +339,7 @@ def convergence_subline(L, args, devc, hbm):
                 setups.append(e0.elapsed_time(e1) * 1e-3)
                 solves.append(e1.elapsed_time(e2) * 1e-3)
             st = ctx.stats()
-            if rep < 3:
+            if rep < reps - 1:
                 ctx.destroy()
         ams = _apply_median(ctx, pr.n, 100, devc, flush=flush)
         ctx.destroy()
@@ -350,15 +348,43 @@ def convergence_subline(L, args, devc, hbm):
                       "solve_s": statistics.median(solves), "iterations": info["iterations"],
                       "converged": info["converged"], "relres": info["relres"],
                       "criterion_evals": st["criterion_evals"], "criterion_screened": st["criterion_screened"],
-                      "criterion_exact": st["criterion_exact"], "sweep_dof_per_s": pr.n / ams,
-                      "apply_ms": ams * 1e3}
-    full = rows["full_fp64"]
+                      "criterion_exact": st["criterion_exact"], "alg1_rounds": st["rounds"],
+                      "sweep_dof_per_s": pr.n / ams, "apply_ms": ams * 1e3}
+    full = rows[forms[0][0]]
     for name, r in rows.items():
         r["speedup_setup_plus_solve_vs_full_fp64"] = (full["setup_s"] + full["solve_s"]) / (r["setup_s"] + r["solve_s"])
         r["within_plus_one_iteration"] = bool(r["converged"] and r["iterations"] <= full["iterations"] + 1)
-    return {"workload": cfg["desc"] + f", tol {cfg['tol']}, SYM weighting, rtol 1e-8", "n": pr.n,
-            "n_patches": pr.n_patches, "rhs": "uniform(-1,1) seed 0", "forms": rows,
-            "learned": learned_subline(L, cfg, pr, dev_in, b, devc)}
+    out = {"workload": cfg["desc"] + f", {cfg['krylov']}, {cfg['weighting']} weighting, rtol 1e-8, "
+                                     f"at most {cfg['maxit']} iterations",
+           "n": pr.n, "n_patches": pr.n_patches, "patch_sizes": sorted(set(pr.patch_sizes.tolist())),
+           "rhs": "uniform(-1,1) seed 0", "forms": rows}
+    if learned:
+        out["learned"] = learned_subline(L, cfg, pr, dev_in, b, devc)
+    return out
+
+
+def config_sublines(L, devc):
+    """The other workloads of the benchmark, full storage against the
+    clustered forms: 2D Q2 Poisson 16^2 (tol 1e-12), graded 2D Stokes 128^2
+    (tol 1e-3 .. 1e-1, FP64 and FP32 entries), 3D Nedelec 64^3 (FP32 / BF16
+    entries, tol 0.1), 3D lognormal Q2 32^3 (tol 0.1, FP64 / FP32 / BF16, and
+    the learned assignment on a matrix sequence)."""
+    return {
+        "poisson2d_16": forms_subline(L, "poisson2d", [("full_fp64", 0.0, "fp64"), ("clustered_fp64", 1e-12, "fp64")],
+                                      devc),
+        "stokes2d_128": forms_subline(L, "stokes2d", [("full_fp64", 0.0, "fp64"),
+                                                      ("clustered_fp64_tol_1e-3", 1e-3, "fp64"),
+                                                      ("clustered_fp64", 1e-2, "fp64"),
+                                                      ("clustered_fp32", 1e-2, "fp32"),
+                                                      ("clustered_fp64_tol_1e-1", 1e-1, "fp64")], devc),
+        "nedelec3d_64": forms_subline(L, "nedelec3d", [("full_fp64", 0.0, "fp64"), ("full_fp32", 0.0, "fp32"),
+                                                       ("full_bf16", 0.0, "bf16"), ("clustered_fp32", 0.1, "fp32"),
+                                                       ("clustered_bf16", 0.1, "bf16")], devc, reps=2),
+        "diffusion3d_32": forms_subline(L, "diffusion3d", [("full_fp64", 0.0, "fp64"),
+                                                           ("clustered_fp64", 0.1, "fp64"),
+                                                           ("clustered_fp32", 0.1, "fp32"),
+                                                           ("clustered_bf16", 0.1, "bf16")], devc, learned=True),
+    }
 
 
 def learned_subline(L, cfg, pr, dev_in, b, devc):
@@ -559,7 +585,7 @@ def run_gpu(args, cfg, ws, rank, local):
         for name, pv, ar in (("fp64_native", "fp64", "native"), ("fp32", "fp32", "pairs"), ("bf16", "bf16", "pairs")):
             variants[name] = _variant(L, dev_in, pr, cfg, b, devc, 50, tol, pv, ar, maxit, r_ref, z_ref)
         out["precisions"] = variants
-        out["per_config"] = {"diffusion3d_32": convergence_subline(L, args, devc, hbm)}
+        out["per_config"] = config_sublines(L, devc)
 
     # end to end: host (pinned) inputs -> device -> setup + solve -> x to host
     if not args.no_e2e:

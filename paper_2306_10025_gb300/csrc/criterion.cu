@@ -1168,6 +1168,10 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_rounds_multi(
         const unsigned long long R = (K == KC) ? ~0ull : ((1ull << K) - 1ull);
         ok = phase_b(seed, j0, R, K, 0, par);
     }
+    // candidates per round: 64, or fewer while rounds make few entries (a
+    // round's pairs among its candidates grow as K^2; on the graded Stokes
+    // mesh about 3 of 64 neighbouring candidates are entries)
+    int klim = KC;
     for (int round = 0; ok && round < count; ++round) {
         const int par = npass & 1;
         ++npass;
@@ -1193,14 +1197,14 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_rounds_multi(
             }
             pos += incl - c;
             unsigned b = bits;
-            while (b && pos < KC) {
+            while (b && pos < klim) {
                 scand[pos++] = wd * 32 + (__ffs(b) - 1);
                 b &= b - 1;
             }
             __syncthreads();
-            if (threadIdx.x == 0) s_found = min(tot, KC);
+            if (threadIdx.x == 0) s_found = min(tot, klim);
             __syncthreads();
-            if (s_found >= KC) break;
+            if (s_found >= klim) break;
         }
         const int K = s_found;
         if (K == 0) break;                         // every patch assigned (same in every block)
@@ -1335,6 +1339,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_rounds_multi(
         // ---- phase B: every other open patch against the entries of R
         if (!phase_b(own, m, R, nR, scand[K - 1] + 1, par)) break;
         m += nR;
+        klim = min(KC, max(16, 2 * nR + 8));       // the same in every block
     }
     // the counts are per thread here: sum each warp's before the atomics
 #pragma unroll

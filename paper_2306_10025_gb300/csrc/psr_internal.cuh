@@ -265,7 +265,10 @@ int build_grouped_tables(psr_ctx* ctx);
 void free_sweep(psr_ctx* ctx);
 
 // sweep_stream.cu (full-storage groups: column-major inverses, thread per row)
-int stream_convert(psr_ctx* ctx, Group& G, const double* db64, cudaStream_t s, int64_t* bytes);
+// entry_of (device, count, may be NULL): the entry of each sorted patch, for
+// a clustered group applied like full storage (one streamed inverse per patch)
+int stream_convert(psr_ctx* ctx, Group& G, const double* db64, cudaStream_t s, int64_t* bytes,
+                   const int32_t* entry_of = nullptr);
 int stream_build_table(psr_ctx* ctx);
 int launch_sweep_stream(psr_ctx* ctx, const double* r, double* z, const int32_t* stop, cudaStream_t s);
 // Clustered FP64 database of a group (p <= 32) as scaled FP32 pairs

@@ -753,15 +753,21 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<std::vector<int32_t>>& gi
         const int64_t ne = (int64_t)G.m * p * p;
         const bool in_place = (db64 == ctx->A_ext + G.mat_off);
         int n_bad = 0;
+        // weakly clustered (more than a quarter of the patches are entries):
+        // tiles would hold one or two patches each, so the group is applied
+        // like full storage, every patch's entry inverse streamed -- unless the
+        // tensor cores are forced or an entry needs its FP64 fallback tiles
+        bool expand = G.m < G.count && (int64_t)G.m * 4 > G.count && ctx->opts.sweep_kernel != PSR_SWEEP_TENSOR;
         if (G.m < G.count) {
             int rc = check_precision(ctx, G, db64, prec, s, &n_bad);
             if (rc != PSR_OK) return rc;
-            n_fallback += n_bad;
+            if (n_bad > 0) expand = false;
+            if (!expand) n_fallback += n_bad;
         }
-        if (G.m == G.count) {
-            // every patch its own entry: column-major stream (sweep_stream.cu)
+        if (G.m == G.count || expand) {
+            // every patch its own entry (or expanded to it): column-major stream (sweep_stream.cu)
             int64_t fb = 0;
-            int rc = stream_convert(ctx, G, db64, s, &fb);
+            int rc = stream_convert(ctx, G, db64, s, &fb, expand ? G.sphi : nullptr);
             if (rc != PSR_OK) return rc;
             PSR_CUDA(ctx, cudaStreamSynchronize(s));
             if (!in_place) psr::dev_free(db64);
@@ -823,7 +829,7 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<std::vector<int32_t>>& gi
             if (!in_place) psr::dev_free(db64);
         }
         G.h_sorted_phi = hs;
-        if (!G.tc && G.m < G.count && p <= 32) {
+        if (!G.tc && !G.stream && G.m < G.count && p <= 32) {
             std::vector<int32_t> wt;
             PSR_CUDA(ctx, psr::dev_alloc(&G.sdofs_t, sizeof(int32_t) * (size_t)count * p));
             count_launch();

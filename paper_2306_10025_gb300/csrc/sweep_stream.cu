@@ -193,17 +193,18 @@ __global__ void __launch_bounds__(256) k_sweep_stream(const StreamDesc* __restri
 }
 
 // FP64 row-major entries -> the column-major storage of the mode; one block
-// per entry.  SM_PAIR: the scale exponent s with max|B| 2^-s in [1/2, 1)
+// per output matrix (output i from entry idx[i], or entry i without idx).  SM_PAIR: the scale exponent s with max|B| 2^-s in [1/2, 1)
 // (0 for a zero matrix), hi = fl32(B 2^-s), lo = fl32(B 2^-s - hi).
 // sym (FP32 / BF16 only): (B + B^T) / 2 before rounding.
 template <int MODE>
 __global__ void __launch_bounds__(256) k_to_stream(const double* __restrict__ src, int m, int p, int sym,
-                                                   void* __restrict__ dst, int32_t* __restrict__ bexp) {
+                                                   void* __restrict__ dst, int32_t* __restrict__ bexp,
+                                                   const int32_t* __restrict__ idx) {
     using ST = typename StreamT<MODE>::st;
     __shared__ double red[8];
     const int pp = p * p;
     for (int i = blockIdx.x; i < m; i += gridDim.x) {
-        const double* B = src + (int64_t)i * pp;
+        const double* B = src + (int64_t)(idx ? idx[i] : i) * pp;
         ST* out = reinterpret_cast<ST*>(dst) + (int64_t)i * pp;
         int ex = 0;
         if constexpr (MODE == SM_PAIR) {
@@ -246,9 +247,11 @@ static size_t stream_elem_bytes(int mode) {
     return (mode == SM_PAIR || mode == SM_F64) ? 8 : (mode == SM_F32 ? 4 : 2);
 }
 
-int stream_convert(psr_ctx* ctx, Group& G, const double* db64, cudaStream_t s, int64_t* bytes) {
+int stream_convert(psr_ctx* ctx, Group& G, const double* db64, cudaStream_t s, int64_t* bytes,
+                   const int32_t* entry_of) {
     const int mode = stream_mode(ctx);
-    const int64_t ne = (int64_t)G.m * G.p * G.p;
+    const int nmat = entry_of ? G.count : G.m;
+    const int64_t ne = (int64_t)nmat * G.p * G.p;
     const size_t es = stream_elem_bytes(mode);
     void* dst = nullptr;
     if (psr::dev_alloc(&dst, es * (size_t)std::max<int64_t>(ne, 1)) != cudaSuccess) {
@@ -257,15 +260,15 @@ int stream_convert(psr_ctx* ctx, Group& G, const double* db64, cudaStream_t s, i
         return PSR_ERR_OOM;
     }
     int32_t* bexp = nullptr;
-    if (mode == SM_PAIR) PSR_CUDA(ctx, psr::dev_alloc(&bexp, sizeof(int32_t) * (size_t)std::max(G.m, 1)));
-    const int blocks = std::max(1, std::min(G.m, 152 * 16));
+    if (mode == SM_PAIR) PSR_CUDA(ctx, psr::dev_alloc(&bexp, sizeof(int32_t) * (size_t)std::max(nmat, 1)));
+    const int blocks = std::max(1, std::min(nmat, 152 * 16));
     const int sym = ctx->opts.symmetrize;
     count_launch();
     switch (mode) {
-        case SM_PAIR: k_to_stream<SM_PAIR><<<blocks, 256, 0, s>>>(db64, G.m, G.p, sym, dst, bexp); break;
-        case SM_F64: k_to_stream<SM_F64><<<blocks, 256, 0, s>>>(db64, G.m, G.p, sym, dst, bexp); break;
-        case SM_F32: k_to_stream<SM_F32><<<blocks, 256, 0, s>>>(db64, G.m, G.p, sym, dst, bexp); break;
-        default: k_to_stream<SM_BF16><<<blocks, 256, 0, s>>>(db64, G.m, G.p, sym, dst, bexp); break;
+        case SM_PAIR: k_to_stream<SM_PAIR><<<blocks, 256, 0, s>>>(db64, nmat, G.p, sym, dst, bexp, entry_of); break;
+        case SM_F64: k_to_stream<SM_F64><<<blocks, 256, 0, s>>>(db64, nmat, G.p, sym, dst, bexp, entry_of); break;
+        case SM_F32: k_to_stream<SM_F32><<<blocks, 256, 0, s>>>(db64, nmat, G.p, sym, dst, bexp, entry_of); break;
+        default: k_to_stream<SM_BF16><<<blocks, 256, 0, s>>>(db64, nmat, G.p, sym, dst, bexp, entry_of); break;
     }
     PSR_CHECK_LAUNCH(ctx, "k_to_stream");
     G.rinv = dst;
@@ -284,7 +287,7 @@ int pair_db_convert(psr_ctx* ctx, Group& G, const double* db64, cudaStream_t s) 
     PSR_CUDA(ctx, psr::dev_alloc(&G.bexp, sizeof(int32_t) * (size_t)std::max(G.m, 1)));
     const int blocks = std::max(1, std::min(G.m, 152 * 8));
     count_launch();
-    k_to_stream<SM_PAIR><<<blocks, 256, 0, s>>>(db64, G.m, G.p, 0, dst, G.bexp);
+    k_to_stream<SM_PAIR><<<blocks, 256, 0, s>>>(db64, G.m, G.p, 0, dst, G.bexp, nullptr);
     PSR_CHECK_LAUNCH(ctx, "pair database conversion");
     G.rinv_pair = dst;
     return PSR_OK;
