@@ -258,10 +258,30 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
             int32_t* first = nullptr;
             CK(psr::dev_alloc(&sing, sizeof(int32_t) * (size_t)np));
             CK(psr::dev_alloc(&first, sizeof(int32_t)));
+            // FP64 pairs, p > 32: the inverses go straight into the streamed
+            // sweep's layout (the sweep layout finds the group streamed)
+            const bool fused = op.store_prec == PSR_PREC_FP64 && op.fp64_arith == PSR_FP64_PAIRS;
             for (auto& G : ctx->groups) {
                 double* base = ctx->A_ext + G.mat_off;
-                rc = launch_batched_inverse(base, (int64_t)G.p * G.p, nullptr, G.count, G.p, base,
-                                            (int64_t)G.p * G.p, sing, s);
+                if (fused && G.p > 32) {
+                    const size_t ne = (size_t)G.count * G.p * G.p;
+                    float2* dst = nullptr;
+                    if (psr::dev_alloc(&dst, sizeof(float2) * std::max<size_t>(ne, 1)) != cudaSuccess) {
+                        cudaGetLastError();
+                        psr::dev_free(sing);
+                        psr::dev_free(first);
+                        set_error(ctx, "out of device memory for the streamed inverses");
+                        FAIL(PSR_ERR_OOM);
+                    }
+                    CK(psr::dev_alloc(&G.bexp, sizeof(int32_t) * (size_t)std::max(G.count, 1)));
+                    rc = launch_batched_inverse_pairs(base, G.count, G.p, dst, G.bexp, sing, s);
+                    G.stream = true;
+                    G.rinv = dst;
+                } else {
+                    rc = launch_batched_inverse(base, (int64_t)G.p * G.p, nullptr, G.count, G.p, base,
+                                                (int64_t)G.p * G.p, sing, s);
+                    G.rinv = base;
+                }
                 if (rc != PSR_OK) { psr::dev_free(sing); psr::dev_free(first); goto fail; }
                 int32_t big = 0x7fffffff;
                 CK(cudaMemcpyAsync(first, &big, sizeof(int32_t), cudaMemcpyHostToDevice, s));
@@ -270,7 +290,6 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
                 CK(cudaMemcpyAsync(&h_first, first, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
                 CK(cudaStreamSynchronize(s));
                 G.m = G.count;
-                G.rinv = base;
                 CK(psr::dev_alloc(&G.sphi, sizeof(int32_t) * (size_t)G.count));
                 count_launch(); k_iota<<<std::max(1, std::min(G.count / 256 + 1, 1024)), 256, 0, s>>>(G.sphi, G.count);
                 G.h_rep.resize(G.count);

@@ -8,6 +8,7 @@
 // multiply-adds instead of the 2p^3 of LU + two triangular solves per column.
 #include "psr_internal.cuh"
 #include "dense.cuh"
+#include "pairs.cuh"
 
 namespace psr {
 
@@ -44,7 +45,8 @@ __global__ void k_batched_inverse(const double* __restrict__ A, int64_t stride_i
 }
 
 int launch_batched_inverse_block(const double* A, int64_t stride_in, const int32_t* index, int32_t batch, int32_t p,
-                                 double* Ainv, int64_t stride_out, int32_t* singular, cudaStream_t s);
+                                 double* Ainv, int64_t stride_out, int32_t* singular, cudaStream_t s,
+                                 float2* pout = nullptr, int32_t* pexp = nullptr);
 
 int launch_batched_inverse(const double* A, int64_t stride_in, const int32_t* index, int32_t batch,
                            int32_t p, double* Ainv, int64_t stride_out, int32_t* singular,
@@ -104,10 +106,18 @@ __device__ __forceinline__ long long abs_key(double x) {
     return b > 0x7ff0000000000000LL ? -1LL : b;
 }
 
+// pout (may be NULL): instead of Ainv, write each inverse in the streamed
+// sweep's FP64-pair layout -- column-major (hi, lo) FP32 pairs of B 2^-e with
+// e the frexp exponent of max|B| (0 for a zero or singular matrix, whose
+// entries are NaN), e to pexp -- without the FP64 round trip through memory.
+// The pairs are split with integer operations (truncated, |error| < 2^-46
+// |B|) where the separate conversion rounds (2^-48).
 __global__ void __launch_bounds__(INV_BT) k_batched_inverse_block(const double* __restrict__ A, int64_t stride_in,
                                                                   const int32_t* __restrict__ index, int32_t batch,
                                                                   int32_t p, double* __restrict__ Ainv,
-                                                                  int64_t stride_out, int32_t* __restrict__ singular) {
+                                                                  int64_t stride_out, int32_t* __restrict__ singular,
+                                                                  float2* __restrict__ pout,
+                                                                  int32_t* __restrict__ pexp) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int ld = p + 1;
     const int t = threadIdx.x;
@@ -197,16 +207,55 @@ __global__ void __launch_bounds__(INV_BT) k_batched_inverse_block(const double* 
             }
             __syncthreads();
         }
-        double* out = Ainv + b * stride_out;
         const double nanv = __longlong_as_double(0x7ff8000000000000LL);
-        for (int e = t; e < p * p; e += nt) out[e] = sing ? nanv : S[(e / p) * ld + (e % p)];
+        if (pout) {
+            // max |B| through the integer order key (NaN ranks lowest), so
+            // the reduction spends no FP64 instruction
+            long long km = -1;
+            if (!sing)
+                for (int e = t; e < p * p; e += nt) km = max(km, abs_key(S[(e / p) * ld + (e % p)]));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) km = max(km, __shfl_xor_sync(0xffffffffu, km, o));
+            __syncthreads();                      // red[] is free again
+            if (lane == 0) red[wid] = __longlong_as_double(km);
+            __syncthreads();
+            km = __double_as_longlong(red[0]);
+            for (int w = 1; w < nw; ++w) km = max(km, __double_as_longlong(red[w]));
+            const double mx = km > 0 ? __longlong_as_double(km) : 0.0;
+            int ex = 0;
+            const bool finite = km < 0x7ff0000000000000LL;   // an infinite entry: the matrix reads as NaN
+            if (mx > 0.0 && finite) frexp(mx, &ex);
+            // B 2^-ex split into (hi, lo) with integer operations only (the
+            // significand's top 24 bits and the next 23, |error| < 2^-46 |B|):
+            // FP64 <-> FP32 conversions would run on the FP64 pipe, which the
+            // elimination above keeps busy
+            float2* out = pout + b * (int64_t)p * p;
+            for (int e = t; e < p * p; e += nt) {
+                const int cb = e / p, ra = e - cb * p;           // out[e] = B[ra][cb]
+                out[e] = split_scaled(sing || !finite ? nanv : S[ra * ld + cb], ex);
+            }
+            if (t == 0) pexp[b] = ex;
+        } else {
+            double* out = Ainv + b * stride_out;
+            for (int e = t; e < p * p; e += nt) out[e] = sing ? nanv : S[(e / p) * ld + (e % p)];
+        }
         if (singular && t == 0) singular[b] = sing ? 1 : 0;
         __syncthreads();
     }
 }
 
+// p > 32: the inverses written straight in the streamed sweep's FP64-pair
+// layout (pout, pexp), the FP64 copy skipped.
+int launch_batched_inverse_pairs(const double* A, int32_t batch, int32_t p, float2* pout, int32_t* pexp,
+                                 int32_t* singular, cudaStream_t s) {
+    if (batch <= 0) return PSR_OK;
+    if (p <= 32 || p > 128) return PSR_ERR_INVALID_ARG;
+    return launch_batched_inverse_block(A, (int64_t)p * p, nullptr, batch, p, nullptr, 0, singular, s, pout, pexp);
+}
+
 int launch_batched_inverse_block(const double* A, int64_t stride_in, const int32_t* index, int32_t batch, int32_t p,
-                                 double* Ainv, int64_t stride_out, int32_t* singular, cudaStream_t s) {
+                                 double* Ainv, int64_t stride_out, int32_t* singular, cudaStream_t s,
+                                 float2* pout, int32_t* pexp) {
     const size_t smem = inv_block_bytes(p);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_batched_inverse_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -217,7 +266,8 @@ int launch_batched_inverse_block(const double* A, int64_t stride_in, const int32
     if (blocks > 152 * 16) blocks = 152 * 16;
     count_launch();
     const int nt = 32 * ((p + 31) / 32);
-    k_batched_inverse_block<<<(int)blocks, nt, smem, s>>>(A, stride_in, index, batch, p, Ainv, stride_out, singular);
+    k_batched_inverse_block<<<(int)blocks, nt, smem, s>>>(A, stride_in, index, batch, p, Ainv, stride_out, singular,
+                                                          pout, pexp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "k_batched_inverse_block");
     return PSR_OK;

@@ -239,6 +239,10 @@ int launch_multiplicity(const int32_t* dofs, int64_t total, int32_t n, int32_t* 
 int launch_batched_inverse(const double* A, int64_t stride_in, const int32_t* index,
                            int32_t batch, int32_t p, double* Ainv, int64_t stride_out,
                            int32_t* singular, cudaStream_t s);
+// 33 <= p <= 128: inverses written in the streamed sweep's FP64-pair layout
+// (column-major scaled (hi, lo) pairs and their exponents), no FP64 copy
+int launch_batched_inverse_pairs(const double* A, int32_t batch, int32_t p, float2* pout, int32_t* pexp,
+                                 int32_t* singular, cudaStream_t s);
 
 // criterion.cu
 struct RoundState;

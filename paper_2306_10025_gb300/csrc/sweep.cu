@@ -764,7 +764,10 @@ int build_sweep_layout(psr_ctx* ctx, const std::vector<std::vector<int32_t>>& gi
             if (n_bad > 0) expand = false;
             if (!expand) n_fallback += n_bad;
         }
-        if (G.m == G.count || expand) {
+        if (G.stream) {
+            // inverses already written in the stream layout by the setup
+            factor_bytes += (int64_t)G.count * p * p * (int64_t)sizeof(float2);
+        } else if (G.m == G.count || expand) {
             // every patch its own entry (or expanded to it): column-major stream (sweep_stream.cu)
             int64_t fb = 0;
             int rc = stream_convert(ctx, G, db64, s, &fb, expand ? G.sphi : nullptr);
