@@ -54,45 +54,37 @@ int validate_inputs(psr_ctx* ctx, const psr_csr* A, const int32_t* offsets, cons
     return PSR_OK;
 }
 
-// One warp per (patch k, local row i): A_k[i][j] = A(dofs_k[i], dofs_k[j]),
-// found by binary search of the sorted CSR row; an absent entry is 0.
-// offsets == nullptr means every patch has pmax DOFs.
+// One warp per patch k, its local rows i in turn: A_k[i][j] = A(dofs_k[i],
+// dofs_k[j]), found by binary search of the sorted CSR row; an absent entry
+// is 0.  offsets == nullptr means every patch has pmax DOFs.  (A warp per
+// (patch, row) had to find its patch by a binary search of the offsets, 17
+// dependent loads per row on the 3D Stokes 48^3 map.)
 __global__ void k_extract(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
                           const double* __restrict__ vals, const int32_t* __restrict__ offsets,
                           const int32_t* __restrict__ dofs, const int64_t* __restrict__ mat_off,
                           int32_t n_patches, int32_t pmax, int64_t total, double* __restrict__ out) {
-    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t f = warp; f < total; f += nwarps) {
-        int k, start, pk;
-        if (offsets) {
-            int lo = 0, hi = n_patches - 1;            // last k with offsets[k] <= f
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (offsets[mid] <= f) lo = mid; else hi = mid - 1;
+    (void)total;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // a warp per patch (its rows in turn, the lanes over its columns)
+    for (int64_t k = warp; k < n_patches; k += nwarps) {
+        const int start = offsets ? offsets[k] : (int)(k * pmax);
+        const int pk = offsets ? offsets[k + 1] - start : pmax;
+        const int64_t base0 = offsets ? mat_off[k] : k * (int64_t)pmax * pmax;
+        for (int i = 0; i < pk; ++i) {
+            const int row = dofs[start + i];
+            const int rs = rowptr[row], re = rowptr[row + 1];
+            const int64_t base = base0 + (int64_t)i * pk;
+            for (int j = lane; j < pk; j += 32) {
+                const int col = dofs[start + j];
+                int lo = rs, hi = re;                   // first e with colidx[e] >= col
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (colidx[mid] < col) lo = mid + 1; else hi = mid;
+                }
+                out[base + j] = (lo < re && colidx[lo] == col) ? vals[lo] : 0.0;
             }
-            k = lo;
-            start = offsets[k];
-            pk = offsets[k + 1] - start;
-        } else {
-            k = (int)(f / pmax);
-            start = k * pmax;
-            pk = pmax;
-        }
-        int i = (int)(f - start);
-        int row = dofs[f];
-        int rs = rowptr[row], re = rowptr[row + 1];
-        int64_t base = (offsets ? mat_off[k] : (int64_t)k * pmax * pmax) + (int64_t)i * pk;
-        for (int j = lane; j < pk; j += 32) {
-            int col = dofs[start + j];
-            int lo = rs, hi = re;                       // first e with colidx[e] >= col
-            while (lo < hi) {
-                int mid = (lo + hi) >> 1;
-                if (colidx[mid] < col) lo = mid + 1; else hi = mid;
-            }
-            double v = (lo < re && colidx[lo] == col) ? vals[lo] : 0.0;
-            out[base + j] = v;
         }
     }
 }
@@ -100,7 +92,7 @@ __global__ void k_extract(const int32_t* __restrict__ rowptr, const int32_t* __r
 int launch_extract(const int32_t* rowptr, const int32_t* colidx, const double* vals,
                    const int32_t* offsets, const int32_t* dofs, const int64_t* mat_off,
                    int32_t n_patches, int32_t pmax, int64_t total, double* A_out, cudaStream_t s) {
-    int64_t warps_needed = total;
+    int64_t warps_needed = n_patches;
     int64_t blocks = (warps_needed * 32 + 255) / 256;
     if (blocks > 152 * 64) blocks = 152 * 64;
     if (blocks < 1) blocks = 1;
