@@ -241,6 +241,42 @@ __global__ void k_sell_fill(const int32_t* __restrict__ rowptr, const int32_t* _
 // before being cut into slices, and rowmap gives each slice row its row of A.
 constexpr int SELL_SIGMA = 1024;
 
+// The row map of the sorted slices: within each window of SELL_SIGMA rows
+// (a block each) the rows in decreasing order of length, ties in row order (a
+// stable sort), by ranking every row against the window's others in shared
+// memory.  Positions past the last row keep -1.
+__global__ void __launch_bounds__(SELL_SIGMA) k_sell_sort_windows(const int32_t* __restrict__ rowptr, int n,
+                                                                  int32_t* __restrict__ rowmap) {
+    __shared__ int32_t slen[SELL_SIGMA];
+    const int w0 = blockIdx.x * SELL_SIGMA;
+    const int cnt = min(SELL_SIGMA, n - w0);
+    const int i = threadIdx.x;
+    if (i < cnt) slen[i] = rowptr[w0 + i + 1] - rowptr[w0 + i];
+    __syncthreads();
+    if (i < cnt) {
+        const int li = slen[i];
+        int rank = 0;
+        for (int j = 0; j < cnt; ++j) {
+            const int lj = slen[j];
+            rank += (lj > li) || (lj == li && j < i);
+        }
+        rowmap[w0 + rank] = w0 + i;
+    }
+}
+
+// Slice widths of the sorted slices: the longest mapped row of each slice.
+__global__ void k_sell_width_map(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ rowmap,
+                                 int nslices, int32_t* __restrict__ width) {
+    const int lane = threadIdx.x & 31;
+    const int sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (sl >= nslices) return;
+    const int r = rowmap[sl * 32 + lane];
+    int len = (r >= 0) ? rowptr[r + 1] - rowptr[r] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
+    if (lane == 0) width[sl] = len;
+}
+
 __global__ void k_sell_fill_map(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
                                 const double* __restrict__ vals, const int32_t* __restrict__ rowmap, int nslices,
                                 const int64_t* __restrict__ sptr, int32_t* __restrict__ scols,
@@ -1549,29 +1585,21 @@ int krylov_alloc(psr_ctx* ctx) {
         int64_t natural = 0;
         for (int q = 0; q < w.nslices; ++q) natural += 32 * (int64_t)hw[q];
         // more than 15 % padding on a large matrix: length-sorted windows
-        std::vector<int32_t> hmap;
-        if (ctx->nnz > 0 && (double)natural > 1.15 * (double)ctx->nnz && ctx->n >= 4 * SELL_SIGMA) {
-            std::vector<int32_t> hrp((size_t)ctx->n + 1);
-            PSR_CUDA(ctx, cudaMemcpy(hrp.data(), ctx->rowptr, sizeof(int32_t) * hrp.size(), cudaMemcpyDeviceToHost));
-            hmap.assign((size_t)w.nslices * 32, -1);
-            std::vector<int32_t> idx;
-            for (int w0 = 0; w0 < ctx->n; w0 += SELL_SIGMA) {
-                const int w1 = std::min(ctx->n, w0 + SELL_SIGMA);
-                idx.resize((size_t)(w1 - w0));
-                for (int i = w0; i < w1; ++i) idx[(size_t)(i - w0)] = i;
-                std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
-                    return hrp[a + 1] - hrp[a] > hrp[b + 1] - hrp[b];
-                });
-                std::copy(idx.begin(), idx.end(), hmap.begin() + w0);
-            }
-            for (int q = 0; q < w.nslices; ++q) {
-                int mx = 0;
-                for (int l = 0; l < 32; ++l) {
-                    const int r = hmap[(size_t)q * 32 + l];
-                    if (r >= 0) mx = std::max(mx, hrp[r + 1] - hrp[r]);
-                }
-                hw[q] = mx;
-            }
+        // more than 15 % padding on a large matrix: length-sorted windows,
+        // their row map built on the device
+        const bool sorted = ctx->nnz > 0 && (double)natural > 1.15 * (double)ctx->nnz && ctx->n >= 4 * SELL_SIGMA;
+        if (sorted) {
+            PSR_CUDA(ctx, psr::dev_alloc(&w.sell_row, sizeof(int32_t) * (size_t)w.nslices * 32));
+            PSR_CUDA(ctx, cudaMemset(w.sell_row, 0xff, sizeof(int32_t) * (size_t)w.nslices * 32));
+            count_launch();
+            k_sell_sort_windows<<<(ctx->n + SELL_SIGMA - 1) / SELL_SIGMA, SELL_SIGMA>>>(ctx->rowptr, ctx->n, w.sell_row);
+            int32_t* widths2 = nullptr;
+            PSR_CUDA(ctx, psr::dev_alloc(&widths2, sizeof(int32_t) * (size_t)w.nslices));
+            count_launch();
+            k_sell_width_map<<<(w.nslices + 7) / 8, 256>>>(ctx->rowptr, w.sell_row, w.nslices, widths2);
+            PSR_CHECK_LAUNCH(ctx, "SELL row map");
+            PSR_CUDA(ctx, cudaMemcpy(hw.data(), widths2, sizeof(int32_t) * hw.size(), cudaMemcpyDeviceToHost));
+            psr::dev_free(widths2);
         }
         std::vector<int64_t> hp((size_t)w.nslices + 1, 0);
         for (int q = 0; q < w.nslices; ++q) hp[q + 1] = hp[q] + 32 * (int64_t)hw[q];
@@ -1581,12 +1609,10 @@ int krylov_alloc(psr_ctx* ctx) {
         PSR_CUDA(ctx, psr::dev_alloc(&w.sell_cols, sizeof(int32_t) * (size_t)total));
         PSR_CUDA(ctx, psr::dev_alloc(&w.sell_vals, sizeof(double) * (size_t)total));
         count_launch();
-        if (hmap.empty()) {
+        if (!sorted) {
             k_sell_fill<<<(w.nslices * 32 + 255) / 256, 256>>>(ctx->rowptr, ctx->colidx, ctx->vals, ctx->n, w.nslices,
                                                                 w.sell_ptr, w.sell_cols, w.sell_vals);
         } else {
-            PSR_CUDA(ctx, psr::dev_alloc(&w.sell_row, sizeof(int32_t) * hmap.size()));
-            PSR_CUDA(ctx, cudaMemcpy(w.sell_row, hmap.data(), sizeof(int32_t) * hmap.size(), cudaMemcpyHostToDevice));
             k_sell_fill_map<<<(w.nslices * 32 + 255) / 256, 256>>>(ctx->rowptr, ctx->colidx, ctx->vals, w.sell_row,
                                                                     w.nslices, w.sell_ptr, w.sell_cols, w.sell_vals);
         }
