@@ -74,6 +74,13 @@ __device__ __forceinline__ float ld_stream(const __nv_bfloat16* q) {
     return __uint_as_float((unsigned)h << 16);          // BF16 -> FP32 is exact
 }
 
+// Two BF16 of one row (columns 2c and 2c + 1, the lower address first) as FP32.
+__device__ __forceinline__ float2 ld_stream_bf16x2(const unsigned* q) {
+    unsigned w;
+    asm volatile("ld.global.nc.b32 %0, [%1];" : "=r"(w) : "l"(q));
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(256) k_sweep_stream(const StreamDesc* __restrict__ gdesc, int ng, int total_rb,
                                                       const double* __restrict__ r, const double* __restrict__ wg,
@@ -149,7 +156,7 @@ __global__ void __launch_bounds__(256) k_sweep_stream(const StreamDesc* __restri
         if (gr < R) {
             const int k = (int)(gr / p);
             const int a = (int)(gr - (int64_t)k * p);
-            const ST* col = Bt + (int64_t)k * p * p + a;
+            const ST* col = Bt + (int64_t)k * p * p + a;   // BF16: column pairs, indexed below
             const XT* xk = xs + (k - k0) * p;
             const int dof = __ldg(sdofs + (int64_t)k * p + a);
             double y;
@@ -175,15 +182,40 @@ __global__ void __launch_bounds__(256) k_sweep_stream(const StreamDesc* __restri
             } else {
                 using CT = typename StreamT<MODE>::xt;
                 CT acc = (CT)0;
-                int b = 0;
-                for (; b + 8 <= p; b += 8) {
-                    CT bv[8];
+                if constexpr (MODE == SM_BF16) {
+                    // columns in pairs: lane a reads (B[a][2c], B[a][2c+1]) as
+                    // one 4-byte word, 128 bytes per warp load
+                    const int pc = (p + 1) >> 1;
+                    const unsigned* col2 = reinterpret_cast<const unsigned*>(Bt) + (int64_t)k * p * pc + a;
+                    const int full = p >> 1;
+                    int c = 0;
+                    for (; c + 4 <= full; c += 4) {
+                        float2 bv[4];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) bv[u] = (CT)ld_stream(col + (int64_t)(b + u) * p);
+                        for (int u = 0; u < 4; ++u) bv[u] = ld_stream_bf16x2(col2 + (int64_t)(c + u) * p);
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) acc = fma(bv[u], xk[b + u], acc);
+                        for (int u = 0; u < 4; ++u) {
+                            acc = fma(bv[u].x, xk[2 * (c + u)], acc);
+                            acc = fma(bv[u].y, xk[2 * (c + u) + 1], acc);
+                        }
+                    }
+                    for (; c < full; ++c) {
+                        const float2 bv = ld_stream_bf16x2(col2 + (int64_t)c * p);
+                        acc = fma(bv.x, xk[2 * c], acc);
+                        acc = fma(bv.y, xk[2 * c + 1], acc);
+                    }
+                    if (p & 1) acc = fma(ld_stream_bf16x2(col2 + (int64_t)full * p).x, xk[p - 1], acc);
+                } else {
+                    int b = 0;
+                    for (; b + 8 <= p; b += 8) {
+                        CT bv[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) bv[u] = (CT)ld_stream(col + (int64_t)(b + u) * p);
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) acc = fma(bv[u], xk[b + u], acc);
+                    }
+                    for (; b < p; ++b) acc = fma((CT)ld_stream(col + (int64_t)b * p), xk[b], acc);
                 }
-                for (; b < p; ++b) acc = fma((CT)ld_stream(col + (int64_t)b * p), xk[b], acc);
                 y = (double)acc;
             }
             atomicAdd(&z[dof], y * __ldg(wsc + dof));
@@ -218,6 +250,23 @@ __global__ void __launch_bounds__(256) k_to_stream(const double* __restrict__ sr
             if (mx > 0.0 && mx <= 1.79e308) frexp(mx, &ex);
             if (threadIdx.x == 0) bexp[i] = ex;
         }
+        if constexpr (MODE == SM_BF16) {
+            // column pairs: (B[a][2c], B[a][2c+1]) adjacent, a zero column
+            // after the last one when p is odd
+            const int pc = (p + 1) >> 1;
+            __nv_bfloat16* o2 = reinterpret_cast<__nv_bfloat16*>(dst) + (int64_t)i * 2 * p * pc;
+            for (int t = threadIdx.x; t < 2 * p * pc; t += blockDim.x) {
+                const int c = t / (2 * p), q = t - c * 2 * p, a = q >> 1, b = 2 * c + (q & 1);
+                double v = 0.0;
+                if (b < p) {
+                    v = B[a * p + b];
+                    if (sym) v = 0.5 * (v + B[b * p + a]);
+                }
+                o2[t] = __float2bfloat16_rn(__double2float_rn(v));
+            }
+            __syncthreads();
+            continue;
+        }
         for (int t = threadIdx.x; t < pp; t += blockDim.x) {
             const int b = t / p, a = t - b * p;           // out[t] = B[a][b]
             double v = B[a * p + b];
@@ -251,7 +300,8 @@ int stream_convert(psr_ctx* ctx, Group& G, const double* db64, cudaStream_t s, i
                    const int32_t* entry_of) {
     const int mode = stream_mode(ctx);
     const int nmat = entry_of ? G.count : G.m;
-    const int64_t ne = (int64_t)nmat * G.p * G.p;
+    // BF16 keeps the columns in pairs (p (p + 1) / 2 pairs for odd p)
+    const int64_t ne = (int64_t)nmat * G.p * (mode == SM_BF16 ? 2 * ((G.p + 1) / 2) : G.p);
     const size_t es = stream_elem_bytes(mode);
     void* dst = nullptr;
     if (psr::dev_alloc(&dst, es * (size_t)std::max<int64_t>(ne, 1)) != cudaSuccess) {
