@@ -101,6 +101,8 @@ def parse():
     ap.add_argument("--prec", default=None)
     ap.add_argument("--prec-check", type=float, default=0.5,
                     help="psr_opts.prec_check of the main line (0 keeps every entry in the storage precision)")
+    ap.add_argument("--match", default="first", choices=["first", "closest"],
+                    help="Alg. 1 assignment rule of the main line (section 3.1: first or closest match)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the precision variants and the sub-line")
@@ -477,7 +479,7 @@ def run_gpu(args, cfg, ws, rank, local):
     x = torch.zeros_like(b)
     stream = torch.cuda.current_stream()
     opts = L.make_opts(tol=tol, store_prec=prec, weighting=cfg["weighting"], krylov=cfg["krylov"], restart=30,
-                       rtol=1e-8, maxit=maxit, fp64_arith="pairs", prec_check=args.prec_check)
+                       rtol=1e-8, maxit=maxit, fp64_arith="pairs", prec_check=args.prec_check, match=args.match)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = peaks.get("hbm_gbs", 6800.0)
@@ -563,7 +565,7 @@ def run_gpu(args, cfg, ws, rank, local):
                    "patch_sizes": sorted(set(pr.patch_sizes.tolist())), "tol": tol, "store_prec": prec,
                    "fp64_arith": "pairs (FP64 inverses as (hi, lo) FP32 pairs, compensated products, ~47 bits)",
                    "krylov": cfg["krylov"] + ("(30)" if cfg["krylov"] == "fgmres" else ""),
-                   "weighting": cfg["weighting"], "maxit": maxit, "rhs": "uniform(-1,1) seed 0",
+                   "weighting": cfg["weighting"], "maxit": maxit, "match": args.match, "rhs": "uniform(-1,1) seed 0",
                    "l2": ("inputs larger than L2 (the stored inverses alone)" if big
                           else "flushed (256 MB write) before every timed step"),
                    "allocations": "library caching allocator, filled by the warm-up steps",

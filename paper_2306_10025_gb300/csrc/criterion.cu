@@ -1515,12 +1515,12 @@ __global__ void k_verify_hints(RoundDev* st, int32_t* __restrict__ phi, int coun
     }
 }
 
-// sigma_max(E), E = (A_c - A_i) B_c^-1 computed in FP64 (lane r forms row r),
-// from the Jacobi eigenvalues of G = E^T E: the "small SVD" of the section 3
-// remark.  A_c, B_c: global (row stride p); ws.E: p x (p+1) shared.
+// sigma_max(E) of E = D B for D = A_c - A_i already in the warp's shared
+// scratch sD (row stride p) and B in global memory (row stride p): E formed
+// in FP64, G = E^T E, the largest eigenvalue of G by cyclic Jacobi (the
+// "small SVD" of the section 3 remark).
 template <int PM>
-__device__ double exact_sigma_warp(const double* __restrict__ Ai, const double* __restrict__ Ac,
-                                   const double* __restrict__ B, int p, WarpScratch ws) {
+__device__ double exact_sigma_d_warp(const double* sD, const double* __restrict__ B, int p, WarpScratch ws) {
     const int lane = threadIdx.x & 31;
     const bool act = lane < p;
     const int ld = p + 1;
@@ -1529,13 +1529,12 @@ __device__ double exact_sigma_warp(const double* __restrict__ Ai, const double* 
     for (int j = 0; j < PM; ++j) e[j] = 0.0;
     if (act) {
         for (int k = 0; k < p; ++k) {
-            const double dk = Ac[lane * p + k] - Ai[lane * p + k];
+            const double dk = sD[lane * p + k];
 #pragma unroll
             for (int j = 0; j < PM; ++j)
                 if (j < p) e[j] = fma(dk, B[k * p + j], e[j]);
         }
     }
-    // column j of E in lane j: read back through shared memory
     __syncwarp();
     if (act) {
 #pragma unroll
@@ -1558,20 +1557,58 @@ __device__ double exact_sigma_warp(const double* __restrict__ Ai, const double* 
     return sqrt(fmax(lam, 0.0));
 }
 
+// D = A_c - A_i into the warp's scratch with coalesced loads; true when the
+// two patches are bitwise equal.
+__device__ __forceinline__ bool stage_d_warp(const double* __restrict__ Ac, const double* __restrict__ Ai, int p,
+                                             double* sD) {
+    const int lane = threadIdx.x & 31;
+    bool same = true;
+    __syncwarp();
+    for (int e = lane; e < p * p; e += 32) {
+        const double a = Ac[e], b = Ai[e];
+        same &= __double_as_longlong(a) == __double_as_longlong(b);
+        sD[e] = a - b;
+    }
+    const bool all_same = __all_sync(0xffffffffu, same);
+    __syncwarp();
+    return all_same;
+}
+
+// Screen thresholds (see multi_thresholds) of every entry, for the
+// closest-match pass.
+__global__ void k_entry_thresholds(const int32_t* __restrict__ rep_l, int m, SketchDB sk, int p, double tol,
+                                   float* __restrict__ thr, float* __restrict__ beta) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int c = rep_l[j];
+    double den[SK];
+#pragma unroll
+    for (int k = 0; k < SK; ++k) den[k] = sk.den[(int64_t)c * SK + k];
+    multi_thresholds(sk.fa[c], sk.rho[c], den, p, tol, thr + (int64_t)j * SK, beta + j);
+}
+
 // Closest-match variant of Alg. 1 (section 3.1): the entries are those of the
 // first-match rounds (an entry is created exactly when no entry passes, which
 // does not depend on which passing entry is taken), and patch i joins the
 // entry with the least d among the entries created before it that pass
 // (d < tol), the lowest index on ties.  Entries before its first match
 // failed already, so a warp per patch compares the first match j0 with the
-// later entries whose representative precedes i (certified decision first,
-// sigma_max by the Jacobi eigenvalues for those that pass).
+// later entries whose representative precedes i, 32 at a time: the lanes
+// screen them with the certified sketch bound (d >= tol), the warp decides
+// the survivors in entry order with the certified cascade against the best
+// distance so far (d < bs, on D staged in shared memory) and takes sigma_max
+// by the Jacobi eigenvalues only for those that beat it.  A zero distance
+// ends the search (nothing can be smaller; ties keep the lower entry), and
+// the evaluations counted are those made up to that point.
 template <int PM>
 __global__ void __launch_bounds__(EVAL_THREADS) k_closest_pass(int count, int p, const double* __restrict__ Ag,
                                                                const double* __restrict__ Ball,
+                                                               const float* __restrict__ B32,
                                                                const double* __restrict__ fro_all,
                                                                const double* __restrict__ w_all,
                                                                const int32_t* __restrict__ rep_l, int m, double tol,
+                                                               SketchDB sk, const float* __restrict__ ethr,
+                                                               const float* __restrict__ ebeta,
                                                                int32_t* __restrict__ phi,
                                                                unsigned long long* __restrict__ evals) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1579,29 +1616,103 @@ __global__ void __launch_bounds__(EVAL_THREADS) k_closest_pass(int count, int p,
     const int wid = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
     const int ld = p + 1;
-    double* wbase = reinterpret_cast<double*>(smem) + (size_t)wid * (p * ld + 64);
+    double* wbase = reinterpret_cast<double*>(smem) + (size_t)wid * ((size_t)p * ld + 64 + 2 * (size_t)p * p);
     WarpScratch ws{wbase, wbase + p * ld, wbase + p * ld + 32};
+    double* sD = wbase + (size_t)p * ld + 64;      // D of the candidate being decided
+    double* sD0 = sD + (size_t)p * p;              // D of the first match
     const int64_t pp = (int64_t)p * p;
     unsigned long long ev = 0;
     for (int i = blockIdx.x * wpb + wid; i < count; i += gridDim.x * wpb) {
         const int j0 = phi[i];
         if (rep_l[j0] == i) continue;                   // a representative keeps its own entry
         const double* Ai = Ag + (int64_t)i * pp;
+        const int r0 = rep_l[j0];
         int best = j0;
-        double bs = exact_sigma_warp<PM>(Ai, Ag + (int64_t)rep_l[j0] * pp, Ball + (int64_t)rep_l[j0] * pp, p, ws);
-        for (int j = j0 + 1; j < m && bs > 0.0; ++j) {
-            const int rj = rep_l[j];
-            if (rj > i) break;                          // entries are created in increasing patch order
-            const double* Ac = Ag + (int64_t)rj * pp;
-            const double* Bc = Ball + (int64_t)rj * pp;
-            double dv;
-            ++ev;
-            const int dec = decide_pair<PM>(Ai, Ac, Bc, p, p, fro_all[rj], tol, ws, &dv, true,
-                                            w_all + (int64_t)rj * PROBE_STRIDE, nullptr);
-            __syncwarp();
-            if (dec != 1) continue;
-            const double sj = (dv == 0.0) ? 0.0 : exact_sigma_warp<PM>(Ai, Ac, Bc, p, ws);
-            if (sj < bs) { bs = sj; best = j; }
+        // bs: the best distance so far; -1 while the first match's distance
+        // (positive unless its D vanishes) has not been needed yet
+        double bs = stage_d_warp(Ag + (int64_t)r0 * pp, Ai, p, sD0) ? 0.0 : -1.0;
+        if (bs < 0.0) {
+            bool zero = true;
+            for (int e = lane; e < p * p; e += 32) zero &= sD0[e] == 0.0;
+            if (__all_sync(0xffffffffu, zero)) bs = 0.0;
+        }
+        auto first_sigma = [&]() {
+            if (bs < 0.0) bs = exact_sigma_d_warp<PM>(sD0, Ball + (int64_t)r0 * pp, p, ws);
+        };
+        // the candidate entries: j0 < j < jend, jend the first entry whose
+        // representative follows i (entries are created in increasing patch order)
+        int lo = j0 + 1, hi = m;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (rep_l[mid] > i) hi = mid; else lo = mid + 1;
+        }
+        const int jend = lo;
+        float v[SK * PM];
+        sketch_load<PM>(sk.Y32 + (int64_t)i * SK * p, p, v);
+        const float fi32 = __double2float_ru(sk.fa[i]);
+        for (int jb = j0 + 1; jb < jend && bs != 0.0; jb += 32) {
+            const int j = jb + lane;
+            bool rej = true;
+            if (j < jend) {
+                const int rj = rep_l[j];
+                const float* yc = sk.Y32 + (int64_t)rj * SK * p;
+                rej = false;
+#pragma unroll
+                for (int k = 0; k < SK; ++k) {
+                    float d2 = 0.f;
+#pragma unroll
+                    for (int r = 0; r < PM; ++r) {
+                        const float d = (r < p) ? yc[k * p + r] - v[k * PM + r] : 0.f;
+                        d2 = fmaf(d, d, d2);
+                    }
+                    if (sqrtf(d2) >= __fmaf_ru(ebeta[j], fi32, ethr[(int64_t)j * SK + k])) rej = true;
+                }
+            }
+            unsigned surv = __ballot_sync(0xffffffffu, !rej);
+            int last = min(jend, jb + 32) - 1;          // the last entry evaluated in this chunk
+            while (surv) {
+                const int l = __ffs(surv) - 1;
+                surv &= surv - 1u;
+                const int jj = jb + l;
+                const int rj = rep_l[jj];
+                const double* Bc = Ball + (int64_t)rj * pp;
+                // only an entry closer than the best so far matters: the
+                // certified decision runs against that distance (tol until the
+                // first match's distance is needed), and sigma_max is computed
+                // for the few that beat it
+                double sj = 0.0;
+                bool better = true;                     // bitwise equal patches: distance 0
+                if (!stage_d_warp(Ag + (int64_t)rj * pp, Ai, p, sD)) {
+                    auto decide = [&](double t) {
+                        double dv;
+                        int dec = decide_pair<PM, true>(nullptr, sD, Bc, p, p, fro_all[rj], t, ws, &dv, false,
+                                                        w_all + (int64_t)rj * PROBE_STRIDE, B32 + (int64_t)rj * pp);
+                        if (dec < 0)
+                            dec = decide_pair<PM, true>(nullptr, sD, Bc, p, p, fro_all[rj], t, ws, &dv, true,
+                                                        w_all + (int64_t)rj * PROBE_STRIDE, nullptr);
+                        return dec == 1;
+                    };
+                    const bool known = bs >= 0.0;
+                    better = decide(known ? bs : tol);
+                    if (better && !known) {             // passes: now the first match's distance is needed
+                        first_sigma();
+                        better = decide(bs);
+                    }
+                    if (better) {
+                        sj = exact_sigma_d_warp<PM>(sD, Bc, p, ws);
+                        better = sj < bs;
+                    }
+                }
+                if (better) {
+                    bs = sj;
+                    best = jj;
+                }
+                if (bs == 0.0) {                        // nothing later can be smaller
+                    last = jj;
+                    break;
+                }
+            }
+            ev += (unsigned long long)(last - jb + 1);
         }
         if (lane == 0) phi[i] = best;
         __syncwarp();
@@ -1965,23 +2076,41 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
             unsigned long long* cev = nullptr;
             PSR_CUDA(ctx, psr::dev_alloc(&cev, sizeof(unsigned long long)));
             PSR_CUDA(ctx, cudaMemsetAsync(cev, 0, sizeof(unsigned long long), s));
-            const size_t smem_c = (size_t)wpb * ((size_t)p * ld + 64) * 8;
+            const size_t smem_c = (size_t)wpb * ((size_t)p * ld + 64 + 2 * (size_t)p * p) * 8;
             const void* kf = (p <= 8) ? (const void*)k_closest_pass<8>
                            : (p <= 16) ? (const void*)k_closest_pass<16> : (const void*)k_closest_pass<32>;
             if ((rc = set_smem(kf, smem_c)) != PSR_OK) break;
+            float *cb32 = nullptr, *ethr = nullptr, *ebeta = nullptr;
+            PSR_CUDA(ctx, psr::dev_alloc(&cb32, sizeof(float) * (size_t)count * p * p));
+            PSR_CUDA(ctx, psr::dev_alloc(&ethr, sizeof(float) * (size_t)G.m * SK));
+            PSR_CUDA(ctx, psr::dev_alloc(&ebeta, sizeof(float) * (size_t)G.m));
+            {
+                const int64_t tot = (int64_t)count * p * p;
+                count_launch();
+                k_round_f32<<<(int)std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 152 * 16)), 256, 0, s>>>(
+                    Ball, tot, cb32);
+                count_launch();
+                k_entry_thresholds<<<(G.m + 127) / 128, 128, 0, s>>>(rep_l, G.m, sk, p, tol, ethr, ebeta);
+            }
             const int cb = std::max(1, std::min((count + wpb - 1) / wpb, 152 * 8));
             count_launch();
             if (p <= 8)
-                k_closest_pass<8><<<cb, EVAL_THREADS, smem_c, s>>>(count, p, Ag, Ball, fro_all, w_all, rep_l, G.m, tol, phi_l, cev);
+                k_closest_pass<8><<<cb, EVAL_THREADS, smem_c, s>>>(count, p, Ag, Ball, cb32, fro_all, w_all, rep_l, G.m,
+                                                                   tol, sk, ethr, ebeta, phi_l, cev);
             else if (p <= 16)
-                k_closest_pass<16><<<cb, EVAL_THREADS, smem_c, s>>>(count, p, Ag, Ball, fro_all, w_all, rep_l, G.m, tol, phi_l, cev);
+                k_closest_pass<16><<<cb, EVAL_THREADS, smem_c, s>>>(count, p, Ag, Ball, cb32, fro_all, w_all, rep_l,
+                                                                    G.m, tol, sk, ethr, ebeta, phi_l, cev);
             else
-                k_closest_pass<32><<<cb, EVAL_THREADS, smem_c, s>>>(count, p, Ag, Ball, fro_all, w_all, rep_l, G.m, tol, phi_l, cev);
+                k_closest_pass<32><<<cb, EVAL_THREADS, smem_c, s>>>(count, p, Ag, Ball, cb32, fro_all, w_all, rep_l,
+                                                                    G.m, tol, sk, ethr, ebeta, phi_l, cev);
             PSR_CHECK_LAUNCH(ctx, "closest-match pass");
             unsigned long long h_cev = 0;
             PSR_CUDA(ctx, cudaMemcpyAsync(&h_cev, cev, sizeof(h_cev), cudaMemcpyDeviceToHost, s));
             PSR_CUDA(ctx, cudaStreamSynchronize(s));
             psr::dev_free(cev);
+            psr::dev_free(cb32);
+            psr::dev_free(ethr);
+            psr::dev_free(ebeta);
             total_evals += (int64_t)h_cev;
             total_decided += (int64_t)h_cev;
         }
