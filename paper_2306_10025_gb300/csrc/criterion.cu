@@ -1516,9 +1516,16 @@ __global__ void k_verify_hints(RoundDev* st, int32_t* __restrict__ phi, int coun
 }
 
 // sigma_max(E) of E = D B for D = A_c - A_i already in the warp's shared
-// scratch sD (row stride p) and B in global memory (row stride p): E formed
-// in FP64, G = E^T E, the largest eigenvalue of G by cyclic Jacobi (the
-// "small SVD" of the section 3 remark).
+// scratch sD (row stride p) and B in global memory (row stride p), E formed in
+// FP64.  lambda_max(G), G = E^T E, by power iteration from E's largest row
+// (the Rayleigh quotients ||E v||^2 rise to it), then certified: a Cholesky
+// factorisation of X I - G - c I with X = lambda (1 + 2^-40) and c covering
+// its backward error proves lambda_max(G) < X, so the value returned is within
+// 2^-41 (relative) of sigma_max.  When the certificate fails (slow
+// convergence) the largest Jacobi eigenvalue of G is taken instead (the
+// "small SVD" of the section 3 remark).  Distances within 2^-40 of each
+// other count as ties only at that level; the cyclic Jacobi solve costs
+// about fifteen times the power iteration and its certificate.
 template <int PM>
 __device__ double exact_sigma_d_warp(const double* sD, const double* __restrict__ B, int p, WarpScratch ws) {
     const int lane = threadIdx.x & 31;
@@ -1545,16 +1552,71 @@ __device__ double exact_sigma_d_warp(const double* sD, const double* __restrict_
     double ecol[PM];
 #pragma unroll
     for (int r = 0; r < PM; ++r) ecol[r] = (act && r < p) ? ws.E[r * ld + lane] : 0.0;
-    __syncwarp();
-    for (int k = 0; k < p; ++k) {
-        double g = 0.0;
-        for (int r = 0; r < p; ++r) g = fma(ecol[r], __shfl_sync(0xffffffffu, ecol[r], k), g);
-        if (act) ws.E[lane * ld + k] = g;
+    // start vector: the largest row of E (lowest row on ties)
+    double rn = 0.0;
+#pragma unroll
+    for (int j = 0; j < PM; ++j) rn = fma(e[j], e[j], rn);
+    double best = act ? rn : -1.0;
+    int br = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, br, o);
+        if (ob > best || (ob == best && oi < br)) { best = ob; br = oi; }
     }
+    if (!(best > 0.0)) return 0.0;                     // E = 0
+    double v = act ? ws.E[br * ld + lane] : 0.0;
+    v /= sqrt(best);
+    double lam = 0.0;
+    int quiet = 0;
+    for (int it = 0; it < 300 && quiet < 3; ++it) {
+        __syncwarp();
+        ws.v[lane] = v;
+        __syncwarp();
+        double wr = 0.0;
+        if (act) {
+#pragma unroll
+            for (int j = 0; j < PM; ++j)
+                if (j < p) wr = fma(e[j], ws.v[j], wr);
+        }
+        const double l2 = warp_sum(wr * wr);           // v^T G v, ||v|| = 1
+        quiet = (l2 - lam <= 0x1p-50 * l2) ? quiet + 1 : 0;
+        lam = fmax(lam, l2);
+        ws.w[lane] = wr;
+        __syncwarp();
+        double uj = 0.0;
+        if (act) {
+#pragma unroll
+            for (int r = 0; r < PM; ++r)
+                if (r < p) uj = fma(ecol[r], ws.w[r], uj);
+        }
+        const double nu = sqrt(warp_sum(uj * uj));
+        if (!(nu > 0.0)) break;
+        v = uj / nu;
+    }
+    // G (or X I - G) into the scratch: G[lane][k] = sum_r E[r][lane] E[r][k]
+    auto build_g = [&](double X, bool neg) {
+        __syncwarp();
+        for (int k = 0; k < p; ++k) {
+            double g = 0.0;
+            for (int r = 0; r < p; ++r) g = fma(ecol[r], __shfl_sync(0xffffffffu, ecol[r], k), g);
+            if (act) ws.E[lane * ld + k] = neg ? ((k == lane ? X : 0.0) - g) : g;
+        }
+        __syncwarp();
+    };
+    const double X = lam * (1.0 + 0x1p-40);
+    build_g(X, true);
+    const double tr = warp_sum(act ? ws.E[lane * ld + lane] : 0.0);
+    if (tr > 0.0) {
+        const double c = 2.0 * gamma_u(p + 1) * tr;
+        if (act) ws.E[lane * ld + lane] -= c;
+        __syncwarp();
+        if (cholesky_warp(ws.E, p, ld) == p) return sqrt(lam);
+    }
+    build_g(0.0, false);
+    const double lj = jacobi_lambda_max_warp(ws.E, p, ld);
     __syncwarp();
-    const double lam = jacobi_lambda_max_warp(ws.E, p, ld);
-    __syncwarp();
-    return sqrt(fmax(lam, 0.0));
+    return sqrt(fmax(lj, 0.0));
 }
 
 // D = A_c - A_i into the warp's scratch with coalesced loads; true when the
