@@ -90,6 +90,16 @@ extern "C" {
 #define PSR_MATCH_CLOSEST 1        /* section 3.1 variant: of the entries existing when the
                                       patch is reached, the one with the least d (< tol)       */
 
+#define PSR_SEARCH_CREATION    0   /* Alg. 1 tests the entries in creation order           */
+#define PSR_SEARCH_NORM_WINDOW 1   /* section 3.1 sorted search: only entries with
+                                      ||A_i||/(1+tol) < ||B_j|| < ||A_i||/(1-tol) (the 2-norms
+                                      of the patch and of the entry's patch, widened by 1e-12)
+                                      are tested, in creation order; the others cannot pass
+                                      (d >= | ||B_j|| - ||A_i|| | / ||B_j||), so phi and the
+                                      entries are those of the creation-order search and only
+                                      the evaluation count drops.  Spectral criterion, first
+                                      match, no seed database or hints; any patch size.    */
+
 typedef struct psr_ctx psr_ctx;    /* opaque, library-owned */
 
 /* Assembled matrix A (section 2: A x = b), CSR, device pointers. */
@@ -136,12 +146,15 @@ typedef struct {
                              ||B~ A_c - I||_F > prec_check, or (CG) is not positive
                              definite, is kept and applied in FP64 instead;
                              0 disables the check                                  */
+    int32_t search;       /* PSR_SEARCH_* of Alg. 1 (psr_setup with the spectral
+                             criterion; the learned and seeded setups take only
+                             PSR_SEARCH_CREATION)                                  */
 } psr_opts;
 
 /* Fill `o` with defaults: tol 0, FP64, SYM, CG, restart 30, rtol 1e-8,
  * maxit 10000, graphs on, AUTO sweep, autotune on, symmetrize on, no MLP,
  * AUTO orthogonalisation, spectral criterion, FP64 pairs, first match,
- * seed 0, precision check 0.5. */
+ * seed 0, precision check 0.5, creation-order search. */
 void psr_default_opts(psr_opts* o);
 
 /* A rectangular CSR matrix (the interpolation P0 of Eq. 2), device pointers. */

@@ -29,6 +29,7 @@ ORTHO = {"auto": 0, "fp64": 1, "split": 2}
 CRITERION = {"spectral": 0, "l1": 1, "varmin": 2}
 FP64_ARITH = {"pairs": 0, "native": 1}
 MATCH = {"first": 0, "closest": 1}
+SEARCH = {"creation": 0, "norm_window": 1}
 
 EXPORTS = ["psr_default_opts", "psr_setup", "psr_apply", "psr_solve", "psr_get_history",
            "psr_get_assignment", "psr_get_stats", "psr_last_error", "psr_destroy", "psr_extract",
@@ -65,7 +66,8 @@ class psr_opts(C.Structure):
                 ("maxit", C.c_int32), ("use_graph", C.c_int32), ("sweep_kernel", C.c_int32),
                 ("autotune", C.c_int32), ("symmetrize", C.c_int32), ("use_mlp", C.c_int32),
                 ("ortho", C.c_int32), ("criterion", C.c_int32), ("fp64_arith", C.c_int32),
-                ("match", C.c_int32), ("seed", C.c_uint64), ("prec_check", C.c_double)]
+                ("match", C.c_int32), ("seed", C.c_uint64), ("prec_check", C.c_double),
+                ("search", C.c_int32)]
 
 
 class psr_train_opts(C.Structure):
@@ -198,7 +200,7 @@ def _need(t, dtype, name):
 def make_opts(tol=0.0, store_prec="fp64", weighting="sym", krylov="cg", restart=30, rtol=1e-8,
               maxit=10000, use_graph=True, sweep_kernel="auto", autotune=True, symmetrize=True,
               use_mlp=False, ortho="auto", criterion="spectral", fp64_arith="pairs", match="first",
-              seed=0, prec_check=0.5) -> psr_opts:
+              seed=0, prec_check=0.5, search="creation") -> psr_opts:
     o = psr_opts()
     load().psr_default_opts(C.byref(o))
     o.tol = tol
@@ -219,6 +221,7 @@ def make_opts(tol=0.0, store_prec="fp64", weighting="sym", krylov="cg", restart=
     o.match = MATCH[match]
     o.seed = int(seed)
     o.prec_check = float(prec_check)
+    o.search = SEARCH[search]
     return o
 
 

@@ -134,7 +134,8 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
         op.sweep_kernel < PSR_SWEEP_AUTO || op.sweep_kernel > PSR_SWEEP_TENSOR || op.ortho < PSR_ORTHO_AUTO ||
         op.ortho > PSR_ORTHO_SPLIT || op.criterion < PSR_CRITERION_SPECTRAL || op.criterion > PSR_CRITERION_VARMIN ||
         op.fp64_arith < PSR_FP64_PAIRS || op.fp64_arith > PSR_FP64_NATIVE || op.match < PSR_MATCH_FIRST ||
-        op.match > PSR_MATCH_CLOSEST || !(op.prec_check >= 0.0)) {
+        op.match > PSR_MATCH_CLOSEST || !(op.prec_check >= 0.0) || op.search < PSR_SEARCH_CREATION ||
+        op.search > PSR_SEARCH_NORM_WINDOW) {
         set_error(ctx, "invalid option value");
         destroy_ctx(ctx);
         return PSR_ERR_INVALID_ARG;
@@ -302,6 +303,10 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
             ctx->stats.criterion_evals = 0;
         } else if (op.criterion == PSR_CRITERION_L1) {
             if (m0 > 0 || hints) { set_error(ctx, "the l1 criterion takes no seed database or hints"); FAIL(PSR_ERR_INVALID_ARG); }
+            if (op.search != PSR_SEARCH_CREATION) {
+                set_error(ctx, "the norm-window search is for the spectral criterion");
+                FAIL(PSR_ERR_INVALID_ARG);
+            }
             rc = run_alg1_l1(ctx, s);
             if (rc != PSR_OK) goto fail;
         } else {
@@ -410,6 +415,7 @@ void psr_default_opts(psr_opts* o) {
     o->match = PSR_MATCH_FIRST;
     o->seed = 0;
     o->prec_check = 0.5;
+    o->search = PSR_SEARCH_CREATION;
 }
 
 int psr_setup(const psr_csr* A, const psr_patches* patches, const psr_opts* opts, void* stream, psr_ctx** out) {

@@ -559,7 +559,13 @@ struct SketchDB {
     const double* fa;              // [count] ||A_i||_F
     const double* rho;             // [count] bound of ||B_i^ A_i - I||_2
     const float* Y32;              // [count][SK][p] y_i rounded to FP32 (the screen's operand)
+    const double* nlo;             // [count] brackets of ||A_i||_2 for the norm-window
+    const double* nhi;             //   search; null when the search is in creation order
 };
+
+__device__ __forceinline__ NormWin norm_window(const SketchDB& sk, int i, double tol) {
+    return norm_window(sk.nlo[i], sk.nhi[i], tol);
+}
 
 
 // Directions of a size group: x_0 = the dominant right singular vector of
@@ -749,9 +755,10 @@ __global__ void __launch_bounds__(EVAL_THREADS) k_round_screen(RoundDev* st, con
         sketch_load<PM>(sk.Y32 + (int64_t)cc * SK * p, p, v);
         const double fi = sk.fa[cc];
         const bool open = cand < count && phi[cc] == -1;
-        const bool rej = open && sketch_bound_rejects<PM>(v, fi, sy, sden, fc, rhoc, p, tol);
+        const bool wout = open && sk.nlo && outside_window(norm_window(sk, cc, tol), sk.nlo[i0], sk.nhi[i0]);
+        const bool rej = open && (wout || sketch_bound_rejects<PM>(v, fi, sy, sden, fc, rhoc, p, tol));
         if (open && rej) my_min = min(my_min, cand);
-        const unsigned opened = __ballot_sync(0xffffffffu, open);
+        const unsigned opened = __ballot_sync(0xffffffffu, open && !wout);
         const unsigned surv = __ballot_sync(0xffffffffu, open && !rej);
         my_evals += __popc(opened);
         my_screened += __popc(opened & ~surv);
@@ -908,6 +915,7 @@ struct MultiWS {
     unsigned long long* accm;      // [count] entries (bit l) that accepted patch i
     unsigned long long* exm;       // [count] pairs of patch i decided by the exact stage
     unsigned long long* rejm;      // [count] pairs of patch i the screen rejected
+    unsigned long long* wom;       // [count] pairs of patch i outside the norm window
     unsigned long long* accA;      // [2][KC] phase A accepts of candidate k, by round parity
     unsigned long long* exA;       // [2][KC] phase A exact-stage pairs of candidate k
     int32_t* npB;                  // [2] phase B pair counts, by round parity
@@ -1029,6 +1037,8 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_rounds_multi(
     __shared__ int scand[KC];
     __shared__ int sridx[KC];                      // slots of the entries of R, in order
     __shared__ unsigned long long srejA[KC], sacc[KC], sexA[KC];
+    __shared__ unsigned long long swinA[KC];       // phase A pairs outside the norm window
+    __shared__ double snlo[KC], snhi[KC];          // candidates' ||A||_2 brackets (norm window)
     __shared__ unsigned short sapair[KC * (KC - 1) / 2];
     __shared__ int s_aoff[KC];
     __shared__ int s_wsum[EVAL_THREADS / 32];
@@ -1047,6 +1057,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_rounds_multi(
     unsigned long long my_evals = 0, my_exact = 0, my_screened = 0, my_decided = 0;
     int m = st->m;
     int nrounds = 0;
+    const bool win = sk.nlo != nullptr;            // norm-window search (no seed database)
     // the open bitmap from phi (a seed database may have assigned some)
     for (int wd = gw; wd < nwords; wd += gwarps) {
         const int i = wd * 32 + lane;
@@ -1061,26 +1072,32 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_rounds_multi(
     // entries of R (slots sridx[0..nR)), the surviving pairs decided by the
     // grid's warps; the warp deciding a patch's last pair assigns it to its
     // first accepting entry, numbered ebase + (its rank in R).  Two grid
-    // barriers; false when one gave up.
-    auto phase_b = [&](const EntrySrc& es, int ebase, unsigned long long R, int nR, int lo, int par) -> bool {
+    // barriers; false when one gave up.  wnd: the norm window applies (the
+    // staged entries are candidates, snlo / snhi hold their brackets).
+    auto phase_b = [&](const EntrySrc& es, int ebase, unsigned long long R, int nR, int lo, int par,
+                       bool wnd) -> bool {
         for (int base = lo + blockIdx.x * blockDim.x; base < count; base += gthreads) {
             const int i = base + threadIdx.x;
             const bool open = i < count && ((__ldcg(mw.obits + (i >> 5)) >> (i & 31)) & 1u);
-            unsigned long long rej = 0ull;
+            unsigned long long rej = 0ull, wo = 0ull;
             if (open) {
                 float v[SK * PM];
                 sketch_load<PM>(sk.Y32 + (int64_t)i * SK * p, p, v);
                 const float fi32 = __double2float_ru(sk.fa[i]);
+                NormWin w{0.0, 0.0};
+                if (wnd) w = norm_window(sk, i, tol);
                 for (int t = 0; t < nR; ++t) {
                     const int l = sridx[t];
-                    if (multi_rejects<PM>(v, fi32, sy + l * SYS, sthr + l * SK, sbeta[l], p)) rej |= 1ull << l;
+                    if (wnd && outside_window(w, snlo[l], snhi[l])) wo |= 1ull << l;
+                    else if (multi_rejects<PM>(v, fi32, sy + l * SYS, sthr + l * SK, sbeta[l], p)) rej |= 1ull << l;
                 }
+                rej |= wo;
             }
             const unsigned long long surv = open ? (R & ~rej) : 0ull;
             const int ns = __popcll(surv);
             if (open && ns == 0) {                 // rejected by every entry: stays open
-                my_evals += nR;
-                my_screened += nR;
+                my_evals += nR - __popcll(wo);
+                my_screened += nR - __popcll(wo);
             }
             int incl = ns;
 #pragma unroll
@@ -1095,6 +1112,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_rounds_multi(
             if (ns) {
                 mw.rem[i] = ns;
                 mw.rejm[i] = rej & R;
+                if (wnd) mw.wom[i] = wo;
                 mw.accm[i] = 0ull;
                 mw.exm[i] = 0ull;
                 int pos = wb + incl - ns;
@@ -1131,6 +1149,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_rounds_multi(
                         phi[i] = ebase + __popcll(R & below_bit(ls));
                         atomicAnd(mw.obits + (i >> 5), ~(1u << (i & 31)));
                     }
+                    if (wnd) path &= ~__ldcg(mw.wom + i);   // skipped entries are not tests
                     my_evals += __popcll(path);
                     my_screened += __popcll(rj & path);
                     my_exact += __popcll(exb & path);
@@ -1166,7 +1185,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_rounds_multi(
         }
         __syncthreads();
         const unsigned long long R = (K == KC) ? ~0ull : ((1ull << K) - 1ull);
-        ok = phase_b(seed, j0, R, K, 0, par);
+        ok = phase_b(seed, j0, R, K, 0, par, false);
     }
     // candidates per round: 64, or fewer while rounds make few entries (a
     // round's pairs among its candidates grow as K^2; on the graded Stokes
@@ -1223,6 +1242,11 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_rounds_multi(
             multi_thresholds(sk.fa[c], sk.rho[c], den, p, tol, sthr + l * SK, sbeta + l);
             sfi[l] = __double2float_ru(sk.fa[c]);
             srejA[l] = 0ull;
+            swinA[l] = 0ull;
+            if (win) {
+                snlo[l] = sk.nlo[c];
+                snhi[l] = sk.nhi[c];
+            }
         }
         if (threadIdx.x == 0) s_na = 0;
         __syncthreads();
@@ -1238,11 +1262,16 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_rounds_multi(
                 for (int kk = 0; kk < SK; ++kk)
 #pragma unroll
                     for (int r = 0; r < PM; ++r) v[kk * PM + r] = sy[k * SYS + kk * 32 + r];
-                unsigned long long rb = 0ull;
+                unsigned long long rb = 0ull, wb = 0ull;
                 const int l1 = min(k, l0 + 32);
-                for (int l = l0; l < l1; ++l)
-                    if (multi_rejects<PM>(v, sfi[k], sy + l * SYS, sthr + l * SK, sbeta[l], p)) rb |= 1ull << l;
-                if (rb) atomicOr(&srejA[k], rb);
+                NormWin w{0.0, 0.0};
+                if (win) w = norm_window(sk, scand[k], tol);
+                for (int l = l0; l < l1; ++l) {
+                    if (win && outside_window(w, snlo[l], snhi[l])) wb |= 1ull << l;
+                    else if (multi_rejects<PM>(v, sfi[k], sy + l * SYS, sthr + l * SK, sbeta[l], p)) rb |= 1ull << l;
+                }
+                if (rb | wb) atomicOr(&srejA[k], rb | wb);
+                if (wb) atomicOr(&swinA[k], wb);
             }
         }
         __syncthreads();
@@ -1323,6 +1352,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_rounds_multi(
                     e = m + __popcll(R & below_bit(ls));
                 }
                 phi[c] = e;
+                path &= ~swinA[k];                 // entries outside the norm window are not tests
                 my_evals += __popcll(path);
                 my_screened += __popcll(srejA[k] & path);
                 my_exact += __popcll(sexA[k] & path);
@@ -1337,7 +1367,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_rounds_multi(
             }
         }
         // ---- phase B: every other open patch against the entries of R
-        if (!phase_b(own, m, R, nR, scand[K - 1] + 1, par)) break;
+        if (!phase_b(own, m, R, nR, scand[K - 1] + 1, par, win)) break;
         m += nR;
         klim = min(KC, max(16, 2 * nR + 8));       // the same in every block
     }
@@ -1515,31 +1545,29 @@ __global__ void k_verify_hints(RoundDev* st, int32_t* __restrict__ phi, int coun
     }
 }
 
-// sigma_max(E) of E = D B for D = A_c - A_i already in the warp's shared
-// scratch sD (row stride p) and B in global memory (row stride p), E formed in
-// FP64.  lambda_max(G), G = E^T E, by power iteration from E's largest row
-// (the Rayleigh quotients ||E v||^2 rise to it), then certified: a Cholesky
-// factorisation of X I - G - c I with X = lambda (1 + 2^-40) and c covering
-// its backward error proves lambda_max(G) < X, so the value returned is within
-// 2^-41 (relative) of sigma_max.  When the certificate fails (slow
-// convergence) the largest Jacobi eigenvalue of G is taken instead (the
-// "small SVD" of the section 3 remark).  Distances within 2^-40 of each
-// other count as ties only at that level; the cyclic Jacobi solve costs
-// about fifteen times the power iteration and its certificate.
+// E = D B (B given, global, row stride p) or E = D (B null) for D in the
+// warp's shared scratch (row stride p), formed in FP64: lane r holds row r in
+// e[] and column r in ecol[]; E itself is left in ws.E (row stride p + 1).
 template <int PM>
-__device__ double exact_sigma_d_warp(const double* sD, const double* __restrict__ B, int p, WarpScratch ws) {
+__device__ void form_e_warp(const double* sD, const double* __restrict__ B, int p, WarpScratch ws, double (&e)[PM],
+                            double (&ecol)[PM]) {
     const int lane = threadIdx.x & 31;
     const bool act = lane < p;
     const int ld = p + 1;
-    double e[PM];
 #pragma unroll
     for (int j = 0; j < PM; ++j) e[j] = 0.0;
     if (act) {
-        for (int k = 0; k < p; ++k) {
-            const double dk = sD[lane * p + k];
+        if (B) {
+            for (int k = 0; k < p; ++k) {
+                const double dk = sD[lane * p + k];
+#pragma unroll
+                for (int j = 0; j < PM; ++j)
+                    if (j < p) e[j] = fma(dk, B[k * p + j], e[j]);
+            }
+        } else {
 #pragma unroll
             for (int j = 0; j < PM; ++j)
-                if (j < p) e[j] = fma(dk, B[k * p + j], e[j]);
+                if (j < p) e[j] = sD[lane * p + j];
         }
     }
     __syncwarp();
@@ -1549,10 +1577,19 @@ __device__ double exact_sigma_d_warp(const double* sD, const double* __restrict_
             if (j < p) ws.E[lane * ld + j] = e[j];
     }
     __syncwarp();
-    double ecol[PM];
 #pragma unroll
     for (int r = 0; r < PM; ++r) ecol[r] = (act && r < p) ? ws.E[r * ld + lane] : 0.0;
-    // start vector: the largest row of E (lowest row on ties)
+}
+
+// Power iteration on G = E^T E from E's largest row (lowest row on ties):
+// the Rayleigh quotients ||E v||^2 (||v|| = 1) rise towards lambda_max(G);
+// stops after three steps that gain less than 2^-50 (relative) or after 300.
+// Returns the largest quotient, 0 when E = 0.
+template <int PM>
+__device__ double power_lambda_warp(const double (&e)[PM], const double (&ecol)[PM], int p, WarpScratch ws) {
+    const int lane = threadIdx.x & 31;
+    const bool act = lane < p;
+    const int ld = p + 1;
     double rn = 0.0;
 #pragma unroll
     for (int j = 0; j < PM; ++j) rn = fma(e[j], e[j], rn);
@@ -1564,7 +1601,7 @@ __device__ double exact_sigma_d_warp(const double* sD, const double* __restrict_
         const int oi = __shfl_xor_sync(0xffffffffu, br, o);
         if (ob > best || (ob == best && oi < br)) { best = ob; br = oi; }
     }
-    if (!(best > 0.0)) return 0.0;                     // E = 0
+    if (!(best > 0.0)) return 0.0;
     double v = act ? ws.E[br * ld + lane] : 0.0;
     v /= sqrt(best);
     double lam = 0.0;
@@ -1579,7 +1616,7 @@ __device__ double exact_sigma_d_warp(const double* sD, const double* __restrict_
             for (int j = 0; j < PM; ++j)
                 if (j < p) wr = fma(e[j], ws.v[j], wr);
         }
-        const double l2 = warp_sum(wr * wr);           // v^T G v, ||v|| = 1
+        const double l2 = warp_sum(wr * wr);
         quiet = (l2 - lam <= 0x1p-50 * l2) ? quiet + 1 : 0;
         lam = fmax(lam, l2);
         ws.w[lane] = wr;
@@ -1594,29 +1631,110 @@ __device__ double exact_sigma_d_warp(const double* sD, const double* __restrict_
         if (!(nu > 0.0)) break;
         v = uj / nu;
     }
-    // G (or X I - G) into the scratch: G[lane][k] = sum_r E[r][lane] E[r][k]
-    auto build_g = [&](double X, bool neg) {
-        __syncwarp();
-        for (int k = 0; k < p; ++k) {
-            double g = 0.0;
-            for (int r = 0; r < p; ++r) g = fma(ecol[r], __shfl_sync(0xffffffffu, ecol[r], k), g);
-            if (act) ws.E[lane * ld + k] = neg ? ((k == lane ? X : 0.0) - g) : g;
-        }
-        __syncwarp();
-    };
-    const double X = lam * (1.0 + 0x1p-40);
-    build_g(X, true);
-    const double tr = warp_sum(act ? ws.E[lane * ld + lane] : 0.0);
-    if (tr > 0.0) {
-        const double c = 2.0 * gamma_u(p + 1) * tr;
-        if (act) ws.E[lane * ld + lane] -= c;
-        __syncwarp();
-        if (cholesky_warp(ws.E, p, ld) == p) return sqrt(lam);
+    __syncwarp();
+    return lam;
+}
+
+// G = E^T E (X = 0, neg false) or X I - G (neg true) into ws.E from the
+// columns of E held in ecol[].
+template <int PM>
+__device__ void gram_warp(const double (&ecol)[PM], int p, double X, bool neg, WarpScratch ws) {
+    const int lane = threadIdx.x & 31;
+    const int ld = p + 1;
+    __syncwarp();
+    for (int k = 0; k < p; ++k) {
+        double g = 0.0;
+        for (int r = 0; r < p; ++r) g = fma(ecol[r], __shfl_sync(0xffffffffu, ecol[r], k), g);
+        if (lane < p) ws.E[lane * ld + k] = neg ? ((k == lane ? X : 0.0) - g) : g;
     }
-    build_g(0.0, false);
-    const double lj = jacobi_lambda_max_warp(ws.E, p, ld);
+    __syncwarp();
+}
+
+// True when lambda_max(E^T E) < X is proved: the Cholesky factorisation of
+// X I - G - c I, G computed, c = 2 gamma_{p+1} tr(X I - G) covering the
+// factorisation's backward error, runs to completion (overwrites ws.E).
+template <int PM>
+__device__ bool lambda_below_warp(const double (&ecol)[PM], int p, double X, WarpScratch ws) {
+    const int lane = threadIdx.x & 31;
+    const int ld = p + 1;
+    gram_warp<PM>(ecol, p, X, true, ws);
+    const double tr = warp_sum(lane < p ? ws.E[lane * ld + lane] : 0.0);
+    if (!(tr > 0.0)) return false;
+    const double c = 2.0 * gamma_u(p + 1) * tr;
+    if (lane < p) ws.E[lane * ld + lane] -= c;
+    __syncwarp();
+    const bool ok = cholesky_warp(ws.E, p, ld) == p;
+    __syncwarp();
+    return ok;
+}
+
+// sigma_max(E) of E = D B for D = A_c - A_i already in the warp's shared
+// scratch sD and B in global memory (row stride p).  lambda_max(E^T E) by the
+// power iteration, certified with X = lambda (1 + 2^-40): the value returned
+// is then within 2^-41 (relative) of sigma_max.  Where the certificate fails
+// (slow convergence) the largest Jacobi eigenvalue of G is taken instead (the
+// "small SVD" of the section 3 remark), at about fifteen times the cost.
+template <int PM>
+__device__ double exact_sigma_d_warp(const double* sD, const double* __restrict__ B, int p, WarpScratch ws) {
+    double e[PM], ecol[PM];
+    form_e_warp<PM>(sD, B, p, ws, e, ecol);
+    const double lam = power_lambda_warp<PM>(e, ecol, p, ws);
+    if (lam == 0.0) return 0.0;
+    if (lambda_below_warp<PM>(ecol, p, lam * (1.0 + 0x1p-40), ws)) return sqrt(lam);
+    gram_warp<PM>(ecol, p, 0.0, false, ws);
+    const double lj = jacobi_lambda_max_warp(ws.E, p, p + 1);
     __syncwarp();
     return sqrt(fmax(lj, 0.0));
+}
+
+// Bracket [*lo, *hi] of ||A||_2 for A in the warp's shared scratch sA (row
+// stride p): lo from the power iteration's quotient (its rounding, a few p u,
+// is far inside the 2^-40 taken off), hi from the first certified
+// X = lambda (1 + 2^(2k - 40)), k = 0..30 (infinite when none is).
+template <int PM>
+__device__ void norm2_bracket_warp(const double* sA, int p, WarpScratch ws, double* lo, double* hi) {
+    double e[PM], ecol[PM];
+    form_e_warp<PM>(sA, nullptr, p, ws, e, ecol);
+    const double lam = power_lambda_warp<PM>(e, ecol, p, ws);
+    *lo = 0.0;
+    *hi = 0.0;
+    if (lam == 0.0) return;
+    *lo = sqrt(lam) * (1.0 - 0x1p-40);
+    *hi = __longlong_as_double(0x7ff0000000000000ll);   // +inf
+    for (int k = 0; k <= 30; ++k) {
+        const double X = lam * (1.0 + ldexp(1.0, 2 * k - 40));
+        if (lambda_below_warp<PM>(ecol, p, X, ws)) {
+            *hi = sqrt(X) * (1.0 + 0x1p-50);
+            break;
+        }
+    }
+}
+
+// Brackets of ||A_i||_2 for a size group's patches, the keys of the
+// norm-window search: a warp per patch, the patch staged in its scratch.
+template <int PM>
+__global__ void __launch_bounds__(EVAL_THREADS) k_patch_norms(const double* __restrict__ Ag, int count, int p,
+                                                              double* __restrict__ nlo, double* __restrict__ nhi) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const int ld = p + 1;
+    double* wbase = reinterpret_cast<double*>(smem) + (size_t)wid * ((size_t)p * ld + 64 + (size_t)p * p);
+    WarpScratch ws{wbase, wbase + p * ld, wbase + p * ld + 32};
+    double* sA = wbase + (size_t)p * ld + 64;
+    const int64_t pp = (int64_t)p * p;
+    for (int i = blockIdx.x * wpb + wid; i < count; i += gridDim.x * wpb) {
+        __syncwarp();
+        for (int e = lane; e < p * p; e += 32) sA[e] = Ag[(int64_t)i * pp + e];
+        __syncwarp();
+        double lo, hi;
+        norm2_bracket_warp<PM>(sA, p, ws, &lo, &hi);
+        if (lane == 0) {
+            nlo[i] = lo;
+            nhi[i] = hi;
+        }
+    }
 }
 
 // D = A_c - A_i into the warp's scratch with coalesced loads; true when the
@@ -1835,6 +1953,15 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
     int rounds_total = 0;
     int first_singular = -1;
     if (m0 > 0 && ctx->groups.size() != 1) { set_error(ctx, "a seed database needs patches of one size"); return PSR_ERR_INVALID_ARG; }
+    const bool window = ctx->opts.search == PSR_SEARCH_NORM_WINDOW;
+    if (window && (m0 > 0 || hints)) {
+        set_error(ctx, "the norm-window search takes no seed database or hints");
+        return PSR_ERR_INVALID_ARG;
+    }
+    if (window && ctx->opts.match == PSR_MATCH_CLOSEST) {
+        set_error(ctx, "the norm-window search is a first-match search");
+        return PSR_ERR_INVALID_ARG;
+    }
     for (size_t g = 0; g < ctx->groups.size() && rc == PSR_OK; ++g) {
         Group& G = ctx->groups[g];
         const int p = G.p, count = G.count;
@@ -1895,7 +2022,25 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         count_launch();
         launch_sketch(Ag, Ball, count, p, skX, skDen, skY32, skF, skR, s);
         PSR_CHECK_LAUNCH(ctx, "patch sketches");
-        const SketchDB sk{skX, skDen, skF, skR, skY32};
+        double* skN = nullptr;                     // [2][count] ||A_i||_2 brackets (norm window)
+        if (window) {
+            PSR_CUDA(ctx, psr::dev_alloc(&skN, sizeof(double) * 2 * (size_t)count));
+            const int wpn = EVAL_THREADS / 32;
+            const size_t smem_n = (size_t)wpn * ((size_t)p * (p + 1) + 64 + (size_t)p * p) * 8;
+            const void* kn = (p <= 8) ? (const void*)k_patch_norms<8>
+                           : (p <= 16) ? (const void*)k_patch_norms<16> : (const void*)k_patch_norms<32>;
+            if ((rc = set_smem(kn, smem_n)) != PSR_OK) break;
+            const int nb = std::max(1, std::min((count + wpn - 1) / wpn, 152 * 8));
+            count_launch();
+            if (p <= 8)
+                k_patch_norms<8><<<nb, EVAL_THREADS, smem_n, s>>>(Ag, count, p, skN, skN + count);
+            else if (p <= 16)
+                k_patch_norms<16><<<nb, EVAL_THREADS, smem_n, s>>>(Ag, count, p, skN, skN + count);
+            else
+                k_patch_norms<32><<<nb, EVAL_THREADS, smem_n, s>>>(Ag, count, p, skN, skN + count);
+            PSR_CHECK_LAUNCH(ctx, "patch norms");
+        }
+        const SketchDB sk{skX, skDen, skF, skR, skY32, skN, window ? skN + count : nullptr};
         SketchDB skd{skX, nullptr, nullptr, nullptr, nullptr};
         double *sdDen = nullptr, *sdF = nullptr, *sdR = nullptr;
         RoundDev init{};
@@ -2022,6 +2167,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
                 PSR_CUDA(ctx, psr::dev_alloc(&mw.accm, 8 * (size_t)count));
                 PSR_CUDA(ctx, psr::dev_alloc(&mw.exm, 8 * (size_t)count));
                 PSR_CUDA(ctx, psr::dev_alloc(&mw.rejm, 8 * (size_t)count));
+                if (window) PSR_CUDA(ctx, psr::dev_alloc(&mw.wom, 8 * (size_t)count));
                 PSR_CUDA(ctx, psr::dev_alloc(&mw.accA, 8 * 2 * KC));
                 PSR_CUDA(ctx, psr::dev_alloc(&mw.exA, 8 * 2 * KC));
                 PSR_CUDA(ctx, psr::dev_alloc(&mw.npB, sizeof(int32_t) * 2));
@@ -2094,6 +2240,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
                 psr::dev_free(mw.accm);
                 psr::dev_free(mw.exm);
                 psr::dev_free(mw.rejm);
+                psr::dev_free(mw.wom);
                 psr::dev_free(mw.accA);
                 psr::dev_free(mw.exA);
                 psr::dev_free(mw.npB);
@@ -2204,7 +2351,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         psr::dev_free(fro_all);
         psr::dev_free(w_all);
         psr::dev_free(sing_all);
-        for (double* q : {skX, skDen, skF, skR, sdDen, sdF, sdR}) psr::dev_free(q);
+        for (double* q : {skX, skDen, skF, skR, sdDen, sdF, sdR, skN}) psr::dev_free(q);
         psr::dev_free(skY32);
         psr::dev_free(sdY32);
         psr::dev_free(surv_list);

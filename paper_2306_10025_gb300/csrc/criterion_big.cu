@@ -542,6 +542,96 @@ __global__ void __launch_bounds__(BT) k_sketch_dirs_big(const double* __restrict
     }
 }
 
+// Brackets [nlo, nhi] of ||A_i||_2 for the norm-window search (the keys of
+// criterion.cu's warp path, for p > 32): a block per patch, thread r row r of
+// A in shared memory.  Power iteration on G = A^T A from A's largest row
+// until the Rayleigh quotient lambda stalls (three steps gaining < 2^-50, at
+// most 300); nlo = sqrt(lambda)(1 - 2^-40), nhi from the first
+// X = lambda (1 + 2^(2k - 40)), k = 0..30, for which the Cholesky
+// factorisation of X I - G - c I (c = 2 gamma_{p+1} tr, its backward error)
+// runs to completion, proving lambda_max(G) < X (infinite when none does).
+// scratch: 2 p^2 doubles per block (G, then the factorised copy).
+__global__ void __launch_bounds__(BT) k_patch_norms_big(const double* __restrict__ Ag, int count, int p,
+                                                        double* __restrict__ nlo, double* __restrict__ nhi,
+                                                        double* __restrict__ scratch) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int ld = p + 1;
+    double* E = reinterpret_cast<double*>(smem);
+    double* v = E + (size_t)p * ld;
+    double* w = v + BT;
+    double* red = w + BT;
+    int* redi = reinterpret_cast<int*>(red + 4);
+    const int r = threadIdx.x;
+    const bool act = r < p;
+    const int64_t pp = (int64_t)p * p;
+    double* Gs = scratch + (int64_t)blockIdx.x * 2 * pp;
+    double* Hs = Gs + pp;
+    for (int i = blockIdx.x; i < count; i += gridDim.x) {
+        __syncthreads();
+        for (int e = r; e < p * p; e += BT) E[(e / p) * ld + (e % p)] = Ag[(int64_t)i * pp + e];
+        __syncthreads();
+        double rn = 0.0;
+        if (act)
+            for (int j = 0; j < p; ++j) rn = fma(E[r * ld + j], E[r * ld + j], rn);
+        double best;
+        int br;
+        bargmax(act ? rn : -1.0, r, red, redi, &best, &br);
+        double lo = 0.0, hi = 0.0;
+        if (best > 0.0) {
+            v[r] = act ? E[br * ld + r] / sqrt(best) : 0.0;
+            double lam = 0.0;
+            int quiet = 0;
+            for (int it = 0; it < 300 && quiet < 3; ++it) {
+                __syncthreads();
+                double wr = 0.0;
+                if (act)
+                    for (int j = 0; j < p; ++j) wr = fma(E[r * ld + j], v[j], wr);
+                const double l2 = bsum(wr * wr, red);
+                quiet = (l2 - lam <= 0x1p-50 * l2) ? quiet + 1 : 0;
+                lam = fmax(lam, l2);
+                w[r] = wr;
+                __syncthreads();
+                double uj = 0.0;
+                if (act)
+                    for (int q = 0; q < p; ++q) uj = fma(E[q * ld + r], w[q], uj);
+                const double nu = sqrt(bsum(uj * uj, red));
+                if (!(nu > 0.0)) break;
+                v[r] = act ? uj / nu : 0.0;
+            }
+            // G = A^T A, thread r column r
+            __syncthreads();
+            if (act)
+                for (int k = 0; k < p; ++k) {
+                    double g = 0.0;
+                    for (int q = 0; q < p; ++q) g = fma(E[q * ld + k], E[q * ld + r], g);
+                    Gs[k * p + r] = g;
+                }
+            lo = sqrt(lam) * (1.0 - 0x1p-40);
+            hi = __longlong_as_double(0x7ff0000000000000ll);
+            for (int k = 0; k <= 30; ++k) {
+                const double X = lam * (1.0 + ldexp(1.0, 2 * k - 40));
+                __syncthreads();
+                if (act)
+                    for (int q = 0; q < p; ++q) Hs[q * p + r] = (q == r ? X : 0.0) - Gs[q * p + r];
+                __syncthreads();
+                const double tr = bsum(act ? Hs[r * p + r] : 0.0, red);
+                if (!(tr > 0.0)) continue;
+                if (act) Hs[r * p + r] -= 2.0 * gamma_u(p + 1) * tr;
+                if (cholesky_block(Hs, p) == p) {
+                    hi = sqrt(X) * (1.0 + 0x1p-50);
+                    break;
+                }
+            }
+        }
+        if (r == 0) {
+            nlo[i] = lo;
+            nhi[i] = hi;
+        }
+    }
+}
+
+size_t norms_big_smem(int p) { return ((size_t)p * (p + 1) + 2 * BT + 4) * 8 + 4 * 4; }
+
 // Screen of one candidate by one warp (lanes over the sketch entries): true
 // when the certified sketch lower bound reaches tol (see criterion.cu for the
 // bound and its rounding terms).
@@ -575,7 +665,9 @@ __global__ void __launch_bounds__(256) k_round_screen_big(RoundBig* st, const in
                                                           int p, const float* __restrict__ Y32,
                                                           const double* __restrict__ den, const double* __restrict__ fa,
                                                           const double* __restrict__ rho, double tol,
-                                                          int32_t* __restrict__ surv_list) {
+                                                          int32_t* __restrict__ surv_list,
+                                                          const double* __restrict__ nlo,
+                                                          const double* __restrict__ nhi) {
     __shared__ float sy[SKB * SKD];
     __shared__ double sden[SKB];
     if (st->done) return;
@@ -594,6 +686,10 @@ __global__ void __launch_bounds__(256) k_round_screen_big(RoundBig* st, const in
     int my_min = count;
     for (int c = i0 + 1 + gw; c < count; c += nw) {
         if (phi[c] != -1) continue;                 // warp-uniform
+        if (nlo && outside_window(norm_window(nlo[c], nhi[c], tol), nlo[i0], nhi[i0])) {
+            my_min = min(my_min, c);                // outside the norm window: not a test
+            continue;
+        }
         ++ev;
         const bool rej = screen_big(Y32 + (int64_t)c * SKB * p, fa[c], sy, sden, fc, rhoc, p, tol);
         if (rej) {
@@ -739,7 +835,8 @@ int run_alg1_big(psr_ctx* ctx, Group& G, const double* Ag, cudaStream_t s, int64
     const int64_t pp = (int64_t)p * p;
     int32_t *phi_l = nullptr, *rep_l = nullptr, *sing_all = nullptr, *surv = nullptr;
     double *Ball = nullptr, *fro_all = nullptr, *w_all = nullptr, *X = nullptr, *den = nullptr, *fa = nullptr,
-           *rho = nullptr, *scratch = nullptr;
+           *rho = nullptr, *scratch = nullptr, *nrm = nullptr;
+    const bool window = ctx->opts.search == PSR_SEARCH_NORM_WINDOW;
     float* Y32 = nullptr;
     RoundBig* st = nullptr;
     RoundBig* h_st = nullptr;
@@ -747,7 +844,8 @@ int run_alg1_big(psr_ctx* ctx, Group& G, const double* Ag, cudaStream_t s, int64
     const int decide_blocks = 152 * 2;
     auto cleanup = [&]() {
         for (void* q : {(void*)rep_l, (void*)sing_all, (void*)surv, (void*)Ball, (void*)fro_all, (void*)w_all,
-                        (void*)X, (void*)den, (void*)fa, (void*)rho, (void*)scratch, (void*)Y32, (void*)st})
+                        (void*)X, (void*)den, (void*)fa, (void*)rho, (void*)scratch, (void*)Y32, (void*)st,
+                        (void*)nrm})
             psr::dev_free(q);
         psr::host_free(h_st);
     };
@@ -787,6 +885,20 @@ int run_alg1_big(psr_ctx* ctx, Group& G, const double* Ag, cudaStream_t s, int64
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "k_entry_big"); cleanup(); psr::dev_free(phi_l); return rc; }
     }
+    if (window) {
+        // ||A_i||_2 brackets of the norm-window search (scratch reused: the
+        // decide blocks outnumber these)
+        const int nb = std::max(1, std::min(count, decide_blocks));
+        BIG_CK(psr::dev_alloc(&nrm, sizeof(double) * 2 * (size_t)count));
+        if ((rc = set_big_smem((const void*)k_patch_norms_big, norms_big_smem(p))) != PSR_OK) {
+            cleanup();
+            psr::dev_free(phi_l);
+            return rc;
+        }
+        count_launch();
+        k_patch_norms_big<<<nb, BT, norms_big_smem(p), s>>>(Ag, count, p, nrm, nrm + count, scratch);
+        BIG_CK(cudaGetLastError());
+    }
     RoundBig init{};
     init.first_singular = -1;
     init.next = 0;
@@ -797,7 +909,8 @@ int run_alg1_big(psr_ctx* ctx, Group& G, const double* Ag, cudaStream_t s, int64
     for (;;) {
         for (int q = 0; q < batch; ++q) {
             count_launch();
-            k_round_screen_big<<<screen_blocks, 256, 0, s>>>(st, phi_l, count, p, Y32, den, fa, rho, tol, surv);
+            k_round_screen_big<<<screen_blocks, 256, 0, s>>>(st, phi_l, count, p, Y32, den, fa, rho, tol, surv, nrm,
+                                                             window ? nrm + count : nullptr);
             count_launch();
             k_round_decide_big<<<decide_blocks, BT, big_smem(p), s>>>(st, phi_l, count, Ag, p, Ball, fro_all, w_all,
                                                                      sing_all, tol, surv, rep_l, scratch);

@@ -71,6 +71,27 @@ __device__ __forceinline__ int warp_sum_i(int v) {
     return v;
 }
 
+// Norm window of Alg. 1's sorted search (section 3.1, after Alg. 1).  Since
+// d(A_i, B_c) = ||(A_c - A_i) B_c^-1||_2 >= ||A_c - A_i||_2 / ||A_c||_2 >=
+// | ||A_c||_2 - ||A_i||_2 | / ||A_c||_2, entry c can pass only when
+// ||A_i|| / (1 + tol) < ||A_c|| < ||A_i|| / (1 - tol); the window is widened
+// by 1e-12 (relative) against rounding.  With ||A_i|| known as a bracket
+// [alo, ahi], the window spans every value in it; an entry whose own bracket
+// [klo, khi] lies wholly outside is skipped: neither tested nor counted.
+struct NormWin {
+    double lo, hi;
+};
+__device__ __forceinline__ NormWin norm_window(double alo, double ahi, double tol) {
+    NormWin w;
+    w.lo = __dmul_rn(__ddiv_rn(alo, 1.0 + tol), 1.0 - 1e-12);
+    w.hi = tol < 1.0 ? __dmul_rn(__ddiv_rn(ahi, 1.0 - tol), 1.0 + 1e-12)
+                     : __longlong_as_double(0x7ff0000000000000ll);
+    return w;
+}
+__device__ __forceinline__ bool outside_window(const NormWin& w, double klo, double khi) {
+    return khi < w.lo || klo > w.hi;
+}
+
 // Device-side status word bits (written by kernels, read by the host).
 enum : int {
     ST_UNSORTED = 1,

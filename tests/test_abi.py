@@ -76,3 +76,33 @@ def test_debug_inject_arguments_without_device():
     import torch
     if not torch.cuda.is_available():
         assert lib.psr_debug_inject(2, 100) == -5
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """Every struct the binding marshals has the header's size and field
+    offsets (a C program built against include/psr.h prints them)."""
+    import ctypes as C
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_2306_10025_gb300 import binding as B
+    structs = {n: c for n, c in vars(B).items()
+               if n.startswith("psr_") and isinstance(c, type) and issubclass(c, C.Structure)}
+    assert {"psr_opts", "psr_stats", "psr_csr", "psr_patches"} <= set(structs)
+    body = ["#include <stdio.h>", "#include <stddef.h>", '#include "psr.h"', "int main(void) {"]
+    want = []
+    for n, c in sorted(structs.items()):
+        body.append(f'printf("%zu\\n", sizeof({n}));')
+        want.append(C.sizeof(c))
+        for f, _ in c._fields_:
+            body.append(f'printf("%zu\\n", offsetof({n}, {f}));')
+            want.append(getattr(c, f).offset)
+    body += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(body) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == want

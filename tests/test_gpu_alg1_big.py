@@ -209,3 +209,104 @@ def test_closest_match_differs_from_first_match_somewhere(lib):
         A = O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d())
         moved += int((O.alg1(A, tol)["phi"] != O.alg1_closest_match(A, tol)["phi"]).sum())
     assert moved >= 30
+
+
+def _window_clear(A, tol, reps, margin=1e-9):
+    """No entry's ||A_c||_2 lies within `margin` (relative) of a patch's
+    widened window edge, so that brackets of a few 1e-12 decide membership
+    as the oracle's exact norms do.  An entry within 1e-13 of the patch's
+    own norm (equal or mirrored patches) is inside on both sides for any
+    tol >= 0, brackets included, and is left out of the check."""
+    nrm = np.linalg.norm(A, ord=2, axis=(1, 2))
+    keys = nrm[np.asarray(reps, dtype=np.int64)]
+    same = np.abs(keys[None, :] - nrm[:, None]) <= 1e-13 * nrm[:, None]
+    lo = nrm / (1.0 + tol) * (1 - 1e-12)
+    gaps = [np.abs(keys[None, :] - lo[:, None]) / lo[:, None]]
+    if tol < 1.0:
+        hi = nrm / (1.0 - tol) * (1 + 1e-12)
+        gaps.append(np.abs(keys[None, :] - hi[:, None]) / hi[:, None])
+    return all(float(np.where(same, np.inf, g).min()) > margin for g in gaps)
+
+
+SORTED_CASES = CLOSEST_CASES + [("diff3d_tight", lambda: P.diffusion3d_q2(4, sigma=1.0, corr_len=2.0, seed=2), 0.05)]
+
+
+@pytest.mark.parametrize("name,make,tol", SORTED_CASES)
+def test_norm_window_search_bit_exact(lib, name, make, tol):
+    """opts.search = norm_window (the sorted search of section 3.1): phi,
+    the representatives and the evaluation count equal the oracle's
+    alg1_sorted, and no more tests are made than in creation order."""
+    pr = make()
+    A = O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d())
+    ref = O.alg1_sorted(A, tol)
+    assert _window_clear(A, tol, ref["reps"])
+    ctx = ctx_for(lib, pr, tol=tol, weighting=pr.weighting, krylov=pr.krylov, search="norm_window")
+    phi, reps, m = ctx.assignment()
+    assert np.array_equal(reps.cpu().numpy(), ref["reps"])
+    assert np.array_equal(phi.cpu().numpy(), ref["phi"])
+    assert ctx.stats()["criterion_evals"] == ref["evals"]
+    assert ref["evals"] <= O.alg1(A, tol)["evals"]
+    ctx.destroy()
+
+
+@pytest.mark.parametrize("case", ["jitter4", "q5"])
+def test_norm_window_search_big_groups(lib, case):
+    """The norm-window search for patches of 33..128 DOFs (the block kernels)
+    per size group, against alg1_sorted: phi, representatives, evaluations."""
+    if case == "jitter4":
+        pr, tols = P.stokes3d_q2q1(4, seed=3), [22.0, 0.9]
+        groups = _groups(pr)
+    else:
+        pr, tols = P.smooth2d_qp(N=10, p=5), [0.2, 0.5]
+        groups = [(36, np.arange(pr.n_patches), O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n,
+                                                                   pr.dofs2d()))]
+    for tol in tols:
+        refs = [O.alg1_sorted(A, tol) for _, _, A in groups]
+        for (_, _, A), r in zip(groups, refs):
+            assert _window_clear(A, tol, r["reps"])
+        ctx = ctx_for(lib, pr, tol=tol, weighting="left", krylov="fgmres", search="norm_window")
+        phi, reps, m = ctx.assignment()
+        phi = phi.cpu().numpy()
+        reps = reps.cpu().numpy()
+        base = 0
+        for (s, idx, _), r in zip(groups, refs):
+            mg = len(r["reps"])
+            assert np.array_equal(phi[idx] - base, r["phi"]), (case, tol, s)
+            assert np.array_equal(reps[base:base + mg], idx[r["reps"]]), (case, tol, s)
+            base += mg
+        assert m == base
+        assert ctx.stats()["criterion_evals"] == sum(r["evals"] for r in refs), (case, tol)
+        ctx.destroy()
+
+
+def test_norm_window_search_rejects_unsupported(lib):
+    """The norm-window search is a first-match search of the spectral
+    criterion: with closest match or the l1 criterion setup fails."""
+    pr = P.poisson2d_q2(4)
+    for kw in (dict(match="closest"), dict(criterion="l1")):
+        with pytest.raises(lib.PsrError):
+            ctx_for(lib, pr, tol=0.1, search="norm_window", **kw)
+
+
+@pytest.mark.parametrize("N", [64, 128])
+def test_norm_window_search_bench_size(lib, N):
+    """The norm-window search on the graded Stokes mesh at the benchmark
+    sizes (4,096 and 16,384 patches of 22 DOFs, tol 1e-2): phi and the
+    representatives of the creation-order search, the evaluation count of
+    the oracle's alg1_sorted, below the creation-order count."""
+    pr = P.stokes2d_q2q1(N, 1.05)
+    tol = 1e-2
+    A = O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d())
+    ref = O.alg1_sorted(A, tol)
+    assert _window_clear(A, tol, ref["reps"])
+    ctx = ctx_for(lib, pr, tol=tol, weighting="left", krylov="fgmres", search="norm_window")
+    phi, reps, m = ctx.assignment()
+    assert np.array_equal(phi.cpu().numpy(), ref["phi"])
+    assert np.array_equal(reps.cpu().numpy(), ref["reps"])
+    ev = ctx.stats()["criterion_evals"]
+    ctx.destroy()
+    assert ev == ref["evals"]
+    ctx = ctx_for(lib, pr, tol=tol, weighting="left", krylov="fgmres")
+    ev0 = ctx.stats()["criterion_evals"]
+    ctx.destroy()
+    assert ev < ev0
