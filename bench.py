@@ -311,7 +311,8 @@ def forms_subline(L, key, forms, devc, reps=4, learned=False):
     setup and solve seconds (CUDA events, median after one warm-up, L2
     flushed before each), iterations, relative residual reached, database
     size, apply rate, and the speedup of setup + solve over the first form
-    (FP64 full storage)."""
+    (FP64 full storage).  A form's optional fourth item holds further
+    options (the norm-window search)."""
     import torch
     cfg = CONFIGS[key]
     pr = build_problem(cfg)
@@ -322,9 +323,11 @@ def forms_subline(L, key, forms, devc, reps=4, learned=False):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=devc)
     stream = torch.cuda.current_stream()
     rows = {}
-    for name, tol, prec in forms:
+    for form in forms:
+        name, tol, prec = form[:3]
+        extra = form[3] if len(form) > 3 else {}
         opts = L.make_opts(tol=tol, store_prec=prec, weighting=cfg["weighting"], krylov=cfg["krylov"], restart=30,
-                           rtol=1e-8, maxit=cfg["maxit"])
+                           rtol=1e-8, maxit=cfg["maxit"], **extra)
         rp, ci, va, dofs, offs = dev_in
         setups, solves = [], []
         for rep in range(reps):
@@ -345,7 +348,7 @@ def forms_subline(L, key, forms, devc, reps=4, learned=False):
                 ctx.destroy()
         ams = _apply_median(ctx, pr.n, 100, devc, flush=flush)
         ctx.destroy()
-        rows[name] = {"tol": tol, "store_prec": prec, "m_p": st["m_p"], "retained_fraction": st["m_p"] / pr.n_patches,
+        rows[name] = {"tol": tol, "store_prec": prec, **extra, "m_p": st["m_p"], "retained_fraction": st["m_p"] / pr.n_patches,
                       "factor_bytes": st["factor_bytes"], "setup_s": statistics.median(setups),
                       "solve_s": statistics.median(solves), "iterations": info["iterations"],
                       "converged": info["converged"], "relres": info["relres"],
@@ -368,15 +371,18 @@ def forms_subline(L, key, forms, devc, reps=4, learned=False):
 def config_sublines(L, devc):
     """The other workloads of the benchmark, full storage against the
     clustered forms: 2D Q2 Poisson 16^2 (tol 1e-12), graded 2D Stokes 128^2
-    (tol 1e-3 .. 1e-1, FP64 and FP32 entries), 3D Nedelec 64^3 (FP32 / BF16
-    entries, tol 0.1), 3D lognormal Q2 32^3 (tol 0.1, FP64 / FP32 / BF16, and
-    the learned assignment on a matrix sequence)."""
+    (tol 1e-3 .. 1e-1, FP64 and FP32 entries, the norm-window search), 3D
+    Nedelec 64^3 (FP32 / BF16 entries, tol 0.1), 3D lognormal Q2 32^3 (tol
+    0.1, FP64 / FP32 / BF16, the norm-window search, and the learned
+    assignment on a matrix sequence)."""
     return {
         "poisson2d_16": forms_subline(L, "poisson2d", [("full_fp64", 0.0, "fp64"), ("clustered_fp64", 1e-12, "fp64")],
                                       devc),
         "stokes2d_128": forms_subline(L, "stokes2d", [("full_fp64", 0.0, "fp64"),
                                                       ("clustered_fp64_tol_1e-3", 1e-3, "fp64"),
                                                       ("clustered_fp64", 1e-2, "fp64"),
+                                                      ("clustered_fp64_norm_window", 1e-2, "fp64",
+                                                       {"search": "norm_window"}),
                                                       ("clustered_fp32", 1e-2, "fp32"),
                                                       ("clustered_fp64_tol_1e-1", 1e-1, "fp64")], devc),
         "nedelec3d_64": forms_subline(L, "nedelec3d", [("full_fp64", 0.0, "fp64"), ("full_fp32", 0.0, "fp32"),
@@ -384,6 +390,8 @@ def config_sublines(L, devc):
                                                        ("clustered_bf16", 0.1, "bf16")], devc, reps=2),
         "diffusion3d_32": forms_subline(L, "diffusion3d", [("full_fp64", 0.0, "fp64"),
                                                            ("clustered_fp64", 0.1, "fp64"),
+                                                           ("clustered_fp64_norm_window", 0.1, "fp64",
+                                                            {"search": "norm_window"}),
                                                            ("clustered_fp32", 0.1, "fp32"),
                                                            ("clustered_bf16", 0.1, "bf16")], devc, learned=True),
     }
