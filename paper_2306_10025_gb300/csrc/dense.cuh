@@ -46,11 +46,21 @@ __device__ __forceinline__ bool gj_invert_warp(double* S, int p, int ld, double*
         if (pv == 0.0) pv = 1.0;                 // singular: keep going, result discarded
         for (int j = lane; j < p; j += 32) {
             const double rj = (j == k ? 1.0 : S[k * ld + j]) / pv;
-            for (int i = 0; i < p; ++i) {
-                if (i == k) continue;
-                const double a = (j == k) ? 0.0 : S[i * ld + j];
-                S[i * ld + j] = fma(-colk[i], rj, a);
+            // every row, eight at a time with the loads ahead of the stores
+            // (row k's value is overwritten below; column k starts from zero)
+            const bool isk = (j == k);
+            int i = 0;
+            for (; i + 8 <= p; i += 8) {
+                double x[8], c[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    x[u] = S[(i + u) * ld + j];
+                    c[u] = colk[i + u];
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) S[(i + u) * ld + j] = fma(-c[u], rj, isk ? 0.0 : x[u]);
             }
+            for (; i < p; ++i) S[i * ld + j] = fma(-colk[i], rj, isk ? 0.0 : S[i * ld + j]);
             S[k * ld + j] = rj;
         }
         __syncwarp();
