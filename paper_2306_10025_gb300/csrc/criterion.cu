@@ -561,11 +561,11 @@ struct SketchDB {
     const float* Y32;              // [count][SK][p] y_i rounded to FP32 (the screen's operand)
     const double* nlo;             // [count] brackets of ||A_i||_2 for the norm-window
     const double* nhi;             //   search; null when the search is in creation order
+    const double* wlo;             // [count] each patch's norm window (norm_window of
+    const double* whi;             //   its bracket)
 };
 
-__device__ __forceinline__ NormWin norm_window(const SketchDB& sk, int i, double tol) {
-    return norm_window(sk.nlo[i], sk.nhi[i], tol);
-}
+__device__ __forceinline__ NormWin norm_window(const SketchDB& sk, int i) { return NormWin{sk.wlo[i], sk.whi[i]}; }
 
 
 // Directions of a size group: x_0 = the dominant right singular vector of
@@ -755,7 +755,7 @@ __global__ void __launch_bounds__(EVAL_THREADS) k_round_screen(RoundDev* st, con
         sketch_load<PM>(sk.Y32 + (int64_t)cc * SK * p, p, v);
         const double fi = sk.fa[cc];
         const bool open = cand < count && phi[cc] == -1;
-        const bool wout = open && sk.nlo && outside_window(norm_window(sk, cc, tol), sk.nlo[i0], sk.nhi[i0]);
+        const bool wout = open && sk.nlo && outside_window(norm_window(sk, cc), sk.nlo[i0], sk.nhi[i0]);
         const bool rej = open && (wout || sketch_bound_rejects<PM>(v, fi, sy, sden, fc, rhoc, p, tol));
         if (open && rej) my_min = min(my_min, cand);
         const unsigned opened = __ballot_sync(0xffffffffu, open && !wout);
@@ -1085,7 +1085,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_rounds_multi(
                 sketch_load<PM>(sk.Y32 + (int64_t)i * SK * p, p, v);
                 const float fi32 = __double2float_ru(sk.fa[i]);
                 NormWin w{0.0, 0.0};
-                if (wnd) w = norm_window(sk, i, tol);
+                if (wnd) w = norm_window(sk, i);
                 for (int t = 0; t < nR; ++t) {
                     const int l = sridx[t];
                     if (wnd && outside_window(w, snlo[l], snhi[l])) wo |= 1ull << l;
@@ -1265,7 +1265,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, 4) k_rounds_multi(
                 unsigned long long rb = 0ull, wb = 0ull;
                 const int l1 = min(k, l0 + 32);
                 NormWin w{0.0, 0.0};
-                if (win) w = norm_window(sk, scand[k], tol);
+                if (win) w = norm_window(sk, scand[k]);
                 for (int l = l0; l < l1; ++l) {
                     if (win && outside_window(w, snlo[l], snhi[l])) wb |= 1ull << l;
                     else if (multi_rejects<PM>(v, sfi[k], sy + l * SYS, sthr + l * SK, sbeta[l], p)) rb |= 1ull << l;
@@ -1584,7 +1584,7 @@ __device__ void form_e_warp(const double* sD, const double* __restrict__ B, int 
 // Power iteration on G = E^T E from E's largest row (lowest row on ties):
 // the Rayleigh quotients ||E v||^2 (||v|| = 1) rise towards lambda_max(G);
 // stops after three steps that gain less than 2^-50 (relative) or after 300.
-// Returns the largest quotient, 0 when E = 0.
+// Returns the largest quotient, 0 when E = 0, NaN when E holds a NaN.
 template <int PM>
 __device__ double power_lambda_warp(const double (&e)[PM], const double (&ecol)[PM], int p, WarpScratch ws) {
     const int lane = threadIdx.x & 31;
@@ -1601,6 +1601,7 @@ __device__ double power_lambda_warp(const double (&e)[PM], const double (&ecol)[
         const int oi = __shfl_xor_sync(0xffffffffu, br, o);
         if (ob > best || (ob == best && oi < br)) { best = ob; br = oi; }
     }
+    if (best != best) return best;                  // NaN
     if (!(best > 0.0)) return 0.0;
     double v = act ? ws.E[br * ld + lane] : 0.0;
     v /= sqrt(best);
@@ -1635,17 +1636,113 @@ __device__ double power_lambda_warp(const double (&e)[PM], const double (&ecol)[
     return lam;
 }
 
-// G = E^T E (X = 0, neg false) or X I - G (neg true) into ws.E from the
-// columns of E held in ecol[].
+// lambda_max(G), G = E^T E, estimated by power iteration: in FP32 on E
+// scaled by a power of two (the direction only), from E's largest row (lowest
+// row on ties), until the unit vector moves by at most 2^-21 in every entry
+// three steps running, or after 500 steps; then the Rayleigh quotient
+// ||E v||^2 / ||v||^2 of that vector in FP64, which is below lambda_max (up
+// to its rounding) and within (vector error)^2 of it.  The GPU's FP64 rate is
+// 1/64 of its FP32 rate, so the iteration costs a few FP64 operations; the
+// quotient is as accurate as the FP32 direction allows (about 1e-13), which
+// brackets a norm but is too coarse for the 2^-40 certificate of a distance.
+// Returns 0 when E = 0, NaN when E holds a NaN.
 template <int PM>
-__device__ void gram_warp(const double (&ecol)[PM], int p, double X, bool neg, WarpScratch ws) {
+__device__ double power_lambda32_warp(const double (&e)[PM], const double (&ecol)[PM], int p, WarpScratch ws) {
     const int lane = threadIdx.x & 31;
+    const bool act = lane < p;
     const int ld = p + 1;
+    double rn = 0.0;
+#pragma unroll
+    for (int j = 0; j < PM; ++j) rn = fma(e[j], e[j], rn);
+    double best = act ? rn : -1.0;
+    int br = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, br, o);
+        if (ob > best || (ob == best && oi < br)) { best = ob; br = oi; }
+    }
+    if (best != best) return best;                  // NaN
+    if (!(best > 0.0)) return 0.0;
+    // scale 2^-x with 2^x the binade of E's largest |entry| (bits, no FP64 op)
+    long long mb = 0;
+#pragma unroll
+    for (int j = 0; j < PM; ++j) mb = max(mb, __double_as_longlong(e[j]) & 0x7fffffffffffffffLL);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    int ex = (int)(mb >> 52) - 1023;
+    ex = max(-1000, min(1000, ex));
+    const double sc = __longlong_as_double((long long)(1023 - ex) << 52);
+    float e32[PM], c32[PM];
+#pragma unroll
+    for (int j = 0; j < PM; ++j) {
+        e32[j] = (float)(e[j] * sc);
+        c32[j] = (float)(ecol[j] * sc);
+    }
+    float* v32 = reinterpret_cast<float*>(ws.v);
+    float* w32 = reinterpret_cast<float*>(ws.w);
+    float v = act ? (float)(ws.E[br * ld + lane] * sc) : 0.f;   // row br of E as the start
+    {
+        const float n0 = sqrtf(warp_sumf(v * v));
+        v = n0 > 0.f ? v / n0 : 0.f;
+    }
+    int quiet = 0;
+    for (int it = 0; it < 500 && quiet < 3; ++it) {
+        __syncwarp();
+        v32[lane] = v;
+        __syncwarp();
+        float wr = 0.f;
+        if (act) {
+#pragma unroll
+            for (int j = 0; j < PM; ++j)
+                if (j < p) wr = fmaf(e32[j], v32[j], wr);
+        }
+        w32[lane] = wr;
+        __syncwarp();
+        float uj = 0.f;
+        if (act) {
+#pragma unroll
+            for (int r = 0; r < PM; ++r)
+                if (r < p) uj = fmaf(c32[r], w32[r], uj);
+        }
+        const float nu = sqrtf(warp_sumf(uj * uj));
+        if (!(nu > 0.f)) break;
+        const float vn = act ? uj / nu : 0.f;
+        float dv = fabsf(vn - v);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dv = fmaxf(dv, __shfl_xor_sync(0xffffffffu, dv, o));
+        quiet = (dv <= 0x1p-21f) ? quiet + 1 : 0;
+        v = vn;
+    }
+    // the FP64 Rayleigh quotient of v
+    const double vd = act ? (double)v : 0.0;
+    __syncwarp();
+    ws.v[lane] = vd;
+    __syncwarp();
+    double wr = 0.0;
+    if (act) {
+#pragma unroll
+        for (int j = 0; j < PM; ++j)
+            if (j < p) wr = fma(e[j], ws.v[j], wr);
+    }
+    const double num = warp_sum(wr * wr);
+    const double den = warp_sum(vd * vd);
+    __syncwarp();
+    return den > 0.0 ? num / den : 0.0;
+}
+
+// G = E^T E (X = 0, neg false) or X I - G (neg true) into dst (row stride
+// dld) from the columns of E held in ecol[].
+template <int PM>
+__device__ void gram_warp(const double (&ecol)[PM], int p, double X, bool neg, double* dst, int dld) {
+    const int lane = threadIdx.x & 31;
     __syncwarp();
     for (int k = 0; k < p; ++k) {
         double g = 0.0;
-        for (int r = 0; r < p; ++r) g = fma(ecol[r], __shfl_sync(0xffffffffu, ecol[r], k), g);
-        if (lane < p) ws.E[lane * ld + k] = neg ? ((k == lane ? X : 0.0) - g) : g;
+#pragma unroll
+        for (int r = 0; r < PM; ++r)
+            if (r < p) g = fma(ecol[r], __shfl_sync(0xffffffffu, ecol[r], k), g);
+        if (lane < p) dst[lane * dld + k] = neg ? ((k == lane ? X : 0.0) - g) : g;
     }
     __syncwarp();
 }
@@ -1657,7 +1754,25 @@ template <int PM>
 __device__ bool lambda_below_warp(const double (&ecol)[PM], int p, double X, WarpScratch ws) {
     const int lane = threadIdx.x & 31;
     const int ld = p + 1;
-    gram_warp<PM>(ecol, p, X, true, ws);
+    gram_warp<PM>(ecol, p, X, true, ws.E, ld);
+    const double tr = warp_sum(lane < p ? ws.E[lane * ld + lane] : 0.0);
+    if (!(tr > 0.0)) return false;
+    const double c = 2.0 * gamma_u(p + 1) * tr;
+    if (lane < p) ws.E[lane * ld + lane] -= c;
+    __syncwarp();
+    const bool ok = cholesky_warp(ws.E, p, ld) == p;
+    __syncwarp();
+    return ok;
+}
+
+// lambda_below_warp with G = E^T E already formed (G: row stride p, shared).
+__device__ bool lambda_below_g_warp(const double* G, int p, double X, WarpScratch ws) {
+    const int lane = threadIdx.x & 31;
+    const int ld = p + 1;
+    __syncwarp();
+    if (lane < p)
+        for (int k = 0; k < p; ++k) ws.E[lane * ld + k] = (k == lane ? X : 0.0) - G[lane * p + k];
+    __syncwarp();
     const double tr = warp_sum(lane < p ? ws.E[lane * ld + lane] : 0.0);
     if (!(tr > 0.0)) return false;
     const double c = 2.0 * gamma_u(p + 1) * tr;
@@ -1679,31 +1794,37 @@ __device__ double exact_sigma_d_warp(const double* sD, const double* __restrict_
     double e[PM], ecol[PM];
     form_e_warp<PM>(sD, B, p, ws, e, ecol);
     const double lam = power_lambda_warp<PM>(e, ecol, p, ws);
-    if (lam == 0.0) return 0.0;
+    if (!(lam > 0.0)) return lam;                   // 0, or NaN for a NaN E
     if (lambda_below_warp<PM>(ecol, p, lam * (1.0 + 0x1p-40), ws)) return sqrt(lam);
-    gram_warp<PM>(ecol, p, 0.0, false, ws);
+    gram_warp<PM>(ecol, p, 0.0, false, ws.E, p + 1);
     const double lj = jacobi_lambda_max_warp(ws.E, p, p + 1);
     __syncwarp();
     return sqrt(fmax(lj, 0.0));
 }
 
 // Bracket [*lo, *hi] of ||A||_2 for A in the warp's shared scratch sA (row
-// stride p): lo from the power iteration's quotient (its rounding, a few p u,
-// is far inside the 2^-40 taken off), hi from the first certified
-// X = lambda (1 + 2^(2k - 40)), k = 0..30 (infinite when none is).
+// stride p; overwritten by A^T A): lo from the Rayleigh quotient of the FP32
+// power iteration (a lower bound up to its rounding, a few p u, far inside
+// the 2^-40 taken off), hi from the first X = lambda (1 + 2^-s),
+// s = 40, 36, 32, 26, 20, 12, 4, -4, -12, whose shifted Cholesky certificate
+// holds (infinite when none does).  G = A^T A is formed once for the tries.
 template <int PM>
-__device__ void norm2_bracket_warp(const double* sA, int p, WarpScratch ws, double* lo, double* hi) {
+__device__ void norm2_bracket_warp(double* sA, int p, WarpScratch ws, double* lo, double* hi) {
     double e[PM], ecol[PM];
     form_e_warp<PM>(sA, nullptr, p, ws, e, ecol);
-    const double lam = power_lambda_warp<PM>(e, ecol, p, ws);
+    const double lam = power_lambda32_warp<PM>(e, ecol, p, ws);
     *lo = 0.0;
     *hi = 0.0;
-    if (lam == 0.0) return;
+    if (lam != lam) *lo = lam;                      // NaN patch: the caller widens it to [0, inf]
+    if (!(lam > 0.0)) return;
     *lo = sqrt(lam) * (1.0 - 0x1p-40);
     *hi = __longlong_as_double(0x7ff0000000000000ll);   // +inf
-    for (int k = 0; k <= 30; ++k) {
-        const double X = lam * (1.0 + ldexp(1.0, 2 * k - 40));
-        if (lambda_below_warp<PM>(ecol, p, X, ws)) {
+    gram_warp<PM>(ecol, p, 0.0, false, sA, p);
+    const int shifts[9] = {-40, -36, -32, -26, -20, -12, -4, 4, 12};
+#pragma unroll 1
+    for (int k = 0; k < 9; ++k) {
+        const double X = lam * (1.0 + __longlong_as_double((long long)(1023 + shifts[k]) << 52));
+        if (lambda_below_g_warp(sA, p, X, ws)) {
             *hi = sqrt(X) * (1.0 + 0x1p-50);
             break;
         }
@@ -1711,10 +1832,13 @@ __device__ void norm2_bracket_warp(const double* sA, int p, WarpScratch ws, doub
 }
 
 // Brackets of ||A_i||_2 for a size group's patches, the keys of the
-// norm-window search: a warp per patch, the patch staged in its scratch.
+// norm-window search, and each patch's window (norm_window): a warp per
+// patch, the patch staged in its scratch.
 template <int PM>
 __global__ void __launch_bounds__(EVAL_THREADS) k_patch_norms(const double* __restrict__ Ag, int count, int p,
-                                                              double* __restrict__ nlo, double* __restrict__ nhi) {
+                                                              double tol, double* __restrict__ nlo,
+                                                              double* __restrict__ nhi, double* __restrict__ wlo,
+                                                              double* __restrict__ whi) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
@@ -1731,8 +1855,12 @@ __global__ void __launch_bounds__(EVAL_THREADS) k_patch_norms(const double* __re
         double lo, hi;
         norm2_bracket_warp<PM>(sA, p, ws, &lo, &hi);
         if (lane == 0) {
+            sanitize_bracket(&lo, &hi);
+            const NormWin w = norm_window(lo, hi, tol);
             nlo[i] = lo;
             nhi[i] = hi;
+            wlo[i] = w.lo;
+            whi[i] = w.hi;
         }
     }
 }
@@ -2022,9 +2150,9 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         count_launch();
         launch_sketch(Ag, Ball, count, p, skX, skDen, skY32, skF, skR, s);
         PSR_CHECK_LAUNCH(ctx, "patch sketches");
-        double* skN = nullptr;                     // [2][count] ||A_i||_2 brackets (norm window)
+        double* skN = nullptr;                     // [4][count] ||A_i||_2 brackets and windows
         if (window) {
-            PSR_CUDA(ctx, psr::dev_alloc(&skN, sizeof(double) * 2 * (size_t)count));
+            PSR_CUDA(ctx, psr::dev_alloc(&skN, sizeof(double) * 4 * (size_t)count));
             const int wpn = EVAL_THREADS / 32;
             const size_t smem_n = (size_t)wpn * ((size_t)p * (p + 1) + 64 + (size_t)p * p) * 8;
             const void* kn = (p <= 8) ? (const void*)k_patch_norms<8>
@@ -2033,14 +2161,20 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
             const int nb = std::max(1, std::min((count + wpn - 1) / wpn, 152 * 8));
             count_launch();
             if (p <= 8)
-                k_patch_norms<8><<<nb, EVAL_THREADS, smem_n, s>>>(Ag, count, p, skN, skN + count);
+                k_patch_norms<8><<<nb, EVAL_THREADS, smem_n, s>>>(Ag, count, p, tol, skN, skN + count,
+                                                                 skN + 2 * (size_t)count, skN + 3 * (size_t)count);
             else if (p <= 16)
-                k_patch_norms<16><<<nb, EVAL_THREADS, smem_n, s>>>(Ag, count, p, skN, skN + count);
+                k_patch_norms<16><<<nb, EVAL_THREADS, smem_n, s>>>(Ag, count, p, tol, skN, skN + count,
+                                                                  skN + 2 * (size_t)count, skN + 3 * (size_t)count);
             else
-                k_patch_norms<32><<<nb, EVAL_THREADS, smem_n, s>>>(Ag, count, p, skN, skN + count);
+                k_patch_norms<32><<<nb, EVAL_THREADS, smem_n, s>>>(Ag, count, p, tol, skN, skN + count,
+                                                                  skN + 2 * (size_t)count, skN + 3 * (size_t)count);
             PSR_CHECK_LAUNCH(ctx, "patch norms");
         }
-        const SketchDB sk{skX, skDen, skF, skR, skY32, skN, window ? skN + count : nullptr};
+        const SketchDB sk{skX, skDen, skF, skR, skY32, skN,
+                          window ? skN + count : nullptr,
+                          window ? skN + 2 * (size_t)count : nullptr,
+                          window ? skN + 3 * (size_t)count : nullptr};
         SketchDB skd{skX, nullptr, nullptr, nullptr, nullptr};
         double *sdDen = nullptr, *sdF = nullptr, *sdR = nullptr;
         RoundDev init{};

@@ -542,18 +542,20 @@ __global__ void __launch_bounds__(BT) k_sketch_dirs_big(const double* __restrict
     }
 }
 
-// Brackets [nlo, nhi] of ||A_i||_2 for the norm-window search (the keys of
-// criterion.cu's warp path, for p > 32): a block per patch, thread r row r of
+// Brackets [nlo, nhi] of ||A_i||_2 for the norm-window search and each
+// patch's window [wlo, whi] (the keys and windows of criterion.cu's warp path,
+// for p > 32): a block per patch, thread r row r of
 // A in shared memory.  Power iteration on G = A^T A from A's largest row
 // until the Rayleigh quotient lambda stalls (three steps gaining < 2^-50, at
 // most 300); nlo = sqrt(lambda)(1 - 2^-40), nhi from the first
-// X = lambda (1 + 2^(2k - 40)), k = 0..30, for which the Cholesky
+// X = lambda (1 + 2^-s), s = 40, 36, 32, 26, 20, 12, 4, -4, -12, for which the Cholesky
 // factorisation of X I - G - c I (c = 2 gamma_{p+1} tr, its backward error)
 // runs to completion, proving lambda_max(G) < X (infinite when none does).
 // scratch: 2 p^2 doubles per block (G, then the factorised copy).
 __global__ void __launch_bounds__(BT) k_patch_norms_big(const double* __restrict__ Ag, int count, int p,
-                                                        double* __restrict__ nlo, double* __restrict__ nhi,
-                                                        double* __restrict__ scratch) {
+                                                        double tol, double* __restrict__ nlo,
+                                                        double* __restrict__ nhi, double* __restrict__ wlo,
+                                                        double* __restrict__ whi, double* __restrict__ scratch) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int ld = p + 1;
     double* E = reinterpret_cast<double*>(smem);
@@ -608,8 +610,10 @@ __global__ void __launch_bounds__(BT) k_patch_norms_big(const double* __restrict
                 }
             lo = sqrt(lam) * (1.0 - 0x1p-40);
             hi = __longlong_as_double(0x7ff0000000000000ll);
-            for (int k = 0; k <= 30; ++k) {
-                const double X = lam * (1.0 + ldexp(1.0, 2 * k - 40));
+            const int shifts[9] = {-40, -36, -32, -26, -20, -12, -4, 4, 12};
+#pragma unroll 1
+            for (int k = 0; k < 9; ++k) {
+                const double X = lam * (1.0 + __longlong_as_double((long long)(1023 + shifts[k]) << 52));
                 __syncthreads();
                 if (act)
                     for (int q = 0; q < p; ++q) Hs[q * p + r] = (q == r ? X : 0.0) - Gs[q * p + r];
@@ -624,8 +628,12 @@ __global__ void __launch_bounds__(BT) k_patch_norms_big(const double* __restrict
             }
         }
         if (r == 0) {
+            sanitize_bracket(&lo, &hi);
+            const NormWin w = norm_window(lo, hi, tol);
             nlo[i] = lo;
             nhi[i] = hi;
+            wlo[i] = w.lo;
+            whi[i] = w.hi;
         }
     }
 }
@@ -667,7 +675,9 @@ __global__ void __launch_bounds__(256) k_round_screen_big(RoundBig* st, const in
                                                           const double* __restrict__ rho, double tol,
                                                           int32_t* __restrict__ surv_list,
                                                           const double* __restrict__ nlo,
-                                                          const double* __restrict__ nhi) {
+                                                          const double* __restrict__ nhi,
+                                                          const double* __restrict__ wlo,
+                                                          const double* __restrict__ whi) {
     __shared__ float sy[SKB * SKD];
     __shared__ double sden[SKB];
     if (st->done) return;
@@ -686,7 +696,7 @@ __global__ void __launch_bounds__(256) k_round_screen_big(RoundBig* st, const in
     int my_min = count;
     for (int c = i0 + 1 + gw; c < count; c += nw) {
         if (phi[c] != -1) continue;                 // warp-uniform
-        if (nlo && outside_window(norm_window(nlo[c], nhi[c], tol), nlo[i0], nhi[i0])) {
+        if (nlo && outside_window(NormWin{wlo[c], whi[c]}, nlo[i0], nhi[i0])) {
             my_min = min(my_min, c);                // outside the norm window: not a test
             continue;
         }
@@ -889,14 +899,16 @@ int run_alg1_big(psr_ctx* ctx, Group& G, const double* Ag, cudaStream_t s, int64
         // ||A_i||_2 brackets of the norm-window search (scratch reused: the
         // decide blocks outnumber these)
         const int nb = std::max(1, std::min(count, decide_blocks));
-        BIG_CK(psr::dev_alloc(&nrm, sizeof(double) * 2 * (size_t)count));
+        BIG_CK(psr::dev_alloc(&nrm, sizeof(double) * 4 * (size_t)count));
         if ((rc = set_big_smem((const void*)k_patch_norms_big, norms_big_smem(p))) != PSR_OK) {
             cleanup();
             psr::dev_free(phi_l);
             return rc;
         }
         count_launch();
-        k_patch_norms_big<<<nb, BT, norms_big_smem(p), s>>>(Ag, count, p, nrm, nrm + count, scratch);
+        k_patch_norms_big<<<nb, BT, norms_big_smem(p), s>>>(Ag, count, p, tol, nrm, nrm + count,
+                                                            nrm + 2 * (size_t)count, nrm + 3 * (size_t)count,
+                                                            scratch);
         BIG_CK(cudaGetLastError());
     }
     RoundBig init{};
@@ -909,8 +921,9 @@ int run_alg1_big(psr_ctx* ctx, Group& G, const double* Ag, cudaStream_t s, int64
     for (;;) {
         for (int q = 0; q < batch; ++q) {
             count_launch();
-            k_round_screen_big<<<screen_blocks, 256, 0, s>>>(st, phi_l, count, p, Y32, den, fa, rho, tol, surv, nrm,
-                                                             window ? nrm + count : nullptr);
+            k_round_screen_big<<<screen_blocks, 256, 0, s>>>(
+                st, phi_l, count, p, Y32, den, fa, rho, tol, surv, nrm, window ? nrm + count : nullptr,
+                window ? nrm + 2 * (size_t)count : nullptr, window ? nrm + 3 * (size_t)count : nullptr);
             count_launch();
             k_round_decide_big<<<decide_blocks, BT, big_smem(p), s>>>(st, phi_l, count, Ag, p, Ball, fro_all, w_all,
                                                                      sing_all, tol, surv, rep_l, scratch);

@@ -78,6 +78,9 @@ __device__ __forceinline__ int warp_sum_i(int v) {
 // by 1e-12 (relative) against rounding.  With ||A_i|| known as a bracket
 // [alo, ahi], the window spans every value in it; an entry whose own bracket
 // [klo, khi] lies wholly outside is skipped: neither tested nor counted.
+// The window is computed once per patch; the per-pair test compares the bit
+// patterns of the (non-negative, non-NaN) bounds as integers, which order
+// like the values and keep the test off the GPU's narrow FP64 pipe.
 struct NormWin {
     double lo, hi;
 };
@@ -89,7 +92,16 @@ __device__ __forceinline__ NormWin norm_window(double alo, double ahi, double to
     return w;
 }
 __device__ __forceinline__ bool outside_window(const NormWin& w, double klo, double khi) {
-    return khi < w.lo || klo > w.hi;
+    return __double_as_longlong(khi) < __double_as_longlong(w.lo) ||
+           __double_as_longlong(klo) > __double_as_longlong(w.hi);
+}
+// A bracket [lo, hi] of a 2-norm made safe for outside_window: a NaN bound
+// (a non-finite patch) becomes the bracket [0, inf], never outside.
+__device__ __forceinline__ void sanitize_bracket(double* lo, double* hi) {
+    if (!(*lo >= 0.0) || !(*hi >= 0.0)) {
+        *lo = 0.0;
+        *hi = __longlong_as_double(0x7ff0000000000000ll);
+    }
 }
 
 // Device-side status word bits (written by kernels, read by the host).
