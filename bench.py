@@ -69,7 +69,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 KT_KERNEL_NAMES = {"sweep": "patch sweep (k_sweep_stream for full-storage groups / k_sweep_* tiles)",
                    "spmv": "k_spmv_sell (SELL SpMV, FP64)",
                    "mdot": "k_arnoldi (fused FGMRES Gram-Schmidt step on FP32 pairs) / k_mdot",
-                   "maxpy": "k_maxpy (FGMRES w -= V h)", "vec": "vector kernels (k_fg_scale / CG updates)"}
+                   "maxpy": "k_maxpy (FGMRES w -= V h)", "vec": "vector kernels (k_fg_scale / CG updates)",
+                   "inverse": "k_batched_inverse_block / k_batched_inverse (setup: Gauss-Jordan, FP64)"}
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one
 # ncu capture) over the algorithmic bytes of that launch, for (config,
@@ -84,6 +85,9 @@ TRAFFIC = {
     ("stokes3d", "spmv"): {"ratio": (808.000256e6 + 6.935552e6) / 788402076.0,
                            "capture": "k_spmv_sell (length-sorted slices), 3D Stokes 24^3: 814.94 MB DRAM for "
                                       "788.40 MB algorithmic"},
+    ("stokes3d", "inverse"): {"ratio": (679.388928e6 + 619.044864e6) / (10648 * 89 * 89 * 16.0),
+                              "capture": "k_batched_inverse_block (the 10,648 patches of 89 DOFs), 3D Stokes 24^3: "
+                                         "1298.43 MB DRAM for 1349.48 MB algorithmic"},
 }
 
 
@@ -263,7 +267,8 @@ def _roofline_of(name, kd, hbm, peak_source, config):
     if kd["frac_fp64"] > kd["frac"]:
         bound = {"bound": "alu", "achieved": kd["achieved_fp64_tflops"], "peak": FP64_PEAK_TFLOPS,
                  "unit": "TFLOP/s (FP64)", "frac": kd["frac_fp64"],
-                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clock x 2 flops x 2070 MHz"}
+                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clock x 2 flops x 2070 MHz (a kernel of "
+                                "independent FMA chains measured 628 G FMA/s, the same)"}
     else:
         bound = {"bound": "hbm", "achieved": kd["achieved_gbs"], "peak": hbm, "unit": "GB/s", "frac": kd["frac"],
                  "peak_source": peak_source}
@@ -272,7 +277,7 @@ def _roofline_of(name, kd, hbm, peak_source, config):
                 traffic=None if tr is None else tr["ratio"] * kd["alg_bytes_per_launch"],
                 traffic_source=None if tr is None else tr["capture"] + " (ratio applied to this launch)",
                 alg_bytes_per_launch=kd["alg_bytes_per_launch"], launch_us=kd["us_per_launch"],
-                share_of_iteration_kernels=kd["share"])
+                share_of_timed_kernels=kd["share"])
 
 
 def _variant(L, dev_in, pr, cfg, b, devc, reps, tol, prec, arith, maxit, r_ref=None, z_ref=None, solve=True):
@@ -550,11 +555,25 @@ def run_gpu(args, cfg, ws, rank, local):
             a[1] += cnt
             a[2] += by
             a[3] += fl
+    # the setup's batched inverses: GPU time from the CUDA events the library
+    # records around their launches (stats t_invert); 2 p^3 flops and 16 p^2
+    # bytes (the patch in, the inverse out) per patch, one launch per size group
+    inv_ms = 1e3 * sum(s_["t_invert"] for s_ in stats)
+    if inv_ms > 0:
+        ps = pr.patch_sizes.astype(np.float64)
+        kt_sum["inverse"] = [inv_ms, st["n_groups"] * len(stats), 16.0 * float((ps ** 2).sum()) * len(stats),
+                             2.0 * float((ps ** 3).sum()) * len(stats)]
     kernels = _kernels_from_timing({k: tuple(v) for k, v in kt_sum.items()}, hbm)
     top = max(kernels, key=lambda k: kernels[k]["ms"])
     roofline = _roofline_of(top, kernels[top], hbm, peak_source, args.config)
-    roofline["timing"] = "CUDA events the library records on the solve stream around each launch, timed steps"
+    roofline["timing"] = ("CUDA events the library records around the batched-inverse launches of each setup, "
+                          "timed steps" if top == "inverse" else
+                          "CUDA events the library records on the solve stream around each launch, timed steps")
     roofline["kernels"] = kernels
+    solve_names = [k for k in kernels if k != "inverse"]
+    solve_top = max(solve_names, key=lambda k: kernels[k]["ms"])
+    solve_roof = _roofline_of(solve_top, kernels[solve_top], hbm, peak_source, args.config)
+    solve_roof["timing"] = "CUDA events the library records on the solve stream around each launch, timed steps"
     sweep_roof = _roofline_of("sweep", kernels["sweep"], hbm, peak_source, args.config)
     # the sweep alone: median of back-to-back applies (larger-than-L2 inputs)
     r_ref = torch.randn(pr.n, dtype=torch.float64, device=devc, generator=torch.Generator(device=devc).manual_seed(7))
@@ -588,7 +607,8 @@ def run_gpu(args, cfg, ws, rank, local):
         "m_p": st["m_p"], "retained_fraction": st["m_p"] / pr.n_patches, "factor_bytes": st["factor_bytes"],
         "criterion_evals": st["criterion_evals"],
         "step_dof_per_s": pr.n * sweeps / sum(times),
-        "roofline": roofline, "sweep_roofline": sweep_roof, "clocks": clocks, "gpu_launches": launches,
+        "roofline": roofline, "solve_roofline": solve_roof, "sweep_roofline": sweep_roof, "clocks": clocks,
+        "gpu_launches": launches,
     }
     if not args.no_extras:
         # the same setup with other storage / arithmetic: rate, error against

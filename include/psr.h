@@ -298,7 +298,10 @@ typedef struct {
     int64_t mlp_hits;             /* patches whose predicted entry verified      */
     int64_t factor_bytes;         /* bytes of stored inverses                   */
     int64_t index_bytes;          /* bytes of phi + maps used by the sweep      */
-    double  t_extract, t_rounds, t_invert, t_convert, t_autotune; /* setup seconds */
+    double  t_extract, t_rounds, t_invert, t_convert, t_autotune; /* setup seconds; t_invert:
+                                     GPU time (CUDA events) of the batched inverses,
+                                     every patch's at tol 0 and before Alg. 1 (part
+                                     of t_rounds)                                  */
     int32_t first_singular;       /* patch index or -1                          */
     int32_t rounds;               /* Alg. 1 rounds: passes of the round kernels
                                      (one makes up to 64 entries for patches of

@@ -262,6 +262,7 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
             // FP64 pairs, p > 32: the inverses go straight into the streamed
             // sweep's layout (the sweep layout finds the group streamed)
             const bool fused = op.store_prec == PSR_PREC_FP64 && op.fp64_arith == PSR_FP64_PAIRS;
+            GpuSpan span;                          // the inverses' GPU time (stats.t_invert)
             for (auto& G : ctx->groups) {
                 double* base = ctx->A_ext + G.mat_off;
                 if (fused && G.p > 32) {
@@ -275,12 +276,16 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
                         FAIL(PSR_ERR_OOM);
                     }
                     CK(psr::dev_alloc(&G.bexp, sizeof(int32_t) * (size_t)std::max(G.count, 1)));
+                    span.begin(s);
                     rc = launch_batched_inverse_pairs(base, G.count, G.p, dst, G.bexp, sing, s);
+                    span.end(s);
                     G.stream = true;
                     G.rinv = dst;
                 } else {
+                    span.begin(s);
                     rc = launch_batched_inverse(base, (int64_t)G.p * G.p, nullptr, G.count, G.p, base,
                                                 (int64_t)G.p * G.p, sing, s);
+                    span.end(s);
                     G.rinv = base;
                 }
                 if (rc != PSR_OK) { psr::dev_free(sing); psr::dev_free(first); goto fail; }
@@ -290,6 +295,7 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
                 int32_t h_first = 0;
                 CK(cudaMemcpyAsync(&h_first, first, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
                 CK(cudaStreamSynchronize(s));
+                ctx->stats.t_invert += span.seconds();
                 G.m = G.count;
                 CK(psr::dev_alloc(&G.sphi, sizeof(int32_t) * (size_t)G.count));
                 count_launch(); k_iota<<<std::max(1, std::min(G.count / 256 + 1, 1024)), 256, 0, s>>>(G.sphi, G.count);

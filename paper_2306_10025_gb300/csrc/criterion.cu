@@ -2130,7 +2130,10 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         PSR_CUDA(ctx, cudaMemsetAsync(phi_l, 0xff, sizeof(int32_t) * count, s));
         // every patch's inverse, norm, probes and sketch, batched (any patch
         // may become an entry)
+        GpuSpan span;                              // the inverses' GPU time (stats.t_invert)
+        span.begin(s);
         rc = launch_batched_inverse(Ag, (int64_t)p * p, nullptr, count, p, Ball, (int64_t)p * p, sing_all, s);
+        span.end(s);
         if (rc != PSR_OK) break;
         count_launch();
         k_entry_fro<<<(count + 7) / 8, 256, 0, s>>>(Ag, Ball, count, p, fro_all, w_all, sing_all, nullptr);
@@ -2478,6 +2481,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
             k_gather_db<<<gb, 256, 0, s>>>(db.A, m0, Ag, rep_l, G.m, p, G.dbA);
         }
         PSR_CUDA(ctx, cudaStreamSynchronize(s));
+        ctx->stats.t_invert += span.seconds();
         G.h_rep.assign(hrep.begin(), hrep.end());   // local patch of each entry, -1 for seed entries
         G.sphi = phi_l;             // local phi in original (unsorted) order
         G.rinv = Bdb;               // FP64 database, converted in the sweep builder

@@ -876,7 +876,10 @@ int run_alg1_big(psr_ctx* ctx, Group& G, const double* Ag, cudaStream_t s, int64
     BIG_CK(psr::dev_alloc(&st, sizeof(RoundBig)));
     BIG_CK(psr::host_alloc(&h_st, sizeof(RoundBig)));
     BIG_CK(cudaMemsetAsync(phi_l, 0xff, sizeof(int32_t) * count, s));
+    GpuSpan span;                                  // the inverses' GPU time (stats.t_invert)
+    span.begin(s);
     rc = launch_batched_inverse(Ag, pp, nullptr, count, p, Ball, pp, sing_all, s);
+    span.end(s);
     if (rc != PSR_OK) { cleanup(); psr::dev_free(phi_l); return rc; }
     const size_t esm = entry_smem(p);
     if ((rc = set_big_smem((const void*)k_entry_big, esm)) != PSR_OK ||
@@ -918,6 +921,7 @@ int run_alg1_big(psr_ctx* ctx, Group& G, const double* Ag, cudaStream_t s, int64
     BIG_CK(cudaMemcpyAsync(st, &init, sizeof(RoundBig), cudaMemcpyHostToDevice, s));
     const int screen_blocks = std::max(1, std::min((count + 7) / 8, 152 * 4));
     int batch = 4, issued = 0;
+    bool inv_read = false;
     for (;;) {
         for (int q = 0; q < batch; ++q) {
             count_launch();
@@ -935,6 +939,10 @@ int run_alg1_big(psr_ctx* ctx, Group& G, const double* Ag, cudaStream_t s, int64
         issued += batch;
         BIG_CK(cudaMemcpyAsync(h_st, st, sizeof(RoundBig), cudaMemcpyDeviceToHost, s));
         BIG_CK(cudaStreamSynchronize(s));
+        if (!inv_read) {                           // the first synchronisation after the inverses
+            ctx->stats.t_invert += span.seconds();
+            inv_read = true;
+        }
         if (h_st->done) break;
         if (issued > count + 8) { set_error(ctx, "Alg. 1 rounds did not terminate"); rc = PSR_ERR_TIMEOUT; break; }
         if (batch < 256) batch *= 2;

@@ -35,6 +35,31 @@ void set_capturing(bool on);
         if (e_ != cudaSuccess) return psr::cuda_fail((ctx), e_, what); \
     } while (0)
 
+// GPU time of a launch sequence on one stream (two CUDA events): begin() and
+// end() around the launches, seconds() once the stream has been synchronised.
+struct GpuSpan {
+    cudaEvent_t a = nullptr, b = nullptr;
+    GpuSpan() {
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) cudaGetLastError();
+    }
+    ~GpuSpan() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+    GpuSpan(const GpuSpan&) = delete;
+    GpuSpan& operator=(const GpuSpan&) = delete;
+    void begin(cudaStream_t s) { if (a) cudaEventRecord(a, s); }
+    void end(cudaStream_t s) { if (b) cudaEventRecord(b, s); }
+    double seconds() const {
+        float ms = 0.f;
+        if (!a || !b || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+            cudaGetLastError();
+            return 0.0;
+        }
+        return ms * 1e-3;
+    }
+};
+
 // Device and pinned host memory of the library go through a caching
 // allocator (memory.cu): freed blocks are kept and handed out again, after a
 // device synchronisation when they were freed since the last one.
