@@ -370,10 +370,16 @@ int psr_release_cached_memory(void);
  *     block more than the grid holds and give up after s spins (about
  *     s x 32 ns); every block then leaves the kernel and the setup returns
  *     PSR_ERR_TIMEOUT.  0 restores the normal barrier (limit 2^24 spins).
+ *   PSR_INJECT_ROUNDS_SPLIT, value 1: the Alg. 1 rounds for patches of at
+ *     most 32 DOFs take the path used where a cooperative launch is not
+ *     available or the pair lists do not fit (one entry per round, a screen
+ *     and a decide launch each); 0 restores the cooperative multi-entry
+ *     kernel.  Host state; the results are the same.
  * Returns PSR_OK, PSR_ERR_INVALID_ARG (unknown kind, negative value) or
  * PSR_ERR_CUDA (PSR_INJECT_BARRIER_WAIT without a device). */
 #define PSR_INJECT_ALLOC_FAIL   1
 #define PSR_INJECT_BARRIER_WAIT 2
+#define PSR_INJECT_ROUNDS_SPLIT 3
 int psr_debug_inject(int32_t what, int64_t value);
 
 /* Instrumentation: number of CUDA kernels this library has launched in the

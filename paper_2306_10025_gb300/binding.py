@@ -592,12 +592,14 @@ def exported_symbols(path: str = LIB_PATH) -> list[str]:
     return found
 
 
-INJECT = {"alloc_fail": 1, "barrier_wait": 2}
+INJECT = {"alloc_fail": 1, "barrier_wait": 2, "rounds_split": 3}
 
 
 def psr_debug_inject(what: str, value: int) -> None:
     """Fault injection for tests (psr_debug_inject): "alloc_fail" makes the
     value-th next device allocation fail (0 disables); "barrier_wait" makes the
     Alg. 1 rounds barriers wait for a block that never arrives, giving up
-    after value spins (0 restores)."""
+    after value spins (0 restores); "rounds_split" (1 / 0) sends the Alg. 1
+    rounds of patches of at most 32 DOFs down the one-entry-per-round path
+    taken without a cooperative launch."""
     _check(load().psr_debug_inject(INJECT[what], int(value)))

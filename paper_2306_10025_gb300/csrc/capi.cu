@@ -771,6 +771,10 @@ int psr_debug_inject(int32_t what, int64_t value) {
         }
         return inject_barrier_wait((long long)value);
     }
+    if (what == PSR_INJECT_ROUNDS_SPLIT) {
+        inject_rounds_split(value != 0);
+        return PSR_OK;
+    }
     set_error(nullptr, "psr_debug_inject: unknown kind");
     return PSR_ERR_INVALID_ARG;
 }

@@ -28,6 +28,7 @@
 // batched pass over the unassigned patches, with no host decision in it.
 #include "psr_internal.cuh"
 #include "dense.cuh"
+#include <atomic>
 
 namespace psr {
 
@@ -2035,6 +2036,9 @@ __global__ void k_round_f32(const double* __restrict__ src, int64_t n, float* __
         dst[e] = (float)src[e];
 }
 
+static std::atomic<bool> g_rounds_split{false};
+void inject_rounds_split(bool on) { g_rounds_split.store(on); }
+
 int inject_barrier_wait(long long spins) {
     const unsigned int extra = spins > 0 ? 1u : 0u;
     const long long limit = spins > 0 ? spins : (1ll << 24);
@@ -2268,6 +2272,7 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         {
             int coop = 0;
             cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
+            if (g_rounds_split.load()) coop = 0;
             const void* kf = (p <= 8) ? (const void*)k_rounds_multi<8>
                            : (p <= 16) ? (const void*)k_rounds_multi<16> : (const void*)k_rounds_multi<32>;
             const size_t smem_multi = (size_t)wpb * (2 * (size_t)p * p + 64) * 8;

@@ -69,6 +69,7 @@ cudaError_t host_alloc(void** p, size_t bytes);
 cudaError_t host_free(void* p);
 void inject_alloc_fail(long long k);      // psr_debug_inject(PSR_INJECT_ALLOC_FAIL, k)
 int inject_barrier_wait(long long spins); // criterion.cu
+void inject_rounds_split(bool on);        // criterion.cu: psr_debug_inject(PSR_INJECT_ROUNDS_SPLIT, 1)
 template <class T>
 inline cudaError_t dev_alloc(T** p, size_t bytes) { return dev_alloc(reinterpret_cast<void**>(p), bytes); }
 template <class T>

@@ -310,3 +310,31 @@ def test_norm_window_search_bench_size(lib, N):
     ev0 = ctx.stats()["criterion_evals"]
     ctx.destroy()
     assert ev < ev0
+
+
+@pytest.mark.parametrize("search", ["creation", "norm_window"])
+def test_split_rounds_path_bit_exact(lib, search):
+    """The path the Alg. 1 rounds take without a cooperative launch (one
+    entry per round, a screen and a decide launch each), forced by the
+    rounds_split injection: phi, the entries and the evaluation count of the
+    oracle (alg1, or alg1_sorted for the norm window), one round per entry."""
+    cases = [("diff3d_b", P.diffusion3d_q2(4, sigma=1.0, corr_len=2.0, seed=2), 0.3),
+             ("stokes", P.stokes2d_q2q1(8, 1.05), 5.0),
+             ("poisson", P.poisson2d_q2(8), 1e-12)]
+    lib.psr_debug_inject("rounds_split", 1)
+    try:
+        for name, pr, tol in cases:
+            A = O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n, pr.dofs2d())
+            ref = O.alg1_sorted(A, tol) if search == "norm_window" else O.alg1(A, tol)
+            if search == "norm_window":
+                assert _window_clear(A, tol, ref["reps"])
+            ctx = ctx_for(lib, pr, tol=tol, weighting=pr.weighting, krylov=pr.krylov, search=search)
+            phi, reps, m = ctx.assignment()
+            st = ctx.stats()
+            assert np.array_equal(reps.cpu().numpy(), ref["reps"]), name
+            assert np.array_equal(phi.cpu().numpy(), ref["phi"]), name
+            assert st["criterion_evals"] == ref["evals"], name
+            assert st["rounds"] == m, name
+            ctx.destroy()
+    finally:
+        lib.psr_debug_inject("rounds_split", 0)
