@@ -369,7 +369,7 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
                 ctx->A_ext_len = 0;
             }
         }
-        rc = krylov_alloc(ctx);
+        rc = krylov_alloc(ctx, s);
         if (rc != PSR_OK) goto fail;
         phase_begin("psr_setup: sweep autotuner");
         t0 = std::chrono::steady_clock::now();

@@ -1553,7 +1553,7 @@ static int kt_collect(psr_ctx* ctx, int done, const int32_t* rflag) {
         if (rk_ != PSR_OK) return rk_;                             \
     } while (0)
 
-int krylov_alloc(psr_ctx* ctx) {
+int krylov_alloc(psr_ctx* ctx, cudaStream_t s) {
     KrylovWS& w = ctx->ws;
     const size_t n = (size_t)ctx->n;
     int m = ctx->opts.restart;
@@ -1578,9 +1578,10 @@ int krylov_alloc(psr_ctx* ctx) {
         int32_t* widths = nullptr;
         PSR_CUDA(ctx, psr::dev_alloc(&widths, sizeof(int32_t) * (size_t)w.nslices));
         count_launch();
-        k_sell_width<<<(w.nslices + 7) / 8, 256>>>(ctx->rowptr, ctx->n, w.nslices, widths);
+        k_sell_width<<<(w.nslices + 7) / 8, 256, 0, s>>>(ctx->rowptr, ctx->n, w.nslices, widths);
         std::vector<int32_t> hw((size_t)w.nslices);
-        PSR_CUDA(ctx, cudaMemcpy(hw.data(), widths, sizeof(int32_t) * hw.size(), cudaMemcpyDeviceToHost));
+        PSR_CUDA(ctx, cudaMemcpyAsync(hw.data(), widths, sizeof(int32_t) * hw.size(), cudaMemcpyDeviceToHost, s));
+        PSR_CUDA(ctx, cudaStreamSynchronize(s));
         psr::dev_free(widths);
         int64_t natural = 0;
         for (int q = 0; q < w.nslices; ++q) natural += 32 * (int64_t)hw[q];
@@ -1590,44 +1591,45 @@ int krylov_alloc(psr_ctx* ctx) {
         const bool sorted = ctx->nnz > 0 && (double)natural > 1.15 * (double)ctx->nnz && ctx->n >= 4 * SELL_SIGMA;
         if (sorted) {
             PSR_CUDA(ctx, psr::dev_alloc(&w.sell_row, sizeof(int32_t) * (size_t)w.nslices * 32));
-            PSR_CUDA(ctx, cudaMemset(w.sell_row, 0xff, sizeof(int32_t) * (size_t)w.nslices * 32));
+            PSR_CUDA(ctx, cudaMemsetAsync(w.sell_row, 0xff, sizeof(int32_t) * (size_t)w.nslices * 32, s));
             count_launch();
-            k_sell_sort_windows<<<(ctx->n + SELL_SIGMA - 1) / SELL_SIGMA, SELL_SIGMA>>>(ctx->rowptr, ctx->n, w.sell_row);
+            k_sell_sort_windows<<<(ctx->n + SELL_SIGMA - 1) / SELL_SIGMA, SELL_SIGMA, 0, s>>>(ctx->rowptr, ctx->n, w.sell_row);
             int32_t* widths2 = nullptr;
             PSR_CUDA(ctx, psr::dev_alloc(&widths2, sizeof(int32_t) * (size_t)w.nslices));
             count_launch();
-            k_sell_width_map<<<(w.nslices + 7) / 8, 256>>>(ctx->rowptr, w.sell_row, w.nslices, widths2);
+            k_sell_width_map<<<(w.nslices + 7) / 8, 256, 0, s>>>(ctx->rowptr, w.sell_row, w.nslices, widths2);
             PSR_CHECK_LAUNCH(ctx, "SELL row map");
-            PSR_CUDA(ctx, cudaMemcpy(hw.data(), widths2, sizeof(int32_t) * hw.size(), cudaMemcpyDeviceToHost));
+            PSR_CUDA(ctx, cudaMemcpyAsync(hw.data(), widths2, sizeof(int32_t) * hw.size(), cudaMemcpyDeviceToHost, s));
+            PSR_CUDA(ctx, cudaStreamSynchronize(s));
             psr::dev_free(widths2);
         }
         std::vector<int64_t> hp((size_t)w.nslices + 1, 0);
         for (int q = 0; q < w.nslices; ++q) hp[q + 1] = hp[q] + 32 * (int64_t)hw[q];
         const int64_t total = std::max<int64_t>(hp.back(), 1);
         PSR_CUDA(ctx, psr::dev_alloc(&w.sell_ptr, sizeof(int64_t) * hp.size()));
-        PSR_CUDA(ctx, cudaMemcpy(w.sell_ptr, hp.data(), sizeof(int64_t) * hp.size(), cudaMemcpyHostToDevice));
+        PSR_CUDA(ctx, cudaMemcpyAsync(w.sell_ptr, hp.data(), sizeof(int64_t) * hp.size(), cudaMemcpyHostToDevice, s));
         PSR_CUDA(ctx, psr::dev_alloc(&w.sell_cols, sizeof(int32_t) * (size_t)total));
         PSR_CUDA(ctx, psr::dev_alloc(&w.sell_vals, sizeof(double) * (size_t)total));
         count_launch();
         if (!sorted) {
-            k_sell_fill<<<(w.nslices * 32 + 255) / 256, 256>>>(ctx->rowptr, ctx->colidx, ctx->vals, ctx->n, w.nslices,
+            k_sell_fill<<<(w.nslices * 32 + 255) / 256, 256, 0, s>>>(ctx->rowptr, ctx->colidx, ctx->vals, ctx->n, w.nslices,
                                                                 w.sell_ptr, w.sell_cols, w.sell_vals);
         } else {
-            k_sell_fill_map<<<(w.nslices * 32 + 255) / 256, 256>>>(ctx->rowptr, ctx->colidx, ctx->vals, w.sell_row,
+            k_sell_fill_map<<<(w.nslices * 32 + 255) / 256, 256, 0, s>>>(ctx->rowptr, ctx->colidx, ctx->vals, w.sell_row,
                                                                     w.nslices, w.sell_ptr, w.sell_cols, w.sell_vals);
         }
         PSR_CHECK_LAUNCH(ctx, "SELL build");
-        PSR_CUDA(ctx, cudaDeviceSynchronize());
+        PSR_CUDA(ctx, cudaStreamSynchronize(s));   // hp (host) is read by the copy above
     }
     w.nspmv = 152 * 16;                     // partial slots available to the SpMV reductions
     PSR_CUDA(ctx, cudaDeviceGetAttribute(&w.sms, cudaDevAttrMultiProcessorCount, ctx->device));
     PSR_CUDA(ctx, psr::dev_alloc(&w.partial, (size_t)std::max(w.nblk * 34, w.nspmv) * 8));
     PSR_CUDA(ctx, psr::dev_alloc(&w.scal, (size_t)scal_count(m) * 8));
-    PSR_CUDA(ctx, cudaMemset(w.scal, 0, (size_t)scal_count(m) * 8));
+    PSR_CUDA(ctx, cudaMemsetAsync(w.scal, 0, (size_t)scal_count(m) * 8, s));
     PSR_CUDA(ctx, psr::dev_alloc(&w.hist, (size_t)(ctx->opts.maxit + 2) * 8));
     PSR_CUDA(ctx, psr::dev_alloc(&w.ictl, 32 * sizeof(int32_t)));
     PSR_CUDA(ctx, psr::dev_alloc(&w.rflag, 64 * sizeof(int32_t)));
-    PSR_CUDA(ctx, cudaMemset(w.rflag, 0, 64 * sizeof(int32_t)));
+    PSR_CUDA(ctx, cudaMemsetAsync(w.rflag, 0, 64 * sizeof(int32_t), s));
     // fused Arnoldi step: cooperative launches of one block per SM
     int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
@@ -1643,8 +1645,9 @@ int krylov_alloc(psr_ctx* ctx) {
     if (w.coop) PSR_CUDA(ctx, psr::dev_alloc(&w.Vs, (size_t)(m + 1) * n * sizeof(float2)));
     PSR_CUDA(ctx, psr::dev_alloc(&w.part_arn, (size_t)4 * 33 * w.sms * sizeof(double)));
     PSR_CUDA(ctx, psr::dev_alloc(&w.bar, 2 * sizeof(unsigned int)));
-    PSR_CUDA(ctx, cudaMemset(w.bar, 0, 2 * sizeof(unsigned int)));
-    PSR_CUDA(ctx, cudaMemset(w.ictl, 0, 32 * sizeof(int32_t)));
+    PSR_CUDA(ctx, cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned int), s));
+    PSR_CUDA(ctx, cudaMemsetAsync(w.ictl, 0, 32 * sizeof(int32_t), s));
+    PSR_CUDA(ctx, cudaStreamSynchronize(s));
     return PSR_OK;
 }
 

@@ -236,6 +236,7 @@ static int ensure_cap(psr_mlp* net, int Bn) {
         return PSR_ERR_OOM;
     }
     cudaMemset(net->cnt, 0, 4);
+    cudaDeviceSynchronize();               // the zero is in place before any stream's kernel reads it
     net->cap = Bn;
     return PSR_OK;
 }
@@ -308,6 +309,7 @@ int psr_mlp_create(int32_t in_dim, int32_t hidden, int32_t classes, psr_mlp** ou
         return PSR_ERR_OOM;
     }
     cudaMemset(net->tc_err, 0, sizeof(int32_t));
+    cudaDeviceSynchronize();               // the zeros are in place before any stream's kernel reads them
     int rc = gemm_tc_prepare();
     if (rc != PSR_OK) { psr_mlp_destroy(net); return rc; }
     *out = net;

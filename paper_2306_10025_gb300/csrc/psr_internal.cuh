@@ -358,7 +358,7 @@ int run_kmeans(psr_ctx* ctx, cudaStream_t s, int m, const std::vector<int32_t>& 
                const std::vector<int32_t>* cls);
 
 // krylov.cu
-int krylov_alloc(psr_ctx* ctx);
+int krylov_alloc(psr_ctx* ctx, cudaStream_t s);
 int krylov_solve(psr_ctx* ctx, const double* b, double* x, cudaStream_t s, psr_solve_info* info);
 void krylov_free(psr_ctx* ctx);
 int kernel_timing_enable(psr_ctx* ctx, bool on);
