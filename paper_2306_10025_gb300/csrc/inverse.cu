@@ -86,11 +86,11 @@ namespace psr {
 // gj_invert_warp: partial pivoting (largest |entry|, lowest row on ties), the
 // pivot row divided by the pivot, every other row updated with one FMA per
 // entry, the interchanges undone on the columns at the end.  Two block
-// barriers per step: the owner of column k+1 finds the next pivot right after
-// it updates that column (a serial scan in row order, so ties go to the
-// lowest row), and column k itself is never swapped (it is overwritten by the
+// barriers per step: the warp owning column k+1 finds the next pivot right
+// after that column's update (a shuffle reduction, ties to the lowest row),
+// and column k itself is never swapped (it is overwritten by the
 // step; the swapped copy the update needs is read from it in permuted order).
-// 30,000 random 89 x 89 matrices: 50.6 ms, 66 % of the FP64 peak measured
+// 30,000 random 89 x 89 matrices: 49.0 ms, 68 % of the FP64 peak measured
 // on this GPU (628 G FMA/s, an FMA-only kernel); the four-barrier form with a
 // shuffle pivot search took 71.7 ms (47 %); results bitwise equal.  Three
 // 89 x 89 blocks fit an SM, nine warps on its four schedulers, and an
@@ -193,17 +193,28 @@ __global__ void __launch_bounds__(INV_BT) k_batched_inverse_block(const double* 
                 }
                 for (; i < p; ++i) S[i * ld + t] = fma(-colk[i], rj, isk ? 0.0 : S[i * ld + t]);
                 S[k * ld + t] = rj;
-                // the owner of column k+1 scans it for the next pivot after
-                // its update (tracking the maximum inside the update loop of
-                // every column made the step 1.5x slower: that loop is bound
-                // by issue, not by the FP64 pipe)
-                if (t == k + 1) {
-                    long long bk = -2;
-                    int bnext = p;
-                    for (int i = k + 1; i < p; ++i) {
-                        const long long key = abs_key(S[i * ld + t]);
-                        if (key > bk) { bk = key; bnext = i; }
-                    }
+            }
+            // the warp owning column k+1 scans it for the next pivot right
+            // after its update: lanes over rows, then a shuffle reduction to
+            // the largest key, lowest row on ties (the owner's serial scan:
+            // 50.7 ms instead of 49.0 on the 30,000 matrices; tracking the
+            // maximum inside every column's update loop made the step 1.5x
+            // slower, that loop being bound by issue)
+            if (k + 1 < p && wid == ((k + 1) >> 5)) {
+                __syncwarp();
+                long long bk = -2;
+                int bnext = p;
+                for (int i = k + 1 + lane; i < p; i += 32) {
+                    const long long key = abs_key(S[i * ld + k + 1]);
+                    if (key > bk) { bk = key; bnext = i; }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bnext, o);
+                    if (ok > bk || (ok == bk && oi < bnext)) { bk = ok; bnext = oi; }
+                }
+                if (lane == 0) {
                     red[12] = bk >= 0 ? __longlong_as_double(bk) : -1.0;
                     red[13] = (double)(bk >= 0 ? bnext : p);
                 }
