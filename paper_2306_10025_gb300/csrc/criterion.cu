@@ -13,9 +13,16 @@
 //      ub + err < tol                                -> accept
 //   4. power iteration on E^T E from the largest row of E; every ||E v|| and
 //      ||E^T w|| / ||w|| is a lower bound; lb - err >= tol -> reject
-//   5. otherwise sigma_max(E) = sqrt(lambda_max(E^T E)) by cyclic Jacobi.
+//      (steps 3-4 first with E in FP32 and its rounding bound, an FP32
+//      Cholesky certificate on X I - G32 among them, then in FP64)
+//   5. Cholesky certificates on X I - G, G = fl(E^T E): a factorisation of
+//      X I - G - c I that succeeds proves lambda_max(G) < X -> accept; the
+//      first non-positive pivot of another gives a vector z with a lower
+//      bound ||E z|| / ||z|| -> reject
+//   6. the near ties left: sigma_max(E) = sqrt(lambda_max(E^T E)) by cyclic
+//      Jacobi.
 // err bounds the GEMM rounding, ||E_computed - E||_F <= p u ||D||_F ||B||_F,
-// so tests 2-4 decide "sigma_max(E_computed) < tol" exactly like step 5.
+// so tests 2-5 decide "sigma_max(E_computed) < tol" exactly like step 6.
 //
 // Alg. 1 in rounds.  Sequential Alg. 1 compares patch i with the entries in
 // creation order and takes the first with d < tol.  Every entry j was created
@@ -1906,7 +1913,8 @@ __global__ void k_entry_thresholds(const int32_t* __restrict__ rep_l, int m, Ske
 // screen them with the certified sketch bound (d >= tol), the warp decides
 // the survivors in entry order with the certified cascade against the best
 // distance so far (d < bs, on D staged in shared memory) and takes sigma_max
-// by the Jacobi eigenvalues only for those that beat it.  A zero distance
+// (exact_sigma_d_warp: a certified power iteration, Jacobi where the
+// certificate fails) only for those that beat it.  A zero distance
 // ends the search (nothing can be smaller; ties keep the lower entry), and
 // the evaluations counted are those made up to that point.
 template <int PM>
