@@ -2109,11 +2109,6 @@ int run_alg1(psr_ctx* ctx, cudaStream_t s, const double* seed_A, int m0, const i
         if (p > 32) {
             // block-per-candidate kernels (criterion_big.cu)
             if (m0 > 0) { set_error(ctx, "a seed database needs patches of at most 32 DOFs"); rc = PSR_ERR_INVALID_ARG; break; }
-            if (ctx->opts.match == PSR_MATCH_CLOSEST) {
-                set_error(ctx, "closest match handles patches of at most 32 DOFs");
-                rc = PSR_ERR_INVALID_ARG;
-                break;
-            }
             int fs = -1;
             const int64_t ev0 = total_evals, sc0 = total_screened;
             rc = run_alg1_big(ctx, G, Ag, s, &total_evals, &total_exact, &total_screened, &fs);

@@ -662,6 +662,185 @@ __device__ __forceinline__ bool screen_big(const float* __restrict__ yi, double 
     return rej;
 }
 
+// sigma_max(E), E = (A_c - A_i) B (A_c, A_i, B global, row stride p), for the
+// closest-match pass, all BT threads: D into sm.E, E = D B into Gs and back
+// into sm.E (row stride p + 1), lambda_max(E^T E) by power iteration from E's
+// largest row (the Rayleigh quotients rise to it; three steps gaining < 2^-50
+// or 300 steps), certified by a Cholesky factorisation of X I - G - c I with
+// G = fl(E^T E) (in Hs), X = lambda (1 + 2^-40) and c = 2 gamma_{p+1} tr
+// covering its backward error: lambda_max(G) < X, so sqrt(lambda) is within
+// 2^-41 of sigma_max.  Where the certificate fails, [lambda, tr G] is halved
+// with the same test (at most 60 times, to 2^-42 relative) and its midpoint
+// taken.  Returns 0 for E = 0, NaN when E holds a NaN.
+__device__ double sigma_big(const double* __restrict__ Ai, const double* __restrict__ Ac,
+                            const double* __restrict__ B, int p, BigSmem sm, double* Gs, double* Hs) {
+    const int r = threadIdx.x;
+    const bool act = r < p;
+    const int ld = p + 1;
+    double* E = sm.E;
+    __syncthreads();
+    if (act)
+        for (int k = 0; k < p; ++k) E[r * ld + k] = Ac[r * p + k] - Ai[r * p + k];
+    __syncthreads();
+    if (act)
+        for (int j = 0; j < p; ++j) {
+            double e = 0.0;
+            for (int k = 0; k < p; ++k) e = fma(E[r * ld + k], B[k * p + j], e);
+            Gs[r * p + j] = e;
+        }
+    __syncthreads();
+    if (act)
+        for (int j = 0; j < p; ++j) E[r * ld + j] = Gs[r * p + j];
+    __syncthreads();
+    double rn = 0.0;
+    if (act)
+        for (int j = 0; j < p; ++j) rn = fma(E[r * ld + j], E[r * ld + j], rn);
+    double best;
+    int br;
+    bargmax(act ? rn : -1.0, r, sm.red, sm.redi, &best, &br);
+    if (best != best) return best;                  // NaN (block-uniform)
+    if (!(best > 0.0)) return 0.0;
+    double* v = sm.v;
+    double* w = sm.w;
+    v[r] = act ? E[br * ld + r] / sqrt(best) : 0.0;
+    double lam = 0.0;
+    int quiet = 0;
+    for (int it = 0; it < 300 && quiet < 3; ++it) {
+        __syncthreads();
+        double wr = 0.0;
+        if (act)
+            for (int j = 0; j < p; ++j) wr = fma(E[r * ld + j], v[j], wr);
+        const double l2 = bsum(wr * wr, sm.red);
+        quiet = (l2 - lam <= 0x1p-50 * l2) ? quiet + 1 : 0;
+        lam = fmax(lam, l2);
+        w[r] = wr;
+        __syncthreads();
+        double uj = 0.0;
+        if (act)
+            for (int q = 0; q < p; ++q) uj = fma(E[q * ld + r], w[q], uj);
+        const double nu = sqrt(bsum(uj * uj, sm.red));
+        if (!(nu > 0.0)) break;
+        v[r] = act ? uj / nu : 0.0;
+    }
+    // G = E^T E into Hs, thread r column r
+    __syncthreads();
+    if (act)
+        for (int k = 0; k < p; ++k) {
+            double g = 0.0;
+            for (int q = 0; q < p; ++q) g = fma(E[q * ld + k], E[q * ld + r], g);
+            Hs[k * p + r] = g;
+        }
+    // lambda_max(G) < X proved when X I - G - c I factors (into Gs)
+    auto below = [&](double X) -> bool {
+        __syncthreads();
+        if (act)
+            for (int q = 0; q < p; ++q) Gs[q * p + r] = (q == r ? X : 0.0) - Hs[q * p + r];
+        __syncthreads();
+        const double tr = bsum(act ? Gs[r * p + r] : 0.0, sm.red);
+        if (!(tr > 0.0)) return false;
+        if (act) Gs[r * p + r] -= 2.0 * gamma_u(p + 1) * tr;
+        return cholesky_block(Gs, p) == p;
+    };
+    if (below(lam * (1.0 + 0x1p-40))) return sqrt(lam);
+    double lo = lam;
+    double hi = bsum(act ? Hs[r * p + r] : 0.0, sm.red) * (1.0 + 0x1p-40);
+    for (int it = 0; it < 60 && hi - lo > 0x1p-42 * hi; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (below(mid)) hi = mid;
+        else lo = mid;
+    }
+    return sqrt(0.5 * (lo + hi));
+}
+
+// Closest match (section 3.1, the variant after Alg. 1) for patches of
+// 33..128 DOFs, after the first-match rounds: a block per patch compares its
+// first match j0 with the later entries whose representative precedes it, in
+// entry order: the certified sketch screen (one warp), then the block's
+// certified decision against the best distance so far (tol until the first
+// match's own distance is needed), and sigma_max (sigma_big) for the first
+// match when a later entry passes and for the entries that pass.  A zero
+// distance ends the search; every entry after j0 up to the last one looked
+// at counts as an evaluation.  scratch: 2 p^2 doubles per block.
+__global__ void __launch_bounds__(BT) k_closest_pass_big(int count, int p, const double* __restrict__ Ag,
+                                                         const double* __restrict__ Ball,
+                                                         const double* __restrict__ fro_all,
+                                                         const double* __restrict__ w_all,
+                                                         const float* __restrict__ Y32, const double* __restrict__ den,
+                                                         const double* __restrict__ fa, const double* __restrict__ rho,
+                                                         const int32_t* __restrict__ rep_l, int m, double tol,
+                                                         int32_t* __restrict__ phi, double* __restrict__ scratch,
+                                                         unsigned long long* __restrict__ evals) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ float sy[SKB * SKD];
+    __shared__ double sden[SKB];
+    __shared__ int s_rej;
+    BigSmem sm = big_layout(smem, p);
+    const int64_t pp = (int64_t)p * p;
+    double* Gs = scratch + (int64_t)blockIdx.x * 2 * pp;
+    double* Hs = Gs + pp;
+    unsigned long long ev = 0;
+    for (int i = blockIdx.x; i < count; i += gridDim.x) {
+        const int j0 = phi[i];
+        if (rep_l[j0] == i) continue;               // an entry keeps its own patch
+        const double* Ai = Ag + (int64_t)i * pp;
+        const int r0 = rep_l[j0];
+        bool same = true;
+        for (int e = threadIdx.x; e < pp; e += blockDim.x)
+            same &= __double_as_longlong(Ag[(int64_t)r0 * pp + e]) == __double_as_longlong(Ai[e]);
+        double bs = __syncthreads_and(same) ? 0.0 : -1.0;   // -1: the first match's distance not known yet
+        int best = j0;
+        int lo = j0 + 1, hi = m;                   // entries j0 < j < jend: representative before i
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (rep_l[mid] > i) hi = mid;
+            else lo = mid + 1;
+        }
+        const int jend = lo;
+        int last = j0;
+        for (int jj = j0 + 1; jj < jend && bs != 0.0; ++jj) {
+            last = jj;
+            const int rj = rep_l[jj];
+            const double t = bs >= 0.0 ? bs : tol;
+            __syncthreads();
+            for (int q = threadIdx.x; q < SKB * SKD; q += blockDim.x) {
+                const int k = q / SKD, c = q % SKD;
+                sy[q] = (c < p) ? Y32[((int64_t)rj * SKB + k) * p + c] : 0.f;
+            }
+            if (threadIdx.x < SKB) sden[threadIdx.x] = den[(int64_t)rj * SKB + threadIdx.x];
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                const bool rej = screen_big(Y32 + (int64_t)i * SKB * p, fa[i], sy, sden, fa[rj], rho[rj], p, t);
+                if (threadIdx.x == 0) s_rej = rej ? 1 : 0;
+            }
+            __syncthreads();
+            if (s_rej) continue;
+            stage_b32(Ball + (int64_t)rj * pp, p, sm.B32);
+            __syncthreads();
+            const BigEntry en{Ag + (int64_t)rj * pp, Ball + (int64_t)rj * pp, sm.B32, w_all + (int64_t)rj * PBS,
+                              fro_all[rj]};
+            double dv;
+            bool ex;
+            int dec = decide_big(Ai, en, p, t, sm, Gs, Hs, &dv, &ex);
+            if (dec == 1 && bs < 0.0) {             // passes: the first match's distance is needed now
+                bs = sigma_big(Ai, Ag + (int64_t)r0 * pp, Ball + (int64_t)r0 * pp, p, sm, Gs, Hs);
+                if (bs == 0.0) break;
+                dec = decide_big(Ai, en, p, bs, sm, Gs, Hs, &dv, &ex);
+            }
+            if (dec == 1) {
+                const double sj = sigma_big(Ai, Ag + (int64_t)rj * pp, Ball + (int64_t)rj * pp, p, sm, Gs, Hs);
+                if (sj < bs) {
+                    bs = sj;
+                    best = jj;
+                }
+            }
+        }
+        ev += (unsigned long long)(last - j0);
+        if (threadIdx.x == 0) phi[i] = best;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && ev) atomicAdd(evals, ev);
+}
+
 struct RoundBig {
     int next, m, done, first_singular;
     int ticket, next_new, nsurv, pad;
@@ -953,6 +1132,37 @@ int run_alg1_big(psr_ctx* ctx, Group& G, const double* Ag, cudaStream_t s, int64
     *exact += (int64_t)h_st->exact;
     *screened += (int64_t)h_st->screened;
     *first_singular_local = h_st->first_singular;
+    if (ctx->opts.match == PSR_MATCH_CLOSEST && G.m > 1) {
+        // closest match: the entries stay, each patch moves to its closest
+        // passing entry (a block per patch)
+        unsigned long long* cev = nullptr;
+        BIG_CK(psr::dev_alloc(&cev, sizeof(unsigned long long)));
+        BIG_CK(cudaMemsetAsync(cev, 0, sizeof(unsigned long long), s));
+        if ((rc = set_big_smem((const void*)k_closest_pass_big, big_smem(p))) != PSR_OK) {
+            psr::dev_free(cev);
+            cleanup();
+            psr::dev_free(phi_l);
+            return rc;
+        }
+        count_launch();
+        k_closest_pass_big<<<std::max(1, std::min(count, decide_blocks)), BT, big_smem(p), s>>>(
+            count, p, Ag, Ball, fro_all, w_all, Y32, den, fa, rho, rep_l, G.m, tol, phi_l, scratch, cev);
+        {
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) {
+                psr::dev_free(cev);
+                rc = cuda_fail(ctx, e, "closest-match pass (p > 32)");
+                cleanup();
+                psr::dev_free(phi_l);
+                return rc;
+            }
+        }
+        unsigned long long h_cev = 0;
+        BIG_CK(cudaMemcpyAsync(&h_cev, cev, sizeof(h_cev), cudaMemcpyDeviceToHost, s));
+        BIG_CK(cudaStreamSynchronize(s));
+        psr::dev_free(cev);
+        *evals += (int64_t)h_cev;
+    }
     std::vector<int32_t> hrep(G.m);
     BIG_CK(cudaMemcpyAsync(hrep.data(), rep_l, sizeof(int32_t) * G.m, cudaMemcpyDeviceToHost, s));
     double* Bdb = nullptr;

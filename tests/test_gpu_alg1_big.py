@@ -338,3 +338,37 @@ def test_split_rounds_path_bit_exact(lib, search):
             ctx.destroy()
     finally:
         lib.psr_debug_inject("rounds_split", 0)
+
+
+@pytest.mark.parametrize("case", ["jitter5", "q5"])
+def test_closest_match_big_groups(lib, case):
+    """Closest match for patches of 33..128 DOFs (a block per patch after the
+    rounds, sigma_max by a certified power iteration): the representatives
+    are Alg. 1's and phi the oracle's alg1_closest_match, per size group; the
+    cases move patches away from their first match."""
+    if case == "jitter5":
+        pr, tols = P.stokes3d_q2q1(5, seed=1), [15.0, 22.0]
+        groups = _groups(pr)
+    else:
+        pr, tols = P.smooth2d_qp(N=10, p=5), [0.2, 2.0]
+        groups = [(36, np.arange(pr.n_patches), O.extract_patches(pr.rowptr, pr.colidx, pr.vals, pr.n,
+                                                                   pr.dofs2d()))]
+    moved = 0
+    for tol in tols:
+        refs = [O.alg1_closest_match(A, tol) for _, _, A in groups]
+        for r in refs:
+            assert r["near_ties"] == []
+        ctx = ctx_for(lib, pr, tol=tol, weighting="left", krylov="fgmres", match="closest")
+        phi, reps, m = ctx.assignment()
+        phi = phi.cpu().numpy()
+        reps = reps.cpu().numpy()
+        base = 0
+        for (s, idx, A), r in zip(groups, refs):
+            mg = len(r["reps"])
+            assert np.array_equal(phi[idx] - base, r["phi"]), (case, tol, s)
+            assert np.array_equal(reps[base:base + mg], idx[r["reps"]]), (case, tol, s)
+            moved += int((r["phi"] != O.alg1(A, tol)["phi"]).sum())
+            base += mg
+        assert m == base
+        ctx.destroy()
+    assert moved >= 10
