@@ -358,6 +358,13 @@ int psr_detect_patches(const psr_csr* A, int32_t row_nnz, int32_t* dofs, int32_t
  * use by live contexts are not touched).  Returns PSR_OK or PSR_ERR_CUDA. */
 int psr_release_cached_memory(void);
 
+/* Bytes of device and of pinned host memory the library's allocator has
+ * handed out and not taken back (cached blocks excluded): contexts, networks
+ * and the buffers of calls in progress on any thread.  A setup that fails
+ * frees what its steps held, so the figures return to their value before
+ * the call.  Either pointer (host) may be NULL.  Returns PSR_OK. */
+int psr_memory_in_use(int64_t* device_bytes, int64_t* host_bytes);
+
 /* Fault injection for tests of the failure paths (the paper has no
  * counterpart).  Nothing here makes a GPU fault: the failures are made on
  * the host or by a bounded wait that runs out.

@@ -37,7 +37,7 @@ EXPORTS = ["psr_default_opts", "psr_setup", "psr_apply", "psr_solve", "psr_get_h
            "psr_setup_seeded", "psr_features", "psr_mlp_create", "psr_mlp_num_params", "psr_mlp_set_params",
            "psr_mlp_get_params", "psr_mlp_loss_grad", "psr_mlp_train_step", "psr_mlp_predict", "psr_mlp_destroy",
            "psr_criterion_noalloc", "psr_set_kernel_timing", "psr_get_kernel_timing", "psr_setup_kmeans",
-           "psr_export_database", "psr_set_coarse", "psr_smooth", "psr_release_cached_memory",
+           "psr_export_database", "psr_set_coarse", "psr_smooth", "psr_release_cached_memory", "psr_memory_in_use",
            "psr_detect_patches", "psr_boundary_classes", "psr_default_train_opts", "psr_mlp_train", "psr_ctx_mlp",
            "psr_setup_learned", "psr_debug_inject"]
 
@@ -138,6 +138,7 @@ def load(path: str = LIB_PATH):
     lib.psr_criterion_noalloc.argtypes = [vp, i32, i32, vp, vp, d, vp, vp, vp]
     lib.psr_kernel_launches.argtypes = []
     lib.psr_release_cached_memory.argtypes = []
+    lib.psr_memory_in_use.argtypes = [vp, vp]
     lib.psr_detect_patches.argtypes = [C.POINTER(psr_csr), i32, vp, i32, C.POINTER(i32), vp]
     lib.psr_set_kernel_timing.argtypes = [vp, i32]
     lib.psr_get_kernel_timing.argtypes = [vp, vp, vp, vp, vp, i32]
@@ -577,6 +578,14 @@ def psr_boundary_classes(rowptr, colidx, vals, dofs, offsets=None, uniform_size=
 def psr_release_cached_memory() -> None:
     """Return the library's cached device and pinned host blocks to the driver."""
     _check(load().psr_release_cached_memory())
+
+
+def psr_memory_in_use() -> tuple[int, int]:
+    """(device bytes, pinned host bytes) the library's allocator has handed
+    out and not taken back."""
+    d, h = C.c_int64(), C.c_int64()
+    _check(load().psr_memory_in_use(C.byref(d), C.byref(h)))
+    return d.value, h.value
 
 
 def exported_symbols(path: str = LIB_PATH) -> list[str]:

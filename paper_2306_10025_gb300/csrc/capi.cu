@@ -125,6 +125,7 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
     auto t_all = std::chrono::steady_clock::now();
     const int nvtx_base = g_nvtx_depth;
     phase_begin("psr_setup");
+    AllocScope scope;                              // a failed setup frees what its steps still hold
     psr_ctx* ctx = new psr_ctx();
     *out = nullptr;
     if (o) ctx->opts = *o; else psr_default_opts(&ctx->opts);
@@ -384,6 +385,7 @@ static int setup_impl(const psr_csr* A, const psr_patches* P, const psr_opts* o,
         (void)t_all;
         *out = ctx;
         phases_close(nvtx_base);
+        scope.commit();
         return PSR_OK;
     }
 fail:

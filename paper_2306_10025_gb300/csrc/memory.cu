@@ -79,6 +79,9 @@ void release_all(Pool& P, bool host) {
 // allocation fails as if the device were out of memory.
 std::atomic<long long> g_fail_countdown{0};
 
+// The open AllocScope of this thread (null: none, or paused).
+thread_local std::unordered_map<void*, bool>* t_scope = nullptr;
+
 cudaError_t alloc_impl(void** p, size_t bytes, bool host) {
     *p = nullptr;
     if (!host && g_fail_countdown.load(std::memory_order_relaxed) > 0 &&
@@ -106,6 +109,7 @@ cudaError_t alloc_impl(void** p, size_t bytes, bool host) {
         P.cached.erase(*p);
         P.cached_bytes -= got;
         P.live[*p] = got;
+        if (t_scope) (*t_scope)[*p] = host;
         return cudaSuccess;
     }
     cudaError_t e = host ? cudaMallocHost(p, n) : cudaMalloc(p, n);
@@ -117,11 +121,13 @@ cudaError_t alloc_impl(void** p, size_t bytes, bool host) {
     }
     if (e != cudaSuccess) { *p = nullptr; return e; }
     P.live[*p] = n;
+    if (t_scope) (*t_scope)[*p] = host;
     return cudaSuccess;
 }
 
 cudaError_t free_impl(void* p, bool host) {
     if (!p) return cudaSuccess;
+    if (t_scope) t_scope->erase(p);
     Cache& C = cache();
     std::lock_guard<std::mutex> lk(C.mu);
     auto& pools = host ? C.host : C.dev;
@@ -154,12 +160,43 @@ cudaError_t free_impl(void* p, bool host) {
 
 void inject_alloc_fail(long long k) { g_fail_countdown.store(k, std::memory_order_relaxed); }
 
+AllocScope::AllocScope() : prev_(t_scope) { t_scope = &held_; }
+
+AllocScope::~AllocScope() {
+    t_scope = prev_;
+    if (committed_) {
+        if (prev_)
+            for (auto& kv : held_) (*prev_)[kv.first] = kv.second;
+        return;
+    }
+    std::unordered_map<void*, bool> left;
+    left.swap(held_);
+    for (auto& kv : left) free_impl(kv.first, kv.second);
+}
+
+AllocPause::AllocPause() : prev_(t_scope) { t_scope = nullptr; }
+AllocPause::~AllocPause() { t_scope = prev_; }
+
 cudaError_t dev_alloc(void** p, size_t bytes) { return alloc_impl(p, bytes, false); }
 cudaError_t dev_free(void* p) { return free_impl(p, false); }
 cudaError_t host_alloc(void** p, size_t bytes) { return alloc_impl(p, bytes, true); }
 cudaError_t host_free(void* p) { return free_impl(p, true); }
 
 }  // namespace psr
+
+extern "C" int psr_memory_in_use(int64_t* device_bytes, int64_t* host_bytes) {
+    using namespace psr;
+    Cache& C = cache();
+    std::lock_guard<std::mutex> lk(C.mu);
+    int64_t d = 0, h = 0;
+    for (auto& kv : C.dev)
+        for (auto& b : kv.second.live) d += (int64_t)b.second;
+    for (auto& kv : C.host)
+        for (auto& b : kv.second.live) h += (int64_t)b.second;
+    if (device_bytes) *device_bytes = d;
+    if (host_bytes) *host_bytes = h;
+    return PSR_OK;
+}
 
 extern "C" int psr_release_cached_memory(void) {
     using namespace psr;

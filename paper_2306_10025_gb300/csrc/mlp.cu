@@ -223,6 +223,7 @@ __global__ void k_features(const double* __restrict__ A, int npch, int p, const 
 
 static int ensure_cap(psr_mlp* net, int Bn) {
     if (Bn <= net->cap) return PSR_OK;
+    psr::AllocPause keep;                  // the network owns these beyond the calling setup
     for (float* p : {net->Z1, net->H1, net->Z2, net->H2, net->L, net->G1, net->G2, net->G3, net->loss_part}) psr::dev_free(p);
     psr::dev_free(net->cnt);
     const size_t bh = (size_t)Bn * net->h, bm = (size_t)Bn * net->m;
@@ -285,6 +286,7 @@ extern "C" {
 
 int psr_mlp_create(int32_t in_dim, int32_t hidden, int32_t classes, psr_mlp** out) {
     if (!out || in_dim < 1 || hidden < 1 || classes < 1) { set_error(nullptr, "invalid MLP shape"); return PSR_ERR_INVALID_ARG; }
+    psr::AllocPause keep;                  // the network outlives any call that creates it
     psr_mlp* net = new psr_mlp();
     net->d = in_dim;
     net->h = hidden;

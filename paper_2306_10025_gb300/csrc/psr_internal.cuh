@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/psr.h"
@@ -74,6 +75,34 @@ template <class T>
 inline cudaError_t dev_alloc(T** p, size_t bytes) { return dev_alloc(reinterpret_cast<void**>(p), bytes); }
 template <class T>
 inline cudaError_t host_alloc(T** p, size_t bytes) { return host_alloc(reinterpret_cast<void**>(p), bytes); }
+
+// Blocks handed out on this thread while an AllocScope is open are recorded
+// in it and a free removes them; a scope that ends without commit() frees
+// the blocks it still holds (the locals of a call that failed part-way), a
+// committed one passes them to the enclosing scope.  AllocPause stops the
+// recording for buffers of objects that outlive the call (a network's
+// activations grown during a setup).
+class AllocScope {
+public:
+    AllocScope();
+    ~AllocScope();
+    AllocScope(const AllocScope&) = delete;
+    AllocScope& operator=(const AllocScope&) = delete;
+    void commit() { committed_ = true; }
+private:
+    std::unordered_map<void*, bool> held_;   // block -> pinned host (else device)
+    std::unordered_map<void*, bool>* prev_;
+    bool committed_ = false;
+};
+class AllocPause {
+public:
+    AllocPause();
+    ~AllocPause();
+    AllocPause(const AllocPause&) = delete;
+    AllocPause& operator=(const AllocPause&) = delete;
+private:
+    std::unordered_map<void*, bool>* prev_;
+};
 
 // ------------------------------------------------------- device helpers
 __device__ __forceinline__ double warp_sum(double v) {

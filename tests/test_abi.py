@@ -73,6 +73,8 @@ def test_debug_inject_arguments_without_device():
     assert lib.psr_debug_inject(1, 0) == 0
     assert lib.psr_debug_inject(3, 1) == 0
     assert lib.psr_debug_inject(3, 0) == 0
+    d, h = L.psr_memory_in_use()
+    assert d >= 0 and h >= 0
     assert lib.psr_debug_inject(7, 1) == -1
     assert lib.psr_debug_inject(1, -1) == -1
     import torch

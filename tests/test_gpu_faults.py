@@ -50,7 +50,10 @@ def check_correct(lib, pr, tol):
 
 @pytest.mark.parametrize("k", [1, 2, 3, 5, 8, 13, 21, 34])
 def test_injected_allocation_failure(lib, k):
+    """The failing setup returns PSR_ERR_OOM and gives back every block it
+    had taken (the library's memory in use is what it was before)."""
     pr = P.poisson2d_q2(8)
+    before = lib.psr_memory_in_use()
     lib.psr_debug_inject("alloc_fail", k)
     try:
         ctx = setup(lib, pr, tol=1e-12, weighting="sym", krylov="cg")
@@ -59,7 +62,29 @@ def test_injected_allocation_failure(lib, k):
     else:                                    # the setup needed fewer allocations than k
         ctx.destroy()
     lib.psr_debug_inject("alloc_fail", 0)
+    assert lib.psr_memory_in_use() == before
     check_correct(lib, pr, 1e-12)
+
+
+@pytest.mark.parametrize("k", [1, 4, 9, 16, 25, 36])
+def test_injected_allocation_failure_large_patches(lib, k):
+    """The same on the 3D Stokes patches (33..128 DOFs: the block kernels'
+    own buffers) with the closest-match pass."""
+    pr = P.stokes3d_q2q1(4, seed=3)
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    args = (t(pr.rowptr, torch.int32), t(pr.colidx, torch.int32), t(pr.vals, torch.float64),
+            t(pr.patch_dofs, torch.int32))
+    opts = lib.make_opts(tol=22.0, weighting="left", krylov="fgmres", match="closest")
+    before = lib.psr_memory_in_use()
+    lib.psr_debug_inject("alloc_fail", k)
+    try:
+        ctx = lib.psr_setup(*args, offsets=t(pr.patch_offsets, torch.int32), opts=opts)
+    except lib.PsrError as e:
+        assert "PSR_ERR_OOM" in str(e)
+    else:
+        ctx.destroy()
+    lib.psr_debug_inject("alloc_fail", 0)
+    assert lib.psr_memory_in_use() == before
 
 
 def test_barrier_wait_runs_out(lib):
