@@ -579,6 +579,7 @@ __global__ void __launch_bounds__(BT) k_patch_norms_big(const double* __restrict
         int br;
         bargmax(act ? rn : -1.0, r, red, redi, &best, &br);
         double lo = 0.0, hi = 0.0;
+        if (best != best) lo = best;                // a NaN patch: widened to [0, inf] below
         if (best > 0.0) {
             v[r] = act ? E[br * ld + r] / sqrt(best) : 0.0;
             double lam = 0.0;

@@ -122,3 +122,25 @@ def test_nan_in_matrix_is_a_singular_patch(lib):
     named = int(str(e.value).split("patch ")[1].split(" ")[0])
     assert named in patches
     check_correct(lib, pr, 1e-12)
+
+
+@pytest.mark.parametrize("case", ["poisson", "stokes3d"])
+def test_nan_with_norm_window_search(lib, case):
+    """A NaN entry under the norm-window search (warp and block norm
+    kernels): the NaN patch's norm bracket widens to [0, inf] instead of
+    poisoning the window tests, and the setup reports a singular patch."""
+    pr = P.poisson2d_q2(8) if case == "poisson" else P.stokes3d_q2q1(4, seed=3)
+    vals = pr.vals.copy()
+    row = int(pr.patch_dofs[5])
+    vals[int(pr.rowptr[row])] = np.nan
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    args = (t(pr.rowptr, torch.int32), t(pr.colidx, torch.int32), t(vals, torch.float64),
+            t(pr.patch_dofs, torch.int32))
+    tol = 1e-12 if case == "poisson" else 22.0
+    opts = lib.make_opts(tol=tol, weighting=pr.weighting, krylov=pr.krylov, search="norm_window")
+    with pytest.raises(lib.PsrError) as e:
+        if pr.uniform_size:
+            lib.psr_setup(*args, uniform_size=pr.uniform_size, opts=opts)
+        else:
+            lib.psr_setup(*args, offsets=t(pr.patch_offsets, torch.int32), opts=opts)
+    assert "PSR_ERR_SINGULAR_PATCH" in str(e.value)
