@@ -947,7 +947,7 @@ def run_exp1(args):
         prow, pcol, pval, n0 = pr.meta["P0"]
         P0 = (t(prow, torch.int32), t(pcol, torch.int32), t(pval, torch.float64), n0)
         b = t(pr.meta["b"], torch.float64)
-        tols = (0.0,) if pr.uniform_size > 32 else (0.0, 0.02, 0.05, 0.1, 0.2)
+        tols = (0.0, 0.02, 0.05, 0.1, 0.2)
         for tol in tols:
             opts = L.make_opts(tol=tol, store_prec="fp64", weighting="left", krylov="fgmres", restart=20,
                                rtol=1e-8, maxit=1000)
