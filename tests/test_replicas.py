@@ -1,6 +1,6 @@
-"""N > 1: the benchmark runs independent replicas (the path needs no data
-exchange in this build); the whole-job value is the units of all ranks over
-the slowest rank's time.  Two gloo ranks on CPU."""
+"""N > 1: the benchmark runs independent replicas (one GPU per replica, no
+data exchange between them); the whole-job value is the units of all ranks
+over the slowest rank's time.  Two gloo ranks on CPU."""
 import os
 import socket
 
