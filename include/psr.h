@@ -180,9 +180,13 @@ typedef struct {
  * larger sizes first.  Groups in which every patch is its own entry are
  * stored column-major and streamed (one launch over all of them).  The CSR
  * and map are copied; the caller may free them afterwards.
- * On success *out owns all derived storage.  Errors: INVALID_ARG,
- * UNSORTED_CSR, UNCOVERED_DOF, SINGULAR_PATCH (psr_last_error names the
- * patch), OOM, CUDA.  Blocks the host. */
+ * opts->match and opts->search pick Alg. 1's rule (first or closest match)
+ * and search (creation order or the norm window); the norm window takes
+ * first match and the spectral criterion (INVALID_ARG otherwise).
+ * On success *out owns all derived storage; on failure every block the call
+ * took is given back.  Errors: INVALID_ARG, UNSORTED_CSR, UNCOVERED_DOF,
+ * SINGULAR_PATCH (psr_last_error names the patch), OOM, TIMEOUT (a bounded
+ * wait of the Alg. 1 rounds gave up), CUDA.  Blocks the host. */
 int psr_setup(const psr_csr* A, const psr_patches* patches, const psr_opts* opts,
               void* stream, psr_ctx** out);
 
@@ -193,8 +197,9 @@ int psr_setup(const psr_csr* A, const psr_patches* patches, const psr_opts* opts
  * n_patches entries in [-1, m0); patch i with hints[i] >= 0 is first compared
  * with that entry (one criterion evaluation) and assigned to it when
  * d < tol; every other patch runs Alg. 1 against the database in creation
- * order (seed entries first) and may append new entries.  Needs tol > 0 and
- * patches of one size p <= 32.  psr_get_stats reports the hits. */
+ * order (seed entries first) and may append new entries.  Needs tol > 0,
+ * patches of one size p <= 32, first match and the creation-order search.
+ * psr_get_stats reports the hits. */
 int psr_setup_seeded(const psr_csr* A, const psr_patches* patches, const psr_opts* opts,
                      const double* seed_A, int32_t m0, const int32_t* hints, void* stream,
                      psr_ctx** out);
