@@ -110,3 +110,49 @@ def test_struct_layouts_match_header(tmp_path):
     subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
     assert got == want
+
+
+def test_option_constants_match_header(tmp_path):
+    """The binding's option names map to the header's #define values (a C
+    program built against include/psr.h prints them)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_2306_10025_gb300 import binding as B
+    groups = {"PREC": ("PSR_PREC_", {"fp64": "FP64", "fp32": "FP32", "bf16": "BF16"}),
+              "WEIGHT": ("PSR_WEIGHT_", {"left": "LEFT", "sym": "SYM"}),
+              "KRYLOV": ("PSR_KRYLOV_", {"cg": "CG", "fgmres": "FGMRES"}),
+              "SWEEP": ("PSR_SWEEP_", {"auto": "AUTO", "grouped": "GROUPED", "pergroup": "PERGROUP",
+                                       "tensor": "TENSOR"}),
+              "ORTHO": ("PSR_ORTHO_", {"auto": "AUTO", "fp64": "FP64", "split": "SPLIT"}),
+              "CRITERION": ("PSR_CRITERION_", {"spectral": "SPECTRAL", "l1": "L1", "varmin": "VARMIN"}),
+              "FP64_ARITH": ("PSR_FP64_", {"pairs": "PAIRS", "native": "NATIVE"}),
+              "MATCH": ("PSR_MATCH_", {"first": "FIRST", "closest": "CLOSEST"}),
+              "SEARCH": ("PSR_SEARCH_", {"creation": "CREATION", "norm_window": "NORM_WINDOW"}),
+              "INJECT": ("PSR_INJECT_", {"alloc_fail": "ALLOC_FAIL", "barrier_wait": "BARRIER_WAIT",
+                                         "rounds_split": "ROUNDS_SPLIT"})}
+    body = ["#include <stdio.h>", '#include "psr.h"', "int main(void) {"]
+    want = []
+    for dict_name, (prefix, names) in groups.items():
+        d = getattr(B, dict_name)
+        assert set(d) == set(names), dict_name
+        for key, suffix in names.items():
+            body.append(f'printf("%d\\n", (int){prefix}{suffix});')
+            want.append(d[key])
+    for code, name in B.ERRORS.items():
+        body.append(f'printf("%d\\n", (int){name});')
+        want.append(code)
+    for k, name in enumerate(B.KT_CLASSES):
+        body.append(f'printf("%d\\n", (int)PSR_KT_{name.upper()});')
+        want.append(k)
+    body.append('printf("%d\\n", (int)PSR_KT_COUNT);')
+    want.append(len(B.KT_CLASSES))
+    body += ["return 0;", "}"]
+    src = tmp_path / "consts.c"
+    src.write_text("\n".join(body) + "\n")
+    exe = tmp_path / "consts"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == want
