@@ -156,3 +156,48 @@ def test_option_constants_match_header(tmp_path):
     subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
     assert got == want
+
+
+def test_plain_c_program_links_and_calls(tmp_path):
+    """A C program built against include/psr.h and linked with libpsr.so
+    (no Python, no torch): the defaults of psr_default_opts, argument
+    checks before any device work, the error text, and the allocator's
+    figures."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2306_10025_gb300 as L
+    libdir = os.path.dirname(L.LIB_PATH)
+    src = tmp_path / "use.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include <string.h>
+#include "psr.h"
+int main(void) {
+    psr_opts o;
+    memset(&o, 0xff, sizeof o);
+    psr_default_opts(&o);
+    printf("%g %d %d %d %d %g %d %d %d %d\n", o.tol, o.store_prec, o.weighting, o.krylov, o.restart, o.rtol,
+           o.maxit, o.match, o.search, o.criterion);
+    psr_ctx* ctx = (psr_ctx*)1;
+    int rc = psr_setup(NULL, NULL, &o, NULL, &ctx);
+    printf("%d %d %d\n", rc, ctx == NULL, psr_last_error(NULL) != NULL && strlen(psr_last_error(NULL)) > 0);
+    int64_t d = -1, h = -1;
+    rc = psr_memory_in_use(&d, &h);
+    printf("%d %lld %lld\n", rc, (long long)d, (long long)h);
+    return 0;
+}
+""")
+    exe = tmp_path / "use"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lpsr",
+                    "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    tol, prec, w, kr, restart, rtol, maxit, match, search, crit = out[0].split()
+    assert float(tol) == 0.0 and int(prec) == 0 and int(w) == 1 and int(kr) == 0 and int(restart) == 30
+    assert float(rtol) == 1e-8 and int(maxit) == 10000 and int(match) == 0 and int(search) == 0 and int(crit) == 0
+    assert out[1].split() == ["-1", "1", "1"]
+    assert out[2].split() == ["0", "0", "0"]
